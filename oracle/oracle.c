@@ -1,0 +1,248 @@
+/*
+ * CPU ORACLE -- test infrastructure only.  Only tests, the smoke check and the
+ * benchmark's CPU-baseline leg may call this code; the rendering library never
+ * does, and this file shares nothing with it.
+ *
+ * Plain, slow, obviously-correct statements of what the method computes:
+ *   - the render (visibility) pass of the multi-attribute compute rasterizer:
+ *     per pixel, the closest point with the lowest depth (Sec. 3.2), as a
+ *     sequential min over all points of a 64-bit key (depth bits, point index);
+ *   - the resolve pass: copy the winning point's attributes, depth and
+ *     coverage into G-buffer planes, no colour averaging (Sec. 3.2);
+ *   - packing of the G-buffer into the network's input tensor (the paper's
+ *     "channel-wise processing" of the rasterizer output, Sec. 4.5, Tab. 3);
+ *   - a front-to-back alpha-compositing Gaussian splat renderer that stands in
+ *     for the Gaussian Renderer that makes training targets (Sec. 4.2).
+ *
+ * Compiled with -ffp-contract=off -fno-fast-math: every float multiply, add
+ * and divide below is a separately rounded IEEE operation.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+static inline uint32_t fbits(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+static inline float bitsf(uint32_t u) { float f; memcpy(&f, &u, 4); return f; }
+
+/*
+ * Render pass (Sec. 3.2): world -> screen, then keep per pixel the point with the
+ * smallest depth, ties to the lowest index.  The key is (bits(w) << 32) | i where
+ * w is the clip-space w (eye-space depth, positive in front of the camera); for
+ * positive floats the bit pattern orders like the value.  Pixel row 0 is the top.
+ * M is row-major, clip = M * (x, y, z, 1).  key[H*W] is overwritten; empty = ~0.
+ */
+void oracle_visibility(const float* xyz, uint64_t n, const float* M, int W, int H, float znear,
+                       float zfar, uint64_t* key) {
+    for (int64_t p = 0; p < (int64_t)W * H; ++p) key[p] = ~0ull;
+    const float hw = 0.5f * (float)W, hh = 0.5f * (float)H;
+    for (uint64_t i = 0; i < n; ++i) {
+        float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+        float cx = ((M[0] * x + M[1] * y) + M[2] * z) + M[3];
+        float cy = ((M[4] * x + M[5] * y) + M[6] * z) + M[7];
+        float cw = ((M[12] * x + M[13] * y) + M[14] * z) + M[15];
+        if (!(cw >= znear && cw <= zfar)) continue;
+        float nx = cx / cw, ny = cy / cw;
+        float sx = (nx + 1.0f) * hw, sy = (1.0f - ny) * hh;
+        if (!(sx >= 0.0f && sx < (float)W && sy >= 0.0f && sy < (float)H)) continue;
+        int px = (int)sx, py = (int)sy;
+        uint64_t k = ((uint64_t)fbits(cw) << 32) | (uint64_t)i;
+        int64_t p = (int64_t)py * W + px;
+        if (k < key[p]) key[p] = k;
+    }
+}
+
+/*
+ * Resolve pass (Sec. 3.2): for each pixel with a winner, depth = high key word,
+ * mask = 1, attribute word c = word c of the winner's record (bit copy).  Empty
+ * pixels get zeros everywhere.  gattr is planar: gattr[c * npx + p].
+ */
+void oracle_resolve(const uint64_t* key, int64_t npx, const uint32_t* attr, int64_t stride_words,
+                    int K, uint32_t* depth, uint8_t* mask, uint32_t* gattr) {
+    for (int64_t p = 0; p < npx; ++p) {
+        uint64_t k = key[p];
+        if (k == ~0ull) {
+            depth[p] = 0u; mask[p] = 0u;
+            for (int c = 0; c < K; ++c) gattr[(int64_t)c * npx + p] = 0u;
+        } else {
+            uint64_t i = k & 0xFFFFFFFFull;
+            depth[p] = (uint32_t)(k >> 32); mask[p] = 1u;
+            for (int c = 0; c < K; ++c) gattr[(int64_t)c * npx + p] = attr[i * stride_words + c];
+        }
+    }
+}
+
+/* float32 -> bfloat16, round to nearest even (the format's definition). */
+uint16_t oracle_bf16(float f) {
+    uint32_t u = fbits(f);
+    if ((u & 0x7FFFFFFFu) > 0x7F800000u) return (uint16_t)((u >> 16) | 0x40u);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+/*
+ * float32 -> FP8 E4M3 (OCP "fn" variant: bias 7, no infinities, max 448,
+ * subnormal step 2^-9), round to nearest even, saturating to +-448, NaN -> 0x7F.
+ */
+uint8_t oracle_e4m3(float f) {
+    if (isnan(f)) return 0x7F;
+    uint8_t s = signbit(f) ? 0x80 : 0x00;
+    double a = fabs((double)f);
+    if (a >= 448.0) return s | 0x7E;
+    int e;
+    double q;                        /* grid spacing around a */
+    if (a < 0x1.0p-6) { e = -6; q = 0x1.0p-9; }
+    else { frexp(a, &e); e -= 1; q = ldexp(1.0, e - 3); }
+    double r = nearbyint(a / q) * q; /* ties to even under the default rounding mode */
+    if (r >= 448.0) return s | 0x7E;
+    if (r < 0x1.0p-6) return s | (uint8_t)(r / 0x1.0p-9);          /* subnormal or zero */
+    int er;
+    double mr = frexp(r, &er);       /* r = mr * 2^er, mr in [0.5, 1) */
+    int exp_field = er - 1 + 7;
+    int man = (int)((mr * 2.0 - 1.0) * 8.0);
+    return s | (uint8_t)(exp_field << 3) | (uint8_t)man;
+}
+
+/*
+ * Pack the G-buffer into the network input, NHWC with cpad channels over an
+ * Hn x Wn canvas (Hn >= H, Wn >= W; the margin is zero).  Channel order: the
+ * nch attribute channels, then depth, then coverage, then zeros.  Attribute
+ * channel j reads G-buffer word ch_word[j] as f32 (fmt 0), u32 (fmt 1) or byte
+ * ch_comp[j] of a u8x4 word (fmt 2), converts it to float and applies
+ * f = v * scale + offset (separate multiply and add).  Depth is the float whose
+ * bits are the depth plane, scaled the same way; coverage is 1.  Empty pixels
+ * are all zero.  out_fmt 0 = f32, 1 = bf16 (RNE), 2 = e4m3 of f * in_scale_inv.
+ */
+void oracle_pack(const uint32_t* depth, const uint8_t* mask, const uint32_t* gattr, int H, int W,
+                 int Hn, int Wn, int nch, const int* ch_word, const int* ch_fmt, const int* ch_comp,
+                 const float* ch_scale, const float* ch_offset, float d_scale, float d_offset,
+                 int cpad, int out_fmt, float in_scale_inv, void* out) {
+    int64_t npx = (int64_t)H * W;
+    float* vals = (float*)malloc(sizeof(float) * (size_t)cpad);
+    for (int y = 0; y < Hn; ++y)
+        for (int x = 0; x < Wn; ++x) {
+            for (int c = 0; c < cpad; ++c) vals[c] = 0.0f;
+            if (y < H && x < W && mask[(int64_t)y * W + x]) {
+                int64_t p = (int64_t)y * W + x;
+                for (int j = 0; j < nch; ++j) {
+                    uint32_t w = gattr[(int64_t)ch_word[j] * npx + p];
+                    float v;
+                    if (ch_fmt[j] == 0) v = bitsf(w);
+                    else if (ch_fmt[j] == 1) v = (float)w;
+                    else v = (float)((w >> (8 * ch_comp[j])) & 255u);
+                    float t = v * ch_scale[j];
+                    vals[j] = t + ch_offset[j];
+                }
+                float t = bitsf(depth[p]) * d_scale;
+                vals[nch] = t + d_offset;
+                vals[nch + 1] = 1.0f;
+            }
+            int64_t o = ((int64_t)y * Wn + x) * cpad;
+            for (int c = 0; c < cpad; ++c) {
+                if (out_fmt == 0) ((float*)out)[o + c] = vals[c];
+                else if (out_fmt == 1) ((uint16_t*)out)[o + c] = oracle_bf16(vals[c]);
+                else ((uint8_t*)out)[o + c] = oracle_e4m3(vals[c] * in_scale_inv);
+            }
+        }
+    free(vals);
+}
+
+/* ---------------------------------------------------------------------------
+ * Gaussian splat renderer (stands in for the Gaussian Renderer of Sec. 4.2).
+ * Every point whose centre projects (same FP32 sequence as above, up to sx, sy)
+ * within 3 sigma of the image is an isotropic 2-D Gaussian at the continuous
+ * centre (sx, sy).  Points are ordered by (w, index) ascending.  For each pixel
+ * centre p = (px + 0.5, py + 0.5), walking that order over the Gaussians with
+ * |p - mu|^2 <= (3 sigma)^2:  a = alpha * exp(-|p - mu|^2 / (2 sigma^2)),
+ * C += T * a * c, T *= (1 - a), stopping once T < 1e-4.  Black background.
+ * Double precision; tiles of 16 x 16 pixels are independent (OpenMP).
+ * ------------------------------------------------------------------------- */
+typedef struct { float w; uint32_t i; double sx, sy; } splat_t;
+
+static int splat_cmp(const void* a, const void* b) {
+    const splat_t* x = (const splat_t*)a;
+    const splat_t* y = (const splat_t*)b;
+    if (x->w < y->w) return -1;
+    if (x->w > y->w) return 1;
+    return (x->i > y->i) - (x->i < y->i);
+}
+
+void oracle_splat(const float* xyz, uint64_t n, const float* M, int W, int H, float znear,
+                  float zfar, const float* colour, double sigma, double alpha, double* out) {
+    const double rad = 3.0 * sigma, rad2 = rad * rad;
+    const float hw = 0.5f * (float)W, hh = 0.5f * (float)H;
+    splat_t* s = (splat_t*)malloc(sizeof(splat_t) * (size_t)(n > 0 ? n : 1));
+    uint64_t m = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+        float cx = ((M[0] * x + M[1] * y) + M[2] * z) + M[3];
+        float cy = ((M[4] * x + M[5] * y) + M[6] * z) + M[7];
+        float cw = ((M[12] * x + M[13] * y) + M[14] * z) + M[15];
+        if (!(cw >= znear && cw <= zfar)) continue;
+        float nx = cx / cw, ny = cy / cw;
+        float sx = (nx + 1.0f) * hw, sy = (1.0f - ny) * hh;
+        if (!((double)sx >= -rad && (double)sx < W + rad && (double)sy >= -rad && (double)sy < H + rad))
+            continue;
+        s[m].w = cw; s[m].i = (uint32_t)i; s[m].sx = sx; s[m].sy = sy; ++m;
+    }
+    qsort(s, (size_t)m, sizeof(splat_t), splat_cmp);
+    const int T = 16;
+    int tx = (W + T - 1) / T, ty = (H + T - 1) / T, nt = tx * ty;
+    /* bin the sorted splats into every tile their 3-sigma disc may touch, keeping order */
+    int64_t* cnt = (int64_t*)calloc((size_t)nt + 1, sizeof(int64_t));
+    int64_t* fill = (int64_t*)calloc((size_t)nt, sizeof(int64_t));
+    int64_t* list = NULL;
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            for (int t = 0; t < nt; ++t) cnt[t + 1] += cnt[t];
+            list = (int64_t*)malloc(sizeof(int64_t) * (size_t)(cnt[nt] > 0 ? cnt[nt] : 1));
+        }
+        for (uint64_t k = 0; k < m; ++k) {
+            int x0 = (int)floor((s[k].sx - rad) / T), x1 = (int)floor((s[k].sx + rad) / T);
+            int y0 = (int)floor((s[k].sy - rad) / T), y1 = (int)floor((s[k].sy + rad) / T);
+            if (x0 < 0) x0 = 0;
+            if (y0 < 0) y0 = 0;
+            if (x1 > tx - 1) x1 = tx - 1;
+            if (y1 > ty - 1) y1 = ty - 1;
+            for (int b = y0; b <= y1; ++b)
+                for (int a = x0; a <= x1; ++a) {
+                    int t = b * tx + a;
+                    if (pass == 0) cnt[t + 1]++;
+                    else list[cnt[t] + fill[t]++] = (int64_t)k;
+                }
+        }
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int t = 0; t < nt; ++t) {
+        int bx = (t % tx) * T, by = (t / tx) * T;
+        for (int py = by; py < by + T && py < H; ++py)
+            for (int px = bx; px < bx + T && px < W; ++px) {
+                double cx = px + 0.5, cy = py + 0.5, Tr = 1.0;
+                double acc[3] = {0.0, 0.0, 0.0};
+                for (int64_t q = cnt[t]; q < cnt[t + 1]; ++q) {
+                    const splat_t* g = &s[list[q]];
+                    double dx = cx - g->sx, dy = cy - g->sy, d2 = dx * dx + dy * dy;
+                    if (d2 > rad2) continue;
+                    double a = alpha * exp(-d2 / (2.0 * sigma * sigma));
+                    const float* c = colour + 3 * (uint64_t)g->i;
+                    for (int j = 0; j < 3; ++j) acc[j] += Tr * a * (double)c[j];
+                    Tr *= 1.0 - a;
+                    if (Tr < 1e-4) break;
+                }
+                double* o = out + 3 * ((int64_t)py * W + px);
+                o[0] = acc[0]; o[1] = acc[1]; o[2] = acc[2];
+            }
+    }
+    free(list);
+    free(fill);
+    free(cnt);
+    free(s);
+}
+
+void oracle_bf16_array(const float* in, int64_t n, uint16_t* out) {
+    for (int64_t i = 0; i < n; ++i) out[i] = oracle_bf16(in[i]);
+}
+
+void oracle_e4m3_array(const float* in, int64_t n, uint8_t* out) {
+    for (int64_t i = 0; i < n; ++i) out[i] = oracle_e4m3(in[i]);
+}
