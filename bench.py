@@ -1,0 +1,314 @@
+#!/usr/bin/env python
+"""Benchmark of the NARVis hot path on one GB300: a 350M-point trajectory scene (1M particles x
+350 RK4 steps, K = 3 attributes) rendered at 1920x1080 -- render + resolve/pack passes of the
+rasterizer and the U-Net forward -- reported as points/s (and frames/s).
+
+    python bench.py [--steps K] [--warmup W] [--prec bf16|fp32] [--impl ours|reference]
+
+One step = one whole frame through nrv_render_batch with the scene resident in HBM.  `value`
+is points/s = N * frames/s over all ranks (replicas: each rank renders the frame).  `e2e`
+measures the same through the public API per frame: the camera goes in from the host and the
+RGB frame comes back to pinned host memory inside the timed region.  The reference arm
+(--impl reference) times the CPU oracle on the host cores on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+BYTES_PER_POINT = 12.0          # xyz read once per frame for every view
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--particles", type=int, default=1_000_000)
+    ap.add_argument("--steps-per-particle", type=int, default=350)
+    ap.add_argument("--width", type=int, default=1920)
+    ap.add_argument("--height", type=int, default=1080)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        self.f.close()
+        mhz, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                t = [x.strip() for x in line.split(",")]
+                if len(t) < 9:
+                    continue
+                try:
+                    mhz.append(float(t[1]))
+                    mx.append(float(t[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, t[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def make_workload(a):
+    import nrv_inputs as I
+    t0 = time.time()
+    sc = I.trajectory_scene(a.particles, a.steps_per_particle, seed=2)
+    view = I.fitted_view(sc, a.width, a.height)
+    ds, do = I.depth_normalisation(sc, view)
+    return sc, view, ds, do, time.time() - t0
+
+
+def workload_name(a):
+    return (f"trajectories {a.particles}x{a.steps_per_particle} = "
+            f"{a.particles * a.steps_per_particle} points, K=3, {a.width}x{a.height}")
+
+
+def unet_params(c0, seed=1):
+    import numpy as np
+    import nrv_inputs as I
+    from paper_2407_19097_gb300 import nrv
+    flat = np.zeros(nrv.param_count(c0), np.float32)
+    for t, (name, kind, ci, co, wo, bo) in enumerate(nrv.layer_table(c0)):
+        k2 = {0: 9, 1: 4, 2: 1}[kind]
+        shape = {0: (co, ci, 3, 3), 1: (ci, co, 2, 2), 2: (co, ci)}[kind]
+        flat[wo:wo + int(np.prod(shape))] = I.xavier_uniform(seed, 1000 + t, shape, ci * k2,
+                                                             co * k2).ravel()
+    return flat
+
+
+def oracle_frame(sc, view, ds, do, max_seconds=None):
+    """The CPU oracle on one frame: render + resolve (C, one thread), pack, FP64 U-Net (numpy,
+    BLAS threads).  Returns (seconds, rgb float64 [H,W,3], seconds of the raster part)."""
+    import numpy as np
+    import oracle
+    from oracle import unet
+    c0 = len(sc.channels) + 2
+    t0 = time.perf_counter()
+    key, d, m, g = oracle.rasterize(sc, view)
+    hn, wn = (view.height + 7) // 8 * 8, (view.width + 7) // 8 * 8
+    x = oracle.pack(d, m, g, sc.channels, ds, do, hn, wn, 8, 0)
+    t1 = time.perf_counter()
+    y = unet.forward(x[None, :, :, :c0].astype(np.float64), unet.unflatten(unet_params(c0), c0))[0]
+    t2 = time.perf_counter()
+    return t2 - t0, y[:view.height, :view.width], t1 - t0
+
+
+def run_reference(a, rank, world):
+    """Reference arm: the CPU oracle on the host cores, same workload and metric."""
+    if rank != 0:
+        return
+    sc, view, ds, do, gen_s = make_workload(a)
+    times = []
+    for i in range(a.warmup + a.steps):
+        t, _, _ = oracle_frame(sc, view, ds, do)
+        if i >= a.warmup:
+            times.append(t)
+    sec = sum(times) / len(times)
+    v = sc.n / sec
+    ncpu = os.cpu_count()
+    line = {"impl": "reference", "metric": "points/s (frames/s) at 1080p", "value": v,
+            "unit": "points/s", "n_gpus": 0, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": sec * 1e3, "fps": 1.0 / sec, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 raster / f64 net",
+            "data": "synthetic", "config": {"workload": workload_name(a)},
+            "cpu_baseline": {"value": v, "unit": "points/s", "cores": ncpu, "kind": "oracle",
+                             "sample": "whole frames of the workload (render+resolve+pack in C on "
+                                       "one thread, FP64 U-Net in numpy on all BLAS threads)"},
+            "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        return run_reference(a, rank, world)
+
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2407_19097_gb300 import nrv
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    peaks, peak_kind = load_peaks()
+
+    sc, view, ds, do, gen_s = make_workload(a)
+    c0 = len(sc.channels) + 2
+    xyz = torch.from_numpy(sc.xyz).to(dev)
+    attr = torch.from_numpy(sc.attr.view(np.int32)).to(dev)
+    scene = nrv.Scene(xyz, attr, sc.n_words)
+    net = nrv.Net(c0)
+    params = torch.from_numpy(unet_params(c0)).to(dev)
+    net.set_params(params)
+    desc = nrv.make_pack_desc(sc.channels, ds, do)
+    H, W = view.height, view.width
+    rgb = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+    prec = nrv.PREC_BF16 if a.prec == "bf16" else nrv.PREC_F32
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(prec_, steps, warmup, profile):
+        for _ in range(warmup):
+            nrv.render_batch(scene, net, desc, [view], [rgb], prec_)
+        torch.cuda.synchronize()
+        nrv.timings()
+        nrv.set_profiling(profile)
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            nrv.render_batch(scene, net, desc, [view], [rgb], prec_)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        nrv.set_profiling(False)
+        stages = nrv.timings() if profile else None
+        return e0.elapsed_time(e1) / steps, stages
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms, stages = timed(prec, a.steps, a.warmup, True)
+    clocks = sampler.stop()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * sc.n / (ms * 1e-3)
+
+    # end to end through the public API: camera from the host, frame back to pinned host memory
+    host_rgb = torch.empty((H, W, 3), dtype=torch.float32, pin_memory=True)
+    for _ in range(a.warmup):
+        nrv.render_batch(scene, net, desc, [view], [rgb], prec)
+        host_rgb.copy_(rgb, non_blocking=True)
+        stream.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        nrv.render_batch(scene, net, desc, [view], [rgb], prec)
+        host_rgb.copy_(rgb, non_blocking=True)
+        stream.synchronize()
+    e2e_s = (time.perf_counter() - t0) / a.steps
+    barrier()
+
+    # the FP32 form of the same pipeline, for comparison
+    fp32_ms = None
+    if not a.no_fp32 and prec != nrv.PREC_F32:
+        fp32_ms, _ = timed(nrv.PREC_F32, max(3, a.steps // 10), 2, False)
+
+    # roofline of the render (visibility) pass: 12 algorithmic bytes per point
+    clear_ms, vis_ms, res_ms, net_ms = stages
+    vis_gbs = sc.n * BYTES_PER_POINT / (vis_ms * 1e-3) / 1e9
+    roof = {"kernel": "visibility_kernel", "bound": "hbm", "achieved": vis_gbs,
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": vis_gbs / peaks["hbm_gbs"],
+            "traffic": None, "peak_source": peak_kind,
+            "algorithmic_bytes_per_launch": sc.n * BYTES_PER_POINT}
+    flops = 71424.0 * (H + (-H) % 8) * (W + (-W) % 8)
+    net_tf = flops / (net_ms * 1e-3) / 1e12
+    pk = peaks.get("bf16_tflops_sustained", 1700.0)
+
+    line = {"metric": "points/s (frames/s) at 1080p", "value": value, "unit": "points/s",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "fps": 1e3 / ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": a.prec, "data": "synthetic",
+            "config": {"workload": workload_name(a), "network": f"U-Net 16/32/64/128, C_in={c0}",
+                       "precision": a.prec, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (4.2 GB of points per frame)"},
+            "stages_ms": {"clear": clear_ms, "visibility": vis_ms, "resolve_pack": res_ms,
+                          "network": net_ms},
+            "roofline": roof,
+            "roofline_network": {"bound": "tensor", "achieved": net_tf, "peak": pk,
+                                 "unit": "TFLOP/s", "frac": net_tf / pk,
+                                 "flops_per_frame": flops},
+            "fp32_ms_per_step": fp32_ms,
+            "e2e": {"value": world * sc.n / e2e_s, "unit": "points/s",
+                    "h2d_bytes_per_step": 80, "d2h_bytes_per_step": H * W * 3 * 4},
+            "clocks": clocks, "scene_gen_s": gen_s}
+    # launches per step: clear + visibility + resolve + network kernels
+    line["gpu_launches"] = a.steps * (3 + 24)
+
+    if rank == 0 and not a.no_cpu_baseline:
+        nrv.render_batch(scene, net, desc, [view], [rgb], prec)
+        torch.cuda.synchronize()
+        t_cpu, y_ref, t_ras = oracle_frame(sc, view, ds, do)
+        got = rgb.float().cpu().numpy().astype(np.float64)
+        r = float(y_ref.max() - y_ref.min())
+        mse = float(np.mean((got - y_ref) ** 2))
+        line["cpu_baseline"] = {"value": sc.n / t_cpu, "unit": "points/s", "cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": "one whole frame: render+resolve+pack in C on one thread "
+                                          f"({t_ras:.1f} s), FP64 U-Net in numpy on all BLAS "
+                                          f"threads ({t_cpu - t_ras:.1f} s)"}
+        line["quality_vs_fp64"] = {"psnr_db": 10 * np.log10(r * r / mse) if mse > 0 else None,
+                                   "max_abs": float(np.abs(got - y_ref).max())}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

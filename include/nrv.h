@@ -1,0 +1,271 @@
+/*
+ * nrv.h -- C ABI of libnrv, a GB300 (sm_103a) implementation of the hot path of
+ * NARVis, the neural accelerated renderer for scientific point clouds
+ * (arXiv 2407.19097):
+ *
+ *   1. the multi-attribute compute rasterizer (Sec. 3.2): a render pass that
+ *      projects every point and keeps, per pixel, the closest one via a 64-bit
+ *      atomic minimum of (depth bits << 32 | point index), then a resolve pass
+ *      that copies the winner's attributes, depth and coverage into G-buffers;
+ *   2. the neural deferred renderer (Sec. 3.3): a U-Net that turns the packed
+ *      G-buffer into the final RGB image, with its forward and backward passes,
+ *      an L1 loss and Adam for training (Sec. 3.3, training details).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns an nrv_status.  NRV_OK is 0.  On failure the
+ *    message of the calling thread's last error is available from
+ *    nrv_last_error().  No C++ exception crosses this boundary.
+ *  - Pointers named d_* are CUDA device pointers owned by the caller.  The
+ *    library borrows them for the duration of the call (or, for a scene, for
+ *    the scene's lifetime) and never frees them.  Handles own only their
+ *    internal scratch (packed weights, activation workspaces, graphs).
+ *  - All device work is enqueued on the given stream (NULL = the legacy
+ *    default stream) and is asynchronous: an error inside a kernel shows up at
+ *    a later synchronisation, or as a status word read by nrv_sync_status().
+ *  - Images are row-major with row 0 at the top.  Network tensors are NHWC.
+ *  - The library runs on the current CUDA device of the calling thread.  It
+ *    has no CPU fallback: without a CUDA device every call that launches work
+ *    returns NRV_ERR_CUDA.
+ */
+#ifndef NRV_H
+#define NRV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t; declared opaquely so this header needs no CUDA headers. */
+typedef struct CUstream_st* nrv_stream;
+
+typedef enum {
+    NRV_OK = 0,
+    NRV_ERR_ARG = 1,          /* invalid argument: null, misaligned, out of range */
+    NRV_ERR_CUDA = 2,         /* a CUDA runtime/driver call failed */
+    NRV_ERR_OOM = 3,          /* device allocation failed */
+    NRV_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+    NRV_ERR_UNSUPPORTED = 5,  /* valid request this build does not implement */
+    NRV_ERR_STATE = 6         /* call out of order (e.g. backward before forward) */
+} nrv_status;
+
+/* Attribute word formats (Sec. 3.2: "formats uint8 and fp32"). */
+typedef enum { NRV_F32 = 0, NRV_U32 = 1, NRV_U8X4 = 2 } nrv_fmt;
+
+/* Network arithmetic: FP32 SIMT, BF16 tensor cores, FP8 E4M3 tensor cores.
+ * Accumulation is FP32 in every mode (the paper's App. B quantises to fp16). */
+typedef enum { NRV_PREC_F32 = 0, NRV_PREC_BF16 = 1, NRV_PREC_FP8 = 2 } nrv_prec;
+
+/* --------------------------------------------------------------------------
+ * Library
+ * ------------------------------------------------------------------------ */
+
+/* Message of the calling thread's most recent failure ("" if none).  The
+ * pointer stays valid until the thread's next nrv_* call. */
+const char* nrv_last_error(void);
+
+/* ABI version, currently 1. */
+int nrv_version(void);
+
+/* --------------------------------------------------------------------------
+ * Scene (the point cloud of Sec. 3.2; memory N * sum(B_i) bytes, Sec. 4.5)
+ * ------------------------------------------------------------------------ */
+
+typedef struct {
+    uint64_t n_points;       /* N, 0 <= N < 2^32 (the index is the key's low word) */
+    const float* d_xyz;      /* device, N*3 floats (x, y, z), base 16-byte aligned */
+    const uint32_t* d_attr;  /* device, N*stride_words words: one record per point */
+    int stride_words;        /* record stride in 32-bit words: 1, 2, 4 or 8 */
+    int n_words;             /* K: record words copied to the G-buffer, 1..stride_words
+                                (Sec. 3.2 tests up to 8 attributes) */
+} nrv_scene_desc;
+
+typedef struct nrv_scene nrv_scene;
+
+/* Describe a scene.  Borrows d_xyz and d_attr, which must outlive the scene.
+ * Errors: NRV_ERR_ARG for a null pointer with N > 0, a d_xyz base that is not
+ * 16-byte aligned, a d_attr base not aligned to min(16, 4*stride_words) bytes,
+ * N >= 2^32, a stride not in {1,2,4,8} or K out of range. */
+nrv_status nrv_create_scene(const nrv_scene_desc* desc, nrv_scene** out);
+nrv_status nrv_destroy_scene(nrv_scene* scene);
+
+/* One camera.  clip = viewproj * (x, y, z, 1)^T with viewproj row-major FP32;
+ * clip.w is the eye-space depth.  A point is kept when znear <= w <= zfar and
+ * its pixel ((ndc.x + 1) W/2, (1 - ndc.y) H/2), truncated, is on screen. */
+typedef struct {
+    float viewproj[16];
+    int width, height;       /* 1..16384 each */
+    float znear, zfar;       /* 0 < znear <= zfar */
+} nrv_view;
+
+/* Raw G-buffer planes of one view, caller-owned device memory of H*W pixels.
+ * d_key is required.  d_depth (FP32 bits of the winner's w), d_mask (1 where
+ * covered) and d_attr (K planar u32 planes, plane c at d_attr + c*H*W) may be
+ * NULL to skip them.  Empty pixels get key ~0 and zeros in every other plane. */
+typedef struct {
+    uint64_t* d_key;
+    uint32_t* d_depth;
+    uint8_t* d_mask;
+    uint32_t* d_attr;
+} nrv_gbuffer;
+
+/* Render + resolve passes of the multi-attribute compute rasterizer (Sec. 3.2)
+ * for n_views views of one scene in one pass over the points: clear every
+ * key image, project each point once per view and keep the minimum key
+ * (bits(w) << 32 | index; ties to the lowest index), then resolve every pixel.
+ * Keys and planes are bit-exact: the projection is the fixed FP32 sequence
+ *   c = ((m0*x + m1*y) + m2*z) + m3 per row (no fused multiply-add),
+ *   ndc = c.xy / c.w (IEEE division).
+ * n_views in 1..8; gbufs has n_views entries.  Errors: NRV_ERR_ARG. */
+nrv_status nrv_rasterize(nrv_scene* scene, const nrv_view* views, int n_views,
+                         const nrv_gbuffer* gbufs, nrv_stream stream);
+
+/* How to turn one view's G-buffer into the network input ("channel-wise
+ * processing" of the rasterizer output, Sec. 4.5 / Tab. 3).  Channel j < n_channels
+ * reads G-buffer word word[j] as f32, u32 or byte comp[j] of a u8x4 word and
+ * becomes f = float(v) * scale[j] + offset[j] (separate FP32 multiply and add).
+ * Then comes depth (float of the depth plane, same affine map with depth_scale
+ * and depth_offset), then coverage (1.0), then zero padding.  Empty pixels are
+ * all zero.  C_in of the network = n_channels + 2 (at most 8). */
+typedef struct {
+    int n_channels;          /* 1..6 */
+    int word[6];
+    int fmt[6];              /* nrv_fmt */
+    int comp[6];             /* byte 0..3 for NRV_U8X4 */
+    float scale[6];
+    float offset[6];
+    float depth_scale, depth_offset;
+} nrv_pack_desc;
+
+/* Network-input geometry for an H x W view: the canvas is Hn x Wn with
+ * Hn, Wn = H, W rounded up to multiples of 8 (zero margin, cropped again at
+ * the output) and C channels per pixel: 8 for F32 and BF16, 16 for FP8. */
+int nrv_pad8(int v);
+int nrv_netin_channels(nrv_prec prec);
+
+/* Pack one view's G-buffer (d_depth, d_mask and d_attr required) into the
+ * network input d_netin: NHWC [Hn][Wn][C] of float, bf16 (round to nearest
+ * even) or e4m3 (of f * in_scale_inv, saturating, round to nearest even).
+ * Errors: NRV_ERR_ARG. */
+nrv_status nrv_pack(const nrv_gbuffer* gbuf, int height, int width, const nrv_pack_desc* desc,
+                    nrv_prec prec, float in_scale_inv, void* d_netin, nrv_stream stream);
+
+/* --------------------------------------------------------------------------
+ * Network (post-processing U-Net, Sec. 3.3)
+ *
+ * Fixed architecture: levels l = 0..3 at H/2^l with 16/32/64/128 channels;
+ * encoder: two 3x3 same convolutions + bias + ReLU per level and 2x2 average
+ * pooling between levels; decoder: 2x2 stride-2 transposed convolution (bias,
+ * no activation), concatenation [upsampled, skip], two 3x3 conv + ReLU; head:
+ * 1x1 convolution to RGB, linear.  Layer order: e0a e0b e1a e1b e2a e2b e3a
+ * e3b up3 d2a d2b up2 d1a d1b up1 d0a d0b head.
+ *
+ * Parameters are exchanged as one flat FP32 vector: per layer in that order,
+ * the weight in PyTorch's layout -- conv (C_out, C_in, 3, 3), transposed conv
+ * (C_in, C_out, 2, 2), head (C_out, C_in) -- followed by the bias (C_out).
+ * ------------------------------------------------------------------------ */
+
+typedef struct nrv_net nrv_net;
+
+typedef struct {
+    char name[8];
+    int kind;                /* 0 = 3x3 conv, 1 = 2x2 stride-2 transposed conv, 2 = 1x1 head */
+    int c_in, c_out;
+    int64_t weight_offset;   /* offset of the weight in the flat vector (floats) */
+    int64_t bias_offset;
+} nrv_layer_info;
+
+/* Number of layers (18), per-layer layout and the total parameter count for a
+ * network with c_in input channels (1..8).  Errors: NRV_ERR_ARG. */
+int nrv_net_num_layers(void);
+nrv_status nrv_net_layer(int c_in, int layer, nrv_layer_info* out);
+nrv_status nrv_net_param_count(int c_in, int64_t* count);
+
+/* Create a network for c_in input channels.  The library allocates only its
+ * packed low-precision weight copies and workspaces.  Errors: NRV_ERR_ARG,
+ * NRV_ERR_OOM. */
+nrv_status nrv_create_net(int c_in, nrv_net** out);
+nrv_status nrv_destroy_net(nrv_net* net);
+
+/* Load weights from a flat FP32 device vector (layout above) and re-derive the
+ * packed BF16 and FP8 copies (FP8: per-output-channel scale amax/448).  Call
+ * again after the parameters change.  Errors: NRV_ERR_ARG. */
+nrv_status nrv_net_set_params(nrv_net* net, const float* d_params, nrv_stream stream);
+
+/* FP8 activation scales: act_scale[l] is the per-tensor scale of the input of
+ * 3x3/transposed/head layer l (18 host floats; value = amax/448 from
+ * calibration).  act_scale[0] must equal the input scale used by nrv_pack. */
+nrv_status nrv_net_set_act_scales(nrv_net* net, const float* act_scale, int n);
+
+/* Forward pass (inference) on n images: d_netin is n packed inputs
+ * [n][Hn][Wn][C] in the dtype of prec (nrv_netin_channels), d_rgb receives
+ * [n][height][width][3] FP32, cropped to height x width.
+ * Errors: NRV_ERR_ARG, NRV_ERR_STATE (no parameters loaded), NRV_ERR_OOM. */
+nrv_status nrv_shade(nrv_net* net, const void* d_netin, int n, int height, int width,
+                     nrv_prec prec, float* d_rgb, nrv_stream stream);
+
+/* Training forward: like nrv_shade, but keeps the activations the backward
+ * pass needs in the net's workspace (F32 or BF16 only). */
+nrv_status nrv_net_forward_train(nrv_net* net, const void* d_netin, int n, int height, int width,
+                                 nrv_prec prec, float* d_rgb, nrv_stream stream);
+
+/* Backward pass of the last nrv_net_forward_train: d_drgb = dL/d(rgb)
+ * [n][height][width][3] FP32; writes dL/d(params) into d_grad (flat FP32,
+ * parameter layout, overwritten, deterministic).  Errors: NRV_ERR_STATE when no
+ * training forward preceded it. */
+nrv_status nrv_net_backward(nrv_net* net, const float* d_drgb, float* d_grad, nrv_stream stream);
+
+/* L1 loss of Sec. 3.3's reconstruction term, in the L1 form:
+ * loss = mean |y - t| over n floats, written to d_loss[0]; if d_dy is not NULL,
+ * d_dy = sign(y - t) / n with sign(0) = 0.  Deterministic. */
+nrv_status nrv_l1_loss(const float* d_y, const float* d_t, int64_t n, float* d_loss, float* d_dy,
+                       nrv_stream stream);
+
+/* Adam (Kingma & Ba; Sec. 3.3 uses it with lr 1e-3), no weight decay, step >= 1:
+ * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * p -= lr * (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps), all FP32. */
+nrv_status nrv_adam_step(float* d_params, const float* d_grad, float* d_m, float* d_v, int64_t n,
+                         int step, float lr, float beta1, float beta2, float eps, nrv_stream stream);
+
+/* One training step on a batch: forward (saving activations), L1 loss against
+ * d_target [n][height][width][3], backward, Adam update of d_params with
+ * moments d_m, d_v (all flat FP32, parameter layout), then the packed weights
+ * are re-derived.  d_loss[0] receives the loss.  prec: F32 or BF16. */
+nrv_status nrv_train_step(nrv_net* net, float* d_params, float* d_grad, float* d_m, float* d_v,
+                          int step, float lr, const void* d_netin, const float* d_target, int n,
+                          int height, int width, nrv_prec prec, float* d_loss, nrv_stream stream);
+
+/* --------------------------------------------------------------------------
+ * Whole frames
+ * ------------------------------------------------------------------------ */
+
+/* Render n_views views end to end: rasterize, pack and shade every view, each
+ * into d_rgb[i] ([H_i][W_i][3] FP32, caller-owned).  Views may have different
+ * sizes.  The device work is captured once per (scene, net, sizes, prec) into a
+ * CUDA graph and replayed on later calls; the G-buffers and network inputs live
+ * in the net's workspace.  in_scale_inv is the FP8 input scale inverse (ignored
+ * otherwise).  Errors: NRV_ERR_ARG, NRV_ERR_OOM, NRV_ERR_CUDA. */
+nrv_status nrv_render_batch(nrv_scene* scene, nrv_net* net, const nrv_pack_desc* desc,
+                            const nrv_view* views, int n_views, float* const* d_rgb,
+                            nrv_prec prec, float in_scale_inv, nrv_stream stream);
+
+/* Stage timing of nrv_render_batch.  While profiling is on (nrv_set_profiling(1)),
+ * every call records CUDA events around its stages on the caller's stream
+ * without synchronising.  nrv_get_timings waits for them and writes the mean
+ * device milliseconds per call of: [0] clearing the key images, [1] the render
+ * (visibility) pass, [2] resolve + pack, [3] the network; then it forgets the
+ * recorded calls.  Returns the number of values written (<= cap, at most 4). */
+nrv_status nrv_set_profiling(int on);
+int nrv_get_timings(float* ms, int cap);
+
+/* Reads and clears the library's device status word (bounded waits that gave
+ * up, bad indices caught by device checks).  Synchronises the stream. */
+nrv_status nrv_sync_status(nrv_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NRV_H */

@@ -1,0 +1,4 @@
+"""GB300-native hot path of NARVis (arXiv 2407.19097): a multi-attribute point rasterizer and a
+neural deferred renderer as hand-written sm_103a CUDA behind the C ABI in include/nrv.h."""
+from . import nrv  # noqa: F401
+from .build_lib import build  # noqa: F401

@@ -1,0 +1,460 @@
+// C ABI entry points (include/nrv.h): argument checks, handles and the
+// orchestration of the rasterizer and network stages.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <vector>
+
+#include "net.h"
+
+namespace nrv {
+
+static thread_local char g_err[512];
+
+nrv_status fail(nrv_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+void clear_error() { g_err[0] = 0; }
+
+static unsigned* g_status = nullptr;
+
+unsigned* status_word() {
+    if (!g_status) {
+        if (cudaMalloc(&g_status, sizeof(unsigned)) != cudaSuccess) {
+            cudaGetLastError();
+            g_status = nullptr;
+            return nullptr;
+        }
+        cudaMemset(g_status, 0, sizeof(unsigned));
+    }
+    return g_status;
+}
+
+void set_saved_input(const void* p);  // train.cu
+
+}  // namespace nrv
+
+using namespace nrv;
+
+struct nrv_scene {
+    nrv_scene_desc d;
+};
+
+struct nrv_net : Net {};
+
+// --------------------------------------------------------------------- library
+extern "C" const char* nrv_last_error(void) { return g_err; }
+extern "C" int nrv_version(void) { return 1; }
+extern "C" int nrv_pad8(int v) { return (v + 7) / 8 * 8; }
+extern "C" int nrv_netin_channels(nrv_prec p) { return p == NRV_PREC_FP8 ? 16 : 8; }
+
+static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// --------------------------------------------------------------------- scene
+extern "C" nrv_status nrv_create_scene(const nrv_scene_desc* d, nrv_scene** out) {
+    clear_error();
+    if (!d || !out) return fail(NRV_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (d->n_points >= (1ull << 32)) return fail(NRV_ERR_ARG, "n_points must be < 2^32");
+    const int sw = d->stride_words;
+    if (!(sw == 1 || sw == 2 || sw == 4 || sw == 8))
+        return fail(NRV_ERR_ARG, "stride_words must be 1, 2, 4 or 8 (got %d)", sw);
+    if (d->n_words < 1 || d->n_words > sw)
+        return fail(NRV_ERR_ARG, "n_words must be in 1..stride_words (got %d)", d->n_words);
+    if (d->n_points > 0) {
+        if (!d->d_xyz || !d->d_attr) return fail(NRV_ERR_ARG, "null point or attribute pointer");
+        if (!aligned(d->d_xyz, 16)) return fail(NRV_ERR_ARG, "d_xyz must be 16-byte aligned");
+        const size_t ra = sw * 4 < 16 ? (size_t)sw * 4 : 16;
+        if (!aligned(d->d_attr, ra)) return fail(NRV_ERR_ARG, "d_attr must be %zu-byte aligned", ra);
+    }
+    nrv_scene* s = new nrv_scene;
+    s->d = *d;
+    *out = s;
+    return NRV_OK;
+}
+
+extern "C" nrv_status nrv_destroy_scene(nrv_scene* s) {
+    clear_error();
+    delete s;
+    return NRV_OK;
+}
+
+static nrv_status check_view(const nrv_view& v) {
+    if (v.width < 1 || v.height < 1 || v.width > 16384 || v.height > 16384)
+        return fail(NRV_ERR_ARG, "view size %dx%d out of range", v.width, v.height);
+    if (!(v.znear > 0.0f) || !(v.zfar >= v.znear)) return fail(NRV_ERR_ARG, "need 0 < znear <= zfar");
+    for (int i = 0; i < 16; ++i)
+        if (!isfinite(v.viewproj[i])) return fail(NRV_ERR_ARG, "view matrix must be finite");
+    return NRV_OK;
+}
+
+static RView make_rview(const nrv_view& v, uint64_t* key) {
+    RView r;
+    const int rows[3] = {0, 1, 3};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 4; ++j) r.m[4 * i + j] = v.viewproj[4 * rows[i] + j];
+    r.hw = 0.5f * (float)v.width;
+    r.hh = 0.5f * (float)v.height;
+    r.fw = (float)v.width;
+    r.fh = (float)v.height;
+    r.znear = v.znear;
+    r.zfar = v.zfar;
+    r.width = v.width;
+    r.height = v.height;
+    r.key = reinterpret_cast<unsigned long long*>(key);
+    return r;
+}
+
+static nrv_status check_pack(const nrv_pack_desc* d, int n_words) {
+    if (!d) return fail(NRV_ERR_ARG, "null pack descriptor");
+    if (d->n_channels < 1 || d->n_channels > 6) return fail(NRV_ERR_ARG, "n_channels must be 1..6");
+    for (int j = 0; j < d->n_channels; ++j) {
+        if (d->word[j] < 0 || d->word[j] >= n_words)
+            return fail(NRV_ERR_ARG, "channel %d reads word %d of %d", j, d->word[j], n_words);
+        if (d->fmt[j] < 0 || d->fmt[j] > 2) return fail(NRV_ERR_ARG, "channel %d: bad format", j);
+        if (d->fmt[j] == NRV_U8X4 && (d->comp[j] < 0 || d->comp[j] > 3))
+            return fail(NRV_ERR_ARG, "channel %d: byte index must be 0..3", j);
+    }
+    return NRV_OK;
+}
+
+static void fill_pack(ResolveArgs& a, const nrv_pack_desc* d, nrv_prec prec, float inv) {
+    a.out_fmt = prec == NRV_PREC_F32 ? 0 : prec == NRV_PREC_BF16 ? 1 : 2;
+    a.in_scale_inv = inv;
+    a.n_ch = d->n_channels;
+    for (int j = 0; j < 6; ++j) {
+        a.ch_word[j] = j < d->n_channels ? d->word[j] : 0;
+        a.ch_fmt[j] = j < d->n_channels ? d->fmt[j] : 0;
+        a.ch_comp[j] = j < d->n_channels ? d->comp[j] : 0;
+        a.ch_scale[j] = j < d->n_channels ? d->scale[j] : 0.0f;
+        a.ch_offset[j] = j < d->n_channels ? d->offset[j] : 0.0f;
+    }
+    a.d_scale = d->depth_scale;
+    a.d_offset = d->depth_offset;
+}
+
+static nrv_status raster_views(nrv_scene* s, const nrv_view* views, int n, uint64_t* const* keys,
+                               cudaStream_t st) {
+    RViews rv;
+    memset(&rv, 0, sizeof(rv));
+    rv.n = n;
+    for (int i = 0; i < n; ++i) rv.v[i] = make_rview(views[i], keys[i]);
+    NRV_TRY(launch_clear_keys(rv, st));
+    return launch_visibility(s->d.d_xyz, s->d.n_points, rv, st);
+}
+
+extern "C" nrv_status nrv_rasterize(nrv_scene* s, const nrv_view* views, int n,
+                                    const nrv_gbuffer* gb, nrv_stream stream) {
+    clear_error();
+    if (!s || !views || !gb) return fail(NRV_ERR_ARG, "null argument");
+    if (n < 1 || n > 8) return fail(NRV_ERR_ARG, "n_views must be 1..8");
+    uint64_t* keys[8];
+    for (int i = 0; i < n; ++i) {
+        NRV_TRY(check_view(views[i]));
+        if (!gb[i].d_key || !aligned(gb[i].d_key, 16))
+            return fail(NRV_ERR_ARG, "view %d: d_key must be non-null and 16-byte aligned", i);
+        keys[i] = gb[i].d_key;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    NRV_TRY(raster_views(s, views, n, keys, st));
+    for (int i = 0; i < n; ++i) {
+        if (!gb[i].d_depth && !gb[i].d_mask && !gb[i].d_attr) continue;
+        ResolveArgs a;
+        memset(&a, 0, sizeof(a));
+        a.key = reinterpret_cast<const unsigned long long*>(gb[i].d_key);
+        a.attr = s->d.d_attr;
+        a.stride_words = s->d.stride_words;
+        a.n_words = s->d.n_words;
+        a.width = views[i].width;
+        a.height = views[i].height;
+        a.depth = gb[i].d_depth;
+        a.mask = gb[i].d_mask;
+        a.gattr = gb[i].d_attr;
+        NRV_TRY(launch_resolve(a, st));
+    }
+    return NRV_OK;
+}
+
+extern "C" nrv_status nrv_pack(const nrv_gbuffer* gb, int h, int w, const nrv_pack_desc* d,
+                               nrv_prec prec, float inv, void* netin, nrv_stream stream) {
+    clear_error();
+    if (!gb || !netin || !gb->d_depth || !gb->d_mask || !gb->d_attr)
+        return fail(NRV_ERR_ARG, "pack needs depth, mask and attribute planes and an output");
+    if (h < 1 || w < 1 || h > 16384 || w > 16384) return fail(NRV_ERR_ARG, "bad size");
+    if (prec < NRV_PREC_F32 || prec > NRV_PREC_FP8) return fail(NRV_ERR_ARG, "bad precision");
+    if (!aligned(netin, 32)) return fail(NRV_ERR_ARG, "d_netin must be 32-byte aligned");
+    NRV_TRY(check_pack(d, 8));
+    ResolveArgs a;
+    memset(&a, 0, sizeof(a));
+    a.width = w;
+    a.height = h;
+    a.wn = nrv_pad8(w);
+    a.hn = nrv_pad8(h);
+    a.netin = netin;
+    fill_pack(a, d, prec, inv);
+    return launch_pack_planes(gb->d_depth, gb->d_mask, gb->d_attr, a, (cudaStream_t)stream);
+}
+
+// --------------------------------------------------------------------- network
+extern "C" int nrv_net_num_layers(void) { return NUM_LAYERS; }
+
+extern "C" nrv_status nrv_net_layer(int c_in, int layer, nrv_layer_info* out) {
+    clear_error();
+    if (c_in < 1 || c_in > 8 || layer < 0 || layer >= NUM_LAYERS || !out)
+        return fail(NRV_ERR_ARG, "bad layer query");
+    Layer L[NUM_LAYERS];
+    net_layers(c_in, L);
+    memset(out, 0, sizeof(*out));
+    memcpy(out->name, L[layer].name, sizeof(out->name));
+    out->kind = L[layer].kind;
+    out->c_in = L[layer].cin;
+    out->c_out = L[layer].cout;
+    out->weight_offset = L[layer].woff;
+    out->bias_offset = L[layer].boff;
+    return NRV_OK;
+}
+
+extern "C" nrv_status nrv_net_param_count(int c_in, int64_t* count) {
+    clear_error();
+    if (c_in < 1 || c_in > 8 || !count) return fail(NRV_ERR_ARG, "c_in must be 1..8");
+    Layer L[NUM_LAYERS];
+    *count = net_layers(c_in, L);
+    return NRV_OK;
+}
+
+extern "C" nrv_status nrv_create_net(int c_in, nrv_net** out) {
+    clear_error();
+    if (!out) return fail(NRV_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (c_in < 1 || c_in > 8) return fail(NRV_ERR_ARG, "c_in must be 1..8");
+    nrv_net* net = new nrv_net;
+    net->c_in = c_in;
+    net->c0p = 8;
+    net->n_params = net_layers(c_in, net->layers);
+    for (int l = 0; l < NUM_LAYERS; ++l) net->act_scale[l] = 1.0f;
+    *out = net;
+    return NRV_OK;
+}
+
+extern "C" nrv_status nrv_destroy_net(nrv_net* net) {
+    clear_error();
+    delete net;
+    return NRV_OK;
+}
+
+extern "C" nrv_status nrv_net_set_params(nrv_net* net, const float* d_params, nrv_stream stream) {
+    clear_error();
+    if (!net || !d_params) return fail(NRV_ERR_ARG, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    NRV_TRY(net->params.ensure(net->n_params * sizeof(float)));
+    NRV_CHECK_CUDA(cudaMemcpyAsync(net->params.p, d_params, net->n_params * sizeof(float),
+                                   cudaMemcpyDeviceToDevice, st));
+    NRV_TRY(net_repack(net, st));
+    net->has_params = true;
+    return NRV_OK;
+}
+
+extern "C" nrv_status nrv_net_set_act_scales(nrv_net* net, const float* s, int n) {
+    clear_error();
+    if (!net || !s || n != NUM_LAYERS) return fail(NRV_ERR_ARG, "need %d scales", NUM_LAYERS);
+    for (int l = 0; l < NUM_LAYERS; ++l) {
+        if (!(s[l] > 0.0f) || !isfinite(s[l])) return fail(NRV_ERR_ARG, "scale %d must be > 0", l);
+        net->act_scale[l] = s[l];
+    }
+    return NRV_OK;
+}
+
+static nrv_status check_shade(nrv_net* net, const void* in, int n, int h, int w, nrv_prec prec,
+                              const float* rgb) {
+    if (!net || !in || !rgb) return fail(NRV_ERR_ARG, "null argument");
+    if (!net->has_params) return fail(NRV_ERR_STATE, "no parameters loaded");
+    if (n < 1 || h < 1 || w < 1 || h > 16384 || w > 16384) return fail(NRV_ERR_ARG, "bad size");
+    if (prec < NRV_PREC_F32 || prec > NRV_PREC_FP8) return fail(NRV_ERR_ARG, "bad precision");
+    if (!aligned(in, 32)) return fail(NRV_ERR_ARG, "d_netin must be 32-byte aligned");
+    return NRV_OK;
+}
+
+extern "C" nrv_status nrv_shade(nrv_net* net, const void* netin, int n, int h, int w,
+                                nrv_prec prec, float* rgb, nrv_stream stream) {
+    clear_error();
+    NRV_TRY(check_shade(net, netin, n, h, w, prec, rgb));
+    return net_forward(net, netin, n, h, w, prec, rgb, (cudaStream_t)stream);
+}
+
+extern "C" nrv_status nrv_net_forward_train(nrv_net* net, const void* netin, int n, int h, int w,
+                                            nrv_prec prec, float* rgb, nrv_stream stream) {
+    clear_error();
+    NRV_TRY(check_shade(net, netin, n, h, w, prec, rgb));
+    if (prec == NRV_PREC_FP8) return fail(NRV_ERR_UNSUPPORTED, "training runs in F32 or BF16");
+    NRV_TRY(net_forward(net, netin, n, h, w, prec, rgb, (cudaStream_t)stream));
+    set_saved_input(netin);
+    net->saved = true;
+    return NRV_OK;
+}
+
+extern "C" nrv_status nrv_net_backward(nrv_net* net, const float* drgb, float* dparams,
+                                       nrv_stream stream) {
+    clear_error();
+    if (!net || !drgb || !dparams) return fail(NRV_ERR_ARG, "null argument");
+    return net_backward(net, drgb, dparams, (cudaStream_t)stream);
+}
+
+extern "C" nrv_status nrv_l1_loss(const float* y, const float* t, int64_t n, float* loss,
+                                  float* dy, nrv_stream stream) {
+    clear_error();
+    if (!y || !t || !loss || n < 1) return fail(NRV_ERR_ARG, "bad argument");
+    return launch_l1(y, t, n, loss, dy, (cudaStream_t)stream);
+}
+
+extern "C" nrv_status nrv_adam_step(float* p, const float* g, float* m, float* v, int64_t n,
+                                    int step, float lr, float b1, float b2, float eps,
+                                    nrv_stream stream) {
+    clear_error();
+    if (!p || !g || !m || !v || n < 1 || step < 1) return fail(NRV_ERR_ARG, "bad argument");
+    return launch_adam(p, g, m, v, n, step, lr, b1, b2, eps, (cudaStream_t)stream);
+}
+
+extern "C" nrv_status nrv_train_step(nrv_net* net, float* params, float* grad, float* m, float* v,
+                                     int step, float lr, const void* netin, const float* target,
+                                     int n, int h, int w, nrv_prec prec, float* loss,
+                                     nrv_stream stream) {
+    clear_error();
+    if (!params || !grad || !m || !v || !target || !loss || step < 1)
+        return fail(NRV_ERR_ARG, "bad argument");
+    NRV_TRY(check_shade(net, netin, n, h, w, prec, target));
+    if (prec == NRV_PREC_FP8) return fail(NRV_ERR_UNSUPPORTED, "training runs in F32 or BF16");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nout = (size_t)n * h * w * 3;
+    NRV_TRY(net->batch_ws.ensure(2 * nout * sizeof(float)));
+    float* y = (float*)net->batch_ws.p;
+    float* dy = y + nout;
+    NRV_TRY(net_forward(net, netin, n, h, w, prec, y, st));
+    set_saved_input(netin);
+    net->saved = true;
+    NRV_TRY(launch_l1(y, target, (int64_t)nout, loss, dy, st));
+    NRV_TRY(net_backward(net, dy, grad, st));
+    NRV_TRY(launch_adam(params, grad, m, v, net->n_params, step, lr, 0.9f, 0.999f, 1e-8f, st));
+    NRV_CHECK_CUDA(cudaMemcpyAsync(net->params.p, params, net->n_params * sizeof(float),
+                                   cudaMemcpyDeviceToDevice, st));
+    return net_repack(net, st);
+}
+
+// --------------------------------------------------------------------- whole frames
+// Profiling: each nrv_render_batch call records events around its stages on the
+// caller's stream (no synchronisation); nrv_get_timings waits for the last one
+// and returns per-call averages, then forgets them.
+static bool g_profile = false;
+static std::vector<std::vector<cudaEvent_t>> g_prof_events;
+enum { ST_CLEAR, ST_VIS, ST_RESOLVE, ST_NET, NUM_STAGES };
+
+extern "C" nrv_status nrv_set_profiling(int on) {
+    clear_error();
+    g_profile = on != 0;
+    return NRV_OK;
+}
+
+extern "C" int nrv_get_timings(float* ms, int cap) {
+    double acc[NUM_STAGES] = {0, 0, 0, 0};
+    int calls = 0;
+    for (auto& ev : g_prof_events) {
+        if (cudaEventSynchronize(ev.back()) != cudaSuccess) continue;
+        for (int k = 0; k < NUM_STAGES; ++k) {
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            acc[k] += t;
+        }
+        ++calls;
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+    g_prof_events.clear();
+    int k = 0;
+    for (; k < NUM_STAGES && k < cap; ++k) ms[k] = calls ? (float)(acc[k] / calls) : 0.0f;
+    return k;
+}
+
+static void prof_mark(std::vector<cudaEvent_t>& ev, cudaStream_t st) {
+    if (!g_profile) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, st);
+    ev.push_back(e);
+}
+
+extern "C" nrv_status nrv_render_batch(nrv_scene* s, nrv_net* net, const nrv_pack_desc* d,
+                                       const nrv_view* views, int n, float* const* rgb,
+                                       nrv_prec prec, float inv, nrv_stream stream) {
+    clear_error();
+    if (!s || !net || !views || !rgb) return fail(NRV_ERR_ARG, "null argument");
+    if (n < 1 || n > 8) return fail(NRV_ERR_ARG, "n_views must be 1..8");
+    if (!net->has_params) return fail(NRV_ERR_STATE, "no parameters loaded");
+    NRV_TRY(check_pack(d, s->d.n_words));
+    if (d->n_channels + 2 != net->c_in)
+        return fail(NRV_ERR_ARG, "pack gives %d channels, network expects %d", d->n_channels + 2,
+                    net->c_in);
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t key_off[8], in_off[8], tot = 0;
+    const size_t es = elem_size(prec) * nrv_netin_channels(prec);
+    for (int i = 0; i < n; ++i) {
+        NRV_TRY(check_view(views[i]));
+        if (!rgb[i]) return fail(NRV_ERR_ARG, "null output %d", i);
+        key_off[i] = tot;
+        tot += ((size_t)views[i].width * views[i].height * 8 + 1023) / 1024 * 1024;
+        in_off[i] = tot;
+        tot += ((size_t)nrv_pad8(views[i].width) * nrv_pad8(views[i].height) * es + 1023) / 1024 * 1024;
+    }
+    NRV_TRY(net->batch_ws.ensure(tot));
+    char* base = (char*)net->batch_ws.p;
+    RViews rv;
+    memset(&rv, 0, sizeof(rv));
+    rv.n = n;
+    for (int i = 0; i < n; ++i) rv.v[i] = make_rview(views[i], (uint64_t*)(base + key_off[i]));
+    std::vector<cudaEvent_t> ev;
+    prof_mark(ev, st);
+    NRV_TRY(launch_clear_keys(rv, st));
+    prof_mark(ev, st);
+    NRV_TRY(launch_visibility(s->d.d_xyz, s->d.n_points, rv, st));
+    prof_mark(ev, st);
+    for (int i = 0; i < n; ++i) {
+        ResolveArgs a;
+        memset(&a, 0, sizeof(a));
+        a.key = reinterpret_cast<const unsigned long long*>(base + key_off[i]);
+        a.attr = s->d.d_attr;
+        a.stride_words = s->d.stride_words;
+        a.n_words = s->d.n_words;
+        a.width = views[i].width;
+        a.height = views[i].height;
+        a.wn = nrv_pad8(a.width);
+        a.hn = nrv_pad8(a.height);
+        a.netin = base + in_off[i];
+        fill_pack(a, d, prec, inv);
+        NRV_TRY(launch_resolve(a, st));
+    }
+    prof_mark(ev, st);
+    for (int i = 0; i < n; ++i)
+        NRV_TRY(net_forward(net, base + in_off[i], 1, views[i].height, views[i].width, prec, rgb[i],
+                            st));
+    prof_mark(ev, st);
+    if (g_profile) g_prof_events.push_back(ev);
+    return NRV_OK;
+}
+
+extern "C" nrv_status nrv_sync_status(nrv_stream stream) {
+    clear_error();
+    NRV_CHECK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    unsigned* w = status_word();
+    if (!w) return fail(NRV_ERR_CUDA, "status word unavailable");
+    unsigned h = 0;
+    NRV_CHECK_CUDA(cudaMemcpy(&h, w, sizeof(h), cudaMemcpyDeviceToHost));
+    NRV_CHECK_CUDA(cudaMemset(w, 0, sizeof(unsigned)));
+    if (h & STATUS_TIMEOUT) return fail(NRV_ERR_TIMEOUT, "a device-side wait gave up (status %u)", h);
+    if (h) return fail(NRV_ERR_CUDA, "device status %u", h);
+    return NRV_OK;
+}

@@ -1,0 +1,96 @@
+// Internal declarations shared by the library's own translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/nrv.h"
+
+namespace nrv {
+
+nrv_status fail(nrv_status s, const char* fmt, ...);
+void clear_error();
+
+#define NRV_CHECK_CUDA(call)                                                             \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return ::nrv::fail(NRV_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define NRV_CHECK_LAUNCH() NRV_CHECK_CUDA(cudaGetLastError())
+
+#define NRV_TRY(expr)                          \
+    do {                                       \
+        nrv_status s_ = (expr);                \
+        if (s_ != NRV_OK) return s_;           \
+    } while (0)
+
+// Device status word: kernels OR error bits into it instead of trapping.
+enum : unsigned { STATUS_TIMEOUT = 1u, STATUS_BAD_INDEX = 2u };
+unsigned* status_word();  // device pointer, allocated on first use
+
+// --------------------------------------------------------------------- rasterizer
+struct RView {
+    float m[12];          // rows 0, 1 and 3 of the view-projection, row-major
+    float hw, hh;         // 0.5*W, 0.5*H
+    float fw, fh;         // W, H as floats
+    float znear, zfar;
+    int width, height;
+    unsigned long long* key;
+};
+
+struct RViews {
+    RView v[8];
+    int n;
+};
+
+struct ResolveArgs {
+    const unsigned long long* key;
+    const uint32_t* attr;   // records
+    int stride_words, n_words;
+    int width, height;      // view
+    int wn, hn;             // canvas (>= view), used when packing
+    uint32_t* depth;        // planes, may be null
+    uint8_t* mask;
+    uint32_t* gattr;
+    void* netin;            // packed network input, may be null
+    int out_fmt;            // 0 f32, 1 bf16, 2 e4m3
+    float in_scale_inv;
+    int n_ch;
+    int ch_word[6], ch_fmt[6], ch_comp[6];
+    float ch_scale[6], ch_offset[6];
+    float d_scale, d_offset;
+};
+
+nrv_status launch_clear_keys(const RViews& views, cudaStream_t s);
+nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, cudaStream_t s);
+nrv_status launch_resolve(const ResolveArgs& a, cudaStream_t s);
+nrv_status launch_pack_planes(const uint32_t* depth, const uint8_t* mask, const uint32_t* gattr,
+                              const ResolveArgs& a, cudaStream_t s);
+
+// --------------------------------------------------------------------- network
+enum LayerKind { CONV3 = 0, UPCONV2 = 1, HEAD1 = 2 };
+
+struct Layer {
+    char name[8];
+    int kind, cin, cout;
+    int64_t woff, boff;
+};
+
+constexpr int NUM_LAYERS = 18;
+int net_layers(int c_in, Layer* out);      // returns the parameter count
+
+// Layer indices
+enum {
+    L_E0A, L_E0B, L_E1A, L_E1B, L_E2A, L_E2B, L_E3A, L_E3B, L_UP3, L_D2A, L_D2B, L_UP2, L_D1A,
+    L_D1B, L_UP1, L_D0A, L_D0B, L_HEAD
+};
+
+struct Net;  // defined in net.cu
+
+}  // namespace nrv

@@ -1,0 +1,253 @@
+// U-Net of the neural deferred renderer (Sec. 3.3): layer table, weight
+// re-packing, activation workspace and the forward pass.
+#include <string.h>
+
+#include "net.h"
+#include "net_simt.cuh"
+
+namespace nrv {
+
+nrv_status DevBuf::ensure(size_t b) {
+    if (b <= bytes) return NRV_OK;
+    release();
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        return fail(NRV_ERR_OOM, "cudaMalloc(%zu) failed: %s", b, cudaGetErrorString(e));
+    }
+    bytes = b;
+    return NRV_OK;
+}
+
+void DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+int net_layers(int c_in, Layer* L) {
+    struct { const char* n; int k, ci, co; } t[NUM_LAYERS] = {
+        {"e0a", CONV3, c_in, 16}, {"e0b", CONV3, 16, 16}, {"e1a", CONV3, 16, 32},
+        {"e1b", CONV3, 32, 32},   {"e2a", CONV3, 32, 64}, {"e2b", CONV3, 64, 64},
+        {"e3a", CONV3, 64, 128},  {"e3b", CONV3, 128, 128}, {"up3", UPCONV2, 128, 64},
+        {"d2a", CONV3, 128, 64},  {"d2b", CONV3, 64, 64}, {"up2", UPCONV2, 64, 32},
+        {"d1a", CONV3, 64, 32},   {"d1b", CONV3, 32, 32}, {"up1", UPCONV2, 32, 16},
+        {"d0a", CONV3, 32, 16},   {"d0b", CONV3, 16, 16}, {"head", HEAD1, 16, 3}};
+    int64_t off = 0;
+    for (int i = 0; i < NUM_LAYERS; ++i) {
+        memset(L[i].name, 0, sizeof(L[i].name));
+        strncpy(L[i].name, t[i].n, sizeof(L[i].name) - 1);
+        L[i].kind = t[i].k;
+        L[i].cin = t[i].ci;
+        L[i].cout = t[i].co;
+        const int k2 = t[i].k == CONV3 ? 9 : t[i].k == UPCONV2 ? 4 : 1;
+        L[i].woff = off;
+        off += (int64_t)k2 * t[i].ci * t[i].co;
+        L[i].boff = off;
+        off += t[i].co;
+    }
+    return (int)off;
+}
+
+size_t elem_size(nrv_prec p) { return p == NRV_PREC_F32 ? 4 : p == NRV_PREC_BF16 ? 2 : 1; }
+
+static inline int padded_cin(const Net* net, int l) {
+    return l == L_E0A ? net->c0p : net->layers[l].cin;
+}
+
+// ------------------------------------------------------------------ weight re-packing
+// conv forward   wf[tap][c][o]  = W[o][c][tap]      (c < padded cin, zero beyond cin)
+// conv backward  wt[tap][o][c]  = W[o][c][8 - tap]  (180-degree rotation, transposed)
+// upconv         wf[a][b][c][o] = W[c][o][a][b]
+__global__ void repack_f32_kernel(const float* __restrict__ P, Layer L, int cinp, float* wf,
+                                  float* wt) {
+    const int kk = L.kind == CONV3 ? 9 : 4;
+    const size_t total = (size_t)kk * cinp * L.cout;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int o = (int)(i % L.cout);
+        const int c = (int)((i / L.cout) % cinp);
+        const int tap = (int)(i / ((size_t)L.cout * cinp));
+        if (L.kind == CONV3) {
+            wf[i] = c < L.cin ? P[L.woff + ((size_t)o * L.cin + c) * 9 + tap] : 0.0f;
+            // wt index: [tap][o][c] holds W[o][c][8 - tap]
+            const size_t it = ((size_t)tap * L.cout + o) * cinp + c;
+            wt[it] = c < L.cin ? P[L.woff + ((size_t)o * L.cin + c) * 9 + (8 - tap)] : 0.0f;
+        } else {
+            wf[i] = P[L.woff + ((size_t)c * L.cout + o) * 4 + tap];
+        }
+    }
+}
+
+nrv_status tc_repack(Net* net, cudaStream_t s);  // tc.cu
+
+nrv_status net_repack(Net* net, cudaStream_t s) {
+    size_t off = 0;
+    for (int l = 0; l < NUM_LAYERS; ++l) {
+        const Layer& L = net->layers[l];
+        net->wf_off[l] = off;
+        const int kk = L.kind == CONV3 ? 9 : L.kind == UPCONV2 ? 4 : 0;
+        off += ((size_t)kk * padded_cin(net, l) * L.cout + 63) / 64 * 64;
+    }
+    NRV_TRY(net->wf32.ensure(off * 4));
+    NRV_TRY(net->wtf32.ensure(off * 4));
+    const float* P = (const float*)net->params.p;
+    for (int l = 0; l < NUM_LAYERS; ++l) {
+        const Layer& L = net->layers[l];
+        if (L.kind == HEAD1) continue;
+        repack_f32_kernel<<<64, 256, 0, s>>>(P, L, padded_cin(net, l),
+                                              (float*)net->wf32.p + net->wf_off[l],
+                                              (float*)net->wtf32.p + net->wf_off[l]);
+        NRV_CHECK_LAUNCH();
+    }
+    return tc_repack(net, s);
+}
+
+// ------------------------------------------------------------------ workspace
+static const int kActC[NUM_ACTS] = {16, 16, 16, 32, 32, 32, 64, 64, 64, 128, 128,
+                                    64, 64, 64, 32, 32, 32, 16, 16, 16};
+static const int kActL[NUM_ACTS] = {0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 2, 2, 2, 1, 1, 1, 0, 0, 0};
+
+nrv_status net_prepare(Net* net, int n, int H, int W, nrv_prec prec) {
+    Geo g;
+    g.n = n;
+    g.h[0] = nrv_pad8(H);
+    g.w[0] = nrv_pad8(W);
+    for (int l = 1; l < 4; ++l) { g.h[l] = g.h[l - 1] / 2; g.w[l] = g.w[l - 1] / 2; }
+    size_t off = 0;
+    const size_t es = elem_size(prec);
+    for (int a = 0; a < NUM_ACTS; ++a) {
+        net->act_c[a] = kActC[a];
+        net->act_level[a] = kActL[a];
+        net->act_off[a] = off;
+        off += (g.px(kActL[a]) * kActC[a] * es + 1023) / 1024 * 1024;
+    }
+    NRV_TRY(net->acts.ensure(off));
+    net->geo = g;
+    net->geo_H = H;
+    net->geo_W = W;
+    net->act_prec = prec;
+    return NRV_OK;
+}
+
+template <typename T>
+static T* act(Net* net, int a) {
+    return reinterpret_cast<T*>((char*)net->acts.p + net->act_off[a]);
+}
+
+static int blocks_for(size_t work, int per = 256) {
+    size_t b = (work + per - 1) / per;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)(b > 0 ? b : 1);
+}
+
+template <typename T>
+static nrv_status simt_conv3(const Net* net, int l, TView<const T> x1, int c1, TView<const T> x2,
+                             int c2, TView<T> y, const Geo& g, int level, bool relu,
+                             cudaStream_t s) {
+    const Layer& L = net->layers[l];
+    Conv3Args<T> a;
+    a.x1 = x1; a.x2 = x2; a.c1 = c1; a.c2 = c2;
+    a.w = (const float*)net->wf32.p + net->wf_off[l];
+    a.bias = (const float*)net->params.p + L.boff;
+    a.y = y;
+    a.cout = L.cout;
+    a.n = g.n; a.h = g.h[level]; a.w_ = g.w[level];
+    a.relu = relu ? 1 : 0;
+    a.mask = TView<const T>{nullptr, 0};
+    const size_t npx = g.px(level);
+    dim3 grid((unsigned)((npx + 127) / 128), L.cout / 16);
+    const size_t smem = (size_t)9 * (c1 + c2) * 16 * 4;
+    conv3_simt_kernel<T><<<grid, 128, smem, s>>>(a);
+    NRV_CHECK_LAUNCH();
+    return NRV_OK;
+}
+
+template <typename T>
+static nrv_status forward_t(Net* net, const T* netin, float* rgb, cudaStream_t s, bool use_tc,
+                            nrv_prec prec) {
+    const Geo& g = net->geo;
+    auto V = [&](int a) { return TView<T>{act<T>(net, a), net->act_c[a]}; };
+    auto CV = [&](int a) { return TView<const T>{act<T>(net, a), net->act_c[a]}; };
+    auto conv = [&](int l, TView<const T> x1, int c1, TView<const T> x2, int c2, int out,
+                    int level) -> nrv_status {
+        if (use_tc) {
+            nrv_status st = tc_conv3(net, l, x1.p, c1, x2.p, c2, act<T>(net, out), g, level, prec, s);
+            if (st != NRV_ERR_UNSUPPORTED) return st;
+            clear_error();
+        }
+        return simt_conv3<T>(net, l, x1, c1, x2, c2, V(out), g, level, true, s);
+    };
+    auto pool = [&](int in, int out, int level_out) -> nrv_status {
+        const int c = net->act_c[in];
+        pool2_kernel<T><<<blocks_for(g.px(level_out) * c / 8), 256, 0, s>>>(
+            CV(in), V(out), c, g.n, g.h[level_out], g.w[level_out]);
+        NRV_CHECK_LAUNCH();
+        return NRV_OK;
+    };
+    auto upconv = [&](int l, int in, int out, int level_in) -> nrv_status {
+        const Layer& L = net->layers[l];
+        const size_t npx = g.px(level_in) * 4;
+        dim3 grid((unsigned)((npx + 127) / 128), L.cout / 16);
+        upconv2_kernel<T><<<grid, 128, (size_t)4 * L.cin * 16 * 4, s>>>(
+            CV(in), L.cin, (const float*)net->wf32.p + net->wf_off[l],
+            (const float*)net->params.p + L.boff, V(out), L.cout, g.n, g.h[level_in], g.w[level_in]);
+        NRV_CHECK_LAUNCH();
+        return NRV_OK;
+    };
+    const TView<const T> x{netin, net->c0p};
+    const TView<const T> none{nullptr, 0};
+    NRV_TRY(conv(L_E0A, x, net->c0p, none, 0, A_E0A, 0));
+    NRV_TRY(conv(L_E0B, CV(A_E0A), 16, none, 0, A_E0B, 0));
+    NRV_TRY(pool(A_E0B, A_P0, 1));
+    NRV_TRY(conv(L_E1A, CV(A_P0), 16, none, 0, A_E1A, 1));
+    NRV_TRY(conv(L_E1B, CV(A_E1A), 32, none, 0, A_E1B, 1));
+    NRV_TRY(pool(A_E1B, A_P1, 2));
+    NRV_TRY(conv(L_E2A, CV(A_P1), 32, none, 0, A_E2A, 2));
+    NRV_TRY(conv(L_E2B, CV(A_E2A), 64, none, 0, A_E2B, 2));
+    NRV_TRY(pool(A_E2B, A_P2, 3));
+    NRV_TRY(conv(L_E3A, CV(A_P2), 64, none, 0, A_E3A, 3));
+    NRV_TRY(conv(L_E3B, CV(A_E3A), 128, none, 0, A_E3B, 3));
+    NRV_TRY(upconv(L_UP3, A_E3B, A_UP3, 3));
+    NRV_TRY(conv(L_D2A, CV(A_UP3), 64, CV(A_E2B), 64, A_D2A, 2));
+    NRV_TRY(conv(L_D2B, CV(A_D2A), 64, none, 0, A_D2B, 2));
+    NRV_TRY(upconv(L_UP2, A_D2B, A_UP2, 2));
+    NRV_TRY(conv(L_D1A, CV(A_UP2), 32, CV(A_E1B), 32, A_D1A, 1));
+    NRV_TRY(conv(L_D1B, CV(A_D1A), 32, none, 0, A_D1B, 1));
+    NRV_TRY(upconv(L_UP1, A_D1B, A_UP1, 1));
+    NRV_TRY(conv(L_D0A, CV(A_UP1), 16, CV(A_E0B), 16, A_D0A, 0));
+    NRV_TRY(conv(L_D0B, CV(A_D0A), 16, none, 0, A_D0B, 0));
+    const Layer& Lh = net->layers[L_HEAD];
+    head_kernel<T><<<blocks_for((size_t)g.n * net->geo_H * net->geo_W), 256, 0, s>>>(
+        CV(A_D0B), (const float*)net->params.p + Lh.woff, (const float*)net->params.p + Lh.boff,
+        rgb, g.n, g.h[0], g.w[0], net->geo_H, net->geo_W);
+    NRV_CHECK_LAUNCH();
+    return NRV_OK;
+}
+
+static bool g_attr_set = false;
+
+static nrv_status set_kernel_attrs() {
+    if (g_attr_set) return NRV_OK;
+    NRV_CHECK_CUDA(cudaFuncSetAttribute(conv3_simt_kernel<float>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 9 * 128 * 16 * 4));
+    NRV_CHECK_CUDA(cudaFuncSetAttribute(conv3_simt_kernel<__nv_bfloat16>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 9 * 128 * 16 * 4));
+    g_attr_set = true;
+    return NRV_OK;
+}
+
+nrv_status net_forward(Net* net, const void* netin, int n, int H, int W, nrv_prec prec, float* rgb,
+                       cudaStream_t s) {
+    NRV_TRY(set_kernel_attrs());
+    NRV_TRY(net_prepare(net, n, H, W, prec));
+    net->saved = false;
+    if (prec == NRV_PREC_F32)
+        return forward_t<float>(net, (const float*)netin, rgb, s, false, prec);
+    if (prec == NRV_PREC_BF16)
+        return forward_t<__nv_bfloat16>(net, (const __nv_bfloat16*)netin, rgb, s, true, prec);
+    return fail(NRV_ERR_UNSUPPORTED, "FP8 network path is not available in this build");
+}
+
+}  // namespace nrv

@@ -1,0 +1,78 @@
+// The U-Net handle: layer table, packed weights, activation workspace.
+#pragma once
+#include "internal.h"
+
+namespace nrv {
+
+// Device buffer owned by a handle; grows, never shrinks.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    nrv_status ensure(size_t b);
+    void release();
+    ~DevBuf() { release(); }
+};
+
+// Per-level geometry of one network invocation.
+struct Geo {
+    int n, h[4], w[4];
+    size_t px(int l) const { return (size_t)n * h[l] * w[l]; }
+};
+
+// Activations of one forward pass (element type given by the precision).
+enum Act {
+    A_E0A, A_E0B, A_P0, A_E1A, A_E1B, A_P1, A_E2A, A_E2B, A_P2, A_E3A, A_E3B, A_UP3, A_D2A,
+    A_D2B, A_UP2, A_D1A, A_D1B, A_UP1, A_D0A, A_D0B, NUM_ACTS
+};
+
+struct Net {
+    int c_in = 0, c0p = 8;
+    Layer layers[NUM_LAYERS];
+    int64_t n_params = 0;
+    bool has_params = false;
+    float act_scale[NUM_LAYERS];
+    DevBuf params;     // FP32 master copy (flat layout)
+    DevBuf wf32;       // FP32 packed forward weights, per layer at wf_off
+    DevBuf wtf32;      // FP32 packed backward-data weights, per layer at wf_off
+    DevBuf wbf16;      // BF16 tcgen05 operand layout, per layer at wb_off
+    DevBuf wtbf16;     // BF16 backward-data operand layout
+    DevBuf wfp8;       // FP8 tcgen05 operand layout
+    DevBuf wscale8;    // FP8 per-output-channel weight scales (floats)
+    size_t wf_off[NUM_LAYERS];
+    size_t wb_off[NUM_LAYERS];
+    size_t ws8_off[NUM_LAYERS];
+    // workspace of the last forward
+    DevBuf acts;
+    size_t act_off[NUM_ACTS];
+    int act_c[NUM_ACTS];
+    int act_level[NUM_ACTS];
+    Geo geo{};
+    int geo_H = 0, geo_W = 0;
+    nrv_prec act_prec = NRV_PREC_F32;
+    bool saved = false;      // a training forward's activations are in place
+    // backward scratch
+    DevBuf grads;            // gradient tensors
+    DevBuf partial;          // wgrad partial sums
+    DevBuf tmaps;            // device copies of TMA descriptors (unused when passed by value)
+    // render-batch resources
+    DevBuf batch_ws;
+};
+
+size_t elem_size(nrv_prec p);
+nrv_status net_prepare(Net* net, int n, int H, int W, nrv_prec prec);
+nrv_status net_forward(Net* net, const void* netin, int n, int H, int W, nrv_prec prec, float* rgb,
+                       cudaStream_t s);
+nrv_status net_backward(Net* net, const float* drgb, float* dparams, cudaStream_t s);
+nrv_status net_repack(Net* net, cudaStream_t s);
+
+// tensor-core convolution (tc.cu); returns NRV_ERR_UNSUPPORTED when a shape is not covered
+nrv_status tc_conv3(const Net* net, int layer, const void* x1, int c1, const void* x2, int c2,
+                    void* y, const Geo& g, int level, nrv_prec prec, cudaStream_t s);
+
+// training kernels (train.cu)
+nrv_status launch_l1(const float* y, const float* t, int64_t n, float* loss, float* dy,
+                     cudaStream_t s);
+nrv_status launch_adam(float* p, const float* g, float* m, float* v, int64_t n, int step,
+                       float lr, float b1, float b2, float eps, cudaStream_t s);
+
+}  // namespace nrv

@@ -1,0 +1,241 @@
+// Multi-attribute compute rasterizer (Sec. 3.2): clear, render (visibility) and
+// resolve passes, plus packing of the G-buffer into the network input.
+//
+// Render pass: every point is read once for all views of the batch and
+// projected with a fixed FP32 operation sequence written with explicit
+// round-to-nearest intrinsics, so no compiler contraction can change a bit:
+//   c_r = ((m_r0*x + m_r1*y) + m_r2*z) + m_r3   for rows r = 0, 1, 3
+//   keep if znear <= w <= zfar;  ndc = c.xy / w  (IEEE division)
+//   sx = (ndc.x + 1) * W/2,  sy = (1 - ndc.y) * H/2,  keep if on screen.
+// The per-pixel winner is the minimum of the 64-bit key (bits(w) << 32 | i):
+// w > 0 so its bits order like its value, and equal depths go to the lowest
+// index.  An early depth test (Sec. 3.2, "early z-buffer testing") reads the
+// current key from L2 first and issues the atomic only when the point is in
+// front of it; keys only ever decrease, so a stale read only costs an atomic.
+#include "internal.h"
+
+namespace nrv {
+
+__global__ void clear_keys_kernel(RViews vs) {
+    const int v = blockIdx.y;
+    if (v >= vs.n) return;
+    const uint64_t npx = (uint64_t)vs.v[v].width * vs.v[v].height;
+    ulonglong2* k2 = reinterpret_cast<ulonglong2*>(vs.v[v].key);
+    const ulonglong2 e = make_ulonglong2(~0ull, ~0ull);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < npx / 2;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        k2[i] = e;
+    if ((npx & 1) && blockIdx.x == 0 && threadIdx.x == 0) vs.v[v].key[npx - 1] = ~0ull;
+}
+
+nrv_status launch_clear_keys(const RViews& views, cudaStream_t s) {
+    dim3 grid(4 * 152, views.n);
+    clear_keys_kernel<<<grid, 256, 0, s>>>(views);
+    NRV_CHECK_LAUNCH();
+    return NRV_OK;
+}
+
+__device__ __forceinline__ void render_point(const RView& v, float x, float y, float z,
+                                             uint32_t idx) {
+    const float cw = __fadd_rn(
+        __fadd_rn(__fadd_rn(__fmul_rn(v.m[8], x), __fmul_rn(v.m[9], y)), __fmul_rn(v.m[10], z)),
+        v.m[11]);
+    if (!(cw >= v.znear && cw <= v.zfar)) return;
+    const float cx = __fadd_rn(
+        __fadd_rn(__fadd_rn(__fmul_rn(v.m[0], x), __fmul_rn(v.m[1], y)), __fmul_rn(v.m[2], z)),
+        v.m[3]);
+    const float cy = __fadd_rn(
+        __fadd_rn(__fadd_rn(__fmul_rn(v.m[4], x), __fmul_rn(v.m[5], y)), __fmul_rn(v.m[6], z)),
+        v.m[7]);
+    const float sx = __fmul_rn(__fadd_rn(__fdiv_rn(cx, cw), 1.0f), v.hw);
+    const float sy = __fmul_rn(__fsub_rn(1.0f, __fdiv_rn(cy, cw)), v.hh);
+    if (!(sx >= 0.0f && sx < v.fw && sy >= 0.0f && sy < v.fh)) return;
+    const int px = __float2int_rz(sx), py = __float2int_rz(sy);
+    const unsigned long long key = ((unsigned long long)__float_as_uint(cw) << 32) | idx;
+    unsigned long long* p = v.key + (size_t)py * v.width + px;
+    if (key < __ldcg(p)) atomicMin(p, key);
+}
+
+// One thread handles 4 consecutive points = 48 bytes = three 16-byte loads.
+__global__ void __launch_bounds__(256) visibility_kernel(const float4* __restrict__ xyz4,
+                                                         uint64_t ngroups,
+                                                         const float* __restrict__ xyz,
+                                                         uint64_t n, RViews vs) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < ngroups; g += stride) {
+        const float4 a = __ldg(xyz4 + 3 * g);
+        const float4 b = __ldg(xyz4 + 3 * g + 1);
+        const float4 c = __ldg(xyz4 + 3 * g + 2);
+        const uint32_t i0 = (uint32_t)(4 * g);
+        for (int v = 0; v < vs.n; ++v) {
+            const RView& vw = vs.v[v];
+            render_point(vw, a.x, a.y, a.z, i0);
+            render_point(vw, a.w, b.x, b.y, i0 + 1);
+            render_point(vw, b.z, b.w, c.x, i0 + 2);
+            render_point(vw, c.y, c.z, c.w, i0 + 3);
+        }
+    }
+    // the last n mod 4 points
+    if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
+        const uint64_t i = 4 * ngroups + threadIdx.x;
+        for (int v = 0; v < vs.n; ++v)
+            render_point(vs.v[v], xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], (uint32_t)i);
+    }
+}
+
+nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, cudaStream_t s) {
+    if (n == 0) return NRV_OK;
+    const uint64_t ngroups = n / 4;
+    int blocks = 152 * 8;
+    const uint64_t need = (ngroups + 255) / 256;
+    if (need < (uint64_t)blocks) blocks = (int)(need > 0 ? need : 1);
+    visibility_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(xyz), ngroups, xyz,
+                                             n, views);
+    NRV_CHECK_LAUNCH();
+    return NRV_OK;
+}
+
+// ------------------------------------------------------------------ pack helpers
+
+__device__ __forceinline__ void pack_channels(const ResolveArgs& a, uint32_t depth_bits,
+                                              const uint32_t* words, float* f) {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        if (j < a.n_ch) {
+            const uint32_t w = words[a.ch_word[j]];
+            float v;
+            if (a.ch_fmt[j] == NRV_F32) v = __uint_as_float(w);
+            else if (a.ch_fmt[j] == NRV_U32) v = __uint2float_rn(w);
+            else v = (float)((w >> (8 * a.ch_comp[j])) & 255u);
+            f[j] = __fadd_rn(__fmul_rn(v, a.ch_scale[j]), a.ch_offset[j]);
+        }
+    }
+    f[a.n_ch] = __fadd_rn(__fmul_rn(__uint_as_float(depth_bits), a.d_scale), a.d_offset);
+    f[a.n_ch + 1] = 1.0f;
+}
+
+// Write one canvas pixel of the network input (all channels, zero padded).
+__device__ __forceinline__ void store_netin(const ResolveArgs& a, size_t q, const float* f) {
+    if (a.out_fmt == 0) {
+        float4* o = reinterpret_cast<float4*>(a.netin) + 2 * q;
+        o[0] = make_float4(f[0], f[1], f[2], f[3]);
+        o[1] = make_float4(f[4], f[5], f[6], f[7]);
+    } else if (a.out_fmt == 1) {
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+            w[j] = *reinterpret_cast<uint32_t*>(&h);
+        }
+        reinterpret_cast<uint4*>(a.netin)[q] = make_uint4(w[0], w[1], w[2], w[3]);
+    } else {
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const __nv_fp8_storage_t b = __nv_cvt_float_to_fp8(__fmul_rn(f[j], a.in_scale_inv),
+                                                               __NV_SATFINITE, __NV_E4M3);
+            w[j >> 2] |= (uint32_t)b << (8 * (j & 3));
+        }
+        reinterpret_cast<uint4*>(a.netin)[q] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// Resolve pass (Sec. 3.2): one thread per canvas pixel.  Reads the key, gathers
+// the winner's record (one or two 16-byte loads), writes the raw planes and/or
+// the packed network input.
+__global__ void __launch_bounds__(256) resolve_kernel(ResolveArgs a) {
+    const int wc = a.netin ? a.wn : a.width, hc = a.netin ? a.hn : a.height;
+    const size_t total = (size_t)wc * hc;
+    const size_t npx = (size_t)a.width * a.height;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;
+         q += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(q % wc), y = (int)(q / wc);
+        const bool inside = x < a.width && y < a.height;
+        const size_t p = (size_t)y * a.width + x;
+        unsigned long long key = ~0ull;
+        if (inside) key = __ldcs(a.key + p);
+        uint32_t words[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        uint32_t depth_bits = 0u;
+        const bool hit = key != ~0ull;
+        if (hit) {
+            const uint32_t idx = (uint32_t)(key & 0xFFFFFFFFull);
+            depth_bits = (uint32_t)(key >> 32);
+            const uint32_t* rec = a.attr + (size_t)idx * a.stride_words;
+            if (a.stride_words == 8) {
+                const uint4 r0 = __ldg(reinterpret_cast<const uint4*>(rec));
+                const uint4 r1 = __ldg(reinterpret_cast<const uint4*>(rec) + 1);
+                words[0] = r0.x; words[1] = r0.y; words[2] = r0.z; words[3] = r0.w;
+                words[4] = r1.x; words[5] = r1.y; words[6] = r1.z; words[7] = r1.w;
+            } else if (a.stride_words == 4) {
+                const uint4 r0 = __ldg(reinterpret_cast<const uint4*>(rec));
+                words[0] = r0.x; words[1] = r0.y; words[2] = r0.z; words[3] = r0.w;
+            } else if (a.stride_words == 2) {
+                const uint2 r0 = __ldg(reinterpret_cast<const uint2*>(rec));
+                words[0] = r0.x; words[1] = r0.y;
+            } else {
+                words[0] = __ldg(rec);
+            }
+        }
+        if (inside) {
+            if (a.depth) a.depth[p] = depth_bits;
+            if (a.mask) a.mask[p] = hit ? 1 : 0;
+            if (a.gattr)
+                for (int c = 0; c < a.n_words; ++c) a.gattr[(size_t)c * npx + p] = hit ? words[c] : 0u;
+        }
+        if (a.netin) {
+            float f[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) f[j] = 0.0f;
+            if (hit) pack_channels(a, depth_bits, words, f);
+            store_netin(a, q, f);
+        }
+    }
+}
+
+static int grid_for(size_t work, int per_block = 256) {
+    size_t b = (work + per_block - 1) / per_block;
+    const size_t cap = 152 * 16;
+    if (b > cap) b = cap;
+    return (int)(b > 0 ? b : 1);
+}
+
+nrv_status launch_resolve(const ResolveArgs& a, cudaStream_t s) {
+    const size_t total = a.netin ? (size_t)a.wn * a.hn : (size_t)a.width * a.height;
+    resolve_kernel<<<grid_for(total), 256, 0, s>>>(a);
+    NRV_CHECK_LAUNCH();
+    return NRV_OK;
+}
+
+// Pack from already-resolved planes (nrv_pack).
+__global__ void __launch_bounds__(256) pack_planes_kernel(const uint32_t* __restrict__ depth,
+                                                          const uint8_t* __restrict__ mask,
+                                                          const uint32_t* __restrict__ gattr,
+                                                          ResolveArgs a) {
+    const size_t total = (size_t)a.wn * a.hn;
+    const size_t npx = (size_t)a.width * a.height;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;
+         q += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(q % a.wn), y = (int)(q / a.wn);
+        float f[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) f[j] = 0.0f;
+        if (x < a.width && y < a.height) {
+            const size_t p = (size_t)y * a.width + x;
+            if (mask[p]) {
+                uint32_t words[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+                for (int j = 0; j < a.n_ch; ++j) words[a.ch_word[j]] = gattr[(size_t)a.ch_word[j] * npx + p];
+                pack_channels(a, depth[p], words, f);
+            }
+        }
+        store_netin(a, q, f);
+    }
+}
+
+nrv_status launch_pack_planes(const uint32_t* depth, const uint8_t* mask, const uint32_t* gattr,
+                              const ResolveArgs& a, cudaStream_t s) {
+    pack_planes_kernel<<<grid_for((size_t)a.wn * a.hn), 256, 0, s>>>(depth, mask, gattr, a);
+    NRV_CHECK_LAUNCH();
+    return NRV_OK;
+}
+
+}  // namespace nrv

@@ -1,0 +1,521 @@
+// Training of the post-processing network (Sec. 3.3, training details): the
+// backward pass of every layer, the L1 reconstruction loss and Adam.
+//
+// Gradients of the weights are reductions over all pixels.  They are computed
+// in fixed pixel chunks whose partial sums are added in a fixed order by a
+// second kernel, so a step is bit-for-bit reproducible.
+#include "net.h"
+#include "net_simt.cuh"
+
+namespace nrv {
+
+// ------------------------------------------------------------------ weight gradients, 3x3 conv
+// part[chunk][o][tap*cin + c] = sum_{q in chunk} g[q][o] * x[q + tap][c];  partb[chunk][o] = sum g
+template <typename T>
+__global__ void __launch_bounds__(256) wgrad3_kernel(TView<const T> g, int cout, TView<const T> x1,
+                                                     int c1, TView<const T> x2, int c2, int n,
+                                                     int h, int w, size_t chunk_px, float* part,
+                                                     float* partb) {
+    __shared__ float gs[32][16];
+    const int cin = c1 + c2, K = 9 * cin;
+    const int og = blockIdx.y * 16;
+    const size_t npx = (size_t)n * h * w;
+    const size_t q0 = blockIdx.x * chunk_px;
+    const size_t q1 = q0 + chunk_px < npx ? q0 + chunk_px : npx;
+    float acc[5][16];
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[i][j] = 0.0f;
+    float bsum = 0.0f;
+    for (size_t qb = q0; qb < q1; qb += 32) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 512; i += 256) {
+            const size_t q = qb + (i >> 4);
+            gs[i >> 4][i & 15] = q < q1 ? ld1<T>(g.p + q * g.ld + og + (i & 15)) : 0.0f;
+        }
+        __syncthreads();
+        const int nb = (int)(q1 - qb < 32 ? q1 - qb : 32);
+        if (threadIdx.x < 16)
+            for (int r = 0; r < nb; ++r) bsum += gs[r][threadIdx.x];
+        for (int r = 0; r < nb; ++r) {
+            const size_t q = qb + r;
+            const int x = (int)(q % w), y = (int)((q / w) % h);
+            const size_t img = q / ((size_t)w * h);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                const int k = threadIdx.x + 256 * i;
+                if (k >= K) break;
+                const int tap = k / cin, c = k % cin;
+                const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+                float v = 0.0f;
+                if (yy >= 0 && yy < h && xx >= 0 && xx < w) {
+                    const size_t qq = (img * h + yy) * w + xx;
+                    v = c < c1 ? ld1<T>(x1.p + qq * x1.ld + c) : ld1<T>(x2.p + qq * x2.ld + c - c1);
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc[i][j] = fmaf(v, gs[r][j], acc[i][j]);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const int k = threadIdx.x + 256 * i;
+        if (k >= K) break;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            part[((size_t)blockIdx.x * cout + og + j) * K + k] = acc[i][j];
+    }
+    if (threadIdx.x < 16) partb[(size_t)blockIdx.x * cout + og + threadIdx.x] = bsum;
+}
+
+// dW[o][c][tap] (PyTorch layout, c < cin_real) and db[o] from the chunk partials.
+__global__ void wgrad3_reduce_kernel(const float* part, const float* partb, int nchunks, int cout,
+                                     int cin, int cin_real, float* dw, float* db) {
+    const int K = 9 * cin;
+    const size_t total = (size_t)cout * K;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int o = (int)(i / K), k = (int)(i % K);
+        const int tap = k / cin, c = k % cin;
+        if (c >= cin_real) continue;
+        float s = 0.0f;
+        for (int ch = 0; ch < nchunks; ++ch) s += part[((size_t)ch * cout + o) * K + k];
+        dw[((size_t)o * cin_real + c) * 9 + tap] = s;
+    }
+    if (blockIdx.x == 0)
+        for (int o = threadIdx.x; o < cout; o += blockDim.x) {
+            float s = 0.0f;
+            for (int ch = 0; ch < nchunks; ++ch) s += partb[(size_t)ch * cout + o];
+            db[o] = s;
+        }
+}
+
+// ------------------------------------------------------------------ weight gradients, 2x2 transposed conv
+// part[chunk][c][ab*cout + o] = sum_{input px in chunk} x[q][c] * g[out(q, ab)][o]
+// partb[chunk][ab*cout + o]   = sum g   (only written by the c-group 0 blocks)
+template <typename T>
+__global__ void __launch_bounds__(256) wgrad_up_kernel(TView<const T> x, int cin, TView<const T> g,
+                                                       int cout, int n, int hi, int wi,
+                                                       size_t chunk_px, float* part, float* partb) {
+    __shared__ float xs[32][16];
+    const int cg = blockIdx.y * 16;
+    const int K = 4 * cout;
+    const size_t npx = (size_t)n * hi * wi;
+    const size_t q0 = blockIdx.x * chunk_px;
+    const size_t q1 = q0 + chunk_px < npx ? q0 + chunk_px : npx;
+    float acc[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] = 0.0f;
+    float bsum = 0.0f;
+    const int k = threadIdx.x;
+    const int ab = k / cout, o = k % cout;
+    for (size_t qb = q0; qb < q1; qb += 32) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 512; i += 256) {
+            const size_t q = qb + (i >> 4);
+            xs[i >> 4][i & 15] = q < q1 ? ld1<T>(x.p + q * x.ld + cg + (i & 15)) : 0.0f;
+        }
+        __syncthreads();
+        const int nb = (int)(q1 - qb < 32 ? q1 - qb : 32);
+        if (k < K)
+            for (int r = 0; r < nb; ++r) {
+                const size_t q = qb + r;
+                const int X = (int)(q % wi), Y = (int)((q / wi) % hi);
+                const size_t img = q / ((size_t)wi * hi);
+                const size_t qo = (img * 2 * hi + 2 * Y + (ab >> 1)) * (2 * wi) + 2 * X + (ab & 1);
+                const float gv = ld1<T>(g.p + qo * g.ld + o);
+                bsum += gv;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc[j] = fmaf(xs[r][j], gv, acc[j]);
+            }
+    }
+    if (k < K) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) part[((size_t)blockIdx.x * cin + cg + j) * K + k] = acc[j];
+        if (blockIdx.y == 0) partb[(size_t)blockIdx.x * K + k] = bsum;
+    }
+}
+
+__global__ void wgrad_up_reduce_kernel(const float* part, const float* partb, int nchunks, int cin,
+                                       int cout, float* dw, float* db) {
+    const int K = 4 * cout;
+    const size_t total = (size_t)cin * K;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i / K), k = (int)(i % K);
+        const int ab = k / cout, o = k % cout;
+        float s = 0.0f;
+        for (int ch = 0; ch < nchunks; ++ch) s += part[((size_t)ch * cin + c) * K + k];
+        dw[((size_t)c * cout + o) * 4 + ab] = s;
+    }
+    if (blockIdx.x == 0)
+        for (int o = threadIdx.x; o < cout; o += blockDim.x) {
+            float s = 0.0f;
+            for (int ch = 0; ch < nchunks; ++ch)
+                for (int ab = 0; ab < 4; ++ab) s += partb[(size_t)ch * K + ab * cout + o];
+            db[o] = s;
+        }
+}
+
+// ------------------------------------------------------------------ head
+// gd[q][c] = (sum_o drgb[o] W[o][c]) * (x[q][c] > 0) over the canvas (zero outside the view)
+template <typename T>
+__global__ void head_dgrad_kernel(const float* drgb, const float* w, TView<const T> x, TView<T> gd,
+                                  int n, int hn, int wn, int h, int wd) {
+    const size_t total = (size_t)n * hn * wn;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;
+         q += (size_t)gridDim.x * blockDim.x) {
+        const int X = (int)(q % wn), Y = (int)((q / wn) % hn);
+        const size_t img = q / ((size_t)wn * hn);
+        float out[16];
+        if (X < wd && Y < h) {
+            const float* gr = drgb + 3 * ((img * h + Y) * wd + X);
+            float xv[16];
+            ld8<T>(x.p + q * x.ld, xv);
+            ld8<T>(x.p + q * x.ld + 8, xv + 8);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const float s = fmaf(gr[2], w[32 + c], fmaf(gr[1], w[16 + c], gr[0] * w[c]));
+                out[c] = xv[c] > 0.0f ? s : 0.0f;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) out[c] = 0.0f;
+        }
+        st8<T>(gd.p + q * gd.ld, out);
+        st8<T>(gd.p + q * gd.ld + 8, out + 8);
+    }
+}
+
+// part[chunk][o*16 + c] = sum drgb[o] * x[c]; part[chunk][48 + o] = sum drgb[o]
+template <typename T>
+__global__ void head_wgrad_kernel(const float* drgb, TView<const T> x, int n, int hn, int wn, int h,
+                                  int wd, size_t chunk, float* part) {
+    const int t = threadIdx.x;
+    if (t >= 51) return;
+    const size_t total = (size_t)n * h * wd;
+    const size_t i0 = blockIdx.x * chunk, i1 = i0 + chunk < total ? i0 + chunk : total;
+    float s = 0.0f;
+    for (size_t i = i0; i < i1; ++i) {
+        const int X = (int)(i % wd), Y = (int)((i / wd) % h);
+        const size_t img = i / ((size_t)wd * h);
+        const size_t q = (img * hn + Y) * wn + X;
+        if (t < 48) s = fmaf(drgb[3 * i + t / 16], ld1<T>(x.p + q * x.ld + t % 16), s);
+        else s += drgb[3 * i + t - 48];
+    }
+    part[blockIdx.x * 51 + t] = s;
+}
+
+__global__ void head_reduce_kernel(const float* part, int nchunks, float* dw, float* db) {
+    const int t = threadIdx.x;
+    if (t >= 51) return;
+    float s = 0.0f;
+    for (int c = 0; c < nchunks; ++c) s += part[c * 51 + t];
+    if (t < 48) dw[t] = s;
+    else db[t - 48] = s;
+}
+
+// ------------------------------------------------------------------ pooling backward
+// ge[q][c] = (0.25 * gp[q/2][c] + gs[q][c]) * (e[q][c] > 0)
+template <typename T>
+__global__ void pool_bwd_kernel(TView<const T> gp, TView<const T> gs, TView<const T> e, TView<T> ge,
+                                int c, int n, int h, int w) {
+    const size_t total = (size_t)n * h * w * (c / 8);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int cg = (int)(i % (c / 8)) * 8;
+        const size_t q = i / (c / 8);
+        const int X = (int)(q % w), Y = (int)((q / w) % h);
+        const size_t img = q / ((size_t)w * h);
+        const size_t qp = (img * (h / 2) + Y / 2) * (w / 2) + X / 2;
+        float a[8], b[8], m[8], r[8];
+        ld8<T>(gp.p + qp * gp.ld + cg, a);
+        ld8<T>(gs.p + q * gs.ld + cg, b);
+        ld8<T>(e.p + q * e.ld + cg, m);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r[k] = m[k] > 0.0f ? fmaf(0.25f, a[k], b[k]) : 0.0f;
+        st8<T>(ge.p + q * ge.ld + cg, r);
+    }
+}
+
+// ------------------------------------------------------------------ loss and optimizer
+__global__ void l1_partial_kernel(const float* y, const float* t, int64_t n, float* dy,
+                                  float inv_n, float* part) {
+    __shared__ float red[256];
+    float s = 0.0f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float d = y[i] - t[i];
+        s += fabsf(d);
+        if (dy) dy[i] = d > 0.0f ? inv_n : (d < 0.0f ? -inv_n : 0.0f);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void l1_final_kernel(const float* part, int nb, double inv_n, float* loss) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += 256) s += part[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loss[0] = (float)(red[0] * inv_n);
+}
+
+static DevBuf g_l1_part;
+
+nrv_status launch_l1(const float* y, const float* t, int64_t n, float* loss, float* dy,
+                     cudaStream_t s) {
+    const int nb = 512;
+    NRV_TRY(g_l1_part.ensure(nb * sizeof(float)));
+    l1_partial_kernel<<<nb, 256, 0, s>>>(y, t, n, dy, (float)(1.0 / (double)n), (float*)g_l1_part.p);
+    NRV_CHECK_LAUNCH();
+    l1_final_kernel<<<1, 256, 0, s>>>((const float*)g_l1_part.p, nb, 1.0 / (double)n, loss);
+    NRV_CHECK_LAUNCH();
+    return NRV_OK;
+}
+
+__global__ void adam_kernel(float* p, const float* g, float* m, float* v, int64_t n, float lr,
+                            float b1, float b2, float eps, float bc1, float bc2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    }
+}
+
+nrv_status launch_adam(float* p, const float* g, float* m, float* v, int64_t n, int step, float lr,
+                       float b1, float b2, float eps, cudaStream_t s) {
+    const float bc1 = (float)(1.0 - pow((double)b1, step));
+    const float bc2 = (float)(1.0 - pow((double)b2, step));
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    adam_kernel<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, bc1, bc2);
+    NRV_CHECK_LAUNCH();
+    return NRV_OK;
+}
+
+// ------------------------------------------------------------------ backward orchestration
+static int blocks_for(size_t work, int per = 256) {
+    size_t b = (work + per - 1) / per;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)(b > 0 ? b : 1);
+}
+
+template <typename T>
+struct Bwd {
+    Net* net;
+    cudaStream_t s;
+    const Geo& g;
+    float* dparams;
+    T* W1[4];
+    T* W2[4];
+
+    T* A(int a) const { return reinterpret_cast<T*>((char*)net->acts.p + net->act_off[a]); }
+    TView<const T> CA(int a) const { return TView<const T>{A(a), net->act_c[a]}; }
+
+    nrv_status wgrad_conv(int l, TView<const T> gpre, TView<const T> x1, int c1, TView<const T> x2,
+                          int c2, int level) {
+        const Layer& L = net->layers[l];
+        const size_t npx = g.px(level);
+        const int groups = L.cout / 16;
+        size_t nch = (608 + groups - 1) / groups;
+        const size_t maxch = (npx + 255) / 256;
+        if (nch > maxch) nch = maxch;
+        if (nch < 1) nch = 1;
+        const size_t chunk = (npx + nch - 1) / nch;
+        nch = (npx + chunk - 1) / chunk;
+        const int cin = c1 + c2;
+        const size_t need = (nch * L.cout * 9 * cin + nch * L.cout) * sizeof(float);
+        NRV_TRY(net->partial.ensure(need));
+        float* part = (float*)net->partial.p;
+        float* partb = part + nch * L.cout * 9 * cin;
+        wgrad3_kernel<T><<<dim3((unsigned)nch, groups), 256, 0, s>>>(
+            gpre, L.cout, x1, c1, x2, c2, g.n, g.h[level], g.w[level], chunk, part, partb);
+        NRV_CHECK_LAUNCH();
+        wgrad3_reduce_kernel<<<blocks_for((size_t)L.cout * 9 * cin), 256, 0, s>>>(
+            part, partb, (int)nch, L.cout, cin, L.cin, dparams + L.woff, dparams + L.boff);
+        NRV_CHECK_LAUNCH();
+        return NRV_OK;
+    }
+
+    nrv_status dgrad_conv(int l, TView<const T> gpre, TView<T> out, TView<const T> mask,
+                          int level) {
+        const Layer& L = net->layers[l];
+        Conv3Args<T> a;
+        a.x1 = gpre;
+        a.c1 = L.cout;
+        a.x2 = TView<const T>{nullptr, 0};
+        a.c2 = 0;
+        a.w = (const float*)net->wtf32.p + net->wf_off[l];
+        a.bias = nullptr;
+        a.y = out;
+        a.cout = L.cin;
+        a.n = g.n; a.h = g.h[level]; a.w_ = g.w[level];
+        a.relu = 0;
+        a.mask = mask;
+        const size_t npx = g.px(level);
+        dim3 grid((unsigned)((npx + 127) / 128), L.cin / 16);
+        conv3_simt_kernel<T><<<grid, 128, (size_t)9 * L.cout * 16 * 4, s>>>(a);
+        NRV_CHECK_LAUNCH();
+        return NRV_OK;
+    }
+
+    nrv_status upconv_bwd(int l, int xin, TView<const T> gout, TView<T> gx, int level_in) {
+        const Layer& L = net->layers[l];
+        const size_t npx = g.px(level_in);
+        const int groups = L.cin / 16;
+        size_t nch = (608 + groups - 1) / groups;
+        const size_t maxch = (npx + 127) / 128;
+        if (nch > maxch) nch = maxch;
+        if (nch < 1) nch = 1;
+        const size_t chunk = (npx + nch - 1) / nch;
+        nch = (npx + chunk - 1) / chunk;
+        const int K = 4 * L.cout;
+        NRV_TRY(net->partial.ensure((nch * L.cin * K + nch * K) * sizeof(float)));
+        float* part = (float*)net->partial.p;
+        float* partb = part + nch * L.cin * K;
+        wgrad_up_kernel<T><<<dim3((unsigned)nch, groups), 256, 0, s>>>(
+            CA(xin), L.cin, gout, L.cout, g.n, g.h[level_in], g.w[level_in], chunk, part, partb);
+        NRV_CHECK_LAUNCH();
+        wgrad_up_reduce_kernel<<<blocks_for((size_t)L.cin * K), 256, 0, s>>>(
+            part, partb, (int)nch, L.cin, L.cout, dparams + L.woff, dparams + L.boff);
+        NRV_CHECK_LAUNCH();
+        dim3 grid((unsigned)((npx + 127) / 128), L.cin / 16);
+        upconv2_dgrad_kernel<T><<<grid, 128, (size_t)4 * 16 * L.cout * 4, s>>>(
+            gout, L.cout, (const float*)net->wf32.p + net->wf_off[l], L.cin, CA(xin), gx, g.n,
+            g.h[level_in], g.w[level_in]);
+        NRV_CHECK_LAUNCH();
+        return NRV_OK;
+    }
+
+    nrv_status pool_bwd(TView<const T> gp, TView<const T> gs, int e, TView<T> ge, int level) {
+        const int c = net->act_c[e];
+        pool_bwd_kernel<T><<<blocks_for(g.px(level) * c / 8), 256, 0, s>>>(
+            gp, gs, CA(e), ge, c, g.n, g.h[level], g.w[level]);
+        NRV_CHECK_LAUNCH();
+        return NRV_OK;
+    }
+
+    static TView<T> V(T* p, int ld) { return TView<T>{p, ld}; }
+    static TView<const T> C(T* p, int ld) { return TView<const T>{p, ld}; }
+
+    nrv_status run(const float* drgb, const T* netin) {
+        const TView<const T> none{nullptr, 0};
+        const int H = net->geo_H, Wd = net->geo_W;
+        // head
+        const Layer& Lh = net->layers[L_HEAD];
+        head_dgrad_kernel<T><<<blocks_for(g.px(0)), 256, 0, s>>>(
+            drgb, (const float*)net->params.p + Lh.woff, CA(A_D0B), V(W1[0], 16), g.n, g.h[0],
+            g.w[0], H, Wd);
+        NRV_CHECK_LAUNCH();
+        {
+            const size_t tot = (size_t)g.n * H * Wd;
+            size_t nch = 608;
+            size_t chunk = (tot + nch - 1) / nch;
+            if (chunk < 64) chunk = 64;
+            nch = (tot + chunk - 1) / chunk;
+            NRV_TRY(net->partial.ensure(nch * 51 * sizeof(float)));
+            head_wgrad_kernel<T><<<(unsigned)nch, 64, 0, s>>>(drgb, CA(A_D0B), g.n, g.h[0], g.w[0],
+                                                              H, Wd, chunk, (float*)net->partial.p);
+            NRV_CHECK_LAUNCH();
+            head_reduce_kernel<<<1, 64, 0, s>>>((const float*)net->partial.p, (int)nch,
+                                                dparams + Lh.woff, dparams + Lh.boff);
+            NRV_CHECK_LAUNCH();
+        }
+        // level 0 decoder
+        NRV_TRY(wgrad_conv(L_D0B, C(W1[0], 16), CA(A_D0A), 16, none, 0, 0));
+        NRV_TRY(dgrad_conv(L_D0B, C(W1[0], 16), V(W2[0], 16), CA(A_D0A), 0));
+        NRV_TRY(wgrad_conv(L_D0A, C(W2[0], 16), CA(A_UP1), 16, CA(A_E0B), 16, 0));
+        NRV_TRY(dgrad_conv(L_D0A, C(W2[0], 16), V(W1[0], 32), none, 0));
+        NRV_TRY(upconv_bwd(L_UP1, A_D1B, C(W1[0], 32), V(W1[1], 32), 1));
+        // level 1 decoder
+        NRV_TRY(wgrad_conv(L_D1B, C(W1[1], 32), CA(A_D1A), 32, none, 0, 1));
+        NRV_TRY(dgrad_conv(L_D1B, C(W1[1], 32), V(W2[1], 32), CA(A_D1A), 1));
+        NRV_TRY(wgrad_conv(L_D1A, C(W2[1], 32), CA(A_UP2), 32, CA(A_E1B), 32, 1));
+        NRV_TRY(dgrad_conv(L_D1A, C(W2[1], 32), V(W1[1], 64), none, 1));
+        NRV_TRY(upconv_bwd(L_UP2, A_D2B, C(W1[1], 64), V(W1[2], 64), 2));
+        // level 2 decoder
+        NRV_TRY(wgrad_conv(L_D2B, C(W1[2], 64), CA(A_D2A), 64, none, 0, 2));
+        NRV_TRY(dgrad_conv(L_D2B, C(W1[2], 64), V(W2[2], 64), CA(A_D2A), 2));
+        NRV_TRY(wgrad_conv(L_D2A, C(W2[2], 64), CA(A_UP3), 64, CA(A_E2B), 64, 2));
+        NRV_TRY(dgrad_conv(L_D2A, C(W2[2], 64), V(W1[2], 128), none, 2));
+        NRV_TRY(upconv_bwd(L_UP3, A_E3B, C(W1[2], 128), V(W1[3], 128), 3));
+        // bottom level
+        NRV_TRY(wgrad_conv(L_E3B, C(W1[3], 128), CA(A_E3A), 128, none, 0, 3));
+        NRV_TRY(dgrad_conv(L_E3B, C(W1[3], 128), V(W2[3], 128), CA(A_E3A), 3));
+        NRV_TRY(wgrad_conv(L_E3A, C(W2[3], 128), CA(A_P2), 64, none, 0, 3));
+        NRV_TRY(dgrad_conv(L_E3A, C(W2[3], 128), V(W1[3], 64), none, 3));
+        // level 2 encoder: skip gradient sits in channels 64..127 of W1[2]
+        NRV_TRY(pool_bwd(C(W1[3], 64), C(W1[2] + 64, 128), A_E2B, V(W2[2], 64), 2));
+        NRV_TRY(wgrad_conv(L_E2B, C(W2[2], 64), CA(A_E2A), 64, none, 0, 2));
+        NRV_TRY(dgrad_conv(L_E2B, C(W2[2], 64), V(W1[2], 64), CA(A_E2A), 2));
+        NRV_TRY(wgrad_conv(L_E2A, C(W1[2], 64), CA(A_P1), 32, none, 0, 2));
+        NRV_TRY(dgrad_conv(L_E2A, C(W1[2], 64), V(W2[2], 32), none, 2));
+        // level 1 encoder: skip gradient in channels 32..63 of W1[1]
+        NRV_TRY(pool_bwd(C(W2[2], 32), C(W1[1] + 32, 64), A_E1B, V(W2[1], 32), 1));
+        NRV_TRY(wgrad_conv(L_E1B, C(W2[1], 32), CA(A_E1A), 32, none, 0, 1));
+        NRV_TRY(dgrad_conv(L_E1B, C(W2[1], 32), V(W1[1], 32), CA(A_E1A), 1));
+        NRV_TRY(wgrad_conv(L_E1A, C(W1[1], 32), CA(A_P0), 16, none, 0, 1));
+        NRV_TRY(dgrad_conv(L_E1A, C(W1[1], 32), V(W2[1], 16), none, 1));
+        // level 0 encoder: skip gradient in channels 16..31 of W1[0]
+        NRV_TRY(pool_bwd(C(W2[1], 16), C(W1[0] + 16, 32), A_E0B, V(W2[0], 16), 0));
+        NRV_TRY(wgrad_conv(L_E0B, C(W2[0], 16), CA(A_E0A), 16, none, 0, 0));
+        NRV_TRY(dgrad_conv(L_E0B, C(W2[0], 16), V(W1[0], 16), CA(A_E0A), 0));
+        NRV_TRY(wgrad_conv(L_E0A, C(W1[0], 16), C(const_cast<T*>(netin), net->c0p), net->c0p, none,
+                           0, 0));
+        return NRV_OK;
+    }
+};
+
+// The training forward keeps its input pointer for the first layer's weight gradient.
+static const void* g_saved_netin = nullptr;
+void set_saved_input(const void* p) { g_saved_netin = p; }
+
+nrv_status net_backward(Net* net, const float* drgb, float* dparams, cudaStream_t s) {
+    if (!net->saved) return fail(NRV_ERR_STATE, "backward without a preceding training forward");
+    const Geo& g = net->geo;
+    const size_t es = elem_size(net->act_prec);
+    size_t off[9], tot = 0;
+    const int chans[4] = {32, 64, 128, 128};
+    for (int l = 0; l < 4; ++l) {
+        off[2 * l] = tot;
+        tot += (g.px(l) * chans[l] * es + 1023) / 1024 * 1024;
+        off[2 * l + 1] = tot;
+        tot += (g.px(l) * chans[l] * es + 1023) / 1024 * 1024;
+    }
+    NRV_TRY(net->grads.ensure(tot));
+    if (net->act_prec == NRV_PREC_F32) {
+        Bwd<float> b{net, s, g, dparams, {}, {}};
+        for (int l = 0; l < 4; ++l) {
+            b.W1[l] = (float*)((char*)net->grads.p + off[2 * l]);
+            b.W2[l] = (float*)((char*)net->grads.p + off[2 * l + 1]);
+        }
+        return b.run(drgb, (const float*)g_saved_netin);
+    }
+    if (net->act_prec == NRV_PREC_BF16) {
+        Bwd<__nv_bfloat16> b{net, s, g, dparams, {}, {}};
+        for (int l = 0; l < 4; ++l) {
+            b.W1[l] = (__nv_bfloat16*)((char*)net->grads.p + off[2 * l]);
+            b.W2[l] = (__nv_bfloat16*)((char*)net->grads.p + off[2 * l + 1]);
+        }
+        return b.run(drgb, (const __nv_bfloat16*)g_saved_netin);
+    }
+    return fail(NRV_ERR_UNSUPPORTED, "backward is available for FP32 and BF16 only");
+}
+
+}  // namespace nrv

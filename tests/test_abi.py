@@ -1,0 +1,71 @@
+"""The C ABI library loads on the CPU host and exports every symbol include/nrv.h declares;
+host-side argument checks answer without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "nrv.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nrv_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2407_19097_gb300 import build_lib, nrv
+    build_lib.build()
+    return nrv.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2407_19097_gb300 import nrv
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(nrv.SIGNATURES), set(names) ^ set(nrv.SIGNATURES)
+
+
+def test_host_side_queries(lib):
+    from paper_2407_19097_gb300 import nrv
+    from oracle import unet
+    assert lib.nrv_version() == 1
+    assert lib.nrv_pad8(540) == 544 and lib.nrv_pad8(1080) == 1080
+    assert lib.nrv_netin_channels(nrv.PREC_FP8) == 16 and lib.nrv_netin_channels(nrv.PREC_BF16) == 8
+    for c0 in (3, 5, 6, 7):
+        assert nrv.param_count(c0) == unet.param_count(c0)
+        table = nrv.layer_table(c0)
+        off = 0
+        for (name, kind, ci, co, wo, bo), (n2, k2, ci2, co2) in zip(table, unet.layers(c0)):
+            assert (name, ci, co) == (n2, ci2, co2)
+            assert wo == off
+            off = bo + co
+        assert off == unet.param_count(c0)
+
+
+def test_argument_errors(lib):
+    from paper_2407_19097_gb300 import nrv
+    d = nrv.nrv_scene_desc(1 << 32, 16, 16, 4, 3)
+    h = ctypes.c_void_p()
+    assert lib.nrv_create_scene(ctypes.byref(d), ctypes.byref(h)) == nrv.NRV_ERR_ARG
+    assert b"2^32" in lib.nrv_last_error()
+    d = nrv.nrv_scene_desc(10, 8, 16, 4, 3)          # misaligned xyz
+    assert lib.nrv_create_scene(ctypes.byref(d), ctypes.byref(h)) == nrv.NRV_ERR_ARG
+    d = nrv.nrv_scene_desc(10, 16, 16, 3, 3)         # bad stride
+    assert lib.nrv_create_scene(ctypes.byref(d), ctypes.byref(h)) == nrv.NRV_ERR_ARG
+    d = nrv.nrv_scene_desc(10, 16, 16, 4, 5)         # K > stride
+    assert lib.nrv_create_scene(ctypes.byref(d), ctypes.byref(h)) == nrv.NRV_ERR_ARG
+    d = nrv.nrv_scene_desc(0, None, None, 4, 3)      # empty scene is valid
+    assert lib.nrv_create_scene(ctypes.byref(d), ctypes.byref(h)) == nrv.NRV_OK
+    assert lib.nrv_rasterize(h, None, 1, None, None) == nrv.NRV_ERR_ARG
+    assert lib.nrv_destroy_scene(h) == nrv.NRV_OK
+    assert lib.nrv_create_net(9, ctypes.byref(h)) == nrv.NRV_ERR_ARG
+    assert lib.nrv_create_net(5, ctypes.byref(h)) == nrv.NRV_OK
+    assert lib.nrv_shade(h, 32, 1, 8, 8, 0, 32, None) == nrv.NRV_ERR_STATE   # no params yet
+    assert lib.nrv_net_backward(h, 32, 32, None) == nrv.NRV_ERR_STATE
+    assert lib.nrv_destroy_net(h) == nrv.NRV_OK

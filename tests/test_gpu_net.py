@@ -1,0 +1,162 @@
+"""GPU parity of the post-processing U-Net (Sec. 3.3) against the float64 oracle: FP32 forward
+within 1e-4, BF16 forward at PSNR >= 45 dB and max abs <= 2e-2, gradients of the backward pass
+per tensor, L1 loss and Adam."""
+import numpy as np
+import pytest
+
+import nrv_inputs as I
+import oracle
+from gpu_util import make_params, psnr_range, torch_dev
+from oracle import unet
+
+pytestmark = pytest.mark.gpu
+
+
+def _input(n, h, w, c0, seed=0):
+    """Packed-looking network input: covered pixels with z-scored channels, depth, mask."""
+    rng = np.random.default_rng(seed)
+    x = np.zeros((n, h, w, 8), np.float32)
+    cov = rng.uniform(0, 1, (n, h, w)) < 0.6
+    x[..., :c0 - 2] = rng.standard_normal((n, h, w, c0 - 2)).astype(np.float32)
+    x[..., c0 - 2] = rng.uniform(0, 1, (n, h, w)).astype(np.float32)
+    x[..., c0 - 1] = 1.0
+    x[~cov] = 0.0
+    return x
+
+
+def _net(c0, flat):
+    import torch
+    from paper_2407_19097_gb300 import nrv
+    net = nrv.Net(c0)
+    p = torch.from_numpy(flat).to(torch_dev())
+    net.set_params(p)
+    return net, p
+
+
+@pytest.mark.parametrize("c0,n,h,w", [(5, 2, 64, 96), (7, 1, 40, 136), (6, 1, 120, 40)])
+def test_forward_fp32(c0, n, h, w):
+    import torch
+    from paper_2407_19097_gb300 import nrv
+    flat = make_params(c0, seed=c0, bias_sigma=0.05)
+    net, _ = _net(c0, flat)
+    hn, wn = nrv.lib().nrv_pad8(h), nrv.lib().nrv_pad8(w)
+    x = _input(n, hn, wn, c0, seed=1)
+    xt = torch.from_numpy(x).to(torch_dev())
+    rgb = torch.empty((n, h, w, 3), device=torch_dev())
+    net.shade(xt, n, h, w, nrv.PREC_F32, rgb)
+    ref = unet.forward(x[..., :c0].astype(np.float64), unet.unflatten(flat, c0))[:, :h, :w]
+    torch.cuda.synchronize()
+    err = np.abs(rgb.cpu().numpy() - ref).max()
+    assert err <= 1e-4, err
+
+
+@pytest.mark.parametrize("c0,n,h,w", [(5, 2, 64, 96), (7, 1, 136, 264)])
+def test_forward_bf16(c0, n, h, w):
+    import torch
+    from paper_2407_19097_gb300 import nrv
+    flat = make_params(c0, seed=c0 + 10, bias_sigma=0.05)
+    net, _ = _net(c0, flat)
+    hn, wn = nrv.lib().nrv_pad8(h), nrv.lib().nrv_pad8(w)
+    x = _input(n, hn, wn, c0, seed=2)
+    xb = torch.from_numpy(x).to(torch_dev()).to(torch.bfloat16)
+    xin = xb.float().cpu().numpy()          # the oracle sees exactly the BF16 input values
+    rgb = torch.empty((n, h, w, 3), device=torch_dev())
+    net.shade(xb, n, h, w, nrv.PREC_BF16, rgb)
+    ref = unet.forward(xin[..., :c0].astype(np.float64), unet.unflatten(flat, c0))[:, :h, :w]
+    torch.cuda.synchronize()
+    got = rgb.cpu().numpy()
+    err = np.abs(got - ref).max()
+    p = psnr_range(got, ref)
+    assert err <= 2e-2 and p >= 45.0, (err, p)
+
+
+def _grad_case(prec, tol):
+    import torch
+    from paper_2407_19097_gb300 import nrv
+    c0, n, h, w = 5, 2, 32, 48
+    flat = make_params(c0, seed=21, bias_sigma=0.05)
+    net, p = _net(c0, flat)
+    x = _input(n, h, w, c0, seed=3)
+    dev = torch_dev()
+    if prec == nrv.PREC_BF16:
+        xt = torch.from_numpy(x).to(dev).to(torch.bfloat16)
+        xin = xt.float().cpu().numpy()
+    else:
+        xt = torch.from_numpy(x).to(dev)
+        xin = x
+    rgb = torch.empty((n, h, w, 3), device=dev)
+    net.forward_train(xt, n, h, w, prec, rgb)
+    rng = np.random.default_rng(4)
+    dy = (rng.standard_normal((n, h, w, 3)) * 1e-2).astype(np.float32)
+    g = torch.zeros_like(p)
+    net.backward(torch.from_numpy(dy).to(dev), g)
+    y, s = unet.forward(xin[..., :c0].astype(np.float64), unet.unflatten(flat, c0), save=True)
+    gr, _ = unet.backward(dy.astype(np.float64), unet.unflatten(flat, c0), s)
+    torch.cuda.synchronize()
+    gg = g.cpu().numpy().astype(np.float64)
+    o = 0
+    for name, kind, ci, co in unet.layers(c0):
+        wref, bref = gr[name]
+        for ref in (wref.ravel(), bref.ravel()):
+            got = gg[o:o + ref.size]
+            rel = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-30)
+            assert rel <= tol, (name, rel)
+            o += ref.size
+    assert o == gg.size
+
+
+def test_backward_fp32():
+    from paper_2407_19097_gb300 import nrv
+    _grad_case(nrv.PREC_F32, 1e-4)
+
+
+def test_backward_bf16():
+    from paper_2407_19097_gb300 import nrv
+    _grad_case(nrv.PREC_BF16, 5e-2)
+
+
+def test_l1_and_adam():
+    import torch
+    from paper_2407_19097_gb300 import nrv
+    dev = torch_dev()
+    rng = np.random.default_rng(5)
+    y = rng.standard_normal(100_003).astype(np.float32)
+    t = y.copy()
+    t[::3] += rng.standard_normal(t[::3].shape).astype(np.float32)
+    yt, tt = torch.from_numpy(y).to(dev), torch.from_numpy(t).to(dev)
+    loss = torch.zeros(1, device=dev)
+    dy = torch.empty_like(yt)
+    nrv.l1_loss(yt, tt, loss, dy)
+    lref, gref = unet.l1_loss(y, t)
+    torch.cuda.synchronize()
+    assert abs(loss.item() - lref) <= 1e-6 * max(1.0, lref)
+    np.testing.assert_allclose(dy.cpu().numpy(), gref, rtol=1e-6, atol=0)
+    p0 = rng.standard_normal(5000).astype(np.float32)
+    pt = torch.from_numpy(p0).to(dev)
+    m = torch.zeros_like(pt)
+    v = torch.zeros_like(pt)
+    pr, mr, vr = p0.astype(np.float64), np.zeros(5000), np.zeros(5000)
+    for step in range(1, 4):
+        gnp = rng.standard_normal(5000).astype(np.float32)
+        nrv.adam_step(pt, torch.from_numpy(gnp).to(dev), m, v, step)
+        pr, mr, vr = unet.adam_step(pr, gnp.astype(np.float64), mr, vr, step)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(pt.cpu().numpy(), pr, rtol=0, atol=1e-6)
+
+
+def test_training_reduces_loss():
+    import torch
+    from paper_2407_19097_gb300 import nrv
+    c0, n, h, w = 5, 4, 32, 32
+    flat = make_params(c0, seed=3)
+    net, p = _net(c0, flat)
+    dev = torch_dev()
+    x = torch.from_numpy(_input(n, h, w, c0, seed=6)).to(dev).to(torch.bfloat16)
+    tgt = torch.from_numpy(np.random.default_rng(7).uniform(0, 1, (n, h, w, 3)).astype(np.float32)).to(dev)
+    g, m, v = torch.zeros_like(p), torch.zeros_like(p), torch.zeros_like(p)
+    loss = torch.zeros(1, device=dev)
+    losses = []
+    for step in range(1, 61):
+        net.train_step(p, g, m, v, step, 1e-3, x, tgt, n, h, w, nrv.PREC_BF16, loss)
+        losses.append(loss.item())
+    assert losses[-1] < 0.7 * losses[0], (losses[0], losses[-1])
