@@ -206,6 +206,11 @@ nrv_status nrv_net_set_act_scales(nrv_net* net, const float* act_scale, int n);
 nrv_status nrv_shade(nrv_net* net, const void* d_netin, int n, int height, int width,
                      nrv_prec prec, float* d_rgb, nrv_stream stream);
 
+/* Which kernel family ran layer `layer` in the net's most recent forward pass:
+ * 0 = SIMT (CUDA cores), 1 = tensor cores (tcgen05), -1 = not run yet or a
+ * bad argument.  Lets callers check that a precision ran where they expect. */
+int nrv_net_layer_backend(const nrv_net* net, int layer);
+
 /* Training forward: like nrv_shade, but keeps the activations the backward
  * pass needs in the net's workspace (F32 or BF16 only). */
 nrv_status nrv_net_forward_train(nrv_net* net, const void* d_netin, int n, int height, int width,

@@ -112,32 +112,49 @@ def conv1(x, w, b):
 
 # ----------------------------------------------------------------------------- network
 
-def forward(x, params: dict, save: bool = False):
+def forward(x, params: dict, save: bool = False, q=None):
     """U-Net forward on NHWC float64 input with H, W divisible by 8.  Returns RGB (and the
-    saved activations when save=True)."""
-    x = np.asarray(x, np.float64)
+    saved activations when save=True; "pre:<layer>" holds each ReLU layer's pre-activation).
+
+    q, if given, is applied to every tensor the network stores between layers (the input,
+    each ReLU output, pooled and upsampled tensors), e.g. rounding to the storage precision
+    of a reduced-precision network; the head's output is not rounded."""
+    rq = (lambda t: t) if q is None else q
+    x = rq(np.asarray(x, np.float64))
     s = {"x": x}
 
     def cr(name, inp):
         w, b = params[name]
-        y = relu(conv3(inp, w, b))
+        pre = conv3(inp, w, b)
+        y = rq(relu(pre))
         s[name] = y
+        if save:
+            s["pre:" + name] = pre
         return y
 
     a = cr("e0b", cr("e0a", x))
-    p = avgpool2(a); s["p0"] = p
+    p = rq(avgpool2(a)); s["p0"] = p
     a = cr("e1b", cr("e1a", p))
-    p = avgpool2(a); s["p1"] = p
+    p = rq(avgpool2(a)); s["p1"] = p
     a = cr("e2b", cr("e2a", p))
-    p = avgpool2(a); s["p2"] = p
+    p = rq(avgpool2(a)); s["p2"] = p
     a = cr("e3b", cr("e3a", p))
     for up, da, db, skip in (("up3", "d2a", "d2b", "e2b"), ("up2", "d1a", "d1b", "e1b"),
                              ("up1", "d0a", "d0b", "e0b")):
-        u = convT2(a, *params[up]); s[up] = u
+        u = rq(convT2(a, *params[up])); s[up] = u
         c = np.concatenate([u, s[skip]], axis=-1); s["cat" + up] = c
         a = cr(db, cr(da, c))
     y = conv1(a, *params["head"])
     return (y, s) if save else y
+
+
+def relu_margin(s: dict) -> float:
+    """Smallest |pre-activation| over every ReLU layer, relative to the largest: a ReLU
+    decision closer to zero than rounding can flip between two precisions."""
+    pres = [v for k, v in s.items() if k.startswith("pre:")]
+    lo = min(float(np.abs(v).min()) for v in pres)
+    hi = max(float(np.abs(v).max()) for v in pres)
+    return lo / hi
 
 
 # ----------------------------------------------------------------------------- backward ops
@@ -178,21 +195,24 @@ def convT2_bwd(x, w, dy):
     return dx, dw, dy.reshape(-1, dy.shape[-1]).sum(axis=0)
 
 
-def backward(dy, params: dict, s: dict):
+def backward(dy, params: dict, s: dict, q=None):
     """Analytic gradients of the network w.r.t. its parameters and its input, given dL/dRGB and
-    the saved forward activations.  ReLU'(0) = 0."""
+    the saved forward activations.  ReLU'(0) = 0.  q, if given, is applied to every gradient
+    tensor passed between layers (the same storage rounding as in forward); parameter
+    gradients are not rounded."""
+    rq = (lambda t: t) if q is None else q
     g = {}
     wh, _ = params["head"]
     a_last = s["d0b"]
     d2 = dy.reshape(-1, dy.shape[-1])
     g["head"] = (d2.T @ a_last.reshape(-1, a_last.shape[-1]), d2.sum(axis=0))
-    da = dy @ wh
+    da = rq(dy @ wh)
 
     def cr_bwd(name, inp, dout):
         dout = dout * (s[name] > 0)
         dx, dw, db = conv3_bwd(inp, params[name][0], dout)
         g[name] = (dw, db)
-        return dx
+        return rq(dx)
 
     dskip = {}
     # decoder, finest level first; `below` is the activation the transposed conv upsampled
@@ -205,12 +225,12 @@ def backward(dy, params: dict, s: dict):
         dskip[skip] = dc[..., cu:]
         dx, dw, db = convT2_bwd(s[below], params[up][0], dc[..., :cu])
         g[up] = (dw, db)
-        da = dx
+        da = rq(dx)
     # encoder, deepest first
     d = cr_bwd("e3b", s["e3a"], da)
     d = cr_bwd("e3a", s["p2"], d)
     for ea, eb, pin in (("e2a", "e2b", "p1"), ("e1a", "e1b", "p0"), ("e0a", "e0b", "x")):
-        d = avgpool2_bwd(d) + dskip[eb]
+        d = rq(avgpool2_bwd(d) + dskip[eb])
         d = cr_bwd(eb, s[ea], d)
         d = cr_bwd(ea, s[pin], d)
     return g, d

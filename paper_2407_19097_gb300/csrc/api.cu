@@ -239,7 +239,10 @@ extern "C" nrv_status nrv_create_net(int c_in, nrv_net** out) {
     net->c_in = c_in;
     net->c0p = 8;
     net->n_params = net_layers(c_in, net->layers);
-    for (int l = 0; l < NUM_LAYERS; ++l) net->act_scale[l] = 1.0f;
+    for (int l = 0; l < NUM_LAYERS; ++l) {
+        net->act_scale[l] = 1.0f;
+        net->backend[l] = -1;
+    }
     *out = net;
     return NRV_OK;
 }
@@ -287,6 +290,11 @@ extern "C" nrv_status nrv_shade(nrv_net* net, const void* netin, int n, int h, i
     clear_error();
     NRV_TRY(check_shade(net, netin, n, h, w, prec, rgb));
     return net_forward(net, netin, n, h, w, prec, rgb, (cudaStream_t)stream);
+}
+
+extern "C" int nrv_net_layer_backend(const nrv_net* net, int layer) {
+    if (!net || layer < 0 || layer >= NUM_LAYERS) return -1;
+    return net->backend[layer];
 }
 
 extern "C" nrv_status nrv_net_forward_train(nrv_net* net, const void* netin, int n, int h, int w,

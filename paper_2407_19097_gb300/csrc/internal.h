@@ -22,7 +22,13 @@ void clear_error();
             return ::nrv::fail(NRV_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
-#define NRV_CHECK_LAUNCH() NRV_CHECK_CUDA(cudaGetLastError())
+#define NRV_CHECK_LAUNCH()                                                               \
+    do {                                                                                 \
+        cudaError_t e_ = cudaGetLastError();                                             \
+        if (e_ != cudaSuccess)                                                           \
+            return ::nrv::fail(NRV_ERR_CUDA, "kernel launch at %s:%d failed: %s", __FILE__, \
+                               __LINE__, cudaGetErrorString(e_));                        \
+    } while (0)
 
 #define NRV_TRY(expr)                          \
     do {                                       \

@@ -174,9 +174,11 @@ static nrv_status forward_t(Net* net, const T* netin, float* rgb, cudaStream_t s
                     int level) -> nrv_status {
         if (use_tc) {
             nrv_status st = tc_conv3(net, l, x1.p, c1, x2.p, c2, act<T>(net, out), g, level, prec, s);
+            net->backend[l] = 1;
             if (st != NRV_ERR_UNSUPPORTED) return st;
             clear_error();
         }
+        net->backend[l] = 0;
         return simt_conv3<T>(net, l, x1, c1, x2, c2, V(out), g, level, true, s);
     };
     auto pool = [&](int in, int out, int level_out) -> nrv_status {
@@ -243,6 +245,7 @@ nrv_status net_forward(Net* net, const void* netin, int n, int H, int W, nrv_pre
     NRV_TRY(set_kernel_attrs());
     NRV_TRY(net_prepare(net, n, H, W, prec));
     net->saved = false;
+    for (int l = 0; l < NUM_LAYERS; ++l) net->backend[l] = net->layers[l].kind == CONV3 ? -1 : 0;
     if (prec == NRV_PREC_F32)
         return forward_t<float>(net, (const float*)netin, rgb, s, false, prec);
     if (prec == NRV_PREC_BF16)

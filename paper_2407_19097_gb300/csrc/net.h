@@ -49,6 +49,7 @@ struct Net {
     Geo geo{};
     int geo_H = 0, geo_W = 0;
     nrv_prec act_prec = NRV_PREC_F32;
+    int backend[NUM_LAYERS];   // 0 SIMT, 1 tcgen05, -1 not run (last forward)
     bool saved = false;      // a training forward's activations are in place
     // backward scratch
     DevBuf grads;            // gradient tensors

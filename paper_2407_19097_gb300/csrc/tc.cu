@@ -1,13 +1,554 @@
-// Tensor-core (tcgen05) convolutions -- placeholder until the kernels land.
+// Tensor-core 3x3 convolution of the U-Net (Sec. 3.3) as an implicit GEMM on the
+// 5th-generation tensor cores (tcgen05 + TMEM), BF16 operands, FP32 accumulation.
+//
+//   D[m][n] = sum_k A[m][k] * B[n][k],   m = 128 consecutive pixels of one row,
+//   n = output channel, k = (tap, input channel) -- K = 9 * C_in.
+//
+// A tile of 128 output pixels needs the input rows y-1..y+1 and pixels
+// x0-1..x0+128 ("halo").  One 5-D TMA load brings them into shared memory as
+// planes of [pixel][8 channels] (16 bytes per pixel): plane (row, chunk) holds
+// 130 pixels.  Each tap's A operand is then just a shared-memory descriptor
+// pointing dx pixels into the plane of row dy -- the nine taps share one copy
+// of the data, zero padding comes from TMA's out-of-bounds fill.  Operands use
+// the no-swizzle K-major layout: core matrices of 8 rows x 16 bytes, rows 16
+// bytes apart (SBO = 128 bytes between 8-row groups), the two 8-element K
+// halves of one MMA (K = 16) LBO bytes apart.
+//
+// The weights of the CTA's output-channel slice stay resident in shared memory
+// ([k-step][half][n][8] BF16).  Warp roles: warp 0 issues TMA loads, warp 1
+// owns TMEM and issues the MMAs, warps 2-5 drain the FP32 accumulator
+// (tcgen05.ld), add the bias, apply ReLU and store BF16 NHWC.  Halo buffers and
+// accumulators are double-buffered so loads, MMAs and the epilogue overlap
+// across the CTA's pixel tiles.  Every wait is bounded: on timeout the kernel
+// records STATUS_TIMEOUT in the status word, drains what it started, frees TMEM
+// and returns.
+#include <cuda.h>
+#include <string.h>
+
 #include "net.h"
 
 namespace nrv {
 
-nrv_status tc_repack(Net*, cudaStream_t) { return NRV_OK; }
+namespace {
 
-nrv_status tc_conv3(const Net*, int, const void*, int, const void*, int, void*, const Geo&, int,
-                    nrv_prec, cudaStream_t) {
-    return fail(NRV_ERR_UNSUPPORTED, "no tensor-core kernel for this shape");
+constexpr int HALO_W = 130;
+constexpr int PLANE = HALO_W * 16;  // bytes of one (row, 8-channel chunk) plane
+constexpr int MAX_KS = 80;
+constexpr int TILE_M = 128;
+constexpr int NTHREADS = 192;
+
+struct TcParams {
+    int n, h, w;             // level geometry
+    int tiles_x, num_ptiles; // pixel tiles
+    int nslices, n_slice;    // output-channel slices and their width
+    int nks;                 // K-steps of 16 channels
+    int nbuf;                // halo buffers (1 or 2)
+    int cout;                // output pixel stride (channels)
+    int has_src2;
+    uint32_t halo_bytes;     // bytes of one halo buffer (both sources)
+    uint32_t src2_off;       // offset of source 2 planes inside a buffer
+    uint32_t tx1, tx2;       // bytes delivered by each TMA load
+    uint32_t w_bytes;        // bytes of one weight slice
+    uint32_t w_region;       // bytes reserved for the weights (aligned)
+    uint32_t idesc;
+    uint32_t tmem_cols;
+    const uint8_t* wpk;      // packed weights [slice][ks][half][n][8] (BF16)
+    const float* bias;
+    __nv_bfloat16* y;
+    unsigned* status;
+    uint32_t a_off[MAX_KS];  // A start offset in the halo buffer, per K-step
+    uint32_t a_lbo[MAX_KS];  // A K-direction byte offset (second half), per K-step
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait (about 2 s): false on timeout or when another role aborted.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                          unsigned* status) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (true) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (global_ns() - t0 > 2000000000ull) {
+            *abort_flag = 1;
+            atomicOr(status, STATUS_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, int c4, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// UMMA shared-memory descriptor, no swizzle (sm_100 format, version 1).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    conv3_tc_kernel(const __grid_constant__ CUtensorMap tm1, const __grid_constant__ CUtensorMap tm2,
+                    const __grid_constant__ TcParams P) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t bars[12];
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t s_w = smem_u32(smem);
+    const uint32_t s_halo = s_w + P.w_region;
+    const uint32_t b_w = smem_u32(&bars[0]);
+    auto b_hfull = [&](int i) { return smem_u32(&bars[1 + i]); };
+    auto b_hempty = [&](int i) { return smem_u32(&bars[3 + i]); };
+    auto b_afull = [&](int i) { return smem_u32(&bars[5 + i]); };
+    auto b_aempty = [&](int i) { return smem_u32(&bars[7 + i]); };
+    const uint32_t b_done = smem_u32(&bars[9]);
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        mbar_init(b_w, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(b_hfull(i), 1);
+            mbar_init(b_hempty(i), 1);
+            mbar_init(b_afull(i), 1);
+            mbar_init(b_aempty(i), 4);
+        }
+        mbar_init(b_done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_slot)),
+                     "r"(P.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    // this CTA's output-channel slice and its pixel tiles
+    const int slice = blockIdx.x % P.nslices;
+    const int cta_in_slice = blockIdx.x / P.nslices;
+    const int ctas_per_slice = gridDim.x / P.nslices;
+    const int my_tiles = cta_in_slice < P.num_ptiles
+                             ? (P.num_ptiles - 1 - cta_in_slice) / ctas_per_slice + 1
+                             : 0;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // weights once, then the halo of every tile
+            mbar_expect_tx(b_w, P.w_bytes);
+            const uint8_t* src = P.wpk + (size_t)slice * P.w_bytes;
+            for (uint32_t o = 0; o < P.w_bytes; o += 16384) {
+                const uint32_t len = P.w_bytes - o < 16384 ? P.w_bytes - o : 16384;
+                bulk_load(s_w + o, src + o, len, b_w);
+            }
+            int issued = 0;
+            for (int i = 0; i < my_tiles; ++i) {
+                const int buf = i % P.nbuf, u = i / P.nbuf;
+                if (!mbar_wait(b_hempty(buf), (u & 1) ^ 1, &abort_flag, P.status)) break;
+                const int pt = cta_in_slice + i * ctas_per_slice;
+                const int xt = pt % P.tiles_x, rest = pt / P.tiles_x;
+                const int yr = rest % P.h, img = rest / P.h;
+                const uint32_t dst = s_halo + (uint32_t)buf * P.halo_bytes;
+                mbar_expect_tx(b_hfull(buf), P.tx1 + P.tx2);
+                tma_load_5d(dst, &tm1, 0, xt * TILE_M - 1, 0, yr - 1, img, b_hfull(buf));
+                if (P.has_src2)
+                    tma_load_5d(dst + P.src2_off, &tm2, 0, xt * TILE_M - 1, 0, yr - 1, img,
+                                b_hfull(buf));
+                issued = i + 1;
+            }
+            // every load issued must have landed before the CTA may exit
+            for (int i = issued - P.nbuf > 0 ? issued - P.nbuf : 0; i < issued; ++i)
+                mbar_wait(b_hfull(i % P.nbuf), (i / P.nbuf) & 1, &abort_flag, P.status);
+            mbar_wait(b_w, 0, &abort_flag, P.status);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            bool ok = mbar_wait(b_w, 0, &abort_flag, P.status);
+            const uint32_t s_wslice = s_w;
+            const uint32_t b_lbo = (uint32_t)P.n_slice * 16;
+            for (int i = 0; ok && i < my_tiles; ++i) {
+                const int buf = i % P.nbuf, u = i / P.nbuf;
+                const int ab = i & 1, ua = i >> 1;
+                if (!mbar_wait(b_hfull(buf), u & 1, &abort_flag, P.status)) break;
+                if (!mbar_wait(b_aempty(ab), (ua & 1) ^ 1, &abort_flag, P.status)) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(ab * P.n_slice);
+                const uint32_t hb = s_halo + (uint32_t)buf * P.halo_bytes;
+                for (int ks = 0; ks < P.nks; ++ks) {
+                    const uint64_t a = sdesc(hb + P.a_off[ks], P.a_lbo[ks], 128);
+                    const uint64_t b = sdesc(s_wslice + (uint32_t)ks * 2 * b_lbo, b_lbo, 128);
+                    mma_bf16(d, a, b, P.idesc, ks > 0 ? 1u : 0u);
+                }
+                mma_commit(b_hempty(buf));
+                mma_commit(b_afull(ab));
+            }
+            // wait until every MMA issued above has completed
+            mma_commit(b_done);
+            mbar_wait(b_done, 0, &abort_flag, P.status);
+        }
+    } else {
+        // epilogue: warps 2..5 own TMEM lanes 32*(warp%4) ..
+        const int q = warp & 3;
+        const int m = 32 * q + lane;
+        for (int i = 0; i < my_tiles; ++i) {
+            const int ab = i & 1, ua = i >> 1;
+            if (!mbar_wait(b_afull(ab), ua & 1, &abort_flag, P.status)) break;
+            tc_fence_after();
+            const int pt = cta_in_slice + i * ctas_per_slice;
+            const int xt = pt % P.tiles_x, rest = pt / P.tiles_x;
+            const int yr = rest % P.h, img = rest / P.h;
+            const int x = xt * TILE_M + m;
+            __nv_bfloat16* out = P.y + (((size_t)img * P.h + yr) * P.w + x) * P.cout +
+                                 (size_t)slice * P.n_slice;
+            const float* bias = P.bias + slice * P.n_slice;
+            for (int c0 = 0; c0 < P.n_slice; c0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * P.n_slice + c0), r);
+                uint32_t packed[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float v0 = fmaxf(__uint_as_float(r[2 * j]) + bias[c0 + 2 * j], 0.0f);
+                    const float v1 = fmaxf(__uint_as_float(r[2 * j + 1]) + bias[c0 + 2 * j + 1], 0.0f);
+                    __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+                    packed[j] = *reinterpret_cast<uint32_t*>(&h2);
+                }
+                if (x < P.w) {
+                    uint4* o4 = reinterpret_cast<uint4*>(out + c0);
+                    o4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                    o4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(b_aempty(ab));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(P.tmem_cols)
+                     : "memory");
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// NHWC BF16 tensor [n][h][w][c] viewed as (8, w, c/8, h, n) so that one box of
+// (8, 130, c/8, 3, 1) lands in shared memory as [row][chunk][pixel][8].
+nrv_status make_halo_map(CUtensorMap* map, const void* base, int n, int h, int w, int c) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return fail(NRV_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
+    if (((uintptr_t)base & 15) != 0) return fail(NRV_ERR_ARG, "tensor base not 16-byte aligned");
+    const cuuint64_t dims[5] = {8, (cuuint64_t)w, (cuuint64_t)(c / 8), (cuuint64_t)h, (cuuint64_t)n};
+    const cuuint64_t strides[4] = {(cuuint64_t)c * 2, 16, (cuuint64_t)w * c * 2,
+                                   (cuuint64_t)h * w * c * 2};
+    const cuuint32_t box[5] = {8, HALO_W, (cuuint32_t)(c / 8), 3, 1};
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides,
+                     box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(NRV_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return NRV_OK;
+}
+
+// One half of a K-step: 8 input channels (chunk) of one tap from one source.
+struct Half {
+    int tap, src, chunk;  // src 0 or 1; tap < 0 marks the zero phantom
+};
+
+struct TcLayerCfg {
+    bool ok = false;
+    int c1 = 0, c2 = 0;
+    int n_slice = 0, nslices = 0, nks = 0;
+    std::vector<Half> halves;
+    size_t w_off = 0;        // byte offset of the packed weights in the BF16 buffer
+    uint32_t w_bytes = 0;    // per slice
+};
+
+TcLayerCfg g_cfg[NUM_LAYERS];
+
+__global__ void pack_tc_weights_kernel(const float* __restrict__ P, int64_t woff, int cin_real,
+                                       int cout, int n_slice, int nslices, int nks,
+                                       const int4* __restrict__ halves, int c1, uint16_t* out) {
+    // out[slice][ks][half][n][8]
+    const size_t total = (size_t)nslices * nks * 2 * n_slice * 8;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int e = (int)(i % 8);
+        const int nl = (int)((i / 8) % n_slice);
+        const int hf = (int)((i / (8 * (size_t)n_slice)) % 2);
+        const int ks = (int)((i / (16 * (size_t)n_slice)) % nks);
+        const int sl = (int)(i / (16 * (size_t)n_slice * nks));
+        const int4 h = halves[2 * ks + hf];
+        float v = 0.0f;
+        if (h.x >= 0) {
+            const int c = (h.y == 0 ? 0 : c1) + 8 * h.z + e;
+            const int o = sl * n_slice + nl;
+            if (c < cin_real) v = P[woff + ((size_t)o * cin_real + c) * 9 + h.x];
+        }
+        __nv_bfloat16 b = __float2bfloat16_rn(v);
+        out[i] = *reinterpret_cast<uint16_t*>(&b);
+    }
+}
+
+DevBuf g_halves;
+
+}  // namespace
+
+static int src_split(int l, int cin_padded, int* c2) {
+    if (l == L_D2A || l == L_D1A || l == L_D0A) {
+        *c2 = cin_padded / 2;
+        return cin_padded / 2;
+    }
+    *c2 = 0;
+    return cin_padded;
+}
+
+nrv_status tc_repack(Net* net, cudaStream_t s) {
+    size_t off = 0;
+    std::vector<int4> all_halves;
+    std::vector<size_t> hoff(NUM_LAYERS, 0);
+    for (int l = 0; l < NUM_LAYERS; ++l) {
+        TcLayerCfg& c = g_cfg[l];
+        c = TcLayerCfg();
+        const Layer& L = net->layers[l];
+        if (L.kind != CONV3) continue;
+        const int cinp = l == L_E0A ? net->c0p : L.cin;
+        c.c1 = src_split(l, cinp, &c.c2);
+        for (int tap = 0; tap < 9; ++tap)
+            for (int src = 0; src < 2; ++src) {
+                const int cs = src == 0 ? c.c1 : c.c2;
+                for (int ch = 0; ch < cs / 8; ++ch) c.halves.push_back(Half{tap, src, ch});
+            }
+        if (c.halves.size() % 2) c.halves.push_back(Half{-1, 0, 0});
+        c.nks = (int)c.halves.size() / 2;
+        if (c.nks > MAX_KS) continue;
+        // widest output slice whose weights fit in 80 KB
+        int ns = L.cout;
+        while (ns > 16 && (size_t)c.nks * 2 * ns * 16 > 80 * 1024) ns /= 2;
+        c.n_slice = ns;
+        c.nslices = L.cout / ns;
+        c.w_bytes = (uint32_t)c.nks * 2 * ns * 16;
+        c.w_off = off;
+        off += ((size_t)c.w_bytes * c.nslices + 1023) / 1024 * 1024;
+        hoff[l] = all_halves.size();
+        for (const Half& h : c.halves) all_halves.push_back(make_int4(h.tap, h.src, h.chunk, 0));
+        c.ok = true;
+    }
+    if (off == 0) return NRV_OK;
+    NRV_TRY(net->wbf16.ensure(off));
+    NRV_TRY(g_halves.ensure(all_halves.size() * sizeof(int4)));
+    NRV_CHECK_CUDA(cudaMemcpyAsync(g_halves.p, all_halves.data(), all_halves.size() * sizeof(int4),
+                                   cudaMemcpyHostToDevice, s));
+    for (int l = 0; l < NUM_LAYERS; ++l) {
+        const TcLayerCfg& c = g_cfg[l];
+        if (!c.ok) continue;
+        const Layer& L = net->layers[l];
+        pack_tc_weights_kernel<<<64, 256, 0, s>>>(
+            (const float*)net->params.p, L.woff, L.cin, L.cout, c.n_slice, c.nslices, c.nks,
+            (const int4*)g_halves.p + hoff[l], c.c1, (uint16_t*)((char*)net->wbf16.p + c.w_off));
+        NRV_CHECK_LAUNCH();
+    }
+    // the host copy of the halves must stay valid until the copy ran
+    NRV_CHECK_CUDA(cudaStreamSynchronize(s));
+    return NRV_OK;
+}
+
+static int g_num_sms = 0;
+
+nrv_status tc_conv3(const Net* net, int l, const void* x1, int c1, const void* x2, int c2, void* y,
+                    const Geo& g, int level, nrv_prec prec, cudaStream_t s) {
+    if (prec != NRV_PREC_BF16) return fail(NRV_ERR_UNSUPPORTED, "tensor-core path is BF16");
+    const TcLayerCfg& c = g_cfg[l];
+    if (!c.ok || c.c1 != c1 || c.c2 != c2) return fail(NRV_ERR_UNSUPPORTED, "layer not configured");
+    const Layer& L = net->layers[l];
+    const int H = g.h[level], W = g.w[level];
+    TcParams P;
+    memset(&P, 0, sizeof(P));
+    P.n = g.n;
+    P.h = H;
+    P.w = W;
+    P.tiles_x = (W + TILE_M - 1) / TILE_M;
+    P.num_ptiles = P.tiles_x * H * g.n;
+    P.nslices = c.nslices;
+    P.n_slice = c.n_slice;
+    P.nks = c.nks;
+    P.cout = L.cout;
+    P.has_src2 = c.c2 > 0;
+    const uint32_t nch1 = c.c1 / 8, nch2 = c.c2 / 8;
+    P.tx1 = 3 * nch1 * PLANE;
+    P.tx2 = 3 * nch2 * PLANE;
+    P.src2_off = (P.tx1 + 127) / 128 * 128;   // TMA destinations are 128-byte aligned
+    P.halo_bytes = (P.src2_off + P.tx2 + 127) / 128 * 128;
+    P.w_bytes = c.w_bytes;
+    P.w_region = (c.w_bytes + 1023) / 1024 * 1024;
+    P.nbuf = (P.w_region + 2 * P.halo_bytes <= 200 * 1024) ? 2 : 1;
+    const uint32_t smem = P.w_region + P.nbuf * P.halo_bytes;
+    if (smem > 220 * 1024) return fail(NRV_ERR_UNSUPPORTED, "tile does not fit in shared memory");
+    P.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(c.n_slice >> 3) << 17) |
+              ((uint32_t)(TILE_M >> 4) << 24);
+    uint32_t cols = 32;
+    while (cols < (uint32_t)(2 * c.n_slice)) cols *= 2;
+    P.tmem_cols = cols;
+    P.wpk = (const uint8_t*)net->wbf16.p + c.w_off;
+    P.bias = (const float*)net->params.p + L.boff;
+    P.y = (__nv_bfloat16*)y;
+    P.status = status_word();
+    if (!P.status) return fail(NRV_ERR_CUDA, "status word unavailable");
+    for (int ks = 0; ks < c.nks; ++ks) {
+        const Half& h0 = c.halves[2 * ks];
+        const Half& h1 = c.halves[2 * ks + 1];
+        auto off = [&](const Half& h) -> uint32_t {
+            const uint32_t base = h.src == 0 ? 0u : P.src2_off;
+            const uint32_t nch = h.src == 0 ? nch1 : nch2;
+            return base + ((uint32_t)(h.tap / 3) * nch + (uint32_t)h.chunk) * PLANE +
+                   (uint32_t)(h.tap % 3) * 16;
+        };
+        P.a_off[ks] = off(h0);
+        const uint32_t o1 = h1.tap < 0 ? P.a_off[ks] : off(h1);
+        if (o1 < P.a_off[ks]) return fail(NRV_ERR_UNSUPPORTED, "descending K layout");
+        P.a_lbo[ks] = o1 - P.a_off[ks];
+        // both K halves read 128 rows of 16 bytes inside the buffer
+        if (o1 + TILE_M * 16 > P.halo_bytes || P.a_lbo[ks] >= (1u << 18))
+            return fail(NRV_ERR_UNSUPPORTED, "A operand outside the halo buffer");
+    }
+    CUtensorMap m1, m2;
+    NRV_TRY(make_halo_map(&m1, x1, g.n, H, W, c.c1));
+    if (P.has_src2) NRV_TRY(make_halo_map(&m2, x2, g.n, H, W, c.c2));
+    else m2 = m1;
+    if (!g_num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 148;
+    }
+    static uint32_t attr_smem = 0;
+    if (smem > attr_smem) {
+        NRV_CHECK_CUDA(cudaFuncSetAttribute(conv3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            220 * 1024));
+        attr_smem = 220 * 1024;
+    }
+    int occ = (int)((227 * 1024) / (smem + 2048));
+    if (occ < 1) occ = 1;
+    if (occ * (int)cols > 512) occ = 512 / (int)cols;
+    int per_slice = (g_num_sms * occ) / c.nslices;
+    if (per_slice < 1) per_slice = 1;
+    if (per_slice > P.num_ptiles) per_slice = P.num_ptiles;
+    conv3_tc_kernel<<<per_slice * c.nslices, NTHREADS, smem, s>>>(m1, m2, P);
+    NRV_CHECK_LAUNCH();
+    return NRV_OK;
 }
 
 }  // namespace nrv

@@ -355,6 +355,14 @@ struct Bwd {
 
     nrv_status dgrad_conv(int l, TView<const T> gpre, TView<T> out, TView<const T> mask,
                           int level) {
+        // this translation unit has its own instance of the kernel template
+        static bool attr = false;
+        if (!attr) {
+            NRV_CHECK_CUDA(cudaFuncSetAttribute(conv3_simt_kernel<T>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                9 * 128 * 16 * 4));
+            attr = true;
+        }
         const Layer& L = net->layers[l];
         Conv3Args<T> a;
         a.x1 = gpre;

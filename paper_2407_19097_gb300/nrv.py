@@ -71,6 +71,7 @@ SIGNATURES = {
     "nrv_net_set_params": (I, [P, P, P]),
     "nrv_net_set_act_scales": (I, [P, ctypes.POINTER(F), I]),
     "nrv_shade": (I, [P, P, I, I, I, I, P, P]),
+    "nrv_net_layer_backend": (I, [P, I]),
     "nrv_net_forward_train": (I, [P, P, I, I, I, I, P, P]),
     "nrv_net_backward": (I, [P, P, P, P]),
     "nrv_l1_loss": (I, [P, P, I64, P, P, P]),
@@ -209,6 +210,10 @@ class Net:
 
     def shade(self, netin, n, height, width, prec, rgb, stream=None):
         check(lib().nrv_shade(self.h, _ptr(netin), n, height, width, prec, _ptr(rgb), _stream(stream)))
+
+    def backends(self):
+        """Per layer: 0 SIMT, 1 tensor cores, -1 not run (most recent forward)."""
+        return [lib().nrv_net_layer_backend(self.h, l) for l in range(lib().nrv_net_num_layers())]
 
     def forward_train(self, netin, n, height, width, prec, rgb, stream=None):
         check(lib().nrv_net_forward_train(self.h, _ptr(netin), n, height, width, prec, _ptr(rgb),

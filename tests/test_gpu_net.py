@@ -68,51 +68,81 @@ def test_forward_bf16(c0, n, h, w):
     err = np.abs(got - ref).max()
     p = psnr_range(got, ref)
     assert err <= 2e-2 and p >= 45.0, (err, p)
+    # every 3x3 convolution ran on the tensor cores
+    kinds = [k for (_, k, _, _, _, _) in nrv.layer_table(c0)]
+    assert [b for b, k in zip(net.backends(), kinds) if k == 0] == [1] * 14, net.backends()
+
+
+def _bf16(t):
+    return oracle.bf16_value(oracle.bf16_bits(np.asarray(t, np.float32))).astype(np.float64)
+
+
+def _fwd_params(flat, c0, prec):
+    """Weights as each forward kernel uses them: the BF16 path's 3x3 convolutions read BF16
+    weights; transposed convs, the head and every backward kernel read the FP32 master copy."""
+    P = unet.unflatten(flat, c0)
+    if prec == 1:
+        P = {k: ((_bf16(w), b) if w.shape[2:] == (3, 3) else (w, b)) for k, (w, b) in P.items()}
+    return P
+
+
+def _clean_case(prec, c0=5, n=2, h=16, w=24, margin=1e-6):
+    """First seeded (weights, input) whose ReLU decisions all clear zero by `margin` (relative),
+    so that FP32/FP64 accumulation order cannot flip one; the oracle decides."""
+    q = _bf16 if prec == 1 else None
+    for sd in range(64):
+        flat = make_params(c0, seed=100 + sd, bias_sigma=0.05)
+        x = _input(n, h, w, c0, seed=sd)
+        xin = _bf16(x) if prec == 1 else x.astype(np.float64)
+        y, s = unet.forward(xin[..., :c0], _fwd_params(flat, c0, prec), save=True, q=q)
+        if unet.relu_margin(s) >= margin:
+            return flat, x, s, q
+    raise AssertionError("no seed with clear ReLU decisions")
 
 
 def _grad_case(prec, tol):
     import torch
     from paper_2407_19097_gb300 import nrv
-    c0, n, h, w = 5, 2, 32, 48
-    flat = make_params(c0, seed=21, bias_sigma=0.05)
+    c0, n, h, w = 5, 2, 16, 24
+    flat, x, s, q = _clean_case(prec, c0, n, h, w)
     net, p = _net(c0, flat)
-    x = _input(n, h, w, c0, seed=3)
     dev = torch_dev()
+    xt = torch.from_numpy(x).to(dev)
     if prec == nrv.PREC_BF16:
-        xt = torch.from_numpy(x).to(dev).to(torch.bfloat16)
-        xin = xt.float().cpu().numpy()
-    else:
-        xt = torch.from_numpy(x).to(dev)
-        xin = x
+        xt = xt.to(torch.bfloat16)
     rgb = torch.empty((n, h, w, 3), device=dev)
     net.forward_train(xt, n, h, w, prec, rgb)
     rng = np.random.default_rng(4)
     dy = (rng.standard_normal((n, h, w, 3)) * 1e-2).astype(np.float32)
     g = torch.zeros_like(p)
     net.backward(torch.from_numpy(dy).to(dev), g)
-    y, s = unet.forward(xin[..., :c0].astype(np.float64), unet.unflatten(flat, c0), save=True)
-    gr, _ = unet.backward(dy.astype(np.float64), unet.unflatten(flat, c0), s)
+    gr, _ = unet.backward(dy.astype(np.float64), unet.unflatten(flat, c0), s, q=q)
     torch.cuda.synchronize()
     gg = g.cpu().numpy().astype(np.float64)
     o = 0
+    errs = {}
     for name, kind, ci, co in unet.layers(c0):
         wref, bref = gr[name]
-        for ref in (wref.ravel(), bref.ravel()):
+        for part, ref in (("w", wref), ("b", bref)):
             got = gg[o:o + ref.size]
-            rel = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-30)
-            assert rel <= tol, (name, rel)
+            errs[name + "." + part] = np.linalg.norm(got - ref.ravel()) / max(np.linalg.norm(ref), 1e-30)
             o += ref.size
     assert o == gg.size
+    report = " ".join(f"{k}={v:.2e}" for k, v in errs.items())
+    assert all(v <= tol for v in errs.values()), report
 
 
 def test_backward_fp32():
+    """FP32 backward vs the float64 oracle."""
     from paper_2407_19097_gb300 import nrv
     _grad_case(nrv.PREC_F32, 1e-4)
 
 
 def test_backward_bf16():
+    """BF16 backward vs the oracle at BF16 storage precision: the same tensors rounded to BF16
+    where the kernels store them, FP32/FP64 accumulation inside each layer."""
     from paper_2407_19097_gb300 import nrv
-    _grad_case(nrv.PREC_BF16, 5e-2)
+    _grad_case(nrv.PREC_BF16, 1e-2)
 
 
 def test_l1_and_adam():

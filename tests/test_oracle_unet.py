@@ -138,3 +138,61 @@ def test_l1_loss_and_adam_match_torch():
         opt.step()
         p, m, v = unet.adam_step(p, grad, m, v, step)
     np.testing.assert_allclose(p, pt.detach().numpy(), rtol=0, atol=1e-15)
+
+
+class _RoundBoth(torch.autograd.Function):
+    """Rounds a float64 tensor to bfloat16 values in forward and its gradient in backward."""
+
+    @staticmethod
+    def forward(ctx, t):
+        return t.to(torch.bfloat16).to(torch.float64)
+
+    @staticmethod
+    def backward(ctx, g):
+        return g.to(torch.bfloat16).to(torch.float64)
+
+
+def _torch_unet_rounded(x_nhwc, flat, c0):
+    """torch.nn.functional U-Net with every stored tensor (and its gradient) rounded to bf16."""
+    R = _RoundBoth.apply
+    p, o = {}, 0
+    for name, kind, ci, co in unet.layers(c0):
+        shp = unet.weight_shape(kind, ci, co)
+        n = int(np.prod(shp))
+        p[name] = (flat[o:o + n].view(shp), flat[o + n:o + n + co])
+        o += n + co
+    cr = lambda name, t: R(F.relu(F.conv2d(t, p[name][0], p[name][1], padding=1)))
+    x = R(x_nhwc).permute(0, 3, 1, 2)
+    e0 = cr("e0b", cr("e0a", x))
+    e1 = cr("e1b", cr("e1a", R(F.avg_pool2d(e0, 2))))
+    e2 = cr("e2b", cr("e2a", R(F.avg_pool2d(e1, 2))))
+    a = cr("e3b", cr("e3a", R(F.avg_pool2d(e2, 2))))
+    for up, da, db, skip in (("up3", "d2a", "d2b", e2), ("up2", "d1a", "d1b", e1), ("up1", "d0a", "d0b", e0)):
+        u = R(F.conv_transpose2d(a, p[up][0], p[up][1], stride=2))
+        a = cr(db, cr(da, R(torch.cat([u, skip], 1))))
+    w, b = p["head"]
+    return F.conv2d(a, w[:, :, None, None], b).permute(0, 2, 3, 1)
+
+
+def test_storage_rounding_hook_matches_torch():
+    """forward/backward with q = bf16 rounding equal torch float64 with bf16 rounding of every
+    stored tensor and of every gradient passed between layers."""
+    import oracle
+    c0 = 5
+    q = lambda t: oracle.bf16_value(oracle.bf16_bits(np.asarray(t, np.float32))).astype(np.float64)
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal((2, 16, 24, c0))
+    flat = _params(c0, seed=13)
+    y, s = unet.forward(x, unet.unflatten(flat, c0), save=True, q=q)
+    xt = torch.tensor(x, requires_grad=True)
+    ft = torch.tensor(flat, requires_grad=True)
+    yt = _torch_unet_rounded(xt, ft, c0)
+    np.testing.assert_allclose(y, yt.detach().numpy(), rtol=1e-9, atol=1e-12)
+    dy = rng.standard_normal(y.shape) * 1e-2
+    (yt * torch.tensor(dy)).sum().backward()
+    g, dx = unet.backward(dy, unet.unflatten(flat, c0), s, q=q)
+    np.testing.assert_allclose(unet.flatten(g, c0), ft.grad.numpy(), rtol=1e-8, atol=1e-12)
+    # with q = identity the hook changes nothing
+    y2 = unet.forward(x, unet.unflatten(flat, c0), q=lambda t: t)
+    np.testing.assert_array_equal(y2, unet.forward(x, unet.unflatten(flat, c0)))
+    assert 0.0 < unet.relu_margin(s) < 1.0
