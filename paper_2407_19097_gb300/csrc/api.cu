@@ -292,6 +292,20 @@ extern "C" nrv_status nrv_shade(nrv_net* net, const void* netin, int n, int h, i
     return net_forward(net, netin, n, h, w, prec, rgb, (cudaStream_t)stream);
 }
 
+extern "C" nrv_status nrv_net_conv3(nrv_net* net, int layer, const void* x1, const void* x2,
+                                    int n, int h, int w, nrv_prec prec, void* y,
+                                    nrv_stream stream) {
+    clear_error();
+    if (!net || !x1 || !y) return fail(NRV_ERR_ARG, "null argument");
+    if (layer < 0 || layer >= NUM_LAYERS || net->layers[layer].kind != CONV3)
+        return fail(NRV_ERR_ARG, "layer %d is not a 3x3 convolution", layer);
+    if (!net->has_params) return fail(NRV_ERR_STATE, "no parameters loaded");
+    if (n < 1 || h < 1 || w < 1 || h > 16384 || w > 16384) return fail(NRV_ERR_ARG, "bad size");
+    if (!aligned(x1, 32) || (x2 && !aligned(x2, 32)) || !aligned(y, 32))
+        return fail(NRV_ERR_ARG, "tensors must be 32-byte aligned");
+    return net_conv3(net, layer, x1, x2, n, h, w, prec, y, (cudaStream_t)stream);
+}
+
 extern "C" int nrv_net_layer_backend(const nrv_net* net, int layer) {
     if (!net || layer < 0 || layer >= NUM_LAYERS) return -1;
     return net->backend[layer];

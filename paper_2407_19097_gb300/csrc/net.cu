@@ -254,3 +254,44 @@ nrv_status net_forward(Net* net, const void* netin, int n, int H, int W, nrv_pre
 }
 
 }  // namespace nrv
+
+namespace nrv {
+
+// One 3x3 conv layer alone (nrv_net_conv3): same kernels and dispatch as the forward pass.
+nrv_status net_conv3(Net* net, int l, const void* x1, const void* x2, int n, int h, int w,
+                     nrv_prec prec, void* y, cudaStream_t s) {
+    NRV_TRY(set_kernel_attrs());
+    const Layer& L = net->layers[l];
+    int c1 = l == L_E0A ? net->c0p : L.cin, c2 = 0;
+    if (l == L_D2A || l == L_D1A || l == L_D0A) {
+        c1 = L.cin / 2;
+        c2 = L.cin / 2;
+    }
+    if ((c2 > 0) != (x2 != nullptr)) return fail(NRV_ERR_ARG, "layer %s: x2 must be %s", L.name,
+                                                 c2 ? "given" : "NULL");
+    Geo g;
+    memset(&g, 0, sizeof(g));
+    g.n = n;
+    g.h[0] = h;
+    g.w[0] = w;
+    if (prec == NRV_PREC_BF16) {
+        nrv_status st = tc_conv3(net, l, x1, c1, x2, c2, y, g, 0, prec, s);
+        net->backend[l] = 1;
+        if (st != NRV_ERR_UNSUPPORTED) return st;
+        clear_error();
+        net->backend[l] = 0;
+        using T = __nv_bfloat16;
+        return simt_conv3<T>(net, l, TView<const T>{(const T*)x1, c1}, c1,
+                             TView<const T>{(const T*)x2, c2}, c2, TView<T>{(T*)y, L.cout}, g, 0,
+                             true, s);
+    }
+    if (prec == NRV_PREC_F32) {
+        net->backend[l] = 0;
+        return simt_conv3<float>(net, l, TView<const float>{(const float*)x1, c1}, c1,
+                                 TView<const float>{(const float*)x2, c2}, c2,
+                                 TView<float>{(float*)y, L.cout}, g, 0, true, s);
+    }
+    return fail(NRV_ERR_UNSUPPORTED, "nrv_net_conv3 runs in F32 or BF16");
+}
+
+}  // namespace nrv

@@ -77,3 +77,8 @@ nrv_status launch_adam(float* p, const float* g, float* m, float* v, int64_t n, 
                        float lr, float b1, float b2, float eps, cudaStream_t s);
 
 }  // namespace nrv
+
+namespace nrv {
+nrv_status net_conv3(Net* net, int l, const void* x1, const void* x2, int n, int h, int w,
+                     nrv_prec prec, void* y, cudaStream_t s);
+}

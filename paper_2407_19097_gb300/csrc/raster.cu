@@ -35,6 +35,30 @@ nrv_status launch_clear_keys(const RViews& views, cudaStream_t s) {
     return NRV_OK;
 }
 
+// Projection + clipping of one point for one view; on success returns the key
+// and the address of its pixel's key.
+__device__ __forceinline__ bool project_point(const RView& v, float x, float y, float z,
+                                              uint32_t idx, unsigned long long*& p,
+                                              unsigned long long& key) {
+    const float cw = __fadd_rn(
+        __fadd_rn(__fadd_rn(__fmul_rn(v.m[8], x), __fmul_rn(v.m[9], y)), __fmul_rn(v.m[10], z)),
+        v.m[11]);
+    if (!(cw >= v.znear && cw <= v.zfar)) return false;
+    const float cx = __fadd_rn(
+        __fadd_rn(__fadd_rn(__fmul_rn(v.m[0], x), __fmul_rn(v.m[1], y)), __fmul_rn(v.m[2], z)),
+        v.m[3]);
+    const float cy = __fadd_rn(
+        __fadd_rn(__fadd_rn(__fmul_rn(v.m[4], x), __fmul_rn(v.m[5], y)), __fmul_rn(v.m[6], z)),
+        v.m[7]);
+    const float sx = __fmul_rn(__fadd_rn(__fdiv_rn(cx, cw), 1.0f), v.hw);
+    const float sy = __fmul_rn(__fsub_rn(1.0f, __fdiv_rn(cy, cw)), v.hh);
+    if (!(sx >= 0.0f && sx < v.fw && sy >= 0.0f && sy < v.fh)) return false;
+    const int px = __float2int_rz(sx), py = __float2int_rz(sy);
+    key = ((unsigned long long)__float_as_uint(cw) << 32) | idx;
+    p = v.key + (size_t)py * v.width + px;
+    return true;
+}
+
 __device__ __forceinline__ void render_point(const RView& v, float x, float y, float z,
                                              uint32_t idx) {
     const float cw = __fadd_rn(
@@ -56,24 +80,50 @@ __device__ __forceinline__ void render_point(const RView& v, float x, float y, f
     if (key < __ldcg(p)) atomicMin(p, key);
 }
 
-// One thread handles 4 consecutive points = 48 bytes = three 16-byte loads.
+// One thread handles 4 consecutive points = 48 bytes = three 16-byte loads, and
+// prefetches its next group while it works on this one.  Per view, the four
+// points are projected first and their four early-depth reads issued together,
+// so each thread keeps four L2 round trips in flight instead of one.
 __global__ void __launch_bounds__(256) visibility_kernel(const float4* __restrict__ xyz4,
                                                          uint64_t ngroups,
                                                          const float* __restrict__ xyz,
                                                          uint64_t n, RViews vs) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < ngroups; g += stride) {
-        const float4 a = __ldg(xyz4 + 3 * g);
-        const float4 b = __ldg(xyz4 + 3 * g + 1);
-        const float4 c = __ldg(xyz4 + 3 * g + 2);
+    uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a, c = a;
+    if (g < ngroups) {
+        a = __ldcs(xyz4 + 3 * g);
+        b = __ldcs(xyz4 + 3 * g + 1);
+        c = __ldcs(xyz4 + 3 * g + 2);
+    }
+    for (; g < ngroups; g += stride) {
+        const uint64_t gn = g + stride;
+        float4 na = a, nb = b, nc = c;
+        if (gn < ngroups) {
+            na = __ldcs(xyz4 + 3 * gn);
+            nb = __ldcs(xyz4 + 3 * gn + 1);
+            nc = __ldcs(xyz4 + 3 * gn + 2);
+        }
+        const float px[4] = {a.x, a.w, b.z, c.y};
+        const float py[4] = {a.y, b.x, b.w, c.z};
+        const float pz[4] = {a.z, b.y, c.x, c.w};
         const uint32_t i0 = (uint32_t)(4 * g);
         for (int v = 0; v < vs.n; ++v) {
             const RView& vw = vs.v[v];
-            render_point(vw, a.x, a.y, a.z, i0);
-            render_point(vw, a.w, b.x, b.y, i0 + 1);
-            render_point(vw, b.z, b.w, c.x, i0 + 2);
-            render_point(vw, c.y, c.z, c.w, i0 + 3);
+            unsigned long long* ptr[4];
+            unsigned long long key[4], cur[4];
+            bool ok[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) ok[j] = project_point(vw, px[j], py[j], pz[j], i0 + j, ptr[j], key[j]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) cur[j] = ok[j] ? __ldcg(ptr[j]) : 0ull;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (ok[j] && key[j] < cur[j]) atomicMin(ptr[j], key[j]);
         }
+        a = na;
+        b = nb;
+        c = nc;
     }
     // the last n mod 4 points
     if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
