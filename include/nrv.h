@@ -206,16 +206,18 @@ nrv_status nrv_net_set_act_scales(nrv_net* net, const float* act_scale, int n);
 nrv_status nrv_shade(nrv_net* net, const void* d_netin, int n, int height, int width,
                      nrv_prec prec, float* d_rgb, nrv_stream stream);
 
-/* One 3x3 convolution layer of the net (kind 0 in the layer table) on its own:
- * y = ReLU(conv3x3(concat(x1, x2)) + bias), zero "same" padding, NHWC.  x1 has
- * the layer's first-source channels (8 for e0a, C_in/2 for the concatenating
- * layers d2a/d1a/d0a, C_in otherwise); x2 holds the skip half for d2a/d1a/d0a
- * and must be NULL for the others.  y is [n][h][w][C_out].  Element type from
- * prec: F32 (SIMT kernel) or BF16 (tensor-core kernel).  The building block of
- * nrv_shade, exposed so a layer can be checked or reused alone.
+/* One layer of the net on its own, NHWC, input [n][h][w][.]:
+ *  - a 3x3 convolution (kind 0): y = ReLU(conv3x3(concat(x1, x2)) + bias), zero
+ *    "same" padding, y [n][h][w][C_out].  x1 has the layer's first-source
+ *    channels (8 for e0a, C_in/2 for the concatenating layers d2a/d1a/d0a, C_in
+ *    otherwise); x2 holds the skip half for d2a/d1a/d0a, NULL for the others;
+ *  - a 2x2 stride-2 transposed convolution (kind 1): y[2i+a][2j+b][o] =
+ *    bias[o] + sum_c x1[i][j][c] W[c][o][a][b], y [n][2h][2w][C_out]; x2 NULL.
+ * Element type from prec: F32 (SIMT kernels) or BF16 (tensor-core kernels).  The
+ * building blocks of nrv_shade, exposed so a layer can be checked or reused alone.
  * Errors: NRV_ERR_ARG, NRV_ERR_STATE (no parameters), NRV_ERR_UNSUPPORTED. */
-nrv_status nrv_net_conv3(nrv_net* net, int layer, const void* d_x1, const void* d_x2, int n, int h,
-                         int w, nrv_prec prec, void* d_y, nrv_stream stream);
+nrv_status nrv_net_run_layer(nrv_net* net, int layer, const void* d_x1, const void* d_x2, int n,
+                             int h, int w, nrv_prec prec, void* d_y, nrv_stream stream);
 
 /* Which kernel family ran layer `layer` in the net's most recent forward pass:
  * 0 = SIMT (CUDA cores), 1 = tensor cores (tcgen05), -1 = not run yet or a

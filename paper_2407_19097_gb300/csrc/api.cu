@@ -48,7 +48,24 @@ struct nrv_scene {
     nrv_scene_desc d;
 };
 
-struct nrv_net : Net {};
+// A captured whole frame (nrv_render_batch) and the device copy of the cameras it reads.
+struct BatchGraph {
+    std::vector<uint64_t> sig;
+    cudaGraphExec_t exec = nullptr;
+    RViews* views_dev = nullptr;
+};
+
+struct nrv_net : Net {
+    std::vector<BatchGraph> graphs;
+    void drop_graphs() {
+        for (BatchGraph& g : graphs) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            if (g.views_dev) cudaFree(g.views_dev);
+        }
+        graphs.clear();
+    }
+    ~nrv_net() { drop_graphs(); }
+};
 
 // --------------------------------------------------------------------- library
 extern "C" const char* nrv_last_error(void) { return g_err; }
@@ -292,18 +309,18 @@ extern "C" nrv_status nrv_shade(nrv_net* net, const void* netin, int n, int h, i
     return net_forward(net, netin, n, h, w, prec, rgb, (cudaStream_t)stream);
 }
 
-extern "C" nrv_status nrv_net_conv3(nrv_net* net, int layer, const void* x1, const void* x2,
-                                    int n, int h, int w, nrv_prec prec, void* y,
-                                    nrv_stream stream) {
+extern "C" nrv_status nrv_net_run_layer(nrv_net* net, int layer, const void* x1, const void* x2,
+                                        int n, int h, int w, nrv_prec prec, void* y,
+                                        nrv_stream stream) {
     clear_error();
     if (!net || !x1 || !y) return fail(NRV_ERR_ARG, "null argument");
-    if (layer < 0 || layer >= NUM_LAYERS || net->layers[layer].kind != CONV3)
-        return fail(NRV_ERR_ARG, "layer %d is not a 3x3 convolution", layer);
+    if (layer < 0 || layer >= NUM_LAYERS || net->layers[layer].kind == HEAD1)
+        return fail(NRV_ERR_ARG, "layer %d is not a 3x3 or transposed convolution", layer);
     if (!net->has_params) return fail(NRV_ERR_STATE, "no parameters loaded");
     if (n < 1 || h < 1 || w < 1 || h > 16384 || w > 16384) return fail(NRV_ERR_ARG, "bad size");
     if (!aligned(x1, 32) || (x2 && !aligned(x2, 32)) || !aligned(y, 32))
         return fail(NRV_ERR_ARG, "tensors must be 32-byte aligned");
-    return net_conv3(net, layer, x1, x2, n, h, w, prec, y, (cudaStream_t)stream);
+    return net_run_layer(net, layer, x1, x2, n, h, w, prec, y, (cudaStream_t)stream);
 }
 
 extern "C" int nrv_net_layer_backend(const nrv_net* net, int layer) {
@@ -438,33 +455,106 @@ extern "C" nrv_status nrv_render_batch(nrv_scene* s, nrv_net* net, const nrv_pac
     memset(&rv, 0, sizeof(rv));
     rv.n = n;
     for (int i = 0; i < n; ++i) rv.v[i] = make_rview(views[i], (uint64_t*)(base + key_off[i]));
-    std::vector<cudaEvent_t> ev;
-    prof_mark(ev, st);
-    NRV_TRY(launch_clear_keys(rv, st));
-    prof_mark(ev, st);
-    NRV_TRY(launch_visibility(s->d.d_xyz, s->d.n_points, rv, st));
-    prof_mark(ev, st);
-    for (int i = 0; i < n; ++i) {
-        ResolveArgs a;
-        memset(&a, 0, sizeof(a));
-        a.key = reinterpret_cast<const unsigned long long*>(base + key_off[i]);
-        a.attr = s->d.d_attr;
-        a.stride_words = s->d.stride_words;
-        a.n_words = s->d.n_words;
-        a.width = views[i].width;
-        a.height = views[i].height;
-        a.wn = nrv_pad8(a.width);
-        a.hn = nrv_pad8(a.height);
-        a.netin = base + in_off[i];
-        fill_pack(a, d, prec, inv);
-        NRV_TRY(launch_resolve(a, st));
+
+    // everything but the cameras is fixed by this signature; a captured frame is replayed
+    auto make_sig = [&]() {
+        std::vector<uint64_t> sig = {(uint64_t)(uintptr_t)s->d.d_xyz, s->d.n_points,
+                                     (uint64_t)(uintptr_t)s->d.d_attr, (uint64_t)s->d.stride_words,
+                                     (uint64_t)s->d.n_words, (uint64_t)prec, (uint64_t)n};
+        for (int i = 0; i < n; ++i) {
+            sig.push_back(((uint64_t)views[i].width << 32) | (uint32_t)views[i].height);
+            sig.push_back((uint64_t)(uintptr_t)rgb[i]);
+        }
+        uint64_t dw[(sizeof(nrv_pack_desc) + 7) / 8] = {};
+        memcpy(dw, d, sizeof(nrv_pack_desc));
+        for (uint64_t w : dw) sig.push_back(w);
+        uint32_t inv_bits;
+        memcpy(&inv_bits, &inv, 4);
+        sig.push_back(inv_bits);
+        // the captured kernels hold these buffers' addresses
+        for (const DevBuf* b : {&net->batch_ws, &net->acts, &net->params, &net->wf32, &net->wbf16}) {
+            sig.push_back((uint64_t)(uintptr_t)b->p);
+            sig.push_back(b->bytes);
+        }
+        return sig;
+    };
+    std::vector<uint64_t> sig = make_sig();
+
+    auto frame = [&](const RViews* views_dev, std::vector<cudaEvent_t>* ev,
+                     cudaStream_t q) -> nrv_status {
+        if (ev) prof_mark(*ev, q);
+        NRV_TRY(launch_clear_keys(rv, q));
+        if (ev) prof_mark(*ev, q);
+        NRV_TRY(launch_visibility(s->d.d_xyz, s->d.n_points, rv, q, views_dev));
+        if (ev) prof_mark(*ev, q);
+        for (int i = 0; i < n; ++i) {
+            ResolveArgs a;
+            memset(&a, 0, sizeof(a));
+            a.key = reinterpret_cast<const unsigned long long*>(base + key_off[i]);
+            a.attr = s->d.d_attr;
+            a.stride_words = s->d.stride_words;
+            a.n_words = s->d.n_words;
+            a.width = views[i].width;
+            a.height = views[i].height;
+            a.wn = nrv_pad8(a.width);
+            a.hn = nrv_pad8(a.height);
+            a.netin = base + in_off[i];
+            fill_pack(a, d, prec, inv);
+            NRV_TRY(launch_resolve(a, q));
+        }
+        if (ev) prof_mark(*ev, q);
+        for (int i = 0; i < n; ++i)
+            NRV_TRY(net_forward(net, base + in_off[i], 1, views[i].height, views[i].width, prec,
+                                rgb[i], q));
+        if (ev) prof_mark(*ev, q);
+        return NRV_OK;
+    };
+
+    if (g_profile) {  // eager, with stage events
+        std::vector<cudaEvent_t> ev;
+        NRV_TRY(frame(nullptr, &ev, st));
+        g_prof_events.push_back(ev);
+        return NRV_OK;
     }
-    prof_mark(ev, st);
-    for (int i = 0; i < n; ++i)
-        NRV_TRY(net_forward(net, base + in_off[i], 1, views[i].height, views[i].width, prec, rgb[i],
-                            st));
-    prof_mark(ev, st);
-    if (g_profile) g_prof_events.push_back(ev);
+    for (BatchGraph& g : net->graphs)
+        if (g.sig == sig) {
+            NRV_CHECK_CUDA(cudaMemcpyAsync(g.views_dev, &rv, sizeof(RViews), cudaMemcpyHostToDevice, st));
+            NRV_CHECK_CUDA(cudaGraphLaunch(g.exec, st));
+            return NRV_OK;
+        }
+    // first frame of this signature: run it, then capture the same work for replay
+    NRV_TRY(frame(nullptr, nullptr, st));
+    if (net->graphs.size() >= 8) net->drop_graphs();
+    BatchGraph g;
+    g.sig = make_sig();   // the eager frame may have grown the workspaces
+    NRV_CHECK_CUDA(cudaMalloc(&g.views_dev, sizeof(RViews)));
+    cudaStream_t cap;
+    NRV_CHECK_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    // the capture stream starts after the eager frame
+    cudaEvent_t ready;
+    NRV_CHECK_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    NRV_CHECK_CUDA(cudaEventRecord(ready, st));
+    NRV_CHECK_CUDA(cudaStreamWaitEvent(cap, ready, 0));
+    cudaGraph_t graph = nullptr;
+    nrv_status fs = NRV_OK;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        fs = frame(g.views_dev, nullptr, cap);
+        e = cudaStreamEndCapture(cap, &graph);
+    }
+    if (e == cudaSuccess && fs == NRV_OK) e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamSynchronize(cap);
+    cudaStreamDestroy(cap);
+    cudaEventDestroy(ready);
+    if (e != cudaSuccess || fs != NRV_OK) {
+        cudaGetLastError();
+        cudaFree(g.views_dev);
+        // the eager frame already produced the output; replay is only an optimisation
+        clear_error();
+        return NRV_OK;
+    }
+    net->graphs.push_back(g);
     return NRV_OK;
 }
 

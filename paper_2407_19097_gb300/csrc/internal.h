@@ -74,7 +74,8 @@ struct ResolveArgs {
 };
 
 nrv_status launch_clear_keys(const RViews& views, cudaStream_t s);
-nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, cudaStream_t s);
+nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, cudaStream_t s,
+                             const RViews* views_dev = nullptr);
 nrv_status launch_resolve(const ResolveArgs& a, cudaStream_t s);
 nrv_status launch_pack_planes(const uint32_t* depth, const uint8_t* mask, const uint32_t* gattr,
                               const ResolveArgs& a, cudaStream_t s);

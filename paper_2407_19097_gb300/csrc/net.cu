@@ -165,6 +165,19 @@ static nrv_status simt_conv3(const Net* net, int l, TView<const T> x1, int c1, T
 }
 
 template <typename T>
+static nrv_status simt_upconv(const Net* net, int l, TView<const T> x, TView<T> y, int n, int hi,
+                              int wi, cudaStream_t s) {
+    const Layer& L = net->layers[l];
+    const size_t npx = (size_t)n * hi * wi * 4;
+    dim3 grid((unsigned)((npx + 127) / 128), L.cout / 16);
+    upconv2_kernel<T><<<grid, 128, (size_t)4 * L.cin * 16 * 4, s>>>(
+        x, L.cin, (const float*)net->wf32.p + net->wf_off[l], (const float*)net->params.p + L.boff,
+        y, L.cout, n, hi, wi);
+    NRV_CHECK_LAUNCH();
+    return NRV_OK;
+}
+
+template <typename T>
 static nrv_status forward_t(Net* net, const T* netin, float* rgb, cudaStream_t s, bool use_tc,
                             nrv_prec prec) {
     const Geo& g = net->geo;
@@ -190,13 +203,15 @@ static nrv_status forward_t(Net* net, const T* netin, float* rgb, cudaStream_t s
     };
     auto upconv = [&](int l, int in, int out, int level_in) -> nrv_status {
         const Layer& L = net->layers[l];
-        const size_t npx = g.px(level_in) * 4;
-        dim3 grid((unsigned)((npx + 127) / 128), L.cout / 16);
-        upconv2_kernel<T><<<grid, 128, (size_t)4 * L.cin * 16 * 4, s>>>(
-            CV(in), L.cin, (const float*)net->wf32.p + net->wf_off[l],
-            (const float*)net->params.p + L.boff, V(out), L.cout, g.n, g.h[level_in], g.w[level_in]);
-        NRV_CHECK_LAUNCH();
-        return NRV_OK;
+        if (use_tc) {
+            nrv_status st = tc_upconv(net, l, act<T>(net, in), act<T>(net, out), g, level_in, prec, s);
+            net->backend[l] = 1;
+            if (st != NRV_ERR_UNSUPPORTED) return st;
+            clear_error();
+        }
+        net->backend[l] = 0;
+        (void)L;
+        return simt_upconv<T>(net, l, CV(in), V(out), g.n, g.h[level_in], g.w[level_in], s);
     };
     const TView<const T> x{netin, net->c0p};
     const TView<const T> none{nullptr, 0};
@@ -257,11 +272,35 @@ nrv_status net_forward(Net* net, const void* netin, int n, int H, int W, nrv_pre
 
 namespace nrv {
 
-// One 3x3 conv layer alone (nrv_net_conv3): same kernels and dispatch as the forward pass.
-nrv_status net_conv3(Net* net, int l, const void* x1, const void* x2, int n, int h, int w,
-                     nrv_prec prec, void* y, cudaStream_t s) {
+// One layer alone (nrv_net_run_layer): same kernels and dispatch as the forward pass.
+nrv_status net_run_layer(Net* net, int l, const void* x1, const void* x2, int n, int h, int w,
+                         nrv_prec prec, void* y, cudaStream_t s) {
     NRV_TRY(set_kernel_attrs());
     const Layer& L = net->layers[l];
+    if (L.kind == UPCONV2) {
+        if (x2) return fail(NRV_ERR_ARG, "layer %s: x2 must be NULL", L.name);
+        Geo g;
+        memset(&g, 0, sizeof(g));
+        g.n = n;
+        g.h[0] = h;
+        g.w[0] = w;
+        if (prec == NRV_PREC_BF16) {
+            nrv_status st = tc_upconv(net, l, x1, y, g, 0, prec, s);
+            net->backend[l] = 1;
+            if (st != NRV_ERR_UNSUPPORTED) return st;
+            clear_error();
+            net->backend[l] = 0;
+            using T = __nv_bfloat16;
+            return simt_upconv<T>(net, l, TView<const T>{(const T*)x1, L.cin},
+                                  TView<T>{(T*)y, L.cout}, n, h, w, s);
+        }
+        if (prec == NRV_PREC_F32) {
+            net->backend[l] = 0;
+            return simt_upconv<float>(net, l, TView<const float>{(const float*)x1, L.cin},
+                                      TView<float>{(float*)y, L.cout}, n, h, w, s);
+        }
+        return fail(NRV_ERR_UNSUPPORTED, "nrv_net_run_layer runs in F32 or BF16");
+    }
     int c1 = l == L_E0A ? net->c0p : L.cin, c2 = 0;
     if (l == L_D2A || l == L_D1A || l == L_D0A) {
         c1 = L.cin / 2;
@@ -291,7 +330,7 @@ nrv_status net_conv3(Net* net, int l, const void* x1, const void* x2, int n, int
                                  TView<const float>{(const float*)x2, c2}, c2,
                                  TView<float>{(float*)y, L.cout}, g, 0, true, s);
     }
-    return fail(NRV_ERR_UNSUPPORTED, "nrv_net_conv3 runs in F32 or BF16");
+    return fail(NRV_ERR_UNSUPPORTED, "nrv_net_run_layer runs in F32 or BF16");
 }
 
 }  // namespace nrv

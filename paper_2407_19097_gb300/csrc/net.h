@@ -69,6 +69,8 @@ nrv_status net_repack(Net* net, cudaStream_t s);
 // tensor-core convolution (tc.cu); returns NRV_ERR_UNSUPPORTED when a shape is not covered
 nrv_status tc_conv3(const Net* net, int layer, const void* x1, int c1, const void* x2, int c2,
                     void* y, const Geo& g, int level, nrv_prec prec, cudaStream_t s);
+nrv_status tc_upconv(const Net* net, int layer, const void* x, void* y, const Geo& g, int level_in,
+                     nrv_prec prec, cudaStream_t s);
 
 // training kernels (train.cu)
 nrv_status launch_l1(const float* y, const float* t, int64_t n, float* loss, float* dy,
@@ -79,6 +81,6 @@ nrv_status launch_adam(float* p, const float* g, float* m, float* v, int64_t n, 
 }  // namespace nrv
 
 namespace nrv {
-nrv_status net_conv3(Net* net, int l, const void* x1, const void* x2, int n, int h, int w,
+nrv_status net_run_layer(Net* net, int l, const void* x1, const void* x2, int n, int h, int w,
                      nrv_prec prec, void* y, cudaStream_t s);
 }

@@ -37,6 +37,15 @@ nrv_status launch_clear_keys(const RViews& views, cudaStream_t s) {
 
 // Projection + clipping of one point for one view; on success returns the key
 // and the address of its pixel's key.
+//
+// The pixel is first found from the fast quotient __fdividef (documented error
+// <= 2 ulp for divisors in [2^-126, 2^126]).  Propagating that error, plus the
+// rounding of the exact sequence, through (q + 1) * W/2 bounds the distance
+// between the fast and the exact sx by W/2 * 2^-22 * (2.25|q| + 1), which the
+// code over-estimates as W/2 * 2^-20 * (|q| + 4).  When sx lies farther than
+// that from every integer (and likewise sy), truncation and the on-screen test
+// give the same answer as the exact sequence; otherwise the exact IEEE
+// divisions decide.  The key's depth is w itself, never a quotient.
 __device__ __forceinline__ bool project_point(const RView& v, float x, float y, float z,
                                               uint32_t idx, unsigned long long*& p,
                                               unsigned long long& key) {
@@ -50,6 +59,21 @@ __device__ __forceinline__ bool project_point(const RView& v, float x, float y, 
     const float cy = __fadd_rn(
         __fadd_rn(__fadd_rn(__fmul_rn(v.m[4], x), __fmul_rn(v.m[5], y)), __fmul_rn(v.m[6], z)),
         v.m[7]);
+    if (cw >= 0x1p-125f && cw <= 0x1p125f) {
+        const float qx = __fdividef(cx, cw), qy = __fdividef(cy, cw);
+        const float ax = __fmul_rn(__fadd_rn(qx, 1.0f), v.hw);
+        const float ay = __fmul_rn(__fsub_rn(1.0f, qy), v.hh);
+        const float ex = (fabsf(qx) + 4.0f) * v.hw * 0x1p-20f;
+        const float ey = (fabsf(qy) + 4.0f) * v.hh * 0x1p-20f;
+        const float fx = floorf(ax), fy = floorf(ay);
+        // (ax - fx) and (fx + 1 - ax) are exact; NaN or infinity fails every test
+        if (ax - fx > ex && (fx + 1.0f) - ax > ex && ay - fy > ey && (fy + 1.0f) - ay > ey) {
+            if (!(fx >= 0.0f && fx < v.fw && fy >= 0.0f && fy < v.fh)) return false;
+            key = ((unsigned long long)__float_as_uint(cw) << 32) | idx;
+            p = v.key + (size_t)(int)fy * v.width + (int)fx;
+            return true;
+        }
+    }
     const float sx = __fmul_rn(__fadd_rn(__fdiv_rn(cx, cw), 1.0f), v.hw);
     const float sy = __fmul_rn(__fsub_rn(1.0f, __fdiv_rn(cy, cw)), v.hh);
     if (!(sx >= 0.0f && sx < v.fw && sy >= 0.0f && sy < v.fh)) return false;
@@ -84,10 +108,20 @@ __device__ __forceinline__ void render_point(const RView& v, float x, float y, f
 // prefetches its next group while it works on this one.  Per view, the four
 // points are projected first and their four early-depth reads issued together,
 // so each thread keeps four L2 round trips in flight instead of one.
+// The views come by value, or -- when a captured frame is replayed with new
+// cameras -- from device memory (views_dev); each block keeps them in shared memory.
+// SINGLE: one view, kept in registers for the whole pass.
+template <bool SINGLE>
 __global__ void __launch_bounds__(256) visibility_kernel(const float4* __restrict__ xyz4,
                                                          uint64_t ngroups,
                                                          const float* __restrict__ xyz,
-                                                         uint64_t n, RViews vs) {
+                                                         uint64_t n, RViews vs_arg,
+                                                         const RViews* __restrict__ views_dev) {
+    __shared__ RViews vs;
+    if (threadIdx.x == 0) vs = views_dev ? *views_dev : vs_arg;
+    __syncthreads();
+    RView v0;
+    if (SINGLE) v0 = vs.v[0];
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a, c = a;
@@ -108,8 +142,8 @@ __global__ void __launch_bounds__(256) visibility_kernel(const float4* __restric
         const float py[4] = {a.y, b.x, b.w, c.z};
         const float pz[4] = {a.z, b.y, c.x, c.w};
         const uint32_t i0 = (uint32_t)(4 * g);
-        for (int v = 0; v < vs.n; ++v) {
-            const RView& vw = vs.v[v];
+        for (int v = 0; v < (SINGLE ? 1 : vs.n); ++v) {
+            const RView& vw = SINGLE ? v0 : vs.v[v];
             unsigned long long* ptr[4];
             unsigned long long key[4], cur[4];
             bool ok[4];
@@ -133,14 +167,19 @@ __global__ void __launch_bounds__(256) visibility_kernel(const float4* __restric
     }
 }
 
-nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, cudaStream_t s) {
+nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, cudaStream_t s,
+                             const RViews* views_dev) {
     if (n == 0) return NRV_OK;
     const uint64_t ngroups = n / 4;
     int blocks = 152 * 8;
     const uint64_t need = (ngroups + 255) / 256;
     if (need < (uint64_t)blocks) blocks = (int)(need > 0 ? need : 1);
-    visibility_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(xyz), ngroups, xyz,
-                                             n, views);
+    if (views.n == 1)
+        visibility_kernel<true><<<blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(xyz), ngroups,
+                                                       xyz, n, views, views_dev);
+    else
+        visibility_kernel<false><<<blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(xyz), ngroups,
+                                                        xyz, n, views, views_dev);
     NRV_CHECK_LAUNCH();
     return NRV_OK;
 }

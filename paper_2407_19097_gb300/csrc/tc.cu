@@ -42,8 +42,10 @@ struct TcParams {
     int tiles_x, num_ptiles; // pixel tiles
     int nslices, n_slice;    // output-channel slices and their width
     int nks;                 // K-steps of 16 channels
-    int nbuf;                // halo buffers (1 or 2)
-    int cout;                // output pixel stride (channels)
+    int nbuf;                // halo buffers (1..4)
+    int cout;                // output channels (pixel stride of the output)
+    int mode;                // 0: 3x3 conv + bias + ReLU; 1: 2x2 stride-2 transposed conv + bias
+    int row0;                // first halo row relative to the tile's row (-1 conv, 0 transposed)
     int has_src2;
     uint32_t halo_bytes;     // bytes of one halo buffer (both sources)
     uint32_t src2_off;       // offset of source 2 planes inside a buffer
@@ -173,7 +175,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     conv3_tc_kernel(const __grid_constant__ CUtensorMap tm1, const __grid_constant__ CUtensorMap tm2,
                     const __grid_constant__ TcParams P) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t bars[12];
+    __shared__ __align__(8) uint64_t bars[16];
+    __shared__ float bias_s[256];
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
 
@@ -182,17 +185,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t s_halo = s_w + P.w_region;
     const uint32_t b_w = smem_u32(&bars[0]);
     auto b_hfull = [&](int i) { return smem_u32(&bars[1 + i]); };
-    auto b_hempty = [&](int i) { return smem_u32(&bars[3 + i]); };
-    auto b_afull = [&](int i) { return smem_u32(&bars[5 + i]); };
-    auto b_aempty = [&](int i) { return smem_u32(&bars[7 + i]); };
-    const uint32_t b_done = smem_u32(&bars[9]);
+    auto b_hempty = [&](int i) { return smem_u32(&bars[5 + i]); };
+    auto b_afull = [&](int i) { return smem_u32(&bars[9 + i]); };
+    auto b_aempty = [&](int i) { return smem_u32(&bars[11 + i]); };
+    const uint32_t b_done = smem_u32(&bars[13]);
+
+    // this CTA's output-channel slice and its pixel tiles
+    const int slice = blockIdx.x % P.nslices;
+    const int cta_in_slice = blockIdx.x / P.nslices;
+    const int ctas_per_slice = gridDim.x / P.nslices;
+    const int my_tiles = cta_in_slice < P.num_ptiles
+                             ? (P.num_ptiles - 1 - cta_in_slice) / ctas_per_slice + 1
+                             : 0;
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
         mbar_init(b_w, 1);
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < 4; ++i) {
             mbar_init(b_hfull(i), 1);
             mbar_init(b_hempty(i), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
             mbar_init(b_afull(i), 1);
             mbar_init(b_aempty(i), 4);
         }
@@ -200,6 +213,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
+    // per output column of this slice: its bias (column n maps to channel n mod cout)
+    for (int i = threadIdx.x; i < P.n_slice; i += NTHREADS)
+        bias_s[i] = P.bias[(slice * P.n_slice + i) % P.cout];
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_slot)),
@@ -211,14 +227,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-
-    // this CTA's output-channel slice and its pixel tiles
-    const int slice = blockIdx.x % P.nslices;
-    const int cta_in_slice = blockIdx.x / P.nslices;
-    const int ctas_per_slice = gridDim.x / P.nslices;
-    const int my_tiles = cta_in_slice < P.num_ptiles
-                             ? (P.num_ptiles - 1 - cta_in_slice) / ctas_per_slice + 1
-                             : 0;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -238,9 +246,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int yr = rest % P.h, img = rest / P.h;
                 const uint32_t dst = s_halo + (uint32_t)buf * P.halo_bytes;
                 mbar_expect_tx(b_hfull(buf), P.tx1 + P.tx2);
-                tma_load_5d(dst, &tm1, 0, xt * TILE_M - 1, 0, yr - 1, img, b_hfull(buf));
+                tma_load_5d(dst, &tm1, 0, xt * TILE_M - 1, 0, yr + P.row0, img, b_hfull(buf));
                 if (P.has_src2)
-                    tma_load_5d(dst + P.src2_off, &tm2, 0, xt * TILE_M - 1, 0, yr - 1, img,
+                    tma_load_5d(dst + P.src2_off, &tm2, 0, xt * TILE_M - 1, 0, yr + P.row0, img,
                                 b_hfull(buf));
                 issued = i + 1;
             }
@@ -252,7 +260,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             bool ok = mbar_wait(b_w, 0, &abort_flag, P.status);
-            const uint32_t s_wslice = s_w;
             const uint32_t b_lbo = (uint32_t)P.n_slice * 16;
             for (int i = 0; ok && i < my_tiles; ++i) {
                 const int buf = i % P.nbuf, u = i / P.nbuf;
@@ -264,7 +271,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const uint32_t hb = s_halo + (uint32_t)buf * P.halo_bytes;
                 for (int ks = 0; ks < P.nks; ++ks) {
                     const uint64_t a = sdesc(hb + P.a_off[ks], P.a_lbo[ks], 128);
-                    const uint64_t b = sdesc(s_wslice + (uint32_t)ks * 2 * b_lbo, b_lbo, 128);
+                    const uint64_t b = sdesc(s_w + (uint32_t)ks * 2 * b_lbo, b_lbo, 128);
                     mma_bf16(d, a, b, P.idesc, ks > 0 ? 1u : 0u);
                 }
                 mma_commit(b_hempty(buf));
@@ -275,33 +282,47 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_wait(b_done, 0, &abort_flag, P.status);
         }
     } else {
-        // epilogue: warps 2..5 own TMEM lanes 32*(warp%4) ..
+        // epilogue: warps 2..5 own TMEM lanes 32*(warp%4) ..; one lane per warp polls
         const int q = warp & 3;
         const int m = 32 * q + lane;
         for (int i = 0; i < my_tiles; ++i) {
             const int ab = i & 1, ua = i >> 1;
-            if (!mbar_wait(b_afull(ab), ua & 1, &abort_flag, P.status)) break;
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(b_afull(ab), ua & 1, &abort_flag, P.status) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
             tc_fence_after();
             const int pt = cta_in_slice + i * ctas_per_slice;
             const int xt = pt % P.tiles_x, rest = pt / P.tiles_x;
             const int yr = rest % P.h, img = rest / P.h;
             const int x = xt * TILE_M + m;
-            __nv_bfloat16* out = P.y + (((size_t)img * P.h + yr) * P.w + x) * P.cout +
-                                 (size_t)slice * P.n_slice;
-            const float* bias = P.bias + slice * P.n_slice;
             for (int c0 = 0; c0 < P.n_slice; c0 += 16) {
                 uint32_t r[16];
                 tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * P.n_slice + c0), r);
                 uint32_t packed[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const float v0 = fmaxf(__uint_as_float(r[2 * j]) + bias[c0 + 2 * j], 0.0f);
-                    const float v1 = fmaxf(__uint_as_float(r[2 * j + 1]) + bias[c0 + 2 * j + 1], 0.0f);
+                    float v0 = __uint_as_float(r[2 * j]) + bias_s[c0 + 2 * j];
+                    float v1 = __uint_as_float(r[2 * j + 1]) + bias_s[c0 + 2 * j + 1];
+                    if (P.mode == 0) {
+                        v0 = fmaxf(v0, 0.0f);
+                        v1 = fmaxf(v1, 0.0f);
+                    }
                     __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
                     packed[j] = *reinterpret_cast<uint32_t*>(&h2);
                 }
                 if (x < P.w) {
-                    uint4* o4 = reinterpret_cast<uint4*>(out + c0);
+                    __nv_bfloat16* dst;
+                    const int ng = slice * P.n_slice + c0;
+                    if (P.mode == 0) {
+                        dst = P.y + (((size_t)img * P.h + yr) * P.w + x) * P.cout + ng;
+                    } else {
+                        // transposed conv: column ng = (2a + b) * cout + o  ->  pixel (2y+a, 2x+b)
+                        const int abi = ng / P.cout, o = ng % P.cout;
+                        dst = P.y + (((size_t)img * 2 * P.h + 2 * yr + (abi >> 1)) * 2 * P.w +
+                                     2 * x + (abi & 1)) * P.cout + o;
+                    }
+                    uint4* o4 = reinterpret_cast<uint4*>(dst);
                     o4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
                     o4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
                 }
@@ -346,15 +367,15 @@ EncodeTiledFn encode_fn() {
 }
 
 // NHWC BF16 tensor [n][h][w][c] viewed as (8, w, c/8, h, n) so that one box of
-// (8, 130, c/8, 3, 1) lands in shared memory as [row][chunk][pixel][8].
-nrv_status make_halo_map(CUtensorMap* map, const void* base, int n, int h, int w, int c) {
+// (8, 130, c/8, rows, 1) lands in shared memory as [row][chunk][pixel][8].
+nrv_status make_halo_map(CUtensorMap* map, const void* base, int n, int h, int w, int c, int rows) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return fail(NRV_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
     if (((uintptr_t)base & 15) != 0) return fail(NRV_ERR_ARG, "tensor base not 16-byte aligned");
     const cuuint64_t dims[5] = {8, (cuuint64_t)w, (cuuint64_t)(c / 8), (cuuint64_t)h, (cuuint64_t)n};
     const cuuint64_t strides[4] = {(cuuint64_t)c * 2, 16, (cuuint64_t)w * c * 2,
                                    (cuuint64_t)h * w * c * 2};
-    const cuuint32_t box[5] = {8, HALO_W, (cuuint32_t)(c / 8), 3, 1};
+    const cuuint32_t box[5] = {8, HALO_W, (cuuint32_t)(c / 8), (cuuint32_t)rows, 1};
     const cuuint32_t es[5] = {1, 1, 1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides,
                      box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -368,9 +389,16 @@ struct Half {
     int tap, src, chunk;  // src 0 or 1; tap < 0 marks the zero phantom
 };
 
+// Per-layer tensor-core configuration.  A 3x3 conv reads a 3-row halo and has
+// K = 9 * C_in; a 2x2 stride-2 transposed conv is a plain GEMM of one input row
+// (K = C_in) against all four kernel positions at once (N = 4 * C_out), and its
+// epilogue scatters column (2a + b) * C_out + o to output pixel (2y + a, 2x + b).
 struct TcLayerCfg {
     bool ok = false;
+    int kind = CONV3;
     int c1 = 0, c2 = 0;
+    int rows = 3, row0 = -1;
+    int ncols = 0;           // GEMM N (C_out, or 4 C_out)
     int n_slice = 0, nslices = 0, nks = 0;
     std::vector<Half> halves;
     size_t w_off = 0;        // byte offset of the packed weights in the BF16 buffer
@@ -379,8 +407,8 @@ struct TcLayerCfg {
 
 TcLayerCfg g_cfg[NUM_LAYERS];
 
-__global__ void pack_tc_weights_kernel(const float* __restrict__ P, int64_t woff, int cin_real,
-                                       int cout, int n_slice, int nslices, int nks,
+__global__ void pack_tc_weights_kernel(const float* __restrict__ P, int64_t woff, int kind,
+                                       int cin_real, int cout, int n_slice, int nslices, int nks,
                                        const int4* __restrict__ halves, int c1, uint16_t* out) {
     // out[slice][ks][half][n][8]
     const size_t total = (size_t)nslices * nks * 2 * n_slice * 8;
@@ -395,8 +423,11 @@ __global__ void pack_tc_weights_kernel(const float* __restrict__ P, int64_t woff
         float v = 0.0f;
         if (h.x >= 0) {
             const int c = (h.y == 0 ? 0 : c1) + 8 * h.z + e;
-            const int o = sl * n_slice + nl;
-            if (c < cin_real) v = P[woff + ((size_t)o * cin_real + c) * 9 + h.x];
+            const int n = sl * n_slice + nl;
+            if (c < cin_real) {
+                if (kind == CONV3) v = P[woff + ((size_t)n * cin_real + c) * 9 + h.x];
+                else v = P[woff + ((size_t)c * cout + n % cout) * 4 + n / cout];
+            }
         }
         __nv_bfloat16 b = __float2bfloat16_rn(v);
         out[i] = *reinterpret_cast<uint16_t*>(&b);
@@ -424,22 +455,36 @@ nrv_status tc_repack(Net* net, cudaStream_t s) {
         TcLayerCfg& c = g_cfg[l];
         c = TcLayerCfg();
         const Layer& L = net->layers[l];
-        if (L.kind != CONV3) continue;
-        const int cinp = l == L_E0A ? net->c0p : L.cin;
-        c.c1 = src_split(l, cinp, &c.c2);
-        for (int tap = 0; tap < 9; ++tap)
-            for (int src = 0; src < 2; ++src) {
-                const int cs = src == 0 ? c.c1 : c.c2;
-                for (int ch = 0; ch < cs / 8; ++ch) c.halves.push_back(Half{tap, src, ch});
-            }
+        if (L.kind == HEAD1) continue;
+        c.kind = L.kind;
+        if (L.kind == CONV3) {
+            const int cinp = l == L_E0A ? net->c0p : L.cin;
+            c.c1 = src_split(l, cinp, &c.c2);
+            c.rows = 3;
+            c.row0 = -1;
+            c.ncols = L.cout;
+            for (int tap = 0; tap < 9; ++tap)
+                for (int src = 0; src < 2; ++src) {
+                    const int cs = src == 0 ? c.c1 : c.c2;
+                    for (int ch = 0; ch < cs / 8; ++ch) c.halves.push_back(Half{tap, src, ch});
+                }
+        } else {
+            c.c1 = L.cin;
+            c.c2 = 0;
+            c.rows = 1;
+            c.row0 = 0;
+            c.ncols = 4 * L.cout;
+            // the one "tap" reads row 0 of the halo at pixel offset +1 (tap index 1)
+            for (int ch = 0; ch < L.cin / 8; ++ch) c.halves.push_back(Half{1, 0, ch});
+        }
         if (c.halves.size() % 2) c.halves.push_back(Half{-1, 0, 0});
         c.nks = (int)c.halves.size() / 2;
         if (c.nks > MAX_KS) continue;
         // widest output slice whose weights fit in 80 KB
-        int ns = L.cout;
+        int ns = c.ncols;
         while (ns > 16 && (size_t)c.nks * 2 * ns * 16 > 80 * 1024) ns /= 2;
         c.n_slice = ns;
-        c.nslices = L.cout / ns;
+        c.nslices = c.ncols / ns;
         c.w_bytes = (uint32_t)c.nks * 2 * ns * 16;
         c.w_off = off;
         off += ((size_t)c.w_bytes * c.nslices + 1023) / 1024 * 1024;
@@ -457,8 +502,9 @@ nrv_status tc_repack(Net* net, cudaStream_t s) {
         if (!c.ok) continue;
         const Layer& L = net->layers[l];
         pack_tc_weights_kernel<<<64, 256, 0, s>>>(
-            (const float*)net->params.p, L.woff, L.cin, L.cout, c.n_slice, c.nslices, c.nks,
-            (const int4*)g_halves.p + hoff[l], c.c1, (uint16_t*)((char*)net->wbf16.p + c.w_off));
+            (const float*)net->params.p, L.woff, c.kind, L.cin, L.cout, c.n_slice, c.nslices,
+            c.nks, (const int4*)g_halves.p + hoff[l], c.c1,
+            (uint16_t*)((char*)net->wbf16.p + c.w_off));
         NRV_CHECK_LAUNCH();
     }
     // the host copy of the halves must stay valid until the copy ran
@@ -466,35 +512,41 @@ nrv_status tc_repack(Net* net, cudaStream_t s) {
     return NRV_OK;
 }
 
+// Launch one tensor-core layer on a level of geometry (n, H, W): a 3x3 conv
+// writes [n][H][W][C_out]; a transposed conv reads level (H, W) and writes
+// [n][2H][2W][C_out].
 static int g_num_sms = 0;
 
-nrv_status tc_conv3(const Net* net, int l, const void* x1, int c1, const void* x2, int c2, void* y,
-                    const Geo& g, int level, nrv_prec prec, cudaStream_t s) {
-    if (prec != NRV_PREC_BF16) return fail(NRV_ERR_UNSUPPORTED, "tensor-core path is BF16");
+static nrv_status tc_launch(const Net* net, int l, const void* x1, int c1, const void* x2, int c2,
+                            void* y, int n, int H, int W, cudaStream_t s) {
     const TcLayerCfg& c = g_cfg[l];
     if (!c.ok || c.c1 != c1 || c.c2 != c2) return fail(NRV_ERR_UNSUPPORTED, "layer not configured");
     const Layer& L = net->layers[l];
-    const int H = g.h[level], W = g.w[level];
     TcParams P;
     memset(&P, 0, sizeof(P));
-    P.n = g.n;
+    P.n = n;
     P.h = H;
     P.w = W;
     P.tiles_x = (W + TILE_M - 1) / TILE_M;
-    P.num_ptiles = P.tiles_x * H * g.n;
+    P.num_ptiles = P.tiles_x * H * n;
     P.nslices = c.nslices;
     P.n_slice = c.n_slice;
     P.nks = c.nks;
     P.cout = L.cout;
+    P.mode = c.kind == CONV3 ? 0 : 1;
+    P.row0 = c.row0;
     P.has_src2 = c.c2 > 0;
     const uint32_t nch1 = c.c1 / 8, nch2 = c.c2 / 8;
-    P.tx1 = 3 * nch1 * PLANE;
-    P.tx2 = 3 * nch2 * PLANE;
+    P.tx1 = c.rows * nch1 * PLANE;
+    P.tx2 = c.rows * nch2 * PLANE;
     P.src2_off = (P.tx1 + 127) / 128 * 128;   // TMA destinations are 128-byte aligned
     P.halo_bytes = (P.src2_off + P.tx2 + 127) / 128 * 128;
     P.w_bytes = c.w_bytes;
     P.w_region = (c.w_bytes + 1023) / 1024 * 1024;
-    P.nbuf = (P.w_region + 2 * P.halo_bytes <= 200 * 1024) ? 2 : 1;
+    // halo stages: as many as fit (up to 4) while the CTA stays under ~110 KB, at least 1
+    int nbuf = 4;
+    while (nbuf > 1 && P.w_region + nbuf * P.halo_bytes > 110 * 1024) --nbuf;
+    P.nbuf = nbuf;
     const uint32_t smem = P.w_region + P.nbuf * P.halo_bytes;
     if (smem > 220 * 1024) return fail(NRV_ERR_UNSUPPORTED, "tile does not fit in shared memory");
     P.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(c.n_slice >> 3) << 17) |
@@ -513,8 +565,8 @@ nrv_status tc_conv3(const Net* net, int l, const void* x1, int c1, const void* x
         auto off = [&](const Half& h) -> uint32_t {
             const uint32_t base = h.src == 0 ? 0u : P.src2_off;
             const uint32_t nch = h.src == 0 ? nch1 : nch2;
-            return base + ((uint32_t)(h.tap / 3) * nch + (uint32_t)h.chunk) * PLANE +
-                   (uint32_t)(h.tap % 3) * 16;
+            const uint32_t row = c.kind == CONV3 ? (uint32_t)(h.tap / 3) : 0u;
+            return base + (row * nch + (uint32_t)h.chunk) * PLANE + (uint32_t)(h.tap % 3) * 16;
         };
         P.a_off[ks] = off(h0);
         const uint32_t o1 = h1.tap < 0 ? P.a_off[ks] : off(h1);
@@ -525,8 +577,8 @@ nrv_status tc_conv3(const Net* net, int l, const void* x1, int c1, const void* x
             return fail(NRV_ERR_UNSUPPORTED, "A operand outside the halo buffer");
     }
     CUtensorMap m1, m2;
-    NRV_TRY(make_halo_map(&m1, x1, g.n, H, W, c.c1));
-    if (P.has_src2) NRV_TRY(make_halo_map(&m2, x2, g.n, H, W, c.c2));
+    NRV_TRY(make_halo_map(&m1, x1, n, H, W, c.c1, c.rows));
+    if (P.has_src2) NRV_TRY(make_halo_map(&m2, x2, n, H, W, c.c2, c.rows));
     else m2 = m1;
     if (!g_num_sms) {
         int dev = 0;
@@ -534,13 +586,15 @@ nrv_status tc_conv3(const Net* net, int l, const void* x1, int c1, const void* x
         cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
         if (g_num_sms <= 0) g_num_sms = 148;
     }
-    static uint32_t attr_smem = 0;
-    if (smem > attr_smem) {
+    static bool attr_set = false;
+    if (!attr_set) {
         NRV_CHECK_CUDA(cudaFuncSetAttribute(conv3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             220 * 1024));
-        attr_smem = 220 * 1024;
+        attr_set = true;
     }
-    int occ = (int)((227 * 1024) / (smem + 2048));
+    // resident CTAs per SM: registers, threads, shared memory, and TMEM columns
+    int occ = 1;
+    NRV_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv3_tc_kernel, NTHREADS, smem));
     if (occ < 1) occ = 1;
     if (occ * (int)cols > 512) occ = 512 / (int)cols;
     int per_slice = (g_num_sms * occ) / c.nslices;
@@ -549,6 +603,21 @@ nrv_status tc_conv3(const Net* net, int l, const void* x1, int c1, const void* x
     conv3_tc_kernel<<<per_slice * c.nslices, NTHREADS, smem, s>>>(m1, m2, P);
     NRV_CHECK_LAUNCH();
     return NRV_OK;
+}
+
+nrv_status tc_conv3(const Net* net, int l, const void* x1, int c1, const void* x2, int c2, void* y,
+                    const Geo& g, int level, nrv_prec prec, cudaStream_t s) {
+    if (prec != NRV_PREC_BF16) return fail(NRV_ERR_UNSUPPORTED, "tensor-core path is BF16");
+    if (net->layers[l].kind != CONV3) return fail(NRV_ERR_UNSUPPORTED, "not a 3x3 conv");
+    return tc_launch(net, l, x1, c1, x2, c2, y, g.n, g.h[level], g.w[level], s);
+}
+
+nrv_status tc_upconv(const Net* net, int l, const void* x, void* y, const Geo& g, int level_in,
+                     nrv_prec prec, cudaStream_t s) {
+    if (prec != NRV_PREC_BF16) return fail(NRV_ERR_UNSUPPORTED, "tensor-core path is BF16");
+    if (net->layers[l].kind != UPCONV2) return fail(NRV_ERR_UNSUPPORTED, "not a transposed conv");
+    return tc_launch(net, l, x, net->layers[l].cin, nullptr, 0, y, g.n, g.h[level_in],
+                     g.w[level_in], s);
 }
 
 }  // namespace nrv

@@ -72,7 +72,7 @@ SIGNATURES = {
     "nrv_net_set_act_scales": (I, [P, ctypes.POINTER(F), I]),
     "nrv_shade": (I, [P, P, I, I, I, I, P, P]),
     "nrv_net_layer_backend": (I, [P, I]),
-    "nrv_net_conv3": (I, [P, I, P, P, I, I, I, I, P, P]),
+    "nrv_net_run_layer": (I, [P, I, P, P, I, I, I, I, P, P]),
     "nrv_net_forward_train": (I, [P, P, I, I, I, I, P, P]),
     "nrv_net_backward": (I, [P, P, P, P]),
     "nrv_l1_loss": (I, [P, P, I64, P, P, P]),
