@@ -241,6 +241,27 @@ nrv_status nrv_net_backward(nrv_net* net, const float* d_drgb, float* d_grad, nr
 nrv_status nrv_l1_loss(const float* d_y, const float* d_t, int64_t n, float* d_loss, float* d_dy,
                        nrv_stream stream);
 
+/* Same loss as nrv_l1_loss for callers that cannot allocate device memory: an
+ * application whose memory pool owns the whole device, a real-time frame loop
+ * that must not stall on the implicit device synchronisation of cudaMalloc and
+ * cudaFree, or a plug-in that is handed its buffers and nothing else.  It
+ * allocates nothing; its scratch (one partial sum per 8192 elements) is a fixed
+ * 64 KiB array in the library's device memory, kept on every device that loads
+ * the library until the process exits.  The paper has no counterpart of this
+ * entry point.
+ *  - n may be at most NRV_L1_NOALLOC_MAX_ELEMENTS; larger n returns NRV_ERR_ARG
+ *    with a message and launches nothing (use nrv_l1_loss then).
+ *  - The first call on a device looks up the array's device address; make that
+ *    first call before any stream capture on that device.
+ *  - All calls share the array.  Each call overwrites every slot it reads, so
+ *    nothing has to be cleared between calls, but calls whose kernels overlap on
+ *    the GPU (different streams without ordering) race on it.
+ * Results agree with nrv_l1_loss to FP32 rounding (the partial sums differ in
+ * grouping); d_dy is identical. */
+#define NRV_L1_NOALLOC_MAX_ELEMENTS 134217728LL
+nrv_status nrv_l1_loss_noalloc(const float* d_y, const float* d_t, int64_t n, float* d_loss,
+                               float* d_dy, nrv_stream stream);
+
 /* Adam (Kingma & Ba; Sec. 3.3 uses it with lr 1e-3), no weight decay, step >= 1:
  * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
  * p -= lr * (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps), all FP32. */

@@ -76,6 +76,7 @@ SIGNATURES = {
     "nrv_net_forward_train": (I, [P, P, I, I, I, I, P, P]),
     "nrv_net_backward": (I, [P, P, P, P]),
     "nrv_l1_loss": (I, [P, P, I64, P, P, P]),
+    "nrv_l1_loss_noalloc": (I, [P, P, I64, P, P, P]),
     "nrv_adam_step": (I, [P, P, P, P, I64, I, F, F, F, F, P]),
     "nrv_train_step": (I, [P, P, P, P, P, I, F, P, P, I, I, I, I, P, P]),
     "nrv_render_batch": (I, [P, P, ctypes.POINTER(nrv_pack_desc), ctypes.POINTER(nrv_view), I,
