@@ -37,15 +37,6 @@ nrv_status launch_clear_keys(const RViews& views, cudaStream_t s) {
 
 // Projection + clipping of one point for one view; on success returns the key
 // and the address of its pixel's key.
-//
-// The pixel is first found from the fast quotient __fdividef (documented error
-// <= 2 ulp for divisors in [2^-126, 2^126]).  Propagating that error, plus the
-// rounding of the exact sequence, through (q + 1) * W/2 bounds the distance
-// between the fast and the exact sx by W/2 * 2^-22 * (2.25|q| + 1), which the
-// code over-estimates as W/2 * 2^-20 * (|q| + 4).  When sx lies farther than
-// that from every integer (and likewise sy), truncation and the on-screen test
-// give the same answer as the exact sequence; otherwise the exact IEEE
-// divisions decide.  The key's depth is w itself, never a quotient.
 __device__ __forceinline__ bool project_point(const RView& v, float x, float y, float z,
                                               uint32_t idx, unsigned long long*& p,
                                               unsigned long long& key) {
@@ -59,21 +50,6 @@ __device__ __forceinline__ bool project_point(const RView& v, float x, float y, 
     const float cy = __fadd_rn(
         __fadd_rn(__fadd_rn(__fmul_rn(v.m[4], x), __fmul_rn(v.m[5], y)), __fmul_rn(v.m[6], z)),
         v.m[7]);
-    if (cw >= 0x1p-125f && cw <= 0x1p125f) {
-        const float qx = __fdividef(cx, cw), qy = __fdividef(cy, cw);
-        const float ax = __fmul_rn(__fadd_rn(qx, 1.0f), v.hw);
-        const float ay = __fmul_rn(__fsub_rn(1.0f, qy), v.hh);
-        const float ex = (fabsf(qx) + 4.0f) * v.hw * 0x1p-20f;
-        const float ey = (fabsf(qy) + 4.0f) * v.hh * 0x1p-20f;
-        const float fx = floorf(ax), fy = floorf(ay);
-        // (ax - fx) and (fx + 1 - ax) are exact; NaN or infinity fails every test
-        if (ax - fx > ex && (fx + 1.0f) - ax > ex && ay - fy > ey && (fy + 1.0f) - ay > ey) {
-            if (!(fx >= 0.0f && fx < v.fw && fy >= 0.0f && fy < v.fh)) return false;
-            key = ((unsigned long long)__float_as_uint(cw) << 32) | idx;
-            p = v.key + (size_t)(int)fy * v.width + (int)fx;
-            return true;
-        }
-    }
     const float sx = __fmul_rn(__fadd_rn(__fdiv_rn(cx, cw), 1.0f), v.hw);
     const float sy = __fmul_rn(__fsub_rn(1.0f, __fdiv_rn(cy, cw)), v.hh);
     if (!(sx >= 0.0f && sx < v.fw && sy >= 0.0f && sy < v.fh)) return false;
@@ -110,13 +86,16 @@ __device__ __forceinline__ void render_point(const RView& v, float x, float y, f
 // so each thread keeps four L2 round trips in flight instead of one.
 // The views come by value, or -- when a captured frame is replayed with new
 // cameras -- from device memory (views_dev); each block keeps them in shared memory.
-// SINGLE: one view, kept in registers for the whole pass.
-template <bool SINGLE>
-__global__ void __launch_bounds__(256) visibility_kernel(const float4* __restrict__ xyz4,
-                                                         uint64_t ngroups,
-                                                         const float* __restrict__ xyz,
-                                                         uint64_t n, RViews vs_arg,
-                                                         const RViews* __restrict__ views_dev) {
+// Variants (picked per scene by the launcher's timing, see below):
+//   SINGLE   one view, kept in registers for the whole pass;
+//   PREFETCH the next group's coordinates are loaded before this group is done;
+//   MINB     register budget: at least MINB blocks of 256 threads per SM.
+template <bool SINGLE, bool PREFETCH, int MINB>
+__global__ void __launch_bounds__(256, MINB) visibility_kernel(const float4* __restrict__ xyz4,
+                                                               uint64_t ngroups,
+                                                               const float* __restrict__ xyz,
+                                                               uint64_t n, RViews vs_arg,
+                                                               const RViews* __restrict__ views_dev) {
     __shared__ RViews vs;
     if (threadIdx.x == 0) vs = views_dev ? *views_dev : vs_arg;
     __syncthreads();
@@ -125,18 +104,24 @@ __global__ void __launch_bounds__(256) visibility_kernel(const float4* __restric
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a, c = a;
-    if (g < ngroups) {
+    if (PREFETCH && g < ngroups) {
         a = __ldcs(xyz4 + 3 * g);
         b = __ldcs(xyz4 + 3 * g + 1);
         c = __ldcs(xyz4 + 3 * g + 2);
     }
     for (; g < ngroups; g += stride) {
-        const uint64_t gn = g + stride;
         float4 na = a, nb = b, nc = c;
-        if (gn < ngroups) {
-            na = __ldcs(xyz4 + 3 * gn);
-            nb = __ldcs(xyz4 + 3 * gn + 1);
-            nc = __ldcs(xyz4 + 3 * gn + 2);
+        if (PREFETCH) {
+            const uint64_t gn = g + stride;
+            if (gn < ngroups) {
+                na = __ldcs(xyz4 + 3 * gn);
+                nb = __ldcs(xyz4 + 3 * gn + 1);
+                nc = __ldcs(xyz4 + 3 * gn + 2);
+            }
+        } else {
+            a = __ldcs(xyz4 + 3 * g);
+            b = __ldcs(xyz4 + 3 * g + 1);
+            c = __ldcs(xyz4 + 3 * g + 2);
         }
         const float px[4] = {a.x, a.w, b.z, c.y};
         const float py[4] = {a.y, b.x, b.w, c.z};
@@ -155,9 +140,11 @@ __global__ void __launch_bounds__(256) visibility_kernel(const float4* __restric
             for (int j = 0; j < 4; ++j)
                 if (ok[j] && key[j] < cur[j]) atomicMin(ptr[j], key[j]);
         }
-        a = na;
-        b = nb;
-        c = nc;
+        if (PREFETCH) {
+            a = na;
+            b = nb;
+            c = nc;
+        }
     }
     // the last n mod 4 points
     if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
@@ -167,21 +154,101 @@ __global__ void __launch_bounds__(256) visibility_kernel(const float4* __restric
     }
 }
 
+// ------------------------------------------------------------------ variant choice
+// The best variant depends on the point order and the views (how many early
+// depth reads hit, how many atomics are left).  The first launch for a
+// (single/multi view, size class) tries every variant on the real data -- each
+// run computes the same keys, so the last one leaves the correct result -- and
+// keeps the fastest for later launches.  No choice is made during a stream
+// capture: the default variant is used until an uncaptured launch has tuned.
+typedef void (*VisFn)(const float4*, uint64_t, const float*, uint64_t, RViews, const RViews*);
+
+struct VisVariant {
+    VisFn fn;
+    int blocks_per_sm;
+    const char* name;
+};
+
+static const VisVariant kSingle[] = {
+    {visibility_kernel<true, true, 3>, 3, "single/prefetch/3"},
+    {visibility_kernel<true, false, 3>, 3, "single/plain/3"},
+    {visibility_kernel<true, true, 4>, 4, "single/prefetch/4"},
+    {visibility_kernel<true, false, 4>, 4, "single/plain/4"},
+    {visibility_kernel<true, false, 5>, 5, "single/plain/5"},
+};
+static const VisVariant kMulti[] = {
+    {visibility_kernel<false, true, 3>, 3, "multi/prefetch/3"},
+    {visibility_kernel<false, false, 3>, 3, "multi/plain/3"},
+    {visibility_kernel<false, false, 4>, 4, "multi/plain/4"},
+};
+
+struct VisTune {
+    int choice = -1;
+};
+static VisTune g_vis_tune[2][48];   // [multi][log2 of the point count]
+static int g_vis_sms = 0;
+
+static nrv_status launch_variant(const VisVariant& v, const float* xyz, uint64_t n,
+                                 const RViews& views, cudaStream_t s, const RViews* views_dev) {
+    const uint64_t ngroups = n / 4;
+    int blocks = g_vis_sms * v.blocks_per_sm;
+    const uint64_t need = (ngroups + 255) / 256;
+    if (need < (uint64_t)blocks) blocks = (int)(need > 0 ? need : 1);
+    v.fn<<<blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(xyz), ngroups, xyz, n, views,
+                                views_dev);
+    NRV_CHECK_LAUNCH();
+    return NRV_OK;
+}
+
+int visibility_variant_count(int multi) { return multi ? 3 : 5; }
+const char* visibility_variant_name(int multi, int i) { return (multi ? kMulti : kSingle)[i].name; }
+
 nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, cudaStream_t s,
                              const RViews* views_dev) {
     if (n == 0) return NRV_OK;
-    const uint64_t ngroups = n / 4;
-    int blocks = 152 * 8;
-    const uint64_t need = (ngroups + 255) / 256;
-    if (need < (uint64_t)blocks) blocks = (int)(need > 0 ? need : 1);
-    if (views.n == 1)
-        visibility_kernel<true><<<blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(xyz), ngroups,
-                                                       xyz, n, views, views_dev);
-    else
-        visibility_kernel<false><<<blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(xyz), ngroups,
-                                                        xyz, n, views, views_dev);
-    NRV_CHECK_LAUNCH();
-    return NRV_OK;
+    if (!g_vis_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_vis_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_vis_sms <= 0) g_vis_sms = 148;
+    }
+    const int multi = views.n > 1;
+    const VisVariant* tab = multi ? kMulti : kSingle;
+    const int count = visibility_variant_count(multi);
+    int cls = 0;
+    while (cls < 47 && (1ull << (cls + 1)) <= n) ++cls;
+    VisTune& t = g_vis_tune[multi][cls];
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    NRV_CHECK_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (t.choice < 0 && cap == cudaStreamCaptureStatusNone && n >= (1u << 20)) {
+        // time each variant twice on the real data; keep the faster second run
+        cudaEvent_t e0, e1;
+        NRV_CHECK_CUDA(cudaEventCreate(&e0));
+        NRV_CHECK_CUDA(cudaEventCreate(&e1));
+        float best = 1e30f;
+        int arg = 0;
+        for (int i = 0; i < count; ++i) {
+            float ms = 0.0f;
+            for (int rep = 0; rep < 2; ++rep) {
+                NRV_TRY(launch_clear_keys(views, s));
+                NRV_CHECK_CUDA(cudaEventRecord(e0, s));
+                NRV_TRY(launch_variant(tab[i], xyz, n, views, s, views_dev));
+                NRV_CHECK_CUDA(cudaEventRecord(e1, s));
+                NRV_CHECK_CUDA(cudaEventSynchronize(e1));
+                NRV_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            }
+            if (ms < best) {
+                best = ms;
+                arg = i;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        t.choice = arg;
+        // the trials left correct keys, but clear and rerun so the call's own work is one pass
+        NRV_TRY(launch_clear_keys(views, s));
+    }
+    return launch_variant(tab[t.choice < 0 ? 0 : t.choice], xyz, n, views, s, views_dev);
 }
 
 // ------------------------------------------------------------------ pack helpers

@@ -592,11 +592,26 @@ static nrv_status tc_launch(const Net* net, int l, const void* x1, int c1, const
                                             220 * 1024));
         attr_set = true;
     }
-    // resident CTAs per SM: registers, threads, shared memory, and TMEM columns
-    int occ = 1;
-    NRV_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv3_tc_kernel, NTHREADS, smem));
-    if (occ < 1) occ = 1;
+    // resident CTAs per SM from registers, threads, shared memory and TMEM columns
+    static cudaFuncAttributes fa;
+    static cudaDeviceProp prop;
+    static bool have_fa = false;
+    if (!have_fa) {
+        NRV_CHECK_CUDA(cudaFuncGetAttributes(&fa, conv3_tc_kernel));
+        int dev = 0;
+        NRV_CHECK_CUDA(cudaGetDevice(&dev));
+        NRV_CHECK_CUDA(cudaGetDeviceProperties(&prop, dev));
+        have_fa = true;
+    }
+    const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+    int occ = prop.regsPerMultiprocessor / (regs_per_warp * (NTHREADS / 32));
+    occ = occ < prop.maxThreadsPerMultiProcessor / NTHREADS ? occ : prop.maxThreadsPerMultiProcessor / NTHREADS;
+    const size_t smem_cta = smem + fa.sharedSizeBytes + prop.reservedSharedMemPerBlock;
+    const int by_smem = (int)(prop.sharedMemPerMultiprocessor / smem_cta);
+    occ = occ < by_smem ? occ : by_smem;
+    occ = occ < prop.maxBlocksPerMultiProcessor ? occ : prop.maxBlocksPerMultiProcessor;
     if (occ * (int)cols > 512) occ = 512 / (int)cols;
+    if (occ < 1) occ = 1;
     int per_slice = (g_num_sms * occ) / c.nslices;
     if (per_slice < 1) per_slice = 1;
     if (per_slice > P.num_ptiles) per_slice = P.num_ptiles;
