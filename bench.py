@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-fp8", action="store_true")
     return ap.parse_args()
 
 
@@ -145,27 +146,57 @@ def oracle_frame(sc, view, ds, do, max_seconds=None):
     return t2 - t0, y[:view.height, :view.width], t1 - t0
 
 
+RASTER_SAMPLE = 32      # the reference arm renders 1/32 of the points per step
+BAND_ROWS = 64          # ... and runs the network on a 64-row band of the frame
+
+
+def oracle_sample(sc, view, ds, do, step):
+    """One bounded sample of a frame on the CPU oracle: render + resolve + pack of a contiguous
+    1/RASTER_SAMPLE of the points (C, one thread) and the FP64 U-Net on a BAND_ROWS-row band of
+    the packed frame (numpy, BLAS threads).  Returns the whole-frame time it extrapolates to."""
+    import numpy as np
+    import oracle
+    from oracle import unet
+    c0 = len(sc.channels) + 2
+    n = sc.n // RASTER_SAMPLE
+    lo = (step % RASTER_SAMPLE) * n
+    part = sc.subset(np.arange(lo, lo + n))
+    t0 = time.perf_counter()
+    key, d, m, g = oracle.rasterize(part, view)
+    hn, wn = (view.height + 7) // 8 * 8, (view.width + 7) // 8 * 8
+    x = oracle.pack(d, m, g, sc.channels, ds, do, hn, wn, 8, 0)
+    t1 = time.perf_counter()
+    r0 = (step * BAND_ROWS) % (hn - BAND_ROWS + 1) // 8 * 8
+    unet.forward(x[None, r0:r0 + BAND_ROWS, :, :c0].astype(np.float64),
+                 unet.unflatten(unet_params(c0), c0))
+    t2 = time.perf_counter()
+    return (t1 - t0) * RASTER_SAMPLE + (t2 - t1) * hn / BAND_ROWS
+
+
 def run_reference(a, rank, world):
-    """Reference arm: the CPU oracle on the host cores, same workload and metric."""
+    """Reference arm: the CPU oracle on the host cores, same workload and metric, each step a
+    bounded sample of the frame extrapolated to the whole frame."""
     if rank != 0:
         return
     sc, view, ds, do, gen_s = make_workload(a)
     times = []
     for i in range(a.warmup + a.steps):
-        t, _, _ = oracle_frame(sc, view, ds, do)
+        t = oracle_sample(sc, view, ds, do, i)
         if i >= a.warmup:
             times.append(t)
     sec = sum(times) / len(times)
     v = sc.n / sec
     ncpu = os.cpu_count()
+    sample = (f"per step: render+resolve+pack of 1/{RASTER_SAMPLE} of the points in C on one "
+              f"thread, FP64 U-Net on a {BAND_ROWS}-row band in numpy on all BLAS threads, "
+              "scaled to a whole frame")
     line = {"impl": "reference", "metric": "points/s (frames/s) at 1080p", "value": v,
             "unit": "points/s", "n_gpus": 0, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": sec * 1e3, "fps": 1.0 / sec, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 raster / f64 net",
             "data": "synthetic", "config": {"workload": workload_name(a)},
             "cpu_baseline": {"value": v, "unit": "points/s", "cores": ncpu, "kind": "oracle",
-                             "sample": "whole frames of the workload (render+resolve+pack in C on "
-                                       "one thread, FP64 U-Net in numpy on all BLAS threads)"},
+                             "sample": sample},
             "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -210,28 +241,30 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
-    def timed(prec_, steps, warmup, profile):
+    def timed(prec_, steps, warmup, profile, inv=1.0):
         for _ in range(warmup):
-            nrv.render_batch(scene, net, desc, [view], [rgb], prec_)
+            nrv.render_batch(scene, net, desc, [view], [rgb], prec_, inv)
         torch.cuda.synchronize()
         nrv.timings()
         nrv.set_profiling(profile)
         barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0 = nrv.lib().nrv_launch_count()
         e0.record(stream)
         for _ in range(steps):
-            nrv.render_batch(scene, net, desc, [view], [rgb], prec_)
+            nrv.render_batch(scene, net, desc, [view], [rgb], prec_, inv)
         e1.record(stream)
         torch.cuda.synchronize()
+        launches = nrv.lib().nrv_launch_count() - n0
         barrier()
         nrv.set_profiling(False)
         stages = nrv.timings() if profile else None
-        return e0.elapsed_time(e1) / steps, stages
+        return e0.elapsed_time(e1) / steps, stages, launches
 
     sampler = ClockSampler(local)
     sampler.start()
-    ms, stages = timed(prec, a.steps, a.warmup, True)
+    ms, stages, launches = timed(prec, a.steps, a.warmup, True)
     clocks = sampler.stop()
     if world > 1:
         t = torch.tensor([ms], device=dev)
@@ -257,7 +290,25 @@ def main():
     # the FP32 form of the same pipeline, for comparison
     fp32_ms = None
     if not a.no_fp32 and prec != nrv.PREC_F32:
-        fp32_ms, _ = timed(nrv.PREC_F32, max(3, a.steps // 10), 2, False)
+        fp32_ms, _, _ = timed(nrv.PREC_F32, max(3, a.steps // 10), 2, False)
+
+    # the FP8 network, calibrated on this frame's BF16 input
+    fp8_ms, fp8_rgb = None, None
+    if not a.no_fp8:
+        key = torch.empty((H, W), dtype=torch.int64, device=dev)
+        dpl = torch.empty((H, W), dtype=torch.int32, device=dev)
+        msk = torch.empty((H, W), dtype=torch.uint8, device=dev)
+        gat = torch.empty((sc.n_words, H, W), dtype=torch.int32, device=dev)
+        nrv.rasterize(scene, [view], [key], [dpl], [msk], [gat])
+        xb = torch.empty(((H + 7) // 8 * 8, (W + 7) // 8 * 8, 8), dtype=torch.bfloat16, device=dev)
+        nrv.pack(dpl, msk, gat, H, W, desc, nrv.PREC_BF16, xb)
+        net.calibrate(xb, 1, H, W)
+        inv8 = 1.0 / net.act_scales()[0]
+        del key, dpl, msk, gat, xb
+        fp8_ms, _, _ = timed(nrv.PREC_FP8, max(5, a.steps // 5), 3, False, inv8)
+        nrv.render_batch(scene, net, desc, [view], [rgb], nrv.PREC_FP8, inv8)
+        torch.cuda.synchronize()
+        fp8_rgb = rgb.float().cpu().numpy().astype(np.float64)
 
     # roofline of the render (visibility) pass: 12 algorithmic bytes per point
     clear_ms, vis_ms, res_ms, net_ms = stages
@@ -284,11 +335,12 @@ def main():
                                  "unit": "TFLOP/s", "frac": net_tf / pk,
                                  "flops_per_frame": flops},
             "fp32_ms_per_step": fp32_ms,
+            "fp8_ms_per_step": fp8_ms,
             "e2e": {"value": world * sc.n / e2e_s, "unit": "points/s",
                     "h2d_bytes_per_step": 80, "d2h_bytes_per_step": H * W * 3 * 4},
             "clocks": clocks, "scene_gen_s": gen_s}
-    # launches per step: clear + visibility + resolve + network kernels
-    line["gpu_launches"] = a.steps * (3 + 24)
+    # library kernels launched inside the timed region (counted by the library)
+    line["gpu_launches"] = int(launches)
 
     if rank == 0 and not a.no_cpu_baseline:
         nrv.render_batch(scene, net, desc, [view], [rgb], prec)
@@ -304,6 +356,10 @@ def main():
                                           f"threads ({t_cpu - t_ras:.1f} s)"}
         line["quality_vs_fp64"] = {"psnr_db": 10 * np.log10(r * r / mse) if mse > 0 else None,
                                    "max_abs": float(np.abs(got - y_ref).max())}
+        if fp8_rgb is not None:
+            mse8 = float(np.mean((fp8_rgb - y_ref) ** 2))
+            line["quality_fp8_vs_fp64"] = {"psnr_db": 10 * np.log10(r * r / mse8) if mse8 > 0 else None,
+                                           "max_abs": float(np.abs(fp8_rgb - y_ref).max())}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -69,6 +69,11 @@ const char* nrv_last_error(void);
 /* ABI version, currently 1. */
 int nrv_version(void);
 
+/* Number of kernels the library has launched in this process so far (all
+ * devices, all threads).  Replays of captured frames count the kernels they
+ * contain.  For benchmarking. */
+uint64_t nrv_launch_count(void);
+
 /* --------------------------------------------------------------------------
  * Scene (the point cloud of Sec. 3.2; memory N * sum(B_i) bytes, Sec. 4.5)
  * ------------------------------------------------------------------------ */
@@ -194,10 +199,25 @@ nrv_status nrv_destroy_net(nrv_net* net);
  * again after the parameters change.  Errors: NRV_ERR_ARG. */
 nrv_status nrv_net_set_params(nrv_net* net, const float* d_params, nrv_stream stream);
 
-/* FP8 activation scales: act_scale[l] is the per-tensor scale of the input of
- * 3x3/transposed/head layer l (18 host floats; value = amax/448 from
- * calibration).  act_scale[0] must equal the input scale used by nrv_pack. */
-nrv_status nrv_net_set_act_scales(nrv_net* net, const float* act_scale, int n);
+/* FP8 (E4M3) network: every tensor the network stores holds E4M3 codes q with
+ * value q * scale, one scale per tensor; weights hold E4M3 codes per output
+ * column with scale max|column| / 448 (App. B quantises to fp16; this goes to
+ * 8 bits).  The 21 tensor scales, in this order: the network input, then
+ * e0a e0b p0 e1a e1b p1 e2a e2b p2 e3a e3b up3 d2a d2b up2 d1a d1b up1 d0a d0b
+ * (the outputs of those layers; p0..p2 the pooled tensors, which must carry the
+ * scale of the tensor they pool).  The input is packed by nrv_pack / passed to
+ * nrv_render_batch with in_scale_inv = 1 / scale[0].
+ *
+ * nrv_net_calibrate runs a BF16 forward on n sample inputs (BF16 NHWC, as for
+ * nrv_shade), sets every scale to max|tensor| / 448 and packs the FP8 weights.
+ * It synchronises the stream.  nrv_net_set_act_scales sets the scales directly
+ * (positive, finite) and packs the weights; nrv_net_get_act_scales reads them.
+ * Both packers need parameters loaded (NRV_ERR_STATE otherwise) and are rerun
+ * by nrv_net_set_params once scales exist. */
+nrv_status nrv_net_calibrate(nrv_net* net, const void* d_netin_bf16, int n, int height, int width,
+                             nrv_stream stream);
+nrv_status nrv_net_set_act_scales(nrv_net* net, const float* scale, int n, nrv_stream stream);
+nrv_status nrv_net_get_act_scales(const nrv_net* net, float* scale, int n);
 
 /* Forward pass (inference) on n images: d_netin is n packed inputs
  * [n][Hn][Wn][C] in the dtype of prec (nrv_netin_channels), d_rgb receives

@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <map>
 #include <vector>
 
@@ -23,6 +24,9 @@ nrv_status fail(nrv_status s, const char* fmt, ...) {
 }
 
 void clear_error() { g_err[0] = 0; }
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 static unsigned* g_status = nullptr;
 
@@ -46,6 +50,7 @@ using namespace nrv;
 
 struct nrv_scene {
     nrv_scene_desc d;
+    DevBuf tiles;   // per-tile depth bounds of the render pass (nrv_rasterize)
 };
 
 // A captured whole frame (nrv_render_batch) and the device copy of the cameras it reads.
@@ -53,6 +58,7 @@ struct BatchGraph {
     std::vector<uint64_t> sig;
     cudaGraphExec_t exec = nullptr;
     RViews* views_dev = nullptr;
+    uint64_t kernels = 0;   // kernel nodes in the graph
 };
 
 struct nrv_net : Net {
@@ -70,6 +76,7 @@ struct nrv_net : Net {
 // --------------------------------------------------------------------- library
 extern "C" const char* nrv_last_error(void) { return g_err; }
 extern "C" int nrv_version(void) { return 1; }
+extern "C" uint64_t nrv_launch_count(void) { return g_launches.load(); }
 extern "C" int nrv_pad8(int v) { return (v + 7) / 8 * 8; }
 extern "C" int nrv_netin_channels(nrv_prec p) { return p == NRV_PREC_FP8 ? 16 : 8; }
 
@@ -164,8 +171,9 @@ static nrv_status raster_views(nrv_scene* s, const nrv_view* views, int n, uint6
     memset(&rv, 0, sizeof(rv));
     rv.n = n;
     for (int i = 0; i < n; ++i) rv.v[i] = make_rview(views[i], keys[i]);
+    NRV_TRY(s->tiles.ensure(visibility_scratch_bytes(rv)));
     NRV_TRY(launch_clear_keys(rv, st));
-    return launch_visibility(s->d.d_xyz, s->d.n_points, rv, st);
+    return launch_visibility(s->d.d_xyz, s->d.n_points, rv, st, nullptr, (uint32_t*)s->tiles.p);
 }
 
 extern "C" nrv_status nrv_rasterize(nrv_scene* s, const nrv_view* views, int n,
@@ -256,10 +264,8 @@ extern "C" nrv_status nrv_create_net(int c_in, nrv_net** out) {
     net->c_in = c_in;
     net->c0p = 8;
     net->n_params = net_layers(c_in, net->layers);
-    for (int l = 0; l < NUM_LAYERS; ++l) {
-        net->act_scale[l] = 1.0f;
-        net->backend[l] = -1;
-    }
+    for (int l = 0; l < NUM_LAYERS; ++l) net->backend[l] = -1;
+    for (int a = 0; a <= NUM_ACTS; ++a) net->act_scale[a] = 1.0f;
     *out = net;
     return NRV_OK;
 }
@@ -282,13 +288,38 @@ extern "C" nrv_status nrv_net_set_params(nrv_net* net, const float* d_params, nr
     return NRV_OK;
 }
 
-extern "C" nrv_status nrv_net_set_act_scales(nrv_net* net, const float* s, int n) {
+extern "C" nrv_status nrv_net_set_act_scales(nrv_net* net, const float* s, int n,
+                                             nrv_stream stream) {
     clear_error();
-    if (!net || !s || n != NUM_LAYERS) return fail(NRV_ERR_ARG, "need %d scales", NUM_LAYERS);
-    for (int l = 0; l < NUM_LAYERS; ++l) {
-        if (!(s[l] > 0.0f) || !isfinite(s[l])) return fail(NRV_ERR_ARG, "scale %d must be > 0", l);
-        net->act_scale[l] = s[l];
-    }
+    if (!net || !s || n != NUM_ACTS + 1) return fail(NRV_ERR_ARG, "need %d scales", NUM_ACTS + 1);
+    if (!net->has_params) return fail(NRV_ERR_STATE, "no parameters loaded");
+    for (int a = 0; a <= NUM_ACTS; ++a)
+        if (!(s[a] > 0.0f) || !isfinite(s[a])) return fail(NRV_ERR_ARG, "scale %d must be > 0", a);
+    for (int a = 0; a <= NUM_ACTS; ++a) net->act_scale[a] = s[a];
+    net->fp8_ready = false;
+    NRV_TRY(tc_repack_fp8(net, (cudaStream_t)stream));
+    net->fp8_ready = true;
+    return NRV_OK;
+}
+
+extern "C" nrv_status nrv_net_get_act_scales(const nrv_net* net, float* s, int n) {
+    clear_error();
+    if (!net || !s || n != NUM_ACTS + 1) return fail(NRV_ERR_ARG, "need %d scales", NUM_ACTS + 1);
+    for (int a = 0; a <= NUM_ACTS; ++a) s[a] = net->act_scale[a];
+    return NRV_OK;
+}
+
+extern "C" nrv_status nrv_net_calibrate(nrv_net* net, const void* d_netin, int n, int h, int w,
+                                        nrv_stream stream) {
+    clear_error();
+    if (!net || !d_netin) return fail(NRV_ERR_ARG, "null argument");
+    if (!net->has_params) return fail(NRV_ERR_STATE, "no parameters loaded");
+    if (n < 1 || h < 1 || w < 1 || h > 16384 || w > 16384) return fail(NRV_ERR_ARG, "bad size");
+    if (!aligned(d_netin, 32)) return fail(NRV_ERR_ARG, "d_netin must be 32-byte aligned");
+    NRV_TRY(net_calibrate(net, d_netin, n, h, w, (cudaStream_t)stream));
+    net->fp8_ready = false;
+    NRV_TRY(tc_repack_fp8(net, (cudaStream_t)stream));
+    net->fp8_ready = true;
     return NRV_OK;
 }
 
@@ -449,6 +480,14 @@ extern "C" nrv_status nrv_render_batch(nrv_scene* s, nrv_net* net, const nrv_pac
         in_off[i] = tot;
         tot += ((size_t)nrv_pad8(views[i].width) * nrv_pad8(views[i].height) * es + 1023) / 1024 * 1024;
     }
+    const size_t tiles_off = tot;
+    {
+        RViews tmp;
+        memset(&tmp, 0, sizeof(tmp));
+        tmp.n = n;
+        for (int i = 0; i < n; ++i) tmp.v[i] = make_rview(views[i], nullptr);
+        tot += (visibility_scratch_bytes(tmp) + 1023) / 1024 * 1024;
+    }
     NRV_TRY(net->batch_ws.ensure(tot));
     char* base = (char*)net->batch_ws.p;
     RViews rv;
@@ -485,7 +524,8 @@ extern "C" nrv_status nrv_render_batch(nrv_scene* s, nrv_net* net, const nrv_pac
         if (ev) prof_mark(*ev, q);
         NRV_TRY(launch_clear_keys(rv, q));
         if (ev) prof_mark(*ev, q);
-        NRV_TRY(launch_visibility(s->d.d_xyz, s->d.n_points, rv, q, views_dev));
+        NRV_TRY(launch_visibility(s->d.d_xyz, s->d.n_points, rv, q, views_dev,
+                                  (uint32_t*)(base + tiles_off)));
         if (ev) prof_mark(*ev, q);
         for (int i = 0; i < n; ++i) {
             ResolveArgs a;
@@ -520,6 +560,7 @@ extern "C" nrv_status nrv_render_batch(nrv_scene* s, nrv_net* net, const nrv_pac
         if (g.sig == sig) {
             NRV_CHECK_CUDA(cudaMemcpyAsync(g.views_dev, &rv, sizeof(RViews), cudaMemcpyHostToDevice, st));
             NRV_CHECK_CUDA(cudaGraphLaunch(g.exec, st));
+            g_launches.fetch_add(g.kernels);
             return NRV_OK;
         }
     // first frame of this signature: run it, then capture the same work for replay
@@ -539,8 +580,12 @@ extern "C" nrv_status nrv_render_batch(nrv_scene* s, nrv_net* net, const nrv_pac
     nrv_status fs = NRV_OK;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
+        const uint64_t before = g_launches.load();
         fs = frame(g.views_dev, nullptr, cap);
         e = cudaStreamEndCapture(cap, &graph);
+        // captured launches run only when the graph is replayed
+        g.kernels = g_launches.load() - before;
+        g_launches.fetch_sub(g.kernels);
     }
     if (e == cudaSuccess && fs == NRV_OK) e = cudaGraphInstantiate(&g.exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);

@@ -22,8 +22,12 @@ void clear_error();
             return ::nrv::fail(NRV_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
+// Kernels launched by the library so far (nrv_launch_count).
+void count_launch();
+
 #define NRV_CHECK_LAUNCH()                                                               \
     do {                                                                                 \
+        ::nrv::count_launch();                                                           \
         cudaError_t e_ = cudaGetLastError();                                             \
         if (e_ != cudaSuccess)                                                           \
             return ::nrv::fail(NRV_ERR_CUDA, "kernel launch at %s:%d failed: %s", __FILE__, \
@@ -74,8 +78,12 @@ struct ResolveArgs {
 };
 
 nrv_status launch_clear_keys(const RViews& views, cudaStream_t s);
+// Render pass.  `tiles` is scratch for the per-tile depth bounds of the culling
+// variant: visibility_scratch_bytes(views) bytes of device memory (may be null,
+// which disables culling).
+size_t visibility_scratch_bytes(const RViews& views);
 nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, cudaStream_t s,
-                             const RViews* views_dev = nullptr);
+                             const RViews* views_dev = nullptr, uint32_t* tiles = nullptr);
 nrv_status launch_resolve(const ResolveArgs& a, cudaStream_t s);
 nrv_status launch_pack_planes(const uint32_t* depth, const uint8_t* mask, const uint32_t* gattr,
                               const ResolveArgs& a, cudaStream_t s);

@@ -265,7 +265,7 @@ nrv_status net_forward(Net* net, const void* netin, int n, int H, int W, nrv_pre
         return forward_t<float>(net, (const float*)netin, rgb, s, false, prec);
     if (prec == NRV_PREC_BF16)
         return forward_t<__nv_bfloat16>(net, (const __nv_bfloat16*)netin, rgb, s, true, prec);
-    return fail(NRV_ERR_UNSUPPORTED, "FP8 network path is not available in this build");
+    return forward_fp8(net, (const uint8_t*)netin, rgb, s);
 }
 
 }  // namespace nrv
@@ -299,9 +299,15 @@ nrv_status net_run_layer(Net* net, int l, const void* x1, const void* x2, int n,
             return simt_upconv<float>(net, l, TView<const float>{(const float*)x1, L.cin},
                                       TView<float>{(float*)y, L.cout}, n, h, w, s);
         }
-        return fail(NRV_ERR_UNSUPPORTED, "nrv_net_run_layer runs in F32 or BF16");
+        if (prec == NRV_PREC_FP8) {
+            int in1, in2, out;
+            layer_scale_index(l, &in1, &in2, &out);
+            net->backend[l] = 1;
+            return tc_upconv(net, l, x1, y, g, 0, prec, s, 1.0f / net->act_scale[out]);
+        }
+        return fail(NRV_ERR_UNSUPPORTED, "nrv_net_run_layer: unknown precision");
     }
-    int c1 = l == L_E0A ? net->c0p : L.cin, c2 = 0;
+    int c1 = l == L_E0A ? (prec == NRV_PREC_FP8 ? 16 : net->c0p) : L.cin, c2 = 0;
     if (l == L_D2A || l == L_D1A || l == L_D0A) {
         c1 = L.cin / 2;
         c2 = L.cin / 2;
@@ -330,7 +336,13 @@ nrv_status net_run_layer(Net* net, int l, const void* x1, const void* x2, int n,
                                  TView<const float>{(const float*)x2, c2}, c2,
                                  TView<float>{(float*)y, L.cout}, g, 0, true, s);
     }
-    return fail(NRV_ERR_UNSUPPORTED, "nrv_net_run_layer runs in F32 or BF16");
+    if (prec == NRV_PREC_FP8) {
+        int in1, in2, out;
+        layer_scale_index(l, &in1, &in2, &out);
+        net->backend[l] = 1;
+        return tc_conv3(net, l, x1, c1, x2, c2, y, g, 0, prec, s, 1.0f / net->act_scale[out]);
+    }
+    return fail(NRV_ERR_UNSUPPORTED, "nrv_net_run_layer: unknown precision");
 }
 
 }  // namespace nrv

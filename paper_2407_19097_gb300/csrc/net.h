@@ -30,7 +30,8 @@ struct Net {
     Layer layers[NUM_LAYERS];
     int64_t n_params = 0;
     bool has_params = false;
-    float act_scale[NUM_LAYERS];
+    float act_scale[NUM_ACTS + 1];   // FP8 scales: [0] input, [1 + a] activation a
+    bool fp8_ready = false;          // FP8 weights packed for the current scales
     DevBuf params;     // FP32 master copy (flat layout)
     DevBuf wf32;       // FP32 packed forward weights, per layer at wf_off
     DevBuf wtf32;      // FP32 packed backward-data weights, per layer at wf_off
@@ -68,9 +69,16 @@ nrv_status net_repack(Net* net, cudaStream_t s);
 
 // tensor-core convolution (tc.cu); returns NRV_ERR_UNSUPPORTED when a shape is not covered
 nrv_status tc_conv3(const Net* net, int layer, const void* x1, int c1, const void* x2, int c2,
-                    void* y, const Geo& g, int level, nrv_prec prec, cudaStream_t s);
+                    void* y, const Geo& g, int level, nrv_prec prec, cudaStream_t s,
+                    float inv_out = 1.0f);
 nrv_status tc_upconv(const Net* net, int layer, const void* x, void* y, const Geo& g, int level_in,
-                     nrv_prec prec, cudaStream_t s);
+                     nrv_prec prec, cudaStream_t s, float inv_out = 1.0f);
+nrv_status tc_repack_fp8(Net* net, cudaStream_t s);
+nrv_status forward_fp8(Net* net, const uint8_t* netin, float* rgb, cudaStream_t s);
+// FP8 scale indices (0 input, 1 + Act) of a layer's first input, second input (-1 if none)
+// and output (-1 for the head)
+void layer_scale_index(int l, int* in1, int* in2, int* out);
+nrv_status net_calibrate(Net* net, const void* netin, int n, int H, int W, cudaStream_t s);
 
 // training kernels (train.cu)
 nrv_status launch_l1(const float* y, const float* t, int64_t n, float* loss, float* dy,

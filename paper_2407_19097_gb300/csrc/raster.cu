@@ -12,6 +12,9 @@
 // index.  An early depth test (Sec. 3.2, "early z-buffer testing") reads the
 // current key from L2 first and issues the atomic only when the point is in
 // front of it; keys only ever decrease, so a stale read only costs an atomic.
+#include <stdio.h>
+#include <stdlib.h>
+
 #include "internal.h"
 
 namespace nrv {
@@ -35,11 +38,46 @@ nrv_status launch_clear_keys(const RViews& views, cudaStream_t s) {
     return NRV_OK;
 }
 
+// Tiles of the culling variant: TILE x TILE pixels; bound[t] holds the largest
+// depth word (key >> 32) over the tile's pixels after a first pass over a
+// subset of the points.  Keys only decrease afterwards, so a point whose depth
+// word exceeds its tile's bound can never win there.
+constexpr int TILE = 16;
+
+// Certainly rejected without the exact division?  The pixel is located with the
+// fast quotient __fdividef (documented error <= 2 ulp for divisors in
+// [2^-126, 2^126]).  Carrying that error and the roundings of the exact
+// sequence through (q + 1) * W/2 bounds |sx_fast - sx_exact| by
+// W/2 * 2^-22 * (2.25 |q| + 1), over-estimated here as W/2 * 2^-20 * (|q| + 4).
+// A point is rejected only when the whole error interval is off screen, or lies
+// inside one tile whose bound is smaller than the point's depth word.
+__device__ __forceinline__ bool cull_point(const RView& v, float cw, float cx, float cy,
+                                           const uint32_t* __restrict__ bound, int tiles_x) {
+    if (!(cw >= 0x1p-125f && cw <= 0x1p125f)) return false;
+    const float qx = __fdividef(cx, cw), qy = __fdividef(cy, cw);
+    const float ax = __fmul_rn(__fadd_rn(qx, 1.0f), v.hw);
+    const float ay = __fmul_rn(__fsub_rn(1.0f, qy), v.hh);
+    const float ex = (fabsf(qx) + 4.0f) * v.hw * 0x1p-20f;
+    const float ey = (fabsf(qy) + 4.0f) * v.hh * 0x1p-20f;
+    if (ax + ex < 0.0f || ax - ex >= v.fw || ay + ey < 0.0f || ay - ey >= v.fh) return true;
+    if (!bound) return false;
+    // tile coordinates: scaling by 1/16 and the differences below are exact
+    const float tx = floorf(ax * (1.0f / TILE)), ty = floorf(ay * (1.0f / TILE));
+    const float rx = ax - tx * TILE, ry = ay - ty * TILE;
+    if (!(rx > ex && TILE - rx > ex && ry > ey && TILE - ry > ey && tx >= 0.0f && ty >= 0.0f &&
+          tx * TILE < v.fw && ty * TILE < v.fh))
+        return false;
+    return __float_as_uint(cw) > __ldg(bound + (int)ty * tiles_x + (int)tx);
+}
+
 // Projection + clipping of one point for one view; on success returns the key
-// and the address of its pixel's key.
+// and the address of its pixel's key.  With a tile bound table, points that
+// cull_point rejects are dropped before the exact divisions.
 __device__ __forceinline__ bool project_point(const RView& v, float x, float y, float z,
                                               uint32_t idx, unsigned long long*& p,
-                                              unsigned long long& key) {
+                                              unsigned long long& key,
+                                              const uint32_t* __restrict__ bound = nullptr,
+                                              int tiles_x = 0, bool cull = false) {
     const float cw = __fadd_rn(
         __fadd_rn(__fadd_rn(__fmul_rn(v.m[8], x), __fmul_rn(v.m[9], y)), __fmul_rn(v.m[10], z)),
         v.m[11]);
@@ -50,6 +88,7 @@ __device__ __forceinline__ bool project_point(const RView& v, float x, float y, 
     const float cy = __fadd_rn(
         __fadd_rn(__fadd_rn(__fmul_rn(v.m[4], x), __fmul_rn(v.m[5], y)), __fmul_rn(v.m[6], z)),
         v.m[7]);
+    if (cull && cull_point(v, cw, cx, cy, bound, tiles_x)) return false;
     const float sx = __fmul_rn(__fadd_rn(__fdiv_rn(cx, cw), 1.0f), v.hw);
     const float sy = __fmul_rn(__fsub_rn(1.0f, __fdiv_rn(cy, cw)), v.hh);
     if (!(sx >= 0.0f && sx < v.fw && sy >= 0.0f && sy < v.fh)) return false;
@@ -90,19 +129,33 @@ __device__ __forceinline__ void render_point(const RView& v, float x, float y, f
 //   SINGLE   one view, kept in registers for the whole pass;
 //   PREFETCH the next group's coordinates are loaded before this group is done;
 //   MINB     register budget: at least MINB blocks of 256 threads per SM.
-template <bool SINGLE, bool PREFETCH, int MINB>
+//   bound    per-tile depth bounds of all views back to back, or null (no culling);
+//            groups [g_begin, ngroups) are processed.
+template <bool SINGLE, bool PREFETCH, int MINB, bool CULL>
 __global__ void __launch_bounds__(256, MINB) visibility_kernel(const float4* __restrict__ xyz4,
                                                                uint64_t ngroups,
                                                                const float* __restrict__ xyz,
                                                                uint64_t n, RViews vs_arg,
-                                                               const RViews* __restrict__ views_dev) {
+                                                               const RViews* __restrict__ views_dev,
+                                                               const uint32_t* __restrict__ bound,
+                                                               uint64_t g_begin) {
     __shared__ RViews vs;
-    if (threadIdx.x == 0) vs = views_dev ? *views_dev : vs_arg;
+    __shared__ int tile_off[8], tiles_x[8];
+    if (threadIdx.x == 0) {
+        vs = views_dev ? *views_dev : vs_arg;
+        int off = 0;
+        for (int v = 0; v < vs.n; ++v) {
+            tiles_x[v] = (vs.v[v].width + TILE - 1) / TILE;
+            tile_off[v] = off;
+            off += tiles_x[v] * ((vs.v[v].height + TILE - 1) / TILE);
+        }
+    }
     __syncthreads();
+    const bool cull = CULL && bound != nullptr;
     RView v0;
     if (SINGLE) v0 = vs.v[0];
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    uint64_t g = g_begin + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a, c = a;
     if (PREFETCH && g < ngroups) {
         a = __ldcs(xyz4 + 3 * g);
@@ -133,7 +186,9 @@ __global__ void __launch_bounds__(256, MINB) visibility_kernel(const float4* __r
             unsigned long long key[4], cur[4];
             bool ok[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) ok[j] = project_point(vw, px[j], py[j], pz[j], i0 + j, ptr[j], key[j]);
+            for (int j = 0; j < 4; ++j)
+                ok[j] = project_point(vw, px[j], py[j], pz[j], i0 + j, ptr[j], key[j],
+                                      cull ? bound + tile_off[v] : nullptr, tiles_x[v], cull);
 #pragma unroll
             for (int j = 0; j < 4; ++j) cur[j] = ok[j] ? __ldcg(ptr[j]) : 0ull;
 #pragma unroll
@@ -154,57 +209,127 @@ __global__ void __launch_bounds__(256, MINB) visibility_kernel(const float4* __r
     }
 }
 
+// Tile bounds: one warp per tile takes the maximum depth word over its pixels
+// (empty pixels hold ~0, so a tile with an empty pixel never culls).
+__global__ void tile_bound_kernel(RViews vs_arg, const RViews* __restrict__ views_dev,
+                                  uint32_t* __restrict__ bound) {
+    const RViews& vs = views_dev ? *views_dev : vs_arg;
+    int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / 32);
+    const int lane = threadIdx.x & 31;
+    int v = 0;
+    uint32_t* out = bound;
+    for (; v < vs.n; ++v) {
+        const int tx = (vs.v[v].width + TILE - 1) / TILE, ty = (vs.v[v].height + TILE - 1) / TILE;
+        if (t < tx * ty) break;
+        t -= tx * ty;
+        out += tx * ty;
+    }
+    if (v >= vs.n) return;    // whole warps leave together
+    const RView& vw = vs.v[v];
+    const int tx = (vw.width + TILE - 1) / TILE;
+    const int x0 = (t % tx) * TILE + (lane & 1) * 8, y = (t / tx) * TILE + lane / 2;
+    unsigned m = 0;
+    if (y < vw.height)
+        for (int k = 0; k < 8; ++k)
+            if (x0 + k < vw.width)
+                m = max(m, (unsigned)(__ldcg(vw.key + (size_t)y * vw.width + x0 + k) >> 32));
+    m = __reduce_max_sync(0xffffffffu, m);
+    if (lane == 0) out[t] = m;
+}
+
+size_t visibility_scratch_bytes(const RViews& views) {
+    size_t tiles = 0;
+    for (int v = 0; v < views.n; ++v)
+        tiles += (size_t)((views.v[v].width + TILE - 1) / TILE) * ((views.v[v].height + TILE - 1) / TILE);
+    return tiles * sizeof(uint32_t);
+}
+
 // ------------------------------------------------------------------ variant choice
 // The best variant depends on the point order and the views (how many early
 // depth reads hit, how many atomics are left).  The first launch for a
 // (single/multi view, size class) tries every variant on the real data -- each
-// run computes the same keys, so the last one leaves the correct result -- and
-// keeps the fastest for later launches.  No choice is made during a stream
-// capture: the default variant is used until an uncaptured launch has tuned.
-typedef void (*VisFn)(const float4*, uint64_t, const float*, uint64_t, RViews, const RViews*);
+// run computes the same keys -- and keeps the fastest for later launches.  No
+// choice is made during a stream capture: the default variant is used until an
+// uncaptured launch has tuned.
+//
+// A culling variant first renders the leading 1/16 of the points without
+// culling, turns the keys into tile bounds, then renders the rest with culling.
+typedef void (*VisFn)(const float4*, uint64_t, const float*, uint64_t, RViews, const RViews*,
+                      const uint32_t*, uint64_t);
 
 struct VisVariant {
     VisFn fn;
-    int blocks_per_sm;
+    bool cull;
     const char* name;
+    int blocks_per_sm;   // resident blocks, from the compiled register count
 };
 
-static const VisVariant kSingle[] = {
-    {visibility_kernel<true, true, 3>, 3, "single/prefetch/3"},
-    {visibility_kernel<true, false, 3>, 3, "single/plain/3"},
-    {visibility_kernel<true, true, 4>, 4, "single/prefetch/4"},
-    {visibility_kernel<true, false, 4>, 4, "single/plain/4"},
-    {visibility_kernel<true, false, 5>, 5, "single/plain/5"},
+static VisVariant kSingle[] = {
+    {visibility_kernel<true, true, 3, false>, false, "single/prefetch/3", 0},
+    {visibility_kernel<true, false, 3, false>, false, "single/plain/3", 0},
+    {visibility_kernel<true, true, 2, false>, false, "single/prefetch/2", 0},
+    {visibility_kernel<true, true, 3, true>, true, "single/prefetch/3/cull", 0},
+    {visibility_kernel<true, false, 3, true>, true, "single/plain/3/cull", 0},
+    {visibility_kernel<true, true, 2, true>, true, "single/prefetch/2/cull", 0},
 };
-static const VisVariant kMulti[] = {
-    {visibility_kernel<false, true, 3>, 3, "multi/prefetch/3"},
-    {visibility_kernel<false, false, 3>, 3, "multi/plain/3"},
-    {visibility_kernel<false, false, 4>, 4, "multi/plain/4"},
+static VisVariant kMulti[] = {
+    {visibility_kernel<false, true, 3, false>, false, "multi/prefetch/3", 0},
+    {visibility_kernel<false, false, 3, false>, false, "multi/plain/3", 0},
+    {visibility_kernel<false, true, 3, true>, true, "multi/prefetch/3/cull", 0},
+    {visibility_kernel<false, false, 3, true>, true, "multi/plain/3/cull", 0},
 };
 
-struct VisTune {
-    int choice = -1;
-};
-static VisTune g_vis_tune[2][48];   // [multi][log2 of the point count]
-static int g_vis_sms = 0;
-
-static nrv_status launch_variant(const VisVariant& v, const float* xyz, uint64_t n,
-                                 const RViews& views, cudaStream_t s, const RViews* views_dev) {
-    const uint64_t ngroups = n / 4;
-    int blocks = g_vis_sms * v.blocks_per_sm;
-    const uint64_t need = (ngroups + 255) / 256;
-    if (need < (uint64_t)blocks) blocks = (int)(need > 0 ? need : 1);
-    v.fn<<<blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(xyz), ngroups, xyz, n, views,
-                                views_dev);
-    NRV_CHECK_LAUNCH();
+static nrv_status resident_blocks(VisVariant& v) {
+    if (v.blocks_per_sm) return NRV_OK;
+    cudaFuncAttributes fa;
+    NRV_CHECK_CUDA(cudaFuncGetAttributes(&fa, v.fn));
+    const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+    int b = 65536 / (regs_per_warp * 8);
+    if (b > 8) b = 8;
+    v.blocks_per_sm = b > 0 ? b : 1;
     return NRV_OK;
 }
 
-int visibility_variant_count(int multi) { return multi ? 3 : 5; }
+static int g_vis_choice[2][48];   // [multi][log2 of the point count]; 0 = untuned
+static int g_vis_sms = 0;
+
+static nrv_status run_variant(VisVariant& v, const float* xyz, uint64_t n,
+                              const RViews& views, cudaStream_t s, const RViews* views_dev,
+                              uint32_t* tiles) {
+    NRV_TRY(resident_blocks(v));
+    const uint64_t ngroups = n / 4;
+    auto launch = [&](uint64_t g0, uint64_t g1, uint64_t npts, const uint32_t* b) -> nrv_status {
+        int blocks = g_vis_sms * v.blocks_per_sm;
+        const uint64_t need = (g1 - g0 + 255) / 256;
+        if (need < (uint64_t)blocks) blocks = (int)(need > 0 ? need : 1);
+        v.fn<<<blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(xyz), g1, xyz, npts, views,
+                                    views_dev, b, g0);
+        NRV_CHECK_LAUNCH();
+        return NRV_OK;
+    };
+    if (!v.cull || !tiles || ngroups < 64) return launch(0, ngroups, n, nullptr);
+    const uint64_t gsub = ngroups / 16;
+    NRV_TRY(launch(0, gsub, 4 * gsub, nullptr));
+    const size_t ntiles = visibility_scratch_bytes(views) / sizeof(uint32_t);
+    tile_bound_kernel<<<(unsigned)((ntiles * 32 + 255) / 256), 256, 0, s>>>(views, views_dev, tiles);
+    NRV_CHECK_LAUNCH();
+    return launch(gsub, ngroups, n, tiles);
+}
+
+int visibility_variant_count(int multi) { return multi ? 4 : 6; }
 const char* visibility_variant_name(int multi, int i) { return (multi ? kMulti : kSingle)[i].name; }
 
+static bool verbose() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("NRV_VERBOSE");
+        v = e && *e && *e != '0';
+    }
+    return v == 1;
+}
+
 nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, cudaStream_t s,
-                             const RViews* views_dev) {
+                             const RViews* views_dev, uint32_t* tiles) {
     if (n == 0) return NRV_OK;
     if (!g_vis_sms) {
         int dev = 0;
@@ -213,14 +338,22 @@ nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, 
         if (g_vis_sms <= 0) g_vis_sms = 148;
     }
     const int multi = views.n > 1;
-    const VisVariant* tab = multi ? kMulti : kSingle;
+    VisVariant* tab = multi ? kMulti : kSingle;
     const int count = visibility_variant_count(multi);
     int cls = 0;
     while (cls < 47 && (1ull << (cls + 1)) <= n) ++cls;
-    VisTune& t = g_vis_tune[multi][cls];
+    int& choice = g_vis_choice[multi][cls];
+    // NRV_VIS_VARIANT=<i> pins variant i (used to check every variant)
+    if (const char* e = getenv("NRV_VIS_VARIANT")) {
+        const int i = atoi(e);
+        if (i >= 0 && i < count) {
+            if (tab[i].cull && !tiles) return fail(NRV_ERR_ARG, "variant %d needs tile scratch", i);
+            return run_variant(tab[i], xyz, n, views, s, views_dev, tiles);
+        }
+    }
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     NRV_CHECK_CUDA(cudaStreamIsCapturing(s, &cap));
-    if (t.choice < 0 && cap == cudaStreamCaptureStatusNone && n >= (1u << 20)) {
+    if (choice == 0 && cap == cudaStreamCaptureStatusNone && n >= (1u << 20)) {
         // time each variant twice on the real data; keep the faster second run
         cudaEvent_t e0, e1;
         NRV_CHECK_CUDA(cudaEventCreate(&e0));
@@ -228,15 +361,17 @@ nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, 
         float best = 1e30f;
         int arg = 0;
         for (int i = 0; i < count; ++i) {
+            if (tab[i].cull && !tiles) continue;
             float ms = 0.0f;
             for (int rep = 0; rep < 2; ++rep) {
                 NRV_TRY(launch_clear_keys(views, s));
                 NRV_CHECK_CUDA(cudaEventRecord(e0, s));
-                NRV_TRY(launch_variant(tab[i], xyz, n, views, s, views_dev));
+                NRV_TRY(run_variant(tab[i], xyz, n, views, s, views_dev, tiles));
                 NRV_CHECK_CUDA(cudaEventRecord(e1, s));
                 NRV_CHECK_CUDA(cudaEventSynchronize(e1));
                 NRV_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
             }
+            if (verbose()) fprintf(stderr, "nrv: render pass %-26s %.3f ms\n", tab[i].name, ms);
             if (ms < best) {
                 best = ms;
                 arg = i;
@@ -244,11 +379,12 @@ nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, 
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        t.choice = arg;
-        // the trials left correct keys, but clear and rerun so the call's own work is one pass
+        choice = arg + 1;
         NRV_TRY(launch_clear_keys(views, s));
     }
-    return launch_variant(tab[t.choice < 0 ? 0 : t.choice], xyz, n, views, s, views_dev);
+    int pick = choice > 0 ? choice - 1 : 0;
+    if (tab[pick].cull && !tiles) pick = 0;
+    return run_variant(tab[pick], xyz, n, views, s, views_dev, tiles);
 }
 
 // ------------------------------------------------------------------ pack helpers

@@ -54,10 +54,13 @@ struct TcParams {
     uint32_t w_region;       // bytes reserved for the weights (aligned)
     uint32_t idesc;
     uint32_t tmem_cols;
-    const uint8_t* wpk;      // packed weights [slice][ks][half][n][8] (BF16)
+    const uint8_t* wpk;      // packed weights [slice][ks][half][n][16 bytes] (BF16 or E4M3)
     const float* bias;
-    __nv_bfloat16* y;
+    void* y;                 // BF16 or E4M3 NHWC output
     unsigned* status;
+    int fp8;                 // E4M3 operands (kind::f8f6f4) and an E4M3 output
+    float inv_out;           // FP8: 1 / scale of the output tensor
+    const float* colscale;   // FP8: per GEMM column, input scale x weight scale
     uint32_t a_off[MAX_KS];  // A start offset in the halo buffer, per K-step
     uint32_t a_lbo[MAX_KS];  // A K-direction byte offset (second half), per K-step
 };
@@ -147,6 +150,16 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
         : "memory");
 }
 
+__device__ __forceinline__ void mma_fp8(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -177,6 +190,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t bars[16];
     __shared__ float bias_s[256];
+    __shared__ float colscale_s[256];
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
 
@@ -214,8 +228,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     // per output column of this slice: its bias (column n maps to channel n mod cout)
-    for (int i = threadIdx.x; i < P.n_slice; i += NTHREADS)
+    for (int i = threadIdx.x; i < P.n_slice; i += NTHREADS) {
         bias_s[i] = P.bias[(slice * P.n_slice + i) % P.cout];
+        colscale_s[i] = P.fp8 ? P.colscale[slice * P.n_slice + i] : 1.0f;
+    }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_slot)),
@@ -272,7 +288,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int ks = 0; ks < P.nks; ++ks) {
                     const uint64_t a = sdesc(hb + P.a_off[ks], P.a_lbo[ks], 128);
                     const uint64_t b = sdesc(s_w + (uint32_t)ks * 2 * b_lbo, b_lbo, 128);
-                    mma_bf16(d, a, b, P.idesc, ks > 0 ? 1u : 0u);
+                    if (P.fp8) mma_fp8(d, a, b, P.idesc, ks > 0 ? 1u : 0u);
+                    else mma_bf16(d, a, b, P.idesc, ks > 0 ? 1u : 0u);
                 }
                 mma_commit(b_hempty(buf));
                 mma_commit(b_afull(ab));
@@ -299,32 +316,43 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int c0 = 0; c0 < P.n_slice; c0 += 16) {
                 uint32_t r[16];
                 tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * P.n_slice + c0), r);
-                uint32_t packed[8];
+                float v[16];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    float v0 = __uint_as_float(r[2 * j]) + bias_s[c0 + 2 * j];
-                    float v1 = __uint_as_float(r[2 * j + 1]) + bias_s[c0 + 2 * j + 1];
-                    if (P.mode == 0) {
-                        v0 = fmaxf(v0, 0.0f);
-                        v1 = fmaxf(v1, 0.0f);
-                    }
-                    __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
-                    packed[j] = *reinterpret_cast<uint32_t*>(&h2);
+                for (int j = 0; j < 16; ++j) {
+                    v[j] = fmaf(__uint_as_float(r[j]), colscale_s[c0 + j], bias_s[c0 + j]);
+                    if (P.mode == 0) v[j] = fmaxf(v[j], 0.0f);
                 }
                 if (x < P.w) {
-                    __nv_bfloat16* dst;
                     const int ng = slice * P.n_slice + c0;
+                    size_t e;   // element offset of the 16 outputs
                     if (P.mode == 0) {
-                        dst = P.y + (((size_t)img * P.h + yr) * P.w + x) * P.cout + ng;
+                        e = (((size_t)img * P.h + yr) * P.w + x) * P.cout + ng;
                     } else {
                         // transposed conv: column ng = (2a + b) * cout + o  ->  pixel (2y+a, 2x+b)
                         const int abi = ng / P.cout, o = ng % P.cout;
-                        dst = P.y + (((size_t)img * 2 * P.h + 2 * yr + (abi >> 1)) * 2 * P.w +
-                                     2 * x + (abi & 1)) * P.cout + o;
+                        e = (((size_t)img * 2 * P.h + 2 * yr + (abi >> 1)) * 2 * P.w + 2 * x +
+                             (abi & 1)) * P.cout + o;
                     }
-                    uint4* o4 = reinterpret_cast<uint4*>(dst);
-                    o4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                    o4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                    if (P.fp8) {
+                        uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(
+                                v[j] * P.inv_out, __NV_SATFINITE, __NV_E4M3);
+                            w[j >> 2] |= (uint32_t)q << (8 * (j & 3));
+                        }
+                        *reinterpret_cast<uint4*>((uint8_t*)P.y + e) = make_uint4(w[0], w[1], w[2], w[3]);
+                    } else {
+                        uint32_t packed[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                            packed[j] = *reinterpret_cast<uint32_t*>(&h2);
+                        }
+                        uint4* o4 = reinterpret_cast<uint4*>((__nv_bfloat16*)P.y + e);
+                        o4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                        o4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                    }
                 }
             }
             tc_fence_before();
@@ -366,25 +394,31 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// NHWC BF16 tensor [n][h][w][c] viewed as (8, w, c/8, h, n) so that one box of
-// (8, 130, c/8, rows, 1) lands in shared memory as [row][chunk][pixel][8].
-nrv_status make_halo_map(CUtensorMap* map, const void* base, int n, int h, int w, int c, int rows) {
+// NHWC tensor [n][h][w][c] of `es`-byte elements viewed as (ce, w, c/ce, h, n),
+// ce = 16 / es elements per 16-byte chunk, so that one box of
+// (ce, 130, c/ce, rows, 1) lands in shared memory as [row][chunk][pixel][16 bytes].
+nrv_status make_halo_map(CUtensorMap* map, const void* base, int n, int h, int w, int c, int rows,
+                         int es) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return fail(NRV_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
     if (((uintptr_t)base & 15) != 0) return fail(NRV_ERR_ARG, "tensor base not 16-byte aligned");
-    const cuuint64_t dims[5] = {8, (cuuint64_t)w, (cuuint64_t)(c / 8), (cuuint64_t)h, (cuuint64_t)n};
-    const cuuint64_t strides[4] = {(cuuint64_t)c * 2, 16, (cuuint64_t)w * c * 2,
-                                   (cuuint64_t)h * w * c * 2};
-    const cuuint32_t box[5] = {8, HALO_W, (cuuint32_t)(c / 8), (cuuint32_t)rows, 1};
-    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides,
-                     box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    const int ce = 16 / es;
+    const cuuint64_t dims[5] = {(cuuint64_t)ce, (cuuint64_t)w, (cuuint64_t)(c / ce), (cuuint64_t)h,
+                                (cuuint64_t)n};
+    const cuuint64_t strides[4] = {(cuuint64_t)c * es, 16, (cuuint64_t)w * c * es,
+                                   (cuuint64_t)h * w * c * es};
+    const cuuint32_t box[5] = {(cuuint32_t)ce, HALO_W, (cuuint32_t)(c / ce), (cuuint32_t)rows, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r = enc(map, es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
+                     5, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(NRV_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return NRV_OK;
 }
 
-// One half of a K-step: 8 input channels (chunk) of one tap from one source.
+// One half of a K-step: one 16-byte chunk of channels (8 BF16 or 16 E4M3) of one
+// tap from one source.
 struct Half {
     int tap, src, chunk;  // src 0 or 1; tap < 0 marks the zero phantom
 };
@@ -396,45 +430,77 @@ struct Half {
 struct TcLayerCfg {
     bool ok = false;
     int kind = CONV3;
-    int c1 = 0, c2 = 0;
+    int c1 = 0, c2 = 0;      // channels per source (padded input width for the first layer)
     int rows = 3, row0 = -1;
     int ncols = 0;           // GEMM N (C_out, or 4 C_out)
     int n_slice = 0, nslices = 0, nks = 0;
     std::vector<Half> halves;
-    size_t w_off = 0;        // byte offset of the packed weights in the BF16 buffer
+    size_t w_off = 0;        // byte offset of the packed weights
     uint32_t w_bytes = 0;    // per slice
+    size_t cs_off = 0;       // FP8: offset (floats) of the per-column scales
 };
 
-TcLayerCfg g_cfg[NUM_LAYERS];
+TcLayerCfg g_cfg[2][NUM_LAYERS];   // [BF16, FP8]
 
+// out[slice][ks][half][n][ce], ce = 8 (BF16) or 16 (E4M3).  FP8 weights are
+// W * fold / s_w[n] in E4M3, fold = scale(skip) / scale(upsampled) for the second
+// source of a concatenating layer, 1 otherwise.
 __global__ void pack_tc_weights_kernel(const float* __restrict__ P, int64_t woff, int kind,
                                        int cin_real, int cout, int n_slice, int nslices, int nks,
-                                       const int4* __restrict__ halves, int c1, uint16_t* out) {
-    // out[slice][ks][half][n][8]
-    const size_t total = (size_t)nslices * nks * 2 * n_slice * 8;
+                                       const int4* __restrict__ halves, int c1, int fp8,
+                                       float fold, const float* __restrict__ s_w, uint8_t* out) {
+    const int ce = fp8 ? 16 : 8;
+    const size_t total = (size_t)nslices * nks * 2 * n_slice * ce;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
          i += (size_t)gridDim.x * blockDim.x) {
-        const int e = (int)(i % 8);
-        const int nl = (int)((i / 8) % n_slice);
-        const int hf = (int)((i / (8 * (size_t)n_slice)) % 2);
-        const int ks = (int)((i / (16 * (size_t)n_slice)) % nks);
-        const int sl = (int)(i / (16 * (size_t)n_slice * nks));
+        const int e = (int)(i % ce);
+        const int nl = (int)((i / ce) % n_slice);
+        const int hf = (int)((i / (ce * (size_t)n_slice)) % 2);
+        const int ks = (int)((i / (2 * ce * (size_t)n_slice)) % nks);
+        const int sl = (int)(i / (2 * ce * (size_t)n_slice * nks));
         const int4 h = halves[2 * ks + hf];
+        const int n = sl * n_slice + nl;
         float v = 0.0f;
         if (h.x >= 0) {
-            const int c = (h.y == 0 ? 0 : c1) + 8 * h.z + e;
-            const int n = sl * n_slice + nl;
+            const int c = (h.y == 0 ? 0 : c1) + ce * h.z + e;
             if (c < cin_real) {
                 if (kind == CONV3) v = P[woff + ((size_t)n * cin_real + c) * 9 + h.x];
                 else v = P[woff + ((size_t)c * cout + n % cout) * 4 + n / cout];
+                if (h.y == 1) v *= fold;
             }
         }
-        __nv_bfloat16 b = __float2bfloat16_rn(v);
-        out[i] = *reinterpret_cast<uint16_t*>(&b);
+        if (fp8) {
+            out[i] = __nv_cvt_float_to_fp8(v / s_w[n], __NV_SATFINITE, __NV_E4M3);
+        } else {
+            __nv_bfloat16 b = __float2bfloat16_rn(v);
+            reinterpret_cast<uint16_t*>(out)[i] = *reinterpret_cast<uint16_t*>(&b);
+        }
     }
 }
 
-DevBuf g_halves;
+// FP8 column scales: s_w[n] = (largest |W * fold| of column n) / 448 (1 if the column
+// is zero) and colscale[n] = s_in * s_w[n], s_in the scale of the layer's input.
+__global__ void fp8_column_scales_kernel(const float* __restrict__ P, int64_t woff, int kind,
+                                         int cin_real, int c1_real, int cout, int ncols,
+                                         float fold, float s_in, float* s_w, float* colscale) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= ncols) return;
+    float amax = 0.0f;
+    for (int c = 0; c < cin_real; ++c) {
+        const float f = c >= c1_real ? fold : 1.0f;
+        if (kind == CONV3) {
+            for (int t = 0; t < 9; ++t)
+                amax = fmaxf(amax, fabsf(P[woff + ((size_t)n * cin_real + c) * 9 + t] * f));
+        } else {
+            amax = fmaxf(amax, fabsf(P[woff + ((size_t)c * cout + n % cout) * 4 + n / cout] * f));
+        }
+    }
+    const float sw = amax > 0.0f ? amax / 448.0f : 1.0f;
+    s_w[n] = sw;
+    colscale[n] = s_in * sw;
+}
+
+DevBuf g_halves[2];
 
 }  // namespace
 
@@ -447,18 +513,19 @@ static int src_split(int l, int cin_padded, int* c2) {
     return cin_padded;
 }
 
-nrv_status tc_repack(Net* net, cudaStream_t s) {
+// Layer configurations and packed weights for one operand precision (0 BF16, 1 FP8).
+static nrv_status build_cfg(Net* net, int pi, std::vector<int4>& all_halves,
+                            std::vector<size_t>& hoff, size_t& wbytes_total) {
+    const int ce = pi ? 16 : 8;
     size_t off = 0;
-    std::vector<int4> all_halves;
-    std::vector<size_t> hoff(NUM_LAYERS, 0);
     for (int l = 0; l < NUM_LAYERS; ++l) {
-        TcLayerCfg& c = g_cfg[l];
+        TcLayerCfg& c = g_cfg[pi][l];
         c = TcLayerCfg();
         const Layer& L = net->layers[l];
         if (L.kind == HEAD1) continue;
         c.kind = L.kind;
         if (L.kind == CONV3) {
-            const int cinp = l == L_E0A ? net->c0p : L.cin;
+            const int cinp = l == L_E0A ? (pi ? 16 : net->c0p) : L.cin;
             c.c1 = src_split(l, cinp, &c.c2);
             c.rows = 3;
             c.row0 = -1;
@@ -466,7 +533,7 @@ nrv_status tc_repack(Net* net, cudaStream_t s) {
             for (int tap = 0; tap < 9; ++tap)
                 for (int src = 0; src < 2; ++src) {
                     const int cs = src == 0 ? c.c1 : c.c2;
-                    for (int ch = 0; ch < cs / 8; ++ch) c.halves.push_back(Half{tap, src, ch});
+                    for (int ch = 0; ch < cs / ce; ++ch) c.halves.push_back(Half{tap, src, ch});
                 }
         } else {
             c.c1 = L.cin;
@@ -475,7 +542,7 @@ nrv_status tc_repack(Net* net, cudaStream_t s) {
             c.row0 = 0;
             c.ncols = 4 * L.cout;
             // the one "tap" reads row 0 of the halo at pixel offset +1 (tap index 1)
-            for (int ch = 0; ch < L.cin / 8; ++ch) c.halves.push_back(Half{1, 0, ch});
+            for (int ch = 0; ch < L.cin / ce; ++ch) c.halves.push_back(Half{1, 0, ch});
         }
         if (c.halves.size() % 2) c.halves.push_back(Half{-1, 0, 0});
         c.nks = (int)c.halves.size() / 2;
@@ -492,36 +559,105 @@ nrv_status tc_repack(Net* net, cudaStream_t s) {
         for (const Half& h : c.halves) all_halves.push_back(make_int4(h.tap, h.src, h.chunk, 0));
         c.ok = true;
     }
+    wbytes_total = off;
+    return NRV_OK;
+}
+
+nrv_status tc_repack(Net* net, cudaStream_t s) {
+    std::vector<int4> all_halves;
+    std::vector<size_t> hoff(NUM_LAYERS, 0);
+    size_t off = 0;
+    NRV_TRY(build_cfg(net, 0, all_halves, hoff, off));
     if (off == 0) return NRV_OK;
     NRV_TRY(net->wbf16.ensure(off));
-    NRV_TRY(g_halves.ensure(all_halves.size() * sizeof(int4)));
-    NRV_CHECK_CUDA(cudaMemcpyAsync(g_halves.p, all_halves.data(), all_halves.size() * sizeof(int4),
+    NRV_TRY(g_halves[0].ensure(all_halves.size() * sizeof(int4)));
+    NRV_CHECK_CUDA(cudaMemcpyAsync(g_halves[0].p, all_halves.data(), all_halves.size() * sizeof(int4),
                                    cudaMemcpyHostToDevice, s));
     for (int l = 0; l < NUM_LAYERS; ++l) {
-        const TcLayerCfg& c = g_cfg[l];
+        const TcLayerCfg& c = g_cfg[0][l];
         if (!c.ok) continue;
         const Layer& L = net->layers[l];
         pack_tc_weights_kernel<<<64, 256, 0, s>>>(
-            (const float*)net->params.p, L.woff, c.kind, L.cin, L.cout, c.n_slice, c.nslices,
-            c.nks, (const int4*)g_halves.p + hoff[l], c.c1,
-            (uint16_t*)((char*)net->wbf16.p + c.w_off));
+            (const float*)net->params.p, L.woff, c.kind, L.cin, L.cout, c.n_slice, c.nslices, c.nks,
+            (const int4*)g_halves[0].p + hoff[l], c.c1, 0, 1.0f, nullptr,
+            (uint8_t*)net->wbf16.p + c.w_off);
         NRV_CHECK_LAUNCH();
     }
     // the host copy of the halves must stay valid until the copy ran
     NRV_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (net->fp8_ready) return tc_repack_fp8(net, s);
     return NRV_OK;
 }
 
-// Launch one tensor-core layer on a level of geometry (n, H, W): a 3x3 conv
-// writes [n][H][W][C_out]; a transposed conv reads level (H, W) and writes
-// [n][2H][2W][C_out].
+// Activation-scale index (0 input, 1 + Act) of each layer's input (first source),
+// second source and output.
+void layer_scale_index(int l, int* in1, int* in2, int* out) {
+    static const int t[NUM_LAYERS][3] = {
+        {0, -1, 1 + A_E0A},         {1 + A_E0A, -1, 1 + A_E0B}, {1 + A_P0, -1, 1 + A_E1A},
+        {1 + A_E1A, -1, 1 + A_E1B}, {1 + A_P1, -1, 1 + A_E2A},  {1 + A_E2A, -1, 1 + A_E2B},
+        {1 + A_P2, -1, 1 + A_E3A},  {1 + A_E3A, -1, 1 + A_E3B}, {1 + A_E3B, -1, 1 + A_UP3},
+        {1 + A_UP3, 1 + A_E2B, 1 + A_D2A}, {1 + A_D2A, -1, 1 + A_D2B}, {1 + A_D2B, -1, 1 + A_UP2},
+        {1 + A_UP2, 1 + A_E1B, 1 + A_D1A}, {1 + A_D1A, -1, 1 + A_D1B}, {1 + A_D1B, -1, 1 + A_UP1},
+        {1 + A_UP1, 1 + A_E0B, 1 + A_D0A}, {1 + A_D0A, -1, 1 + A_D0B}, {1 + A_D0B, -1, -1}};
+    *in1 = t[l][0];
+    *in2 = t[l][1];
+    *out = t[l][2];
+}
+
+nrv_status tc_repack_fp8(Net* net, cudaStream_t s) {
+    std::vector<int4> all_halves;
+    std::vector<size_t> hoff(NUM_LAYERS, 0);
+    size_t off = 0;
+    NRV_TRY(build_cfg(net, 1, all_halves, hoff, off));
+    size_t cs = 0;
+    for (int l = 0; l < NUM_LAYERS; ++l) {
+        TcLayerCfg& c = g_cfg[1][l];
+        if (!c.ok) continue;
+        c.cs_off = cs;
+        cs += (size_t)c.ncols;
+    }
+    NRV_TRY(net->wfp8.ensure(off));
+    NRV_TRY(net->wscale8.ensure(2 * cs * sizeof(float)));
+    NRV_TRY(g_halves[1].ensure(all_halves.size() * sizeof(int4)));
+    NRV_CHECK_CUDA(cudaMemcpyAsync(g_halves[1].p, all_halves.data(), all_halves.size() * sizeof(int4),
+                                   cudaMemcpyHostToDevice, s));
+    float* s_w = (float*)net->wscale8.p;
+    float* colscale = s_w + cs;
+    for (int l = 0; l < NUM_LAYERS; ++l) {
+        const TcLayerCfg& c = g_cfg[1][l];
+        if (!c.ok) continue;
+        const Layer& L = net->layers[l];
+        int in1, in2, out;
+        layer_scale_index(l, &in1, &in2, &out);
+        const float s_in = net->act_scale[in1];
+        const float fold = in2 >= 0 ? net->act_scale[in2] / s_in : 1.0f;
+        const int c1_real = c.c2 > 0 ? c.c1 : L.cin;
+        fp8_column_scales_kernel<<<(c.ncols + 127) / 128, 128, 0, s>>>(
+            (const float*)net->params.p, L.woff, c.kind, L.cin, c1_real, L.cout, c.ncols, fold,
+            s_in, s_w + c.cs_off, colscale + c.cs_off);
+        NRV_CHECK_LAUNCH();
+        pack_tc_weights_kernel<<<64, 256, 0, s>>>(
+            (const float*)net->params.p, L.woff, c.kind, L.cin, L.cout, c.n_slice, c.nslices, c.nks,
+            (const int4*)g_halves[1].p + hoff[l], c.c1, 1, fold, s_w + c.cs_off,
+            (uint8_t*)net->wfp8.p + c.w_off);
+        NRV_CHECK_LAUNCH();
+    }
+    NRV_CHECK_CUDA(cudaStreamSynchronize(s));
+    return NRV_OK;
+}
+
 static int g_num_sms = 0;
 
+// Launch one tensor-core layer on a level of geometry (n, H, W): a 3x3 conv
+// writes [n][H][W][C_out]; a transposed conv reads level (H, W) and writes
+// [n][2H][2W][C_out].  FP8: operands and output E4M3, inv_out = 1 / output scale.
 static nrv_status tc_launch(const Net* net, int l, const void* x1, int c1, const void* x2, int c2,
-                            void* y, int n, int H, int W, cudaStream_t s) {
-    const TcLayerCfg& c = g_cfg[l];
+                            void* y, int n, int H, int W, cudaStream_t s, int fp8, float inv_out) {
+    const TcLayerCfg& c = g_cfg[fp8][l];
     if (!c.ok || c.c1 != c1 || c.c2 != c2) return fail(NRV_ERR_UNSUPPORTED, "layer not configured");
+    if (fp8 && !net->fp8_ready) return fail(NRV_ERR_STATE, "FP8 needs activation scales");
     const Layer& L = net->layers[l];
+    const int es = fp8 ? 1 : 2, ce = 16 / es;
     TcParams P;
     memset(&P, 0, sizeof(P));
     P.n = n;
@@ -536,7 +672,7 @@ static nrv_status tc_launch(const Net* net, int l, const void* x1, int c1, const
     P.mode = c.kind == CONV3 ? 0 : 1;
     P.row0 = c.row0;
     P.has_src2 = c.c2 > 0;
-    const uint32_t nch1 = c.c1 / 8, nch2 = c.c2 / 8;
+    const uint32_t nch1 = c.c1 / ce, nch2 = c.c2 / ce;
     P.tx1 = c.rows * nch1 * PLANE;
     P.tx2 = c.rows * nch2 * PLANE;
     P.src2_off = (P.tx1 + 127) / 128 * 128;   // TMA destinations are 128-byte aligned
@@ -549,14 +685,22 @@ static nrv_status tc_launch(const Net* net, int l, const void* x1, int c1, const
     P.nbuf = nbuf;
     const uint32_t smem = P.w_region + P.nbuf * P.halo_bytes;
     if (smem > 220 * 1024) return fail(NRV_ERR_UNSUPPORTED, "tile does not fit in shared memory");
-    P.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(c.n_slice >> 3) << 17) |
+    // instruction descriptor: FP32 accumulator; A/B BF16 (kind::f16) or E4M3 (kind::f8f6f4)
+    const uint32_t ab_fmt = fp8 ? 0u : 1u;
+    P.idesc = (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(c.n_slice >> 3) << 17) |
               ((uint32_t)(TILE_M >> 4) << 24);
     uint32_t cols = 32;
     while (cols < (uint32_t)(2 * c.n_slice)) cols *= 2;
     P.tmem_cols = cols;
-    P.wpk = (const uint8_t*)net->wbf16.p + c.w_off;
+    P.wpk = (const uint8_t*)(fp8 ? net->wfp8.p : net->wbf16.p) + c.w_off;
     P.bias = (const float*)net->params.p + L.boff;
-    P.y = (__nv_bfloat16*)y;
+    P.y = y;
+    P.fp8 = fp8;
+    P.inv_out = inv_out;
+    if (fp8) {
+        size_t cs_total = net->wscale8.bytes / (2 * sizeof(float));
+        P.colscale = (const float*)net->wscale8.p + cs_total + c.cs_off;
+    }
     P.status = status_word();
     if (!P.status) return fail(NRV_ERR_CUDA, "status word unavailable");
     for (int ks = 0; ks < c.nks; ++ks) {
@@ -577,8 +721,8 @@ static nrv_status tc_launch(const Net* net, int l, const void* x1, int c1, const
             return fail(NRV_ERR_UNSUPPORTED, "A operand outside the halo buffer");
     }
     CUtensorMap m1, m2;
-    NRV_TRY(make_halo_map(&m1, x1, n, H, W, c.c1, c.rows));
-    if (P.has_src2) NRV_TRY(make_halo_map(&m2, x2, n, H, W, c.c2, c.rows));
+    NRV_TRY(make_halo_map(&m1, x1, n, H, W, c.c1, c.rows, es));
+    if (P.has_src2) NRV_TRY(make_halo_map(&m2, x2, n, H, W, c.c2, c.rows, es));
     else m2 = m1;
     if (!g_num_sms) {
         int dev = 0;
@@ -621,18 +765,21 @@ static nrv_status tc_launch(const Net* net, int l, const void* x1, int c1, const
 }
 
 nrv_status tc_conv3(const Net* net, int l, const void* x1, int c1, const void* x2, int c2, void* y,
-                    const Geo& g, int level, nrv_prec prec, cudaStream_t s) {
-    if (prec != NRV_PREC_BF16) return fail(NRV_ERR_UNSUPPORTED, "tensor-core path is BF16");
+                    const Geo& g, int level, nrv_prec prec, cudaStream_t s, float inv_out) {
+    if (prec != NRV_PREC_BF16 && prec != NRV_PREC_FP8)
+        return fail(NRV_ERR_UNSUPPORTED, "tensor-core path is BF16 or FP8");
     if (net->layers[l].kind != CONV3) return fail(NRV_ERR_UNSUPPORTED, "not a 3x3 conv");
-    return tc_launch(net, l, x1, c1, x2, c2, y, g.n, g.h[level], g.w[level], s);
+    return tc_launch(net, l, x1, c1, x2, c2, y, g.n, g.h[level], g.w[level], s,
+                     prec == NRV_PREC_FP8, inv_out);
 }
 
 nrv_status tc_upconv(const Net* net, int l, const void* x, void* y, const Geo& g, int level_in,
-                     nrv_prec prec, cudaStream_t s) {
-    if (prec != NRV_PREC_BF16) return fail(NRV_ERR_UNSUPPORTED, "tensor-core path is BF16");
+                     nrv_prec prec, cudaStream_t s, float inv_out) {
+    if (prec != NRV_PREC_BF16 && prec != NRV_PREC_FP8)
+        return fail(NRV_ERR_UNSUPPORTED, "tensor-core path is BF16 or FP8");
     if (net->layers[l].kind != UPCONV2) return fail(NRV_ERR_UNSUPPORTED, "not a transposed conv");
     return tc_launch(net, l, x, net->layers[l].cin, nullptr, 0, y, g.n, g.h[level_in],
-                     g.w[level_in], s);
+                     g.w[level_in], s, prec == NRV_PREC_FP8, inv_out);
 }
 
 }  // namespace nrv

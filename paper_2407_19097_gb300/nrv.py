@@ -57,6 +57,7 @@ P, I, I64, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_float
 SIGNATURES = {
     "nrv_last_error": (ctypes.c_char_p, []),
     "nrv_version": (I, []),
+    "nrv_launch_count": (ctypes.c_uint64, []),
     "nrv_pad8": (I, [I]),
     "nrv_netin_channels": (I, [I]),
     "nrv_create_scene": (I, [ctypes.POINTER(nrv_scene_desc), ctypes.POINTER(P)]),
@@ -69,7 +70,9 @@ SIGNATURES = {
     "nrv_create_net": (I, [I, ctypes.POINTER(P)]),
     "nrv_destroy_net": (I, [P]),
     "nrv_net_set_params": (I, [P, P, P]),
-    "nrv_net_set_act_scales": (I, [P, ctypes.POINTER(F), I]),
+    "nrv_net_set_act_scales": (I, [P, ctypes.POINTER(F), I, P]),
+    "nrv_net_get_act_scales": (I, [P, ctypes.POINTER(F), I]),
+    "nrv_net_calibrate": (I, [P, P, I, I, I, P]),
     "nrv_shade": (I, [P, P, I, I, I, I, P, P]),
     "nrv_net_layer_backend": (I, [P, I]),
     "nrv_net_run_layer": (I, [P, I, P, P, I, I, I, I, P, P]),
@@ -208,7 +211,15 @@ class Net:
 
     def set_act_scales(self, scales):
         arr = (F * len(scales))(*[float(s) for s in scales])
-        check(lib().nrv_net_set_act_scales(self.h, arr, len(scales)))
+        check(lib().nrv_net_set_act_scales(self.h, arr, len(scales), _stream(None)))
+
+    def act_scales(self):
+        arr = (F * 21)()
+        check(lib().nrv_net_get_act_scales(self.h, arr, 21))
+        return [arr[i] for i in range(21)]
+
+    def calibrate(self, netin_bf16, n, height, width, stream=None):
+        check(lib().nrv_net_calibrate(self.h, _ptr(netin_bf16), n, height, width, _stream(stream)))
 
     def shade(self, netin, n, height, width, prec, rgb, stream=None):
         check(lib().nrv_shade(self.h, _ptr(netin), n, height, width, prec, _ptr(rgb), _stream(stream)))

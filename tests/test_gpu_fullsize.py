@@ -1,0 +1,89 @@
+"""Full-size parity of the render and resolve passes (Sec. 3.2) on the benchmark workloads:
+keys and G-buffer planes bit-exact against the CPU oracle for whole frames, for every variant
+of the render pass (the launcher picks one by timing; each must give identical keys), plus the
+BF16 network on the full 1080p trajectory frame against the float64 oracle."""
+import os
+
+import numpy as np
+import pytest
+
+import nrv_inputs as I
+import oracle
+from gpu_util import gpu_raster, make_params, psnr_range, torch_dev, upload_scene
+from oracle import unet
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def trajectories():
+    return I.trajectory_scene(1_000_000, 350, seed=2)        # 350M points
+
+
+def _with_variant(i, fn):
+    os.environ["NRV_VIS_VARIANT"] = str(i)
+    try:
+        return fn()
+    finally:
+        del os.environ["NRV_VIS_VARIANT"]
+
+
+def test_trajectories_350m_1080p_every_variant(trajectories):
+    from paper_2407_19097_gb300 import nrv
+    sc = trajectories
+    view = I.fitted_view(sc, 1920, 1080)
+    scene = upload_scene(sc)
+    ref = oracle.rasterize(sc, view)
+    for i in range(6):
+        got = _with_variant(i, lambda: gpu_raster(scene, [view]))[0]
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b), f"variant {i} differs"
+    got = gpu_raster(scene, [view])[0]          # the tuned choice
+    assert np.array_equal(got[0], ref[0])
+    assert (ref[2] > 0).mean() > 0.05
+
+
+def test_vortex_grid_50m_1080p():
+    sc = I.vortex_grid_scene(368, seed=1)                       # 49.8M points
+    view = I.cube_view(1920, 1080)
+    scene = upload_scene(sc)
+    got = gpu_raster(scene, [view])[0]
+    ref = oracle.rasterize(sc, view)
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+
+
+def test_terrain_200m_eight_views_every_variant():
+    sc = I.terrain_scene(14142, seed=7)                         # 200M points
+    sizes = [(2160, 2160), (2160, 2160), (1920, 1080), (1920, 1080), (1920, 1080), (1920, 1080),
+             (960, 540), (960, 540)]
+    views = I.orbit_views(sc, sizes, seed=11, stereo_pairs=1)
+    scene = upload_scene(sc)
+    keys = [oracle.visibility(sc.xyz, v) for v in views]
+    for i in range(4):
+        got = _with_variant(i, lambda: gpu_raster(scene, views, planes=False))
+        for v, (g,), k in zip(views, got, keys):
+            assert np.array_equal(g, k), f"variant {i} differs"
+
+
+def test_network_bf16_full_frame(trajectories):
+    import torch
+    from paper_2407_19097_gb300 import nrv
+    sc = trajectories
+    view = I.fitted_view(sc, 1920, 1080)
+    scene = upload_scene(sc)
+    c0 = len(sc.channels) + 2
+    flat = make_params(c0, seed=1)
+    net = nrv.Net(c0)
+    net.set_params(torch.from_numpy(flat).to(torch_dev()))
+    ds, do = I.depth_normalisation(sc, view)
+    desc = nrv.make_pack_desc(sc.channels, ds, do)
+    out = torch.empty((1080, 1920, 3), device=torch_dev())
+    nrv.render_batch(scene, net, desc, [view], [out], nrv.PREC_BF16)
+    torch.cuda.synchronize()
+    _, d, m, g = oracle.rasterize(sc, view)
+    xb = oracle.pack(d, m, g, sc.channels, ds, do, 1080, 1920, 8, 1)
+    x = oracle.bf16_value(xb).astype(np.float64)
+    ref = unet.forward(x[None, :, :, :c0], unet.unflatten(flat, c0))[0]
+    got = out.cpu().numpy()
+    assert psnr_range(got, ref) >= 45.0 and np.abs(got - ref).max() <= 2e-2
