@@ -19,22 +19,28 @@ __device__ __forceinline__ uint8_t enc8(float f) {
     return __nv_cvt_float_to_fp8(f, __NV_SATFINITE, __NV_E4M3);
 }
 
-// y = E4M3(mean of the 2x2 window), input and output share one scale; 16 channels per thread.
+// y = E4M3(mean of the 2x2 window), input and output share one scale.  Tensors
+// are row-planar (planes of 16 channels x w pixels per image row); one thread
+// makes one 16-byte output chunk, pixels fastest.
 __global__ void pool2_fp8_kernel(const uint8_t* __restrict__ x, uint8_t* __restrict__ y, int c,
                                  int n, int ho, int wo) {
-    const size_t total = (size_t)n * ho * wo * (c / 16);
+    const int nch = c / 16;
+    const size_t total = (size_t)n * ho * wo * nch;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
          i += (size_t)gridDim.x * blockDim.x) {
-        const int cg = (int)(i % (c / 16)) * 16;
-        const size_t q = i / (c / 16);
-        const int xo = (int)(q % wo), yo = (int)((q / wo) % ho);
-        const size_t img = q / ((size_t)wo * ho);
+        const int xo = (int)(i % wo);
+        const int ch = (int)((i / wo) % nch);
+        const size_t row = i / ((size_t)wo * nch);   // img * ho + yo
+        const int yo = (int)(row % ho);
+        const size_t img = row / ho;
         const int wi = 2 * wo;
-        const size_t q00 = (img * 2 * ho + 2 * yo) * wi + 2 * xo;
-        const uint4 a = *reinterpret_cast<const uint4*>(x + q00 * c + cg);
-        const uint4 b = *reinterpret_cast<const uint4*>(x + (q00 + 1) * c + cg);
-        const uint4 d = *reinterpret_cast<const uint4*>(x + (q00 + wi) * c + cg);
-        const uint4 e = *reinterpret_cast<const uint4*>(x + (q00 + wi + 1) * c + cg);
+        const size_t r0 = img * 2 * ho + 2 * yo;
+        const uint8_t* p0 = x + ((r0 * nch + ch) * wi + 2 * xo) * 16;
+        const uint8_t* p1 = x + (((r0 + 1) * nch + ch) * wi + 2 * xo) * 16;
+        const uint4 a = *reinterpret_cast<const uint4*>(p0);
+        const uint4 b = *reinterpret_cast<const uint4*>(p0 + 16);
+        const uint4 d = *reinterpret_cast<const uint4*>(p1);
+        const uint4 e = *reinterpret_cast<const uint4*>(p1 + 16);
         const uint8_t* pa = reinterpret_cast<const uint8_t*>(&a);
         const uint8_t* pb = reinterpret_cast<const uint8_t*>(&b);
         const uint8_t* pd = reinterpret_cast<const uint8_t*>(&d);
@@ -44,11 +50,12 @@ __global__ void pool2_fp8_kernel(const uint8_t* __restrict__ x, uint8_t* __restr
 #pragma unroll
         for (int k = 0; k < 16; ++k)
             po[k] = enc8(0.25f * ((dec8(pa[k]) + dec8(pb[k])) + (dec8(pd[k]) + dec8(pe[k]))));
-        *reinterpret_cast<uint4*>(y + q * c + cg) = o;
+        *reinterpret_cast<uint4*>(y + i * 16) = o;
     }
 }
 
-// rgb[o] = bias[o] + sum_c W[o][c] * (x_c * s), cropped to h x wd.
+// rgb[o] = bias[o] + sum_c W[o][c] * (x_c * s), cropped to h x wd (16 channels:
+// one plane, so the row-planar tensor is also plain NHWC).
 __global__ void head_fp8_kernel(const uint8_t* __restrict__ x, float s, const float* w,
                                 const float* bias, float* rgb, int n, int hn, int wn, int h,
                                 int wd) {

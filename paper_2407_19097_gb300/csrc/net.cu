@@ -181,8 +181,10 @@ template <typename T>
 static nrv_status forward_t(Net* net, const T* netin, float* rgb, cudaStream_t s, bool use_tc,
                             nrv_prec prec) {
     const Geo& g = net->geo;
-    auto V = [&](int a) { return TView<T>{act<T>(net, a), net->act_c[a]}; };
-    auto CV = [&](int a) { return TView<const T>{act<T>(net, a), net->act_c[a]}; };
+    // BF16 activations are row-planar (the tensor-core layout), FP32 ones NHWC
+    const int planar = sizeof(T) == 2 ? 1 : 0;
+    auto V = [&](int a) { return TView<T>{act<T>(net, a), net->act_c[a], planar}; };
+    auto CV = [&](int a) { return TView<const T>{act<T>(net, a), net->act_c[a], planar}; };
     auto conv = [&](int l, TView<const T> x1, int c1, TView<const T> x2, int c2, int out,
                     int level) -> nrv_status {
         if (use_tc) {
@@ -213,7 +215,7 @@ static nrv_status forward_t(Net* net, const T* netin, float* rgb, cudaStream_t s
         (void)L;
         return simt_upconv<T>(net, l, CV(in), V(out), g.n, g.h[level_in], g.w[level_in], s);
     };
-    const TView<const T> x{netin, net->c0p};
+    const TView<const T> x{netin, net->c0p, planar};   // one plane: also plain NHWC
     const TView<const T> none{nullptr, 0};
     NRV_TRY(conv(L_E0A, x, net->c0p, none, 0, A_E0A, 0));
     NRV_TRY(conv(L_E0B, CV(A_E0A), 16, none, 0, A_E0B, 0));
@@ -272,77 +274,98 @@ nrv_status net_forward(Net* net, const void* netin, int n, int H, int W, nrv_pre
 
 namespace nrv {
 
-// One layer alone (nrv_net_run_layer): same kernels and dispatch as the forward pass.
+// 16-byte chunks between NHWC and row-planar order: `rows` image rows of w
+// pixels with nch chunks each (planar index (row * nch + ch) * w + x).
+__global__ void relayout_kernel(const uint4* __restrict__ src, uint4* __restrict__ dst, size_t rows,
+                                int w, int nch, int to_planar) {
+    const size_t total = rows * (size_t)w * nch;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % w);
+        const size_t t = i / w;
+        const int ch = (int)(t % nch);
+        const size_t row = t / nch;
+        const size_t nhwc = (row * w + x) * nch + ch;
+        if (to_planar) dst[i] = src[nhwc];
+        else dst[nhwc] = src[i];
+    }
+}
+
+static nrv_status relayout(const void* src, void* dst, size_t rows, int w, int c, size_t es,
+                           bool to_planar, cudaStream_t s) {
+    const int nch = (int)(c * es / 16);
+    relayout_kernel<<<blocks_for(rows * w * nch), 256, 0, s>>>((const uint4*)src, (uint4*)dst, rows,
+                                                               w, nch, to_planar ? 1 : 0);
+    NRV_CHECK_LAUNCH();
+    return NRV_OK;
+}
+
+// One layer alone (nrv_net_run_layer): same kernels and dispatch as the forward
+// pass.  The caller's tensors are NHWC; BF16 and FP8 layers run on row-planar
+// copies in the handle's scratch, as inside the network.
 nrv_status net_run_layer(Net* net, int l, const void* x1, const void* x2, int n, int h, int w,
                          nrv_prec prec, void* y, cudaStream_t s) {
     NRV_TRY(set_kernel_attrs());
     const Layer& L = net->layers[l];
-    if (L.kind == UPCONV2) {
-        if (x2) return fail(NRV_ERR_ARG, "layer %s: x2 must be NULL", L.name);
-        Geo g;
-        memset(&g, 0, sizeof(g));
-        g.n = n;
-        g.h[0] = h;
-        g.w[0] = w;
-        if (prec == NRV_PREC_BF16) {
-            nrv_status st = tc_upconv(net, l, x1, y, g, 0, prec, s);
-            net->backend[l] = 1;
-            if (st != NRV_ERR_UNSUPPORTED) return st;
-            clear_error();
-            net->backend[l] = 0;
-            using T = __nv_bfloat16;
-            return simt_upconv<T>(net, l, TView<const T>{(const T*)x1, L.cin},
-                                  TView<T>{(T*)y, L.cout}, n, h, w, s);
+    const bool up = L.kind == UPCONV2;
+    int c1 = L.cin, c2 = 0;
+    if (!up) {
+        c1 = l == L_E0A ? (prec == NRV_PREC_FP8 ? 16 : net->c0p) : L.cin;
+        if (l == L_D2A || l == L_D1A || l == L_D0A) {
+            c1 = L.cin / 2;
+            c2 = L.cin / 2;
         }
-        if (prec == NRV_PREC_F32) {
-            net->backend[l] = 0;
-            return simt_upconv<float>(net, l, TView<const float>{(const float*)x1, L.cin},
-                                      TView<float>{(float*)y, L.cout}, n, h, w, s);
-        }
-        if (prec == NRV_PREC_FP8) {
-            int in1, in2, out;
-            layer_scale_index(l, &in1, &in2, &out);
-            net->backend[l] = 1;
-            return tc_upconv(net, l, x1, y, g, 0, prec, s, 1.0f / net->act_scale[out]);
-        }
-        return fail(NRV_ERR_UNSUPPORTED, "nrv_net_run_layer: unknown precision");
     }
-    int c1 = l == L_E0A ? (prec == NRV_PREC_FP8 ? 16 : net->c0p) : L.cin, c2 = 0;
-    if (l == L_D2A || l == L_D1A || l == L_D0A) {
-        c1 = L.cin / 2;
-        c2 = L.cin / 2;
-    }
-    if ((c2 > 0) != (x2 != nullptr)) return fail(NRV_ERR_ARG, "layer %s: x2 must be %s", L.name,
-                                                 c2 ? "given" : "NULL");
+    if ((c2 > 0) != (x2 != nullptr))
+        return fail(NRV_ERR_ARG, "layer %s: x2 must be %s", L.name, c2 ? "given" : "NULL");
     Geo g;
     memset(&g, 0, sizeof(g));
     g.n = n;
     g.h[0] = h;
     g.w[0] = w;
-    if (prec == NRV_PREC_BF16) {
-        nrv_status st = tc_conv3(net, l, x1, c1, x2, c2, y, g, 0, prec, s);
-        net->backend[l] = 1;
-        if (st != NRV_ERR_UNSUPPORTED) return st;
-        clear_error();
-        net->backend[l] = 0;
-        using T = __nv_bfloat16;
-        return simt_conv3<T>(net, l, TView<const T>{(const T*)x1, c1}, c1,
-                             TView<const T>{(const T*)x2, c2}, c2, TView<T>{(T*)y, L.cout}, g, 0,
-                             true, s);
-    }
     if (prec == NRV_PREC_F32) {
         net->backend[l] = 0;
+        if (up)
+            return simt_upconv<float>(net, l, TView<const float>{(const float*)x1, L.cin},
+                                      TView<float>{(float*)y, L.cout}, n, h, w, s);
         return simt_conv3<float>(net, l, TView<const float>{(const float*)x1, c1}, c1,
                                  TView<const float>{(const float*)x2, c2}, c2,
                                  TView<float>{(float*)y, L.cout}, g, 0, true, s);
     }
+    if (prec != NRV_PREC_BF16 && prec != NRV_PREC_FP8)
+        return fail(NRV_ERR_UNSUPPORTED, "nrv_net_run_layer: unknown precision");
+    const size_t es = elem_size(prec);
+    const size_t rows_in = (size_t)n * h, rows_out = up ? 2 * rows_in : rows_in;
+    const int w_out = up ? 2 * w : w;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t b1 = al(rows_in * w * c1 * es), b2 = al(rows_in * w * c2 * es);
+    const size_t by = al(rows_out * w_out * L.cout * es);
+    NRV_TRY(net->layer_ws.ensure(b1 + b2 + by));
+    char* ws = (char*)net->layer_ws.p;
+    void *p1 = ws, *p2 = c2 ? ws + b1 : nullptr, *py = ws + b1 + b2;
+    NRV_TRY(relayout(x1, p1, rows_in, w, c1, es, true, s));
+    if (c2) NRV_TRY(relayout(x2, p2, rows_in, w, c2, es, true, s));
+    float inv_out = 1.0f;
     if (prec == NRV_PREC_FP8) {
         int in1, in2, out;
         layer_scale_index(l, &in1, &in2, &out);
-        net->backend[l] = 1;
-        return tc_conv3(net, l, x1, c1, x2, c2, y, g, 0, prec, s, 1.0f / net->act_scale[out]);
+        inv_out = 1.0f / net->act_scale[out];
     }
-    return fail(NRV_ERR_UNSUPPORTED, "nrv_net_run_layer: unknown precision");
+    nrv_status st = up ? tc_upconv(net, l, p1, py, g, 0, prec, s, inv_out)
+                       : tc_conv3(net, l, p1, c1, p2, c2, py, g, 0, prec, s, inv_out);
+    net->backend[l] = 1;
+    if (st == NRV_ERR_UNSUPPORTED && prec == NRV_PREC_BF16) {
+        clear_error();
+        net->backend[l] = 0;
+        using T = __nv_bfloat16;
+        st = up ? simt_upconv<T>(net, l, TView<const T>{(const T*)p1, L.cin, 1},
+                                 TView<T>{(T*)py, L.cout, 1}, n, h, w, s)
+                : simt_conv3<T>(net, l, TView<const T>{(const T*)p1, c1, 1}, c1,
+                                TView<const T>{(const T*)p2, c2, 1}, c2,
+                                TView<T>{(T*)py, L.cout, 1}, g, 0, true, s);
+    }
+    NRV_TRY(st);
+    return relayout(py, y, rows_out, w_out, L.cout, es, false, s);
 }
 
 }  // namespace nrv

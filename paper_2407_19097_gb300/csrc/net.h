@@ -58,6 +58,7 @@ struct Net {
     DevBuf tmaps;            // device copies of TMA descriptors (unused when passed by value)
     // render-batch resources
     DevBuf batch_ws;
+    DevBuf layer_ws;         // row-planar copies for nrv_net_run_layer
 };
 
 size_t elem_size(nrv_prec p);

@@ -1,7 +1,8 @@
 // SIMT kernels of the post-processing U-Net (Sec. 3.3): the FP32 form of the
 // network, and the small memory-bound layers (pooling, transposed conv, head)
-// of every precision.  Tensors are NHWC views {ptr, channel stride}; storage is
-// float or bfloat16, arithmetic always FP32 with FMA.
+// of every precision.  Tensors are views {ptr, channels, layout} in NHWC or in
+// the row-planar layout of the tensor-core path (see TView); storage is float
+// or bfloat16, arithmetic always FP32 with FMA.
 #pragma once
 #include "internal.h"
 
@@ -48,10 +49,23 @@ template <> __device__ __forceinline__ void st8<__nv_bfloat16>(__nv_bfloat16* p,
     *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
+// A tensor of `ld` channels per pixel, rows of w pixels (w passed per access).
+//  planar == 0: NHWC, element (row, x, c) at (row * w + x) * ld + c;
+//  planar == 1: row-planar, the layout of the BF16 / FP8 activations of the
+//     tensor-core path: each image row holds its channels as ld / ce planes of
+//     w pixels x 16 bytes (ce = 16 / sizeof(T) channels per plane), so element
+//     (row, x, c) sits at ((row * (ld / ce) + c / ce) * w + x) * ce + c % ce.
+// Accesses of 8 channels start at a multiple of 8, inside one plane.
 template <typename T>
 struct TView {
     T* p;
-    int ld;   // elements between consecutive pixels
+    int ld;          // channels per pixel
+    int planar = 0;
+    __device__ __forceinline__ T* at(size_t row, int x, int c, int w) const {
+        if (!planar) return p + (row * (size_t)w + x) * ld + c;
+        constexpr int ce = 16 / (int)sizeof(T);
+        return p + ((row * (size_t)(ld / ce) + c / ce) * w + x) * ce + c % ce;
+    }
 };
 
 // ---------------------------------------------------------------- 3x3 conv
@@ -95,12 +109,12 @@ __global__ void __launch_bounds__(128) conv3_simt_kernel(Conv3Args<T> a) {
     for (int tap = 0; tap < 9; ++tap) {
         const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
         if (yy < 0 || yy >= a.h || xx < 0 || xx >= a.w_) continue;
-        const size_t qq = (img * a.h + yy) * a.w_ + xx;
+        const size_t rr = img * a.h + yy;
         const float* wt = ws + (size_t)tap * cin * 16;
         for (int c = 0; c < cin; c += 8) {
             float v[8];
-            if (c < a.c1) ld8<T>(a.x1.p + qq * a.x1.ld + c, v);
-            else ld8<T>(a.x2.p + qq * a.x2.ld + (c - a.c1), v);
+            if (c < a.c1) ld8<T>(a.x1.at(rr, xx, c, a.w_), v);
+            else ld8<T>(a.x2.at(rr, xx, c - a.c1, a.w_), v);
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const float4* w4 = reinterpret_cast<const float4*>(wt + (c + k) * 16);
@@ -119,38 +133,50 @@ __global__ void __launch_bounds__(128) conv3_simt_kernel(Conv3Args<T> a) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) acc[j] = fmaxf(acc[j], 0.0f);
     }
+    const size_t row = img * a.h + y;
     if (a.mask.p) {
         float m[16];
-        ld8<T>(a.mask.p + q * a.mask.ld + og, m);
-        ld8<T>(a.mask.p + q * a.mask.ld + og + 8, m + 8);
+        ld8<T>(a.mask.at(row, x, og, a.w_), m);
+        ld8<T>(a.mask.at(row, x, og + 8, a.w_), m + 8);
 #pragma unroll
         for (int j = 0; j < 16; ++j) acc[j] = m[j] > 0.0f ? acc[j] : 0.0f;
     }
-    T* yp = a.y.p + q * a.y.ld + og;
-    st8<T>(yp, acc);
-    st8<T>(yp + 8, acc + 8);
+    st8<T>(a.y.at(row, x, og, a.w_), acc);
+    st8<T>(a.y.at(row, x, og + 8, a.w_), acc + 8);
 }
 
 // ---------------------------------------------------------------- 2x2 average pool
+// Threads walk the channel groups fastest for NHWC and the pixels fastest for
+// row-planar tensors, so neighbouring threads touch neighbouring bytes.
 template <typename T>
 __global__ void pool2_kernel(TView<const T> x, TView<T> y, int c, int n, int ho, int wo) {
-    const size_t total = (size_t)n * ho * wo * (c / 8);
+    const int ng = c / 8;
+    const size_t total = (size_t)n * ho * wo * ng;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
          i += (size_t)gridDim.x * blockDim.x) {
-        const int cg = (int)(i % (c / 8)) * 8;
-        const size_t q = i / (c / 8);
-        const int xo = (int)(q % wo), yo = (int)((q / wo) % ho);
-        const size_t img = q / ((size_t)wo * ho);
+        int cg, xo;
+        size_t row;   // output row img * ho + yo
+        if (y.planar) {
+            xo = (int)(i % wo);
+            cg = (int)((i / wo) % ng) * 8;
+            row = i / ((size_t)wo * ng);
+        } else {
+            cg = (int)(i % ng) * 8;
+            xo = (int)((i / ng) % wo);
+            row = i / ((size_t)ng * wo);
+        }
+        const int yo = (int)(row % ho);
+        const size_t img = row / ho;
         const int wi = 2 * wo;
-        const size_t q00 = (img * 2 * ho + 2 * yo) * wi + 2 * xo;
+        const size_t r0 = img * 2 * ho + 2 * yo;
         float a[8], b[8], cc[8], d[8], r[8];
-        ld8<T>(x.p + q00 * x.ld + cg, a);
-        ld8<T>(x.p + (q00 + 1) * x.ld + cg, b);
-        ld8<T>(x.p + (q00 + wi) * x.ld + cg, cc);
-        ld8<T>(x.p + (q00 + wi + 1) * x.ld + cg, d);
+        ld8<T>(x.at(r0, 2 * xo, cg, wi), a);
+        ld8<T>(x.at(r0, 2 * xo + 1, cg, wi), b);
+        ld8<T>(x.at(r0 + 1, 2 * xo, cg, wi), cc);
+        ld8<T>(x.at(r0 + 1, 2 * xo + 1, cg, wi), d);
 #pragma unroll
         for (int k = 0; k < 8; ++k) r[k] = 0.25f * ((a[k] + b[k]) + (cc[k] + d[k]));
-        st8<T>(y.p + q * y.ld + cg, r);
+        st8<T>(y.at(row, xo, cg, wo), r);
     }
 }
 
@@ -175,22 +201,22 @@ __global__ void __launch_bounds__(128) upconv2_kernel(TView<const T> x, int cin,
     if (q >= (size_t)n * ho * wo) return;
     const int X = (int)(q % wo), Y = (int)((q / wo) % ho);
     const size_t img = q / ((size_t)wo * ho);
-    const size_t qi = (img * hi + Y / 2) * wi + X / 2;
+    const size_t ri = img * hi + Y / 2;
     const float* wt = ws + (size_t)((Y & 1) * 2 + (X & 1)) * cin * 16;
     float acc[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) acc[j] = bias[og + j];
     for (int c = 0; c < cin; c += 8) {
         float v[8];
-        ld8<T>(x.p + qi * x.ld + c, v);
+        ld8<T>(x.at(ri, X / 2, c, wi), v);
 #pragma unroll
         for (int k = 0; k < 8; ++k)
 #pragma unroll
             for (int j = 0; j < 16; ++j) acc[j] = fmaf(v[k], wt[(c + k) * 16 + j], acc[j]);
     }
-    T* yp = y.p + q * y.ld + og;
-    st8<T>(yp, acc);
-    st8<T>(yp + 8, acc + 8);
+    const size_t ro = img * ho + Y;
+    st8<T>(y.at(ro, X, og, wo), acc);
+    st8<T>(y.at(ro, X, og + 8, wo), acc + 8);
 }
 
 // Backward data pass of the transposed conv, masked by (xin > 0) (the input was
@@ -216,24 +242,26 @@ __global__ void __launch_bounds__(128) upconv2_dgrad_kernel(TView<const T> g, in
 #pragma unroll
     for (int k = 0; k < 16; ++k) acc[k] = 0.0f;
     for (int ab = 0; ab < 4; ++ab) {
-        const size_t qo = (img * 2 * hi + 2 * Y + (ab >> 1)) * (2 * wi) + 2 * X + (ab & 1);
+        const size_t ro = img * 2 * hi + 2 * Y + (ab >> 1);
+        const int xo = 2 * X + (ab & 1);
         const float* wt = ws + (size_t)ab * 16 * cout;
         for (int o = 0; o < cout; o += 8) {
             float v[8];
-            ld8<T>(g.p + qo * g.ld + o, v);
+            ld8<T>(g.at(ro, xo, o, 2 * wi), v);
 #pragma unroll
             for (int m = 0; m < 8; ++m)
 #pragma unroll
                 for (int k = 0; k < 16; ++k) acc[k] = fmaf(v[m], wt[k * cout + o + m], acc[k]);
         }
     }
+    const size_t ri = img * hi + Y;
     float mk[16];
-    ld8<T>(xin.p + q * xin.ld + cg, mk);
-    ld8<T>(xin.p + q * xin.ld + cg + 8, mk + 8);
+    ld8<T>(xin.at(ri, X, cg, wi), mk);
+    ld8<T>(xin.at(ri, X, cg + 8, wi), mk + 8);
 #pragma unroll
     for (int k = 0; k < 16; ++k) acc[k] = mk[k] > 0.0f ? acc[k] : 0.0f;
-    st8<T>(gx.p + q * gx.ld + cg, acc);
-    st8<T>(gx.p + q * gx.ld + cg + 8, acc + 8);
+    st8<T>(gx.at(ri, X, cg, wi), acc);
+    st8<T>(gx.at(ri, X, cg + 8, wi), acc + 8);
 }
 
 // ---------------------------------------------------------------- 1x1 head -> RGB (cropped)
@@ -245,10 +273,10 @@ __global__ void head_kernel(TView<const T> x, const float* w, const float* bias,
          i += (size_t)gridDim.x * blockDim.x) {
         const int X = (int)(i % wd), Y = (int)((i / wd) % h);
         const size_t img = i / ((size_t)wd * h);
-        const size_t q = (img * hn + Y) * wn + X;
+        const size_t r = img * hn + Y;
         float v[16];
-        ld8<T>(x.p + q * x.ld, v);
-        ld8<T>(x.p + q * x.ld + 8, v + 8);
+        ld8<T>(x.at(r, X, 0, wn), v);
+        ld8<T>(x.at(r, X, 8, wn), v + 8);
 #pragma unroll
         for (int o = 0; o < 3; ++o) {
             float s = bias[o];

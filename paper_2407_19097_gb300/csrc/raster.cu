@@ -371,7 +371,7 @@ nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, 
                 NRV_CHECK_CUDA(cudaEventSynchronize(e1));
                 NRV_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
             }
-            if (verbose()) fprintf(stderr, "nrv: render pass %-26s %.3f ms\n", tab[i].name, ms);
+            if (verbose()) fprintf(stderr, "nrv: render pass %d %-26s %.3f ms\n", i, tab[i].name, ms);
             if (ms < best) {
                 best = ms;
                 arg = i;

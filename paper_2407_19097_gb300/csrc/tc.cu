@@ -1,27 +1,45 @@
 // Tensor-core 3x3 convolution of the U-Net (Sec. 3.3) as an implicit GEMM on the
-// 5th-generation tensor cores (tcgen05 + TMEM), BF16 operands, FP32 accumulation.
+// 5th-generation tensor cores (tcgen05 + TMEM), BF16 or E4M3 operands, FP32
+// accumulation.
 //
-//   D[m][n] = sum_k A[m][k] * B[n][k],   m = 128 consecutive pixels of one row,
+//   D[m][n] = sum_k A[m][k] * B[n][k],   m = output pixel of a row tile,
 //   n = output channel, k = (tap, input channel) -- K = 9 * C_in.
 //
-// A tile of 128 output pixels needs the input rows y-1..y+1 and pixels
-// x0-1..x0+128 ("halo").  One 5-D TMA load brings them into shared memory as
-// planes of [pixel][8 channels] (16 bytes per pixel): plane (row, chunk) holds
-// 130 pixels.  Each tap's A operand is then just a shared-memory descriptor
-// pointing dx pixels into the plane of row dy -- the nine taps share one copy
-// of the data, zero padding comes from TMA's out-of-bounds fill.  Operands use
-// the no-swizzle K-major layout: core matrices of 8 rows x 16 bytes, rows 16
-// bytes apart (SBO = 128 bytes between 8-row groups), the two 8-element K
-// halves of one MMA (K = 16) LBO bytes apart.
+// Activations are stored row-planar: each image row holds its channels as
+// planes of W pixels x 16 bytes (8 BF16 or 16 E4M3 channels per plane).  One
+// 4-D TMA load (box: 128 pixels x all planes of one row) brings an input row
+// into a shared-memory slot as planes of 128 pixels; every plane is one
+// contiguous 2 KB run in global memory.  A tile makes 126 output pixels
+// x0..x0+125 from the 128 loaded pixels x0-1..x0+126 of the rows y-1, y, y+1;
+// each tap's A operand is a shared-memory descriptor pointing dx pixels into
+// the plane of its row, so the nine taps share one copy of the data and zero
+// padding comes from TMA's out-of-bounds fill.  The MMA still computes 128
+// rows; rows 126 and 127 read past their plane (into slack) and are dropped.
+//
+// Each CTA walks a contiguous run of tiles down the image rows of one tile
+// column, so input rows sit in a ring of slots: a tile loads only the one row
+// it adds, and a slot is released (by tcgen05.commit) once the following tile
+// no longer reads it.  Operands use the no-swizzle K-major layout: core
+// matrices of 8 rows x 16 bytes, rows 16 bytes apart (SBO = 128 bytes between
+// 8-row groups), the two 16-byte K halves of one MMA LBO bytes apart -- both
+// halves always come from the same row slot.
 //
 // The weights of the CTA's output-channel slice stay resident in shared memory
-// ([k-step][half][n][8] BF16).  Warp roles: warp 0 issues TMA loads, warp 1
+// ([k-step][half][n][16 bytes]).  Warp roles: warp 0 issues TMA loads, warp 1
 // owns TMEM and issues the MMAs, warps 2-5 drain the FP32 accumulator
-// (tcgen05.ld), add the bias, apply ReLU and store BF16 NHWC.  Halo buffers and
-// accumulators are double-buffered so loads, MMAs and the epilogue overlap
-// across the CTA's pixel tiles.  Every wait is bounded: on timeout the kernel
-// records STATUS_TIMEOUT in the status word, drains what it started, frees TMEM
-// and returns.
+// (tcgen05.ld), scale, add the bias, apply ReLU and store row-planar output.
+// Accumulators are double-buffered.  The MMA issue loop is kept free of
+// branches and of dependent parameter loads (the operand kind is a template
+// parameter, the per-K-step descriptor words sit in shared memory and are read
+// one step ahead): with narrow N the issuing thread, not the tensor pipe, sets
+// the pace.  Every wait is bounded: on timeout the
+// kernel records STATUS_TIMEOUT in the status word, waits (bounded) for its
+// own copies in flight, frees TMEM and returns.
+//
+// The 2x2 stride-2 transposed conv runs through the same kernel as a GEMM of
+// one input row (K = C_in, tiles of 128 pixels, no halo) against all four
+// kernel positions at once (N = 4 C_out); its epilogue scatters column
+// (2a + b) * C_out + o to output pixel (2y + a, 2x + b).
 #include <cuda.h>
 #include <string.h>
 
@@ -31,38 +49,43 @@ namespace nrv {
 
 namespace {
 
-constexpr int HALO_W = 130;
-constexpr int PLANE = HALO_W * 16;  // bytes of one (row, 8-channel chunk) plane
+constexpr int PLANE = 2048;   // bytes of one (row, 16-byte channel chunk) plane: 128 pixels
 constexpr int MAX_KS = 80;
+constexpr int MAX_SLOTS = 8;
 constexpr int TILE_M = 128;
 constexpr int NTHREADS = 192;
 
 struct TcParams {
-    int n, h, w;             // level geometry
-    int tiles_x, num_ptiles; // pixel tiles
+    int n, h, w;             // input level geometry
+    int tile_w;              // output pixels per tile (126 conv, 128 transposed conv)
+    int xoff;                // first loaded pixel relative to the tile's first pixel
+    int tiles_x, ntiles;     // tiles per row, tiles per slice (n * tiles_x * h)
+    int ctas_per_slice;
     int nslices, n_slice;    // output-channel slices and their width
-    int nks;                 // K-steps of 16 channels
-    int nbuf;                // halo buffers (1..4)
-    int cout;                // output channels (pixel stride of the output)
+    int nks;                 // K-steps (two 16-byte halves each)
+    int rows, row0;          // input rows per tile, first one relative to the tile's row
+    int nslot;               // row slots in the ring
+    int cout;                // output channels
+    int out_nch;             // 16-byte planes per output row
     int mode;                // 0: 3x3 conv + bias + ReLU; 1: 2x2 stride-2 transposed conv + bias
-    int row0;                // first halo row relative to the tile's row (-1 conv, 0 transposed)
     int has_src2;
-    uint32_t halo_bytes;     // bytes of one halo buffer (both sources)
-    uint32_t src2_off;       // offset of source 2 planes inside a buffer
-    uint32_t tx1, tx2;       // bytes delivered by each TMA load
+    uint32_t slot_bytes;     // bytes of one row slot (both sources, plus read slack)
+    uint32_t src2_off;       // offset of source 2 planes inside a slot
+    uint32_t tx_bytes;       // bytes one row load delivers (both sources)
     uint32_t w_bytes;        // bytes of one weight slice
     uint32_t w_region;       // bytes reserved for the weights (aligned)
     uint32_t idesc;
     uint32_t tmem_cols;
     const uint8_t* wpk;      // packed weights [slice][ks][half][n][16 bytes] (BF16 or E4M3)
     const float* bias;
-    void* y;                 // BF16 or E4M3 NHWC output
+    void* y;                 // BF16 or E4M3 row-planar output
     unsigned* status;
     int fp8;                 // E4M3 operands (kind::f8f6f4) and an E4M3 output
     float inv_out;           // FP8: 1 / scale of the output tensor
     const float* colscale;   // FP8: per GEMM column, input scale x weight scale
-    uint32_t a_off[MAX_KS];  // A start offset in the halo buffer, per K-step
-    uint32_t a_lbo[MAX_KS];  // A K-direction byte offset (second half), per K-step
+    // per K-step: low word of the A descriptor relative to its row slot,
+    // (offset >> 4) | (LBO >> 4) << 16, with the row (0..2) in bits 30-31
+    uint32_t a_lo[MAX_KS];
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -88,26 +111,29 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// One test of the phase; the thread may be suspended (up to the hint, 0.5 ms)
+// until the phase completes, so waiting warps do not spin on the issue slots.
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(500000u)
         : "memory");
     return ok != 0;
 }
 
-// Bounded wait (about 2 s): false on timeout or when another role aborted.
+// Bounded wait (about 2 s): false on timeout or, when heed_abort, as soon as
+// another role has aborted.
 __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                          unsigned* status) {
+                          unsigned* status, bool heed_abort = true) {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (true) {
         if (mbar_try(bar, parity)) return true;
-        if (*abort_flag) return false;
+        if (heed_abort && *abort_flag) return false;
         if (global_ns() - t0 > 2000000000ull) {
             *abort_flag = 1;
             atomicOr(status, STATUS_TIMEOUT);
@@ -116,12 +142,12 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_fla
     }
 }
 
-__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
-                                            int c2, int c3, int c4, uint32_t bar) {
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, uint32_t bar) {
     asm volatile(
-        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
         : "memory");
 }
 
@@ -132,12 +158,6 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
             dst),
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
-}
-
-// UMMA shared-memory descriptor, no swizzle (sm_100 format, version 1).
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
@@ -184,38 +204,52 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Tile t of a slice covers pixels [xt * tile_w, +tile_w) of row y of image img,
+// t = (img * tiles_x + xt) * h + y: consecutive tiles walk down one column.
+struct TileRef {
+    int col, y, img, xt;
+};
+__device__ __forceinline__ TileRef tile_of(const TcParams& P, int t) {
+    TileRef r;
+    r.col = t / P.h;
+    r.y = t - r.col * P.h;
+    r.img = r.col / P.tiles_x;
+    r.xt = r.col - r.img * P.tiles_x;
+    return r;
+}
+
+template <bool FP8>
 __global__ void __launch_bounds__(NTHREADS, 1)
     conv3_tc_kernel(const __grid_constant__ CUtensorMap tm1, const __grid_constant__ CUtensorMap tm2,
                     const __grid_constant__ TcParams P) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t bars[16];
+    __shared__ __align__(8) uint64_t bars[2 * MAX_SLOTS + 6];
     __shared__ float bias_s[256];
     __shared__ float colscale_s[256];
+    __shared__ uint32_t alo_s[MAX_KS + 1];
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const uint32_t s_w = smem_u32(smem);
-    const uint32_t s_halo = s_w + P.w_region;
+    const uint32_t s_ring = s_w + P.w_region;
     const uint32_t b_w = smem_u32(&bars[0]);
     auto b_hfull = [&](int i) { return smem_u32(&bars[1 + i]); };
-    auto b_hempty = [&](int i) { return smem_u32(&bars[5 + i]); };
-    auto b_afull = [&](int i) { return smem_u32(&bars[9 + i]); };
-    auto b_aempty = [&](int i) { return smem_u32(&bars[11 + i]); };
-    const uint32_t b_done = smem_u32(&bars[13]);
+    auto b_hempty = [&](int i) { return smem_u32(&bars[1 + MAX_SLOTS + i]); };
+    auto b_afull = [&](int i) { return smem_u32(&bars[1 + 2 * MAX_SLOTS + i]); };
+    auto b_aempty = [&](int i) { return smem_u32(&bars[3 + 2 * MAX_SLOTS + i]); };
+    const uint32_t b_done = smem_u32(&bars[5 + 2 * MAX_SLOTS]);
 
-    // this CTA's output-channel slice and its pixel tiles
+    // this CTA's output-channel slice and its run of tiles
     const int slice = blockIdx.x % P.nslices;
-    const int cta_in_slice = blockIdx.x / P.nslices;
-    const int ctas_per_slice = gridDim.x / P.nslices;
-    const int my_tiles = cta_in_slice < P.num_ptiles
-                             ? (P.num_ptiles - 1 - cta_in_slice) / ctas_per_slice + 1
-                             : 0;
+    const int cta = blockIdx.x / P.nslices;
+    const int t_begin = (int)(((long long)cta * P.ntiles) / P.ctas_per_slice);
+    const int t_end = (int)(((long long)(cta + 1) * P.ntiles) / P.ctas_per_slice);
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
         mbar_init(b_w, 1);
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < MAX_SLOTS; ++i) {
             mbar_init(b_hfull(i), 1);
             mbar_init(b_hempty(i), 1);
         }
@@ -230,8 +264,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // per output column of this slice: its bias (column n maps to channel n mod cout)
     for (int i = threadIdx.x; i < P.n_slice; i += NTHREADS) {
         bias_s[i] = P.bias[(slice * P.n_slice + i) % P.cout];
-        colscale_s[i] = P.fp8 ? P.colscale[slice * P.n_slice + i] : 1.0f;
+        colscale_s[i] = FP8 ? P.colscale[slice * P.n_slice + i] : 1.0f;
     }
+    for (int i = threadIdx.x; i <= MAX_KS; i += NTHREADS) alo_s[i] = i < P.nks ? P.a_lo[i] : 0u;
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_slot)),
@@ -246,102 +281,165 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            // weights once, then the halo of every tile
+            // weights once, then each input row once per run of tiles
             mbar_expect_tx(b_w, P.w_bytes);
             const uint8_t* src = P.wpk + (size_t)slice * P.w_bytes;
             for (uint32_t o = 0; o < P.w_bytes; o += 16384) {
                 const uint32_t len = P.w_bytes - o < 16384 ? P.w_bytes - o : 16384;
                 bulk_load(s_w + o, src + o, len, b_w);
             }
-            int issued = 0;
-            for (int i = 0; i < my_tiles; ++i) {
-                const int buf = i % P.nbuf, u = i / P.nbuf;
-                if (!mbar_wait(b_hempty(buf), (u & 1) ^ 1, &abort_flag, P.status)) break;
-                const int pt = cta_in_slice + i * ctas_per_slice;
-                const int xt = pt % P.tiles_x, rest = pt / P.tiles_x;
-                const int yr = rest % P.h, img = rest / P.h;
-                const uint32_t dst = s_halo + (uint32_t)buf * P.halo_bytes;
-                mbar_expect_tx(b_hfull(buf), P.tx1 + P.tx2);
-                tma_load_5d(dst, &tm1, 0, xt * TILE_M - 1, 0, yr + P.row0, img, b_hfull(buf));
-                if (P.has_src2)
-                    tma_load_5d(dst + P.src2_off, &tm2, 0, xt * TILE_M - 1, 0, yr + P.row0, img,
-                                b_hfull(buf));
-                issued = i + 1;
+            int seq = 0, cur_col = -1, next_row = 0;
+            bool ok = true;
+            for (int t = t_begin; ok && t < t_end; ++t) {
+                const TileRef r = tile_of(P, t);
+                if (r.col != cur_col) {
+                    cur_col = r.col;
+                    next_row = r.y + P.row0;
+                }
+                const int last = r.y + P.row0 + P.rows - 1;
+                // 8-byte elements: pixel x starts at element 2x (16-byte aligned)
+                const int xe = 2 * (r.xt * P.tile_w + P.xoff);
+                for (; next_row <= last; ++next_row, ++seq) {
+                    const int slot = seq % P.nslot, u = seq / P.nslot;
+                    if (!mbar_wait(b_hempty(slot), (u & 1) ^ 1, &abort_flag, P.status)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t dst = s_ring + (uint32_t)slot * P.slot_bytes;
+                    mbar_expect_tx(b_hfull(slot), P.tx_bytes);
+                    tma_load_4d(dst, &tm1, xe, 0, next_row, r.img, b_hfull(slot));
+                    if (P.has_src2)
+                        tma_load_4d(dst + P.src2_off, &tm2, xe, 0, next_row, r.img, b_hfull(slot));
+                }
             }
             // every load issued must have landed before the CTA may exit
-            for (int i = issued - P.nbuf > 0 ? issued - P.nbuf : 0; i < issued; ++i)
-                mbar_wait(b_hfull(i % P.nbuf), (i / P.nbuf) & 1, &abort_flag, P.status);
-            mbar_wait(b_w, 0, &abort_flag, P.status);
+            for (int q = seq - P.nslot > 0 ? seq - P.nslot : 0; q < seq; ++q)
+                mbar_wait(b_hfull(q % P.nslot), (q / P.nslot) & 1, &abort_flag, P.status, false);
+            mbar_wait(b_w, 0, &abort_flag, P.status, false);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             bool ok = mbar_wait(b_w, 0, &abort_flag, P.status);
+            // descriptor high words: SBO = 128 bytes, version 1; B: K halves n_slice * 16 bytes apart
+            const uint32_t hi = (128u >> 4) | (1u << 14);
             const uint32_t b_lbo = (uint32_t)P.n_slice * 16;
-            for (int i = 0; ok && i < my_tiles; ++i) {
-                const int buf = i % P.nbuf, u = i / P.nbuf;
+            const uint32_t b_lo0 = ((s_w >> 4) & 0x3FFFu) | ((b_lbo >> 4) << 16);
+            const uint32_t b_step = (2 * b_lbo) >> 4;
+            int seq_end = 0, cur_col = -1, next_row = 0, waited = 0, released = 0, i = 0;
+            for (int t = t_begin; ok && t < t_end; ++t, ++i) {
+                // the same row schedule as the loader
+                const TileRef r = tile_of(P, t);
+                if (r.col != cur_col) {
+                    cur_col = r.col;
+                    next_row = r.y + P.row0;
+                }
+                const int last = r.y + P.row0 + P.rows - 1;
+                if (next_row <= last) {
+                    seq_end += last - next_row + 1;
+                    next_row = last + 1;
+                }
+                const int first = seq_end - P.rows;   // load number of row y + row0
+                for (; waited < seq_end; ++waited)
+                    if (!mbar_wait(b_hfull(waited % P.nslot), (waited / P.nslot) & 1, &abort_flag,
+                                   P.status)) {
+                        ok = false;
+                        break;
+                    }
+                if (!ok) break;
                 const int ab = i & 1, ua = i >> 1;
-                if (!mbar_wait(b_hfull(buf), u & 1, &abort_flag, P.status)) break;
                 if (!mbar_wait(b_aempty(ab), (ua & 1) ^ 1, &abort_flag, P.status)) break;
                 tc_fence_after();
+                // descriptor start (>> 4) of the slots holding rows y+row0 .. y+row0+rows-1
+                auto slot_base = [&](int k) {
+                    return (s_ring + (uint32_t)((first + k) % P.nslot) * P.slot_bytes) >> 4;
+                };
+                const uint32_t base0 = slot_base(0);
+                const uint32_t base1 = P.rows > 1 ? slot_base(1) : base0;
+                const uint32_t base2 = P.rows > 2 ? slot_base(2) : base0;
                 const uint32_t d = tmem + (uint32_t)(ab * P.n_slice);
-                const uint32_t hb = s_halo + (uint32_t)buf * P.halo_bytes;
+                uint32_t e = alo_s[0];
+                uint32_t b_lo = b_lo0;
                 for (int ks = 0; ks < P.nks; ++ks) {
-                    const uint64_t a = sdesc(hb + P.a_off[ks], P.a_lbo[ks], 128);
-                    const uint64_t b = sdesc(s_w + (uint32_t)ks * 2 * b_lbo, b_lbo, 128);
-                    if (P.fp8) mma_fp8(d, a, b, P.idesc, ks > 0 ? 1u : 0u);
+                    const uint32_t e_next = alo_s[ks + 1];   // read ahead (last one unused)
+                    const uint32_t k = e >> 30;
+                    const uint32_t bk = k == 0 ? base0 : (k == 1 ? base1 : base2);
+                    const uint64_t a = ((uint64_t)hi << 32) | (bk + (e & 0x3FFFFFFFu));
+                    const uint64_t b = ((uint64_t)hi << 32) | b_lo;
+                    if (FP8) mma_fp8(d, a, b, P.idesc, ks > 0 ? 1u : 0u);
                     else mma_bf16(d, a, b, P.idesc, ks > 0 ? 1u : 0u);
+                    e = e_next;
+                    b_lo += b_step;
                 }
-                mma_commit(b_hempty(buf));
+                // release the rows the next tile of this run no longer reads
+                int keep = seq_end;
+                if (t + 1 < t_end) {
+                    const TileRef r2 = tile_of(P, t + 1);
+                    if (r2.col == cur_col) {
+                        const int last2 = r2.y + P.row0 + P.rows - 1;
+                        keep = seq_end + (last2 >= next_row ? last2 - next_row + 1 : 0) - P.rows;
+                    }
+                }
+                for (; released < keep; ++released) mma_commit(b_hempty(released % P.nslot));
                 mma_commit(b_afull(ab));
             }
             // wait until every MMA issued above has completed
             mma_commit(b_done);
-            mbar_wait(b_done, 0, &abort_flag, P.status);
+            mbar_wait(b_done, 0, &abort_flag, P.status, false);
         }
     } else {
         // epilogue: warps 2..5 own TMEM lanes 32*(warp%4) ..; one lane per warp polls
         const int q = warp & 3;
         const int m = 32 * q + lane;
-        for (int i = 0; i < my_tiles; ++i) {
+        constexpr int ce = FP8 ? 16 : 8;   // channels per 16-byte plane
+        int i = 0;
+        for (int t = t_begin; t < t_end; ++t, ++i) {
             const int ab = i & 1, ua = i >> 1;
             int ok = 1;
             if (lane == 0) ok = mbar_wait(b_afull(ab), ua & 1, &abort_flag, P.status) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             tc_fence_after();
-            const int pt = cta_in_slice + i * ctas_per_slice;
-            const int xt = pt % P.tiles_x, rest = pt / P.tiles_x;
-            const int yr = rest % P.h, img = rest / P.h;
-            const int x = xt * TILE_M + m;
+            const TileRef r = tile_of(P, t);
+            const int x = r.xt * P.tile_w + m;
+            const bool valid = m < P.tile_w && x < P.w;
+            const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * P.n_slice);
             for (int c0 = 0; c0 < P.n_slice; c0 += 16) {
-                uint32_t r[16];
-                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * P.n_slice + c0), r);
+                uint32_t v32[16];
+                tmem_ld16(tbase + (uint32_t)c0, v32);
                 float v[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    v[j] = fmaf(__uint_as_float(r[j]), colscale_s[c0 + j], bias_s[c0 + j]);
+                    v[j] = fmaf(__uint_as_float(v32[j]), colscale_s[c0 + j], bias_s[c0 + j]);
                     if (P.mode == 0) v[j] = fmaxf(v[j], 0.0f);
                 }
-                if (x < P.w) {
+                if (valid) {
                     const int ng = slice * P.n_slice + c0;
-                    size_t e;   // element offset of the 16 outputs
+                    size_t row;   // output image row
+                    int xo, wo, o;
                     if (P.mode == 0) {
-                        e = (((size_t)img * P.h + yr) * P.w + x) * P.cout + ng;
+                        row = (size_t)r.img * P.h + r.y;
+                        xo = x;
+                        wo = P.w;
+                        o = ng;
                     } else {
                         // transposed conv: column ng = (2a + b) * cout + o  ->  pixel (2y+a, 2x+b)
-                        const int abi = ng / P.cout, o = ng % P.cout;
-                        e = (((size_t)img * 2 * P.h + 2 * yr + (abi >> 1)) * 2 * P.w + 2 * x +
-                             (abi & 1)) * P.cout + o;
+                        const int abi = ng / P.cout;
+                        o = ng - abi * P.cout;
+                        row = (size_t)r.img * 2 * P.h + 2 * r.y + (abi >> 1);
+                        xo = 2 * x + (abi & 1);
+                        wo = 2 * P.w;
                     }
-                    if (P.fp8) {
+                    uint8_t* dst = (uint8_t*)P.y +
+                                   ((row * P.out_nch + (size_t)(o / ce)) * wo + xo) * 16;
+                    if (FP8) {
                         uint32_t w[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(
+                            const __nv_fp8_storage_t c8 = __nv_cvt_float_to_fp8(
                                 v[j] * P.inv_out, __NV_SATFINITE, __NV_E4M3);
-                            w[j >> 2] |= (uint32_t)q << (8 * (j & 3));
+                            w[j >> 2] |= (uint32_t)c8 << (8 * (j & 3));
                         }
-                        *reinterpret_cast<uint4*>((uint8_t*)P.y + e) = make_uint4(w[0], w[1], w[2], w[3]);
+                        *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
                     } else {
                         uint32_t packed[8];
 #pragma unroll
@@ -349,9 +447,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
                             packed[j] = *reinterpret_cast<uint32_t*>(&h2);
                         }
-                        uint4* o4 = reinterpret_cast<uint4*>((__nv_bfloat16*)P.y + e);
-                        o4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                        o4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                        // channels o..o+7 and o+8..o+15 sit in consecutive planes
+                        *reinterpret_cast<uint4*>(dst) =
+                            make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                        *reinterpret_cast<uint4*>(dst + (size_t)wo * 16) =
+                            make_uint4(packed[4], packed[5], packed[6], packed[7]);
                     }
                 }
             }
@@ -394,24 +494,23 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// NHWC tensor [n][h][w][c] of `es`-byte elements viewed as (ce, w, c/ce, h, n),
-// ce = 16 / es elements per 16-byte chunk, so that one box of
-// (ce, 130, c/ce, rows, 1) lands in shared memory as [row][chunk][pixel][16 bytes].
-nrv_status make_halo_map(CUtensorMap* map, const void* base, int n, int h, int w, int c, int rows,
-                         int es) {
+// Row-planar tensor [n][h][nch][w][16 bytes] viewed as 8-byte elements
+// (2w, nch, h, n): one box of (256, nch, 1, 1) is 128 pixels of every plane of
+// one row and lands in shared memory as [plane][128 pixels][16 bytes].  Each
+// plane is a contiguous 2 KB run in global memory.  Pixels outside [0, w) and
+// rows outside [0, h) read as zero.
+nrv_status make_planar_map(CUtensorMap* map, const void* base, int n, int h, int w, int nch) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return fail(NRV_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
     if (((uintptr_t)base & 15) != 0) return fail(NRV_ERR_ARG, "tensor base not 16-byte aligned");
-    const int ce = 16 / es;
-    const cuuint64_t dims[5] = {(cuuint64_t)ce, (cuuint64_t)w, (cuuint64_t)(c / ce), (cuuint64_t)h,
-                                (cuuint64_t)n};
-    const cuuint64_t strides[4] = {(cuuint64_t)c * es, 16, (cuuint64_t)w * c * es,
-                                   (cuuint64_t)h * w * c * es};
-    const cuuint32_t box[5] = {(cuuint32_t)ce, HALO_W, (cuuint32_t)(c / ce), (cuuint32_t)rows, 1};
-    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    CUresult r = enc(map, es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
-                     5, const_cast<void*>(base), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    if (nch < 1 || nch > 256) return fail(NRV_ERR_UNSUPPORTED, "planes per row out of range");
+    const cuuint64_t dims[4] = {(cuuint64_t)2 * w, (cuuint64_t)nch, (cuuint64_t)h, (cuuint64_t)n};
+    const cuuint64_t row = (cuuint64_t)w * 16;
+    const cuuint64_t strides[3] = {row, row * nch, row * nch * h};
+    const cuuint32_t box[4] = {2 * TILE_M, (cuuint32_t)nch, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<void*>(base), dims, strides,
+                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(NRV_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return NRV_OK;
@@ -530,21 +629,28 @@ static nrv_status build_cfg(Net* net, int pi, std::vector<int4>& all_halves,
             c.rows = 3;
             c.row0 = -1;
             c.ncols = L.cout;
-            for (int tap = 0; tap < 9; ++tap)
-                for (int src = 0; src < 2; ++src) {
-                    const int cs = src == 0 ? c.c1 : c.c2;
-                    for (int ch = 0; ch < cs / ce; ++ch) c.halves.push_back(Half{tap, src, ch});
-                }
+            // K order: kernel row dy, then dx, source, channel chunk; the two halves
+            // of a K-step come from one input row (a zero phantom pads an odd row)
+            for (int dy = 0; dy < 3; ++dy) {
+                const size_t start = c.halves.size();
+                for (int dx = 0; dx < 3; ++dx)
+                    for (int src = 0; src < 2; ++src) {
+                        const int cs = src == 0 ? c.c1 : c.c2;
+                        for (int ch = 0; ch < cs / ce; ++ch)
+                            c.halves.push_back(Half{3 * dy + dx, src, ch});
+                    }
+                if ((c.halves.size() - start) % 2) c.halves.push_back(Half{-1, 0, 0});
+            }
         } else {
             c.c1 = L.cin;
             c.c2 = 0;
             c.rows = 1;
             c.row0 = 0;
             c.ncols = 4 * L.cout;
-            // the one "tap" reads row 0 of the halo at pixel offset +1 (tap index 1)
-            for (int ch = 0; ch < L.cin / ce; ++ch) c.halves.push_back(Half{1, 0, ch});
+            // one input row, no halo: every chunk at tap 0
+            for (int ch = 0; ch < L.cin / ce; ++ch) c.halves.push_back(Half{0, 0, ch});
+            if (c.halves.size() % 2) c.halves.push_back(Half{-1, 0, 0});
         }
-        if (c.halves.size() % 2) c.halves.push_back(Half{-1, 0, 0});
         c.nks = (int)c.halves.size() / 2;
         if (c.nks > MAX_KS) continue;
         // widest output slice whose weights fit in 80 KB
@@ -650,41 +756,57 @@ static int g_num_sms = 0;
 
 // Launch one tensor-core layer on a level of geometry (n, H, W): a 3x3 conv
 // writes [n][H][W][C_out]; a transposed conv reads level (H, W) and writes
-// [n][2H][2W][C_out].  FP8: operands and output E4M3, inv_out = 1 / output scale.
+// [n][2H][2W][C_out]; all tensors row-planar.  FP8: operands and output E4M3,
+// inv_out = 1 / output scale.
 static nrv_status tc_launch(const Net* net, int l, const void* x1, int c1, const void* x2, int c2,
                             void* y, int n, int H, int W, cudaStream_t s, int fp8, float inv_out) {
     const TcLayerCfg& c = g_cfg[fp8][l];
     if (!c.ok || c.c1 != c1 || c.c2 != c2) return fail(NRV_ERR_UNSUPPORTED, "layer not configured");
     if (fp8 && !net->fp8_ready) return fail(NRV_ERR_STATE, "FP8 needs activation scales");
+    if (n <= 0 || H <= 0 || W <= 0) return fail(NRV_ERR_ARG, "empty tensor");
     const Layer& L = net->layers[l];
     const int es = fp8 ? 1 : 2, ce = 16 / es;
+    const bool conv = c.kind == CONV3;
     TcParams P;
     memset(&P, 0, sizeof(P));
     P.n = n;
     P.h = H;
     P.w = W;
-    P.tiles_x = (W + TILE_M - 1) / TILE_M;
-    P.num_ptiles = P.tiles_x * H * n;
+    P.tile_w = conv ? TILE_M - 2 : TILE_M;
+    P.xoff = conv ? -1 : 0;
+    P.tiles_x = (W + P.tile_w - 1) / P.tile_w;
+    const long long ntiles = (long long)P.tiles_x * H * n;
+    if (ntiles > 0x3FFFFFFFll) return fail(NRV_ERR_UNSUPPORTED, "too many tiles");
+    P.ntiles = (int)ntiles;
     P.nslices = c.nslices;
     P.n_slice = c.n_slice;
     P.nks = c.nks;
-    P.cout = L.cout;
-    P.mode = c.kind == CONV3 ? 0 : 1;
+    P.rows = c.rows;
     P.row0 = c.row0;
+    P.cout = L.cout;
+    P.out_nch = L.cout / ce;
+    P.mode = conv ? 0 : 1;
     P.has_src2 = c.c2 > 0;
     const uint32_t nch1 = c.c1 / ce, nch2 = c.c2 / ce;
-    P.tx1 = c.rows * nch1 * PLANE;
-    P.tx2 = c.rows * nch2 * PLANE;
-    P.src2_off = (P.tx1 + 127) / 128 * 128;   // TMA destinations are 128-byte aligned
-    P.halo_bytes = (P.src2_off + P.tx2 + 127) / 128 * 128;
+    P.src2_off = (nch1 * PLANE + 127) / 128 * 128;   // TMA destinations are 128-byte aligned
+    const uint32_t used = nch2 ? P.src2_off + nch2 * PLANE : nch1 * PLANE;
+    // slack: rows 126 and 127 of a conv tile read up to 32 bytes past their plane
+    P.slot_bytes = (used + 32 + 127) / 128 * 128;
+    P.tx_bytes = (nch1 + nch2) * PLANE;
     P.w_bytes = c.w_bytes;
     P.w_region = (c.w_bytes + 1023) / 1024 * 1024;
-    // halo stages: as many as fit (up to 4) while the CTA stays under ~110 KB, at least 1
-    int nbuf = 4;
-    while (nbuf > 1 && P.w_region + nbuf * P.halo_bytes > 110 * 1024) --nbuf;
-    P.nbuf = nbuf;
-    const uint32_t smem = P.w_region + P.nbuf * P.halo_bytes;
-    if (smem > 220 * 1024) return fail(NRV_ERR_UNSUPPORTED, "tile does not fit in shared memory");
+    // ring slots: up to 8 within ~110 KB (several CTAs per SM) when that leaves two
+    // rows of read-ahead, otherwise as many as fit in one CTA per SM
+    auto fits = [&](int ns, uint32_t budget) {
+        return P.w_region + (uint32_t)ns * P.slot_bytes <= budget;
+    };
+    uint32_t budget = 110 * 1024;
+    if (!fits(c.rows + 2, budget)) budget = 215 * 1024;
+    int nslot = MAX_SLOTS;
+    while (nslot > c.rows && !fits(nslot, budget)) --nslot;
+    if (!fits(nslot, 215 * 1024)) return fail(NRV_ERR_UNSUPPORTED, "tile does not fit in shared memory");
+    P.nslot = nslot;
+    const uint32_t smem = P.w_region + (uint32_t)nslot * P.slot_bytes;
     // instruction descriptor: FP32 accumulator; A/B BF16 (kind::f16) or E4M3 (kind::f8f6f4)
     const uint32_t ab_fmt = fp8 ? 0u : 1u;
     P.idesc = (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(c.n_slice >> 3) << 17) |
@@ -706,23 +828,23 @@ static nrv_status tc_launch(const Net* net, int l, const void* x1, int c1, const
     for (int ks = 0; ks < c.nks; ++ks) {
         const Half& h0 = c.halves[2 * ks];
         const Half& h1 = c.halves[2 * ks + 1];
-        auto off = [&](const Half& h) -> uint32_t {
-            const uint32_t base = h.src == 0 ? 0u : P.src2_off;
-            const uint32_t nch = h.src == 0 ? nch1 : nch2;
-            const uint32_t row = c.kind == CONV3 ? (uint32_t)(h.tap / 3) : 0u;
-            return base + (row * nch + (uint32_t)h.chunk) * PLANE + (uint32_t)(h.tap % 3) * 16;
+        auto rel = [&](const Half& h) -> uint32_t {
+            return (h.src == 0 ? 0u : P.src2_off) + (uint32_t)h.chunk * PLANE +
+                   (uint32_t)(conv ? h.tap % 3 : 0) * 16;
         };
-        P.a_off[ks] = off(h0);
-        const uint32_t o1 = h1.tap < 0 ? P.a_off[ks] : off(h1);
-        if (o1 < P.a_off[ks]) return fail(NRV_ERR_UNSUPPORTED, "descending K layout");
-        P.a_lbo[ks] = o1 - P.a_off[ks];
-        // both K halves read 128 rows of 16 bytes inside the buffer
-        if (o1 + TILE_M * 16 > P.halo_bytes || P.a_lbo[ks] >= (1u << 18))
-            return fail(NRV_ERR_UNSUPPORTED, "A operand outside the halo buffer");
+        const int dy = conv ? h0.tap / 3 : 0;
+        if (h0.tap < 0 || (h1.tap >= 0 && conv && h1.tap / 3 != dy))
+            return fail(NRV_ERR_UNSUPPORTED, "K-step halves from different rows");
+        const uint32_t o0 = rel(h0), o1 = h1.tap < 0 ? o0 : rel(h1);
+        if (o1 < o0) return fail(NRV_ERR_UNSUPPORTED, "descending K layout");
+        // both halves read 128 rows of 16 bytes inside the slot (with its slack)
+        if (o1 + TILE_M * 16 > P.slot_bytes || (o1 - o0) >= (1u << 18))
+            return fail(NRV_ERR_UNSUPPORTED, "A operand outside the row slot");
+        P.a_lo[ks] = (o0 >> 4) | (((o1 - o0) >> 4) << 16) | ((uint32_t)dy << 30);
     }
     CUtensorMap m1, m2;
-    NRV_TRY(make_halo_map(&m1, x1, n, H, W, c.c1, c.rows, es));
-    if (P.has_src2) NRV_TRY(make_halo_map(&m2, x2, n, H, W, c.c2, c.rows, es));
+    NRV_TRY(make_planar_map(&m1, x1, n, H, W, (int)nch1));
+    if (P.has_src2) NRV_TRY(make_planar_map(&m2, x2, n, H, W, (int)nch2));
     else m2 = m1;
     if (!g_num_sms) {
         int dev = 0;
@@ -730,23 +852,28 @@ static nrv_status tc_launch(const Net* net, int l, const void* x1, int c1, const
         cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
         if (g_num_sms <= 0) g_num_sms = 148;
     }
-    static bool attr_set = false;
-    if (!attr_set) {
-        NRV_CHECK_CUDA(cudaFuncSetAttribute(conv3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    auto kern = fp8 ? conv3_tc_kernel<true> : conv3_tc_kernel<false>;
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[fp8]) {
+        NRV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             220 * 1024));
-        attr_set = true;
+        attr_set[fp8] = true;
     }
     // resident CTAs per SM from registers, threads, shared memory and TMEM columns
-    static cudaFuncAttributes fa;
+    static cudaFuncAttributes fa_k[2];
     static cudaDeviceProp prop;
-    static bool have_fa = false;
-    if (!have_fa) {
-        NRV_CHECK_CUDA(cudaFuncGetAttributes(&fa, conv3_tc_kernel));
+    static bool have_fa[2] = {false, false}, have_prop = false;
+    if (!have_prop) {
         int dev = 0;
         NRV_CHECK_CUDA(cudaGetDevice(&dev));
         NRV_CHECK_CUDA(cudaGetDeviceProperties(&prop, dev));
-        have_fa = true;
+        have_prop = true;
     }
+    if (!have_fa[fp8]) {
+        NRV_CHECK_CUDA(cudaFuncGetAttributes(&fa_k[fp8], kern));
+        have_fa[fp8] = true;
+    }
+    const cudaFuncAttributes& fa = fa_k[fp8];
     const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
     int occ = prop.regsPerMultiprocessor / (regs_per_warp * (NTHREADS / 32));
     occ = occ < prop.maxThreadsPerMultiProcessor / NTHREADS ? occ : prop.maxThreadsPerMultiProcessor / NTHREADS;
@@ -758,8 +885,9 @@ static nrv_status tc_launch(const Net* net, int l, const void* x1, int c1, const
     if (occ < 1) occ = 1;
     int per_slice = (g_num_sms * occ) / c.nslices;
     if (per_slice < 1) per_slice = 1;
-    if (per_slice > P.num_ptiles) per_slice = P.num_ptiles;
-    conv3_tc_kernel<<<per_slice * c.nslices, NTHREADS, smem, s>>>(m1, m2, P);
+    if (per_slice > P.ntiles) per_slice = P.ntiles;
+    P.ctas_per_slice = per_slice;
+    kern<<<per_slice * c.nslices, NTHREADS, smem, s>>>(m1, m2, P);
     NRV_CHECK_LAUNCH();
     return NRV_OK;
 }

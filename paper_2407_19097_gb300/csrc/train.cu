@@ -32,7 +32,8 @@ __global__ void __launch_bounds__(256) wgrad3_kernel(TView<const T> g, int cout,
         __syncthreads();
         for (int i = threadIdx.x; i < 512; i += 256) {
             const size_t q = qb + (i >> 4);
-            gs[i >> 4][i & 15] = q < q1 ? ld1<T>(g.p + q * g.ld + og + (i & 15)) : 0.0f;
+            gs[i >> 4][i & 15] =
+                q < q1 ? ld1<T>(g.at(q / w, (int)(q % w), og + (i & 15), w)) : 0.0f;
         }
         __syncthreads();
         const int nb = (int)(q1 - qb < 32 ? q1 - qb : 32);
@@ -50,8 +51,8 @@ __global__ void __launch_bounds__(256) wgrad3_kernel(TView<const T> g, int cout,
                 const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
                 float v = 0.0f;
                 if (yy >= 0 && yy < h && xx >= 0 && xx < w) {
-                    const size_t qq = (img * h + yy) * w + xx;
-                    v = c < c1 ? ld1<T>(x1.p + qq * x1.ld + c) : ld1<T>(x2.p + qq * x2.ld + c - c1);
+                    const size_t rr = img * h + yy;
+                    v = c < c1 ? ld1<T>(x1.at(rr, xx, c, w)) : ld1<T>(x2.at(rr, xx, c - c1, w));
                 }
 #pragma unroll
                 for (int j = 0; j < 16; ++j) acc[i][j] = fmaf(v, gs[r][j], acc[i][j]);
@@ -114,7 +115,8 @@ __global__ void __launch_bounds__(256) wgrad_up_kernel(TView<const T> x, int cin
         __syncthreads();
         for (int i = threadIdx.x; i < 512; i += 256) {
             const size_t q = qb + (i >> 4);
-            xs[i >> 4][i & 15] = q < q1 ? ld1<T>(x.p + q * x.ld + cg + (i & 15)) : 0.0f;
+            xs[i >> 4][i & 15] =
+                q < q1 ? ld1<T>(x.at(q / wi, (int)(q % wi), cg + (i & 15), wi)) : 0.0f;
         }
         __syncthreads();
         const int nb = (int)(q1 - qb < 32 ? q1 - qb : 32);
@@ -123,8 +125,8 @@ __global__ void __launch_bounds__(256) wgrad_up_kernel(TView<const T> x, int cin
                 const size_t q = qb + r;
                 const int X = (int)(q % wi), Y = (int)((q / wi) % hi);
                 const size_t img = q / ((size_t)wi * hi);
-                const size_t qo = (img * 2 * hi + 2 * Y + (ab >> 1)) * (2 * wi) + 2 * X + (ab & 1);
-                const float gv = ld1<T>(g.p + qo * g.ld + o);
+                const float gv = ld1<T>(
+                    g.at(img * 2 * hi + 2 * Y + (ab >> 1), 2 * X + (ab & 1), o, 2 * wi));
                 bsum += gv;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) acc[j] = fmaf(xs[r][j], gv, acc[j]);
@@ -172,8 +174,8 @@ __global__ void head_dgrad_kernel(const float* drgb, const float* w, TView<const
         if (X < wd && Y < h) {
             const float* gr = drgb + 3 * ((img * h + Y) * wd + X);
             float xv[16];
-            ld8<T>(x.p + q * x.ld, xv);
-            ld8<T>(x.p + q * x.ld + 8, xv + 8);
+            ld8<T>(x.at(img * hn + Y, X, 0, wn), xv);
+            ld8<T>(x.at(img * hn + Y, X, 8, wn), xv + 8);
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
                 const float s = fmaf(gr[2], w[32 + c], fmaf(gr[1], w[16 + c], gr[0] * w[c]));
@@ -183,8 +185,8 @@ __global__ void head_dgrad_kernel(const float* drgb, const float* w, TView<const
 #pragma unroll
             for (int c = 0; c < 16; ++c) out[c] = 0.0f;
         }
-        st8<T>(gd.p + q * gd.ld, out);
-        st8<T>(gd.p + q * gd.ld + 8, out + 8);
+        st8<T>(gd.at(img * hn + Y, X, 0, wn), out);
+        st8<T>(gd.at(img * hn + Y, X, 8, wn), out + 8);
     }
 }
 
@@ -200,8 +202,7 @@ __global__ void head_wgrad_kernel(const float* drgb, TView<const T> x, int n, in
     for (size_t i = i0; i < i1; ++i) {
         const int X = (int)(i % wd), Y = (int)((i / wd) % h);
         const size_t img = i / ((size_t)wd * h);
-        const size_t q = (img * hn + Y) * wn + X;
-        if (t < 48) s = fmaf(drgb[3 * i + t / 16], ld1<T>(x.p + q * x.ld + t % 16), s);
+        if (t < 48) s = fmaf(drgb[3 * i + t / 16], ld1<T>(x.at(img * hn + Y, X, t % 16, wn)), s);
         else s += drgb[3 * i + t - 48];
     }
     part[blockIdx.x * 51 + t] = s;
@@ -228,14 +229,14 @@ __global__ void pool_bwd_kernel(TView<const T> gp, TView<const T> gs, TView<cons
         const size_t q = i / (c / 8);
         const int X = (int)(q % w), Y = (int)((q / w) % h);
         const size_t img = q / ((size_t)w * h);
-        const size_t qp = (img * (h / 2) + Y / 2) * (w / 2) + X / 2;
+        const size_t row = img * h + Y;
         float a[8], b[8], m[8], r[8];
-        ld8<T>(gp.p + qp * gp.ld + cg, a);
-        ld8<T>(gs.p + q * gs.ld + cg, b);
-        ld8<T>(e.p + q * e.ld + cg, m);
+        ld8<T>(gp.at(img * (h / 2) + Y / 2, X / 2, cg, w / 2), a);
+        ld8<T>(gs.at(row, X, cg, w), b);
+        ld8<T>(e.at(row, X, cg, w), m);
 #pragma unroll
         for (int k = 0; k < 8; ++k) r[k] = m[k] > 0.0f ? fmaf(0.25f, a[k], b[k]) : 0.0f;
-        st8<T>(ge.p + q * ge.ld + cg, r);
+        st8<T>(ge.at(row, X, cg, w), r);
     }
 }
 
@@ -326,7 +327,10 @@ struct Bwd {
     T* W2[4];
 
     T* A(int a) const { return reinterpret_cast<T*>((char*)net->acts.p + net->act_off[a]); }
-    TView<const T> CA(int a) const { return TView<const T>{A(a), net->act_c[a]}; }
+    // saved activations: row-planar in BF16 (the tensor-core layout), NHWC in FP32
+    TView<const T> CA(int a) const {
+        return TView<const T>{A(a), net->act_c[a], sizeof(T) == 2 ? 1 : 0};
+    }
 
     nrv_status wgrad_conv(int l, TView<const T> gpre, TView<const T> x1, int c1, TView<const T> x2,
                           int c2, int level) {
