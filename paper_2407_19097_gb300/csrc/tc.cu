@@ -83,8 +83,9 @@ struct TcParams {
     int fp8;                 // E4M3 operands (kind::f8f6f4) and an E4M3 output
     float inv_out;           // FP8: 1 / scale of the output tensor
     const float* colscale;   // FP8: per GEMM column, input scale x weight scale
-    // per K-step: low word of the A descriptor relative to its row slot,
-    // (offset >> 4) | (LBO >> 4) << 16, with the row (0..2) in bits 30-31
+    // per K-step of one input row (every row of a tile has the same pattern):
+    // low word of the A descriptor relative to the row's slot,
+    // (offset >> 4) | (LBO >> 4) << 16; K-step ks reads row ks / (nks / rows)
     uint32_t a_lo[MAX_KS];
 };
 
@@ -206,16 +207,33 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
 
 // Tile t of a slice covers pixels [xt * tile_w, +tile_w) of row y of image img,
 // t = (img * tiles_x + xt) * h + y: consecutive tiles walk down one column.
-struct TileRef {
+// The walker steps through a run of tiles without divisions.
+struct TileWalk {
     int col, y, img, xt;
+    __device__ __forceinline__ void init(const TcParams& P, int t) {
+        col = t / P.h;
+        y = t - col * P.h;
+        img = col / P.tiles_x;
+        xt = col - img * P.tiles_x;
+    }
+    __device__ __forceinline__ void next(const TcParams& P) {
+        if (++y == P.h) {
+            y = 0;
+            ++col;
+            if (++xt == P.tiles_x) {
+                xt = 0;
+                ++img;
+            }
+        }
+    }
 };
-__device__ __forceinline__ TileRef tile_of(const TcParams& P, int t) {
-    TileRef r;
-    r.col = t / P.h;
-    r.y = t - r.col * P.h;
-    r.img = r.col / P.tiles_x;
-    r.xt = r.col - r.img * P.tiles_x;
-    return r;
+
+// Ring position (slot, phase parity of its use) advanced without divisions.
+__device__ __forceinline__ void ring_next(int& slot, uint32_t& phase, int nslot) {
+    if (++slot == nslot) {
+        slot = 0;
+        phase ^= 1u;
+    }
 }
 
 template <bool FP8>
@@ -288,99 +306,119 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const uint32_t len = P.w_bytes - o < 16384 ? P.w_bytes - o : 16384;
                 bulk_load(s_w + o, src + o, len, b_w);
             }
-            int seq = 0, cur_col = -1, next_row = 0;
+            TileWalk w;
+            w.init(P, t_begin);
+            int cur_col = -1, next_row = 0, nloads = 0, slot = 0;
+            uint32_t phase = 0;
             bool ok = true;
-            for (int t = t_begin; ok && t < t_end; ++t) {
-                const TileRef r = tile_of(P, t);
-                if (r.col != cur_col) {
-                    cur_col = r.col;
-                    next_row = r.y + P.row0;
+            for (int t = t_begin; ok && t < t_end; ++t, w.next(P)) {
+                if (w.col != cur_col) {
+                    cur_col = w.col;
+                    next_row = w.y + P.row0;
                 }
-                const int last = r.y + P.row0 + P.rows - 1;
+                const int last = w.y + P.row0 + P.rows - 1;
                 // 8-byte elements: pixel x starts at element 2x (16-byte aligned)
-                const int xe = 2 * (r.xt * P.tile_w + P.xoff);
-                for (; next_row <= last; ++next_row, ++seq) {
-                    const int slot = seq % P.nslot, u = seq / P.nslot;
-                    if (!mbar_wait(b_hempty(slot), (u & 1) ^ 1, &abort_flag, P.status)) {
+                const int xe = 2 * (w.xt * P.tile_w + P.xoff);
+                for (; next_row <= last; ++next_row) {
+                    if (!mbar_wait(b_hempty(slot), phase ^ 1u, &abort_flag, P.status)) {
                         ok = false;
                         break;
                     }
                     const uint32_t dst = s_ring + (uint32_t)slot * P.slot_bytes;
                     mbar_expect_tx(b_hfull(slot), P.tx_bytes);
-                    tma_load_4d(dst, &tm1, xe, 0, next_row, r.img, b_hfull(slot));
+                    tma_load_4d(dst, &tm1, xe, 0, next_row, w.img, b_hfull(slot));
                     if (P.has_src2)
-                        tma_load_4d(dst + P.src2_off, &tm2, xe, 0, next_row, r.img, b_hfull(slot));
+                        tma_load_4d(dst + P.src2_off, &tm2, xe, 0, next_row, w.img, b_hfull(slot));
+                    ++nloads;
+                    ring_next(slot, phase, P.nslot);
                 }
             }
-            // every load issued must have landed before the CTA may exit
-            for (int q = seq - P.nslot > 0 ? seq - P.nslot : 0; q < seq; ++q)
-                mbar_wait(b_hfull(q % P.nslot), (q / P.nslot) & 1, &abort_flag, P.status, false);
+            // every load issued must have landed before the CTA may exit: the last
+            // min(nloads, nslot) loads, walking the ring backwards
+            for (int q = nloads < P.nslot ? nloads : P.nslot; q > 0; --q) {
+                if (slot == 0) {
+                    slot = P.nslot - 1;
+                    phase ^= 1u;
+                } else {
+                    --slot;
+                }
+                mbar_wait(b_hfull(slot), phase, &abort_flag, P.status, false);
+            }
             mbar_wait(b_w, 0, &abort_flag, P.status, false);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             bool ok = mbar_wait(b_w, 0, &abort_flag, P.status);
             // descriptor high words: SBO = 128 bytes, version 1; B: K halves n_slice * 16 bytes apart
-            const uint32_t hi = (128u >> 4) | (1u << 14);
+            const uint64_t hi = (uint64_t)((128u >> 4) | (1u << 14)) << 32;
             const uint32_t b_lbo = (uint32_t)P.n_slice * 16;
             const uint32_t b_lo0 = ((s_w >> 4) & 0x3FFFu) | ((b_lbo >> 4) << 16);
             const uint32_t b_step = (2 * b_lbo) >> 4;
-            int seq_end = 0, cur_col = -1, next_row = 0, waited = 0, released = 0, i = 0;
-            for (int t = t_begin; ok && t < t_end; ++t, ++i) {
+            const uint32_t ring16 = s_ring >> 4, slot16 = P.slot_bytes >> 4;
+            const int ks_row = P.nks / P.rows;   // K-steps per input row
+            TileWalk w;
+            w.init(P, t_begin);
+            int cur_col = -1, next_row = 0;
+            int loaded = 0, waited = 0, released = 0;   // row-load counts
+            int end_slot = 0;                         // slot of load number `loaded`
+            int wslot = 0, rslot = 0;
+            uint32_t wphase = 0;
+            for (int t = t_begin, i = 0; ok && t < t_end; ++t, ++i) {
                 // the same row schedule as the loader
-                const TileRef r = tile_of(P, t);
-                if (r.col != cur_col) {
-                    cur_col = r.col;
-                    next_row = r.y + P.row0;
+                if (w.col != cur_col) {
+                    cur_col = w.col;
+                    next_row = w.y + P.row0;
                 }
-                const int last = r.y + P.row0 + P.rows - 1;
-                if (next_row <= last) {
-                    seq_end += last - next_row + 1;
-                    next_row = last + 1;
+                const int last = w.y + P.row0 + P.rows - 1;
+                for (; next_row <= last; ++next_row) {
+                    ++loaded;
+                    if (++end_slot == P.nslot) end_slot = 0;
                 }
-                const int first = seq_end - P.rows;   // load number of row y + row0
-                for (; waited < seq_end; ++waited)
-                    if (!mbar_wait(b_hfull(waited % P.nslot), (waited / P.nslot) & 1, &abort_flag,
-                                   P.status)) {
+                for (; waited < loaded; ++waited) {
+                    if (!mbar_wait(b_hfull(wslot), wphase, &abort_flag, P.status)) {
                         ok = false;
                         break;
                     }
-                if (!ok) break;
-                const int ab = i & 1, ua = i >> 1;
-                if (!mbar_wait(b_aempty(ab), (ua & 1) ^ 1, &abort_flag, P.status)) break;
-                tc_fence_after();
-                // descriptor start (>> 4) of the slots holding rows y+row0 .. y+row0+rows-1
-                auto slot_base = [&](int k) {
-                    return (s_ring + (uint32_t)((first + k) % P.nslot) * P.slot_bytes) >> 4;
-                };
-                const uint32_t base0 = slot_base(0);
-                const uint32_t base1 = P.rows > 1 ? slot_base(1) : base0;
-                const uint32_t base2 = P.rows > 2 ? slot_base(2) : base0;
-                const uint32_t d = tmem + (uint32_t)(ab * P.n_slice);
-                uint32_t e = alo_s[0];
-                uint32_t b_lo = b_lo0;
-                for (int ks = 0; ks < P.nks; ++ks) {
-                    const uint32_t e_next = alo_s[ks + 1];   // read ahead (last one unused)
-                    const uint32_t k = e >> 30;
-                    const uint32_t bk = k == 0 ? base0 : (k == 1 ? base1 : base2);
-                    const uint64_t a = ((uint64_t)hi << 32) | (bk + (e & 0x3FFFFFFFu));
-                    const uint64_t b = ((uint64_t)hi << 32) | b_lo;
-                    if (FP8) mma_fp8(d, a, b, P.idesc, ks > 0 ? 1u : 0u);
-                    else mma_bf16(d, a, b, P.idesc, ks > 0 ? 1u : 0u);
-                    e = e_next;
-                    b_lo += b_step;
+                    ring_next(wslot, wphase, P.nslot);
                 }
-                // release the rows the next tile of this run no longer reads
-                int keep = seq_end;
-                if (t + 1 < t_end) {
-                    const TileRef r2 = tile_of(P, t + 1);
-                    if (r2.col == cur_col) {
-                        const int last2 = r2.y + P.row0 + P.rows - 1;
-                        keep = seq_end + (last2 >= next_row ? last2 - next_row + 1 : 0) - P.rows;
+                if (!ok) break;
+                const int ab = i & 1;
+                if (!mbar_wait(b_aempty(ab), ((i >> 1) & 1) ^ 1, &abort_flag, P.status)) break;
+                tc_fence_after();
+                // the tile's rows y+row0 .. y+row0+rows-1 are the last `rows` loads
+                int s0 = end_slot - P.rows;
+                if (s0 < 0) s0 += P.nslot;
+                const uint32_t d = tmem + (uint32_t)(ab * P.n_slice);
+                uint32_t b_lo = b_lo0;
+                int ks = 0;
+                for (int k = 0; k < P.rows; ++k) {
+                    const uint32_t base = ring16 + (uint32_t)s0 * slot16;
+                    if (++s0 == P.nslot) s0 = 0;
+                    uint32_t e = alo_s[0];
+                    for (int j = 0; j < ks_row; ++j, ++ks) {
+                        const uint32_t e_next = alo_s[j + 1];   // read ahead
+                        const uint64_t a = hi | (uint64_t)(base + e);
+                        const uint64_t b = hi | (uint64_t)b_lo;
+                        if (FP8) mma_fp8(d, a, b, P.idesc, ks > 0 ? 1u : 0u);
+                        else mma_bf16(d, a, b, P.idesc, ks > 0 ? 1u : 0u);
+                        e = e_next;
+                        b_lo += b_step;
                     }
                 }
-                for (; released < keep; ++released) mma_commit(b_hempty(released % P.nslot));
+                // release the rows the next tile of this run no longer reads
+                int keep = loaded;
+                TileWalk w2 = w;
+                w2.next(P);
+                if (t + 1 < t_end && w2.col == cur_col) {
+                    const int last2 = w2.y + P.row0 + P.rows - 1;
+                    keep = loaded + (last2 >= next_row ? last2 - next_row + 1 : 0) - P.rows;
+                }
+                for (; released < keep; ++released) {
+                    mma_commit(b_hempty(rslot));
+                    if (++rslot == P.nslot) rslot = 0;
+                }
                 mma_commit(b_afull(ab));
+                w = w2;
             }
             // wait until every MMA issued above has completed
             mma_commit(b_done);
@@ -391,16 +429,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int q = warp & 3;
         const int m = 32 * q + lane;
         constexpr int ce = FP8 ? 16 : 8;   // channels per 16-byte plane
-        int i = 0;
-        for (int t = t_begin; t < t_end; ++t, ++i) {
-            const int ab = i & 1, ua = i >> 1;
+        TileWalk w;
+        w.init(P, t_begin);
+        for (int t = t_begin, i = 0; t < t_end; ++t, ++i, w.next(P)) {
+            const int ab = i & 1;
             int ok = 1;
-            if (lane == 0) ok = mbar_wait(b_afull(ab), ua & 1, &abort_flag, P.status) ? 1 : 0;
+            if (lane == 0) ok = mbar_wait(b_afull(ab), (i >> 1) & 1, &abort_flag, P.status) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             tc_fence_after();
-            const TileRef r = tile_of(P, t);
-            const int x = r.xt * P.tile_w + m;
+            const int x = w.xt * P.tile_w + m;
             const bool valid = m < P.tile_w && x < P.w;
             const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * P.n_slice);
             for (int c0 = 0; c0 < P.n_slice; c0 += 16) {
@@ -417,7 +455,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     size_t row;   // output image row
                     int xo, wo, o;
                     if (P.mode == 0) {
-                        row = (size_t)r.img * P.h + r.y;
+                        row = (size_t)w.img * P.h + w.y;
                         xo = x;
                         wo = P.w;
                         o = ng;
@@ -425,21 +463,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         // transposed conv: column ng = (2a + b) * cout + o  ->  pixel (2y+a, 2x+b)
                         const int abi = ng / P.cout;
                         o = ng - abi * P.cout;
-                        row = (size_t)r.img * 2 * P.h + 2 * r.y + (abi >> 1);
+                        row = (size_t)w.img * 2 * P.h + 2 * w.y + (abi >> 1);
                         xo = 2 * x + (abi & 1);
                         wo = 2 * P.w;
                     }
                     uint8_t* dst = (uint8_t*)P.y +
                                    ((row * P.out_nch + (size_t)(o / ce)) * wo + xo) * 16;
                     if (FP8) {
-                        uint32_t w[4] = {0u, 0u, 0u, 0u};
+                        uint32_t wd[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             const __nv_fp8_storage_t c8 = __nv_cvt_float_to_fp8(
                                 v[j] * P.inv_out, __NV_SATFINITE, __NV_E4M3);
-                            w[j >> 2] |= (uint32_t)c8 << (8 * (j & 3));
+                            wd[j >> 2] |= (uint32_t)c8 << (8 * (j & 3));
                         }
-                        *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+                        *reinterpret_cast<uint4*>(dst) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
                     } else {
                         uint32_t packed[8];
 #pragma unroll
@@ -795,63 +833,9 @@ static nrv_status tc_launch(const Net* net, int l, const void* x1, int c1, const
     P.tx_bytes = (nch1 + nch2) * PLANE;
     P.w_bytes = c.w_bytes;
     P.w_region = (c.w_bytes + 1023) / 1024 * 1024;
-    // ring slots: up to 8 within ~110 KB (several CTAs per SM) when that leaves two
-    // rows of read-ahead, otherwise as many as fit in one CTA per SM
-    auto fits = [&](int ns, uint32_t budget) {
-        return P.w_region + (uint32_t)ns * P.slot_bytes <= budget;
-    };
-    uint32_t budget = 110 * 1024;
-    if (!fits(c.rows + 2, budget)) budget = 215 * 1024;
-    int nslot = MAX_SLOTS;
-    while (nslot > c.rows && !fits(nslot, budget)) --nslot;
-    if (!fits(nslot, 215 * 1024)) return fail(NRV_ERR_UNSUPPORTED, "tile does not fit in shared memory");
-    P.nslot = nslot;
-    const uint32_t smem = P.w_region + (uint32_t)nslot * P.slot_bytes;
-    // instruction descriptor: FP32 accumulator; A/B BF16 (kind::f16) or E4M3 (kind::f8f6f4)
-    const uint32_t ab_fmt = fp8 ? 0u : 1u;
-    P.idesc = (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(c.n_slice >> 3) << 17) |
-              ((uint32_t)(TILE_M >> 4) << 24);
     uint32_t cols = 32;
     while (cols < (uint32_t)(2 * c.n_slice)) cols *= 2;
     P.tmem_cols = cols;
-    P.wpk = (const uint8_t*)(fp8 ? net->wfp8.p : net->wbf16.p) + c.w_off;
-    P.bias = (const float*)net->params.p + L.boff;
-    P.y = y;
-    P.fp8 = fp8;
-    P.inv_out = inv_out;
-    if (fp8) {
-        size_t cs_total = net->wscale8.bytes / (2 * sizeof(float));
-        P.colscale = (const float*)net->wscale8.p + cs_total + c.cs_off;
-    }
-    P.status = status_word();
-    if (!P.status) return fail(NRV_ERR_CUDA, "status word unavailable");
-    for (int ks = 0; ks < c.nks; ++ks) {
-        const Half& h0 = c.halves[2 * ks];
-        const Half& h1 = c.halves[2 * ks + 1];
-        auto rel = [&](const Half& h) -> uint32_t {
-            return (h.src == 0 ? 0u : P.src2_off) + (uint32_t)h.chunk * PLANE +
-                   (uint32_t)(conv ? h.tap % 3 : 0) * 16;
-        };
-        const int dy = conv ? h0.tap / 3 : 0;
-        if (h0.tap < 0 || (h1.tap >= 0 && conv && h1.tap / 3 != dy))
-            return fail(NRV_ERR_UNSUPPORTED, "K-step halves from different rows");
-        const uint32_t o0 = rel(h0), o1 = h1.tap < 0 ? o0 : rel(h1);
-        if (o1 < o0) return fail(NRV_ERR_UNSUPPORTED, "descending K layout");
-        // both halves read 128 rows of 16 bytes inside the slot (with its slack)
-        if (o1 + TILE_M * 16 > P.slot_bytes || (o1 - o0) >= (1u << 18))
-            return fail(NRV_ERR_UNSUPPORTED, "A operand outside the row slot");
-        P.a_lo[ks] = (o0 >> 4) | (((o1 - o0) >> 4) << 16) | ((uint32_t)dy << 30);
-    }
-    CUtensorMap m1, m2;
-    NRV_TRY(make_planar_map(&m1, x1, n, H, W, (int)nch1));
-    if (P.has_src2) NRV_TRY(make_planar_map(&m2, x2, n, H, W, (int)nch2));
-    else m2 = m1;
-    if (!g_num_sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (g_num_sms <= 0) g_num_sms = 148;
-    }
     auto kern = fp8 ? conv3_tc_kernel<true> : conv3_tc_kernel<false>;
     static bool attr_set[2] = {false, false};
     if (!attr_set[fp8]) {
@@ -874,14 +858,77 @@ static nrv_status tc_launch(const Net* net, int l, const void* x1, int c1, const
         have_fa[fp8] = true;
     }
     const cudaFuncAttributes& fa = fa_k[fp8];
-    const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
-    int occ = prop.regsPerMultiprocessor / (regs_per_warp * (NTHREADS / 32));
-    occ = occ < prop.maxThreadsPerMultiProcessor / NTHREADS ? occ : prop.maxThreadsPerMultiProcessor / NTHREADS;
-    const size_t smem_cta = smem + fa.sharedSizeBytes + prop.reservedSharedMemPerBlock;
-    const int by_smem = (int)(prop.sharedMemPerMultiprocessor / smem_cta);
-    occ = occ < by_smem ? occ : by_smem;
-    occ = occ < prop.maxBlocksPerMultiProcessor ? occ : prop.maxBlocksPerMultiProcessor;
-    if (occ * (int)cols > 512) occ = 512 / (int)cols;
+    auto occupancy = [&](uint32_t smem_dyn) {
+        const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+        int o = prop.regsPerMultiprocessor / (regs_per_warp * (NTHREADS / 32));
+        o = o < prop.maxThreadsPerMultiProcessor / NTHREADS ? o : prop.maxThreadsPerMultiProcessor / NTHREADS;
+        const size_t smem_cta = smem_dyn + fa.sharedSizeBytes + prop.reservedSharedMemPerBlock;
+        const int by_smem = (int)(prop.sharedMemPerMultiprocessor / smem_cta);
+        o = o < by_smem ? o : by_smem;
+        o = o < prop.maxBlocksPerMultiProcessor ? o : prop.maxBlocksPerMultiProcessor;
+        if (o * (int)cols > 512) o = 512 / (int)cols;
+        return o;
+    };
+    // ring slots: two rows of read-ahead (more co-resident CTAs give the tensor pipe
+    // several MMA issuers), then as many more as keep that occupancy; within 215 KB
+    auto smem_for = [&](int ns) { return P.w_region + (uint32_t)ns * P.slot_bytes; };
+    int nslot = c.rows + 2;
+    while (nslot > c.rows && smem_for(nslot) > 215 * 1024) --nslot;
+    if (smem_for(nslot) > 215 * 1024) return fail(NRV_ERR_UNSUPPORTED, "tile does not fit in shared memory");
+    const int occ0 = occupancy(smem_for(nslot));
+    while (nslot < MAX_SLOTS && smem_for(nslot + 1) <= 215 * 1024 &&
+           occupancy(smem_for(nslot + 1)) >= occ0)
+        ++nslot;
+    P.nslot = nslot;
+    const uint32_t smem = smem_for(nslot);
+    // instruction descriptor: FP32 accumulator; A/B BF16 (kind::f16) or E4M3 (kind::f8f6f4)
+    const uint32_t ab_fmt = fp8 ? 0u : 1u;
+    P.idesc = (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(c.n_slice >> 3) << 17) |
+              ((uint32_t)(TILE_M >> 4) << 24);
+    P.wpk = (const uint8_t*)(fp8 ? net->wfp8.p : net->wbf16.p) + c.w_off;
+    P.bias = (const float*)net->params.p + L.boff;
+    P.y = y;
+    P.fp8 = fp8;
+    P.inv_out = inv_out;
+    if (fp8) {
+        size_t cs_total = net->wscale8.bytes / (2 * sizeof(float));
+        P.colscale = (const float*)net->wscale8.p + cs_total + c.cs_off;
+    }
+    P.status = status_word();
+    if (!P.status) return fail(NRV_ERR_CUDA, "status word unavailable");
+    if (c.nks % c.rows) return fail(NRV_ERR_UNSUPPORTED, "K-steps not a whole number per row");
+    const int ks_row = c.nks / c.rows;
+    for (int ks = 0; ks < c.nks; ++ks) {
+        const Half& h0 = c.halves[2 * ks];
+        const Half& h1 = c.halves[2 * ks + 1];
+        auto rel = [&](const Half& h) -> uint32_t {
+            return (h.src == 0 ? 0u : P.src2_off) + (uint32_t)h.chunk * PLANE +
+                   (uint32_t)(conv ? h.tap % 3 : 0) * 16;
+        };
+        const int dy = conv ? h0.tap / 3 : 0;
+        if (h0.tap < 0 || dy != ks / ks_row || (h1.tap >= 0 && conv && h1.tap / 3 != dy))
+            return fail(NRV_ERR_UNSUPPORTED, "K-step halves out of row order");
+        const uint32_t o0 = rel(h0), o1 = h1.tap < 0 ? o0 : rel(h1);
+        if (o1 < o0) return fail(NRV_ERR_UNSUPPORTED, "descending K layout");
+        // both halves read 128 rows of 16 bytes inside the slot (with its slack)
+        if (o1 + TILE_M * 16 > P.slot_bytes || (o1 - o0) >= (1u << 18))
+            return fail(NRV_ERR_UNSUPPORTED, "A operand outside the row slot");
+        const uint32_t word = (o0 >> 4) | (((o1 - o0) >> 4) << 16);
+        if (ks < ks_row) P.a_lo[ks] = word;
+        else if (P.a_lo[ks % ks_row] != word)
+            return fail(NRV_ERR_UNSUPPORTED, "rows of a tile with different K patterns");
+    }
+    CUtensorMap m1, m2;
+    NRV_TRY(make_planar_map(&m1, x1, n, H, W, (int)nch1));
+    if (P.has_src2) NRV_TRY(make_planar_map(&m2, x2, n, H, W, (int)nch2));
+    else m2 = m1;
+    if (!g_num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 148;
+    }
+    int occ = occupancy(smem);
     if (occ < 1) occ = 1;
     int per_slice = (g_num_sms * occ) / c.nslices;
     if (per_slice < 1) per_slice = 1;
