@@ -74,6 +74,13 @@ int nrv_version(void);
  * contain.  For benchmarking. */
 uint64_t nrv_launch_count(void);
 
+/* Number of compiled variants of the render pass (visibility) kernel for one
+ * view (multi_view = 0) or a batch of views (multi_view != 0).  All variants
+ * compute the same keys; the library times them on the first large launch and
+ * keeps the fastest.  Setting the environment variable NRV_VIS_VARIANT to an
+ * index below this count pins that variant (used to check each one). */
+int nrv_render_variants(int multi_view);
+
 /* --------------------------------------------------------------------------
  * Scene (the point cloud of Sec. 3.2; memory N * sum(B_i) bytes, Sec. 4.5)
  * ------------------------------------------------------------------------ */
@@ -90,11 +97,21 @@ typedef struct {
 typedef struct nrv_scene nrv_scene;
 
 /* Describe a scene.  Borrows d_xyz and d_attr, which must outlive the scene.
+ * The first render derives from d_xyz a bounding box for every chunk of 32
+ * consecutive points (ceil(N/32) * 24 bytes of device memory, owned by the
+ * scene) for occlusion culling in the render pass.
  * Errors: NRV_ERR_ARG for a null pointer with N > 0, a d_xyz base that is not
  * 16-byte aligned, a d_attr base not aligned to min(16, 4*stride_words) bytes,
  * N >= 2^32, a stride not in {1,2,4,8} or K out of range. */
 nrv_status nrv_create_scene(const nrv_scene_desc* desc, nrv_scene** out);
 nrv_status nrv_destroy_scene(nrv_scene* scene);
+
+/* Tell the scene that the positions behind d_xyz changed: the next render
+ * recomputes the chunk bounds (on its stream) before it uses them.  Rendering
+ * after a change without this call may drop points that are now visible.
+ * No counterpart in the paper (its rasterizer relies on early depth tests
+ * alone).  Errors: NRV_ERR_ARG for a null scene. */
+nrv_status nrv_scene_refresh(nrv_scene* scene);
 
 /* One camera.  clip = viewproj * (x, y, z, 1)^T with viewproj row-major FP32;
  * clip.w is the eye-space depth.  A point is kept when znear <= w <= zfar and
@@ -117,9 +134,12 @@ typedef struct {
 } nrv_gbuffer;
 
 /* Render + resolve passes of the multi-attribute compute rasterizer (Sec. 3.2)
- * for n_views views of one scene in one pass over the points: clear every
- * key image, project each point once per view and keep the minimum key
- * (bits(w) << 32 | index; ties to the lowest index), then resolve every pixel.
+ * for n_views views of one scene: clear every key image, project each point
+ * once per view and keep the minimum key (bits(w) << 32 | index; ties to the
+ * lowest index), then resolve every pixel.  The render pass may skip chunks of
+ * points that provably cannot set a key (outside every view, or behind the
+ * depths already written over all the pixels they can reach); the keys are the
+ * same as when every point is projected.
  * Keys and planes are bit-exact: the projection is the fixed FP32 sequence
  *   c = ((m0*x + m1*y) + m2*z) + m3 per row (no fused multiply-add),
  *   ndc = c.xy / c.w (IEEE division).

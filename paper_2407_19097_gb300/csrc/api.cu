@@ -50,8 +50,19 @@ using namespace nrv;
 
 struct nrv_scene {
     nrv_scene_desc d;
-    DevBuf tiles;   // per-tile depth bounds of the render pass (nrv_rasterize)
+    DevBuf tiles;    // per-tile depth bounds of the render pass (nrv_rasterize)
+    DevBuf chunks;   // bounding box of every 32-point chunk (chunk culling)
+    bool chunks_ok = false;
 };
+
+// The chunk bounds are derived from the positions on first use and after nrv_scene_refresh.
+static nrv_status ensure_chunks(nrv_scene* s, cudaStream_t st) {
+    if (s->chunks_ok || s->d.n_points == 0) return NRV_OK;
+    NRV_TRY(s->chunks.ensure(chunk_count(s->d.n_points) * 6 * sizeof(float)));
+    NRV_TRY(launch_chunk_bounds(s->d.d_xyz, s->d.n_points, s->chunks.p, st));
+    s->chunks_ok = true;
+    return NRV_OK;
+}
 
 // A captured whole frame (nrv_render_batch) and the device copy of the cameras it reads.
 struct BatchGraph {
@@ -77,6 +88,9 @@ struct nrv_net : Net {
 extern "C" const char* nrv_last_error(void) { return g_err; }
 extern "C" int nrv_version(void) { return 1; }
 extern "C" uint64_t nrv_launch_count(void) { return g_launches.load(); }
+extern "C" int nrv_render_variants(int multi_view) {
+    return nrv::visibility_variant_count(multi_view != 0);
+}
 extern "C" int nrv_pad8(int v) { return (v + 7) / 8 * 8; }
 extern "C" int nrv_netin_channels(nrv_prec p) { return p == NRV_PREC_FP8 ? 16 : 8; }
 
@@ -108,6 +122,13 @@ extern "C" nrv_status nrv_create_scene(const nrv_scene_desc* d, nrv_scene** out)
 extern "C" nrv_status nrv_destroy_scene(nrv_scene* s) {
     clear_error();
     delete s;
+    return NRV_OK;
+}
+
+extern "C" nrv_status nrv_scene_refresh(nrv_scene* s) {
+    clear_error();
+    if (!s) return fail(NRV_ERR_ARG, "null scene");
+    s->chunks_ok = false;
     return NRV_OK;
 }
 
@@ -172,8 +193,10 @@ static nrv_status raster_views(nrv_scene* s, const nrv_view* views, int n, uint6
     rv.n = n;
     for (int i = 0; i < n; ++i) rv.v[i] = make_rview(views[i], keys[i]);
     NRV_TRY(s->tiles.ensure(visibility_scratch_bytes(rv)));
+    NRV_TRY(ensure_chunks(s, st));
     NRV_TRY(launch_clear_keys(rv, st));
-    return launch_visibility(s->d.d_xyz, s->d.n_points, rv, st, nullptr, (uint32_t*)s->tiles.p);
+    return launch_visibility(s->d.d_xyz, s->d.n_points, rv, st, nullptr, (uint32_t*)s->tiles.p,
+                             s->chunks.p);
 }
 
 extern "C" nrv_status nrv_rasterize(nrv_scene* s, const nrv_view* views, int n,
@@ -498,6 +521,7 @@ extern "C" nrv_status nrv_render_batch(nrv_scene* s, nrv_net* net, const nrv_pac
     // everything but the cameras is fixed by this signature; a captured frame is replayed
     auto make_sig = [&]() {
         std::vector<uint64_t> sig = {(uint64_t)(uintptr_t)s->d.d_xyz, s->d.n_points,
+                                     (uint64_t)(uintptr_t)s->chunks.p,
                                      (uint64_t)(uintptr_t)s->d.d_attr, (uint64_t)s->d.stride_words,
                                      (uint64_t)s->d.n_words, (uint64_t)prec, (uint64_t)n};
         for (int i = 0; i < n; ++i) {
@@ -517,6 +541,7 @@ extern "C" nrv_status nrv_render_batch(nrv_scene* s, nrv_net* net, const nrv_pac
         }
         return sig;
     };
+    NRV_TRY(ensure_chunks(s, st));
     std::vector<uint64_t> sig = make_sig();
 
     auto frame = [&](const RViews* views_dev, std::vector<cudaEvent_t>* ev,
@@ -525,7 +550,7 @@ extern "C" nrv_status nrv_render_batch(nrv_scene* s, nrv_net* net, const nrv_pac
         NRV_TRY(launch_clear_keys(rv, q));
         if (ev) prof_mark(*ev, q);
         NRV_TRY(launch_visibility(s->d.d_xyz, s->d.n_points, rv, q, views_dev,
-                                  (uint32_t*)(base + tiles_off)));
+                                  (uint32_t*)(base + tiles_off), s->chunks.p));
         if (ev) prof_mark(*ev, q);
         for (int i = 0; i < n; ++i) {
             ResolveArgs a;

@@ -79,11 +79,20 @@ struct ResolveArgs {
 
 nrv_status launch_clear_keys(const RViews& views, cudaStream_t s);
 // Render pass.  `tiles` is scratch for the per-tile depth bounds of the culling
-// variant: visibility_scratch_bytes(views) bytes of device memory (may be null,
-// which disables culling).
+// variants: visibility_scratch_bytes(views) bytes of device memory (may be null,
+// which disables culling).  `chunks` holds the bounding boxes of the scene's
+// 32-point chunks (6 floats each, chunk_count(n) of them, from
+// launch_chunk_bounds; may be null, which disables chunk culling).
 size_t visibility_scratch_bytes(const RViews& views);
+constexpr int RENDER_CHUNK = 32;
+__host__ __device__ inline uint64_t chunk_count(uint64_t n) { return (n + RENDER_CHUNK - 1) / RENDER_CHUNK; }
+nrv_status launch_chunk_bounds(const float* xyz, uint64_t n, void* chunks, cudaStream_t s);
+// Render-pass variants (raster.cu): how many there are for one view / a batch, and their names.
+int visibility_variant_count(int multi);
+const char* visibility_variant_name(int multi, int i);
 nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, cudaStream_t s,
-                             const RViews* views_dev = nullptr, uint32_t* tiles = nullptr);
+                             const RViews* views_dev = nullptr, uint32_t* tiles = nullptr,
+                             const void* chunks = nullptr);
 nrv_status launch_resolve(const ResolveArgs& a, cudaStream_t s);
 nrv_status launch_pack_planes(const uint32_t* depth, const uint8_t* mask, const uint32_t* gattr,
                               const ResolveArgs& a, cudaStream_t s);

@@ -70,12 +70,12 @@ __device__ __forceinline__ bool cull_point(const RView& v, float cw, float cx, f
     return __float_as_uint(cw) > __ldg(bound + (int)ty * tiles_x + (int)tx);
 }
 
-// Projection + clipping of one point for one view; on success returns the key
-// and the address of its pixel's key.  With a tile bound table, points that
-// cull_point rejects are dropped before the exact divisions.
+// Projection + clipping of one point for one view; on success returns the
+// pixel (row-major index) and the depth word of the key (bits of w).  With a
+// tile bound table, points that cull_point rejects are dropped before the
+// exact divisions.
 __device__ __forceinline__ bool project_point(const RView& v, float x, float y, float z,
-                                              uint32_t idx, unsigned long long*& p,
-                                              unsigned long long& key,
+                                              uint32_t& pix, uint32_t& dbits,
                                               const uint32_t* __restrict__ bound = nullptr,
                                               int tiles_x = 0, bool cull = false) {
     const float cw = __fadd_rn(
@@ -93,8 +93,8 @@ __device__ __forceinline__ bool project_point(const RView& v, float x, float y, 
     const float sy = __fmul_rn(__fsub_rn(1.0f, __fdiv_rn(cy, cw)), v.hh);
     if (!(sx >= 0.0f && sx < v.fw && sy >= 0.0f && sy < v.fh)) return false;
     const int px = __float2int_rz(sx), py = __float2int_rz(sy);
-    key = ((unsigned long long)__float_as_uint(cw) << 32) | idx;
-    p = v.key + (size_t)py * v.width + px;
+    pix = (uint32_t)py * (uint32_t)v.width + (uint32_t)px;
+    dbits = __float_as_uint(cw);
     return true;
 }
 
@@ -131,18 +131,26 @@ __device__ __forceinline__ void render_point(const RView& v, float x, float y, f
 //   MINB     register budget: at least MINB blocks of 256 threads per SM.
 //   bound    per-tile depth bounds of all views back to back, or null (no culling);
 //            groups [g_begin, ngroups) are processed.
+// Indices are 32-bit: N < 2^32, so there are fewer than 2^30 groups.
 template <bool SINGLE, bool PREFETCH, int MINB, bool CULL>
 __global__ void __launch_bounds__(256, MINB) visibility_kernel(const float4* __restrict__ xyz4,
-                                                               uint64_t ngroups,
+                                                               uint32_t ngroups,
                                                                const float* __restrict__ xyz,
-                                                               uint64_t n, RViews vs_arg,
+                                                               uint64_t n,
+                                                               const __grid_constant__ RViews vs_arg,
                                                                const RViews* __restrict__ views_dev,
                                                                const uint32_t* __restrict__ bound,
-                                                               uint64_t g_begin) {
+                                                               uint32_t g_begin) {
     __shared__ RViews vs;
     __shared__ int tile_off[8], tiles_x[8];
+    {
+        // the views: a word-wise copy into shared memory (no local copy of the parameter)
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(views_dev ? views_dev : &vs_arg);
+        for (int i = threadIdx.x; i < (int)(sizeof(RViews) / 4); i += blockDim.x)
+            reinterpret_cast<uint32_t*>(&vs)[i] = src[i];
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        vs = views_dev ? *views_dev : vs_arg;
         int off = 0;
         for (int v = 0; v < vs.n; ++v) {
             tiles_x[v] = (vs.v[v].width + TILE - 1) / TILE;
@@ -154,8 +162,8 @@ __global__ void __launch_bounds__(256, MINB) visibility_kernel(const float4* __r
     const bool cull = CULL && bound != nullptr;
     RView v0;
     if (SINGLE) v0 = vs.v[0];
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    uint64_t g = g_begin + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    uint32_t g = g_begin + blockIdx.x * blockDim.x + threadIdx.x;
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a, c = a;
     if (PREFETCH && g < ngroups) {
         a = __ldcs(xyz4 + 3 * g);
@@ -165,7 +173,7 @@ __global__ void __launch_bounds__(256, MINB) visibility_kernel(const float4* __r
     for (; g < ngroups; g += stride) {
         float4 na = a, nb = b, nc = c;
         if (PREFETCH) {
-            const uint64_t gn = g + stride;
+            const uint32_t gn = g + stride;
             if (gn < ngroups) {
                 na = __ldcs(xyz4 + 3 * gn);
                 nb = __ldcs(xyz4 + 3 * gn + 1);
@@ -179,21 +187,23 @@ __global__ void __launch_bounds__(256, MINB) visibility_kernel(const float4* __r
         const float px[4] = {a.x, a.w, b.z, c.y};
         const float py[4] = {a.y, b.x, b.w, c.z};
         const float pz[4] = {a.z, b.y, c.x, c.w};
-        const uint32_t i0 = (uint32_t)(4 * g);
+        const uint32_t i0 = 4 * g;
         for (int v = 0; v < (SINGLE ? 1 : vs.n); ++v) {
             const RView& vw = SINGLE ? v0 : vs.v[v];
-            unsigned long long* ptr[4];
-            unsigned long long key[4], cur[4];
+            uint32_t pix[4], db[4];
+            unsigned long long cur[4];
             bool ok[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                ok[j] = project_point(vw, px[j], py[j], pz[j], i0 + j, ptr[j], key[j],
+                ok[j] = project_point(vw, px[j], py[j], pz[j], pix[j], db[j],
                                       cull ? bound + tile_off[v] : nullptr, tiles_x[v], cull);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) cur[j] = ok[j] ? __ldcg(ptr[j]) : 0ull;
+            for (int j = 0; j < 4; ++j) cur[j] = ok[j] ? __ldcg(vw.key + pix[j]) : 0ull;
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (ok[j] && key[j] < cur[j]) atomicMin(ptr[j], key[j]);
+            for (int j = 0; j < 4; ++j) {
+                const unsigned long long key = ((unsigned long long)db[j] << 32) | (i0 + j);
+                if (ok[j] && key < cur[j]) atomicMin(vw.key + pix[j], key);
+            }
         }
         if (PREFETCH) {
             a = na;
@@ -237,6 +247,221 @@ __global__ void tile_bound_kernel(RViews vs_arg, const RViews* __restrict__ view
     if (lane == 0) out[t] = m;
 }
 
+// ------------------------------------------------------------------ chunk culling
+// The points are taken in chunks of 32 consecutive points, each with a bounding
+// box (centre and half extents) computed from the positions once per scene.  A
+// chunk-culling render pass renders every S-th chunk in full, turns the keys
+// into tile depth bounds, then tests every other chunk's box against them, view
+// by view: a chunk wholly outside the depth range or the screen, or whose
+// nearest possible depth lies behind every pixel of the tiles it can touch, is
+// skipped; the others render point by point.  Keys do not change: a skipped
+// point could not have set one (keys only decrease, so a bound read earlier
+// stays a valid bound).
+
+// Chunk box: centre c = (lo + hi) / 2 and half extents e >= max(hi - c, c - lo),
+// the differences rounded up, so |p - c| <= e holds exactly for every point p.
+// Stored as 6 floats per chunk: cx cy cz ex ey ez.  One warp per chunk.
+__global__ void chunk_bounds_kernel(const float* __restrict__ xyz, uint64_t n,
+                                    float* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t nch = chunk_count(n);
+    const uint64_t warps = (gridDim.x * (uint64_t)blockDim.x) / 32;
+    for (uint64_t c = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; c < nch; c += warps) {
+        const uint64_t i0 = c * RENDER_CHUNK;
+        const uint64_t i = i0 + lane < n ? i0 + lane : i0;   // lanes past the end repeat the first point
+        float v[3] = {xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            float lo = v[d], hi = v[d];
+            for (int o = 16; o > 0; o >>= 1) {
+                lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            }
+            const float ctr = 0.5f * lo + 0.5f * hi;
+            const float e = fmaxf(__fsub_ru(hi, ctr), __fsub_ru(ctr, lo));
+            if (lane == d) out[6 * c + d] = ctr;
+            if (lane == 3 + d) out[6 * c + 3 + d] = e;
+        }
+    }
+}
+
+nrv_status launch_chunk_bounds(const float* xyz, uint64_t n, void* chunks, cudaStream_t s) {
+    if (n == 0) return NRV_OK;
+    uint64_t blocks = (chunk_count(n) * 32 + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    chunk_bounds_kernel<<<(unsigned)blocks, 256, 0, s>>>(xyz, n, (float*)chunks);
+    NRV_CHECK_LAUNCH();
+    return NRV_OK;
+}
+
+// True when no point in the box (c, e) can set a key of view v, given the tile
+// depth bounds (null: depth range and screen only).  Allowances: 1e-5 of the
+// magnitudes summed in each clip coordinate covers the rounding of the points'
+// own FP32 sequences and of this arithmetic (both below 1e-6 of that sum); the
+// screen rectangle is widened by half a pixel plus 1e-5 of its extent.
+__device__ __forceinline__ bool chunk_hidden(const RView& v, const float* c, const float* e,
+                                             const uint32_t* __restrict__ bound, int tiles_x,
+                                             int tiles_y) {
+    const float ax = fabsf(c[0]) + e[0], ay = fabsf(c[1]) + e[1], az = fabsf(c[2]) + e[2];
+    const float w = fmaf(v.m[8], c[0], fmaf(v.m[9], c[1], fmaf(v.m[10], c[2], v.m[11])));
+    const float X = fmaf(v.m[0], c[0], fmaf(v.m[1], c[1], fmaf(v.m[2], c[2], v.m[3])));
+    const float Y = fmaf(v.m[4], c[0], fmaf(v.m[5], c[1], fmaf(v.m[6], c[2], v.m[7])));
+    // |row . (p - c)| <= |row| . e over the box, plus the allowance
+    auto spread = [&](int r, float& allow) {
+        const float* m = v.m + 4 * r;
+        allow = 1e-5f * (fabsf(m[0]) * ax + fabsf(m[1]) * ay + fabsf(m[2]) * az + fabsf(m[3]));
+        return fabsf(m[0]) * e[0] + fabsf(m[1]) * e[1] + fabsf(m[2]) * e[2];
+    };
+    float ew, ex, ey;
+    const float dw = spread(2, ew) + ew;
+    const float wlo = w - dw, whi = w + dw;
+    if (whi < v.znear || wlo > v.zfar) return true;           // wholly outside the depth range
+    if (!(wlo > 0.5f * v.znear)) return false;                // w may come near 0: no screen bound
+    const float dx = spread(0, ex) + ex, dy = spread(1, ey) + ey;
+    const float xl = X - dx, xh = X + dx, yl = Y - dy, yh = Y + dy;
+    const float nxl = fminf(__fdividef(xl, wlo), __fdividef(xl, whi));
+    const float nxh = fmaxf(__fdividef(xh, wlo), __fdividef(xh, whi));
+    const float nyl = fminf(__fdividef(yl, wlo), __fdividef(yl, whi));
+    const float nyh = fmaxf(__fdividef(yh, wlo), __fdividef(yh, whi));
+    const float mx = 0.5f + 1e-5f * v.hw * (fabsf(nxl) + fabsf(nxh) + 2.0f);
+    const float my = 0.5f + 1e-5f * v.hh * (fabsf(nyl) + fabsf(nyh) + 2.0f);
+    const float sx0 = (nxl + 1.0f) * v.hw - mx, sx1 = (nxh + 1.0f) * v.hw + mx;
+    const float sy0 = (1.0f - nyh) * v.hh - my, sy1 = (1.0f - nyl) * v.hh + my;
+    if (!(sx1 >= 0.0f && sy1 >= 0.0f && sx0 < v.fw && sy0 < v.fh)) {
+        // wholly off screen -- unless a NaN made every comparison fail
+        return sx1 < 0.0f || sy1 < 0.0f || sx0 >= v.fw || sy0 >= v.fh;
+    }
+    if (!bound) return false;
+    const int tx0 = sx0 > 0.0f ? (int)(sx0 * (1.0f / TILE)) : 0;
+    const int ty0 = sy0 > 0.0f ? (int)(sy0 * (1.0f / TILE)) : 0;
+    const int tx1 = sx1 < v.fw ? (int)(sx1 * (1.0f / TILE)) : tiles_x - 1;
+    const int ty1 = sy1 < v.fh ? (int)(sy1 * (1.0f / TILE)) : tiles_y - 1;
+    if (tx1 - tx0 >= 8 || ty1 - ty0 >= 8) return false;        // larger than 8 x 8 tiles: not tested
+    uint32_t m = 0;
+    for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) m = max(m, __ldg(bound + ty * tiles_x + tx));
+    // an empty pixel leaves the bound at 0xFFFFFFFF (a NaN): never hidden
+    return wlo > __uint_as_float(m);
+}
+
+// Chunk-culling render pass.  prepass != 0: chunks 0, S, 2S, ... in full, one
+// warp per chunk, one point per lane.  prepass == 0: every other chunk, 32
+// chunks per warp step -- each lane tests one chunk against every view, then the
+// warp renders the surviving chunks, up to four at a time (each lane takes one
+// point of each, so four early depth reads are in flight per lane).
+__global__ void __launch_bounds__(256) chunk_render_kernel(const float* __restrict__ xyz, uint64_t n,
+                                                           const float* __restrict__ chunks,
+                                                           const __grid_constant__ RViews vs_arg,
+                                                           const RViews* __restrict__ views_dev,
+                                                           const uint32_t* __restrict__ bound,
+                                                           int prepass, uint32_t S) {
+    __shared__ RViews vs;
+    __shared__ int tile_off[8], tiles_x[8], tiles_y[8];
+    {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(views_dev ? views_dev : &vs_arg);
+        for (int i = threadIdx.x; i < (int)(sizeof(RViews) / 4); i += blockDim.x)
+            reinterpret_cast<uint32_t*>(&vs)[i] = src[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int off = 0;
+        for (int v = 0; v < vs.n; ++v) {
+            tiles_x[v] = (vs.v[v].width + TILE - 1) / TILE;
+            tiles_y[v] = (vs.v[v].height + TILE - 1) / TILE;
+            tile_off[v] = off;
+            off += tiles_x[v] * tiles_y[v];
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const uint32_t nch = (uint32_t)chunk_count(n);
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) / 32;
+    const uint32_t all = (1u << vs.n) - 1u;
+    // up to four chunks: one point of each per lane, then per view four projections,
+    // four early depth reads and the atomics
+    auto render4 = [&](const uint32_t* k, const uint32_t* vm, int cnt) {
+        float x[4], y[4], z[4];
+        uint32_t idx[4];
+        bool in[4];
+        uint32_t vall = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint64_t i = (uint64_t)k[j] * RENDER_CHUNK + lane;
+            in[j] = j < cnt && i < n;
+            idx[j] = (uint32_t)i;
+            x[j] = y[j] = z[j] = 0.0f;
+            if (in[j]) {
+                x[j] = xyz[3 * i];
+                y[j] = xyz[3 * i + 1];
+                z[j] = xyz[3 * i + 2];
+                vall |= vm[j];
+            }
+        }
+        while (vall) {
+            const int v = __ffs(vall) - 1;
+            vall &= vall - 1;
+            const RView& vw = vs.v[v];
+            uint32_t pix[4], db[4];
+            bool ok[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                ok[j] = in[j] && ((vm[j] >> v) & 1u) && project_point(vw, x[j], y[j], z[j], pix[j], db[j]);
+            unsigned long long cur[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) cur[j] = ok[j] ? __ldcg(vw.key + pix[j]) : 0ull;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const unsigned long long key = ((unsigned long long)db[j] << 32) | idx[j];
+                if (ok[j] && key < cur[j]) atomicMin(vw.key + pix[j], key);
+            }
+        }
+    };
+    if (prepass) {
+        // four prepass chunks per warp step
+        for (uint32_t k0 = warp * 4 * S; k0 < nch; k0 += nwarps * 4 * S) {
+            uint32_t k[4], vm[4];
+            int cnt = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                k[j] = k0 + j * S;
+                vm[j] = all;
+                if (k[j] < nch) cnt = j + 1;
+            }
+            render4(k, vm, cnt);
+        }
+        return;
+    }
+    for (uint32_t g = warp; g < (nch + 31) / 32; g += nwarps) {
+        const uint32_t kk = g * 32 + lane;
+        uint32_t vis = 0;
+        if (kk < nch && kk % S != 0) {
+            const float2* cp = reinterpret_cast<const float2*>(chunks + 6 * (size_t)kk);
+            const float2 a = __ldg(cp), b = __ldg(cp + 1), d = __ldg(cp + 2);
+            const float c[3] = {a.x, a.y, b.x}, e[3] = {b.y, d.x, d.y};
+            for (int v = 0; v < vs.n; ++v)
+                if (!chunk_hidden(vs.v[v], c, e, bound ? bound + tile_off[v] : nullptr, tiles_x[v],
+                                  tiles_y[v]))
+                    vis |= 1u << v;
+        }
+        uint32_t todo = __ballot_sync(0xffffffffu, vis != 0);
+        while (todo) {
+            uint32_t k[4] = {0u, 0u, 0u, 0u}, vm[4] = {0u, 0u, 0u, 0u};
+            int cnt = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (todo) {
+                    const int src = __ffs(todo) - 1;
+                    todo &= todo - 1;
+                    k[j] = g * 32 + src;
+                    vm[j] = __shfl_sync(0xffffffffu, vis, src);
+                    cnt = j + 1;
+                }
+            render4(k, vm, cnt);
+        }
+    }
+}
+
 size_t visibility_scratch_bytes(const RViews& views) {
     size_t tiles = 0;
     for (int v = 0; v < views.n; ++v)
@@ -254,14 +479,15 @@ size_t visibility_scratch_bytes(const RViews& views) {
 //
 // A culling variant first renders the leading 1/16 of the points without
 // culling, turns the keys into tile bounds, then renders the rest with culling.
-typedef void (*VisFn)(const float4*, uint64_t, const float*, uint64_t, RViews, const RViews*,
-                      const uint32_t*, uint64_t);
+typedef void (*VisFn)(const float4*, uint32_t, const float*, uint64_t, RViews, const RViews*,
+                      const uint32_t*, uint32_t);
 
 struct VisVariant {
-    VisFn fn;
+    VisFn fn;            // null for a chunk-culling variant
     bool cull;
     const char* name;
     int blocks_per_sm;   // resident blocks, from the compiled register count
+    uint32_t chunk_S;    // chunk culling: every S-th chunk renders in the prepass (0: not chunked)
 };
 
 static VisVariant kSingle[] = {
@@ -271,18 +497,25 @@ static VisVariant kSingle[] = {
     {visibility_kernel<true, true, 3, true>, true, "single/prefetch/3/cull", 0},
     {visibility_kernel<true, false, 3, true>, true, "single/plain/3/cull", 0},
     {visibility_kernel<true, true, 2, true>, true, "single/prefetch/2/cull", 0},
+    {visibility_kernel<true, true, 4, false>, false, "single/prefetch/4", 0},
+    {visibility_kernel<true, false, 4, false>, false, "single/plain/4", 0},
+    {nullptr, true, "single/chunks/16", 0, 16},
+    {nullptr, true, "single/chunks/64", 0, 64},
 };
 static VisVariant kMulti[] = {
     {visibility_kernel<false, true, 3, false>, false, "multi/prefetch/3", 0},
     {visibility_kernel<false, false, 3, false>, false, "multi/plain/3", 0},
     {visibility_kernel<false, true, 3, true>, true, "multi/prefetch/3/cull", 0},
     {visibility_kernel<false, false, 3, true>, true, "multi/plain/3/cull", 0},
+    {nullptr, true, "multi/chunks/16", 0, 16},
+    {nullptr, true, "multi/chunks/64", 0, 64},
 };
 
 static nrv_status resident_blocks(VisVariant& v) {
     if (v.blocks_per_sm) return NRV_OK;
     cudaFuncAttributes fa;
-    NRV_CHECK_CUDA(cudaFuncGetAttributes(&fa, v.fn));
+    if (v.fn) NRV_CHECK_CUDA(cudaFuncGetAttributes(&fa, v.fn));
+    else NRV_CHECK_CUDA(cudaFuncGetAttributes(&fa, chunk_render_kernel));
     const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
     int b = 65536 / (regs_per_warp * 8);
     if (b > 8) b = 8;
@@ -295,28 +528,42 @@ static int g_vis_sms = 0;
 
 static nrv_status run_variant(VisVariant& v, const float* xyz, uint64_t n,
                               const RViews& views, cudaStream_t s, const RViews* views_dev,
-                              uint32_t* tiles) {
+                              uint32_t* tiles, const void* chunks) {
     NRV_TRY(resident_blocks(v));
+    const size_t ntiles = visibility_scratch_bytes(views) / sizeof(uint32_t);
+    if (v.chunk_S) {
+        if (!tiles || !chunks) return fail(NRV_ERR_ARG, "chunk culling needs tiles and chunk bounds");
+        const int blocks = g_vis_sms * v.blocks_per_sm;
+        const float* ch = reinterpret_cast<const float*>(chunks);
+        chunk_render_kernel<<<blocks, 256, 0, s>>>(xyz, n, ch, views, views_dev, nullptr, 1, v.chunk_S);
+        NRV_CHECK_LAUNCH();
+        tile_bound_kernel<<<(unsigned)((ntiles * 32 + 255) / 256), 256, 0, s>>>(views, views_dev, tiles);
+        NRV_CHECK_LAUNCH();
+        chunk_render_kernel<<<blocks, 256, 0, s>>>(xyz, n, ch, views, views_dev, tiles, 0, v.chunk_S);
+        NRV_CHECK_LAUNCH();
+        return NRV_OK;
+    }
     const uint64_t ngroups = n / 4;
     auto launch = [&](uint64_t g0, uint64_t g1, uint64_t npts, const uint32_t* b) -> nrv_status {
         int blocks = g_vis_sms * v.blocks_per_sm;
         const uint64_t need = (g1 - g0 + 255) / 256;
         if (need < (uint64_t)blocks) blocks = (int)(need > 0 ? need : 1);
-        v.fn<<<blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(xyz), g1, xyz, npts, views,
-                                    views_dev, b, g0);
+        v.fn<<<blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(xyz), (uint32_t)g1, xyz, npts,
+                                    views, views_dev, b, (uint32_t)g0);
         NRV_CHECK_LAUNCH();
         return NRV_OK;
     };
     if (!v.cull || !tiles || ngroups < 64) return launch(0, ngroups, n, nullptr);
     const uint64_t gsub = ngroups / 16;
     NRV_TRY(launch(0, gsub, 4 * gsub, nullptr));
-    const size_t ntiles = visibility_scratch_bytes(views) / sizeof(uint32_t);
     tile_bound_kernel<<<(unsigned)((ntiles * 32 + 255) / 256), 256, 0, s>>>(views, views_dev, tiles);
     NRV_CHECK_LAUNCH();
     return launch(gsub, ngroups, n, tiles);
 }
 
-int visibility_variant_count(int multi) { return multi ? 4 : 6; }
+int visibility_variant_count(int multi) {
+    return multi ? (int)(sizeof(kMulti) / sizeof(kMulti[0])) : (int)(sizeof(kSingle) / sizeof(kSingle[0]));
+}
 const char* visibility_variant_name(int multi, int i) { return (multi ? kMulti : kSingle)[i].name; }
 
 static bool verbose() {
@@ -329,7 +576,7 @@ static bool verbose() {
 }
 
 nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, cudaStream_t s,
-                             const RViews* views_dev, uint32_t* tiles) {
+                             const RViews* views_dev, uint32_t* tiles, const void* chunks) {
     if (n == 0) return NRV_OK;
     if (!g_vis_sms) {
         int dev = 0;
@@ -348,7 +595,8 @@ nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, 
         const int i = atoi(e);
         if (i >= 0 && i < count) {
             if (tab[i].cull && !tiles) return fail(NRV_ERR_ARG, "variant %d needs tile scratch", i);
-            return run_variant(tab[i], xyz, n, views, s, views_dev, tiles);
+            if (tab[i].chunk_S && !chunks) return fail(NRV_ERR_ARG, "variant %d needs chunk bounds", i);
+            return run_variant(tab[i], xyz, n, views, s, views_dev, tiles, chunks);
         }
     }
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -361,12 +609,12 @@ nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, 
         float best = 1e30f;
         int arg = 0;
         for (int i = 0; i < count; ++i) {
-            if (tab[i].cull && !tiles) continue;
+            if ((tab[i].cull && !tiles) || (tab[i].chunk_S && !chunks)) continue;
             float ms = 0.0f;
             for (int rep = 0; rep < 2; ++rep) {
                 NRV_TRY(launch_clear_keys(views, s));
                 NRV_CHECK_CUDA(cudaEventRecord(e0, s));
-                NRV_TRY(run_variant(tab[i], xyz, n, views, s, views_dev, tiles));
+                NRV_TRY(run_variant(tab[i], xyz, n, views, s, views_dev, tiles, chunks));
                 NRV_CHECK_CUDA(cudaEventRecord(e1, s));
                 NRV_CHECK_CUDA(cudaEventSynchronize(e1));
                 NRV_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
@@ -383,8 +631,8 @@ nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, 
         NRV_TRY(launch_clear_keys(views, s));
     }
     int pick = choice > 0 ? choice - 1 : 0;
-    if (tab[pick].cull && !tiles) pick = 0;
-    return run_variant(tab[pick], xyz, n, views, s, views_dev, tiles);
+    if ((tab[pick].cull && !tiles) || (tab[pick].chunk_S && !chunks)) pick = 0;
+    return run_variant(tab[pick], xyz, n, views, s, views_dev, tiles, chunks);
 }
 
 // ------------------------------------------------------------------ pack helpers
@@ -435,7 +683,7 @@ __device__ __forceinline__ void store_netin(const ResolveArgs& a, size_t q, cons
 // Resolve pass (Sec. 3.2): one thread per canvas pixel.  Reads the key, gathers
 // the winner's record (one or two 16-byte loads), writes the raw planes and/or
 // the packed network input.
-__global__ void __launch_bounds__(256) resolve_kernel(ResolveArgs a) {
+__global__ void __launch_bounds__(256) resolve_kernel(const __grid_constant__ ResolveArgs a) {
     const int wc = a.netin ? a.wn : a.width, hc = a.netin ? a.hn : a.height;
     const size_t total = (size_t)wc * hc;
     const size_t npx = (size_t)a.width * a.height;
@@ -502,7 +750,7 @@ nrv_status launch_resolve(const ResolveArgs& a, cudaStream_t s) {
 __global__ void __launch_bounds__(256) pack_planes_kernel(const uint32_t* __restrict__ depth,
                                                           const uint8_t* __restrict__ mask,
                                                           const uint32_t* __restrict__ gattr,
-                                                          ResolveArgs a) {
+                                                          const __grid_constant__ ResolveArgs a) {
     const size_t total = (size_t)a.wn * a.hn;
     const size_t npx = (size_t)a.width * a.height;
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;

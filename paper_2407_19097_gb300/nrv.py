@@ -58,10 +58,12 @@ SIGNATURES = {
     "nrv_last_error": (ctypes.c_char_p, []),
     "nrv_version": (I, []),
     "nrv_launch_count": (ctypes.c_uint64, []),
+    "nrv_render_variants": (I, [I]),
     "nrv_pad8": (I, [I]),
     "nrv_netin_channels": (I, [I]),
     "nrv_create_scene": (I, [ctypes.POINTER(nrv_scene_desc), ctypes.POINTER(P)]),
     "nrv_destroy_scene": (I, [P]),
+    "nrv_scene_refresh": (I, [P]),
     "nrv_rasterize": (I, [P, ctypes.POINTER(nrv_view), I, ctypes.POINTER(nrv_gbuffer), P]),
     "nrv_pack": (I, [ctypes.POINTER(nrv_gbuffer), I, I, ctypes.POINTER(nrv_pack_desc), I, F, P, P]),
     "nrv_net_num_layers": (I, []),

@@ -37,6 +37,8 @@ def test_host_side_queries(lib):
     assert lib.nrv_version() == 1
     assert lib.nrv_pad8(540) == 544 and lib.nrv_pad8(1080) == 1080
     assert lib.nrv_netin_channels(nrv.PREC_FP8) == 16 and lib.nrv_netin_channels(nrv.PREC_BF16) == 8
+    # render-pass variants: brute force and culling ones, for one view and for batches
+    assert lib.nrv_render_variants(0) >= 4 and lib.nrv_render_variants(1) >= 4
     for c0 in (3, 5, 6, 7):
         assert nrv.param_count(c0) == unet.param_count(c0)
         table = nrv.layer_table(c0)
@@ -63,6 +65,8 @@ def test_argument_errors(lib):
     d = nrv.nrv_scene_desc(0, None, None, 4, 3)      # empty scene is valid
     assert lib.nrv_create_scene(ctypes.byref(d), ctypes.byref(h)) == nrv.NRV_OK
     assert lib.nrv_rasterize(h, None, 1, None, None) == nrv.NRV_ERR_ARG
+    assert lib.nrv_scene_refresh(h) == nrv.NRV_OK
+    assert lib.nrv_scene_refresh(None) == nrv.NRV_ERR_ARG
     assert lib.nrv_destroy_scene(h) == nrv.NRV_OK
     assert lib.nrv_create_net(9, ctypes.byref(h)) == nrv.NRV_ERR_ARG
     assert lib.nrv_create_net(5, ctypes.byref(h)) == nrv.NRV_OK

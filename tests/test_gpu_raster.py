@@ -105,3 +105,62 @@ def test_pack_bit_exact(prec, cpad):
     got = got.view(np.uint16) if prec == 1 else got
     assert np.array_equal(got, ref)
     assert (om > 0).mean() > 0.05
+
+
+def _pinned(i, fn):
+    import os
+    os.environ["NRV_VIS_VARIANT"] = str(i)
+    try:
+        return fn()
+    finally:
+        del os.environ["NRV_VIS_VARIANT"]
+
+
+def _every_variant(sc, views, scene=None):
+    """Keys and planes of every render-pass variant (chunk culling included) equal the oracle's."""
+    from paper_2407_19097_gb300 import nrv
+    scene = scene or upload_scene(sc)
+    refs = [oracle.rasterize(sc, v) for v in views]
+    count = nrv.lib().nrv_render_variants(1 if len(views) > 1 else 0)
+    assert count >= 2
+    for i in range(count):
+        got = _pinned(i, lambda: gpu_raster(scene, views))
+        for g, ref in zip(got, refs):
+            for a, b in zip(g, ref):
+                assert np.array_equal(a, b), f"variant {i}: {(a != b).sum()} pixels differ"
+    return refs
+
+
+def test_every_variant_ragged_single_and_multi_view():
+    # n = 105035: neither a multiple of 4 nor of the 32-point chunk
+    sc = I.trajectory_scene(3001, 35, seed=2)
+    views = [I.fitted_view(sc, 1920, 1080), I.fitted_view(sc, 37, 23, direction=(1, 0.3, 0.2))]
+    _every_variant(sc, views[:1])
+    _every_variant(sc, views)
+
+
+def test_every_variant_camera_inside_the_cloud():
+    # chunks straddle the near plane, lie behind the camera and beyond the far plane
+    sc = I.cube_scene(400_003, k=3, seed=4)
+    v = I.make_view((0.5, 0.45, 0.52), (0.9, 0.6, 0.1), 640, 480, znear=0.05, zfar=0.6)
+    refs = _every_variant(sc, [v])
+    assert (refs[0][2] > 0).mean() > 0.05
+
+
+def test_scene_refresh_after_points_move():
+    import dataclasses
+    import torch
+    from paper_2407_19097_gb300 import nrv
+    sc = I.trajectory_scene(20000, 50, seed=3)          # 1M points: chunks mostly hidden
+    v = I.fitted_view(sc, 640, 480)
+    scene = upload_scene(sc)
+    _every_variant(sc, [v], scene)
+    # pull every 7th chunk of 32 points halfway towards the camera: hidden chunks become visible
+    xyz = sc.xyz.copy()
+    eye = np.asarray(v.eye, np.float32)
+    idx = np.arange(len(xyz))
+    sel = (idx // 32) % 7 == 3
+    xyz[sel] = 0.5 * xyz[sel] + 0.5 * eye
+    scene.xyz.copy_(torch.from_numpy(xyz).to(scene.xyz.device))
+    nrv.check(nrv.lib().nrv_scene_refresh(scene.h))
+    _every_variant(dataclasses.replace(sc, xyz=xyz), [v], scene)
