@@ -346,9 +346,11 @@ __device__ __forceinline__ bool chunk_hidden(const RView& v, const float* c, con
 
 // Chunk-culling render pass.  prepass != 0: chunks 0, S, 2S, ... in full, one
 // warp per chunk, one point per lane.  prepass == 0: every other chunk, 32
-// chunks per warp step -- each lane tests one chunk against every view, then the
-// warp renders the surviving chunks, up to four at a time (each lane takes one
-// point of each, so four early depth reads are in flight per lane).
+// chunks per warp step -- each lane tests one chunk against every view and the
+// survivors join the warp's queue in shared memory; whenever four are queued the
+// warp renders them (each lane takes one point of each, so four early depth
+// reads are in flight per lane).  Rendering only full groups of four keeps the
+// lanes busy: a group costs the same instructions however many chunks it holds.
 __global__ void __launch_bounds__(256) chunk_render_kernel(const float* __restrict__ xyz, uint64_t n,
                                                            const float* __restrict__ chunks,
                                                            const __grid_constant__ RViews vs_arg,
@@ -432,6 +434,22 @@ __global__ void __launch_bounds__(256) chunk_render_kernel(const float* __restri
         }
         return;
     }
+    // this warp's queue of surviving chunks (at most 3 left over + 32 new)
+    __shared__ uint32_t q_k[8][36];
+    __shared__ uint8_t q_m[8][36];
+    uint32_t* qk = q_k[threadIdx.x / 32];
+    uint8_t* qm = q_m[threadIdx.x / 32];
+    int qn = 0;   // queued, the same in every lane
+    auto render_queued = [&](int from, int cnt) {
+        uint32_t k[4] = {0u, 0u, 0u, 0u}, vm[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (j < cnt) {
+                k[j] = qk[from + j];
+                vm[j] = qm[from + j];
+            }
+        render4(k, vm, cnt);
+    };
     for (uint32_t g = warp; g < (nch + 31) / 32; g += nwarps) {
         const uint32_t kk = g * 32 + lane;
         uint32_t vis = 0;
@@ -444,22 +462,21 @@ __global__ void __launch_bounds__(256) chunk_render_kernel(const float* __restri
                                   tiles_y[v]))
                     vis |= 1u << v;
         }
-        uint32_t todo = __ballot_sync(0xffffffffu, vis != 0);
-        while (todo) {
-            uint32_t k[4] = {0u, 0u, 0u, 0u}, vm[4] = {0u, 0u, 0u, 0u};
-            int cnt = 0;
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (todo) {
-                    const int src = __ffs(todo) - 1;
-                    todo &= todo - 1;
-                    k[j] = g * 32 + src;
-                    vm[j] = __shfl_sync(0xffffffffu, vis, src);
-                    cnt = j + 1;
-                }
-            render4(k, vm, cnt);
+        const uint32_t ball = __ballot_sync(0xffffffffu, vis != 0);
+        if (vis) {
+            const int at = qn + __popc(ball & ((1u << lane) - 1u));
+            qk[at] = kk;
+            qm[at] = (uint8_t)vis;
         }
+        qn += __popc(ball);
+        __syncwarp();
+        while (qn >= 4) {
+            qn -= 4;
+            render_queued(qn, 4);
+        }
+        __syncwarp();
     }
+    if (qn > 0) render_queued(0, qn);
 }
 
 size_t visibility_scratch_bytes(const RViews& views) {
