@@ -252,7 +252,7 @@ __global__ void tile_bound_kernel(RViews vs_arg, const RViews* __restrict__ view
 // box (centre and half extents) computed from the positions once per scene.  A
 // chunk-culling render pass renders every S-th chunk in full, turns the keys
 // into tile depth bounds, then tests every other chunk's box against them, view
-// by view: a chunk wholly outside the depth range or the screen, or whose
+// by view (in one or two parts, the bounds rebuilt before the second): a chunk wholly outside the depth range or the screen, or whose
 // nearest possible depth lies behind every pixel of the tiles it can touch, is
 // skipped; the others render point by point.  Keys do not change: a skipped
 // point could not have set one (keys only decrease, so a bound read earlier
@@ -345,8 +345,8 @@ __device__ __forceinline__ bool chunk_hidden(const RView& v, const float* c, con
 }
 
 // Chunk-culling render pass.  prepass != 0: chunks 0, S, 2S, ... in full, one
-// warp per chunk, one point per lane.  prepass == 0: every other chunk, 32
-// chunks per warp step -- each lane tests one chunk against every view and the
+// warp per chunk, one point per lane.  prepass == 0: every other chunk of the
+// groups [g_begin, g_end), 32 chunks per warp step -- each lane tests one chunk against every view and the
 // survivors join the warp's queue in shared memory; whenever four are queued the
 // warp renders them (each lane takes one point of each, so four early depth
 // reads are in flight per lane).  Rendering only full groups of four keeps the
@@ -356,7 +356,8 @@ __global__ void __launch_bounds__(256) chunk_render_kernel(const float* __restri
                                                            const __grid_constant__ RViews vs_arg,
                                                            const RViews* __restrict__ views_dev,
                                                            const uint32_t* __restrict__ bound,
-                                                           int prepass, uint32_t S) {
+                                                           int prepass, uint32_t S, uint32_t g_begin,
+                                                           uint32_t g_end) {
     __shared__ RViews vs;
     __shared__ int tile_off[8], tiles_x[8], tiles_y[8];
     {
@@ -450,7 +451,8 @@ __global__ void __launch_bounds__(256) chunk_render_kernel(const float* __restri
             }
         render4(k, vm, cnt);
     };
-    for (uint32_t g = warp; g < (nch + 31) / 32; g += nwarps) {
+    // culled pass over the chunk groups [g_begin, g_end) of 32 chunks
+    for (uint32_t g = g_begin + warp; g < g_end; g += nwarps) {
         const uint32_t kk = g * 32 + lane;
         uint32_t vis = 0;
         if (kk < nch && kk % S != 0) {
@@ -505,6 +507,7 @@ struct VisVariant {
     const char* name;
     int blocks_per_sm;   // resident blocks, from the compiled register count
     uint32_t chunk_S;    // chunk culling: every S-th chunk renders in the prepass (0: not chunked)
+    int phases;          // chunk culling: culled passes, tile bounds rebuilt before each
 };
 
 static VisVariant kSingle[] = {
@@ -516,16 +519,18 @@ static VisVariant kSingle[] = {
     {visibility_kernel<true, true, 2, true>, true, "single/prefetch/2/cull", 0},
     {visibility_kernel<true, true, 4, false>, false, "single/prefetch/4", 0},
     {visibility_kernel<true, false, 4, false>, false, "single/plain/4", 0},
-    {nullptr, true, "single/chunks/16", 0, 16},
-    {nullptr, true, "single/chunks/64", 0, 64},
+    {nullptr, true, "single/chunks/16", 0, 16, 1},
+    {nullptr, true, "single/chunks/16x2", 0, 16, 2},
+    {nullptr, true, "single/chunks/16x4", 0, 16, 4},
 };
 static VisVariant kMulti[] = {
     {visibility_kernel<false, true, 3, false>, false, "multi/prefetch/3", 0},
     {visibility_kernel<false, false, 3, false>, false, "multi/plain/3", 0},
     {visibility_kernel<false, true, 3, true>, true, "multi/prefetch/3/cull", 0},
     {visibility_kernel<false, false, 3, true>, true, "multi/plain/3/cull", 0},
-    {nullptr, true, "multi/chunks/16", 0, 16},
-    {nullptr, true, "multi/chunks/64", 0, 64},
+    {nullptr, true, "multi/chunks/16", 0, 16, 1},
+    {nullptr, true, "multi/chunks/16x2", 0, 16, 2},
+    {nullptr, true, "multi/chunks/16x4", 0, 16, 4},
 };
 
 static nrv_status resident_blocks(VisVariant& v) {
@@ -552,12 +557,21 @@ static nrv_status run_variant(VisVariant& v, const float* xyz, uint64_t n,
         if (!tiles || !chunks) return fail(NRV_ERR_ARG, "chunk culling needs tiles and chunk bounds");
         const int blocks = g_vis_sms * v.blocks_per_sm;
         const float* ch = reinterpret_cast<const float*>(chunks);
-        chunk_render_kernel<<<blocks, 256, 0, s>>>(xyz, n, ch, views, views_dev, nullptr, 1, v.chunk_S);
+        const uint32_t ngroups = (uint32_t)((chunk_count(n) + 31) / 32);
+        chunk_render_kernel<<<blocks, 256, 0, s>>>(xyz, n, ch, views, views_dev, nullptr, 1, v.chunk_S,
+                                                   0u, 0u);
         NRV_CHECK_LAUNCH();
-        tile_bound_kernel<<<(unsigned)((ntiles * 32 + 255) / 256), 256, 0, s>>>(views, views_dev, tiles);
-        NRV_CHECK_LAUNCH();
-        chunk_render_kernel<<<blocks, 256, 0, s>>>(xyz, n, ch, views, views_dev, tiles, 0, v.chunk_S);
-        NRV_CHECK_LAUNCH();
+        // the chunk groups in `phases` consecutive parts, the tile bounds rebuilt from the
+        // keys so far before each part (later parts meet tighter bounds)
+        for (int ph = 0; ph < v.phases; ++ph) {
+            const uint32_t g0 = (uint32_t)((uint64_t)ngroups * ph / v.phases);
+            const uint32_t g1 = (uint32_t)((uint64_t)ngroups * (ph + 1) / v.phases);
+            tile_bound_kernel<<<(unsigned)((ntiles * 32 + 255) / 256), 256, 0, s>>>(views, views_dev, tiles);
+            NRV_CHECK_LAUNCH();
+            chunk_render_kernel<<<blocks, 256, 0, s>>>(xyz, n, ch, views, views_dev, tiles, 0,
+                                                       v.chunk_S, g0, g1);
+            NRV_CHECK_LAUNCH();
+        }
         return NRV_OK;
     }
     const uint64_t ngroups = n / 4;
