@@ -53,7 +53,7 @@ constexpr int PLANE = 2048;   // bytes of one (row, 16-byte channel chunk) plane
 constexpr int MAX_KS = 80;
 constexpr int MAX_SLOTS = 8;
 constexpr int TILE_M = 128;
-constexpr int NTHREADS = 192;
+constexpr int NTHREADS = 224;   // producer, MMA issuer, 4 epilogue warps, second MMA issuer
 
 struct TcParams {
     int n, h, w;             // input level geometry
@@ -65,6 +65,8 @@ struct TcParams {
     int nks;                 // K-steps (two 16-byte halves each)
     int rows, row0;          // input rows per tile, first one relative to the tile's row
     int nslot;               // row slots in the ring
+    int nissue;              // MMA issuers (1 or 2): issuer i takes the K-steps ks = i (mod nissue)
+                             // into its own partial accumulator, the epilogue adds them
     int cout;                // output channels
     int out_nch;             // 16-byte planes per output row
     int mode;                // 0: 3x3 conv + bias + ReLU; 1: 2x2 stride-2 transposed conv + bias
@@ -269,13 +271,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_init(b_w, 1);
         for (int i = 0; i < MAX_SLOTS; ++i) {
             mbar_init(b_hfull(i), 1);
-            mbar_init(b_hempty(i), 1);
+            mbar_init(b_hempty(i), P.nissue);
         }
         for (int i = 0; i < 2; ++i) {
-            mbar_init(b_afull(i), 1);
+            mbar_init(b_afull(i), P.nissue);
             mbar_init(b_aempty(i), 4);
         }
-        mbar_init(b_done, 1);
+        mbar_init(b_done, P.nissue);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -346,8 +348,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             mbar_wait(b_w, 0, &abort_flag, P.status, false);
         }
-    } else if (warp == 1) {
-        if (lane == 0) {
+    } else if (warp == 1 || warp == 6) {
+        const int iss = warp == 1 ? 0 : 1;   // this warp's issuer number
+        if (lane == 0 && iss < P.nissue) {
             bool ok = mbar_wait(b_w, 0, &abort_flag, P.status);
             // descriptor high words: SBO = 128 bytes, version 1; B: K halves n_slice * 16 bytes apart
             const uint64_t hi = (uint64_t)((128u >> 4) | (1u << 14)) << 32;
@@ -356,6 +359,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint32_t b_step = (2 * b_lbo) >> 4;
             const uint32_t ring16 = s_ring >> 4, slot16 = P.slot_bytes >> 4;
             const int ks_row = P.nks / P.rows;   // K-steps per input row
+            const int nis = P.nissue;
             TileWalk w;
             w.init(P, t_begin);
             int cur_col = -1, next_row = 0;
@@ -388,22 +392,29 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 // the tile's rows y+row0 .. y+row0+rows-1 are the last `rows` loads
                 int s0 = end_slot - P.rows;
                 if (s0 < 0) s0 += P.nslot;
-                const uint32_t d = tmem + (uint32_t)(ab * P.n_slice);
-                uint32_t b_lo = b_lo0;
-                int ks = 0;
-                for (int k = 0; k < P.rows; ++k) {
-                    const uint32_t base = ring16 + (uint32_t)s0 * slot16;
-                    if (++s0 == P.nslot) s0 = 0;
-                    uint32_t e = alo_s[0];
-                    for (int j = 0; j < ks_row; ++j, ++ks) {
-                        const uint32_t e_next = alo_s[j + 1];   // read ahead
-                        const uint64_t a = hi | (uint64_t)(base + e);
-                        const uint64_t b = hi | (uint64_t)b_lo;
-                        if (FP8) mma_fp8(d, a, b, P.idesc, ks > 0 ? 1u : 0u);
-                        else mma_bf16(d, a, b, P.idesc, ks > 0 ? 1u : 0u);
-                        e = e_next;
-                        b_lo += b_step;
+                const uint32_t d = tmem + (uint32_t)((ab * nis + iss) * P.n_slice);
+                // K-steps iss, iss + nis, ...: row k = ks / ks_row, position j = ks % ks_row
+                uint32_t b_lo = b_lo0 + (uint32_t)iss * b_step;
+                const uint32_t b_adv = (uint32_t)nis * b_step;
+                uint32_t base = ring16 + (uint32_t)s0 * slot16;
+                int j = iss;
+                uint32_t e = alo_s[j];
+                for (int ks = iss; ks < P.nks; ks += nis) {
+                    int jn = j + nis;                              // next position, read ahead
+                    const bool wrap = jn >= ks_row;
+                    if (wrap) jn -= ks_row;
+                    const uint32_t e_next = alo_s[jn];
+                    const uint64_t a = hi | (uint64_t)(base + e);
+                    const uint64_t b = hi | (uint64_t)b_lo;
+                    if (FP8) mma_fp8(d, a, b, P.idesc, ks >= nis ? 1u : 0u);
+                    else mma_bf16(d, a, b, P.idesc, ks >= nis ? 1u : 0u);
+                    if (wrap) {
+                        if (++s0 == P.nslot) s0 = 0;
+                        base = ring16 + (uint32_t)s0 * slot16;
                     }
+                    j = jn;
+                    e = e_next;
+                    b_lo += b_adv;
                 }
                 // release the rows the next tile of this run no longer reads
                 int keep = loaded;
@@ -420,11 +431,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 mma_commit(b_afull(ab));
                 w = w2;
             }
-            // wait until every MMA issued above has completed
+            // wait until every MMA issued above (by both issuers) has completed
             mma_commit(b_done);
             mbar_wait(b_done, 0, &abort_flag, P.status, false);
         }
-    } else {
+    } else if (warp >= 2 && warp <= 5) {
         // epilogue: warps 2..5 own TMEM lanes 32*(warp%4) ..; one lane per warp polls
         const int q = warp & 3;
         const int m = 32 * q + lane;
@@ -440,14 +451,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             tc_fence_after();
             const int x = w.xt * P.tile_w + m;
             const bool valid = m < P.tile_w && x < P.w;
-            const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * P.n_slice);
+            const uint32_t tbase =
+                tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * P.nissue * P.n_slice);
             for (int c0 = 0; c0 < P.n_slice; c0 += 16) {
                 uint32_t v32[16];
                 tmem_ld16(tbase + (uint32_t)c0, v32);
+                float acc[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc[j] = __uint_as_float(v32[j]);
+                if (P.nissue == 2) {
+                    tmem_ld16(tbase + (uint32_t)(P.n_slice + c0), v32);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) acc[j] += __uint_as_float(v32[j]);
+                }
                 float v[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    v[j] = fmaf(__uint_as_float(v32[j]), colscale_s[c0 + j], bias_s[c0 + j]);
+                    v[j] = fmaf(acc[j], colscale_s[c0 + j], bias_s[c0 + j]);
                     if (P.mode == 0) v[j] = fmaxf(v[j], 0.0f);
                 }
                 if (valid) {
@@ -833,8 +853,11 @@ static nrv_status tc_launch(const Net* net, int l, const void* x1, int c1, const
     P.tx_bytes = (nch1 + nch2) * PLANE;
     P.w_bytes = c.w_bytes;
     P.w_region = (c.w_bytes + 1023) / 1024 * 1024;
+    // two MMA issuers where both partial accumulators of both tile buffers fit in 256
+    // TMEM columns and every input row has at least two K-steps (the issue loop's read-ahead)
+    P.nissue = (4 * c.n_slice <= 256 && c.nks / c.rows >= 2) ? 2 : 1;
     uint32_t cols = 32;
-    while (cols < (uint32_t)(2 * c.n_slice)) cols *= 2;
+    while (cols < (uint32_t)(2 * P.nissue * c.n_slice)) cols *= 2;
     P.tmem_cols = cols;
     auto kern = fp8 ? conv3_tc_kernel<true> : conv3_tc_kernel<false>;
     static bool attr_set[2] = {false, false};
