@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-fp8", action="store_true")
+    ap.add_argument("--config", default="c3", choices=["c3", "c2", "c4", "c5"],
+                    help="c3 (default): the 350M-point trajectory frame; c2: 50M-point vortex grid "
+                         "frame with network precision vs FP64; c4: 200M-point terrain, 8 views of "
+                         "uneven size in one batch; c5: training step time and held-out quality")
     return ap.parse_args()
 
 
@@ -207,6 +211,225 @@ def run_reference(a, rank, world):
     print(json.dumps(line), flush=True)
 
 
+
+def _events_ms(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _quality(got, ref):
+    import numpy as np
+    r = float(ref.max() - ref.min())
+    mse = float(np.mean((got - ref) ** 2))
+    return {"psnr_db": 10 * np.log10(r * r / mse) if mse > 0 else None,
+            "max_abs": float(np.abs(got - ref).max())}
+
+
+def run_c2(a):
+    """50M-point jittered vortex grid (K = 5), one 1080p view: render + resolve + pack rate, and
+    the network in FP32, BF16 and FP8 -- time and error against the FP64 oracle on this frame."""
+    import numpy as np
+    import torch
+    import nrv_inputs as I
+    from oracle import unet
+    import oracle
+    from paper_2407_19097_gb300 import nrv
+    dev = torch.device("cuda", 0)
+    t0 = time.time()
+    sc = I.vortex_grid_scene(368, seed=1)
+    view = I.cube_view(1920, 1080)
+    ds, do = I.depth_normalisation(sc, view)
+    gen_s = time.time() - t0
+    c0 = len(sc.channels) + 2
+    scene = nrv.Scene(torch.from_numpy(sc.xyz).to(dev), torch.from_numpy(sc.attr.view(np.int32)).to(dev),
+                      sc.n_words)
+    net = nrv.Net(c0)
+    net.set_params(torch.from_numpy(unet_params(c0)).to(dev))
+    desc = nrv.make_pack_desc(sc.channels, ds, do)
+    H, W = view.height, view.width
+    rgb = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, prec in (("fp32", nrv.PREC_F32), ("bf16", nrv.PREC_BF16)):
+        nrv.set_profiling(True)
+        ms = _events_ms(lambda: nrv.render_batch(scene, net, desc, [view], [rgb], prec), a.steps, a.warmup,
+                        stream)
+        nrv.set_profiling(False)
+        st = nrv.timings()
+        out[name] = {"frame_ms": ms, "render_ms": st[1], "resolve_pack_ms": st[2], "network_ms": st[3],
+                     "rgb": rgb.float().cpu().numpy().astype(np.float64)}
+    # FP8, calibrated on this frame's BF16 input
+    key = torch.empty((H, W), dtype=torch.int64, device=dev)
+    dpl = torch.empty((H, W), dtype=torch.int32, device=dev)
+    msk = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    gat = torch.empty((sc.n_words, H, W), dtype=torch.int32, device=dev)
+    nrv.rasterize(scene, [view], [key], [dpl], [msk], [gat])
+    xb = torch.empty(((H + 7) // 8 * 8, (W + 7) // 8 * 8, 8), dtype=torch.bfloat16, device=dev)
+    nrv.pack(dpl, msk, gat, H, W, desc, nrv.PREC_BF16, xb)
+    net.calibrate(xb, 1, H, W)
+    inv8 = 1.0 / net.act_scales()[0]
+    nrv.set_profiling(True)
+    ms8 = _events_ms(lambda: nrv.render_batch(scene, net, desc, [view], [rgb], nrv.PREC_FP8, inv8),
+                     a.steps, a.warmup, stream)
+    nrv.set_profiling(False)
+    st = nrv.timings()
+    out["fp8"] = {"frame_ms": ms8, "render_ms": st[1], "resolve_pack_ms": st[2], "network_ms": st[3],
+                  "rgb": rgb.float().cpu().numpy().astype(np.float64)}
+    # the FP64 oracle frame
+    _, d, m, g = oracle.rasterize(sc, view)
+    hn, wn = (H + 7) // 8 * 8, (W + 7) // 8 * 8
+    x = oracle.pack(d, m, g, sc.channels, ds, do, hn, wn, 8, 0)
+    y = unet.forward(x[None, :, :, :c0].astype(np.float64), unet.unflatten(unet_params(c0), c0))[0][:H, :W]
+    line = {"config": "c2", "metric": "points/s (frames/s) at 1080p",
+            "workload": f"vortex grid 368^3 = {sc.n} points, K=5, 1920x1080", "data": "synthetic",
+            "value": sc.n / (out["bf16"]["frame_ms"] * 1e-3), "unit": "points/s",
+            "render_points_per_s": sc.n / ((out["bf16"]["render_ms"] + out["bf16"]["resolve_pack_ms"]) * 1e-3),
+            "scene_gen_s": gen_s}
+    for k, v in out.items():
+        line[k] = {kk: vv for kk, vv in v.items() if kk != "rgb"}
+        line[k]["vs_fp64"] = _quality(v["rgb"], y)
+    print(json.dumps(line), flush=True)
+
+
+def run_c4(a):
+    """200M-point terrain (RGB u8x4 + intensity), 8 views of uneven size (2 x 2160^2 stereo,
+    4 x 1920x1080, 2 x 960x540) rendered and shaded in one nrv_render_batch call."""
+    import numpy as np
+    import torch
+    import nrv_inputs as I
+    from paper_2407_19097_gb300 import nrv
+    dev = torch.device("cuda", 0)
+    t0 = time.time()
+    sc = I.terrain_scene(14142, seed=7)
+    sizes = [(2160, 2160), (2160, 2160), (1920, 1080), (1920, 1080), (1920, 1080), (1920, 1080),
+             (960, 540), (960, 540)]
+    views = I.orbit_views(sc, sizes, seed=11, stereo_pairs=1)
+    ds, do = I.depth_normalisation(sc, views[2])
+    gen_s = time.time() - t0
+    c0 = len(sc.channels) + 2
+    scene = nrv.Scene(torch.from_numpy(sc.xyz).to(dev), torch.from_numpy(sc.attr.view(np.int32)).to(dev),
+                      sc.n_words)
+    net = nrv.Net(c0)
+    net.set_params(torch.from_numpy(unet_params(c0)).to(dev))
+    desc = nrv.make_pack_desc(sc.channels, ds, do)
+    rgbs = [torch.empty((v.height, v.width, 3), dtype=torch.float32, device=dev) for v in views]
+    stream = torch.cuda.current_stream()
+    ms = _events_ms(lambda: nrv.render_batch(scene, net, desc, views, rgbs, nrv.PREC_BF16), a.steps,
+                    a.warmup, stream)
+    nrv.set_profiling(True)
+    _events_ms(lambda: nrv.render_batch(scene, net, desc, views, rgbs, nrv.PREC_BF16), 5, 1, stream)
+    nrv.set_profiling(False)
+    st = nrv.timings()
+    px = sum(v.width * v.height for v in views)
+    line = {"config": "c4", "metric": "aggregate point-views/s and frames/s, 8 views",
+            "workload": f"terrain 14142^2 = {sc.n} points, 8 views {sizes}", "data": "synthetic",
+            "value": sc.n * len(views) / (ms * 1e-3), "unit": "point-views/s",
+            "frames_per_s": len(views) / (ms * 1e-3), "batch_ms": ms, "pixels_per_batch": px,
+            "stages_ms": {"clear": st[0], "render_pass_all_views": st[1], "resolve_pack": st[2],
+                          "network_all_views": st[3]},
+            "precision": "bf16", "scene_gen_s": gen_s}
+    print(json.dumps(line), flush=True)
+
+
+def run_c5(a):
+    """Training (Sec. 3.3): the U-Net learns to turn G-buffers of a trajectory scene into
+    Gaussian-splat targets (the CPU splatter standing in for the paper's Gaussian Renderer).
+    56 training and 8 held-out hemisphere views at 512^2, random 256^2 crops, batch 16, Adam
+    lr 1e-3, BF16 forward/backward.  Reports the step time and held-out PSNR/SSIM of the trained
+    network and of the method without it (transfer-function colour of the winning point)."""
+    import numpy as np
+    import torch
+    import nrv_inputs as I
+    import oracle
+    from oracle import metrics
+    from paper_2407_19097_gb300 import nrv
+    dev = torch.device("cuda", 0)
+    steps = 2000
+    t0 = time.time()
+    sc = I.trajectory_scene(20000, 350, seed=2)
+    colours = I.point_colours(sc)
+    size, n_views, n_train, crop, batch = 512, 64, 56, 256, 16
+    views = I.hemisphere_views(sc, n_views, size, size, seed=5)
+    c0 = len(sc.channels) + 2
+    scene = nrv.Scene(torch.from_numpy(sc.xyz).to(dev), torch.from_numpy(sc.attr.view(np.int32)).to(dev),
+                      sc.n_words)
+    ds, do = I.depth_normalisation(sc, views[0])
+    desc = nrv.make_pack_desc(sc.channels, ds, do)
+    X, targets, baselines = [], [], []
+    for v in views:
+        key = torch.empty((size, size), dtype=torch.int64, device=dev)
+        depth = torch.empty((size, size), dtype=torch.int32, device=dev)
+        mask = torch.empty((size, size), dtype=torch.uint8, device=dev)
+        gattr = torch.empty((sc.n_words, size, size), dtype=torch.int32, device=dev)
+        nrv.rasterize(scene, [v], [key], [depth], [mask], [gattr])
+        x = torch.empty((size, size, 8), dtype=torch.bfloat16, device=dev)
+        nrv.pack(depth, mask, gattr, size, size, desc, nrv.PREC_BF16, x)
+        X.append(x)
+        targets.append(np.clip(oracle.splat(sc.xyz, v, colours), 0.0, 1.0).astype(np.float32))
+        k = key.cpu().numpy().view(np.uint64)
+        hit = k != np.uint64(0xFFFFFFFFFFFFFFFF)
+        base = np.zeros((size, size, 3), np.float32)
+        base[hit] = colours[(k[hit] & np.uint64(0xFFFFFFFF)).astype(np.int64)]
+        baselines.append(base)
+    X = torch.stack(X)
+    T = torch.from_numpy(np.stack(targets)).to(dev)
+    prep_s = time.time() - t0
+    net = nrv.Net(c0)
+    p = torch.empty((nrv.param_count(c0),), device=dev)
+    net.init_params(1, p)
+    g, m, vv = torch.zeros_like(p), torch.zeros_like(p), torch.zeros_like(p)
+    loss = torch.zeros(1, device=dev)
+    xb = torch.empty((batch, crop, crop, 8), dtype=torch.bfloat16, device=dev)
+    tb = torch.empty((batch, crop, crop, 3), dtype=torch.float32, device=dev)
+    crops = [I.random_crops(9, s, batch, n_train, size, size, crop) for s in range(steps)]
+    stream = torch.cuda.current_stream()
+
+    def fill(s):
+        for b, (vi, y0, x0) in enumerate(crops[s]):
+            xb[b].copy_(X[vi, y0:y0 + crop, x0:x0 + crop])
+            tb[b].copy_(T[vi, y0:y0 + crop, x0:x0 + crop])
+
+    # crops are gathered outside the timed region; the step is forward, loss, backward, Adam
+    step_ms, losses = [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for s in range(steps):
+        fill(s)
+        if s >= 10:
+            e0.record(stream)
+        net.train_step(p, g, m, vv, s + 1, 1e-3, xb, tb, batch, crop, crop, nrv.PREC_BF16, loss)
+        if s >= 10:
+            e1.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+        if (s + 1) % 200 == 0:
+            losses.append(float(loss.item()))
+    out = torch.empty((n_views - n_train, size, size, 3), device=dev)
+    net.shade(X[n_train:].contiguous(), n_views - n_train, size, size, nrv.PREC_BF16, out)
+    torch.cuda.synchronize()
+    y = np.clip(out.cpu().numpy(), 0.0, 1.0)
+    held = range(n_views - n_train)
+    line = {"config": "c5", "metric": "training step time (ms) and held-out PSNR vs splat targets",
+            "workload": f"trajectories 20000x350 = {sc.n} points, {n_train}+{n_views - n_train} views "
+                        f"at {size}^2, {crop}^2 crops, batch {batch}, {steps} steps",
+            "data": "synthetic", "value": float(np.median(step_ms)), "unit": "ms/step",
+            "higher_is_better": False, "precision": "bf16",
+            "pixels_per_step": batch * crop * crop,
+            "held_out_psnr_db": {"network": float(np.mean([metrics.psnr(y[i], targets[n_train + i]) for i in held])),
+                                 "rasterizer_alone": float(np.mean([metrics.psnr(baselines[n_train + i], targets[n_train + i]) for i in held]))},
+            "held_out_ssim": {"network": float(np.mean([metrics.ssim(y[i], targets[n_train + i]) for i in held])),
+                              "rasterizer_alone": float(np.mean([metrics.ssim(baselines[n_train + i], targets[n_train + i]) for i in held]))},
+            "loss_every_200_steps": losses, "prep_s": prep_s}
+    print(json.dumps(line), flush=True)
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -214,6 +437,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if a.impl == "reference":
         return run_reference(a, rank, world)
+    if a.config != "c3":
+        import __graft_entry__
+        __graft_entry__.build()
+        return {"c2": run_c2, "c4": run_c4, "c5": run_c5}[a.config](a)
 
     import numpy as np
     import torch

@@ -219,6 +219,31 @@ nrv_status nrv_destroy_net(nrv_net* net);
  * again after the parameters change.  Errors: NRV_ERR_ARG. */
 nrv_status nrv_net_set_params(nrv_net* net, const float* d_params, nrv_stream stream);
 
+/* Fill the caller's d_params (parameter count floats, device) with a seeded
+ * Xavier-uniform draw and load it: biases 0; element i of layer t's weight (in
+ * the layout above) = the FP32 value nearest to -b + 2b*u, b = sqrt(6 / (fan_in
+ * + fan_out)), fan = channels x kernel area, u = the top 53 bits of output i of
+ * SplitMix64 stream 1000 + t as a double in [0, 1).  The stream's state is the
+ * (stream)-th output of the SplitMix64 sequence seeded with `seed`; the i-th
+ * output of a sequence with state s is mix(s + (i+1) * 0x9E3779B97F4A7C15).  The
+ * paper trains its network from scratch (Sec. 3.3) and gives no initialisation;
+ * this is the library's.  Errors: NRV_ERR_ARG. */
+nrv_status nrv_net_init_params(nrv_net* net, uint64_t seed, float* d_params, nrv_stream stream);
+
+/* Copy the net's FP32 parameters (layout above) to the caller's device buffer.
+ * Errors: NRV_ERR_ARG, NRV_ERR_STATE (no parameters loaded). */
+nrv_status nrv_net_get_params(const nrv_net* net, float* d_out, nrv_stream stream);
+
+/* Save the parameters and, when set, the FP8 activation scales to a file, or
+ * load them (replacing both, repacking every low-precision copy).  Format:
+ * "NRVNET01", int32 c_in, int32 flags (bit 0: scales present), int64 parameter
+ * count, the FP32 parameters, 21 FP32 scales; little-endian.  Both synchronise
+ * the stream.  No counterpart in the paper.  Errors: NRV_ERR_ARG (I/O, a file
+ * for another input width, a malformed file), NRV_ERR_STATE (save without
+ * parameters). */
+nrv_status nrv_net_save(const nrv_net* net, const char* path, nrv_stream stream);
+nrv_status nrv_net_load(nrv_net* net, const char* path, nrv_stream stream);
+
 /* FP8 (E4M3) network: every tensor the network stores holds E4M3 codes q with
  * value q * scale, one scale per tensor; weights hold E4M3 codes per output
  * column with scale max|column| / 448 (App. B quantises to fp16; this goes to

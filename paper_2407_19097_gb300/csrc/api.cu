@@ -311,6 +311,36 @@ extern "C" nrv_status nrv_net_set_params(nrv_net* net, const float* d_params, nr
     return NRV_OK;
 }
 
+extern "C" nrv_status nrv_net_init_params(nrv_net* net, uint64_t seed, float* d_params,
+                                          nrv_stream stream) {
+    clear_error();
+    if (!net || !d_params) return fail(NRV_ERR_ARG, "null argument");
+    NRV_TRY(net_init_params(net, seed, d_params, (cudaStream_t)stream));
+    return nrv_net_set_params(net, d_params, stream);
+}
+
+extern "C" nrv_status nrv_net_get_params(const nrv_net* net, float* d_out, nrv_stream stream) {
+    clear_error();
+    if (!net || !d_out) return fail(NRV_ERR_ARG, "null argument");
+    if (!net->has_params) return fail(NRV_ERR_STATE, "no parameters loaded");
+    NRV_CHECK_CUDA(cudaMemcpyAsync(d_out, net->params.p, net->n_params * sizeof(float),
+                                   cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return NRV_OK;
+}
+
+extern "C" nrv_status nrv_net_save(const nrv_net* net, const char* path, nrv_stream stream) {
+    clear_error();
+    if (!net || !path) return fail(NRV_ERR_ARG, "null argument");
+    return net_save(net, path, (cudaStream_t)stream);
+}
+
+extern "C" nrv_status nrv_net_load(nrv_net* net, const char* path, nrv_stream stream) {
+    clear_error();
+    if (!net || !path) return fail(NRV_ERR_ARG, "null argument");
+    net->drop_graphs();   // captured frames hold the old packed weights' addresses
+    return net_load(net, path, (cudaStream_t)stream);
+}
+
 extern "C" nrv_status nrv_net_set_act_scales(nrv_net* net, const float* s, int n,
                                              nrv_stream stream) {
     clear_error();

@@ -67,6 +67,10 @@ nrv_status net_forward(Net* net, const void* netin, int n, int H, int W, nrv_pre
                        cudaStream_t s);
 nrv_status net_backward(Net* net, const float* drgb, float* dparams, cudaStream_t s);
 nrv_status net_repack(Net* net, cudaStream_t s);
+// parameters in and out (netio.cu): Xavier-uniform draw into d_params, file save / load
+nrv_status net_init_params(const Net* net, uint64_t seed, float* d_params, cudaStream_t s);
+nrv_status net_save(const Net* net, const char* path, cudaStream_t s);
+nrv_status net_load(Net* net, const char* path, cudaStream_t s);
 
 // tensor-core convolution (tc.cu); returns NRV_ERR_UNSUPPORTED when a shape is not covered
 nrv_status tc_conv3(const Net* net, int layer, const void* x1, int c1, const void* x2, int c2,

@@ -72,6 +72,10 @@ SIGNATURES = {
     "nrv_create_net": (I, [I, ctypes.POINTER(P)]),
     "nrv_destroy_net": (I, [P]),
     "nrv_net_set_params": (I, [P, P, P]),
+    "nrv_net_init_params": (I, [P, ctypes.c_uint64, P, P]),
+    "nrv_net_get_params": (I, [P, P, P]),
+    "nrv_net_save": (I, [P, ctypes.c_char_p, P]),
+    "nrv_net_load": (I, [P, ctypes.c_char_p, P]),
     "nrv_net_set_act_scales": (I, [P, ctypes.POINTER(F), I, P]),
     "nrv_net_get_act_scales": (I, [P, ctypes.POINTER(F), I]),
     "nrv_net_calibrate": (I, [P, P, I, I, I, P]),
@@ -210,6 +214,19 @@ class Net:
 
     def set_params(self, params, stream=None):
         check(lib().nrv_net_set_params(self.h, _ptr(params), _stream(stream)))
+
+    def init_params(self, seed, params, stream=None):
+        """Seeded Xavier-uniform draw into `params` (device float32, param_count), then loaded."""
+        check(lib().nrv_net_init_params(self.h, int(seed), _ptr(params), _stream(stream)))
+
+    def get_params(self, out, stream=None):
+        check(lib().nrv_net_get_params(self.h, _ptr(out), _stream(stream)))
+
+    def save(self, path, stream=None):
+        check(lib().nrv_net_save(self.h, str(path).encode(), _stream(stream)))
+
+    def load(self, path, stream=None):
+        check(lib().nrv_net_load(self.h, str(path).encode(), _stream(stream)))
 
     def set_act_scales(self, scales):
         arr = (F * len(scales))(*[float(s) for s in scales])

@@ -72,4 +72,7 @@ def test_argument_errors(lib):
     assert lib.nrv_create_net(5, ctypes.byref(h)) == nrv.NRV_OK
     assert lib.nrv_shade(h, 32, 1, 8, 8, 0, 32, None) == nrv.NRV_ERR_STATE   # no params yet
     assert lib.nrv_net_backward(h, 32, 32, None) == nrv.NRV_ERR_STATE
+    assert lib.nrv_net_save(h, b"/nonexistent/net.bin", None) == nrv.NRV_ERR_STATE
+    assert lib.nrv_net_get_params(h, 32, None) == nrv.NRV_ERR_STATE
+    assert lib.nrv_net_load(h, b"/nonexistent/net.bin", None) == nrv.NRV_ERR_ARG
     assert lib.nrv_destroy_net(h) == nrv.NRV_OK
