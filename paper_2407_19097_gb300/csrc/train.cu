@@ -10,64 +10,108 @@
 namespace nrv {
 
 // ------------------------------------------------------------------ weight gradients, 3x3 conv
-// part[chunk][o][tap*cin + c] = sum_{q in chunk} g[q][o] * x[q + tap][c];  partb[chunk][o] = sum g
+// part[blk][o][tap*cin + c] = sum over the pixels of block blk's tiles of g[q][o] * x[q + tap][c];
+// partb[blk][o] = sum of g.  A tile is two image rows x 128 pixels; the block stages the
+// tile's gradients (16 output channels) and its input rows with a one-pixel halo (CG input
+// channels) in shared memory as FP32, then each thread accumulates a 4 (output) x 4 (input)
+// block of one tap -- 16 FMAs per pair of 16-byte shared loads.  Grid: (blocks over tiles,
+// output groups of 16, input groups of CG); 144 threads = 9 taps x 4 x 4 blocks (CG = 16) or
+// 72 (CG = 8).  Each block takes a contiguous run of tiles, so partials are summed in a
+// fixed order: the result is deterministic.
+constexpr int WG_TW = 128;            // tile width (pixels)
+constexpr int WG_THREADS = 144;
+
 template <typename T>
-__global__ void __launch_bounds__(256) wgrad3_kernel(TView<const T> g, int cout, TView<const T> x1,
-                                                     int c1, TView<const T> x2, int c2, int n,
-                                                     int h, int w, size_t chunk_px, float* part,
-                                                     float* partb) {
-    __shared__ float gs[32][16];
-    const int cin = c1 + c2, K = 9 * cin;
-    const int og = blockIdx.y * 16;
-    const size_t npx = (size_t)n * h * w;
-    const size_t q0 = blockIdx.x * chunk_px;
-    const size_t q1 = q0 + chunk_px < npx ? q0 + chunk_px : npx;
-    float acc[5][16];
+__global__ void __launch_bounds__(WG_THREADS) wgrad3_kernel(TView<const T> g, int cout,
+                                                            TView<const T> x1, int c1,
+                                                            TView<const T> x2, int c2, int n,
+                                                            int h, int w, int tiles_per_block,
+                                                            float* part, float* partb) {
+    constexpr int CGMAX = 16;
+    __shared__ __align__(16) float gs[2 * WG_TW][16];
+    __shared__ __align__(16) float xs[4][WG_TW + 2][CGMAX];
+    const int cin = c1 + c2;
+    const int CG = cin < 16 ? cin : 16;   // 8 (the packed first-layer input) or 16
+    const int og = blockIdx.y * 16, cg = blockIdx.z * CG;
+    const int t = threadIdx.x;
+    const int ncb = CG / 4;               // 4-channel blocks of the input group
+    const bool active = t < 9 * 4 * ncb;
+    const int tap = t / (4 * ncb), ob = (t / ncb) % 4, cb = t % ncb;
+    const int dy = tap / 3, dx = tap % 3;
+    // which source holds this input group
+    const TView<const T> xv = cg < c1 ? x1 : x2;
+    const int cx = cg < c1 ? cg : cg - c1;
+    const int tiles_x = (w + WG_TW - 1) / WG_TW, pairs = (h + 1) / 2;
+    const long long ntiles = (long long)n * pairs * tiles_x;
+    float acc[4][4];
 #pragma unroll
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[i][j] = 0.0f;
-    float bsum = 0.0f;
-    for (size_t qb = q0; qb < q1; qb += 32) {
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+    float bsum[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const long long t0 = (long long)blockIdx.x * tiles_per_block;
+    const long long t1 = t0 + tiles_per_block < ntiles ? t0 + tiles_per_block : ntiles;
+    for (long long tile = t0; tile < t1; ++tile) {
+        const int xt = (int)(tile % tiles_x);
+        const long long rest = tile / tiles_x;
+        const int pr = (int)(rest % pairs);
+        const int img = (int)(rest / pairs);
+        const int x0 = xt * WG_TW, y0 = 2 * pr;
         __syncthreads();
-        for (int i = threadIdx.x; i < 512; i += 256) {
-            const size_t q = qb + (i >> 4);
-            gs[i >> 4][i & 15] =
-                q < q1 ? ld1<T>(g.at(q / w, (int)(q % w), og + (i & 15), w)) : 0.0f;
+        // gradients of the tile's 2 x 128 pixels, 16 output channels (zero outside the image)
+        for (int i = t; i < 2 * WG_TW * 2; i += WG_THREADS) {
+            const int half = i & 1, px = (i >> 1) % WG_TW, py = (i >> 1) / WG_TW;
+            const int y = y0 + py, x = x0 + px;
+            float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (y < h && x < w) ld8<T>(g.at((size_t)img * h + y, x, og + 8 * half, w), v);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) gs[py * WG_TW + px][8 * half + k] = v[k];
+        }
+        // input rows y0-1 .. y0+2, pixels x0-1 .. x0+128, CG channels (zero padding)
+        const int nxh = CG / 8;
+        for (int i = t; i < 4 * (WG_TW + 2) * nxh; i += WG_THREADS) {
+            const int part8 = i % nxh, px = (i / nxh) % (WG_TW + 2), ry = (i / nxh) / (WG_TW + 2);
+            const int y = y0 - 1 + ry, x = x0 - 1 + px;
+            float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (y >= 0 && y < h && x >= 0 && x < w)
+                ld8<T>(xv.at((size_t)img * h + y, x, cx + 8 * part8, w), v);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) xs[ry][px][8 * part8 + k] = v[k];
         }
         __syncthreads();
-        const int nb = (int)(q1 - qb < 32 ? q1 - qb : 32);
-        if (threadIdx.x < 16)
-            for (int r = 0; r < nb; ++r) bsum += gs[r][threadIdx.x];
-        for (int r = 0; r < nb; ++r) {
-            const size_t q = qb + r;
-            const int x = (int)(q % w), y = (int)((q / w) % h);
-            const size_t img = q / ((size_t)w * h);
+        if (active) {
+            for (int py = 0; py < 2; ++py) {
+                const float* grow = &gs[py * WG_TW][4 * ob];
+                const float* xrow = &xs[py + dy][dx][4 * cb];
+#pragma unroll 4
+                for (int px = 0; px < WG_TW; ++px) {
+                    const float4 gv = *reinterpret_cast<const float4*>(grow + px * 16);
+                    const float4 xv4 = *reinterpret_cast<const float4*>(xrow + px * CGMAX);
+                    const float ga[4] = {gv.x, gv.y, gv.z, gv.w};
+                    const float xa[4] = {xv4.x, xv4.y, xv4.z, xv4.w};
 #pragma unroll
-            for (int i = 0; i < 5; ++i) {
-                const int k = threadIdx.x + 256 * i;
-                if (k >= K) break;
-                const int tap = k / cin, c = k % cin;
-                const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-                float v = 0.0f;
-                if (yy >= 0 && yy < h && xx >= 0 && xx < w) {
-                    const size_t rr = img * h + yy;
-                    v = c < c1 ? ld1<T>(x1.at(rr, xx, c, w)) : ld1<T>(x2.at(rr, xx, c - c1, w));
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ga[i], xa[j], acc[i][j]);
+                    if (tap == 0 && cb == 0) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) bsum[i] += ga[i];
+                    }
                 }
-#pragma unroll
-                for (int j = 0; j < 16; ++j) acc[i][j] = fmaf(v, gs[r][j], acc[i][j]);
             }
         }
     }
+    if (!active) return;
+    const int K = 9 * cin;
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        const int k = threadIdx.x + 256 * i;
-        if (k >= K) break;
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-            part[((size_t)blockIdx.x * cout + og + j) * K + k] = acc[i][j];
-    }
-    if (threadIdx.x < 16) partb[(size_t)blockIdx.x * cout + og + threadIdx.x] = bsum;
+        for (int j = 0; j < 4; ++j)
+            part[((size_t)blockIdx.x * cout + og + 4 * ob + i) * K + tap * cin + cg + 4 * cb + j] =
+                acc[i][j];
+    if (blockIdx.z == 0 && tap == 0 && cb == 0)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) partb[(size_t)blockIdx.x * cout + og + 4 * ob + i] = bsum[i];
 }
 
 // dW[o][c][tap] (PyTorch layout, c < cin_real) and db[o] from the chunk partials.
@@ -335,24 +379,28 @@ struct Bwd {
     nrv_status wgrad_conv(int l, TView<const T> gpre, TView<const T> x1, int c1, TView<const T> x2,
                           int c2, int level) {
         const Layer& L = net->layers[l];
-        const size_t npx = g.px(level);
-        const int groups = L.cout / 16;
-        size_t nch = (608 + groups - 1) / groups;
-        const size_t maxch = (npx + 255) / 256;
-        if (nch > maxch) nch = maxch;
-        if (nch < 1) nch = 1;
-        const size_t chunk = (npx + nch - 1) / nch;
-        nch = (npx + chunk - 1) / chunk;
         const int cin = c1 + c2;
-        const size_t need = (nch * L.cout * 9 * cin + nch * L.cout) * sizeof(float);
+        const int CG = cin < 16 ? cin : 16;
+        if (cin % CG || (c2 && c1 % CG) || L.cout % 16)
+            return fail(NRV_ERR_UNSUPPORTED, "weight gradient: channel groups");
+        const int h = g.h[level], w = g.w[level];
+        const long long ntiles = (long long)g.n * ((h + 1) / 2) * ((w + WG_TW - 1) / WG_TW);
+        const int groups = (L.cout / 16) * (cin / CG);
+        // about 4 blocks per SM in all, each a contiguous run of tiles
+        long long nblk = (152LL * 4 + groups - 1) / groups;
+        if (nblk > ntiles) nblk = ntiles;
+        if (nblk < 1) nblk = 1;
+        const int tpb = (int)((ntiles + nblk - 1) / nblk);
+        nblk = (ntiles + tpb - 1) / tpb;
+        const size_t need = ((size_t)nblk * L.cout * 9 * cin + (size_t)nblk * L.cout) * sizeof(float);
         NRV_TRY(net->partial.ensure(need));
         float* part = (float*)net->partial.p;
-        float* partb = part + nch * L.cout * 9 * cin;
-        wgrad3_kernel<T><<<dim3((unsigned)nch, groups), 256, 0, s>>>(
-            gpre, L.cout, x1, c1, x2, c2, g.n, g.h[level], g.w[level], chunk, part, partb);
+        float* partb = part + (size_t)nblk * L.cout * 9 * cin;
+        wgrad3_kernel<T><<<dim3((unsigned)nblk, L.cout / 16, cin / CG), WG_THREADS, 0, s>>>(
+            gpre, L.cout, x1, c1, x2, c2, g.n, h, w, tpb, part, partb);
         NRV_CHECK_LAUNCH();
         wgrad3_reduce_kernel<<<blocks_for((size_t)L.cout * 9 * cin), 256, 0, s>>>(
-            part, partb, (int)nch, L.cout, cin, L.cin, dparams + L.woff, dparams + L.boff);
+            part, partb, (int)nblk, L.cout, cin, L.cin, dparams + L.woff, dparams + L.boff);
         NRV_CHECK_LAUNCH();
         return NRV_OK;
     }
