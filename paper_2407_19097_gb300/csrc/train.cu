@@ -11,25 +11,31 @@ namespace nrv {
 
 // ------------------------------------------------------------------ weight gradients, 3x3 conv
 // part[blk][o][tap*cin + c] = sum over the pixels of block blk's tiles of g[q][o] * x[q + tap][c];
-// partb[blk][o] = sum of g.  A tile is two image rows x 128 pixels; the block stages the
-// tile's gradients (16 output channels) and its input rows with a one-pixel halo (CG input
+// partb[blk][o] = sum of g.  A tile is 256 pixels: R rows x TW pixels, TW = 128, 64 or 32
+// (the widest that the image width fills), R = 256 / TW.  The block stages the tile's
+// gradients (16 output channels) and its input rows with a one-pixel halo (CG input
 // channels) in shared memory as FP32, then each thread accumulates a 4 (output) x 4 (input)
 // block of one tap -- 16 FMAs per pair of 16-byte shared loads.  Grid: (blocks over tiles,
 // output groups of 16, input groups of CG); 144 threads = 9 taps x 4 x 4 blocks (CG = 16) or
 // 72 (CG = 8).  Each block takes a contiguous run of tiles, so partials are summed in a
 // fixed order: the result is deterministic.
-constexpr int WG_TW = 128;            // tile width (pixels)
+constexpr int WG_TILE = 256;          // pixels per tile
 constexpr int WG_THREADS = 144;
+constexpr int WG_XS = 520;            // staged input pixels: max over TW of (R + 2) x (TW + 2)
+
+inline int wgrad_tile_width(int w) { return w >= 128 ? 128 : (w >= 64 ? 64 : 32); }
 
 template <typename T>
 __global__ void __launch_bounds__(WG_THREADS) wgrad3_kernel(TView<const T> g, int cout,
                                                             TView<const T> x1, int c1,
                                                             TView<const T> x2, int c2, int n,
-                                                            int h, int w, int tiles_per_block,
-                                                            float* part, float* partb) {
+                                                            int h, int w, int TW,
+                                                            int tiles_per_block, float* part,
+                                                            float* partb) {
     constexpr int CGMAX = 16;
-    __shared__ __align__(16) float gs[2 * WG_TW][16];
-    __shared__ __align__(16) float xs[4][WG_TW + 2][CGMAX];
+    __shared__ __align__(16) float gs[WG_TILE][16];
+    __shared__ __align__(16) float xs[WG_XS][CGMAX];
+    const int R = WG_TILE / TW;
     const int cin = c1 + c2;
     const int CG = cin < 16 ? cin : 16;   // 8 (the packed first-layer input) or 16
     const int og = blockIdx.y * 16, cg = blockIdx.z * CG;
@@ -41,7 +47,7 @@ __global__ void __launch_bounds__(WG_THREADS) wgrad3_kernel(TView<const T> g, in
     // which source holds this input group
     const TView<const T> xv = cg < c1 ? x1 : x2;
     const int cx = cg < c1 ? cg : cg - c1;
-    const int tiles_x = (w + WG_TW - 1) / WG_TW, pairs = (h + 1) / 2;
+    const int tiles_x = (w + TW - 1) / TW, pairs = (h + R - 1) / R;
     const long long ntiles = (long long)n * pairs * tiles_x;
     float acc[4][4];
 #pragma unroll
@@ -56,35 +62,35 @@ __global__ void __launch_bounds__(WG_THREADS) wgrad3_kernel(TView<const T> g, in
         const long long rest = tile / tiles_x;
         const int pr = (int)(rest % pairs);
         const int img = (int)(rest / pairs);
-        const int x0 = xt * WG_TW, y0 = 2 * pr;
+        const int x0 = xt * TW, y0 = R * pr;
         __syncthreads();
-        // gradients of the tile's 2 x 128 pixels, 16 output channels (zero outside the image)
-        for (int i = t; i < 2 * WG_TW * 2; i += WG_THREADS) {
-            const int half = i & 1, px = (i >> 1) % WG_TW, py = (i >> 1) / WG_TW;
+        // gradients of the tile's R x TW pixels, 16 output channels (zero outside the image)
+        for (int i = t; i < WG_TILE * 2; i += WG_THREADS) {
+            const int half = i & 1, px = (i >> 1) % TW, py = (i >> 1) / TW;
             const int y = y0 + py, x = x0 + px;
             float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             if (y < h && x < w) ld8<T>(g.at((size_t)img * h + y, x, og + 8 * half, w), v);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) gs[py * WG_TW + px][8 * half + k] = v[k];
+            for (int k = 0; k < 8; ++k) gs[py * TW + px][8 * half + k] = v[k];
         }
-        // input rows y0-1 .. y0+2, pixels x0-1 .. x0+128, CG channels (zero padding)
+        // input rows y0-1 .. y0+R, pixels x0-1 .. x0+TW, CG channels (zero padding)
         const int nxh = CG / 8;
-        for (int i = t; i < 4 * (WG_TW + 2) * nxh; i += WG_THREADS) {
-            const int part8 = i % nxh, px = (i / nxh) % (WG_TW + 2), ry = (i / nxh) / (WG_TW + 2);
+        for (int i = t; i < (R + 2) * (TW + 2) * nxh; i += WG_THREADS) {
+            const int part8 = i % nxh, px = (i / nxh) % (TW + 2), ry = (i / nxh) / (TW + 2);
             const int y = y0 - 1 + ry, x = x0 - 1 + px;
             float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             if (y >= 0 && y < h && x >= 0 && x < w)
                 ld8<T>(xv.at((size_t)img * h + y, x, cx + 8 * part8, w), v);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) xs[ry][px][8 * part8 + k] = v[k];
+            for (int k = 0; k < 8; ++k) xs[ry * (TW + 2) + px][8 * part8 + k] = v[k];
         }
         __syncthreads();
         if (active) {
-            for (int py = 0; py < 2; ++py) {
-                const float* grow = &gs[py * WG_TW][4 * ob];
-                const float* xrow = &xs[py + dy][dx][4 * cb];
+            for (int py = 0; py < R; ++py) {
+                const float* grow = &gs[py * TW][4 * ob];
+                const float* xrow = &xs[(py + dy) * (TW + 2) + dx][4 * cb];
 #pragma unroll 4
-                for (int px = 0; px < WG_TW; ++px) {
+                for (int px = 0; px < TW; ++px) {
                     const float4 gv = *reinterpret_cast<const float4*>(grow + px * 16);
                     const float4 xv4 = *reinterpret_cast<const float4*>(xrow + px * CGMAX);
                     const float ga[4] = {gv.x, gv.y, gv.z, gv.w};
@@ -114,26 +120,48 @@ __global__ void __launch_bounds__(WG_THREADS) wgrad3_kernel(TView<const T> g, in
         for (int i = 0; i < 4; ++i) partb[(size_t)blockIdx.x * cout + og + 4 * ob + i] = bsum[i];
 }
 
-// dW[o][c][tap] (PyTorch layout, c < cin_real) and db[o] from the chunk partials.
-__global__ void wgrad3_reduce_kernel(const float* part, const float* partb, int nchunks, int cout,
-                                     int cin, int cin_real, float* dw, float* db) {
-    const int K = 9 * cin;
-    const size_t total = (size_t)cout * K;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int o = (int)(i / K), k = (int)(i % K);
-        const int tap = k / cin, c = k % cin;
-        if (c >= cin_real) continue;
-        float s = 0.0f;
-        for (int ch = 0; ch < nchunks; ++ch) s += part[((size_t)ch * cout + o) * K + k];
-        dw[((size_t)o * cin_real + c) * 9 + tap] = s;
-    }
-    if (blockIdx.x == 0)
-        for (int o = threadIdx.x; o < cout; o += blockDim.x) {
-            float s = 0.0f;
-            for (int ch = 0; ch < nchunks; ++ch) s += partb[(size_t)ch * cout + o];
-            db[o] = s;
+// Sums of per-chunk partials: sum i = part[0*stride + i] + part[1*stride + i] + ..., eight
+// threads per sum each taking every eighth chunk, their results added in a fixed order (the
+// result does not depend on timing).  `mode` says where sum i goes (PyTorch layouts):
+//  0  3x3 conv weight: i = o*9*cin + tap*cin + c -> dw[(o*cin_real + c)*9 + tap] (c < cin_real)
+//  1  transposed conv weight: i = c*4*cout + ab*cout + o -> dw[(c*cout + o)*4 + ab]
+//  2  copy: dw[i]
+//  3  transposed conv bias: i = o, each chunk contributing part[ab*cout + o] for ab = 0..3
+__global__ void reduce_partials_kernel(const float* __restrict__ part, int nchunks, size_t stride,
+                                       int count, int mode, int cout, int cin, int cin_real,
+                                       float* __restrict__ dw) {
+    __shared__ float red[8][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = blockIdx.x * 32 + tx;
+    float s = 0.0f;
+    if (i < count)
+        for (int ch = ty; ch < nchunks; ch += 8) {
+            const float* pc = part + (size_t)ch * stride;
+            if (mode == 3) s += ((pc[i] + pc[cout + i]) + pc[2 * cout + i]) + pc[3 * cout + i];
+            else s += pc[i];
         }
+    red[ty][tx] = s;
+    __syncthreads();
+    if (ty != 0 || i >= count) return;
+    float t = red[0][tx];
+    for (int k = 1; k < 8; ++k) t += red[k][tx];
+    if (mode == 0) {
+        const int K = 9 * cin, o = i / K, k = i % K, tap = k / cin, c = k % cin;
+        if (c < cin_real) dw[((size_t)o * cin_real + c) * 9 + tap] = t;
+    } else if (mode == 1) {
+        const int K = 4 * cout, c = i / K, k = i % K, ab = k / cout, o = k % cout;
+        dw[((size_t)c * cout + o) * 4 + ab] = t;
+    } else {
+        dw[i] = t;
+    }
+}
+
+static nrv_status reduce_partials(const float* part, int nchunks, size_t stride, int count, int mode,
+                                  int cout, int cin, int cin_real, float* dw, cudaStream_t s) {
+    reduce_partials_kernel<<<(count + 31) / 32, dim3(32, 8), 0, s>>>(part, nchunks, stride, count,
+                                                                     mode, cout, cin, cin_real, dw);
+    NRV_CHECK_LAUNCH();
+    return NRV_OK;
 }
 
 // ------------------------------------------------------------------ weight gradients, 2x2 transposed conv
@@ -183,27 +211,6 @@ __global__ void __launch_bounds__(256) wgrad_up_kernel(TView<const T> x, int cin
     }
 }
 
-__global__ void wgrad_up_reduce_kernel(const float* part, const float* partb, int nchunks, int cin,
-                                       int cout, float* dw, float* db) {
-    const int K = 4 * cout;
-    const size_t total = (size_t)cin * K;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i / K), k = (int)(i % K);
-        const int ab = k / cout, o = k % cout;
-        float s = 0.0f;
-        for (int ch = 0; ch < nchunks; ++ch) s += part[((size_t)ch * cin + c) * K + k];
-        dw[((size_t)c * cout + o) * 4 + ab] = s;
-    }
-    if (blockIdx.x == 0)
-        for (int o = threadIdx.x; o < cout; o += blockDim.x) {
-            float s = 0.0f;
-            for (int ch = 0; ch < nchunks; ++ch)
-                for (int ab = 0; ab < 4; ++ab) s += partb[(size_t)ch * K + ab * cout + o];
-            db[o] = s;
-        }
-}
-
 // ------------------------------------------------------------------ head
 // gd[q][c] = (sum_o drgb[o] W[o][c]) * (x[q][c] > 0) over the canvas (zero outside the view)
 template <typename T>
@@ -234,31 +241,46 @@ __global__ void head_dgrad_kernel(const float* drgb, const float* w, TView<const
     }
 }
 
-// part[chunk][o*16 + c] = sum drgb[o] * x[c]; part[chunk][48 + o] = sum drgb[o]
+// part[blk][o*16 + c] = sum drgb[o] * x[c]; part[blk][48 + o] = sum drgb[o], over the block's
+// chunk of cropped pixels: every thread keeps all 51 sums, then the block adds them (warp
+// shuffles, then the 8 warps in order).
 template <typename T>
-__global__ void head_wgrad_kernel(const float* drgb, TView<const T> x, int n, int hn, int wn, int h,
-                                  int wd, size_t chunk, float* part) {
-    const int t = threadIdx.x;
-    if (t >= 51) return;
+__global__ void __launch_bounds__(256) head_wgrad_kernel(const float* drgb, TView<const T> x, int n,
+                                                         int hn, int wn, int h, int wd,
+                                                         size_t chunk, float* part) {
+    __shared__ float red[8][51];
+    float acc[51];
+#pragma unroll
+    for (int k = 0; k < 51; ++k) acc[k] = 0.0f;
     const size_t total = (size_t)n * h * wd;
     const size_t i0 = blockIdx.x * chunk, i1 = i0 + chunk < total ? i0 + chunk : total;
-    float s = 0.0f;
-    for (size_t i = i0; i < i1; ++i) {
+    for (size_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const int X = (int)(i % wd), Y = (int)((i / wd) % h);
         const size_t img = i / ((size_t)wd * h);
-        if (t < 48) s = fmaf(drgb[3 * i + t / 16], ld1<T>(x.at(img * hn + Y, X, t % 16, wn)), s);
-        else s += drgb[3 * i + t - 48];
+        float v[16];
+        ld8<T>(x.at(img * hn + Y, X, 0, wn), v);
+        ld8<T>(x.at(img * hn + Y, X, 8, wn), v + 8);
+        const float d[3] = {drgb[3 * i], drgb[3 * i + 1], drgb[3 * i + 2]};
+#pragma unroll
+        for (int o = 0; o < 3; ++o) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[o * 16 + c] = fmaf(d[o], v[c], acc[o * 16 + c]);
+            acc[48 + o] += d[o];
+        }
     }
-    part[blockIdx.x * 51 + t] = s;
-}
-
-__global__ void head_reduce_kernel(const float* part, int nchunks, float* dw, float* db) {
-    const int t = threadIdx.x;
-    if (t >= 51) return;
-    float s = 0.0f;
-    for (int c = 0; c < nchunks; ++c) s += part[c * 51 + t];
-    if (t < 48) dw[t] = s;
-    else db[t - 48] = s;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 51; ++k) {
+        float a = acc[k];
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+        if (lane == 0) red[wp][k] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < 51) {
+        float a = red[0][threadIdx.x];
+        for (int k = 1; k < (int)(blockDim.x / 32); ++k) a += red[k][threadIdx.x];
+        part[blockIdx.x * 51 + threadIdx.x] = a;
+    }
 }
 
 // ------------------------------------------------------------------ pooling backward
@@ -384,7 +406,8 @@ struct Bwd {
         if (cin % CG || (c2 && c1 % CG) || L.cout % 16)
             return fail(NRV_ERR_UNSUPPORTED, "weight gradient: channel groups");
         const int h = g.h[level], w = g.w[level];
-        const long long ntiles = (long long)g.n * ((h + 1) / 2) * ((w + WG_TW - 1) / WG_TW);
+        const int TW = wgrad_tile_width(w), R = WG_TILE / TW;
+        const long long ntiles = (long long)g.n * ((h + R - 1) / R) * ((w + TW - 1) / TW);
         const int groups = (L.cout / 16) * (cin / CG);
         // about 4 blocks per SM in all, each a contiguous run of tiles
         long long nblk = (152LL * 4 + groups - 1) / groups;
@@ -397,12 +420,12 @@ struct Bwd {
         float* part = (float*)net->partial.p;
         float* partb = part + (size_t)nblk * L.cout * 9 * cin;
         wgrad3_kernel<T><<<dim3((unsigned)nblk, L.cout / 16, cin / CG), WG_THREADS, 0, s>>>(
-            gpre, L.cout, x1, c1, x2, c2, g.n, h, w, tpb, part, partb);
+            gpre, L.cout, x1, c1, x2, c2, g.n, h, w, TW, tpb, part, partb);
         NRV_CHECK_LAUNCH();
-        wgrad3_reduce_kernel<<<blocks_for((size_t)L.cout * 9 * cin), 256, 0, s>>>(
-            part, partb, (int)nblk, L.cout, cin, L.cin, dparams + L.woff, dparams + L.boff);
-        NRV_CHECK_LAUNCH();
-        return NRV_OK;
+        NRV_TRY(reduce_partials(part, (int)nblk, (size_t)L.cout * 9 * cin, L.cout * 9 * cin, 0, L.cout,
+                                cin, L.cin, dparams + L.woff, s));
+        return reduce_partials(partb, (int)nblk, L.cout, L.cout, 2, L.cout, cin, L.cin,
+                               dparams + L.boff, s);
     }
 
     nrv_status dgrad_conv(int l, TView<const T> gpre, TView<T> out, TView<const T> mask,
@@ -452,9 +475,10 @@ struct Bwd {
         wgrad_up_kernel<T><<<dim3((unsigned)nch, groups), 256, 0, s>>>(
             CA(xin), L.cin, gout, L.cout, g.n, g.h[level_in], g.w[level_in], chunk, part, partb);
         NRV_CHECK_LAUNCH();
-        wgrad_up_reduce_kernel<<<blocks_for((size_t)L.cin * K), 256, 0, s>>>(
-            part, partb, (int)nch, L.cin, L.cout, dparams + L.woff, dparams + L.boff);
-        NRV_CHECK_LAUNCH();
+        NRV_TRY(reduce_partials(part, (int)nch, (size_t)L.cin * K, L.cin * K, 1, L.cout, L.cin, L.cin,
+                                dparams + L.woff, s));
+        NRV_TRY(reduce_partials(partb, (int)nch, K, L.cout, 3, L.cout, L.cin, L.cin,
+                                dparams + L.boff, s));
         dim3 grid((unsigned)((npx + 127) / 128), L.cin / 16);
         upconv2_dgrad_kernel<T><<<grid, 128, (size_t)4 * 16 * L.cout * 4, s>>>(
             gout, L.cout, (const float*)net->wf32.p + net->wf_off[l], L.cin, CA(xin), gx, g.n,
@@ -490,12 +514,13 @@ struct Bwd {
             if (chunk < 64) chunk = 64;
             nch = (tot + chunk - 1) / chunk;
             NRV_TRY(net->partial.ensure(nch * 51 * sizeof(float)));
-            head_wgrad_kernel<T><<<(unsigned)nch, 64, 0, s>>>(drgb, CA(A_D0B), g.n, g.h[0], g.w[0],
-                                                              H, Wd, chunk, (float*)net->partial.p);
+            head_wgrad_kernel<T><<<(unsigned)nch, 256, 0, s>>>(drgb, CA(A_D0B), g.n, g.h[0], g.w[0],
+                                                               H, Wd, chunk, (float*)net->partial.p);
             NRV_CHECK_LAUNCH();
-            head_reduce_kernel<<<1, 64, 0, s>>>((const float*)net->partial.p, (int)nch,
-                                                dparams + Lh.woff, dparams + Lh.boff);
-            NRV_CHECK_LAUNCH();
+            // weight (48) and bias (3) are consecutive in the parameter vector
+            if (Lh.boff != Lh.woff + 48) return fail(NRV_ERR_STATE, "head parameter layout");
+            NRV_TRY(reduce_partials((const float*)net->partial.p, (int)nch, 51, 51, 2, 3, 16, 16,
+                                    dparams + Lh.woff, s));
         }
         // level 0 decoder
         NRV_TRY(wgrad_conv(L_D0B, C(W1[0], 16), CA(A_D0A), 16, none, 0, 0));
