@@ -79,6 +79,11 @@ nrv_status tc_conv3(const Net* net, int layer, const void* x1, int c1, const voi
 nrv_status tc_upconv(const Net* net, int layer, const void* x, void* y, const Geo& g, int level_in,
                      nrv_prec prec, cudaStream_t s, float inv_out = 1.0f);
 nrv_status tc_repack_fp8(Net* net, cudaStream_t s);
+// data gradient of 3x3 conv layer l on the tensor cores (BF16, row-planar): out = conv3x3 of
+// the output gradient gin with the flipped, transposed kernel, zeroed where mask <= 0 (mask
+// may be null); NRV_ERR_UNSUPPORTED when the layer has no such path
+nrv_status tc_dgrad(const Net* net, int l, const void* gin, void* out, const void* mask, int n, int H,
+                    int W, cudaStream_t s);
 nrv_status forward_fp8(Net* net, const uint8_t* netin, float* rgb, cudaStream_t s);
 // FP8 scale indices (0 input, 1 + Act) of a layer's first input, second input (-1 if none)
 // and output (-1 for the head)

@@ -56,12 +56,16 @@ template <> __device__ __forceinline__ void st8<__nv_bfloat16>(__nv_bfloat16* p,
 //     w pixels x 16 bytes (ce = 16 / sizeof(T) channels per plane), so element
 //     (row, x, c) sits at ((row * (ld / ce) + c / ce) * w + x) * ce + c % ce.
 // Accesses of 8 channels start at a multiple of 8, inside one plane.
+// coff: the view starts at channel coff of the tensor (a channel range of a wider tensor,
+// e.g. the skip half of a concatenation's gradient).
 template <typename T>
 struct TView {
     T* p;
-    int ld;          // channels per pixel
+    int ld;          // channels per pixel of the underlying tensor
     int planar = 0;
+    int coff = 0;
     __device__ __forceinline__ T* at(size_t row, int x, int c, int w) const {
+        c += coff;
         if (!planar) return p + (row * (size_t)w + x) * ld + c;
         constexpr int ce = 16 / (int)sizeof(T);
         return p + ((row * (size_t)(ld / ce) + c / ce) * w + x) * ce + c % ce;

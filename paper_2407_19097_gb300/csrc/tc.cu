@@ -69,7 +69,8 @@ struct TcParams {
                              // into its own partial accumulator, the epilogue adds them
     int cout;                // output channels
     int out_nch;             // 16-byte planes per output row
-    int mode;                // 0: 3x3 conv + bias + ReLU; 1: 2x2 stride-2 transposed conv + bias
+    int mode;                // 0: 3x3 conv (+ bias, ReLU); 1: 2x2 stride-2 transposed conv + bias
+    int relu;                // mode 0: apply ReLU (forward); 0 for the data gradient
     int has_src2;
     uint32_t slot_bytes;     // bytes of one row slot (both sources, plus read slack)
     uint32_t src2_off;       // offset of source 2 planes inside a slot
@@ -79,7 +80,9 @@ struct TcParams {
     uint32_t idesc;
     uint32_t tmem_cols;
     const uint8_t* wpk;      // packed weights [slice][ks][half][n][16 bytes] (BF16 or E4M3)
-    const float* bias;
+    const float* bias;       // null: no bias (the data gradient)
+    const uint8_t* mask;     // null, or a row-planar BF16 tensor shaped like the output: outputs
+                             // where it is not positive are zeroed (ReLU of the layer below)
     void* y;                 // BF16 or E4M3 row-planar output
     unsigned* status;
     int fp8;                 // E4M3 operands (kind::f8f6f4) and an E4M3 output
@@ -283,7 +286,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     // per output column of this slice: its bias (column n maps to channel n mod cout)
     for (int i = threadIdx.x; i < P.n_slice; i += NTHREADS) {
-        bias_s[i] = P.bias[(slice * P.n_slice + i) % P.cout];
+        bias_s[i] = P.bias ? P.bias[(slice * P.n_slice + i) % P.cout] : 0.0f;
         colscale_s[i] = FP8 ? P.colscale[slice * P.n_slice + i] : 1.0f;
     }
     for (int i = threadIdx.x; i <= MAX_KS; i += NTHREADS) alo_s[i] = i < P.nks ? P.a_lo[i] : 0u;
@@ -468,7 +471,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     v[j] = fmaf(acc[j], colscale_s[c0 + j], bias_s[c0 + j]);
-                    if (P.mode == 0) v[j] = fmaxf(v[j], 0.0f);
+                    if (P.relu) v[j] = fmaxf(v[j], 0.0f);
                 }
                 if (valid) {
                     const int ng = slice * P.n_slice + c0;
@@ -499,6 +502,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         }
                         *reinterpret_cast<uint4*>(dst) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
                     } else {
+                        if (P.mask) {
+                            // the same two planes of the mask tensor
+                            const size_t off = (size_t)(dst - (uint8_t*)P.y);
+                            const uint4 m0 = *reinterpret_cast<const uint4*>(P.mask + off);
+                            const uint4 m1 =
+                                *reinterpret_cast<const uint4*>(P.mask + off + (size_t)wo * 16);
+                            const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const uint32_t bits = (mw[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+                                // BF16 bits of a positive number: sign clear, not +0, not NaN
+                                const bool pos = bits != 0u && bits < 0x7F81u;
+                                if (!pos) v[j] = 0.0f;
+                            }
+                        }
                         uint32_t packed[8];
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
@@ -598,6 +616,9 @@ struct TcLayerCfg {
 };
 
 TcLayerCfg g_cfg[2][NUM_LAYERS];   // [BF16, FP8]
+TcLayerCfg g_cfg_dg[NUM_LAYERS];   // BF16 data gradients of the 3x3 convs
+
+constexpr int KIND_DGRAD = 3;   // packing of the data-gradient weights (BF16)
 
 // out[slice][ks][half][n][ce], ce = 8 (BF16) or 16 (E4M3).  FP8 weights are
 // W * fold / s_w[n] in E4M3, fold = scale(skip) / scale(upsampled) for the second
@@ -620,7 +641,11 @@ __global__ void pack_tc_weights_kernel(const float* __restrict__ P, int64_t woff
         float v = 0.0f;
         if (h.x >= 0) {
             const int c = (h.y == 0 ? 0 : c1) + ce * h.z + e;
-            if (c < cin_real) {
+            if (kind == KIND_DGRAD) {
+                // data gradient: column n = forward input channel, K = (tap, forward output
+                // channel c); the kernel flipped: W[c][n][8 - tap]
+                if (c < cout && n < cin_real) v = P[woff + ((size_t)c * cin_real + n) * 9 + (8 - h.x)];
+            } else if (c < cin_real) {
                 if (kind == CONV3) v = P[woff + ((size_t)n * cin_real + c) * 9 + h.x];
                 else v = P[woff + ((size_t)c * cout + n % cout) * 4 + n / cout];
                 if (h.y == 1) v *= fold;
@@ -657,7 +682,7 @@ __global__ void fp8_column_scales_kernel(const float* __restrict__ P, int64_t wo
     colscale[n] = s_in * sw;
 }
 
-DevBuf g_halves[2];
+DevBuf g_halves[3];   // K orders of the BF16, FP8 and data-gradient weights
 
 }  // namespace
 
@@ -727,6 +752,71 @@ static nrv_status build_cfg(Net* net, int pi, std::vector<int4>& all_halves,
     return NRV_OK;
 }
 
+// Data gradients of the 3x3 convs as 3x3 convs of the output gradient (C_out channels in)
+// with the kernel flipped and transposed (C_in channels out); BF16 only.  Not for the first
+// layer: the network input needs no gradient.
+static nrv_status build_cfg_dgrad(Net* net, std::vector<int4>& all_halves, std::vector<size_t>& hoff,
+                                  size_t& wbytes_total) {
+    const int ce = 8;
+    size_t off = 0;
+    for (int l = 0; l < NUM_LAYERS; ++l) {
+        TcLayerCfg& c = g_cfg_dg[l];
+        c = TcLayerCfg();
+        const Layer& L = net->layers[l];
+        if (L.kind != CONV3 || l == L_E0A || L.cout % ce || L.cin % 16) continue;
+        c.kind = CONV3;
+        c.c1 = L.cout;
+        c.c2 = 0;
+        c.rows = 3;
+        c.row0 = -1;
+        c.ncols = L.cin;
+        for (int dy = 0; dy < 3; ++dy) {
+            const size_t start = c.halves.size();
+            for (int dx = 0; dx < 3; ++dx)
+                for (int ch = 0; ch < L.cout / ce; ++ch) c.halves.push_back(Half{3 * dy + dx, 0, ch});
+            if ((c.halves.size() - start) % 2) c.halves.push_back(Half{-1, 0, 0});
+        }
+        c.nks = (int)c.halves.size() / 2;
+        if (c.nks > MAX_KS) continue;
+        int ns = c.ncols;
+        while (ns > 16 && (size_t)c.nks * 2 * ns * 16 > 80 * 1024) ns /= 2;
+        c.n_slice = ns;
+        c.nslices = c.ncols / ns;
+        c.w_bytes = (uint32_t)c.nks * 2 * ns * 16;
+        c.w_off = off;
+        off += ((size_t)c.w_bytes * c.nslices + 1023) / 1024 * 1024;
+        hoff[l] = all_halves.size();
+        for (const Half& h : c.halves) all_halves.push_back(make_int4(h.tap, h.src, h.chunk, 0));
+        c.ok = true;
+    }
+    wbytes_total = off;
+    return NRV_OK;
+}
+
+static nrv_status tc_repack_dgrad(Net* net, cudaStream_t s) {
+    std::vector<int4> all_halves;
+    std::vector<size_t> hoff(NUM_LAYERS, 0);
+    size_t off = 0;
+    NRV_TRY(build_cfg_dgrad(net, all_halves, hoff, off));
+    if (off == 0) return NRV_OK;
+    NRV_TRY(net->wtbf16.ensure(off));
+    NRV_TRY(g_halves[2].ensure(all_halves.size() * sizeof(int4)));
+    NRV_CHECK_CUDA(cudaMemcpyAsync(g_halves[2].p, all_halves.data(), all_halves.size() * sizeof(int4),
+                                   cudaMemcpyHostToDevice, s));
+    for (int l = 0; l < NUM_LAYERS; ++l) {
+        const TcLayerCfg& c = g_cfg_dg[l];
+        if (!c.ok) continue;
+        const Layer& L = net->layers[l];
+        pack_tc_weights_kernel<<<64, 256, 0, s>>>(
+            (const float*)net->params.p, L.woff, KIND_DGRAD, L.cin, L.cout, c.n_slice, c.nslices,
+            c.nks, (const int4*)g_halves[2].p + hoff[l], c.c1, 0, 1.0f, nullptr,
+            (uint8_t*)net->wtbf16.p + c.w_off);
+        NRV_CHECK_LAUNCH();
+    }
+    NRV_CHECK_CUDA(cudaStreamSynchronize(s));
+    return NRV_OK;
+}
+
 nrv_status tc_repack(Net* net, cudaStream_t s) {
     std::vector<int4> all_halves;
     std::vector<size_t> hoff(NUM_LAYERS, 0);
@@ -749,6 +839,7 @@ nrv_status tc_repack(Net* net, cudaStream_t s) {
     }
     // the host copy of the halves must stay valid until the copy ran
     NRV_CHECK_CUDA(cudaStreamSynchronize(s));
+    NRV_TRY(tc_repack_dgrad(net, s));
     if (net->fp8_ready) return tc_repack_fp8(net, s);
     return NRV_OK;
 }
@@ -816,13 +907,15 @@ static int g_num_sms = 0;
 // writes [n][H][W][C_out]; a transposed conv reads level (H, W) and writes
 // [n][2H][2W][C_out]; all tensors row-planar.  FP8: operands and output E4M3,
 // inv_out = 1 / output scale.
-static nrv_status tc_launch(const Net* net, int l, const void* x1, int c1, const void* x2, int c2,
-                            void* y, int n, int H, int W, cudaStream_t s, int fp8, float inv_out) {
-    const TcLayerCfg& c = g_cfg[fp8][l];
+// c: the layer configuration; wpk: its packed weights; bias (null: none); relu; mask (null:
+// none); cout: the output channels (C_out of the conv, or C_in of a data gradient).
+static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* wpk,
+                            const float* bias, int relu, const void* mask, int cout, const void* x1,
+                            int c1, const void* x2, int c2, void* y, int n, int H, int W,
+                            cudaStream_t s, int fp8, float inv_out) {
     if (!c.ok || c.c1 != c1 || c.c2 != c2) return fail(NRV_ERR_UNSUPPORTED, "layer not configured");
     if (fp8 && !net->fp8_ready) return fail(NRV_ERR_STATE, "FP8 needs activation scales");
     if (n <= 0 || H <= 0 || W <= 0) return fail(NRV_ERR_ARG, "empty tensor");
-    const Layer& L = net->layers[l];
     const int es = fp8 ? 1 : 2, ce = 16 / es;
     const bool conv = c.kind == CONV3;
     TcParams P;
@@ -841,9 +934,11 @@ static nrv_status tc_launch(const Net* net, int l, const void* x1, int c1, const
     P.nks = c.nks;
     P.rows = c.rows;
     P.row0 = c.row0;
-    P.cout = L.cout;
-    P.out_nch = L.cout / ce;
+    P.cout = cout;
+    P.out_nch = cout / ce;
     P.mode = conv ? 0 : 1;
+    P.relu = relu;
+    P.mask = (const uint8_t*)mask;
     P.has_src2 = c.c2 > 0;
     const uint32_t nch1 = c.c1 / ce, nch2 = c.c2 / ce;
     P.src2_off = (nch1 * PLANE + 127) / 128 * 128;   // TMA destinations are 128-byte aligned
@@ -908,8 +1003,8 @@ static nrv_status tc_launch(const Net* net, int l, const void* x1, int c1, const
     const uint32_t ab_fmt = fp8 ? 0u : 1u;
     P.idesc = (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(c.n_slice >> 3) << 17) |
               ((uint32_t)(TILE_M >> 4) << 24);
-    P.wpk = (const uint8_t*)(fp8 ? net->wfp8.p : net->wbf16.p) + c.w_off;
-    P.bias = (const float*)net->params.p + L.boff;
+    P.wpk = wpk;
+    P.bias = bias;
     P.y = y;
     P.fp8 = fp8;
     P.inv_out = inv_out;
@@ -966,18 +1061,36 @@ nrv_status tc_conv3(const Net* net, int l, const void* x1, int c1, const void* x
                     const Geo& g, int level, nrv_prec prec, cudaStream_t s, float inv_out) {
     if (prec != NRV_PREC_BF16 && prec != NRV_PREC_FP8)
         return fail(NRV_ERR_UNSUPPORTED, "tensor-core path is BF16 or FP8");
-    if (net->layers[l].kind != CONV3) return fail(NRV_ERR_UNSUPPORTED, "not a 3x3 conv");
-    return tc_launch(net, l, x1, c1, x2, c2, y, g.n, g.h[level], g.w[level], s,
-                     prec == NRV_PREC_FP8, inv_out);
+    const Layer& L = net->layers[l];
+    if (L.kind != CONV3) return fail(NRV_ERR_UNSUPPORTED, "not a 3x3 conv");
+    const int fp8 = prec == NRV_PREC_FP8;
+    const TcLayerCfg& c = g_cfg[fp8][l];
+    const uint8_t* w = (const uint8_t*)(fp8 ? net->wfp8.p : net->wbf16.p) + c.w_off;
+    return tc_launch(net, c, w, (const float*)net->params.p + L.boff, 1, nullptr, L.cout, x1, c1,
+                     x2, c2, y, g.n, g.h[level], g.w[level], s, fp8, inv_out);
+}
+
+nrv_status tc_dgrad(const Net* net, int l, const void* gin, void* out, const void* mask, int n, int H,
+                    int W, cudaStream_t s) {
+    const Layer& L = net->layers[l];
+    const TcLayerCfg& c = g_cfg_dg[l];
+    if (L.kind != CONV3 || !c.ok) return fail(NRV_ERR_UNSUPPORTED, "no tensor-core data gradient");
+    const uint8_t* w = (const uint8_t*)net->wtbf16.p + c.w_off;
+    return tc_launch(net, c, w, nullptr, 0, mask, L.cin, gin, L.cout, nullptr, 0, out, n, H, W, s, 0,
+                     1.0f);
 }
 
 nrv_status tc_upconv(const Net* net, int l, const void* x, void* y, const Geo& g, int level_in,
                      nrv_prec prec, cudaStream_t s, float inv_out) {
     if (prec != NRV_PREC_BF16 && prec != NRV_PREC_FP8)
         return fail(NRV_ERR_UNSUPPORTED, "tensor-core path is BF16 or FP8");
-    if (net->layers[l].kind != UPCONV2) return fail(NRV_ERR_UNSUPPORTED, "not a transposed conv");
-    return tc_launch(net, l, x, net->layers[l].cin, nullptr, 0, y, g.n, g.h[level_in],
-                     g.w[level_in], s, prec == NRV_PREC_FP8, inv_out);
+    const Layer& L = net->layers[l];
+    if (L.kind != UPCONV2) return fail(NRV_ERR_UNSUPPORTED, "not a transposed conv");
+    const int fp8 = prec == NRV_PREC_FP8;
+    const TcLayerCfg& c = g_cfg[fp8][l];
+    const uint8_t* w = (const uint8_t*)(fp8 ? net->wfp8.p : net->wbf16.p) + c.w_off;
+    return tc_launch(net, c, w, (const float*)net->params.p + L.boff, 0, nullptr, L.cout, x, L.cin,
+                     nullptr, 0, y, g.n, g.h[level_in], g.w[level_in], s, fp8, inv_out);
 }
 
 }  // namespace nrv

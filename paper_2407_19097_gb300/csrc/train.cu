@@ -430,6 +430,19 @@ struct Bwd {
 
     nrv_status dgrad_conv(int l, TView<const T> gpre, TView<T> out, TView<const T> mask,
                           int level) {
+        // BF16: on the tensor cores (a 3x3 conv with the flipped, transposed kernel)
+        if (sizeof(T) == 2) {
+            const Layer& L = net->layers[l];
+            const bool fits = gpre.planar && out.planar && !gpre.coff && !out.coff &&
+                              gpre.ld == L.cout && out.ld == L.cin &&
+                              (!mask.p || (mask.planar && !mask.coff && mask.ld == L.cin));
+            if (fits) {
+                const nrv_status st = tc_dgrad(net, l, gpre.p, out.p, mask.p, g.n, g.h[level],
+                                               g.w[level], s);
+                if (st != NRV_ERR_UNSUPPORTED) return st;
+                clear_error();
+            }
+        }
         // this translation unit has its own instance of the kernel template
         static bool attr = false;
         if (!attr) {
@@ -495,8 +508,13 @@ struct Bwd {
         return NRV_OK;
     }
 
-    static TView<T> V(T* p, int ld) { return TView<T>{p, ld}; }
-    static TView<const T> C(T* p, int ld) { return TView<const T>{p, ld}; }
+    // gradients: row-planar in BF16 (the tensor-core layout), NHWC in FP32; coff selects a
+    // channel range (the skip half of a concatenation's gradient)
+    static constexpr int kPlanar = sizeof(T) == 2 ? 1 : 0;
+    static TView<T> V(T* p, int ld) { return TView<T>{p, ld, kPlanar}; }
+    static TView<const T> C(T* p, int ld, int coff = 0) {
+        return TView<const T>{p, ld, kPlanar, coff};
+    }
 
     nrv_status run(const float* drgb, const T* netin) {
         const TView<const T> none{nullptr, 0};
@@ -546,19 +564,19 @@ struct Bwd {
         NRV_TRY(wgrad_conv(L_E3A, C(W2[3], 128), CA(A_P2), 64, none, 0, 3));
         NRV_TRY(dgrad_conv(L_E3A, C(W2[3], 128), V(W1[3], 64), none, 3));
         // level 2 encoder: skip gradient sits in channels 64..127 of W1[2]
-        NRV_TRY(pool_bwd(C(W1[3], 64), C(W1[2] + 64, 128), A_E2B, V(W2[2], 64), 2));
+        NRV_TRY(pool_bwd(C(W1[3], 64), C(W1[2], 128, 64), A_E2B, V(W2[2], 64), 2));
         NRV_TRY(wgrad_conv(L_E2B, C(W2[2], 64), CA(A_E2A), 64, none, 0, 2));
         NRV_TRY(dgrad_conv(L_E2B, C(W2[2], 64), V(W1[2], 64), CA(A_E2A), 2));
         NRV_TRY(wgrad_conv(L_E2A, C(W1[2], 64), CA(A_P1), 32, none, 0, 2));
         NRV_TRY(dgrad_conv(L_E2A, C(W1[2], 64), V(W2[2], 32), none, 2));
         // level 1 encoder: skip gradient in channels 32..63 of W1[1]
-        NRV_TRY(pool_bwd(C(W2[2], 32), C(W1[1] + 32, 64), A_E1B, V(W2[1], 32), 1));
+        NRV_TRY(pool_bwd(C(W2[2], 32), C(W1[1], 64, 32), A_E1B, V(W2[1], 32), 1));
         NRV_TRY(wgrad_conv(L_E1B, C(W2[1], 32), CA(A_E1A), 32, none, 0, 1));
         NRV_TRY(dgrad_conv(L_E1B, C(W2[1], 32), V(W1[1], 32), CA(A_E1A), 1));
         NRV_TRY(wgrad_conv(L_E1A, C(W1[1], 32), CA(A_P0), 16, none, 0, 1));
         NRV_TRY(dgrad_conv(L_E1A, C(W1[1], 32), V(W2[1], 16), none, 1));
         // level 0 encoder: skip gradient in channels 16..31 of W1[0]
-        NRV_TRY(pool_bwd(C(W2[1], 16), C(W1[0] + 16, 32), A_E0B, V(W2[0], 16), 0));
+        NRV_TRY(pool_bwd(C(W2[1], 16), C(W1[0], 32, 16), A_E0B, V(W2[0], 16), 0));
         NRV_TRY(wgrad_conv(L_E0B, C(W2[0], 16), CA(A_E0A), 16, none, 0, 0));
         NRV_TRY(dgrad_conv(L_E0B, C(W2[0], 16), V(W1[0], 16), CA(A_E0A), 0));
         NRV_TRY(wgrad_conv(L_E0A, C(W1[0], 16), C(const_cast<T*>(netin), net->c0p), net->c0p, none,
