@@ -390,7 +390,7 @@ extern "C" nrv_status nrv_shade(nrv_net* net, const void* netin, int n, int h, i
                                 nrv_prec prec, float* rgb, nrv_stream stream) {
     clear_error();
     NRV_TRY(check_shade(net, netin, n, h, w, prec, rgb));
-    return net_forward(net, netin, n, h, w, prec, rgb, (cudaStream_t)stream);
+    return net_forward(net, netin, n, h, w, prec, rgb, (cudaStream_t)stream, false);
 }
 
 extern "C" nrv_status nrv_net_run_layer(nrv_net* net, int layer, const void* x1, const void* x2,
@@ -600,7 +600,7 @@ extern "C" nrv_status nrv_render_batch(nrv_scene* s, nrv_net* net, const nrv_pac
         if (ev) prof_mark(*ev, q);
         for (int i = 0; i < n; ++i)
             NRV_TRY(net_forward(net, base + in_off[i], 1, views[i].height, views[i].width, prec,
-                                rgb[i], q));
+                                rgb[i], q, false));
         if (ev) prof_mark(*ev, q);
         return NRV_OK;
     };

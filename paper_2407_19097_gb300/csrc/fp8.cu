@@ -128,7 +128,7 @@ nrv_status net_calibrate(Net* net, const void* netin, int n, int H, int W, cudaS
     return NRV_OK;
 }
 
-nrv_status forward_fp8(Net* net, const uint8_t* netin, float* rgb, cudaStream_t s) {
+nrv_status forward_fp8(Net* net, const uint8_t* netin, float* rgb, cudaStream_t s, bool keep_acts) {
     if (!net->fp8_ready) return fail(NRV_ERR_STATE, "FP8 needs activation scales (calibrate first)");
     const Geo& g = net->geo;
     auto A = [&](int a) { return (uint8_t*)net->acts.p + net->act_off[a]; };
@@ -168,8 +168,19 @@ nrv_status forward_fp8(Net* net, const uint8_t* netin, float* rgb, cudaStream_t 
     NRV_TRY(conv(L_D1B, A(A_D1A), 32, nullptr, 0, A_D1B, 1));
     NRV_TRY(up(L_UP1, A_D1B, A_UP1, 1));
     NRV_TRY(conv(L_D0A, A(A_UP1), 16, A(A_E0B), 16, A_D0A, 0));
-    NRV_TRY(conv(L_D0B, A(A_D0A), 16, nullptr, 0, A_D0B, 0));
     const Layer& Lh = net->layers[L_HEAD];
+    {
+        // the head in the last conv's epilogue
+        const float* P = (const float*)net->params.p;
+        const TcHead head{P + Lh.woff, P + Lh.boff, rgb, net->geo_H, net->geo_W,
+                          net->act_scale[1 + A_D0B], keep_acts};
+        const nrv_status st = tc_conv3(net, L_D0B, A(A_D0A), 16, nullptr, 0, A(A_D0B), g, 0,
+                                       NRV_PREC_FP8, s, inv(A_D0B), &head);
+        net->backend[L_D0B] = 1;
+        if (st != NRV_ERR_UNSUPPORTED) return st;
+        clear_error();
+    }
+    NRV_TRY(conv(L_D0B, A(A_D0A), 16, nullptr, 0, A_D0B, 0));
     head_fp8_kernel<<<blocks_for((size_t)g.n * net->geo_H * net->geo_W), 256, 0, s>>>(
         A(A_D0B), net->act_scale[1 + A_D0B], (const float*)net->params.p + Lh.woff,
         (const float*)net->params.p + Lh.boff, rgb, g.n, g.h[0], g.w[0], net->geo_H, net->geo_W);

@@ -179,7 +179,7 @@ static nrv_status simt_upconv(const Net* net, int l, TView<const T> x, TView<T> 
 
 template <typename T>
 static nrv_status forward_t(Net* net, const T* netin, float* rgb, cudaStream_t s, bool use_tc,
-                            nrv_prec prec) {
+                            nrv_prec prec, bool keep_acts) {
     const Geo& g = net->geo;
     // BF16 activations are row-planar (the tensor-core layout), FP32 ones NHWC
     const int planar = sizeof(T) == 2 ? 1 : 0;
@@ -236,8 +236,18 @@ static nrv_status forward_t(Net* net, const T* netin, float* rgb, cudaStream_t s
     NRV_TRY(conv(L_D1B, CV(A_D1A), 32, none, 0, A_D1B, 1));
     NRV_TRY(upconv(L_UP1, A_D1B, A_UP1, 1));
     NRV_TRY(conv(L_D0A, CV(A_UP1), 16, CV(A_E0B), 16, A_D0A, 0));
-    NRV_TRY(conv(L_D0B, CV(A_D0A), 16, none, 0, A_D0B, 0));
     const Layer& Lh = net->layers[L_HEAD];
+    if (use_tc) {
+        // the head in the last conv's epilogue
+        const float* P = (const float*)net->params.p;
+        const TcHead head{P + Lh.woff, P + Lh.boff, rgb, net->geo_H, net->geo_W, 1.0f, keep_acts};
+        const nrv_status st = tc_conv3(net, L_D0B, act<T>(net, A_D0A), 16, nullptr, 0,
+                                       act<T>(net, A_D0B), g, 0, prec, s, 1.0f, &head);
+        net->backend[L_D0B] = 1;
+        if (st != NRV_ERR_UNSUPPORTED) return st;
+        clear_error();
+    }
+    NRV_TRY(conv(L_D0B, CV(A_D0A), 16, none, 0, A_D0B, 0));
     head_kernel<T><<<blocks_for((size_t)g.n * net->geo_H * net->geo_W), 256, 0, s>>>(
         CV(A_D0B), (const float*)net->params.p + Lh.woff, (const float*)net->params.p + Lh.boff,
         rgb, g.n, g.h[0], g.w[0], net->geo_H, net->geo_W);
@@ -258,16 +268,17 @@ static nrv_status set_kernel_attrs() {
 }
 
 nrv_status net_forward(Net* net, const void* netin, int n, int H, int W, nrv_prec prec, float* rgb,
-                       cudaStream_t s) {
+                       cudaStream_t s, bool keep_acts) {
     NRV_TRY(set_kernel_attrs());
     NRV_TRY(net_prepare(net, n, H, W, prec));
     net->saved = false;
     for (int l = 0; l < NUM_LAYERS; ++l) net->backend[l] = net->layers[l].kind == CONV3 ? -1 : 0;
     if (prec == NRV_PREC_F32)
-        return forward_t<float>(net, (const float*)netin, rgb, s, false, prec);
+        return forward_t<float>(net, (const float*)netin, rgb, s, false, prec, keep_acts);
     if (prec == NRV_PREC_BF16)
-        return forward_t<__nv_bfloat16>(net, (const __nv_bfloat16*)netin, rgb, s, true, prec);
-    return forward_fp8(net, (const uint8_t*)netin, rgb, s);
+        return forward_t<__nv_bfloat16>(net, (const __nv_bfloat16*)netin, rgb, s, true, prec,
+                                        keep_acts);
+    return forward_fp8(net, (const uint8_t*)netin, rgb, s, keep_acts);
 }
 
 }  // namespace nrv

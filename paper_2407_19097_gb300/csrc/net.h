@@ -63,8 +63,9 @@ struct Net {
 
 size_t elem_size(nrv_prec p);
 nrv_status net_prepare(Net* net, int n, int H, int W, nrv_prec prec);
+// keep_acts false: the last conv's output, which only a backward reads, need not be stored
 nrv_status net_forward(Net* net, const void* netin, int n, int H, int W, nrv_prec prec, float* rgb,
-                       cudaStream_t s);
+                       cudaStream_t s, bool keep_acts = true);
 nrv_status net_backward(Net* net, const float* drgb, float* dparams, cudaStream_t s);
 nrv_status net_repack(Net* net, cudaStream_t s);
 // parameters in and out (netio.cu): Xavier-uniform draw into d_params, file save / load
@@ -72,10 +73,22 @@ nrv_status net_init_params(const Net* net, uint64_t seed, float* d_params, cudaS
 nrv_status net_save(const Net* net, const char* path, cudaStream_t s);
 nrv_status net_load(Net* net, const char* path, cudaStream_t s);
 
+// The 1x1 head fused into the last conv's epilogue: weights w[3][16], bias b[3], output
+// rgb[n][h][w_px][3] FP32 cropped to h x w_px; scale: E4M3 scale of the stored conv output
+// (1 for BF16); store_y false skips storing the conv output itself.
+struct TcHead {
+    const float* w;
+    const float* b;
+    float* rgb;
+    int h, w_px;
+    float scale;
+    bool store_y;
+};
+
 // tensor-core convolution (tc.cu); returns NRV_ERR_UNSUPPORTED when a shape is not covered
 nrv_status tc_conv3(const Net* net, int layer, const void* x1, int c1, const void* x2, int c2,
                     void* y, const Geo& g, int level, nrv_prec prec, cudaStream_t s,
-                    float inv_out = 1.0f);
+                    float inv_out = 1.0f, const TcHead* head = nullptr);
 nrv_status tc_upconv(const Net* net, int layer, const void* x, void* y, const Geo& g, int level_in,
                      nrv_prec prec, cudaStream_t s, float inv_out = 1.0f);
 nrv_status tc_repack_fp8(Net* net, cudaStream_t s);
@@ -84,7 +97,7 @@ nrv_status tc_repack_fp8(Net* net, cudaStream_t s);
 // may be null); NRV_ERR_UNSUPPORTED when the layer has no such path
 nrv_status tc_dgrad(const Net* net, int l, const void* gin, void* out, const void* mask, int n, int H,
                     int W, cudaStream_t s);
-nrv_status forward_fp8(Net* net, const uint8_t* netin, float* rgb, cudaStream_t s);
+nrv_status forward_fp8(Net* net, const uint8_t* netin, float* rgb, cudaStream_t s, bool keep_acts);
 // FP8 scale indices (0 input, 1 + Act) of a layer's first input, second input (-1 if none)
 // and output (-1 for the head)
 void layer_scale_index(int l, int* in1, int* in2, int* out);

@@ -88,6 +88,15 @@ struct TcParams {
     int fp8;                 // E4M3 operands (kind::f8f6f4) and an E4M3 output
     float inv_out;           // FP8: 1 / scale of the output tensor
     const float* colscale;   // FP8: per GEMM column, input scale x weight scale
+    // optional 1x1 head on the stored outputs of a 16-channel conv (one slice):
+    // rgb[img][y][x][o] = head_b[o] + sum_c head_w[o][c] * stored_c (as read back,
+    // E4M3 codes times head_s), for y < rgb_h, x < rgb_w; store_y 0 skips the store
+    const float* head_w;
+    const float* head_b;
+    float* rgb;
+    int rgb_h, rgb_w;
+    float head_s;
+    int store_y;
     // per K-step of one input row (every row of a tile has the same pattern):
     // low word of the A descriptor relative to the row's slot,
     // (offset >> 4) | (LBO >> 4) << 16; K-step ks reads row ks / (nks / rows)
@@ -241,14 +250,30 @@ __device__ __forceinline__ void ring_next(int& slot, uint32_t& phase, int nslot)
     }
 }
 
+// rgb of one pixel from its 16 stored channels (the 1x1 head, bias first, then
+// one fused multiply-add per channel in channel order)
+__device__ __forceinline__ void head_store(const TcParams& P, const float* hw, int img, int y,
+                                           int x, const float* v) {
+    if (y >= P.rgb_h || x >= P.rgb_w) return;
+    float* out = P.rgb + (((size_t)img * P.rgb_h + y) * P.rgb_w + x) * 3;
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+        float acc = hw[48 + o];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc = fmaf(hw[o * 16 + c], v[c], acc);
+        out[o] = acc;
+    }
+}
+
 template <bool FP8>
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(NTHREADS, 4)
     conv3_tc_kernel(const __grid_constant__ CUtensorMap tm1, const __grid_constant__ CUtensorMap tm2,
                     const __grid_constant__ TcParams P) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t bars[2 * MAX_SLOTS + 6];
     __shared__ float bias_s[256];
     __shared__ float colscale_s[256];
+    __shared__ float head_ws[52];
     __shared__ uint32_t alo_s[MAX_KS + 1];
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
@@ -290,6 +315,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         colscale_s[i] = FP8 ? P.colscale[slice * P.n_slice + i] : 1.0f;
     }
     for (int i = threadIdx.x; i <= MAX_KS; i += NTHREADS) alo_s[i] = i < P.nks ? P.a_lo[i] : 0u;
+    if (P.head_w && threadIdx.x < 51)
+        head_ws[threadIdx.x] = threadIdx.x < 48 ? P.head_w[threadIdx.x] : P.head_b[threadIdx.x - 48];
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_slot)),
@@ -500,7 +527,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                 v[j] * P.inv_out, __NV_SATFINITE, __NV_E4M3);
                             wd[j >> 2] |= (uint32_t)c8 << (8 * (j & 3));
                         }
-                        *reinterpret_cast<uint4*>(dst) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+                        if (P.store_y)
+                            *reinterpret_cast<uint4*>(dst) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+                        if (P.head_w) {
+                            // the decoded codes, as a separate head kernel would read them
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                __nv_fp8_e4m3 q;
+                                q.__x = (uint8_t)(wd[j >> 2] >> (8 * (j & 3)));
+                                v[j] = float(q) * P.head_s;
+                            }
+                            head_store(P, head_ws, w.img, w.y, x, v);
+                        }
                     } else {
                         if (P.mask) {
                             // the same two planes of the mask tensor
@@ -524,10 +562,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             packed[j] = *reinterpret_cast<uint32_t*>(&h2);
                         }
                         // channels o..o+7 and o+8..o+15 sit in consecutive planes
-                        *reinterpret_cast<uint4*>(dst) =
-                            make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                        *reinterpret_cast<uint4*>(dst + (size_t)wo * 16) =
-                            make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                        if (P.store_y) {
+                            *reinterpret_cast<uint4*>(dst) =
+                                make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                            *reinterpret_cast<uint4*>(dst + (size_t)wo * 16) =
+                                make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                        }
+                        if (P.head_w) {
+                            // the rounded BF16 values, as a separate head kernel would read them
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const __nv_bfloat162 h2 =
+                                    *reinterpret_cast<const __nv_bfloat162*>(&packed[j]);
+                                v[2 * j] = __low2float(h2);
+                                v[2 * j + 1] = __high2float(h2);
+                            }
+                            head_store(P, head_ws, w.img, w.y, x, v);
+                        }
                     }
                 }
             }
@@ -912,7 +963,7 @@ static int g_num_sms = 0;
 static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* wpk,
                             const float* bias, int relu, const void* mask, int cout, const void* x1,
                             int c1, const void* x2, int c2, void* y, int n, int H, int W,
-                            cudaStream_t s, int fp8, float inv_out) {
+                            cudaStream_t s, int fp8, float inv_out, const TcHead* head = nullptr) {
     if (!c.ok || c.c1 != c1 || c.c2 != c2) return fail(NRV_ERR_UNSUPPORTED, "layer not configured");
     if (fp8 && !net->fp8_ready) return fail(NRV_ERR_STATE, "FP8 needs activation scales");
     if (n <= 0 || H <= 0 || W <= 0) return fail(NRV_ERR_ARG, "empty tensor");
@@ -1008,6 +1059,18 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
     P.y = y;
     P.fp8 = fp8;
     P.inv_out = inv_out;
+    P.store_y = 1;
+    if (head) {
+        if (!conv || c.nslices != 1 || c.n_slice != 16 || cout != 16 || !relu)
+            return fail(NRV_ERR_UNSUPPORTED, "the fused head needs a 16-channel conv");
+        P.head_w = head->w;
+        P.head_b = head->b;
+        P.rgb = head->rgb;
+        P.rgb_h = head->h;
+        P.rgb_w = head->w_px;
+        P.head_s = head->scale;
+        P.store_y = head->store_y ? 1 : 0;
+    }
     if (fp8) {
         size_t cs_total = net->wscale8.bytes / (2 * sizeof(float));
         P.colscale = (const float*)net->wscale8.p + cs_total + c.cs_off;
@@ -1058,7 +1121,8 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
 }
 
 nrv_status tc_conv3(const Net* net, int l, const void* x1, int c1, const void* x2, int c2, void* y,
-                    const Geo& g, int level, nrv_prec prec, cudaStream_t s, float inv_out) {
+                    const Geo& g, int level, nrv_prec prec, cudaStream_t s, float inv_out,
+                    const TcHead* head) {
     if (prec != NRV_PREC_BF16 && prec != NRV_PREC_FP8)
         return fail(NRV_ERR_UNSUPPORTED, "tensor-core path is BF16 or FP8");
     const Layer& L = net->layers[l];
@@ -1067,7 +1131,7 @@ nrv_status tc_conv3(const Net* net, int l, const void* x1, int c1, const void* x
     const TcLayerCfg& c = g_cfg[fp8][l];
     const uint8_t* w = (const uint8_t*)(fp8 ? net->wfp8.p : net->wbf16.p) + c.w_off;
     return tc_launch(net, c, w, (const float*)net->params.p + L.boff, 1, nullptr, L.cout, x1, c1,
-                     x2, c2, y, g.n, g.h[level], g.w[level], s, fp8, inv_out);
+                     x2, c2, y, g.n, g.h[level], g.w[level], s, fp8, inv_out, head);
 }
 
 nrv_status tc_dgrad(const Net* net, int l, const void* gin, void* out, const void* mask, int n, int H,
