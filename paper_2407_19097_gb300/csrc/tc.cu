@@ -308,6 +308,13 @@ __global__ void __launch_bounds__(NTHREADS, 4)
         mbar_init(b_done, P.nissue);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        // the weights (packed long before this launch; see the dependency wait below)
+        mbar_expect_tx(b_w, P.w_bytes);
+        const uint8_t* src = P.wpk + (size_t)slice * P.w_bytes;
+        for (uint32_t o = 0; o < P.w_bytes; o += 16384) {
+            const uint32_t len = P.w_bytes - o < 16384 ? P.w_bytes - o : 16384;
+            bulk_load(s_w + o, src + o, len, b_w);
+        }
     }
     // per output column of this slice: its bias (column n maps to channel n mod cout)
     for (int i = threadIdx.x; i < P.n_slice; i += NTHREADS) {
@@ -328,16 +335,17 @@ __global__ void __launch_bounds__(NTHREADS, 4)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
+    // Programmatic dependent launch: everything above may overlap the previous kernel
+    // (it reads only weights, biases and scales, written at least two launches earlier);
+    // activations are read, and outputs written, only after the previous kernel has
+    // completed.  Dependents may start once every CTA has issued its last row load (after
+    // this wait), so anything they read before their own wait was written at least two
+    // launches back.  Both instructions do nothing for a plain launch.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     if (warp == 0) {
         if (lane == 0) {
-            // weights once, then each input row once per run of tiles
-            mbar_expect_tx(b_w, P.w_bytes);
-            const uint8_t* src = P.wpk + (size_t)slice * P.w_bytes;
-            for (uint32_t o = 0; o < P.w_bytes; o += 16384) {
-                const uint32_t len = P.w_bytes - o < 16384 ? P.w_bytes - o : 16384;
-                bulk_load(s_w + o, src + o, len, b_w);
-            }
+            // each input row once per run of tiles (the weights are already on their way)
             TileWalk w;
             w.init(P, t_begin);
             int cur_col = -1, next_row = 0, nloads = 0, slot = 0;
@@ -365,6 +373,8 @@ __global__ void __launch_bounds__(NTHREADS, 4)
                     ring_next(slot, phase, P.nslot);
                 }
             }
+            // this CTA's inputs are all requested: the next layer may start launching
+            asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
             // every load issued must have landed before the CTA may exit: the last
             // min(nloads, nslot) loads, walking the ring backwards
             for (int q = nloads < P.nslot ? nloads : P.nslot; q > 0; --q) {
@@ -954,6 +964,16 @@ nrv_status tc_repack_fp8(Net* net, cudaStream_t s) {
 
 static int g_num_sms = 0;
 
+// Programmatic dependent launch of the tensor-core layers, unless NRV_PDL=0.
+static bool pdl_enabled() {
+    static int on = -1;
+    if (on < 0) {
+        const char* e = getenv("NRV_PDL");
+        on = (e && e[0] == '0') ? 0 : 1;
+    }
+    return on == 1;
+}
+
 // Launch one tensor-core layer on a level of geometry (n, H, W): a 3x3 conv
 // writes [n][H][W][C_out]; a transposed conv reads level (H, W) and writes
 // [n][2H][2W][C_out]; all tensors row-planar.  FP8: operands and output E4M3,
@@ -1027,7 +1047,7 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
         have_fa[fp8] = true;
     }
     const cudaFuncAttributes& fa = fa_k[fp8];
-    auto occupancy = [&](uint32_t smem_dyn) {
+    auto occupancy = [&](uint32_t smem_dyn, bool count_tmem = true) {
         const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
         int o = prop.regsPerMultiprocessor / (regs_per_warp * (NTHREADS / 32));
         o = o < prop.maxThreadsPerMultiProcessor / NTHREADS ? o : prop.maxThreadsPerMultiProcessor / NTHREADS;
@@ -1035,7 +1055,7 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
         const int by_smem = (int)(prop.sharedMemPerMultiprocessor / smem_cta);
         o = o < by_smem ? o : by_smem;
         o = o < prop.maxBlocksPerMultiProcessor ? o : prop.maxBlocksPerMultiProcessor;
-        if (o * (int)cols > 512) o = 512 / (int)cols;
+        if (count_tmem && o * (int)cols > 512) o = 512 / (int)cols;
         return o;
     };
     // ring slots: two rows of read-ahead (more co-resident CTAs give the tensor pipe
@@ -1049,7 +1069,7 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
            occupancy(smem_for(nslot + 1)) >= occ0)
         ++nslot;
     P.nslot = nslot;
-    const uint32_t smem = smem_for(nslot);
+    uint32_t smem = smem_for(nslot);
     // instruction descriptor: FP32 accumulator; A/B BF16 (kind::f16) or E4M3 (kind::f8f6f4)
     const uint32_t ab_fmt = fp8 ? 0u : 1u;
     P.idesc = (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(c.n_slice >> 3) << 17) |
@@ -1111,11 +1131,34 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
     }
     int occ = occupancy(smem);
     if (occ < 1) occ = 1;
+    // The block scheduler does not see TMEM: where registers and shared memory would admit
+    // more CTAs per SM than the TMEM columns, pad the shared memory so that it does not
+    // place them (a CTA beyond the TMEM budget would stall in its allocation while other
+    // SMs idle, e.g. when CTAs are placed while the previous kernel drains).
+    if (occupancy(smem, false) > occ) {
+        const size_t per_cta = prop.sharedMemPerMultiprocessor / (size_t)(occ + 1) + 1;
+        const size_t fixed = fa.sharedSizeBytes + prop.reservedSharedMemPerBlock;
+        if (per_cta > fixed) {
+            const uint32_t pad = (uint32_t)((per_cta - fixed + 127) / 128 * 128);
+            if (pad > smem && pad <= 215 * 1024) smem = pad;
+        }
+    }
     int per_slice = (g_num_sms * occ) / c.nslices;
     if (per_slice < 1) per_slice = 1;
     if (per_slice > P.ntiles) per_slice = P.ntiles;
     P.ctas_per_slice = per_slice;
-    kern<<<per_slice * c.nslices, NTHREADS, smem, s>>>(m1, m2, P);
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)(per_slice * c.nslices));
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    NRV_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, m1, m2, P));
     NRV_CHECK_LAUNCH();
     return NRV_OK;
 }
