@@ -149,15 +149,18 @@ nrv_status forward_fp8(Net* net, const uint8_t* netin, float* rgb, cudaStream_t 
         net->backend[l] = 1;
         return tc_upconv(net, l, A(in), A(out), g, level_in, NRV_PREC_FP8, s, inv(out));
     };
+    // a 3x3 conv and the pool of its output to the next level (separate kernels: at level 0
+    // the FP8 epilogue is the bottleneck and a fused pool measured slower)
+    auto conv_pool = [&](int l, int in, int c1, int out, int level, int pooled) -> nrv_status {
+        NRV_TRY(conv(l, A(in), c1, nullptr, 0, out, level));
+        return pool(out, pooled, level + 1);
+    };
     NRV_TRY(conv(L_E0A, netin, 16, nullptr, 0, A_E0A, 0));
-    NRV_TRY(conv(L_E0B, A(A_E0A), 16, nullptr, 0, A_E0B, 0));
-    NRV_TRY(pool(A_E0B, A_P0, 1));
+    NRV_TRY(conv_pool(L_E0B, A_E0A, 16, A_E0B, 0, A_P0));
     NRV_TRY(conv(L_E1A, A(A_P0), 16, nullptr, 0, A_E1A, 1));
-    NRV_TRY(conv(L_E1B, A(A_E1A), 32, nullptr, 0, A_E1B, 1));
-    NRV_TRY(pool(A_E1B, A_P1, 2));
+    NRV_TRY(conv_pool(L_E1B, A_E1A, 32, A_E1B, 1, A_P1));
     NRV_TRY(conv(L_E2A, A(A_P1), 32, nullptr, 0, A_E2A, 2));
-    NRV_TRY(conv(L_E2B, A(A_E2A), 64, nullptr, 0, A_E2B, 2));
-    NRV_TRY(pool(A_E2B, A_P2, 3));
+    NRV_TRY(conv_pool(L_E2B, A_E2A, 64, A_E2B, 2, A_P2));
     NRV_TRY(conv(L_E3A, A(A_P2), 64, nullptr, 0, A_E3A, 3));
     NRV_TRY(conv(L_E3B, A(A_E3A), 128, nullptr, 0, A_E3B, 3));
     NRV_TRY(up(L_UP3, A_E3B, A_UP3, 3));

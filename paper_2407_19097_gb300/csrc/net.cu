@@ -215,17 +215,26 @@ static nrv_status forward_t(Net* net, const T* netin, float* rgb, cudaStream_t s
         (void)L;
         return simt_upconv<T>(net, l, CV(in), V(out), g.n, g.h[level_in], g.w[level_in], s);
     };
+    // a 3x3 conv whose output is also pooled to the next level (fused on the tensor cores)
+    auto conv_pool = [&](int l, int in, int c1, int out, int level, int pooled) -> nrv_status {
+        if (use_tc) {
+            nrv_status st = tc_conv3(net, l, act<T>(net, in), c1, nullptr, 0, act<T>(net, out), g,
+                                     level, prec, s, 1.0f, nullptr, act<T>(net, pooled));
+            net->backend[l] = 1;
+            if (st != NRV_ERR_UNSUPPORTED) return st;
+            clear_error();
+        }
+        NRV_TRY(conv(l, CV(in), c1, TView<const T>{nullptr, 0}, 0, out, level));
+        return pool(out, pooled, level + 1);
+    };
     const TView<const T> x{netin, net->c0p, planar};   // one plane: also plain NHWC
     const TView<const T> none{nullptr, 0};
     NRV_TRY(conv(L_E0A, x, net->c0p, none, 0, A_E0A, 0));
-    NRV_TRY(conv(L_E0B, CV(A_E0A), 16, none, 0, A_E0B, 0));
-    NRV_TRY(pool(A_E0B, A_P0, 1));
+    NRV_TRY(conv_pool(L_E0B, A_E0A, 16, A_E0B, 0, A_P0));
     NRV_TRY(conv(L_E1A, CV(A_P0), 16, none, 0, A_E1A, 1));
-    NRV_TRY(conv(L_E1B, CV(A_E1A), 32, none, 0, A_E1B, 1));
-    NRV_TRY(pool(A_E1B, A_P1, 2));
+    NRV_TRY(conv_pool(L_E1B, A_E1A, 32, A_E1B, 1, A_P1));
     NRV_TRY(conv(L_E2A, CV(A_P1), 32, none, 0, A_E2A, 2));
-    NRV_TRY(conv(L_E2B, CV(A_E2A), 64, none, 0, A_E2B, 2));
-    NRV_TRY(pool(A_E2B, A_P2, 3));
+    NRV_TRY(conv_pool(L_E2B, A_E2A, 64, A_E2B, 2, A_P2));
     NRV_TRY(conv(L_E3A, CV(A_P2), 64, none, 0, A_E3A, 3));
     NRV_TRY(conv(L_E3B, CV(A_E3A), 128, none, 0, A_E3B, 3));
     NRV_TRY(upconv(L_UP3, A_E3B, A_UP3, 3));

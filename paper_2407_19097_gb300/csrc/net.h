@@ -88,7 +88,8 @@ struct TcHead {
 // tensor-core convolution (tc.cu); returns NRV_ERR_UNSUPPORTED when a shape is not covered
 nrv_status tc_conv3(const Net* net, int layer, const void* x1, int c1, const void* x2, int c2,
                     void* y, const Geo& g, int level, nrv_prec prec, cudaStream_t s,
-                    float inv_out = 1.0f, const TcHead* head = nullptr);
+                    float inv_out = 1.0f, const TcHead* head = nullptr,
+                    void* pool_y = nullptr);   // pool_y: also the 2x2 average pool of y
 nrv_status tc_upconv(const Net* net, int layer, const void* x, void* y, const Geo& g, int level_in,
                      nrv_prec prec, cudaStream_t s, float inv_out = 1.0f);
 nrv_status tc_repack_fp8(Net* net, cudaStream_t s);

@@ -97,6 +97,11 @@ struct TcParams {
     int rgb_h, rgb_w;
     float head_s;
     int store_y;
+    // optional 2x2 average pool of the stored output (mode 0, even h and w): row-planar
+    // [n][h/2][out_nch][w/2][16 bytes] in the output's precision (and FP8 scale)
+    void* pool_y;            // (BF16 only)
+    uint32_t stash_off;      // pool: shared-memory copy of the even row's stored values,
+                             // [16-byte word][128 lanes][16 bytes], after the ring
     // per K-step of one input row (every row of a tile has the same pattern):
     // low word of the A descriptor relative to the row's slot,
     // (offset >> 4) | (LBO >> 4) << 16; K-step ks reads row ks / (nks / rows)
@@ -291,8 +296,10 @@ __global__ void __launch_bounds__(NTHREADS, 4)
     // this CTA's output-channel slice and its run of tiles
     const int slice = blockIdx.x % P.nslices;
     const int cta = blockIdx.x / P.nslices;
-    const int t_begin = (int)(((long long)cta * P.ntiles) / P.ctas_per_slice);
-    const int t_end = (int)(((long long)(cta + 1) * P.ntiles) / P.ctas_per_slice);
+    // (pooling: runs of whole row pairs, so one thread stores both rows of its pixel)
+    const int pair = P.pool_y ? 2 : 1;
+    const int t_begin = pair * (int)(((long long)cta * (P.ntiles / pair)) / P.ctas_per_slice);
+    const int t_end = pair * (int)(((long long)(cta + 1) * (P.ntiles / pair)) / P.ctas_per_slice);
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
@@ -578,6 +585,12 @@ __global__ void __launch_bounds__(NTHREADS, 4)
                             *reinterpret_cast<uint4*>(dst + (size_t)wo * 16) =
                                 make_uint4(packed[4], packed[5], packed[6], packed[7]);
                         }
+                        if (P.pool_y && !(w.y & 1)) {
+                            uint4* st = reinterpret_cast<uint4*>(smem + P.stash_off) +
+                                        (c0 / 8) * TILE_M + m;
+                            st[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                            st[TILE_M] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                        }
                         if (P.head_w) {
                             // the rounded BF16 values, as a separate head kernel would read them
 #pragma unroll
@@ -588,6 +601,53 @@ __global__ void __launch_bounds__(NTHREADS, 4)
                                 v[2 * j + 1] = __high2float(h2);
                             }
                             head_store(P, head_ws, w.img, w.y, x, v);
+                        }
+                    }
+                }
+                if (!FP8 && P.pool_y && (w.y & 1)) {
+                    // 2x2 average pool (BF16): rows y - 1 (kept in shared memory by this
+                    // thread for the previous tile) and y, pixels x (this lane) and x + 1
+                    // (the next lane), as the stored values; the mean is rounded to BF16
+                    const size_t prow = (size_t)w.img * (P.h >> 1) + (w.y >> 1);
+                    const int wp = P.w >> 1;
+                    const int o = slice * P.n_slice + c0;
+#pragma unroll
+                    for (int h8 = 0; h8 < 16; h8 += 8) {
+                        float a[8], c[8];
+                        if (valid) {
+                            const uint4 raw = *reinterpret_cast<const uint4*>(
+                                smem + P.stash_off + (((c0 + h8) / 8) * TILE_M + m) * 16);
+                            const uint32_t rw[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&rw[j]);
+                                a[2 * j] = __low2float(h2);
+                                a[2 * j + 1] = __high2float(h2);
+                            }
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                c[j] = __bfloat162float(__float2bfloat16_rn(v[h8 + j]));
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) a[j] = c[j] = 0.0f;
+                        }
+                        float r[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const float b = __shfl_down_sync(0xffffffffu, a[j], 1);
+                            const float d = __shfl_down_sync(0xffffffffu, c[j], 1);
+                            r[j] = 0.25f * ((a[j] + b) + (c[j] + d));
+                        }
+                        if (valid && !(m & 1)) {
+                            uint32_t pk[4];
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                __nv_bfloat162 h2 = __floats2bfloat162_rn(r[2 * j], r[2 * j + 1]);
+                                pk[j] = *reinterpret_cast<uint32_t*>(&h2);
+                            }
+                            uint8_t* dst = (uint8_t*)P.pool_y +
+                                ((prow * P.out_nch + (size_t)((o + h8) / 8)) * wp + (x >> 1)) * 16;
+                            *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                         }
                     }
                 }
@@ -983,7 +1043,8 @@ static bool pdl_enabled() {
 static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* wpk,
                             const float* bias, int relu, const void* mask, int cout, const void* x1,
                             int c1, const void* x2, int c2, void* y, int n, int H, int W,
-                            cudaStream_t s, int fp8, float inv_out, const TcHead* head = nullptr) {
+                            cudaStream_t s, int fp8, float inv_out, const TcHead* head = nullptr,
+                            void* pool_y = nullptr) {
     if (!c.ok || c.c1 != c1 || c.c2 != c2) return fail(NRV_ERR_UNSUPPORTED, "layer not configured");
     if (fp8 && !net->fp8_ready) return fail(NRV_ERR_STATE, "FP8 needs activation scales");
     if (n <= 0 || H <= 0 || W <= 0) return fail(NRV_ERR_ARG, "empty tensor");
@@ -1060,7 +1121,9 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
     };
     // ring slots: two rows of read-ahead (more co-resident CTAs give the tensor pipe
     // several MMA issuers), then as many more as keep that occupancy; within 215 KB
-    auto smem_for = [&](int ns) { return P.w_region + (uint32_t)ns * P.slot_bytes; };
+    // pool: one 16-byte word per 16 stored bytes of a lane, 128 lanes
+    const uint32_t stash_bytes = pool_y ? (uint32_t)(c.n_slice * es / 16) * TILE_M * 16 : 0u;
+    auto smem_for = [&](int ns) { return P.w_region + (uint32_t)ns * P.slot_bytes + stash_bytes; };
     int nslot = c.rows + 2;
     while (nslot > c.rows && smem_for(nslot) > 215 * 1024) --nslot;
     if (smem_for(nslot) > 215 * 1024) return fail(NRV_ERR_UNSUPPORTED, "tile does not fit in shared memory");
@@ -1070,6 +1133,7 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
         ++nslot;
     P.nslot = nslot;
     uint32_t smem = smem_for(nslot);
+    P.stash_off = P.w_region + (uint32_t)nslot * P.slot_bytes;
     // instruction descriptor: FP32 accumulator; A/B BF16 (kind::f16) or E4M3 (kind::f8f6f4)
     const uint32_t ab_fmt = fp8 ? 0u : 1u;
     P.idesc = (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(c.n_slice >> 3) << 17) |
@@ -1080,6 +1144,11 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
     P.fp8 = fp8;
     P.inv_out = inv_out;
     P.store_y = 1;
+    if (pool_y) {
+        if (!conv || fp8 || (H & 1) || (W & 1) || mask || head)
+            return fail(NRV_ERR_UNSUPPORTED, "the fused pool needs a 3x3 conv on an even grid");
+        P.pool_y = pool_y;
+    }
     if (head) {
         if (!conv || c.nslices != 1 || c.n_slice != 16 || cout != 16 || !relu)
             return fail(NRV_ERR_UNSUPPORTED, "the fused head needs a 16-channel conv");
@@ -1165,7 +1234,7 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
 
 nrv_status tc_conv3(const Net* net, int l, const void* x1, int c1, const void* x2, int c2, void* y,
                     const Geo& g, int level, nrv_prec prec, cudaStream_t s, float inv_out,
-                    const TcHead* head) {
+                    const TcHead* head, void* pool_y) {
     if (prec != NRV_PREC_BF16 && prec != NRV_PREC_FP8)
         return fail(NRV_ERR_UNSUPPORTED, "tensor-core path is BF16 or FP8");
     const Layer& L = net->layers[l];
@@ -1174,7 +1243,7 @@ nrv_status tc_conv3(const Net* net, int l, const void* x1, int c1, const void* x
     const TcLayerCfg& c = g_cfg[fp8][l];
     const uint8_t* w = (const uint8_t*)(fp8 ? net->wfp8.p : net->wbf16.p) + c.w_off;
     return tc_launch(net, c, w, (const float*)net->params.p + L.boff, 1, nullptr, L.cout, x1, c1,
-                     x2, c2, y, g.n, g.h[level], g.w[level], s, fp8, inv_out, head);
+                     x2, c2, y, g.n, g.h[level], g.w[level], s, fp8, inv_out, head, pool_y);
 }
 
 nrv_status tc_dgrad(const Net* net, int l, const void* gin, void* out, const void* mask, int n, int H,
