@@ -284,6 +284,37 @@ nrv_status nrv_shade(nrv_net* net, const void* d_netin, int n, int height, int w
 nrv_status nrv_net_run_layer(nrv_net* net, int layer, const void* d_x1, const void* d_x2, int n,
                              int h, int w, nrv_prec prec, void* d_y, nrv_stream stream);
 
+/* Weight and bias gradient of one 3x3 convolution layer (Sec. 3.3's network; the
+ * backward of nrv_net_backward, exposed so that it can be checked or reused alone):
+ *   dW[o][c][u][v] = sum_p dy[p][o] * x[p + (u - 1, v - 1)][c]  (zero outside),
+ *   db[o] = sum_p dy[p][o],
+ * over all n*h*w pixels p.  d_dy: [n][h][w][C_out] (the gradient at the layer's
+ * pre-activation output), d_x1: [n][h][w][c1], d_x2: [n][h][w][c2] for the
+ * concatenating decoder layers (else NULL), all NHWC in `prec` (F32 or BF16; the
+ * first layer's input has the padded width of nrv_pack).  Writes dW (PyTorch
+ * layout) and db into their places in d_grad (the flat parameter layout); other
+ * entries are untouched.  BF16 runs on the tensor cores (FP32 accumulation, then a
+ * fixed-order sum of partials: deterministic); F32 on the CUDA cores.  Uses the
+ * net's workspaces (one call at a time per net).
+ * Errors: NRV_ERR_ARG (null, misaligned, not a 3x3 layer, x2 given or missing),
+ * NRV_ERR_UNSUPPORTED (FP8). */
+nrv_status nrv_net_layer_wgrad(nrv_net* net, int layer, const void* d_dy, const void* d_x1,
+                               const void* d_x2, int n, int h, int w, nrv_prec prec,
+                               float* d_grad, nrv_stream stream);
+
+/* Data gradient of one 3x3 convolution layer (the backward of Sec. 3.3's network,
+ * exposed like nrv_net_layer_wgrad):
+ *   dx[p][c] = sum_{o,u,v} W[o][c][u][v] * dy[p - (u - 1, v - 1)][o]  (zero outside),
+ * then dx[p][c] = 0 where d_mask[p][c] <= 0 when d_mask is not NULL (the ReLU of the layer
+ * below: pass its output).  d_dy: [n][h][w][C_out], d_mask and d_dx: [n][h][w][C_in] (both
+ * halves of a concatenation), NHWC in `prec` (F32 or BF16).  BF16 runs on the tensor cores
+ * with the kernel flipped and transposed (FP32 accumulation, BF16 output); F32 on the CUDA
+ * cores.  Not for the first layer (its input needs no gradient).
+ * Errors: NRV_ERR_ARG (null, misaligned, not a 3x3 layer, the first layer), NRV_ERR_STATE (no
+ * parameters), NRV_ERR_UNSUPPORTED (FP8). */
+nrv_status nrv_net_layer_dgrad(nrv_net* net, int layer, const void* d_dy, const void* d_mask,
+                               int n, int h, int w, nrv_prec prec, void* d_dx, nrv_stream stream);
+
 /* Which kernel family ran layer `layer` in the net's most recent forward pass:
  * 0 = SIMT (CUDA cores), 1 = tensor cores (tcgen05), -1 = not run yet or a
  * bad argument.  Lets callers check that a precision ran where they expect. */

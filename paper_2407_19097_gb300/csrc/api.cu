@@ -407,6 +407,31 @@ extern "C" nrv_status nrv_net_run_layer(nrv_net* net, int layer, const void* x1,
     return net_run_layer(net, layer, x1, x2, n, h, w, prec, y, (cudaStream_t)stream);
 }
 
+extern "C" nrv_status nrv_net_layer_wgrad(nrv_net* net, int layer, const void* dy, const void* x1,
+                                          const void* x2, int n, int h, int w, nrv_prec prec,
+                                          float* grad, nrv_stream stream) {
+    clear_error();
+    if (!net || !dy || !x1 || !grad) return fail(NRV_ERR_ARG, "null argument");
+    if (layer < 0 || layer >= NUM_LAYERS) return fail(NRV_ERR_ARG, "bad layer %d", layer);
+    if (n < 1 || h < 1 || w < 1 || h > 16384 || w > 16384) return fail(NRV_ERR_ARG, "bad size");
+    if (!aligned(dy, 32) || !aligned(x1, 32) || (x2 && !aligned(x2, 32)) || !aligned(grad, 16))
+        return fail(NRV_ERR_ARG, "tensors must be 32-byte aligned (grad 16-byte)");
+    return net_layer_wgrad(net, layer, dy, x1, x2, n, h, w, prec, grad, (cudaStream_t)stream);
+}
+
+extern "C" nrv_status nrv_net_layer_dgrad(nrv_net* net, int layer, const void* dy, const void* mask,
+                                          int n, int h, int w, nrv_prec prec, void* dx,
+                                          nrv_stream stream) {
+    clear_error();
+    if (!net || !dy || !dx) return fail(NRV_ERR_ARG, "null argument");
+    if (layer < 0 || layer >= NUM_LAYERS) return fail(NRV_ERR_ARG, "bad layer %d", layer);
+    if (!net->has_params) return fail(NRV_ERR_STATE, "no parameters loaded");
+    if (n < 1 || h < 1 || w < 1 || h > 16384 || w > 16384) return fail(NRV_ERR_ARG, "bad size");
+    if (!aligned(dy, 32) || !aligned(dx, 32) || (mask && !aligned(mask, 32)))
+        return fail(NRV_ERR_ARG, "tensors must be 32-byte aligned");
+    return net_layer_dgrad(net, layer, dy, mask, n, h, w, prec, dx, (cudaStream_t)stream);
+}
+
 extern "C" int nrv_net_layer_backend(const nrv_net* net, int layer) {
     if (!net || layer < 0 || layer >= NUM_LAYERS) return -1;
     return net->backend[layer];

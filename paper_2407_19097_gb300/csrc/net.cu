@@ -311,7 +311,7 @@ __global__ void relayout_kernel(const uint4* __restrict__ src, uint4* __restrict
     }
 }
 
-static nrv_status relayout(const void* src, void* dst, size_t rows, int w, int c, size_t es,
+nrv_status relayout(const void* src, void* dst, size_t rows, int w, int c, size_t es,
                            bool to_planar, cudaStream_t s) {
     const int nch = (int)(c * es / 16);
     relayout_kernel<<<blocks_for(rows * w * nch), 256, 0, s>>>((const uint4*)src, (uint4*)dst, rows,

@@ -1,5 +1,7 @@
 // The U-Net handle: layer table, packed weights, activation workspace.
 #pragma once
+#include <cuda.h>
+
 #include "internal.h"
 
 namespace nrv {
@@ -67,6 +69,16 @@ nrv_status net_prepare(Net* net, int n, int H, int W, nrv_prec prec);
 nrv_status net_forward(Net* net, const void* netin, int n, int H, int W, nrv_prec prec, float* rgb,
                        cudaStream_t s, bool keep_acts = true);
 nrv_status net_backward(Net* net, const float* drgb, float* dparams, cudaStream_t s);
+// weight and bias gradient of one 3x3 conv layer from NHWC tensors (train.cu)
+nrv_status net_layer_wgrad(Net* net, int l, const void* dy, const void* x1, const void* x2, int n,
+                           int h, int w, nrv_prec prec, float* dgrad, cudaStream_t s);
+// data gradient of one 3x3 conv layer from NHWC tensors (train.cu)
+nrv_status net_layer_dgrad(Net* net, int l, const void* dy, const void* mask, int n, int h, int w,
+                           nrv_prec prec, void* dx, cudaStream_t s);
+// 16-byte chunks between NHWC and row-planar order (net.cu): `rows` rows of w pixels, c
+// channels of es bytes
+nrv_status relayout(const void* src, void* dst, size_t rows, int w, int c, size_t es,
+                    bool to_planar, cudaStream_t s);
 nrv_status net_repack(Net* net, cudaStream_t s);
 // parameters in and out (netio.cu): Xavier-uniform draw into d_params, file save / load
 nrv_status net_init_params(const Net* net, uint64_t seed, float* d_params, cudaStream_t s);
@@ -93,6 +105,18 @@ nrv_status tc_conv3(const Net* net, int layer, const void* x1, int c1, const voi
 nrv_status tc_upconv(const Net* net, int layer, const void* x, void* y, const Geo& g, int level_in,
                      nrv_prec prec, cudaStream_t s, float inv_out = 1.0f);
 nrv_status tc_repack_fp8(Net* net, cudaStream_t s);
+// TMA map of a row-planar tensor [n][h][nch][w][16 bytes] (tc.cu): boxes of 128 pixels x
+// box_planes planes of one row
+nrv_status tc_planar_map(CUtensorMap* map, const void* base, int n, int h, int w, int nch,
+                         int box_planes);
+// Weight gradient of 3x3 conv layer l on the tensor cores (wgrad_tc.cu), BF16 row-planar:
+// part[split][o][tap][c] (FP32 partial sums over each split's pixels, c over all input channels)
+// for the output gradient g (C_out channels) and the layer input (x1: c1 channels, x2: c2 or
+// none); *nsplit receives the number of splits.  NRV_ERR_UNSUPPORTED when the shape is not
+// covered (input channels not a multiple of 16).
+nrv_status tc_wgrad(const Net* net, int l, const void* g, const void* x1, int c1, const void* x2,
+                    int c2, int n, int H, int W, float* part, size_t part_floats, int* nsplit,
+                    cudaStream_t s);
 // data gradient of 3x3 conv layer l on the tensor cores (BF16, row-planar): out = conv3x3 of
 // the output gradient gin with the flipped, transposed kernel, zeroed where mask <= 0 (mask
 // may be null); NRV_ERR_UNSUPPORTED when the layer has no such path

@@ -44,6 +44,7 @@
 #include <string.h>
 
 #include "net.h"
+#include "tcgen05.cuh"
 
 namespace nrv {
 
@@ -107,122 +108,6 @@ struct TcParams {
     // (offset >> 4) | (LBO >> 4) << 16; K-step ks reads row ks / (nks / rows)
     uint32_t a_lo[MAX_KS];
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-// One test of the phase; the thread may be suspended (up to the hint, 0.5 ms)
-// until the phase completes, so waiting warps do not spin on the issue slots.
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity), "r"(500000u)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait (about 2 s): false on timeout or, when heed_abort, as soon as
-// another role has aborted.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                          unsigned* status, bool heed_abort = true) {
-    if (mbar_try(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    while (true) {
-        if (mbar_try(bar, parity)) return true;
-        if (heed_abort && *abort_flag) return false;
-        if (global_ns() - t0 > 2000000000ull) {
-            *abort_flag = 1;
-            atomicOr(status, STATUS_TIMEOUT);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
-                                            int c2, int c3, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
-                                          uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_fp8(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                        uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-        "%11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 
 // Tile t of a slice covers pixels [xt * tile_w, +tile_w) of row y of image img,
 // t = (img * tiles_x + xt) * h + y: consecutive tiles walk down one column.
@@ -696,15 +581,18 @@ EncodeTiledFn encode_fn() {
 // one row and lands in shared memory as [plane][128 pixels][16 bytes].  Each
 // plane is a contiguous 2 KB run in global memory.  Pixels outside [0, w) and
 // rows outside [0, h) read as zero.
-nrv_status make_planar_map(CUtensorMap* map, const void* base, int n, int h, int w, int nch) {
+nrv_status make_planar_map(CUtensorMap* map, const void* base, int n, int h, int w, int nch,
+                           int box_planes = 0) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return fail(NRV_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
     if (((uintptr_t)base & 15) != 0) return fail(NRV_ERR_ARG, "tensor base not 16-byte aligned");
     if (nch < 1 || nch > 256) return fail(NRV_ERR_UNSUPPORTED, "planes per row out of range");
+    if (box_planes <= 0) box_planes = nch;
+    if (box_planes > nch) return fail(NRV_ERR_UNSUPPORTED, "box wider than the tensor");
     const cuuint64_t dims[4] = {(cuuint64_t)2 * w, (cuuint64_t)nch, (cuuint64_t)h, (cuuint64_t)n};
     const cuuint64_t row = (cuuint64_t)w * 16;
     const cuuint64_t strides[3] = {row, row * nch, row * nch * h};
-    const cuuint32_t box[4] = {2 * TILE_M, (cuuint32_t)nch, 1, 1};
+    const cuuint32_t box[4] = {2 * TILE_M, (cuuint32_t)box_planes, 1, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<void*>(base), dims, strides,
                      box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -1254,6 +1142,11 @@ nrv_status tc_dgrad(const Net* net, int l, const void* gin, void* out, const voi
     const uint8_t* w = (const uint8_t*)net->wtbf16.p + c.w_off;
     return tc_launch(net, c, w, nullptr, 0, mask, L.cin, gin, L.cout, nullptr, 0, out, n, H, W, s, 0,
                      1.0f);
+}
+
+nrv_status tc_planar_map(CUtensorMap* map, const void* base, int n, int h, int w, int nch,
+                         int box_planes) {
+    return make_planar_map(map, base, n, h, w, nch, box_planes);
 }
 
 nrv_status tc_upconv(const Net* net, int l, const void* x, void* y, const Geo& g, int level_in,

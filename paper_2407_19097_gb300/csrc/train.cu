@@ -241,6 +241,37 @@ __global__ void head_dgrad_kernel(const float* drgb, const float* w, TView<const
     }
 }
 
+// partb[blk][o] = sum of g[p][o] over the block's run of pixels p (the bias gradient of a
+// 3x3 conv): one plane of 8 channels at a time, thread i taking pixels i, i + 256, ...,
+// then a fixed-order tree over the threads.
+template <typename T>
+__global__ void __launch_bounds__(256) bias_grad_kernel(TView<const T> g, int cout, int w,
+                                                        size_t npx, size_t chunk, float* partb) {
+    __shared__ float red[256][9];
+    const size_t p0 = blockIdx.x * chunk, p1 = p0 + chunk < npx ? p0 + chunk : npx;
+    for (int c0 = 0; c0 < cout; c0 += 8) {
+        float acc[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        for (size_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+            float v[8];
+            ld8<T>(g.at(p / w, (int)(p % w), c0, w), v);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] += v[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) red[threadIdx.x][k] = acc[k];
+        __syncthreads();
+        for (int st = 128; st > 0; st >>= 1) {
+            if ((int)threadIdx.x < st) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) red[threadIdx.x][k] += red[threadIdx.x + st][k];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x < 8) partb[(size_t)blockIdx.x * cout + c0 + threadIdx.x] = red[0][threadIdx.x];
+        __syncthreads();
+    }
+}
+
 // part[blk][o*16 + c] = sum drgb[o] * x[c]; part[blk][48 + o] = sum drgb[o], over the block's
 // chunk of cropped pixels: every thread keeps all 51 sums, then the block adds them (warp
 // shuffles, then the 8 warps in order).
@@ -402,6 +433,37 @@ struct Bwd {
                           int c2, int level) {
         const Layer& L = net->layers[l];
         const int cin = c1 + c2;
+        if (sizeof(T) == 2) {
+            // BF16: the weight gradient on the tensor cores, the bias gradient beside it
+            const bool fits = gpre.planar && !gpre.coff && gpre.ld == L.cout && x1.planar &&
+                              !x1.coff && x1.ld == c1 &&
+                              (!c2 || (x2.planar && !x2.coff && x2.ld == c2));
+            if (fits) {
+                const int groups = cin / 16 > 0 ? cin / 16 : 1;
+                const size_t per_split = (size_t)L.cout * 9 * cin;
+                const size_t max_split = (size_t)(304 + groups - 1) / groups;
+                const int nb = 304;
+                NRV_TRY(net->partial.ensure((max_split * per_split + (size_t)nb * L.cout) * sizeof(float)));
+                float* part = (float*)net->partial.p;
+                float* partb = part + max_split * per_split;
+                int nsplit = 0;
+                const nrv_status st = tc_wgrad(net, l, gpre.p, x1.p, c1, c2 ? x2.p : nullptr, c2, g.n,
+                                               g.h[level], g.w[level], part, max_split * per_split,
+                                               &nsplit, s);
+                if (st == NRV_OK) {
+                    NRV_TRY(reduce_partials(part, nsplit, per_split, (int)per_split, 0, L.cout, cin,
+                                            L.cin, dparams + L.woff, s));
+                    const size_t npx = g.px(level);
+                    const size_t chunk = (npx + nb - 1) / nb;
+                    bias_grad_kernel<T><<<nb, 256, 0, s>>>(gpre, L.cout, g.w[level], npx, chunk, partb);
+                    NRV_CHECK_LAUNCH();
+                    return reduce_partials(partb, nb, L.cout, L.cout, 2, L.cout, cin, L.cin,
+                                           dparams + L.boff, s);
+                }
+                if (st != NRV_ERR_UNSUPPORTED) return st;
+                clear_error();
+            }
+        }
         const int CG = cin < 16 ? cin : 16;
         if (cin % CG || (c2 && c1 % CG) || L.cout % 16)
             return fail(NRV_ERR_UNSUPPORTED, "weight gradient: channel groups");
@@ -588,6 +650,75 @@ struct Bwd {
 // The training forward keeps its input pointer for the first layer's weight gradient.
 static const void* g_saved_netin = nullptr;
 void set_saved_input(const void* p) { g_saved_netin = p; }
+
+nrv_status net_layer_wgrad(Net* net, int l, const void* dy, const void* x1, const void* x2, int n,
+                           int h, int w, nrv_prec prec, float* dgrad, cudaStream_t s) {
+    const Layer& L = net->layers[l];
+    if (L.kind != CONV3) return fail(NRV_ERR_ARG, "layer %s is not a 3x3 convolution", L.name);
+    int c1 = l == L_E0A ? net->c0p : L.cin, c2 = 0;
+    if (l == L_D2A || l == L_D1A || l == L_D0A) c1 = c2 = L.cin / 2;
+    if ((c2 > 0) != (x2 != nullptr))
+        return fail(NRV_ERR_ARG, "layer %s: x2 must be %s", L.name, c2 ? "given" : "NULL");
+    Geo g;
+    memset(&g, 0, sizeof(g));
+    g.n = n;
+    g.h[0] = h;
+    g.w[0] = w;
+    if (prec == NRV_PREC_F32) {
+        using T = float;
+        Bwd<T> b{net, s, g, dgrad, {}, {}};
+        return b.wgrad_conv(l, TView<const T>{(const T*)dy, L.cout}, TView<const T>{(const T*)x1, c1},
+                            c1, TView<const T>{(const T*)x2, c2}, c2, 0);
+    }
+    if (prec != NRV_PREC_BF16) return fail(NRV_ERR_UNSUPPORTED, "weight gradients in F32 or BF16");
+    // BF16: row-planar copies, as the backward pass keeps its tensors
+    using T = __nv_bfloat16;
+    const size_t rows = (size_t)n * h;
+    auto al = [](size_t bytes) { return (bytes + 255) / 256 * 256; };
+    const size_t bg = al(rows * w * L.cout * 2), b1 = al(rows * w * c1 * 2), b2 = al(rows * w * c2 * 2);
+    NRV_TRY(net->layer_ws.ensure(bg + b1 + b2));
+    char* ws = (char*)net->layer_ws.p;
+    T *pg = (T*)ws, *p1 = (T*)(ws + bg), *p2 = c2 ? (T*)(ws + bg + b1) : nullptr;
+    NRV_TRY(relayout(dy, pg, rows, w, L.cout, 2, true, s));
+    NRV_TRY(relayout(x1, p1, rows, w, c1, 2, true, s));
+    if (c2) NRV_TRY(relayout(x2, p2, rows, w, c2, 2, true, s));
+    Bwd<T> b{net, s, g, dgrad, {}, {}};
+    return b.wgrad_conv(l, TView<const T>{pg, L.cout, 1}, TView<const T>{p1, c1, 1}, c1,
+                        TView<const T>{p2, c2, 1}, c2, 0);
+}
+
+nrv_status net_layer_dgrad(Net* net, int l, const void* dy, const void* mask, int n, int h, int w,
+                           nrv_prec prec, void* dx, cudaStream_t s) {
+    const Layer& L = net->layers[l];
+    if (L.kind != CONV3 || l == L_E0A)
+        return fail(NRV_ERR_ARG, "layer %s has no data gradient here", L.name);
+    Geo g;
+    memset(&g, 0, sizeof(g));
+    g.n = n;
+    g.h[0] = h;
+    g.w[0] = w;
+    if (prec == NRV_PREC_F32) {
+        using T = float;
+        Bwd<T> b{net, s, g, nullptr, {}, {}};
+        return b.dgrad_conv(l, TView<const T>{(const T*)dy, L.cout}, TView<T>{(T*)dx, L.cin},
+                            TView<const T>{(const T*)mask, mask ? L.cin : 0}, 0);
+    }
+    if (prec != NRV_PREC_BF16) return fail(NRV_ERR_UNSUPPORTED, "data gradients in F32 or BF16");
+    using T = __nv_bfloat16;
+    const size_t rows = (size_t)n * h;
+    auto al = [](size_t bytes) { return (bytes + 255) / 256 * 256; };
+    const size_t bg = al(rows * w * L.cout * 2), bm = mask ? al(rows * w * L.cin * 2) : 0,
+                 bo = al(rows * w * L.cin * 2);
+    NRV_TRY(net->layer_ws.ensure(bg + bm + bo));
+    char* ws = (char*)net->layer_ws.p;
+    T *pg = (T*)ws, *pm = mask ? (T*)(ws + bg) : nullptr, *po = (T*)(ws + bg + bm);
+    NRV_TRY(relayout(dy, pg, rows, w, L.cout, 2, true, s));
+    if (mask) NRV_TRY(relayout(mask, pm, rows, w, L.cin, 2, true, s));
+    Bwd<T> b{net, s, g, nullptr, {}, {}};
+    NRV_TRY(b.dgrad_conv(l, TView<const T>{pg, L.cout, 1}, TView<T>{po, L.cin, 1},
+                         TView<const T>{pm, mask ? L.cin : 0, mask ? 1 : 0}, 0));
+    return relayout(po, dx, rows, w, L.cin, 2, false, s);
+}
 
 nrv_status net_backward(Net* net, const float* drgb, float* dparams, cudaStream_t s) {
     if (!net->saved) return fail(NRV_ERR_STATE, "backward without a preceding training forward");

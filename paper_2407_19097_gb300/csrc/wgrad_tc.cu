@@ -1,0 +1,253 @@
+// Weight gradient of a 3x3 convolution on the tensor cores (the backward pass of
+// Sec. 3.3's network, trained with Adam as in Sec. 4.1):
+//
+//   dW[o][c][tap] = sum over pixels p of  g[p][o] * x[p + shift(tap)][c]
+//
+// as a GEMM with M = output channel o (padded to the 128 lanes of TMEM), K = pixels and
+// N = (tap, c) for a group of 16 input channels: N = 9 x 16 = 144, so one MMA of K = 16
+// pixels serves all nine taps.  Both operands come straight from the row-planar BF16
+// layout ([row][plane][pixel][8 channels]), which is the MN-major no-swizzle operand
+// layout: a core matrix is 8 consecutive pixels (K) x 16 bytes (8 channels of M or N),
+// K-adjacent core matrices 128 bytes apart (LBO), MN-adjacent ones one 2 KB plane apart
+// (SBO).  A tile is 128 pixels x0..x0+127 of one row: its A block is the output gradient
+// (all C_out planes), its B block nine shifted copies of the group's two input planes --
+// rows y-1, y, y+1 at pixel offsets -1, 0, +1 -- loaded by TMA, so the nine taps are
+// nine consecutive N blocks and zero padding is TMA's out-of-bounds fill.
+//
+// Each CTA takes a channel group and a contiguous range of tiles (a split of K), sums
+// its MMAs in one TMEM accumulator and writes its partial dW; partials are added in a
+// fixed order afterwards (deterministic).  Warp 0 issues TMA into two stages, warp 1
+// owns TMEM and issues the MMAs, warps 2-5 read the accumulator at the end.  Waits are
+// bounded: on timeout the kernel sets STATUS_TIMEOUT, drains its copies, frees TMEM and
+// returns.
+#include "net.h"
+#include "tcgen05.cuh"
+
+namespace nrv {
+
+namespace {
+
+constexpr int WG_NT = 192;           // producer, MMA issuer, 4 epilogue warps
+constexpr int WG_PLANE = 2048;       // one plane of a 128-pixel tile
+constexpr int WG_N = 144;            // 9 taps x 16 channels
+constexpr uint32_t WG_B_BYTES = 9 * 2 * WG_PLANE;
+constexpr int WG_COLS = 256;         // TMEM columns allocated (>= WG_N)
+
+struct WgParams {
+    int n, h, w;
+    int tiles_x, ntiles;   // tiles of 128 pixels: t = (img * h + y) * tiles_x + xt
+    int nsplit;            // CTAs per channel group (blockIdx.x)
+    int cout, cin;         // channels of the output gradient and of the whole input
+    int groups1;           // channel groups that read source 1 (the rest read source 2)
+    uint32_t a_bytes;      // output-gradient block of a stage (C_out / 8 planes)
+    uint32_t stage_bytes;  // a_bytes + the nine input blocks
+    uint32_t idesc;
+    float* part;           // [split][o][tap][c]
+    unsigned* status;
+};
+
+__device__ __forceinline__ uint64_t wg_desc(uint32_t saddr) {
+    // start address, LBO = 128 bytes (K), SBO = one plane (M / N), version 1, no swizzle
+    const uint64_t lo = ((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16);
+    const uint64_t hi = (uint64_t)((WG_PLANE >> 4) | (1u << 14));
+    return lo | (hi << 32);
+}
+
+__global__ void __launch_bounds__(WG_NT, 1)
+    wgrad_tc_kernel(const __grid_constant__ CUtensorMap tg, const __grid_constant__ CUtensorMap t1,
+                    const __grid_constant__ CUtensorMap t2, const __grid_constant__ WgParams P) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t bars[5];
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t s0 = smem_u32(smem);
+    auto b_full = [&](int i) { return smem_u32(&bars[i]); };
+    auto b_empty = [&](int i) { return smem_u32(&bars[2 + i]); };
+    const uint32_t b_done = smem_u32(&bars[4]);
+
+    const int split = blockIdx.x, grp = blockIdx.y;
+    const int t_begin = (int)(((long long)split * P.ntiles) / P.nsplit);
+    const int t_end = (int)(((long long)(split + 1) * P.ntiles) / P.nsplit);
+    const CUtensorMap* tx = grp < P.groups1 ? &t1 : &t2;
+    const int plane0 = 2 * (grp < P.groups1 ? grp : grp - P.groups1);
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(b_full(i), 1);
+            mbar_init(b_empty(i), 1);
+        }
+        mbar_init(b_done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_slot)),
+                     "r"(WG_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int nloads = 0;
+            for (int t = t_begin, i = 0; t < t_end; ++t, ++i) {
+                const int st = i & 1;
+                if (!mbar_wait(b_empty(st), ((i >> 1) & 1) ^ 1u, &abort_flag, P.status)) break;
+                const int xt = t % P.tiles_x;
+                const int row = t / P.tiles_x;
+                const int y = row % P.h, img = row / P.h;
+                const int x0 = xt * 128;
+                const uint32_t sa = s0 + (uint32_t)st * P.stage_bytes;
+                const uint32_t sb = sa + P.a_bytes;
+                mbar_expect_tx(b_full(st), P.a_bytes + WG_B_BYTES);
+                tma_load_4d(sa, &tg, 2 * x0, 0, y, img, b_full(st));
+                for (int dy = 0; dy < 3; ++dy)
+                    for (int dx = 0; dx < 3; ++dx)
+                        tma_load_4d(sb + (uint32_t)(3 * dy + dx) * 2 * WG_PLANE, tx,
+                                    2 * (x0 - 1 + dx), plane0, y + dy - 1, img, b_full(st));
+                ++nloads;
+            }
+            // the last loads issued must land before the CTA may exit
+            const int last = nloads;
+            for (int i = last - 2 < 0 ? 0 : last - 2; i < last; ++i)
+                mbar_wait(b_full(i & 1), (i >> 1) & 1, &abort_flag, P.status, false);
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && t_end > t_begin) {
+            bool ok = true;
+            for (int t = t_begin, i = 0; ok && t < t_end; ++t, ++i) {
+                const int st = i & 1;
+                if (!mbar_wait(b_full(st), (i >> 1) & 1, &abort_flag, P.status)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sa = s0 + (uint32_t)st * P.stage_bytes;
+                const uint32_t sb = sa + P.a_bytes;
+#pragma unroll
+                for (int ks = 0; ks < 8; ++ks)   // 16 pixels per K-step
+                    mma_bf16(tmem, wg_desc(sa + 256u * ks), wg_desc(sb + 256u * ks), P.idesc,
+                             (i > 0 || ks > 0) ? 1u : 0u);
+                mma_commit(b_empty(st));
+            }
+            mma_commit(b_done);
+            mbar_wait(b_done, 0, &abort_flag, P.status, false);
+        }
+    } else {
+        // epilogue: TMEM lane o (warp quadrant q = warp % 4) holds dW[o][tap][16 channels]
+        const int q = warp & 3;
+        const int o = 32 * q + lane;
+        bool ok = true;
+        if (t_end > t_begin) {
+            int r = 1;
+            if (lane == 0) r = mbar_wait(b_done, 0, &abort_flag, P.status) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, r, 0) != 0;
+            tc_fence_after();
+        }
+        if (ok && 32 * q < P.cout) {
+            float* dst = P.part + ((size_t)split * P.cout + o) * 9 * P.cin + 16 * grp;
+            for (int tap = 0; tap < 9; ++tap) {
+                uint32_t v[16];
+                if (t_end > t_begin) {
+                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * tap), v);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = 0u;   // an empty split adds nothing
+                }
+                if (o < P.cout) {
+                    float4* d = reinterpret_cast<float4*>(dst + (size_t)tap * P.cin);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        d[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                           __uint_as_float(v[4 * j + 2]),
+                                           __uint_as_float(v[4 * j + 3]));
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(WG_COLS)
+                     : "memory");
+    }
+}
+
+}  // namespace
+
+nrv_status tc_wgrad(const Net* net, int l, const void* g, const void* x1, int c1, const void* x2,
+                    int c2, int n, int H, int W, float* part, size_t part_floats, int* nsplit,
+                    cudaStream_t s) {
+    const Layer& L = net->layers[l];
+    const int cin = c1 + c2;
+    if (L.kind != CONV3 || c1 % 16 || c2 % 16 || cin != L.cin || L.cout % 8 || L.cout > 128)
+        return fail(NRV_ERR_UNSUPPORTED, "tensor-core weight gradient: channel counts");
+    if (n <= 0 || H <= 0 || W <= 0) return fail(NRV_ERR_ARG, "empty tensor");
+    WgParams P;
+    memset(&P, 0, sizeof(P));
+    P.n = n;
+    P.h = H;
+    P.w = W;
+    P.tiles_x = (W + 127) / 128;
+    const long long ntiles = (long long)P.tiles_x * H * n;
+    if (ntiles > 0x3FFFFFFFll) return fail(NRV_ERR_UNSUPPORTED, "too many tiles");
+    P.ntiles = (int)ntiles;
+    P.cout = L.cout;
+    P.cin = cin;
+    P.groups1 = c1 / 16;
+    P.a_bytes = (uint32_t)(L.cout / 8) * WG_PLANE;
+    // the A descriptor spans 16 planes (M = 128) from its block: keep that inside the stage
+    P.stage_bytes = P.a_bytes + WG_B_BYTES;
+    if (P.stage_bytes < 16u * WG_PLANE) return fail(NRV_ERR_UNSUPPORTED, "stage too small");
+    // FP32 accumulator; A and B BF16, both MN-major; N = 144, M = 128
+    P.idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+              ((uint32_t)(WG_N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    P.status = status_word();
+    if (!P.status) return fail(NRV_ERR_CUDA, "status word unavailable");
+    const uint32_t smem = 2 * P.stage_bytes;
+    if (smem > 215 * 1024) return fail(NRV_ERR_UNSUPPORTED, "stages do not fit");
+    static bool attr = false;
+    if (!attr) {
+        NRV_CHECK_CUDA(cudaFuncSetAttribute(wgrad_tc_kernel,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, 215 * 1024));
+        attr = true;
+    }
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        NRV_CHECK_CUDA(cudaGetDevice(&dev));
+        NRV_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        if (sms <= 0) sms = 148;
+    }
+    const int groups = cin / 16;
+    const int per_sm = smem <= 110 * 1024 ? 2 : 1;   // TMEM: 256 columns each
+    long long ns = (long long)sms * per_sm / groups;
+    if (ns < 1) ns = 1;
+    if (ns > ntiles) ns = ntiles;
+    const size_t per_split = (size_t)L.cout * 9 * cin;
+    if ((size_t)ns * per_split > part_floats) ns = (long long)(part_floats / per_split);
+    if (ns < 1) return fail(NRV_ERR_ARG, "partial buffer too small");
+    P.nsplit = (int)ns;
+    P.part = part;
+    CUtensorMap mg, m1, m2;
+    NRV_TRY(tc_planar_map(&mg, g, n, H, W, L.cout / 8, L.cout / 8));
+    NRV_TRY(tc_planar_map(&m1, x1, n, H, W, c1 / 8, 2));
+    if (c2) NRV_TRY(tc_planar_map(&m2, x2, n, H, W, c2 / 8, 2));
+    else m2 = m1;
+    wgrad_tc_kernel<<<dim3((unsigned)ns, (unsigned)groups), WG_NT, smem, s>>>(mg, m1, m2, P);
+    NRV_CHECK_LAUNCH();
+    *nsplit = (int)ns;
+    return NRV_OK;
+}
+
+}  // namespace nrv

@@ -82,6 +82,8 @@ SIGNATURES = {
     "nrv_shade": (I, [P, P, I, I, I, I, P, P]),
     "nrv_net_layer_backend": (I, [P, I]),
     "nrv_net_run_layer": (I, [P, I, P, P, I, I, I, I, P, P]),
+    "nrv_net_layer_wgrad": (I, [P, I, P, P, P, I, I, I, I, P, P]),
+    "nrv_net_layer_dgrad": (I, [P, I, P, P, I, I, I, I, P, P]),
     "nrv_net_forward_train": (I, [P, P, I, I, I, I, P, P]),
     "nrv_net_backward": (I, [P, P, P, P]),
     "nrv_l1_loss": (I, [P, P, I64, P, P, P]),
@@ -250,6 +252,17 @@ class Net:
     def forward_train(self, netin, n, height, width, prec, rgb, stream=None):
         check(lib().nrv_net_forward_train(self.h, _ptr(netin), n, height, width, prec, _ptr(rgb),
                                           _stream(stream)))
+
+    def layer_wgrad(self, layer, dy, x1, x2, n, height, width, prec, grad, stream=None):
+        """Weight and bias gradient of 3x3 layer `layer` into its place in `grad`."""
+        check(lib().nrv_net_layer_wgrad(self.h, layer, _ptr(dy), _ptr(x1),
+                                        None if x2 is None else _ptr(x2), n, height, width, prec,
+                                        _ptr(grad), _stream(stream)))
+
+    def layer_dgrad(self, layer, dy, mask, n, height, width, prec, dx, stream=None):
+        """Data gradient of 3x3 layer `layer`, zeroed where `mask` <= 0 (if given)."""
+        check(lib().nrv_net_layer_dgrad(self.h, layer, _ptr(dy), None if mask is None else _ptr(mask),
+                                        n, height, width, prec, _ptr(dx), _stream(stream)))
 
     def backward(self, drgb, grad, stream=None):
         check(lib().nrv_net_backward(self.h, _ptr(drgb), _ptr(grad), _stream(stream)))
