@@ -284,19 +284,21 @@ nrv_status nrv_shade(nrv_net* net, const void* d_netin, int n, int height, int w
 nrv_status nrv_net_run_layer(nrv_net* net, int layer, const void* d_x1, const void* d_x2, int n,
                              int h, int w, nrv_prec prec, void* d_y, nrv_stream stream);
 
-/* Weight and bias gradient of one 3x3 convolution layer (Sec. 3.3's network; the
- * backward of nrv_net_backward, exposed so that it can be checked or reused alone):
- *   dW[o][c][u][v] = sum_p dy[p][o] * x[p + (u - 1, v - 1)][c]  (zero outside),
- *   db[o] = sum_p dy[p][o],
- * over all n*h*w pixels p.  d_dy: [n][h][w][C_out] (the gradient at the layer's
- * pre-activation output), d_x1: [n][h][w][c1], d_x2: [n][h][w][c2] for the
- * concatenating decoder layers (else NULL), all NHWC in `prec` (F32 or BF16; the
+/* Weight and bias gradient of one 3x3 or 2x2 stride-2 transposed convolution layer
+ * (Sec. 3.3's network; the backward of nrv_net_backward, exposed so that it can be
+ * checked or reused alone):
+ *   3x3:        dW[o][c][u][v] = sum_p dy[p][o] * x[p + (u - 1, v - 1)][c]  (zero outside),
+ *   transposed: dW[c][o][a][b] = sum_(i,j) x[i][j][c] * dy[2i + a][2j + b][o],
+ *   db[o] = sum of dy[.][o] over all output pixels.
+ * d_x1: [n][h][w][c1] and d_x2: [n][h][w][c2] for the concatenating decoder layers
+ * (else NULL); d_dy: [n][h][w][C_out] (3x3: the gradient at the layer's pre-activation
+ * output) or [n][2h][2w][C_out] (transposed); all NHWC in `prec` (F32 or BF16; the
  * first layer's input has the padded width of nrv_pack).  Writes dW (PyTorch
  * layout) and db into their places in d_grad (the flat parameter layout); other
  * entries are untouched.  BF16 runs on the tensor cores (FP32 accumulation, then a
  * fixed-order sum of partials: deterministic); F32 on the CUDA cores.  Uses the
  * net's workspaces (one call at a time per net).
- * Errors: NRV_ERR_ARG (null, misaligned, not a 3x3 layer, x2 given or missing),
+ * Errors: NRV_ERR_ARG (null, misaligned, the head, x2 given or missing),
  * NRV_ERR_UNSUPPORTED (FP8). */
 nrv_status nrv_net_layer_wgrad(nrv_net* net, int layer, const void* d_dy, const void* d_x1,
                                const void* d_x2, int n, int h, int w, nrv_prec prec,

@@ -109,6 +109,18 @@ nrv_status tc_repack_fp8(Net* net, cudaStream_t s);
 // box_planes planes of one row
 nrv_status tc_planar_map(CUtensorMap* map, const void* base, int n, int h, int w, int nch,
                          int box_planes);
+// TMA map of the pixels of one parity b of a row-planar tensor with `rows` rows (all images)
+// of w pixels (w even) and nch planes: 8-byte elements (half, parity, pixel pair, plane, row);
+// a box is 128 pixel pairs x box_planes planes of one row at one parity (tc.cu)
+nrv_status tc_parity_map(CUtensorMap* map, const void* base, int rows, int w, int nch,
+                         int box_planes);
+// Weight gradient of a 2x2 stride-2 transposed conv on the tensor cores (wgrad_tc.cu):
+// part[split][c][ab * C_out + o] over the input level (n, H, W); x at (H, W), g at (2H, 2W),
+// both BF16 row-planar; g holds g_ld channels of which C_out from channel g_off on (the
+// upsampled half of a concatenation's gradient).
+nrv_status tc_wgrad_up(const Net* net, int l, const void* g, int g_ld, int g_off, const void* x,
+                       int n, int H, int W, float* part, size_t part_floats, int* nsplit,
+                       cudaStream_t s);
 // Weight gradient of 3x3 conv layer l on the tensor cores (wgrad_tc.cu), BF16 row-planar:
 // part[split][o][tap][c] (FP32 partial sums over each split's pixels, c over all input channels)
 // for the output gradient g (C_out channels) and the layer input (x1: c1 channels, x2: c2 or

@@ -1149,6 +1149,26 @@ nrv_status tc_planar_map(CUtensorMap* map, const void* base, int n, int h, int w
     return make_planar_map(map, base, n, h, w, nch, box_planes);
 }
 
+nrv_status tc_parity_map(CUtensorMap* map, const void* base, int rows, int w, int nch,
+                         int box_planes) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return fail(NRV_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
+    if (((uintptr_t)base & 15) != 0) return fail(NRV_ERR_ARG, "tensor base not 16-byte aligned");
+    if ((w & 1) || nch < 1 || nch > 256 || box_planes < 1 || box_planes > nch)
+        return fail(NRV_ERR_UNSUPPORTED, "parity view shape");
+    // 8-byte elements: (half, parity, pixel pair, plane, row)
+    const cuuint64_t dims[5] = {2, 2, (cuuint64_t)w / 2, (cuuint64_t)nch, (cuuint64_t)rows};
+    const cuuint64_t row = (cuuint64_t)w * 16;
+    const cuuint64_t strides[4] = {16, 32, row, row * nch};
+    const cuuint32_t box[5] = {2, 1, TILE_M, (cuuint32_t)box_planes, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, const_cast<void*>(base), dims, strides,
+                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(NRV_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return NRV_OK;
+}
+
 nrv_status tc_upconv(const Net* net, int l, const void* x, void* y, const Geo& g, int level_in,
                      nrv_prec prec, cudaStream_t s, float inv_out) {
     if (prec != NRV_PREC_BF16 && prec != NRV_PREC_FP8)

@@ -533,8 +533,37 @@ struct Bwd {
         return NRV_OK;
     }
 
-    nrv_status upconv_bwd(int l, int xin, TView<const T> gout, TView<T> gx, int level_in) {
+    // weight and bias gradient of transposed conv l: x at level_in, gout one level up
+    nrv_status wgrad_up(int l, TView<const T> x, TView<const T> gout, int level_in) {
         const Layer& L = net->layers[l];
+        if (sizeof(T) == 2 && x.planar && !x.coff && x.ld == L.cin && gout.planar &&
+            gout.ld % 8 == 0 && gout.coff % 8 == 0 && gout.coff + L.cout <= gout.ld) {
+            // BF16: on the tensor cores, the bias gradient beside it
+            const int groups = 4 * L.cout <= 128 ? 1 : 2;
+            const size_t per_split = (size_t)L.cin * 4 * L.cout;
+            const size_t max_split = (size_t)(304 + groups - 1) / groups;
+            const int nb = 304;
+            NRV_TRY(net->partial.ensure((max_split * per_split + (size_t)nb * L.cout) * sizeof(float)));
+            float* part = (float*)net->partial.p;
+            float* partb = part + max_split * per_split;
+            int nsplit = 0;
+            const nrv_status st = tc_wgrad_up(net, l, gout.p, gout.ld, gout.coff, x.p, g.n,
+                                              g.h[level_in], g.w[level_in], part,
+                                              max_split * per_split, &nsplit, s);
+            if (st == NRV_OK) {
+                NRV_TRY(reduce_partials(part, nsplit, per_split, (int)per_split, 1, L.cout, L.cin,
+                                        L.cin, dparams + L.woff, s));
+                const int wo = 2 * g.w[level_in];
+                const size_t npx = (size_t)g.n * 2 * g.h[level_in] * wo;
+                const size_t chunk = (npx + nb - 1) / nb;
+                bias_grad_kernel<T><<<nb, 256, 0, s>>>(gout, L.cout, wo, npx, chunk, partb);
+                NRV_CHECK_LAUNCH();
+                return reduce_partials(partb, nb, L.cout, L.cout, 2, L.cout, L.cin, L.cin,
+                                       dparams + L.boff, s);
+            }
+            if (st != NRV_ERR_UNSUPPORTED) return st;
+            clear_error();
+        }
         const size_t npx = g.px(level_in);
         const int groups = L.cin / 16;
         size_t nch = (608 + groups - 1) / groups;
@@ -548,12 +577,18 @@ struct Bwd {
         float* part = (float*)net->partial.p;
         float* partb = part + nch * L.cin * K;
         wgrad_up_kernel<T><<<dim3((unsigned)nch, groups), 256, 0, s>>>(
-            CA(xin), L.cin, gout, L.cout, g.n, g.h[level_in], g.w[level_in], chunk, part, partb);
+            x, L.cin, gout, L.cout, g.n, g.h[level_in], g.w[level_in], chunk, part, partb);
         NRV_CHECK_LAUNCH();
         NRV_TRY(reduce_partials(part, (int)nch, (size_t)L.cin * K, L.cin * K, 1, L.cout, L.cin, L.cin,
                                 dparams + L.woff, s));
-        NRV_TRY(reduce_partials(partb, (int)nch, K, L.cout, 3, L.cout, L.cin, L.cin,
-                                dparams + L.boff, s));
+        return reduce_partials(partb, (int)nch, K, L.cout, 3, L.cout, L.cin, L.cin,
+                               dparams + L.boff, s);
+    }
+
+    nrv_status upconv_bwd(int l, int xin, TView<const T> gout, TView<T> gx, int level_in) {
+        const Layer& L = net->layers[l];
+        const size_t npx = g.px(level_in);
+        NRV_TRY(wgrad_up(l, CA(xin), gout, level_in));
         dim3 grid((unsigned)((npx + 127) / 128), L.cin / 16);
         upconv2_dgrad_kernel<T><<<grid, 128, (size_t)4 * 16 * L.cout * 4, s>>>(
             gout, L.cout, (const float*)net->wf32.p + net->wf_off[l], L.cin, CA(xin), gx, g.n,
@@ -654,7 +689,34 @@ void set_saved_input(const void* p) { g_saved_netin = p; }
 nrv_status net_layer_wgrad(Net* net, int l, const void* dy, const void* x1, const void* x2, int n,
                            int h, int w, nrv_prec prec, float* dgrad, cudaStream_t s) {
     const Layer& L = net->layers[l];
-    if (L.kind != CONV3) return fail(NRV_ERR_ARG, "layer %s is not a 3x3 convolution", L.name);
+    if (L.kind == UPCONV2) {
+        // transposed conv: x1 at (n, h, w), dy at (n, 2h, 2w)
+        if (x2) return fail(NRV_ERR_ARG, "layer %s: x2 must be NULL", L.name);
+        Geo g;
+        memset(&g, 0, sizeof(g));
+        g.n = n;
+        g.h[0] = h;
+        g.w[0] = w;
+        if (prec == NRV_PREC_F32) {
+            using T = float;
+            Bwd<T> b{net, s, g, dgrad, {}, {}};
+            return b.wgrad_up(l, TView<const T>{(const T*)x1, L.cin},
+                              TView<const T>{(const T*)dy, L.cout}, 0);
+        }
+        if (prec != NRV_PREC_BF16) return fail(NRV_ERR_UNSUPPORTED, "weight gradients in F32 or BF16");
+        using T = __nv_bfloat16;
+        const size_t rows = (size_t)n * h;
+        auto al = [](size_t bytes) { return (bytes + 255) / 256 * 256; };
+        const size_t bg = al(4 * rows * w * L.cout * 2), bx = al(rows * w * L.cin * 2);
+        NRV_TRY(net->layer_ws.ensure(bg + bx));
+        char* ws = (char*)net->layer_ws.p;
+        T *pg = (T*)ws, *px = (T*)(ws + bg);
+        NRV_TRY(relayout(dy, pg, 2 * rows, 2 * w, L.cout, 2, true, s));
+        NRV_TRY(relayout(x1, px, rows, w, L.cin, 2, true, s));
+        Bwd<T> b{net, s, g, dgrad, {}, {}};
+        return b.wgrad_up(l, TView<const T>{px, L.cin, 1}, TView<const T>{pg, L.cout, 1}, 0);
+    }
+    if (L.kind != CONV3) return fail(NRV_ERR_ARG, "layer %s has no weight gradient here", L.name);
     int c1 = l == L_E0A ? net->c0p : L.cin, c2 = 0;
     if (l == L_D2A || l == L_D1A || l == L_D0A) c1 = c2 = L.cin / 2;
     if ((c2 > 0) != (x2 != nullptr))

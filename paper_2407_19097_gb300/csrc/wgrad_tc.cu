@@ -14,6 +14,16 @@
 // rows y-1, y, y+1 at pixel offsets -1, 0, +1 -- loaded by TMA, so the nine taps are
 // nine consecutive N blocks and zero padding is TMA's out-of-bounds fill.
 //
+// The 2x2 stride-2 transposed conv's weight gradient,
+//
+//   dW[c][o][a][b] = sum over input pixels (i, j) of  x[i][j][c] * g[2i + a][2j + b][o],
+//
+// runs through the same kernel with the roles turned: M = (a, b, o) -- four kernel
+// positions of C_out channels, split over CTAs by a where 4 C_out > 128 -- K = input
+// pixels j of one row and N = C_in.  A 5-D TMA view of the output gradient (8-byte half,
+// pixel parity b, j, plane, row) loads the pixels of one parity as a dense tile, so each
+// (a, b) block is again an MN-major operand; the input row is the B block.
+//
 // Each CTA takes a channel group and a contiguous range of tiles (a split of K), sums
 // its MMAs in one TMEM accumulator and writes its partial dW; partials are added in a
 // fixed order afterwards (deterministic).  Warp 0 issues TMA into two stages, warp 1
@@ -34,11 +44,17 @@ constexpr uint32_t WG_B_BYTES = 9 * 2 * WG_PLANE;
 constexpr int WG_COLS = 256;         // TMEM columns allocated (>= WG_N)
 
 struct WgParams {
-    int n, h, w;
+    int mode;              // 0: 3x3 conv; 1: 2x2 stride-2 transposed conv
+    int n, h, w;           // input level geometry
     int tiles_x, ntiles;   // tiles of 128 pixels: t = (img * h + y) * tiles_x + xt
     int nsplit;            // CTAs per channel group (blockIdx.x)
     int cout, cin;         // channels of the output gradient and of the whole input
     int groups1;           // channel groups that read source 1 (the rest read source 2)
+    int n_ab;              // mode 1: kernel positions (a, b) per CTA (4, or 2 when split by a)
+    int g_plane0;          // mode 1: first plane of the output gradient's channels
+    int m_real;            // mode 1: A rows that hold data (n_ab * C_out)
+    int ncols;             // accumulator columns to read (144, or C_in)
+    uint32_t b_bytes;      // B block of a stage
     uint32_t a_bytes;      // output-gradient block of a stage (C_out / 8 planes)
     uint32_t stage_bytes;  // a_bytes + the nine input blocks
     uint32_t idesc;
@@ -72,6 +88,7 @@ __global__ void __launch_bounds__(WG_NT, 1)
     const int t_end = (int)(((long long)(split + 1) * P.ntiles) / P.nsplit);
     const CUtensorMap* tx = grp < P.groups1 ? &t1 : &t2;
     const int plane0 = 2 * (grp < P.groups1 ? grp : grp - P.groups1);
+    const int ab0 = grp * P.n_ab;   // mode 1: first kernel position of this CTA
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
@@ -107,12 +124,23 @@ __global__ void __launch_bounds__(WG_NT, 1)
                 const int x0 = xt * 128;
                 const uint32_t sa = s0 + (uint32_t)st * P.stage_bytes;
                 const uint32_t sb = sa + P.a_bytes;
-                mbar_expect_tx(b_full(st), P.a_bytes + WG_B_BYTES);
-                tma_load_4d(sa, &tg, 2 * x0, 0, y, img, b_full(st));
-                for (int dy = 0; dy < 3; ++dy)
-                    for (int dx = 0; dx < 3; ++dx)
-                        tma_load_4d(sb + (uint32_t)(3 * dy + dx) * 2 * WG_PLANE, tx,
-                                    2 * (x0 - 1 + dx), plane0, y + dy - 1, img, b_full(st));
+                mbar_expect_tx(b_full(st), P.a_bytes + P.b_bytes);
+                if (P.mode == 0) {
+                    tma_load_4d(sa, &tg, 2 * x0, 0, y, img, b_full(st));
+                    for (int dy = 0; dy < 3; ++dy)
+                        for (int dx = 0; dx < 3; ++dx)
+                            tma_load_4d(sb + (uint32_t)(3 * dy + dx) * 2 * WG_PLANE, tx,
+                                        2 * (x0 - 1 + dx), plane0, y + dy - 1, img, b_full(st));
+                } else {
+                    // kernel position (a, b): output row 2y + a, output pixels 2j + b
+                    const uint32_t ab_bytes = P.a_bytes / (uint32_t)P.n_ab;
+                    for (int k = 0; k < P.n_ab; ++k) {
+                        const int ab = ab0 + k;
+                        tma_load_5d(sa + (uint32_t)k * ab_bytes, &tg, 0, ab & 1, x0, P.g_plane0,
+                                    (img * P.h + y) * 2 + (ab >> 1), b_full(st));
+                    }
+                    tma_load_4d(sb, &t1, 2 * x0, 0, y, img, b_full(st));
+                }
                 ++nloads;
             }
             // the last loads issued must land before the CTA may exit
@@ -152,7 +180,25 @@ __global__ void __launch_bounds__(WG_NT, 1)
             ok = __shfl_sync(0xffffffffu, r, 0) != 0;
             tc_fence_after();
         }
-        if (ok && 32 * q < P.cout) {
+        if (ok && P.mode == 1 && 32 * q < P.m_real) {
+            // row m = (ab - ab0) * C_out + o; column c -> part[split][c][ab * C_out + o]
+            const int k4 = 4 * P.cout;
+            float* dst = P.part + (size_t)split * P.cin * k4 + ab0 * P.cout + o;
+            for (int c0 = 0; c0 < P.ncols; c0 += 16) {
+                uint32_t v[16];
+                if (t_end > t_begin) {
+                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = 0u;
+                }
+                if (o < P.m_real) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) dst[(size_t)(c0 + j) * k4] = __uint_as_float(v[j]);
+                }
+            }
+        }
+        if (ok && P.mode == 0 && 32 * q < P.cout) {
             float* dst = P.part + ((size_t)split * P.cout + o) * 9 * P.cin + 16 * grp;
             for (int tap = 0; tap < 9; ++tap) {
                 uint32_t v[16];
@@ -185,35 +231,15 @@ __global__ void __launch_bounds__(WG_NT, 1)
 
 }  // namespace
 
-nrv_status tc_wgrad(const Net* net, int l, const void* g, const void* x1, int c1, const void* x2,
-                    int c2, int n, int H, int W, float* part, size_t part_floats, int* nsplit,
-                    cudaStream_t s) {
-    const Layer& L = net->layers[l];
-    const int cin = c1 + c2;
-    if (L.kind != CONV3 || c1 % 16 || c2 % 16 || cin != L.cin || L.cout % 8 || L.cout > 128)
-        return fail(NRV_ERR_UNSUPPORTED, "tensor-core weight gradient: channel counts");
-    if (n <= 0 || H <= 0 || W <= 0) return fail(NRV_ERR_ARG, "empty tensor");
-    WgParams P;
-    memset(&P, 0, sizeof(P));
-    P.n = n;
-    P.h = H;
-    P.w = W;
-    P.tiles_x = (W + 127) / 128;
-    const long long ntiles = (long long)P.tiles_x * H * n;
-    if (ntiles > 0x3FFFFFFFll) return fail(NRV_ERR_UNSUPPORTED, "too many tiles");
-    P.ntiles = (int)ntiles;
-    P.cout = L.cout;
-    P.cin = cin;
-    P.groups1 = c1 / 16;
-    P.a_bytes = (uint32_t)(L.cout / 8) * WG_PLANE;
-    // the A descriptor spans 16 planes (M = 128) from its block: keep that inside the stage
-    P.stage_bytes = P.a_bytes + WG_B_BYTES;
-    if (P.stage_bytes < 16u * WG_PLANE) return fail(NRV_ERR_UNSUPPORTED, "stage too small");
-    // FP32 accumulator; A and B BF16, both MN-major; N = 144, M = 128
-    P.idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
-              ((uint32_t)(WG_N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// Launch: grid (splits, groups), two stages of (A block, B block), partials in `part`.
+static nrv_status wg_launch(WgParams& P, int groups, const CUtensorMap& mg, const CUtensorMap& m1,
+                            const CUtensorMap& m2, size_t per_split, float* part,
+                            size_t part_floats, int* nsplit, cudaStream_t s) {
     P.status = status_word();
     if (!P.status) return fail(NRV_ERR_CUDA, "status word unavailable");
+    // the A descriptor spans 16 planes (M = 128) from its block: keep that inside the stage
+    P.stage_bytes = P.a_bytes + P.b_bytes;
+    if (P.stage_bytes < 16u * WG_PLANE) P.stage_bytes = 16u * WG_PLANE;
     const uint32_t smem = 2 * P.stage_bytes;
     if (smem > 215 * 1024) return fail(NRV_ERR_UNSUPPORTED, "stages do not fit");
     static bool attr = false;
@@ -229,25 +255,94 @@ nrv_status tc_wgrad(const Net* net, int l, const void* g, const void* x1, int c1
         NRV_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         if (sms <= 0) sms = 148;
     }
-    const int groups = cin / 16;
     const int per_sm = smem <= 110 * 1024 ? 2 : 1;   // TMEM: 256 columns each
     long long ns = (long long)sms * per_sm / groups;
     if (ns < 1) ns = 1;
-    if (ns > ntiles) ns = ntiles;
-    const size_t per_split = (size_t)L.cout * 9 * cin;
+    if (ns > P.ntiles) ns = P.ntiles;
     if ((size_t)ns * per_split > part_floats) ns = (long long)(part_floats / per_split);
     if (ns < 1) return fail(NRV_ERR_ARG, "partial buffer too small");
     P.nsplit = (int)ns;
     P.part = part;
+    wgrad_tc_kernel<<<dim3((unsigned)ns, (unsigned)groups), WG_NT, smem, s>>>(mg, m1, m2, P);
+    NRV_CHECK_LAUNCH();
+    *nsplit = (int)ns;
+    return NRV_OK;
+}
+
+static nrv_status wg_geometry(WgParams& P, int n, int H, int W) {
+    if (n <= 0 || H <= 0 || W <= 0) return fail(NRV_ERR_ARG, "empty tensor");
+    P.n = n;
+    P.h = H;
+    P.w = W;
+    P.tiles_x = (W + 127) / 128;
+    const long long ntiles = (long long)P.tiles_x * H * n;
+    if (ntiles > 0x3FFFFFFFll) return fail(NRV_ERR_UNSUPPORTED, "too many tiles");
+    P.ntiles = (int)ntiles;
+    return NRV_OK;
+}
+
+// instruction descriptor: FP32 accumulator, A and B BF16 MN-major, M = 128
+static uint32_t wg_idesc(int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+nrv_status tc_wgrad(const Net* net, int l, const void* g, const void* x1, int c1, const void* x2,
+                    int c2, int n, int H, int W, float* part, size_t part_floats, int* nsplit,
+                    cudaStream_t s) {
+    const Layer& L = net->layers[l];
+    const int cin = c1 + c2;
+    if (L.kind != CONV3 || c1 % 16 || c2 % 16 || cin != L.cin || L.cout % 8 || L.cout > 128)
+        return fail(NRV_ERR_UNSUPPORTED, "tensor-core weight gradient: channel counts");
+    WgParams P;
+    memset(&P, 0, sizeof(P));
+    P.mode = 0;
+    NRV_TRY(wg_geometry(P, n, H, W));
+    P.cout = L.cout;
+    P.cin = cin;
+    P.groups1 = c1 / 16;
+    P.n_ab = 1;
+    P.m_real = L.cout;
+    P.ncols = WG_N;
+    P.a_bytes = (uint32_t)(L.cout / 8) * WG_PLANE;
+    P.b_bytes = WG_B_BYTES;
+    P.idesc = wg_idesc(WG_N);
     CUtensorMap mg, m1, m2;
     NRV_TRY(tc_planar_map(&mg, g, n, H, W, L.cout / 8, L.cout / 8));
     NRV_TRY(tc_planar_map(&m1, x1, n, H, W, c1 / 8, 2));
     if (c2) NRV_TRY(tc_planar_map(&m2, x2, n, H, W, c2 / 8, 2));
     else m2 = m1;
-    wgrad_tc_kernel<<<dim3((unsigned)ns, (unsigned)groups), WG_NT, smem, s>>>(mg, m1, m2, P);
-    NRV_CHECK_LAUNCH();
-    *nsplit = (int)ns;
-    return NRV_OK;
+    return wg_launch(P, cin / 16, mg, m1, m2, (size_t)L.cout * 9 * cin, part, part_floats, nsplit, s);
+}
+
+nrv_status tc_wgrad_up(const Net* net, int l, const void* g, int g_ld, int g_off, const void* x,
+                       int n, int H, int W, float* part, size_t part_floats, int* nsplit,
+                       cudaStream_t s) {
+    const Layer& L = net->layers[l];
+    if (L.kind != UPCONV2 || L.cin % 16 || L.cin > 256 || L.cout % 8 || L.cout > 64 || g_ld % 8 ||
+        g_off % 8 || g_off + L.cout > g_ld)
+        return fail(NRV_ERR_UNSUPPORTED, "tensor-core weight gradient: channel counts");
+    WgParams P;
+    memset(&P, 0, sizeof(P));
+    P.mode = 1;
+    NRV_TRY(wg_geometry(P, n, H, W));
+    P.cout = L.cout;
+    P.cin = L.cin;
+    P.groups1 = 0;
+    // kernel positions per CTA: all four while 4 C_out rows fit in M = 128, else split by a
+    const int groups = 4 * L.cout <= 128 ? 1 : 2;
+    P.n_ab = 4 / groups;
+    P.m_real = P.n_ab * L.cout;
+    P.ncols = L.cin;
+    P.a_bytes = (uint32_t)P.n_ab * (L.cout / 8) * WG_PLANE;
+    P.b_bytes = (uint32_t)(L.cin / 8) * WG_PLANE;
+    P.idesc = wg_idesc(L.cin);
+    CUtensorMap mg, m1;
+    P.g_plane0 = g_off / 8;
+    NRV_TRY(tc_parity_map(&mg, g, n * 2 * H, 2 * W, g_ld / 8, L.cout / 8));
+    NRV_TRY(tc_planar_map(&m1, x, n, H, W, L.cin / 8, L.cin / 8));
+    return wg_launch(P, groups, mg, m1, m1, (size_t)L.cin * 4 * L.cout, part, part_floats, nsplit,
+                     s);
 }
 
 }  // namespace nrv

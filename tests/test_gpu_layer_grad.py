@@ -139,3 +139,45 @@ def test_layer_dgrad(layer, name, masked, prec):
     else:
         err = np.abs(got - ref).max() / max(1.0, np.abs(ref).max())
         assert err <= 1e-5, err
+
+
+UPCONV = [(i, name) for i, (name, kind, _, _) in enumerate(unet.layers(C0)) if kind == "convT2"]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("layer,name", UPCONV)
+def test_upconv_wgrad(layer, name, prec):
+    """Transposed conv weight and bias gradients (BF16: tensor cores with a parity view of the
+    output gradient; F32: CUDA cores) against the oracle's convT2_bwd on the same values, within
+    the FP32 summation bound.  Input 300 wide (three 128-pixel tiles, ragged) and enough rows
+    that each K-split sums several tiles."""
+    import torch
+    from paper_2407_19097_gb300 import nrv
+    net = nrv.Net(C0)
+    net.set_params(torch.from_numpy(make_params(C0, seed=9)).to(torch_dev()))
+    _, _, ci, co = unet.layers(C0)[layer]
+    n, h, w = 2, 100, 300
+    rng = np.random.default_rng(300 + layer)
+    x = rng.standard_normal((n, h, w, ci)).astype(np.float32)
+    dy = (rng.standard_normal((n, 2 * h, 2 * w, co)) * 0.1).astype(np.float32)
+    dt = torch.bfloat16 if prec == 1 else torch.float32
+    xt = torch.from_numpy(x).to(torch_dev()).to(dt).contiguous()
+    dyt = torch.from_numpy(dy).to(torch_dev()).to(dt).contiguous()
+    off, total = _offsets(C0)
+    grad = torch.full((total,), float("nan"), device=torch_dev())
+    net.layer_wgrad(layer, dyt, xt, None, n, h, w, prec, grad)
+    torch.cuda.synchronize()
+    g = grad.cpu().numpy().astype(np.float64)
+    xv = _bf16(x) if prec == 1 else x.astype(np.float64)
+    dv = _bf16(dy) if prec == 1 else dy.astype(np.float64)
+    wz = np.zeros(unet.weight_shape("convT2", ci, co))
+    _, dw_ref, db_ref = unet.convT2_bwd(xv, wz, dv)
+    _, dw_abs, db_abs = unet.convT2_bwd(np.abs(xv), wz, np.abs(dv))
+    o, wsz, ob, _ = off[name]
+    dw = g[o:o + wsz].reshape(dw_ref.shape)
+    db = g[ob:ob + co]
+    assert np.all(np.isfinite(dw)) and np.all(np.isfinite(db))
+    assert np.all(np.abs(dw - dw_ref) <= 1e-5 * dw_abs + 1e-30), float(np.abs(dw - dw_ref).max())
+    assert np.all(np.abs(db - db_ref) <= 1e-5 * db_abs + 1e-30), float(np.abs(db - db_ref).max())
+    rest = np.concatenate([g[:o], g[ob + co:]])
+    assert np.all(np.isnan(rest))
