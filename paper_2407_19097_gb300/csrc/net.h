@@ -119,16 +119,17 @@ nrv_status tc_parity_map(CUtensorMap* map, const void* base, int rows, int w, in
 // both BF16 row-planar; g holds g_ld channels of which C_out from channel g_off on (the
 // upsampled half of a concatenation's gradient).
 nrv_status tc_wgrad_up(const Net* net, int l, const void* g, int g_ld, int g_off, const void* x,
-                       int n, int H, int W, float* part, size_t part_floats, int* nsplit,
-                       cudaStream_t s);
+                       int n, int H, int W, float* part, size_t part_floats, float* partb,
+                       int* nsplit, cudaStream_t s);
 // Weight gradient of 3x3 conv layer l on the tensor cores (wgrad_tc.cu), BF16 row-planar:
 // part[split][o][tap][c] (FP32 partial sums over each split's pixels, c over all input channels)
 // for the output gradient g (C_out channels) and the layer input (x1: c1 channels, x2: c2 or
-// none); *nsplit receives the number of splits.  NRV_ERR_UNSUPPORTED when the shape is not
-// covered (input channels not a multiple of 16).
+// none), and partb[split][o] (bias; the transposed conv: partb[split][ab * C_out + o]);
+// *nsplit receives the number of splits.  NRV_ERR_UNSUPPORTED when the shape is not covered
+// (input channels not a multiple of 16, except one group of 8).
 nrv_status tc_wgrad(const Net* net, int l, const void* g, const void* x1, int c1, const void* x2,
-                    int c2, int n, int H, int W, float* part, size_t part_floats, int* nsplit,
-                    cudaStream_t s);
+                    int c2, int n, int H, int W, float* part, size_t part_floats, float* partb,
+                    int* nsplit, cudaStream_t s);
 // data gradient of 3x3 conv layer l on the tensor cores (BF16, row-planar): out = conv3x3 of
 // the output gradient gin with the flipped, transposed kernel, zeroed where mask <= 0 (mask
 // may be null); NRV_ERR_UNSUPPORTED when the layer has no such path

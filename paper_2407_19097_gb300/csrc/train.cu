@@ -241,37 +241,6 @@ __global__ void head_dgrad_kernel(const float* drgb, const float* w, TView<const
     }
 }
 
-// partb[blk][o] = sum of g[p][o] over the block's run of pixels p (the bias gradient of a
-// 3x3 conv): one plane of 8 channels at a time, thread i taking pixels i, i + 256, ...,
-// then a fixed-order tree over the threads.
-template <typename T>
-__global__ void __launch_bounds__(256) bias_grad_kernel(TView<const T> g, int cout, int w,
-                                                        size_t npx, size_t chunk, float* partb) {
-    __shared__ float red[256][9];
-    const size_t p0 = blockIdx.x * chunk, p1 = p0 + chunk < npx ? p0 + chunk : npx;
-    for (int c0 = 0; c0 < cout; c0 += 8) {
-        float acc[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        for (size_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-            float v[8];
-            ld8<T>(g.at(p / w, (int)(p % w), c0, w), v);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) acc[k] += v[k];
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) red[threadIdx.x][k] = acc[k];
-        __syncthreads();
-        for (int st = 128; st > 0; st >>= 1) {
-            if ((int)threadIdx.x < st) {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) red[threadIdx.x][k] += red[threadIdx.x + st][k];
-            }
-            __syncthreads();
-        }
-        if (threadIdx.x < 8) partb[(size_t)blockIdx.x * cout + c0 + threadIdx.x] = red[0][threadIdx.x];
-        __syncthreads();
-    }
-}
-
 // part[blk][o*16 + c] = sum drgb[o] * x[c]; part[blk][48 + o] = sum drgb[o], over the block's
 // chunk of cropped pixels: every thread keeps all 51 sums, then the block adds them (warp
 // shuffles, then the 8 warps in order).
@@ -442,22 +411,17 @@ struct Bwd {
                 const int groups = cin / 16 > 0 ? cin / 16 : 1;
                 const size_t per_split = (size_t)L.cout * 9 * cin;
                 const size_t max_split = (size_t)(304 + groups - 1) / groups;
-                const int nb = 304;
-                NRV_TRY(net->partial.ensure((max_split * per_split + (size_t)nb * L.cout) * sizeof(float)));
+                NRV_TRY(net->partial.ensure((max_split * (per_split + L.cout)) * sizeof(float)));
                 float* part = (float*)net->partial.p;
                 float* partb = part + max_split * per_split;
                 int nsplit = 0;
                 const nrv_status st = tc_wgrad(net, l, gpre.p, x1.p, c1, c2 ? x2.p : nullptr, c2, g.n,
                                                g.h[level], g.w[level], part, max_split * per_split,
-                                               &nsplit, s);
+                                               partb, &nsplit, s);
                 if (st == NRV_OK) {
                     NRV_TRY(reduce_partials(part, nsplit, per_split, (int)per_split, 0, L.cout, cin,
                                             L.cin, dparams + L.woff, s));
-                    const size_t npx = g.px(level);
-                    const size_t chunk = (npx + nb - 1) / nb;
-                    bias_grad_kernel<T><<<nb, 256, 0, s>>>(gpre, L.cout, g.w[level], npx, chunk, partb);
-                    NRV_CHECK_LAUNCH();
-                    return reduce_partials(partb, nb, L.cout, L.cout, 2, L.cout, cin, L.cin,
+                    return reduce_partials(partb, nsplit, L.cout, L.cout, 2, L.cout, cin, L.cin,
                                            dparams + L.boff, s);
                 }
                 if (st != NRV_ERR_UNSUPPORTED) return st;
@@ -542,23 +506,18 @@ struct Bwd {
             const int groups = 4 * L.cout <= 128 ? 1 : 2;
             const size_t per_split = (size_t)L.cin * 4 * L.cout;
             const size_t max_split = (size_t)(304 + groups - 1) / groups;
-            const int nb = 304;
-            NRV_TRY(net->partial.ensure((max_split * per_split + (size_t)nb * L.cout) * sizeof(float)));
+            NRV_TRY(net->partial.ensure((max_split * (per_split + 4 * L.cout)) * sizeof(float)));
             float* part = (float*)net->partial.p;
             float* partb = part + max_split * per_split;
             int nsplit = 0;
             const nrv_status st = tc_wgrad_up(net, l, gout.p, gout.ld, gout.coff, x.p, g.n,
                                               g.h[level_in], g.w[level_in], part,
-                                              max_split * per_split, &nsplit, s);
+                                              max_split * per_split, partb, &nsplit, s);
             if (st == NRV_OK) {
                 NRV_TRY(reduce_partials(part, nsplit, per_split, (int)per_split, 1, L.cout, L.cin,
                                         L.cin, dparams + L.woff, s));
-                const int wo = 2 * g.w[level_in];
-                const size_t npx = (size_t)g.n * 2 * g.h[level_in] * wo;
-                const size_t chunk = (npx + nb - 1) / nb;
-                bias_grad_kernel<T><<<nb, 256, 0, s>>>(gout, L.cout, wo, npx, chunk, partb);
-                NRV_CHECK_LAUNCH();
-                return reduce_partials(partb, nb, L.cout, L.cout, 2, L.cout, L.cin, L.cin,
+                // per split: the four kernel positions' sums of each channel
+                return reduce_partials(partb, nsplit, 4 * L.cout, L.cout, 3, L.cout, L.cin, L.cin,
                                        dparams + L.boff, s);
             }
             if (st != NRV_ERR_UNSUPPORTED) return st;

@@ -24,6 +24,9 @@
 // pixel parity b, j, plane, row) loads the pixels of one parity as a dense tile, so each
 // (a, b) block is again an MN-major operand; the input row is the B block.
 //
+// The bias gradient comes out of the same MMAs: two constant planes of BF16 ones follow
+// each B block, so 16 more accumulator columns hold sum_p g[p][row].
+//
 // Each CTA takes a channel group and a contiguous range of tiles (a split of K), sums
 // its MMAs in one TMEM accumulator and writes its partial dW; partials are added in a
 // fixed order afterwards (deterministic).  Warp 0 issues TMA into two stages, warp 1
@@ -41,6 +44,7 @@ constexpr int WG_NT = 192;           // producer, MMA issuer, 4 epilogue warps
 constexpr int WG_PLANE = 2048;       // one plane of a 128-pixel tile
 constexpr int WG_N = 144;            // 9 taps x 16 channels
 constexpr uint32_t WG_B_BYTES = 9 * 2 * WG_PLANE;
+constexpr uint32_t WG_ONES = 2 * WG_PLANE;   // two planes of ones after each B block
 constexpr int WG_COLS = 256;         // TMEM columns allocated (>= WG_N)
 
 struct WgParams {
@@ -53,12 +57,16 @@ struct WgParams {
     int n_ab;              // mode 1: kernel positions (a, b) per CTA (4, or 2 when split by a)
     int g_plane0;          // mode 1: first plane of the output gradient's channels
     int m_real;            // mode 1: A rows that hold data (n_ab * C_out)
-    int ncols;             // accumulator columns to read (144, or C_in)
-    uint32_t b_bytes;      // B block of a stage
+    int ncols;             // weight columns of the accumulator (144, or C_in); the bias
+                           // column follows
+    int b_planes;          // mode 0: planes per tap loaded (2, or 1 for an 8-channel input)
+    uint32_t b_bytes;      // bytes TMA brings into the B block per stage
+    uint32_t b_bytes_span; // B block size in shared memory (the ones planes follow it)
     uint32_t a_bytes;      // output-gradient block of a stage (C_out / 8 planes)
     uint32_t stage_bytes;  // a_bytes + the nine input blocks
     uint32_t idesc;
-    float* part;           // [split][o][tap][c]
+    float* part;           // [split][o][tap][c] (mode 0) or [split][c][ab * C_out + o]
+    float* partb;          // bias: [split][o] (mode 0) or [split][ab * C_out + o]
     unsigned* status;
 };
 
@@ -87,7 +95,7 @@ __global__ void __launch_bounds__(WG_NT, 1)
     const int t_begin = (int)(((long long)split * P.ntiles) / P.nsplit);
     const int t_end = (int)(((long long)(split + 1) * P.ntiles) / P.nsplit);
     const CUtensorMap* tx = grp < P.groups1 ? &t1 : &t2;
-    const int plane0 = 2 * (grp < P.groups1 ? grp : grp - P.groups1);
+    const int plane0 = P.b_planes * (grp < P.groups1 ? grp : grp - P.groups1);   // in its source
     const int ab0 = grp * P.n_ab;   // mode 1: first kernel position of this CTA
 
     if (threadIdx.x == 0) {
@@ -98,6 +106,23 @@ __global__ void __launch_bounds__(WG_NT, 1)
         }
         mbar_init(b_done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    {
+        // constant parts of both stages: the ones planes (BF16 1.0), and for a one-plane
+        // input the unused second plane of every tap (zero)
+        const uint4 one = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+        for (int st = 0; st < 2; ++st) {
+            uint8_t* b = smem + (size_t)st * P.stage_bytes + P.a_bytes;
+            uint4* ones = reinterpret_cast<uint4*>(b + P.b_bytes_span);
+            for (int i = threadIdx.x; i < (int)(WG_ONES / 16); i += WG_NT) ones[i] = one;
+            if (P.mode == 0 && P.b_planes == 1)
+                for (int i = threadIdx.x; i < 9 * WG_PLANE / 16; i += WG_NT) {
+                    const int tap = i / (WG_PLANE / 16), r = i % (WG_PLANE / 16);
+                    reinterpret_cast<uint4*>(b + (size_t)tap * 2 * WG_PLANE + WG_PLANE)[r] =
+                        make_uint4(0u, 0u, 0u, 0u);
+                }
+        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
@@ -197,9 +222,18 @@ __global__ void __launch_bounds__(WG_NT, 1)
                     for (int j = 0; j < 16; ++j) dst[(size_t)(c0 + j) * k4] = __uint_as_float(v[j]);
                 }
             }
+            // bias column: sum of the output gradient at this row's kernel position
+            uint32_t v[16];
+            if (t_end > t_begin) {
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)P.ncols, v);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = 0u;
+            }
+            if (o < P.m_real) P.partb[(size_t)split * k4 + ab0 * P.cout + o] = __uint_as_float(v[0]);
         }
         if (ok && P.mode == 0 && 32 * q < P.cout) {
-            float* dst = P.part + ((size_t)split * P.cout + o) * 9 * P.cin + 16 * grp;
+            float* dst = P.part + ((size_t)split * P.cout + o) * 9 * P.cin + 8 * P.b_planes * grp;
             for (int tap = 0; tap < 9; ++tap) {
                 uint32_t v[16];
                 if (t_end > t_begin) {
@@ -209,13 +243,25 @@ __global__ void __launch_bounds__(WG_NT, 1)
                     for (int j = 0; j < 16; ++j) v[j] = 0u;   // an empty split adds nothing
                 }
                 if (o < P.cout) {
+                    // 16 channels of the group (8 with a one-plane input)
                     float4* d = reinterpret_cast<float4*>(dst + (size_t)tap * P.cin);
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
-                        d[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                        if (j < 2 * P.b_planes) d[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
                                            __uint_as_float(v[4 * j + 2]),
                                            __uint_as_float(v[4 * j + 3]));
                 }
+            }
+            if (grp == 0) {
+                // bias column (every channel group computes it; the first one writes it)
+                uint32_t v[16];
+                if (t_end > t_begin) {
+                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)P.ncols, v);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = 0u;
+                }
+                if (o < P.cout) P.partb[(size_t)split * P.cout + o] = __uint_as_float(v[0]);
             }
         }
     }
@@ -234,11 +280,11 @@ __global__ void __launch_bounds__(WG_NT, 1)
 // Launch: grid (splits, groups), two stages of (A block, B block), partials in `part`.
 static nrv_status wg_launch(WgParams& P, int groups, const CUtensorMap& mg, const CUtensorMap& m1,
                             const CUtensorMap& m2, size_t per_split, float* part,
-                            size_t part_floats, int* nsplit, cudaStream_t s) {
+                            size_t part_floats, float* partb, int* nsplit, cudaStream_t s) {
     P.status = status_word();
     if (!P.status) return fail(NRV_ERR_CUDA, "status word unavailable");
     // the A descriptor spans 16 planes (M = 128) from its block: keep that inside the stage
-    P.stage_bytes = P.a_bytes + P.b_bytes;
+    P.stage_bytes = P.a_bytes + P.b_bytes_span + WG_ONES;
     if (P.stage_bytes < 16u * WG_PLANE) P.stage_bytes = 16u * WG_PLANE;
     const uint32_t smem = 2 * P.stage_bytes;
     if (smem > 215 * 1024) return fail(NRV_ERR_UNSUPPORTED, "stages do not fit");
@@ -263,6 +309,7 @@ static nrv_status wg_launch(WgParams& P, int groups, const CUtensorMap& mg, cons
     if (ns < 1) return fail(NRV_ERR_ARG, "partial buffer too small");
     P.nsplit = (int)ns;
     P.part = part;
+    P.partb = partb;
     wgrad_tc_kernel<<<dim3((unsigned)ns, (unsigned)groups), WG_NT, smem, s>>>(mg, m1, m2, P);
     NRV_CHECK_LAUNCH();
     *nsplit = (int)ns;
@@ -288,11 +335,13 @@ static uint32_t wg_idesc(int N) {
 }
 
 nrv_status tc_wgrad(const Net* net, int l, const void* g, const void* x1, int c1, const void* x2,
-                    int c2, int n, int H, int W, float* part, size_t part_floats, int* nsplit,
-                    cudaStream_t s) {
+                    int c2, int n, int H, int W, float* part, size_t part_floats, float* partb,
+                    int* nsplit, cudaStream_t s) {
     const Layer& L = net->layers[l];
     const int cin = c1 + c2;
-    if (L.kind != CONV3 || c1 % 16 || c2 % 16 || cin != L.cin || L.cout % 8 || L.cout > 128)
+    // channel groups of 16 (two planes per tap), or one group of 8 (the packed input)
+    const int bp = (c1 % 16 == 0 && c2 % 16 == 0) ? 2 : (c1 == 8 && c2 == 0 ? 1 : 0);
+    if (L.kind != CONV3 || !bp || L.cout % 8 || L.cout > 128 || (bp == 2 && cin != L.cin))
         return fail(NRV_ERR_UNSUPPORTED, "tensor-core weight gradient: channel counts");
     WgParams P;
     memset(&P, 0, sizeof(P));
@@ -300,26 +349,29 @@ nrv_status tc_wgrad(const Net* net, int l, const void* g, const void* x1, int c1
     NRV_TRY(wg_geometry(P, n, H, W));
     P.cout = L.cout;
     P.cin = cin;
-    P.groups1 = c1 / 16;
+    P.groups1 = c1 / (8 * bp);
     P.n_ab = 1;
     P.m_real = L.cout;
     P.ncols = WG_N;
+    P.b_planes = bp;
     P.a_bytes = (uint32_t)(L.cout / 8) * WG_PLANE;
-    P.b_bytes = WG_B_BYTES;
-    P.idesc = wg_idesc(WG_N);
+    P.b_bytes = 9u * bp * WG_PLANE;
+    P.b_bytes_span = WG_B_BYTES;
+    P.idesc = wg_idesc(WG_N + 16);
     CUtensorMap mg, m1, m2;
     NRV_TRY(tc_planar_map(&mg, g, n, H, W, L.cout / 8, L.cout / 8));
-    NRV_TRY(tc_planar_map(&m1, x1, n, H, W, c1 / 8, 2));
-    if (c2) NRV_TRY(tc_planar_map(&m2, x2, n, H, W, c2 / 8, 2));
+    NRV_TRY(tc_planar_map(&m1, x1, n, H, W, c1 / 8, bp));
+    if (c2) NRV_TRY(tc_planar_map(&m2, x2, n, H, W, c2 / 8, bp));
     else m2 = m1;
-    return wg_launch(P, cin / 16, mg, m1, m2, (size_t)L.cout * 9 * cin, part, part_floats, nsplit, s);
+    return wg_launch(P, cin / (8 * bp), mg, m1, m2, (size_t)L.cout * 9 * cin, part, part_floats,
+                     partb, nsplit, s);
 }
 
 nrv_status tc_wgrad_up(const Net* net, int l, const void* g, int g_ld, int g_off, const void* x,
-                       int n, int H, int W, float* part, size_t part_floats, int* nsplit,
-                       cudaStream_t s) {
+                       int n, int H, int W, float* part, size_t part_floats, float* partb,
+                       int* nsplit, cudaStream_t s) {
     const Layer& L = net->layers[l];
-    if (L.kind != UPCONV2 || L.cin % 16 || L.cin > 256 || L.cout % 8 || L.cout > 64 || g_ld % 8 ||
+    if (L.kind != UPCONV2 || L.cin % 16 || L.cin > 128 || L.cout % 8 || L.cout > 64 || g_ld % 8 ||
         g_off % 8 || g_off + L.cout > g_ld)
         return fail(NRV_ERR_UNSUPPORTED, "tensor-core weight gradient: channel counts");
     WgParams P;
@@ -334,15 +386,17 @@ nrv_status tc_wgrad_up(const Net* net, int l, const void* g, int g_ld, int g_off
     P.n_ab = 4 / groups;
     P.m_real = P.n_ab * L.cout;
     P.ncols = L.cin;
+    P.b_planes = 2;
     P.a_bytes = (uint32_t)P.n_ab * (L.cout / 8) * WG_PLANE;
     P.b_bytes = (uint32_t)(L.cin / 8) * WG_PLANE;
-    P.idesc = wg_idesc(L.cin);
+    P.b_bytes_span = P.b_bytes;
+    P.idesc = wg_idesc(L.cin + 16);
     CUtensorMap mg, m1;
     P.g_plane0 = g_off / 8;
     NRV_TRY(tc_parity_map(&mg, g, n * 2 * H, 2 * W, g_ld / 8, L.cout / 8));
     NRV_TRY(tc_planar_map(&m1, x, n, H, W, L.cin / 8, L.cin / 8));
-    return wg_launch(P, groups, mg, m1, m1, (size_t)L.cin * 4 * L.cout, part, part_floats, nsplit,
-                     s);
+    return wg_launch(P, groups, mg, m1, m1, (size_t)L.cin * 4 * L.cout, part, part_floats, partb,
+                     nsplit, s);
 }
 
 }  // namespace nrv
