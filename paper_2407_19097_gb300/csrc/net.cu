@@ -60,12 +60,27 @@ static inline int padded_cin(const Net* net, int l) {
 // conv forward   wf[tap][c][o]  = W[o][c][tap]      (c < padded cin, zero beyond cin)
 // conv backward  wt[tap][o][c]  = W[o][c][8 - tap]  (180-degree rotation, transposed)
 // upconv         wf[a][b][c][o] = W[c][o][a][b]
-__global__ void repack_f32_kernel(const float* __restrict__ P, Layer L, int cinp, float* wf,
-                                  float* wt) {
-    const int kk = L.kind == CONV3 ? 9 : 4;
-    const size_t total = (size_t)kk * cinp * L.cout;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
+// All layers in one launch: element i belongs to the layer whose range holds it.
+struct RepackJobs {
+    int n;
+    size_t start[NUM_LAYERS + 1];
+    Layer L[NUM_LAYERS];
+    int cinp[NUM_LAYERS];
+    size_t off[NUM_LAYERS];   // offset (floats) in wf and wt
+};
+
+__global__ void repack_f32_kernel(const float* __restrict__ P, const __grid_constant__ RepackJobs J,
+                                  float* wf_all, float* wt_all) {
+    const size_t all = J.start[J.n];
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < all;
+         g += (size_t)gridDim.x * blockDim.x) {
+        int j = 0;
+        while (g >= J.start[j + 1]) ++j;
+        const Layer& L = J.L[j];
+        const int cinp = J.cinp[j];
+        float* wf = wf_all + J.off[j];
+        float* wt = wt_all + J.off[j];
+        const size_t i = g - J.start[j];
         const int o = (int)(i % L.cout);
         const int c = (int)((i / L.cout) % cinp);
         const int tap = (int)(i / ((size_t)L.cout * cinp));
@@ -93,14 +108,23 @@ nrv_status net_repack(Net* net, cudaStream_t s) {
     NRV_TRY(net->wf32.ensure(off * 4));
     NRV_TRY(net->wtf32.ensure(off * 4));
     const float* P = (const float*)net->params.p;
+    RepackJobs J;
+    memset(&J, 0, sizeof(J));
     for (int l = 0; l < NUM_LAYERS; ++l) {
         const Layer& L = net->layers[l];
         if (L.kind == HEAD1) continue;
-        repack_f32_kernel<<<64, 256, 0, s>>>(P, L, padded_cin(net, l),
-                                              (float*)net->wf32.p + net->wf_off[l],
-                                              (float*)net->wtf32.p + net->wf_off[l]);
-        NRV_CHECK_LAUNCH();
+        const int kk = L.kind == CONV3 ? 9 : 4;
+        J.L[J.n] = L;
+        J.cinp[J.n] = padded_cin(net, l);
+        J.off[J.n] = net->wf_off[l];
+        J.start[J.n + 1] = J.start[J.n] + (size_t)kk * J.cinp[J.n] * L.cout;
+        ++J.n;
     }
+    size_t blocks = (J.start[J.n] + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    repack_f32_kernel<<<(unsigned)(blocks ? blocks : 1), 256, 0, s>>>(P, J, (float*)net->wf32.p,
+                                                                    (float*)net->wtf32.p);
+    NRV_CHECK_LAUNCH();
     return tc_repack(net, s);
 }
 

@@ -632,40 +632,75 @@ constexpr int KIND_DGRAD = 3;   // packing of the data-gradient weights (BF16)
 // out[slice][ks][half][n][ce], ce = 8 (BF16) or 16 (E4M3).  FP8 weights are
 // W * fold / s_w[n] in E4M3, fold = scale(skip) / scale(upsampled) for the second
 // source of a concatenating layer, 1 otherwise.
-__global__ void pack_tc_weights_kernel(const float* __restrict__ P, int64_t woff, int kind,
-                                       int cin_real, int cout, int n_slice, int nslices, int nks,
-                                       const int4* __restrict__ halves, int c1, int fp8,
-                                       float fold, const float* __restrict__ s_w, uint8_t* out) {
-    const int ce = fp8 ? 16 : 8;
-    const size_t total = (size_t)nslices * nks * 2 * n_slice * ce;
+// One packing job: a layer's weights in one operand layout.
+struct PackJob {
+    int64_t woff;
+    int kind, cin_real, cout, n_slice, nslices, nks, c1, fp8;
+    float fold;
+    const float* s_w;
+    const int4* halves;
+    uint8_t* out;
+};
+
+// Element i of job J (i < nslices * nks * 2 * n_slice * ce).
+__device__ __forceinline__ void pack_element(const float* __restrict__ P, const PackJob& J,
+                                             size_t i) {
+    const int ce = J.fp8 ? 16 : 8;
+    const int e = (int)(i % ce);
+    const int nl = (int)((i / ce) % J.n_slice);
+    const int hf = (int)((i / (ce * (size_t)J.n_slice)) % 2);
+    const int ks = (int)((i / (2 * ce * (size_t)J.n_slice)) % J.nks);
+    const int sl = (int)(i / (2 * ce * (size_t)J.n_slice * J.nks));
+    const int4 h = J.halves[2 * ks + hf];
+    const int n = sl * J.n_slice + nl;
+    float v = 0.0f;
+    if (h.x >= 0) {
+        const int c = (h.y == 0 ? 0 : J.c1) + ce * h.z + e;
+        if (J.kind == KIND_DGRAD) {
+            // data gradient: column n = forward input channel, K = (tap, forward output
+            // channel c); the kernel flipped: W[c][n][8 - tap]
+            if (c < J.cout && n < J.cin_real)
+                v = P[J.woff + ((size_t)c * J.cin_real + n) * 9 + (8 - h.x)];
+        } else if (c < J.cin_real) {
+            if (J.kind == CONV3) v = P[J.woff + ((size_t)n * J.cin_real + c) * 9 + h.x];
+            else v = P[J.woff + ((size_t)c * J.cout + n % J.cout) * 4 + n / J.cout];
+            if (h.y == 1) v *= J.fold;
+        }
+    }
+    if (J.fp8) {
+        J.out[i] = __nv_cvt_float_to_fp8(v / J.s_w[n], __NV_SATFINITE, __NV_E4M3);
+    } else {
+        __nv_bfloat16 b = __float2bfloat16_rn(v);
+        reinterpret_cast<uint16_t*>(J.out)[i] = *reinterpret_cast<uint16_t*>(&b);
+    }
+}
+
+__device__ __forceinline__ size_t pack_count(const PackJob& J) {
+    return (size_t)J.nslices * J.nks * 2 * J.n_slice * (J.fp8 ? 16 : 8);
+}
+
+__global__ void pack_tc_weights_kernel(const float* __restrict__ P, const __grid_constant__ PackJob J) {
+    const size_t total = pack_count(J);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x)
+        pack_element(P, J, i);
+}
+
+// Every layer of one layout in one launch: element i belongs to the job whose range holds it.
+struct PackJobs {
+    int n;
+    size_t start[NUM_LAYERS + 1];
+    PackJob job[NUM_LAYERS];
+};
+
+__global__ void pack_tc_weights_all_kernel(const float* __restrict__ P,
+                                           const __grid_constant__ PackJobs J) {
+    const size_t total = J.start[J.n];
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
          i += (size_t)gridDim.x * blockDim.x) {
-        const int e = (int)(i % ce);
-        const int nl = (int)((i / ce) % n_slice);
-        const int hf = (int)((i / (ce * (size_t)n_slice)) % 2);
-        const int ks = (int)((i / (2 * ce * (size_t)n_slice)) % nks);
-        const int sl = (int)(i / (2 * ce * (size_t)n_slice * nks));
-        const int4 h = halves[2 * ks + hf];
-        const int n = sl * n_slice + nl;
-        float v = 0.0f;
-        if (h.x >= 0) {
-            const int c = (h.y == 0 ? 0 : c1) + ce * h.z + e;
-            if (kind == KIND_DGRAD) {
-                // data gradient: column n = forward input channel, K = (tap, forward output
-                // channel c); the kernel flipped: W[c][n][8 - tap]
-                if (c < cout && n < cin_real) v = P[woff + ((size_t)c * cin_real + n) * 9 + (8 - h.x)];
-            } else if (c < cin_real) {
-                if (kind == CONV3) v = P[woff + ((size_t)n * cin_real + c) * 9 + h.x];
-                else v = P[woff + ((size_t)c * cout + n % cout) * 4 + n / cout];
-                if (h.y == 1) v *= fold;
-            }
-        }
-        if (fp8) {
-            out[i] = __nv_cvt_float_to_fp8(v / s_w[n], __NV_SATFINITE, __NV_E4M3);
-        } else {
-            __nv_bfloat16 b = __float2bfloat16_rn(v);
-            reinterpret_cast<uint16_t*>(out)[i] = *reinterpret_cast<uint16_t*>(&b);
-        }
+        int j = 0;
+        while (i >= J.start[j + 1]) ++j;
+        pack_element(P, J.job[j], i - J.start[j]);
     }
 }
 
@@ -692,6 +727,35 @@ __global__ void fp8_column_scales_kernel(const float* __restrict__ P, int64_t wo
 }
 
 DevBuf g_halves[3];   // K orders of the BF16, FP8 and data-gradient weights
+std::vector<int4> g_halves_host[3];   // what g_halves holds (the copy's source stays valid)
+
+// Upload a K-order table when it differs from the device copy.  Only then does the host
+// wait for the copy (the table depends on layer shapes, not on weight values).
+nrv_status upload_halves(int k, const std::vector<int4>& h, cudaStream_t s) {
+    if (h.size() == g_halves_host[k].size() &&
+        memcmp(h.data(), g_halves_host[k].data(), h.size() * sizeof(int4)) == 0 && g_halves[k].p)
+        return NRV_OK;
+    NRV_CHECK_CUDA(cudaStreamSynchronize(s));   // an earlier copy may still read the old table
+    g_halves_host[k] = h;
+    NRV_TRY(g_halves[k].ensure(h.size() * sizeof(int4)));
+    NRV_CHECK_CUDA(cudaMemcpyAsync(g_halves[k].p, g_halves_host[k].data(), h.size() * sizeof(int4),
+                                   cudaMemcpyHostToDevice, s));
+    return NRV_OK;
+}
+
+// One launch for a table of packing jobs.
+nrv_status pack_all(const float* P, PackJobs& J, cudaStream_t s) {
+    J.start[0] = 0;
+    for (int j = 0; j < J.n; ++j)
+        J.start[j + 1] = J.start[j] + (size_t)J.job[j].nslices * J.job[j].nks * 2 * J.job[j].n_slice *
+                                          (J.job[j].fp8 ? 16 : 8);
+    if (J.n == 0) return NRV_OK;
+    size_t blocks = (J.start[J.n] + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    pack_tc_weights_all_kernel<<<(unsigned)blocks, 256, 0, s>>>(P, J);
+    NRV_CHECK_LAUNCH();
+    return NRV_OK;
+}
 
 }  // namespace
 
@@ -809,21 +873,18 @@ static nrv_status tc_repack_dgrad(Net* net, cudaStream_t s) {
     NRV_TRY(build_cfg_dgrad(net, all_halves, hoff, off));
     if (off == 0) return NRV_OK;
     NRV_TRY(net->wtbf16.ensure(off));
-    NRV_TRY(g_halves[2].ensure(all_halves.size() * sizeof(int4)));
-    NRV_CHECK_CUDA(cudaMemcpyAsync(g_halves[2].p, all_halves.data(), all_halves.size() * sizeof(int4),
-                                   cudaMemcpyHostToDevice, s));
+    NRV_TRY(upload_halves(2, all_halves, s));
+    PackJobs J;
+    memset(&J, 0, sizeof(J));
     for (int l = 0; l < NUM_LAYERS; ++l) {
         const TcLayerCfg& c = g_cfg_dg[l];
         if (!c.ok) continue;
         const Layer& L = net->layers[l];
-        pack_tc_weights_kernel<<<64, 256, 0, s>>>(
-            (const float*)net->params.p, L.woff, KIND_DGRAD, L.cin, L.cout, c.n_slice, c.nslices,
-            c.nks, (const int4*)g_halves[2].p + hoff[l], c.c1, 0, 1.0f, nullptr,
-            (uint8_t*)net->wtbf16.p + c.w_off);
-        NRV_CHECK_LAUNCH();
+        J.job[J.n++] = PackJob{L.woff, KIND_DGRAD, L.cin, L.cout, c.n_slice, c.nslices, c.nks, c.c1, 0,
+                               1.0f, nullptr, (const int4*)g_halves[2].p + hoff[l],
+                               (uint8_t*)net->wtbf16.p + c.w_off};
     }
-    NRV_CHECK_CUDA(cudaStreamSynchronize(s));
-    return NRV_OK;
+    return pack_all((const float*)net->params.p, J, s);
 }
 
 nrv_status tc_repack(Net* net, cudaStream_t s) {
@@ -833,21 +894,18 @@ nrv_status tc_repack(Net* net, cudaStream_t s) {
     NRV_TRY(build_cfg(net, 0, all_halves, hoff, off));
     if (off == 0) return NRV_OK;
     NRV_TRY(net->wbf16.ensure(off));
-    NRV_TRY(g_halves[0].ensure(all_halves.size() * sizeof(int4)));
-    NRV_CHECK_CUDA(cudaMemcpyAsync(g_halves[0].p, all_halves.data(), all_halves.size() * sizeof(int4),
-                                   cudaMemcpyHostToDevice, s));
+    NRV_TRY(upload_halves(0, all_halves, s));
+    PackJobs J;
+    memset(&J, 0, sizeof(J));
     for (int l = 0; l < NUM_LAYERS; ++l) {
         const TcLayerCfg& c = g_cfg[0][l];
         if (!c.ok) continue;
         const Layer& L = net->layers[l];
-        pack_tc_weights_kernel<<<64, 256, 0, s>>>(
-            (const float*)net->params.p, L.woff, c.kind, L.cin, L.cout, c.n_slice, c.nslices, c.nks,
-            (const int4*)g_halves[0].p + hoff[l], c.c1, 0, 1.0f, nullptr,
-            (uint8_t*)net->wbf16.p + c.w_off);
-        NRV_CHECK_LAUNCH();
+        J.job[J.n++] = PackJob{L.woff, c.kind, L.cin, L.cout, c.n_slice, c.nslices, c.nks, c.c1, 0,
+                               1.0f, nullptr, (const int4*)g_halves[0].p + hoff[l],
+                               (uint8_t*)net->wbf16.p + c.w_off};
     }
-    // the host copy of the halves must stay valid until the copy ran
-    NRV_CHECK_CUDA(cudaStreamSynchronize(s));
+    NRV_TRY(pack_all((const float*)net->params.p, J, s));
     NRV_TRY(tc_repack_dgrad(net, s));
     if (net->fp8_ready) return tc_repack_fp8(net, s);
     return NRV_OK;
@@ -882,9 +940,7 @@ nrv_status tc_repack_fp8(Net* net, cudaStream_t s) {
     }
     NRV_TRY(net->wfp8.ensure(off));
     NRV_TRY(net->wscale8.ensure(2 * cs * sizeof(float)));
-    NRV_TRY(g_halves[1].ensure(all_halves.size() * sizeof(int4)));
-    NRV_CHECK_CUDA(cudaMemcpyAsync(g_halves[1].p, all_halves.data(), all_halves.size() * sizeof(int4),
-                                   cudaMemcpyHostToDevice, s));
+    NRV_TRY(upload_halves(1, all_halves, s));
     float* s_w = (float*)net->wscale8.p;
     float* colscale = s_w + cs;
     for (int l = 0; l < NUM_LAYERS; ++l) {
@@ -900,13 +956,12 @@ nrv_status tc_repack_fp8(Net* net, cudaStream_t s) {
             (const float*)net->params.p, L.woff, c.kind, L.cin, c1_real, L.cout, c.ncols, fold,
             s_in, s_w + c.cs_off, colscale + c.cs_off);
         NRV_CHECK_LAUNCH();
-        pack_tc_weights_kernel<<<64, 256, 0, s>>>(
-            (const float*)net->params.p, L.woff, c.kind, L.cin, L.cout, c.n_slice, c.nslices, c.nks,
-            (const int4*)g_halves[1].p + hoff[l], c.c1, 1, fold, s_w + c.cs_off,
-            (uint8_t*)net->wfp8.p + c.w_off);
+        const PackJob job{L.woff, c.kind, L.cin, L.cout, c.n_slice, c.nslices, c.nks, c.c1, 1,
+                          fold, s_w + c.cs_off, (const int4*)g_halves[1].p + hoff[l],
+                          (uint8_t*)net->wfp8.p + c.w_off};
+        pack_tc_weights_kernel<<<64, 256, 0, s>>>((const float*)net->params.p, job);
         NRV_CHECK_LAUNCH();
     }
-    NRV_CHECK_CUDA(cudaStreamSynchronize(s));
     return NRV_OK;
 }
 

@@ -127,39 +127,59 @@ __global__ void __launch_bounds__(WG_THREADS) wgrad3_kernel(TView<const T> g, in
 //  1  transposed conv weight: i = c*4*cout + ab*cout + o -> dw[(c*cout + o)*4 + ab]
 //  2  copy: dw[i]
 //  3  transposed conv bias: i = o, each chunk contributing part[ab*cout + o] for ab = 0..3
-__global__ void reduce_partials_kernel(const float* __restrict__ part, int nchunks, size_t stride,
-                                       int count, int mode, int cout, int cin, int cin_real,
-                                       float* __restrict__ dw) {
-    __shared__ float red[8][33];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i = blockIdx.x * 32 + tx;
+struct ReduceSeg {
+    const float* part;
+    int nchunks;
+    size_t stride;
+    int count, mode, cout, cin, cin_real;
+    float* dw;
+};
+
+__device__ __forceinline__ void reduce_item(const ReduceSeg& R, int i, int tx, int ty,
+                                            float (*red)[33]) {
     float s = 0.0f;
-    if (i < count)
-        for (int ch = ty; ch < nchunks; ch += 8) {
-            const float* pc = part + (size_t)ch * stride;
-            if (mode == 3) s += ((pc[i] + pc[cout + i]) + pc[2 * cout + i]) + pc[3 * cout + i];
+    if (i < R.count)
+        for (int ch = ty; ch < R.nchunks; ch += 8) {
+            const float* pc = R.part + (size_t)ch * R.stride;
+            if (R.mode == 3) s += ((pc[i] + pc[R.cout + i]) + pc[2 * R.cout + i]) + pc[3 * R.cout + i];
             else s += pc[i];
         }
     red[ty][tx] = s;
     __syncthreads();
-    if (ty != 0 || i >= count) return;
+    if (ty != 0 || i >= R.count) return;
     float t = red[0][tx];
     for (int k = 1; k < 8; ++k) t += red[k][tx];
-    if (mode == 0) {
-        const int K = 9 * cin, o = i / K, k = i % K, tap = k / cin, c = k % cin;
-        if (c < cin_real) dw[((size_t)o * cin_real + c) * 9 + tap] = t;
-    } else if (mode == 1) {
-        const int K = 4 * cout, c = i / K, k = i % K, ab = k / cout, o = k % cout;
-        dw[((size_t)c * cout + o) * 4 + ab] = t;
+    if (R.mode == 0) {
+        const int K = 9 * R.cin, o = i / K, k = i % K, tap = k / R.cin, c = k % R.cin;
+        if (c < R.cin_real) R.dw[((size_t)o * R.cin_real + c) * 9 + tap] = t;
+    } else if (R.mode == 1) {
+        const int K = 4 * R.cout, c = i / K, k = i % K, ab = k / R.cout, o = k % R.cout;
+        R.dw[((size_t)c * R.cout + o) * 4 + ab] = t;
     } else {
-        dw[i] = t;
+        R.dw[i] = t;
     }
 }
 
+// Two reductions (a layer's weights and its bias) in one launch: the first segment's
+// blocks, then the second's.
+__global__ void reduce_partials_kernel(const __grid_constant__ ReduceSeg A,
+                                       const __grid_constant__ ReduceSeg B) {
+    __shared__ float red[8][33];
+    const int nba = (A.count + 31) / 32;
+    const bool first = (int)blockIdx.x < nba;
+    const int blk = first ? (int)blockIdx.x : (int)blockIdx.x - nba;
+    reduce_item(first ? A : B, blk * 32 + threadIdx.x, threadIdx.x, threadIdx.y, red);
+}
+
 static nrv_status reduce_partials(const float* part, int nchunks, size_t stride, int count, int mode,
-                                  int cout, int cin, int cin_real, float* dw, cudaStream_t s) {
-    reduce_partials_kernel<<<(count + 31) / 32, dim3(32, 8), 0, s>>>(part, nchunks, stride, count,
-                                                                     mode, cout, cin, cin_real, dw);
+                                  int cout, int cin, int cin_real, float* dw, cudaStream_t s,
+                                  const ReduceSeg* second = nullptr) {
+    const ReduceSeg A{part, nchunks, stride, count, mode, cout, cin, cin_real, dw};
+    ReduceSeg B;
+    memset(&B, 0, sizeof(B));
+    if (second) B = *second;
+    const int blocks = (A.count + 31) / 32 + (B.count + 31) / 32;
+    reduce_partials_kernel<<<blocks, dim3(32, 8), 0, s>>>(A, B);
     NRV_CHECK_LAUNCH();
     return NRV_OK;
 }
@@ -419,10 +439,10 @@ struct Bwd {
                                                g.h[level], g.w[level], part, max_split * per_split,
                                                partb, &nsplit, s);
                 if (st == NRV_OK) {
-                    NRV_TRY(reduce_partials(part, nsplit, per_split, (int)per_split, 0, L.cout, cin,
-                                            L.cin, dparams + L.woff, s));
-                    return reduce_partials(partb, nsplit, L.cout, L.cout, 2, L.cout, cin, L.cin,
-                                           dparams + L.boff, s);
+                    const ReduceSeg bias{partb, nsplit, (size_t)L.cout, L.cout, 2, L.cout, cin, L.cin,
+                                         dparams + L.boff};
+                    return reduce_partials(part, nsplit, per_split, (int)per_split, 0, L.cout, cin,
+                                           L.cin, dparams + L.woff, s, &bias);
                 }
                 if (st != NRV_ERR_UNSUPPORTED) return st;
                 clear_error();
@@ -514,11 +534,11 @@ struct Bwd {
                                               g.h[level_in], g.w[level_in], part,
                                               max_split * per_split, partb, &nsplit, s);
             if (st == NRV_OK) {
-                NRV_TRY(reduce_partials(part, nsplit, per_split, (int)per_split, 1, L.cout, L.cin,
-                                        L.cin, dparams + L.woff, s));
-                // per split: the four kernel positions' sums of each channel
-                return reduce_partials(partb, nsplit, 4 * L.cout, L.cout, 3, L.cout, L.cin, L.cin,
-                                       dparams + L.boff, s);
+                // bias, per split: the four kernel positions' sums of each channel
+                const ReduceSeg bias{partb, nsplit, (size_t)4 * L.cout, L.cout, 3, L.cout, L.cin,
+                                     L.cin, dparams + L.boff};
+                return reduce_partials(part, nsplit, per_split, (int)per_split, 1, L.cout, L.cin,
+                                       L.cin, dparams + L.woff, s, &bias);
             }
             if (st != NRV_ERR_UNSUPPORTED) return st;
             clear_error();
