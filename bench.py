@@ -61,6 +61,52 @@ def network_floor_ms(H, W, c0, hbm_gbs, tflops):
     return sum(max(f / (tflops * 1e12), b / (hbm_gbs * 1e9)) for f, b in layers) * 1e3
 
 
+def measure_local_peaks(dev):
+    """Peaks the measured-peaks file does not hold, measured on this GPU with the library's
+    probes: FP32 FMA throughput (the FP32 network's roofline), random 64-bit atomicMin on a
+    16.6 MB (one 1080p key image, L2-resident) buffer (the depth test's), and an FP8 GEMM
+    through cuBLASLt (torch._scaled_mm; None where unavailable)."""
+    import torch
+    from paper_2407_19097_gb300 import nrv
+    stream = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    def timed_ms(fn, reps=5, warm=2):
+        for _ in range(warm):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    blocks, iters = sms * 8, 2048
+    out = torch.empty(blocks * 256, device=dev)
+    ms = timed_ms(lambda: nrv.check(nrv.lib().nrv_probe_ffma(nrv._ptr(out), blocks, iters, nrv._stream())))
+    ffma = 16.0 * iters * blocks * 256 / (ms * 1e-3) / 1e12
+    words, ops = 1920 * 1080, 1 << 26
+    buf = torch.zeros(words, dtype=torch.int64, device=dev)
+    ms = timed_ms(lambda: nrv.check(nrv.lib().nrv_probe_atomic_min(nrv._ptr(buf), words, ops, 7,
+                                                                    nrv._stream())))
+    atom = ops / (ms * 1e-3) / 1e9
+    fp8 = None
+    try:
+        n = 8192
+        a8 = torch.randn(n, n, device=dev).to(torch.float8_e4m3fn)
+        b8 = torch.randn(n, n, device=dev).to(torch.float8_e4m3fn).t()
+        one = torch.ones((), device=dev)
+        ms = timed_ms(lambda: torch._scaled_mm(a8, b8, scale_a=one, scale_b=one,
+                                               out_dtype=torch.bfloat16), reps=20)
+        fp8 = 2.0 * n ** 3 / (ms * 1e-3) / 1e12
+    except Exception:
+        fp8 = None
+    return {"fp32_ffma_tflops": ffma, "atomic64_min_g_per_s_l2": atom, "fp8_gemm_tflops": fp8,
+            "note": "measured in this run: FFMA probe (8 independent chains per thread), "
+                    "random 64-bit atomicMin over 2.07M words, cuBLASLt FP8 e4m3 8192^3"}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -84,10 +130,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-fp8", action="store_true")
-    ap.add_argument("--config", default="c3", choices=["c3", "c2", "c4", "c5"],
+    ap.add_argument("--config", default="c3", choices=["c3", "c2", "c4", "c5", "train"],
                     help="c3 (default): the 350M-point trajectory frame; c2: 50M-point vortex grid "
                          "frame with network precision vs FP64; c4: 200M-point terrain, 8 views of "
-                         "uneven size in one batch; c5: training step time and held-out quality")
+                         "uneven size in one batch; c5: training step time and held-out quality; "
+                         "train: the training step alone on seeded inputs of c5's shape")
     return ap.parse_args()
 
 
@@ -372,6 +419,40 @@ def run_c4(a):
     print(json.dumps(line), flush=True)
 
 
+def run_train(a):
+    """The training step alone (forward, L1 loss, backward, Adam, weight repack) on seeded
+    inputs of C5's shape: batch 16 of 256^2 crops, C0 = 5 (K = 3), BF16.  No targets from the
+    splatter (random targets): for timing and profiling the kernels of a step."""
+    import numpy as np
+    import torch
+    from paper_2407_19097_gb300 import nrv
+    dev = torch.device("cuda", 0)
+    c0, B, S = 5, 16, 256
+    net = nrv.Net(c0)
+    p = torch.from_numpy(unet_params(c0)).to(dev)
+    net.set_params(p)
+    g, m, v = torch.zeros_like(p), torch.zeros_like(p), torch.zeros_like(p)
+    loss = torch.zeros(1, device=dev)
+    rng = np.random.default_rng(5)
+    x = torch.from_numpy(rng.random((B, S, S, 8), dtype=np.float32)).to(dev)
+    x[..., c0:] = 0
+    x = x.to(torch.bfloat16)
+    t = torch.from_numpy(rng.random((B, S, S, 3), dtype=np.float32)).to(dev)
+    step = [0]
+
+    def one():
+        step[0] += 1
+        net.train_step(p, g, m, v, step[0], 1e-3, x, t, B, S, S, nrv.PREC_BF16, loss)
+
+    stream = torch.cuda.current_stream()
+    ms = _events_ms(one, max(a.steps, 1), max(a.warmup, 1), stream)
+    line = {"config": "train", "metric": "training step time (ms)", "value": ms, "unit": "ms/step",
+            "higher_is_better": False, "workload": f"batch {B} of {S}x{S}, C0={c0}, BF16",
+            "pixels_per_step": B * S * S, "data": "synthetic (seeded inputs and targets)",
+            "loss": float(loss.item())}
+    print(json.dumps(line), flush=True)
+
+
 def run_c5(a):
     """Training (Sec. 3.3): the U-Net learns to turn G-buffers of a trajectory scene into
     Gaussian-splat targets (the CPU splatter standing in for the paper's Gaussian Renderer).
@@ -472,7 +553,7 @@ def main():
     if a.config != "c3":
         import __graft_entry__
         __graft_entry__.build()
-        return {"c2": run_c2, "c4": run_c4, "c5": run_c5}[a.config](a)
+        return {"c2": run_c2, "c4": run_c4, "c5": run_c5, "train": run_train}[a.config](a)
 
     import numpy as np
     import torch
@@ -585,6 +666,8 @@ def main():
     e2e_s = (time.perf_counter() - t0) / a.steps
     barrier()
 
+    local_peaks = measure_local_peaks(dev) if rank == 0 else None
+
     # the FP32 form of the same pipeline, for comparison
     fp32_ms = None
     if not a.no_fp32 and prec != nrv.PREC_F32:
@@ -649,6 +732,15 @@ def main():
                                  "stage_floor_note": "sum over layers of max(FLOP time at the "
                                  "sustained tensor peak, byte time at the HBM peak)"},
             "fp32_ms_per_step": fp32_ms,
+            "local_peaks": local_peaks,
+            "roofline_network_fp32": (
+                {"bound": "alu", "achieved": flops / ((fp32_ms - clear_ms - vis_ms - res_ms) * 1e-3) / 1e12,
+                 "peak": local_peaks["fp32_ffma_tflops"], "unit": "TFLOP/s",
+                 "frac": flops / ((fp32_ms - clear_ms - vis_ms - res_ms) * 1e-3) / 1e12
+                 / local_peaks["fp32_ffma_tflops"],
+                 "note": "FP32 network (CUDA cores) time = FP32 frame minus the BF16 frame's "
+                         "clear, render and resolve stages; peak from the FFMA probe"}
+                if fp32_ms and local_peaks else None),
             "fp8_ms_per_step": fp8_ms,
             "e2e": {"value": world * sc.n / e2e_s, "unit": "points/s",
                     "h2d_bytes_per_step": 80, "d2h_bytes_per_step": H * W * 3 * 4,

@@ -317,6 +317,16 @@ nrv_status nrv_net_layer_wgrad(nrv_net* net, int layer, const void* d_dy, const 
 nrv_status nrv_net_layer_dgrad(nrv_net* net, int layer, const void* d_dy, const void* d_mask,
                                int n, int h, int w, nrv_prec prec, void* d_dx, nrv_stream stream);
 
+/* Microbenchmarks behind rooflines that need a measured peak (asynchronous on `stream`;
+ * the caller times them).  nrv_probe_ffma: `blocks` blocks of 256 threads, each thread
+ * 8 independent FP32 FMA chains of `iters` steps (16 * iters FLOPs per thread), one result
+ * per thread into d_out (blocks * 256 floats).  nrv_probe_atomic_min: n_ops 64-bit
+ * atomicMin at pseudo-random words of d_buf[n_words] (SplitMix64 of seed and the operation
+ * index).  Errors: NRV_ERR_ARG. */
+nrv_status nrv_probe_ffma(float* d_out, int blocks, int iters, nrv_stream stream);
+nrv_status nrv_probe_atomic_min(unsigned long long* d_buf, int64_t n_words, int64_t n_ops,
+                                uint64_t seed, nrv_stream stream);
+
 /* Which kernel family ran layer `layer` in the net's most recent forward pass:
  * 0 = SIMT (CUDA cores), 1 = tensor cores (tcgen05), -1 = not run yet or a
  * bad argument.  Lets callers check that a precision ran where they expect. */

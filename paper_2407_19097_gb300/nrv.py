@@ -84,6 +84,8 @@ SIGNATURES = {
     "nrv_net_run_layer": (I, [P, I, P, P, I, I, I, I, P, P]),
     "nrv_net_layer_wgrad": (I, [P, I, P, P, P, I, I, I, I, P, P]),
     "nrv_net_layer_dgrad": (I, [P, I, P, P, I, I, I, I, P, P]),
+    "nrv_probe_ffma": (I, [P, I, I, P]),
+    "nrv_probe_atomic_min": (I, [P, I64, I64, ctypes.c_uint64, P]),
     "nrv_net_forward_train": (I, [P, P, I, I, I, I, P, P]),
     "nrv_net_backward": (I, [P, P, P, P]),
     "nrv_l1_loss": (I, [P, P, I64, P, P, P]),
