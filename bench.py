@@ -363,6 +363,14 @@ def run_c2(a):
     st = nrv.timings()
     out["fp8"] = {"frame_ms": ms8, "render_ms": st[1], "resolve_pack_ms": st[2], "network_ms": st[3],
                   "rgb": rgb.float().cpu().numpy().astype(np.float64)}
+    # mixed: E4M3 for levels 1-3, BF16 for level 0
+    nrv.set_profiling(True)
+    ms8m = _events_ms(lambda: nrv.render_batch(scene, net, desc, [view], [rgb], nrv.PREC_FP8_MIXED),
+                      a.steps, a.warmup, stream)
+    nrv.set_profiling(False)
+    st = nrv.timings()
+    out["fp8_mixed"] = {"frame_ms": ms8m, "render_ms": st[1], "resolve_pack_ms": st[2],
+                        "network_ms": st[3], "rgb": rgb.float().cpu().numpy().astype(np.float64)}
     # the FP64 oracle frame
     _, d, m, g = oracle.rasterize(sc, view)
     hn, wn = (H + 7) // 8 * 8, (W + 7) // 8 * 8
@@ -674,7 +682,7 @@ def main():
         fp32_ms, _, _ = timed(nrv.PREC_F32, max(3, a.steps // 10), 2, False)
 
     # the FP8 network, calibrated on this frame's BF16 input
-    fp8_ms, fp8_rgb = None, None
+    fp8_ms, fp8_rgb, fp8m_ms, fp8m_rgb = None, None, None, None
     if not a.no_fp8:
         key = torch.empty((H, W), dtype=torch.int64, device=dev)
         dpl = torch.empty((H, W), dtype=torch.int32, device=dev)
@@ -690,6 +698,11 @@ def main():
         nrv.render_batch(scene, net, desc, [view], [rgb], nrv.PREC_FP8, inv8)
         torch.cuda.synchronize()
         fp8_rgb = rgb.float().cpu().numpy().astype(np.float64)
+        # mixed: E4M3 for levels 1-3, BF16 for level 0 (its input is the BF16 G-buffer)
+        fp8m_ms, _, _ = timed(nrv.PREC_FP8_MIXED, max(5, a.steps // 5), 3, False)
+        nrv.render_batch(scene, net, desc, [view], [rgb], nrv.PREC_FP8_MIXED)
+        torch.cuda.synchronize()
+        fp8m_rgb = rgb.float().cpu().numpy().astype(np.float64)
 
     # roofline of the render pass (the dominant stage): 12 algorithmic bytes per point --
     # every point's position; with chunk culling the pass reads far fewer bytes than that
@@ -742,6 +755,7 @@ def main():
                          "clear, render and resolve stages; peak from the FFMA probe"}
                 if fp32_ms and local_peaks else None),
             "fp8_ms_per_step": fp8_ms,
+            "fp8_mixed_ms_per_step": fp8m_ms,
             "e2e": {"value": world * sc.n / e2e_s, "unit": "points/s",
                     "h2d_bytes_per_step": 80, "d2h_bytes_per_step": H * W * 3 * 4,
                     "copies": "each frame's RGB copy to pinned host memory overlaps the next "
@@ -764,10 +778,11 @@ def main():
                                           f"threads ({t_cpu - t_ras:.1f} s)"}
         line["quality_vs_fp64"] = {"psnr_db": 10 * np.log10(r * r / mse) if mse > 0 else None,
                                    "max_abs": float(np.abs(got - y_ref).max())}
-        if fp8_rgb is not None:
-            mse8 = float(np.mean((fp8_rgb - y_ref) ** 2))
-            line["quality_fp8_vs_fp64"] = {"psnr_db": 10 * np.log10(r * r / mse8) if mse8 > 0 else None,
-                                           "max_abs": float(np.abs(fp8_rgb - y_ref).max())}
+        for key8, img in (("quality_fp8_vs_fp64", fp8_rgb), ("quality_fp8_mixed_vs_fp64", fp8m_rgb)):
+            if img is not None:
+                mse8 = float(np.mean((img - y_ref) ** 2))
+                line[key8] = {"psnr_db": 10 * np.log10(r * r / mse8) if mse8 > 0 else None,
+                              "max_abs": float(np.abs(img - y_ref).max())}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -56,7 +56,14 @@ typedef enum { NRV_F32 = 0, NRV_U32 = 1, NRV_U8X4 = 2 } nrv_fmt;
 
 /* Network arithmetic: FP32 SIMT, BF16 tensor cores, FP8 E4M3 tensor cores.
  * Accumulation is FP32 in every mode (the paper's App. B quantises to fp16). */
-typedef enum { NRV_PREC_F32 = 0, NRV_PREC_BF16 = 1, NRV_PREC_FP8 = 2 } nrv_prec;
+/* Network precision.  NRV_PREC_FP8_MIXED: E4M3 operands and activations for levels 1-3,
+ * BF16 for the full-resolution level 0 (its input is the BF16 G-buffer, as for BF16). */
+typedef enum {
+    NRV_PREC_F32 = 0,
+    NRV_PREC_BF16 = 1,
+    NRV_PREC_FP8 = 2,
+    NRV_PREC_FP8_MIXED = 3
+} nrv_prec;
 
 /* --------------------------------------------------------------------------
  * Library

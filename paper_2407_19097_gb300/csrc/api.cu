@@ -93,6 +93,8 @@ extern "C" int nrv_render_variants(int multi_view) {
 }
 extern "C" int nrv_pad8(int v) { return (v + 7) / 8 * 8; }
 extern "C" int nrv_netin_channels(nrv_prec p) { return p == NRV_PREC_FP8 ? 16 : 8; }
+// precision of the packed network input (the mixed FP8 network reads a BF16 input)
+static nrv_prec netin_prec(nrv_prec p) { return p == NRV_PREC_FP8_MIXED ? NRV_PREC_BF16 : p; }
 
 static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
@@ -172,6 +174,7 @@ static nrv_status check_pack(const nrv_pack_desc* d, int n_words) {
 }
 
 static void fill_pack(ResolveArgs& a, const nrv_pack_desc* d, nrv_prec prec, float inv) {
+    prec = netin_prec(prec);
     a.out_fmt = prec == NRV_PREC_F32 ? 0 : prec == NRV_PREC_BF16 ? 1 : 2;
     a.in_scale_inv = inv;
     a.n_ch = d->n_channels;
@@ -237,7 +240,7 @@ extern "C" nrv_status nrv_pack(const nrv_gbuffer* gb, int h, int w, const nrv_pa
     if (!gb || !netin || !gb->d_depth || !gb->d_mask || !gb->d_attr)
         return fail(NRV_ERR_ARG, "pack needs depth, mask and attribute planes and an output");
     if (h < 1 || w < 1 || h > 16384 || w > 16384) return fail(NRV_ERR_ARG, "bad size");
-    if (prec < NRV_PREC_F32 || prec > NRV_PREC_FP8) return fail(NRV_ERR_ARG, "bad precision");
+    if (prec < NRV_PREC_F32 || prec > NRV_PREC_FP8_MIXED) return fail(NRV_ERR_ARG, "bad precision");
     if (!aligned(netin, 32)) return fail(NRV_ERR_ARG, "d_netin must be 32-byte aligned");
     NRV_TRY(check_pack(d, 8));
     ResolveArgs a;
@@ -381,7 +384,7 @@ static nrv_status check_shade(nrv_net* net, const void* in, int n, int h, int w,
     if (!net || !in || !rgb) return fail(NRV_ERR_ARG, "null argument");
     if (!net->has_params) return fail(NRV_ERR_STATE, "no parameters loaded");
     if (n < 1 || h < 1 || w < 1 || h > 16384 || w > 16384) return fail(NRV_ERR_ARG, "bad size");
-    if (prec < NRV_PREC_F32 || prec > NRV_PREC_FP8) return fail(NRV_ERR_ARG, "bad precision");
+    if (prec < NRV_PREC_F32 || prec > NRV_PREC_FP8_MIXED) return fail(NRV_ERR_ARG, "bad precision");
     if (!aligned(in, 32)) return fail(NRV_ERR_ARG, "d_netin must be 32-byte aligned");
     return NRV_OK;
 }
@@ -441,7 +444,7 @@ extern "C" nrv_status nrv_net_forward_train(nrv_net* net, const void* netin, int
                                             nrv_prec prec, float* rgb, nrv_stream stream) {
     clear_error();
     NRV_TRY(check_shade(net, netin, n, h, w, prec, rgb));
-    if (prec == NRV_PREC_FP8) return fail(NRV_ERR_UNSUPPORTED, "training runs in F32 or BF16");
+    if (prec >= NRV_PREC_FP8) return fail(NRV_ERR_UNSUPPORTED, "training runs in F32 or BF16");
     NRV_TRY(net_forward(net, netin, n, h, w, prec, rgb, (cudaStream_t)stream));
     set_saved_input(netin);
     net->saved = true;
@@ -478,7 +481,7 @@ extern "C" nrv_status nrv_train_step(nrv_net* net, float* params, float* grad, f
     if (!params || !grad || !m || !v || !target || !loss || step < 1)
         return fail(NRV_ERR_ARG, "bad argument");
     NRV_TRY(check_shade(net, netin, n, h, w, prec, target));
-    if (prec == NRV_PREC_FP8) return fail(NRV_ERR_UNSUPPORTED, "training runs in F32 or BF16");
+    if (prec >= NRV_PREC_FP8) return fail(NRV_ERR_UNSUPPORTED, "training runs in F32 or BF16");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t nout = (size_t)n * h * w * 3;
     NRV_TRY(net->batch_ws.ensure(2 * nout * sizeof(float)));
@@ -549,7 +552,7 @@ extern "C" nrv_status nrv_render_batch(nrv_scene* s, nrv_net* net, const nrv_pac
                     net->c_in);
     cudaStream_t st = (cudaStream_t)stream;
     size_t key_off[8], in_off[8], tot = 0;
-    const size_t es = elem_size(prec) * nrv_netin_channels(prec);
+    const size_t es = elem_size(netin_prec(prec)) * nrv_netin_channels(netin_prec(prec));
     for (int i = 0; i < n; ++i) {
         NRV_TRY(check_view(views[i]));
         if (!rgb[i]) return fail(NRV_ERR_ARG, "null output %d", i);

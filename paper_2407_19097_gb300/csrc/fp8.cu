@@ -54,6 +54,67 @@ __global__ void pool2_fp8_kernel(const uint8_t* __restrict__ x, uint8_t* __restr
     }
 }
 
+// Level 0 -> level 1 of the mixed network: y = E4M3((mean of the 2x2 window of the BF16
+// tensor x) * inv_scale), the mean with the pool kernel's arithmetic.  x row-planar BF16
+// [n][2ho][c/8][2wo][8], y row-planar E4M3 [n][ho][c/16][wo][16]; one thread per 16 output
+// channels of one pixel, pixels fastest.
+__global__ void pool2_bf16_to_fp8_kernel(const __nv_bfloat16* __restrict__ x, uint8_t* __restrict__ y,
+                                         int c, int n, int ho, int wo, float inv_scale) {
+    const int nch = c / 16, nb = c / 8;
+    const size_t total = (size_t)n * ho * wo * nch;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int xo = (int)(i % wo);
+        const int ch = (int)((i / wo) % nch);
+        const size_t row = i / ((size_t)wo * nch);   // img * ho + yo
+        const int yo = (int)(row % ho);
+        const size_t img = row / ho;
+        const int wi = 2 * wo;
+        const size_t r0 = img * 2 * ho + 2 * yo;
+        uint32_t wd[4] = {0u, 0u, 0u, 0u};
+        for (int hp = 0; hp < 2; ++hp) {   // the two BF16 planes of this 16-channel group
+            const int pl = 2 * ch + hp;
+            const __nv_bfloat16* p0 = x + ((r0 * nb + pl) * (size_t)wi + 2 * xo) * 8;
+            const __nv_bfloat16* p1 = x + (((r0 + 1) * nb + pl) * (size_t)wi + 2 * xo) * 8;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float a = __bfloat162float(p0[k]), b = __bfloat162float(p0[8 + k]);
+                const float d = __bfloat162float(p1[k]), e = __bfloat162float(p1[8 + k]);
+                const float m = 0.25f * ((a + b) + (d + e));
+                const int j = 8 * hp + k;
+                wd[j >> 2] |= (uint32_t)enc8(m * inv_scale) << (8 * (j & 3));
+            }
+        }
+        *reinterpret_cast<uint4*>(y + ((row * nch + ch) * (size_t)wo + xo) * 16) =
+            make_uint4(wd[0], wd[1], wd[2], wd[3]);
+    }
+}
+
+// Level 1 -> level 0 of the mixed network: y = BF16(decoded E4M3 code * scale); x row-planar
+// E4M3 [rows][c/16][w][16], y row-planar BF16 [rows][c/8][w][8]; one thread per 8 values.
+__global__ void fp8_to_bf16_kernel(const uint8_t* __restrict__ x, __nv_bfloat16* __restrict__ y,
+                                   int c, size_t rows, int w, float scale) {
+    const int nb = c / 8, nch = c / 16;
+    const size_t total = rows * (size_t)w * nb;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int xx = (int)(i % w);
+        const int pl = (int)((i / w) % nb);
+        const size_t row = i / ((size_t)w * nb);
+        const uint8_t* src = x + ((row * nch + pl / 2) * (size_t)w + xx) * 16 + 8 * (pl & 1);
+        const uint2 raw = *reinterpret_cast<const uint2*>(src);
+        const uint8_t* b = reinterpret_cast<const uint8_t*>(&raw);
+        uint32_t pk[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(dec8(b[2 * j]) * scale, dec8(b[2 * j + 1]) * scale);
+            pk[j] = *reinterpret_cast<uint32_t*>(&h2);
+        }
+        *reinterpret_cast<uint4*>(y + ((row * nb + pl) * (size_t)w + xx) * 8) =
+            make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+}
+
 // rgb[o] = bias[o] + sum_c W[o][c] * (x_c * s), cropped to h x wd (16 channels:
 // one plane, so the row-planar tensor is also plain NHWC).
 __global__ void head_fp8_kernel(const uint8_t* __restrict__ x, float s, const float* w,
@@ -189,6 +250,62 @@ nrv_status forward_fp8(Net* net, const uint8_t* netin, float* rgb, cudaStream_t 
         (const float*)net->params.p + Lh.boff, rgb, g.n, g.h[0], g.w[0], net->geo_H, net->geo_W);
     NRV_CHECK_LAUNCH();
     return NRV_OK;
+}
+
+nrv_status forward_fp8_mixed(Net* net, const void* netin, float* rgb, cudaStream_t s) {
+    if (!net->fp8_ready) return fail(NRV_ERR_STATE, "FP8 needs activation scales (calibrate first)");
+    const Geo& g = net->geo;
+    auto A = [&](int a) { return (uint8_t*)net->acts.p + net->act_off[a]; };
+    auto inv = [&](int a) { return 1.0f / net->act_scale[1 + a]; };
+    for (int l = 0; l < NUM_LAYERS; ++l) net->backend[l] = net->layers[l].kind == HEAD1 ? 0 : 1;
+    auto conv8 = [&](int l, const void* x1, int c1, const void* x2, int c2, int out,
+                     int level) -> nrv_status {
+        return tc_conv3(net, l, x1, c1, x2, c2, A(out), g, level, NRV_PREC_FP8, s, inv(out));
+    };
+    auto pool8 = [&](int in, int out, int level_out) -> nrv_status {
+        const int c = net->act_c[in];
+        pool2_fp8_kernel<<<blocks_for(g.px(level_out) * c / 16), 256, 0, s>>>(
+            A(in), A(out), c, g.n, g.h[level_out], g.w[level_out]);
+        NRV_CHECK_LAUNCH();
+        return NRV_OK;
+    };
+    auto up8 = [&](int l, int in, int out, int level_in) -> nrv_status {
+        return tc_upconv(net, l, A(in), A(out), g, level_in, NRV_PREC_FP8, s, inv(out));
+    };
+    // level 0 encoder in BF16 from the BF16 input
+    NRV_TRY(tc_conv3(net, L_E0A, netin, net->c0p, nullptr, 0, A(A_E0A), g, 0, NRV_PREC_BF16, s));
+    NRV_TRY(tc_conv3(net, L_E0B, A(A_E0A), 16, nullptr, 0, A(A_E0B), g, 0, NRV_PREC_BF16, s));
+    // pooled to level 1 and quantised with the scale of e0b's output
+    pool2_bf16_to_fp8_kernel<<<blocks_for(g.px(1)), 256, 0, s>>>(
+        (const __nv_bfloat16*)A(A_E0B), A(A_P0), 16, g.n, g.h[1], g.w[1], inv(A_P0));
+    NRV_CHECK_LAUNCH();
+    // levels 1-3 in E4M3
+    NRV_TRY(conv8(L_E1A, A(A_P0), 16, nullptr, 0, A_E1A, 1));
+    NRV_TRY(conv8(L_E1B, A(A_E1A), 32, nullptr, 0, A_E1B, 1));
+    NRV_TRY(pool8(A_E1B, A_P1, 2));
+    NRV_TRY(conv8(L_E2A, A(A_P1), 32, nullptr, 0, A_E2A, 2));
+    NRV_TRY(conv8(L_E2B, A(A_E2A), 64, nullptr, 0, A_E2B, 2));
+    NRV_TRY(pool8(A_E2B, A_P2, 3));
+    NRV_TRY(conv8(L_E3A, A(A_P2), 64, nullptr, 0, A_E3A, 3));
+    NRV_TRY(conv8(L_E3B, A(A_E3A), 128, nullptr, 0, A_E3B, 3));
+    NRV_TRY(up8(L_UP3, A_E3B, A_UP3, 3));
+    NRV_TRY(conv8(L_D2A, A(A_UP3), 64, A(A_E2B), 64, A_D2A, 2));
+    NRV_TRY(conv8(L_D2B, A(A_D2A), 64, nullptr, 0, A_D2B, 2));
+    NRV_TRY(up8(L_UP2, A_D2B, A_UP2, 2));
+    NRV_TRY(conv8(L_D1A, A(A_UP2), 32, A(A_E1B), 32, A_D1A, 1));
+    NRV_TRY(conv8(L_D1B, A(A_D1A), 32, nullptr, 0, A_D1B, 1));
+    // back to BF16 for level 0: d1b's output decoded into d1a's slot (no longer read)
+    const size_t rows1 = (size_t)g.n * g.h[1];
+    fp8_to_bf16_kernel<<<blocks_for(rows1 * g.w[1] * 4), 256, 0, s>>>(
+        A(A_D1B), (__nv_bfloat16*)A(A_D1A), 32, rows1, g.w[1], net->act_scale[1 + A_D1B]);
+    NRV_CHECK_LAUNCH();
+    NRV_TRY(tc_upconv(net, L_UP1, A(A_D1A), A(A_UP1), g, 1, NRV_PREC_BF16, s));
+    NRV_TRY(tc_conv3(net, L_D0A, A(A_UP1), 16, A(A_E0B), 16, A(A_D0A), g, 0, NRV_PREC_BF16, s));
+    const Layer& Lh = net->layers[L_HEAD];
+    const float* P = (const float*)net->params.p;
+    const TcHead head{P + Lh.woff, P + Lh.boff, rgb, net->geo_H, net->geo_W, 1.0f, false};
+    return tc_conv3(net, L_D0B, A(A_D0A), 16, nullptr, 0, A(A_D0B), g, 0, NRV_PREC_BF16, s, 1.0f,
+                    &head);
 }
 
 }  // namespace nrv

@@ -50,7 +50,8 @@ int net_layers(int c_in, Layer* L) {
     return (int)off;
 }
 
-size_t elem_size(nrv_prec p) { return p == NRV_PREC_F32 ? 4 : p == NRV_PREC_BF16 ? 2 : 1; }
+// bytes per stored activation value (the mixed FP8 network keeps level 0 in BF16)
+size_t elem_size(nrv_prec p) { return p == NRV_PREC_F32 ? 4 : (p == NRV_PREC_FP8 ? 1 : 2); }
 
 static inline int padded_cin(const Net* net, int l) {
     return l == L_E0A ? net->c0p : net->layers[l].cin;
@@ -311,6 +312,7 @@ nrv_status net_forward(Net* net, const void* netin, int n, int H, int W, nrv_pre
     if (prec == NRV_PREC_BF16)
         return forward_t<__nv_bfloat16>(net, (const __nv_bfloat16*)netin, rgb, s, true, prec,
                                         keep_acts);
+    if (prec == NRV_PREC_FP8_MIXED) return forward_fp8_mixed(net, netin, rgb, s);
     return forward_fp8(net, (const uint8_t*)netin, rgb, s, keep_acts);
 }
 

@@ -136,6 +136,8 @@ nrv_status tc_wgrad(const Net* net, int l, const void* g, const void* x1, int c1
 nrv_status tc_dgrad(const Net* net, int l, const void* gin, void* out, const void* mask, int n, int H,
                     int W, cudaStream_t s);
 nrv_status forward_fp8(Net* net, const uint8_t* netin, float* rgb, cudaStream_t s, bool keep_acts);
+// levels 1-3 in E4M3, level 0 in BF16 (fp8.cu); netin is the BF16 packed input
+nrv_status forward_fp8_mixed(Net* net, const void* netin, float* rgb, cudaStream_t s);
 // FP8 scale indices (0 input, 1 + Act) of a layer's first input, second input (-1 if none)
 // and output (-1 for the head)
 void layer_scale_index(int l, int* in1, int* in2, int* out);
