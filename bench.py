@@ -27,6 +27,9 @@ sys.path.insert(0, ROOT)
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 BYTES_PER_POINT = 12.0          # xyz read once per frame for every view
+# DRAM bytes the render pass of the 350M-point 1080p trajectory frame moves (one ncu capture:
+# chunk boxes and the positions of prepass and surviving chunks, tile-bound reads, atomics)
+RENDER_TRAFFIC_BYTES = 1.251e9
 
 
 def network_floor_ms(H, W, c0, hbm_gbs, tflops):
@@ -713,7 +716,12 @@ def main():
     roof = {"kernel": "render pass (chunk_render_kernel x2 + tile_bound_kernel, tuned variant)",
             "bound": "hbm", "achieved": vis_gbs,
             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": vis_gbs / peaks["hbm_gbs"],
-            "traffic": None, "peak_source": peak_kind,
+            "traffic": RENDER_TRAFFIC_BYTES if (a.particles, a.steps_per_particle, W, H) ==
+                       (1_000_000, 350, 1920, 1080) else None,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum summed over the "
+                              "render pass's launches of one frame (variant single/chunks/16x2), "
+                              "profiles/render_pass_dram_traffic_trajectories_350m_1080p.md",
+            "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": sc.n * BYTES_PER_POINT,
             "note": "chunk culling skips points that provably cannot win, so DRAM traffic is "
                     "below the algorithmic bytes; the brute-force pass is reported beside it"}
