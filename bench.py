@@ -110,6 +110,18 @@ def measure_local_peaks(dev):
                     "random 64-bit atomicMin over 2.07M words, cuBLASLt FP8 e4m3 8192^3"}
 
 
+def job_rate(ms, units_per_rank, world, device=None):
+    """Whole-job throughput of `world` replicas: the slowest rank's time per step (max over
+    ranks; every rank must call this) and units_per_rank * world / that time, per second."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * units_per_rank / (ms * 1e-3)
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -633,11 +645,7 @@ def main():
         del os.environ["NRV_VIS_VARIANT"]
     else:
         os.environ["NRV_VIS_VARIANT"] = pinned
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * sc.n / (ms * 1e-3)
+    ms, value = job_rate(ms, sc.n, world, dev)
 
     # end to end through the public API: camera from the host, every frame back to pinned host
     # memory.  Frames alternate between two output buffers; frame i's copy runs on a copy
