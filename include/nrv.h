@@ -311,16 +311,19 @@ nrv_status nrv_net_layer_wgrad(nrv_net* net, int layer, const void* d_dy, const 
                                const void* d_x2, int n, int h, int w, nrv_prec prec,
                                float* d_grad, nrv_stream stream);
 
-/* Data gradient of one 3x3 convolution layer (the backward of Sec. 3.3's network,
- * exposed like nrv_net_layer_wgrad):
- *   dx[p][c] = sum_{o,u,v} W[o][c][u][v] * dy[p - (u - 1, v - 1)][o]  (zero outside),
+/* Data gradient of one 3x3 or 2x2 stride-2 transposed convolution layer (the backward of
+ * Sec. 3.3's network, exposed like nrv_net_layer_wgrad):
+ *   3x3:        dx[p][c] = sum_{o,u,v} W[o][c][u][v] * dy[p - (u - 1, v - 1)][o]  (zero outside),
+ *   transposed: dx[i][j][c] = sum_{o,a,b} W[c][o][a][b] * dy[2i + a][2j + b][o],
  * then dx[p][c] = 0 where d_mask[p][c] <= 0 when d_mask is not NULL (the ReLU of the layer
- * below: pass its output).  d_dy: [n][h][w][C_out], d_mask and d_dx: [n][h][w][C_in] (both
- * halves of a concatenation), NHWC in `prec` (F32 or BF16).  BF16 runs on the tensor cores
- * with the kernel flipped and transposed (FP32 accumulation, BF16 output); F32 on the CUDA
- * cores.  Not for the first layer (its input needs no gradient).
- * Errors: NRV_ERR_ARG (null, misaligned, not a 3x3 layer, the first layer), NRV_ERR_STATE (no
- * parameters), NRV_ERR_UNSUPPORTED (FP8). */
+ * below: pass its output; required for a transposed conv).  d_dy: [n][h][w][C_out] (3x3) or
+ * [n][2h][2w][C_out] (transposed); d_mask and d_dx: [n][h][w][C_in] (both halves of a
+ * concatenation); NHWC in `prec` (F32 or BF16).  BF16 runs on the tensor cores (the 3x3
+ * kernel flipped and transposed; the transposed conv's four kernel positions as one K),
+ * FP32 accumulation, BF16 output; F32 on the CUDA cores.  Not for the first layer (its input
+ * needs no gradient).
+ * Errors: NRV_ERR_ARG (null, misaligned, the head, the first layer, a transposed conv without
+ * mask), NRV_ERR_STATE (no parameters), NRV_ERR_UNSUPPORTED (FP8). */
 nrv_status nrv_net_layer_dgrad(nrv_net* net, int layer, const void* d_dy, const void* d_mask,
                                int n, int h, int w, nrv_prec prec, void* d_dx, nrv_stream stream);
 

@@ -135,6 +135,11 @@ nrv_status tc_wgrad(const Net* net, int l, const void* g, const void* x1, int c1
 // may be null); NRV_ERR_UNSUPPORTED when the layer has no such path
 nrv_status tc_dgrad(const Net* net, int l, const void* gin, void* out, const void* mask, int n, int H,
                     int W, cudaStream_t s);
+// data gradient of transposed conv l on the tensor cores (BF16, row-planar): out (C_in at the
+// input level (n, H, W)) from the output gradient g at (2H, 2W), which holds g_ld channels of
+// which C_out from g_off on, zeroed where mask (shaped like out) is not positive
+nrv_status tc_updgrad(const Net* net, int l, const void* g, int g_ld, int g_off, const void* mask,
+                      void* out, int n, int H, int W, cudaStream_t s);
 nrv_status forward_fp8(Net* net, const uint8_t* netin, float* rgb, cudaStream_t s, bool keep_acts);
 // levels 1-3 in E4M3, level 0 in BF16 (fp8.cu); netin is the BF16 packed input
 nrv_status forward_fp8_mixed(Net* net, const void* netin, float* rgb, cudaStream_t s);

@@ -36,6 +36,12 @@
 // kernel records STATUS_TIMEOUT in the status word, waits (bounded) for its
 // own copies in flight, frees TMEM and returns.
 //
+// The data gradient of the 2x2 stride-2 transposed conv (mode 2) is a GEMM of one input
+// row's pixels (M) against K = (a, b, C_out): each "row load" is four 5-D TMA boxes of the
+// output gradient at output row 2y + a and pixel parity b (dense [plane][pixel][16 bytes]
+// tiles, K-major like any input row), the weights W[c][o][a][b] resident as B, and the
+// epilogue of mode 0 (mask, no bias, no ReLU).
+//
 // The 2x2 stride-2 transposed conv runs through the same kernel as a GEMM of
 // one input row (K = C_in, tiles of 128 pixels, no halo) against all four
 // kernel positions at once (N = 4 C_out); its epilogue scatters column
@@ -70,7 +76,10 @@ struct TcParams {
                              // into its own partial accumulator, the epilogue adds them
     int cout;                // output channels
     int out_nch;             // 16-byte planes per output row
-    int mode;                // 0: 3x3 conv (+ bias, ReLU); 1: 2x2 stride-2 transposed conv + bias
+    int mode;                // 0: 3x3 conv (+ bias, ReLU); 1: 2x2 stride-2 transposed conv + bias;
+                             // 2: data gradient of the transposed conv (stored like mode 0)
+    int parity_plane0;       // mode 2: first plane of the output gradient's channels
+    uint32_t ab_bytes;       // mode 2: bytes of one (a, b) block of a row slot
     int relu;                // mode 0: apply ReLU (forward); 0 for the data gradient
     int has_src2;
     uint32_t slot_bytes;     // bytes of one row slot (both sources, plus read slack)
@@ -258,9 +267,18 @@ __global__ void __launch_bounds__(NTHREADS, 4)
                     }
                     const uint32_t dst = s_ring + (uint32_t)slot * P.slot_bytes;
                     mbar_expect_tx(b_hfull(slot), P.tx_bytes);
-                    tma_load_4d(dst, &tm1, xe, 0, next_row, w.img, b_hfull(slot));
-                    if (P.has_src2)
-                        tma_load_4d(dst + P.src2_off, &tm2, xe, 0, next_row, w.img, b_hfull(slot));
+                    if (P.mode == 2) {
+                        // output rows 2y + a, pixels 2x + b of the gradient: four blocks
+                        for (int k = 0; k < 4; ++k)
+                            tma_load_5d(dst + (uint32_t)k * P.ab_bytes, &tm1, 0, k & 1, xe >> 1,
+                                        P.parity_plane0, (w.img * P.h + next_row) * 2 + (k >> 1),
+                                        b_hfull(slot));
+                    } else {
+                        tma_load_4d(dst, &tm1, xe, 0, next_row, w.img, b_hfull(slot));
+                        if (P.has_src2)
+                            tma_load_4d(dst + P.src2_off, &tm2, xe, 0, next_row, w.img,
+                                        b_hfull(slot));
+                    }
                     ++nloads;
                     ring_next(slot, phase, P.nslot);
                 }
@@ -406,7 +424,7 @@ __global__ void __launch_bounds__(NTHREADS, 4)
                     const int ng = slice * P.n_slice + c0;
                     size_t row;   // output image row
                     int xo, wo, o;
-                    if (P.mode == 0) {
+                    if (P.mode != 1) {
                         row = (size_t)w.img * P.h + w.y;
                         xo = x;
                         wo = P.w;
@@ -627,7 +645,8 @@ struct TcLayerCfg {
 TcLayerCfg g_cfg[2][NUM_LAYERS];   // [BF16, FP8]
 TcLayerCfg g_cfg_dg[NUM_LAYERS];   // BF16 data gradients of the 3x3 convs
 
-constexpr int KIND_DGRAD = 3;   // packing of the data-gradient weights (BF16)
+constexpr int KIND_DGRAD = 3;    // packing of the 3x3 data-gradient weights (BF16)
+constexpr int KIND_UPDGRAD = 4;  // packing of the transposed conv's data-gradient weights
 
 // out[slice][ks][half][n][ce], ce = 8 (BF16) or 16 (E4M3).  FP8 weights are
 // W * fold / s_w[n] in E4M3, fold = scale(skip) / scale(upsampled) for the second
@@ -656,7 +675,11 @@ __device__ __forceinline__ void pack_element(const float* __restrict__ P, const 
     float v = 0.0f;
     if (h.x >= 0) {
         const int c = (h.y == 0 ? 0 : J.c1) + ce * h.z + e;
-        if (J.kind == KIND_DGRAD) {
+        if (J.kind == KIND_UPDGRAD) {
+            // column n = the transposed conv's input channel, K = (a b, output channel c):
+            // W[n][c][a][b]
+            if (c < J.cout && n < J.cin_real) v = P[J.woff + ((size_t)n * J.cout + c) * 4 + h.x];
+        } else if (J.kind == KIND_DGRAD) {
             // data gradient: column n = forward input channel, K = (tap, forward output
             // channel c); the kernel flipped: W[c][n][8 - tap]
             if (c < J.cout && n < J.cin_real)
@@ -836,6 +859,30 @@ static nrv_status build_cfg_dgrad(Net* net, std::vector<int4>& all_halves, std::
         TcLayerCfg& c = g_cfg_dg[l];
         c = TcLayerCfg();
         const Layer& L = net->layers[l];
+        if (L.kind == UPCONV2 && L.cout % 16 == 0 && L.cin % 16 == 0) {
+            // transposed conv: K = (a b, C_out) from the four parity blocks of a row slot
+            c.kind = KIND_UPDGRAD;
+            c.c1 = L.cout;
+            c.c2 = 0;
+            c.rows = 1;
+            c.row0 = 0;
+            c.ncols = L.cin;
+            for (int ab = 0; ab < 4; ++ab)
+                for (int ch = 0; ch < L.cout / ce; ++ch) c.halves.push_back(Half{ab, 0, ch});
+            c.nks = (int)c.halves.size() / 2;
+            if (c.nks > MAX_KS) continue;
+            int ns = c.ncols;
+            while (ns > 16 && (size_t)c.nks * 2 * ns * 16 > 80 * 1024) ns /= 2;
+            c.n_slice = ns;
+            c.nslices = c.ncols / ns;
+            c.w_bytes = (uint32_t)c.nks * 2 * ns * 16;
+            c.w_off = off;
+            off += ((size_t)c.w_bytes * c.nslices + 1023) / 1024 * 1024;
+            hoff[l] = all_halves.size();
+            for (const Half& h : c.halves) all_halves.push_back(make_int4(h.tap, h.src, h.chunk, 0));
+            c.ok = true;
+            continue;
+        }
         if (L.kind != CONV3 || l == L_E0A || L.cout % ce || L.cin % 16) continue;
         c.kind = CONV3;
         c.c1 = L.cout;
@@ -880,7 +927,8 @@ static nrv_status tc_repack_dgrad(Net* net, cudaStream_t s) {
         const TcLayerCfg& c = g_cfg_dg[l];
         if (!c.ok) continue;
         const Layer& L = net->layers[l];
-        J.job[J.n++] = PackJob{L.woff, KIND_DGRAD, L.cin, L.cout, c.n_slice, c.nslices, c.nks, c.c1, 0,
+        const int kind = c.kind == KIND_UPDGRAD ? KIND_UPDGRAD : KIND_DGRAD;
+        J.job[J.n++] = PackJob{L.woff, kind, L.cin, L.cout, c.n_slice, c.nslices, c.nks, c.c1, 0,
                                1.0f, nullptr, (const int4*)g_halves[2].p + hoff[l],
                                (uint8_t*)net->wtbf16.p + c.w_off};
     }
@@ -987,12 +1035,13 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
                             const float* bias, int relu, const void* mask, int cout, const void* x1,
                             int c1, const void* x2, int c2, void* y, int n, int H, int W,
                             cudaStream_t s, int fp8, float inv_out, const TcHead* head = nullptr,
-                            void* pool_y = nullptr) {
+                            void* pool_y = nullptr, int g_ld = 0, int g_off = 0) {
     if (!c.ok || c.c1 != c1 || c.c2 != c2) return fail(NRV_ERR_UNSUPPORTED, "layer not configured");
     if (fp8 && !net->fp8_ready) return fail(NRV_ERR_STATE, "FP8 needs activation scales");
     if (n <= 0 || H <= 0 || W <= 0) return fail(NRV_ERR_ARG, "empty tensor");
     const int es = fp8 ? 1 : 2, ce = 16 / es;
     const bool conv = c.kind == CONV3;
+    const bool updg = c.kind == KIND_UPDGRAD;   // mode 2
     TcParams P;
     memset(&P, 0, sizeof(P));
     P.n = n;
@@ -1011,16 +1060,17 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
     P.row0 = c.row0;
     P.cout = cout;
     P.out_nch = cout / ce;
-    P.mode = conv ? 0 : 1;
+    P.mode = conv ? 0 : (updg ? 2 : 1);
     P.relu = relu;
     P.mask = (const uint8_t*)mask;
     P.has_src2 = c.c2 > 0;
     const uint32_t nch1 = c.c1 / ce, nch2 = c.c2 / ce;
     P.src2_off = (nch1 * PLANE + 127) / 128 * 128;   // TMA destinations are 128-byte aligned
-    const uint32_t used = nch2 ? P.src2_off + nch2 * PLANE : nch1 * PLANE;
+    P.ab_bytes = nch1 * PLANE;
+    const uint32_t used = updg ? 4 * nch1 * PLANE : (nch2 ? P.src2_off + nch2 * PLANE : nch1 * PLANE);
     // slack: rows 126 and 127 of a conv tile read up to 32 bytes past their plane
     P.slot_bytes = (used + 32 + 127) / 128 * 128;
-    P.tx_bytes = (nch1 + nch2) * PLANE;
+    P.tx_bytes = updg ? 4 * nch1 * PLANE : (nch1 + nch2) * PLANE;
     P.w_bytes = c.w_bytes;
     P.w_region = (c.w_bytes + 1023) / 1024 * 1024;
     // two MMA issuers where both partial accumulators of both tile buffers fit in 256
@@ -1115,6 +1165,7 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
         const Half& h0 = c.halves[2 * ks];
         const Half& h1 = c.halves[2 * ks + 1];
         auto rel = [&](const Half& h) -> uint32_t {
+            if (updg) return (uint32_t)h.tap * P.ab_bytes + (uint32_t)h.chunk * PLANE;
             return (h.src == 0 ? 0u : P.src2_off) + (uint32_t)h.chunk * PLANE +
                    (uint32_t)(conv ? h.tap % 3 : 0) * 16;
         };
@@ -1132,7 +1183,15 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
             return fail(NRV_ERR_UNSUPPORTED, "rows of a tile with different K patterns");
     }
     CUtensorMap m1, m2;
-    NRV_TRY(make_planar_map(&m1, x1, n, H, W, (int)nch1));
+    if (updg) {
+        // the output gradient at (2H, 2W), g_ld channels of which C_out from g_off on
+        if (g_ld < (int)c.c1 || g_off < 0 || g_off % ce || g_off + c.c1 > g_ld || g_ld % ce)
+            return fail(NRV_ERR_ARG, "gradient view");
+        P.parity_plane0 = g_off / ce;
+        NRV_TRY(tc_parity_map(&m1, x1, n * 2 * H, 2 * W, g_ld / ce, (int)nch1));
+    } else {
+        NRV_TRY(make_planar_map(&m1, x1, n, H, W, (int)nch1));
+    }
     if (P.has_src2) NRV_TRY(make_planar_map(&m2, x2, n, H, W, (int)nch2));
     else m2 = m1;
     if (!g_num_sms) {
@@ -1222,6 +1281,17 @@ nrv_status tc_parity_map(CUtensorMap* map, const void* base, int rows, int w, in
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(NRV_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return NRV_OK;
+}
+
+nrv_status tc_updgrad(const Net* net, int l, const void* g, int g_ld, int g_off, const void* mask,
+                      void* out, int n, int H, int W, cudaStream_t s) {
+    const Layer& L = net->layers[l];
+    const TcLayerCfg& c = g_cfg_dg[l];
+    if (L.kind != UPCONV2 || !c.ok || c.kind != KIND_UPDGRAD)
+        return fail(NRV_ERR_UNSUPPORTED, "no tensor-core data gradient");
+    const uint8_t* w = (const uint8_t*)net->wtbf16.p + c.w_off;
+    return tc_launch(net, c, w, nullptr, 0, mask, L.cin, g, L.cout, nullptr, 0, out, n, H, W, s, 0,
+                     1.0f, nullptr, nullptr, g_ld, g_off);
 }
 
 nrv_status tc_upconv(const Net* net, int l, const void* x, void* y, const Geo& g, int level_in,

@@ -564,16 +564,30 @@ struct Bwd {
                                dparams + L.boff, s);
     }
 
-    nrv_status upconv_bwd(int l, int xin, TView<const T> gout, TView<T> gx, int level_in) {
+    // data gradient of transposed conv l at level_in, zeroed where the layer's input xm (a
+    // ReLU output) is not positive
+    nrv_status dgrad_up(int l, TView<const T> gout, TView<const T> xm, TView<T> gx, int level_in) {
         const Layer& L = net->layers[l];
         const size_t npx = g.px(level_in);
-        NRV_TRY(wgrad_up(l, CA(xin), gout, level_in));
+        if (sizeof(T) == 2 && gout.planar && gx.planar && !gx.coff && gx.ld == L.cin && xm.planar &&
+            !xm.coff && xm.ld == L.cin) {
+            // BF16: on the tensor cores
+            const nrv_status st = tc_updgrad(net, l, gout.p, gout.ld, gout.coff, xm.p, gx.p, g.n,
+                                             g.h[level_in], g.w[level_in], s);
+            if (st != NRV_ERR_UNSUPPORTED) return st;
+            clear_error();
+        }
         dim3 grid((unsigned)((npx + 127) / 128), L.cin / 16);
         upconv2_dgrad_kernel<T><<<grid, 128, (size_t)4 * 16 * L.cout * 4, s>>>(
-            gout, L.cout, (const float*)net->wf32.p + net->wf_off[l], L.cin, CA(xin), gx, g.n,
+            gout, L.cout, (const float*)net->wf32.p + net->wf_off[l], L.cin, xm, gx, g.n,
             g.h[level_in], g.w[level_in]);
         NRV_CHECK_LAUNCH();
         return NRV_OK;
+    }
+
+    nrv_status upconv_bwd(int l, int xin, TView<const T> gout, TView<T> gx, int level_in) {
+        NRV_TRY(wgrad_up(l, CA(xin), gout, level_in));
+        return dgrad_up(l, gout, CA(xin), gx, level_in);
     }
 
     nrv_status pool_bwd(TView<const T> gp, TView<const T> gs, int e, TView<T> ge, int level) {
@@ -731,6 +745,36 @@ nrv_status net_layer_wgrad(Net* net, int l, const void* dy, const void* x1, cons
 nrv_status net_layer_dgrad(Net* net, int l, const void* dy, const void* mask, int n, int h, int w,
                            nrv_prec prec, void* dx, cudaStream_t s) {
     const Layer& L = net->layers[l];
+    if (L.kind == UPCONV2) {
+        // transposed conv: dy at (n, 2h, 2w), mask and dx at (n, h, w)
+        if (!mask) return fail(NRV_ERR_ARG, "layer %s: the mask (the layer's input) is required", L.name);
+        Geo g;
+        memset(&g, 0, sizeof(g));
+        g.n = n;
+        g.h[0] = h;
+        g.w[0] = w;
+        if (prec == NRV_PREC_F32) {
+            using T = float;
+            Bwd<T> b{net, s, g, nullptr, {}, {}};
+            return b.dgrad_up(l, TView<const T>{(const T*)dy, L.cout}, TView<const T>{(const T*)mask, L.cin},
+                              TView<T>{(T*)dx, L.cin}, 0);
+        }
+        if (prec != NRV_PREC_BF16) return fail(NRV_ERR_UNSUPPORTED, "data gradients in F32 or BF16");
+        using T = __nv_bfloat16;
+        const size_t rows = (size_t)n * h;
+        auto al = [](size_t bytes) { return (bytes + 255) / 256 * 256; };
+        const size_t bg = al(4 * rows * w * L.cout * 2), bm = al(rows * w * L.cin * 2),
+                     bo = al(rows * w * L.cin * 2);
+        NRV_TRY(net->layer_ws.ensure(bg + bm + bo));
+        char* ws = (char*)net->layer_ws.p;
+        T *pg = (T*)ws, *pm = (T*)(ws + bg), *po = (T*)(ws + bg + bm);
+        NRV_TRY(relayout(dy, pg, 2 * rows, 2 * w, L.cout, 2, true, s));
+        NRV_TRY(relayout(mask, pm, rows, w, L.cin, 2, true, s));
+        Bwd<T> b{net, s, g, nullptr, {}, {}};
+        NRV_TRY(b.dgrad_up(l, TView<const T>{pg, L.cout, 1}, TView<const T>{pm, L.cin, 1},
+                           TView<T>{po, L.cin, 1}, 0));
+        return relayout(po, dx, rows, w, L.cin, 2, false, s);
+    }
     if (L.kind != CONV3 || l == L_E0A)
         return fail(NRV_ERR_ARG, "layer %s has no data gradient here", L.name);
     Geo g;

@@ -181,3 +181,53 @@ def test_upconv_wgrad(layer, name, prec):
     assert np.all(np.abs(db - db_ref) <= 1e-5 * db_abs + 1e-30), float(np.abs(db - db_ref).max())
     rest = np.concatenate([g[:o], g[ob + co:]])
     assert np.all(np.isnan(rest))
+
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("layer,name", UPCONV)
+def test_upconv_dgrad(layer, name, prec):
+    """Transposed conv data gradient, masked by the layer's input (a ReLU output): BF16 on the
+    tensor cores (parity views of the output gradient, BF16 weights, FP32 accumulation, rounded
+    once), against the float64 oracle on the BF16 values, rounded once: within one BF16 ulp plus
+    the FP32 summation bound over K = 4 C_out products, and almost all bit for bit.  F32 (CUDA
+    cores): within 1e-5 of the largest value.  Masked outputs are exactly zero."""
+    import torch
+    from paper_2407_19097_gb300 import nrv
+    flat = make_params(C0, seed=13 + layer)
+    net = nrv.Net(C0)
+    net.set_params(torch.from_numpy(flat).to(torch_dev()))
+    _, _, ci, co = unet.layers(C0)[layer]
+    n, h, w = 2, 5, 300
+    rng = np.random.default_rng(400 + layer)
+    dy = (rng.standard_normal((n, 2 * h, 2 * w, co)) * 0.1).astype(np.float32)
+    mk = rng.standard_normal((n, h, w, ci)).astype(np.float32)
+    mk[mk < 0] = 0.0
+    dt = torch.bfloat16 if prec == 1 else torch.float32
+    dyt = torch.from_numpy(dy).to(torch_dev()).to(dt).contiguous()
+    mt = torch.from_numpy(mk).to(torch_dev()).to(dt).contiguous()
+    dx = torch.empty((n, h, w, ci), dtype=dt, device=torch_dev())
+    net.layer_dgrad(layer, dyt, mt, n, h, w, prec, dx)
+    torch.cuda.synchronize()
+    got = dx.float().cpu().numpy().astype(np.float64)
+    W, _ = unet.unflatten(flat.astype(np.float64), C0)[name]
+    Wq = _bf16(W) if prec == 1 else W
+    dv = _bf16(dy) if prec == 1 else dy.astype(np.float64)
+    zero = np.zeros((n, h, w, ci))
+    ref = unet.convT2_bwd(zero, Wq, dv)[0]
+    S = unet.convT2_bwd(zero, np.abs(Wq), np.abs(dv))[0]
+    keep = mk > 0
+    ref = np.where(keep, ref, 0.0)
+    assert np.all(got[~keep] == 0.0)
+    if prec == 1:
+        ref = _bf16(ref)
+        K = 4 * co
+        big = np.maximum(np.abs(got), np.abs(ref))
+        ulp = np.exp2(np.floor(np.log2(np.maximum(big, 1e-30))) - 7)
+        bound = ulp + K * 2.0 ** -24 / (1 - K * 2.0 ** -24) * S
+        worst = float(np.max(np.abs(got - ref) / bound))
+        exact = float(np.mean(got == ref))
+        assert exact >= 0.99 and worst <= 1.0, (exact, worst)
+    else:
+        err = np.abs(got - ref).max() / max(1.0, np.abs(ref).max())
+        assert err <= 1e-5, err
