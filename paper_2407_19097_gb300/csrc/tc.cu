@@ -25,10 +25,15 @@
 // halves always come from the same row slot.
 //
 // The weights of the CTA's output-channel slice stay resident in shared memory
-// ([k-step][half][n][16 bytes]).  Warp roles: warp 0 issues TMA loads, warp 1
-// owns TMEM and issues the MMAs, warps 2-5 drain the FP32 accumulator
-// (tcgen05.ld), scale, add the bias, apply ReLU and store row-planar output.
-// Accumulators are double-buffered.  The MMA issue loop is kept free of
+// ([k-step][half][n][16 bytes]).  Warp roles: warp 0 issues TMA loads, warps 1
+// and 6 issue the MMAs (alternate K-steps into two partial accumulators where
+// TMEM allows; warp 1 owns the allocation), warps 2-5 drain the FP32
+// accumulators (tcgen05.ld), add the partials, scale, add the bias, apply ReLU
+// (or a data gradient's ReLU mask) and store row-planar output -- and, where
+// asked, the 2x2 average pool of that output or the 1x1 head on it.
+// Accumulators are double-buffered.  The loader reads activations only after
+// griddepcontrol.wait (programmatic dependent launch: the setup and the weight
+// load overlap the previous kernel).  The MMA issue loop is kept free of
 // branches and of dependent parameter loads (the operand kind is a template
 // parameter, the per-K-step descriptor words sit in shared memory and are read
 // one step ahead): with narrow N the issuing thread, not the tensor pipe, sets
