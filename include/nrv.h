@@ -173,7 +173,8 @@ typedef struct {
 
 /* Network-input geometry for an H x W view: the canvas is Hn x Wn with
  * Hn, Wn = H, W rounded up to multiples of 8 (zero margin, cropped again at
- * the output) and C channels per pixel: 8 for F32 and BF16, 16 for FP8. */
+ * the output) and C channels per pixel: 8 for F32, BF16 and FP8_MIXED (a BF16
+ * input), 16 for FP8. */
 int nrv_pad8(int v);
 int nrv_netin_channels(nrv_prec prec);
 
@@ -265,7 +266,12 @@ nrv_status nrv_net_load(nrv_net* net, const char* path, nrv_stream stream);
  * It synchronises the stream.  nrv_net_set_act_scales sets the scales directly
  * (positive, finite) and packs the weights; nrv_net_get_act_scales reads them.
  * Both packers need parameters loaded (NRV_ERR_STATE otherwise) and are rerun
- * by nrv_net_set_params once scales exist. */
+ * by nrv_net_set_params once scales exist.
+ *
+ * NRV_PREC_FP8_MIXED uses the same scales for levels 1-3 only: level 0 (the
+ * input, e0a, e0b, up1, d0a, d0b) stays BF16 and the input is the BF16 packed
+ * input.  All-E4M3 storage misses a 2e-2 max-abs bound against an FP64 forward
+ * on full frames; the mixed network meets it. */
 nrv_status nrv_net_calibrate(nrv_net* net, const void* d_netin_bf16, int n, int height, int width,
                              nrv_stream stream);
 nrv_status nrv_net_set_act_scales(nrv_net* net, const float* scale, int n, nrv_stream stream);
@@ -403,7 +409,7 @@ nrv_status nrv_train_step(nrv_net* net, float* d_params, float* d_grad, float* d
  * sizes.  The device work is captured once per (scene, net, sizes, prec) into a
  * CUDA graph and replayed on later calls; the G-buffers and network inputs live
  * in the net's workspace.  in_scale_inv is the FP8 input scale inverse (ignored
- * otherwise).  Errors: NRV_ERR_ARG, NRV_ERR_OOM, NRV_ERR_CUDA. */
+ * otherwise, FP8_MIXED included).  Errors: NRV_ERR_ARG, NRV_ERR_OOM, NRV_ERR_CUDA. */
 nrv_status nrv_render_batch(nrv_scene* scene, nrv_net* net, const nrv_pack_desc* desc,
                             const nrv_view* views, int n_views, float* const* d_rgb,
                             nrv_prec prec, float in_scale_inv, nrv_stream stream);
