@@ -27,6 +27,10 @@
  *  - The library runs on the current CUDA device of the calling thread.  It
  *    has no CPU fallback: without a CUDA device every call that launches work
  *    returns NRV_ERR_CUDA.
+ *  - Calls that launch work share process-wide tables (the packed-weight
+ *    layouts of the tensor-core kernels, the tuned render-pass variant, kernel
+ *    attributes): make them from one host thread at a time.  A scene or net
+ *    handle and its workspaces serve one call at a time.
  */
 #ifndef NRV_H
 #define NRV_H
