@@ -58,3 +58,98 @@ def test_order_invariance_random(simple_view):
     b = oracle.splat(pts[perm], v, c[perm])
     np.testing.assert_array_equal(a, b)
     assert a.max() <= 1.0 and a.min() >= 0.0
+
+
+# ----------------------------------------------------------------- multi-tile screens
+# The splatter bins Gaussians into 16 x 16 tiles.  On a 64 x 64 screen (4 x 4 tiles) these pins
+# place Gaussians on tile corners, edges and the screen border, so that their 3-sigma discs
+# reach one, two or four tiles (or lie partly off screen), and check every pixel of the image.
+W64, H48 = 64, 48
+M64 = [2, 0, 0, 0, 0, 2, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0]   # sx = (2x/z + 1) W/2, sy = (1 - 2y/z) H/2
+
+
+def _pt64(sx, sy, z, h=H48):
+    """World point projecting to (sx, sy) at depth z on a 64-pixel-wide screen of height h
+    (with h = 64, dyadic values are reproduced exactly by the FP32 projection)."""
+    return [(sx / 32.0 - 1.0) * z / 2.0, (1.0 - sy / (h / 2.0)) * z / 2.0, z]
+
+
+def _closed_form_single(sx, sy, colour, h):
+    """Image of one Gaussian alone: 0.6 exp(-d^2 / (2 sigma^2)) c within 3 sigma, else 0."""
+    py, px = np.mgrid[0:h, 0:W64]
+    d2 = (px + 0.5 - sx) ** 2 + (py + 0.5 - sy) ** 2
+    a = np.where(d2 <= 4.5 ** 2, 0.6 * np.exp(-d2 / (2 * 1.5 ** 2)), 0.0)
+    return a[..., None] * np.asarray(colour, np.float32).astype(np.float64)
+
+
+# centres: a tile corner (4 tiles), a vertical edge (2 tiles), a horizontal edge, a tile
+# interior far from edges (1 tile), a corner of the screen and points off screen whose discs
+# still reach it
+CENTRES = [(16.0, 16.0), (32.0, 8.5), (40.25, 32.0), (8.0, 40.0), (0.0, 0.0), (-3.5, 20.0),
+           (66.0, 63.75), (63.5, 67.0), (47.75, 15.5), (31.875, 48.125), (20.0, 30.0),
+           (43.5, 52.0)]
+
+
+def test_single_gaussians_across_tile_edges(simple_view):
+    v = simple_view(M64, W64, 64, 0.5, 10.0)
+    c = [0.3, 0.6, 0.9]
+    for sx, sy in CENTRES:
+        img = oracle.splat(np.array([_pt64(sx, sy, 1.0, 64)], np.float32), v,
+                           np.array([c], np.float32))
+        np.testing.assert_allclose(img, _closed_form_single(sx, sy, c, 64), rtol=1e-12, atol=0,
+                                   err_msg=f"centre {(sx, sy)}")
+        assert img.sum() > 0.0
+
+
+def _project64(xyz):
+    """The projection of the splatter (FP32, separate roundings) for the test matrix."""
+    x, y, z = (xyz[:, k].astype(np.float32) for k in range(3))
+    cx = np.float32(2) * x
+    cy = np.float32(2) * y
+    cw = z
+    sx = (cx / cw + np.float32(1)) * np.float32(32)
+    sy = (np.float32(1) - cy / cw) * np.float32(24)
+    return cw, sx.astype(np.float64), sy.astype(np.float64)
+
+
+def _brute_force_splat(xyz, colour, znear, zfar):
+    """Unbinned compositing: every pixel walks the whole list sorted by (w, index)."""
+    cw, sx, sy = _project64(xyz)
+    keep = [i for i in range(len(cw)) if znear <= cw[i] <= zfar and -4.5 <= sx[i] < W64 + 4.5
+            and -4.5 <= sy[i] < H48 + 4.5]
+    order = sorted(keep, key=lambda i: (float(cw[i]), i))
+    out = np.zeros((H48, W64, 3))
+    for py in range(H48):
+        for px in range(W64):
+            cx, cy, tr = px + 0.5, py + 0.5, 1.0
+            acc = [0.0, 0.0, 0.0]
+            for i in order:
+                dx, dy = cx - sx[i], cy - sy[i]
+                d2 = dx * dx + dy * dy
+                if d2 > 4.5 * 4.5:
+                    continue
+                a = 0.6 * math.exp(-d2 / (2.0 * 1.5 * 1.5))
+                for j in range(3):
+                    acc[j] += tr * a * float(colour[i, j])
+                tr *= 1.0 - a
+                if tr < 1e-4:
+                    break
+            out[py, px] = acc
+    return out
+
+
+def test_random_multi_tile_scene_matches_unbinned_loop(simple_view):
+    v = simple_view(M64, W64, H48, 0.5, 10.0)
+    rng = np.random.default_rng(11)
+    n = 160
+    sx = rng.uniform(-6.0, W64 + 6.0, n)
+    sy = rng.uniform(-6.0, H48 + 6.0, n)
+    z = rng.uniform(0.4, 3.0, n)                       # some in front of the near plane
+    pts = np.array([_pt64(a, b, c) for a, b, c in zip(sx, sy, z)], np.float32)
+    # a few exact depth ties: the lower index goes first
+    pts[10:14, 2] = pts[9, 2]
+    colour = rng.uniform(0, 1, (n, 3)).astype(np.float32)
+    got = oracle.splat(pts, v, colour)
+    want = _brute_force_splat(pts, colour, 0.5, 10.0)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-15)
+    assert (got.sum(axis=2) > 0).mean() > 0.5          # the scene covers most tiles
