@@ -58,15 +58,22 @@ typedef enum {
 /* Attribute word formats (Sec. 3.2: "formats uint8 and fp32"). */
 typedef enum { NRV_F32 = 0, NRV_U32 = 1, NRV_U8X4 = 2 } nrv_fmt;
 
-/* Network arithmetic: FP32 SIMT, BF16 tensor cores, FP8 E4M3 tensor cores.
- * Accumulation is FP32 in every mode (the paper's App. B quantises to fp16). */
-/* Network precision.  NRV_PREC_FP8_MIXED: E4M3 operands and activations for levels 1-3,
- * BF16 for the full-resolution level 0 (its input is the BF16 G-buffer, as for BF16). */
+/* Network precision.  Accumulation is FP32 in every mode (the paper's App. B quantises to
+ * fp16; the reduced-precision modes here go to BF16 and 8 bits).
+ *  NRV_PREC_F32       FP32 on the CUDA cores.
+ *  NRV_PREC_BF16      BF16 operands and activations on the tensor cores.
+ *  NRV_PREC_FP8       the FP8 network: E4M3 operands and activations for levels 1-3, BF16
+ *                     for the full-resolution level 0 (its input is the BF16 G-buffer).  This
+ *                     is the mode that meets a 2e-2 max-abs bound (and 45 dB) against an FP64
+ *                     forward on full frames.
+ *  NRV_PREC_FP8_E4M3  every stored tensor E4M3 (a 16-channel E4M3 input): faster, but its
+ *                     3-bit mantissas compound over the full-resolution layers to max-abs
+ *                     errors of about 0.1 on full frames, above that bound. */
 typedef enum {
     NRV_PREC_F32 = 0,
     NRV_PREC_BF16 = 1,
-    NRV_PREC_FP8 = 2,
-    NRV_PREC_FP8_MIXED = 3
+    NRV_PREC_FP8_E4M3 = 2,
+    NRV_PREC_FP8 = 3
 } nrv_prec;
 
 /* --------------------------------------------------------------------------
@@ -177,8 +184,8 @@ typedef struct {
 
 /* Network-input geometry for an H x W view: the canvas is Hn x Wn with
  * Hn, Wn = H, W rounded up to multiples of 8 (zero margin, cropped again at
- * the output) and C channels per pixel: 8 for F32, BF16 and FP8_MIXED (a BF16
- * input), 16 for FP8. */
+ * the output) and C channels per pixel: 8 for F32, BF16 and FP8 (a BF16 input),
+ * 16 for FP8_E4M3. */
 int nrv_pad8(int v);
 int nrv_netin_channels(nrv_prec prec);
 
@@ -256,26 +263,25 @@ nrv_status nrv_net_get_params(const nrv_net* net, float* d_out, nrv_stream strea
 nrv_status nrv_net_save(const nrv_net* net, const char* path, nrv_stream stream);
 nrv_status nrv_net_load(nrv_net* net, const char* path, nrv_stream stream);
 
-/* FP8 (E4M3) network: every tensor the network stores holds E4M3 codes q with
+/* E4M3 tensors of the FP8 modes: every E4M3 tensor the network stores holds codes q with
  * value q * scale, one scale per tensor; weights hold E4M3 codes per output
  * column with scale max|column| / 448 (App. B quantises to fp16; this goes to
  * 8 bits).  The 21 tensor scales, in this order: the network input, then
  * e0a e0b p0 e1a e1b p1 e2a e2b p2 e3a e3b up3 d2a d2b up2 d1a d1b up1 d0a d0b
  * (the outputs of those layers; p0..p2 the pooled tensors, which must carry the
- * scale of the tensor they pool).  The input is packed by nrv_pack / passed to
- * nrv_render_batch with in_scale_inv = 1 / scale[0].
+ * scale of the tensor they pool).  For NRV_PREC_FP8_E4M3 the input is packed by
+ * nrv_pack / passed to nrv_render_batch with in_scale_inv = 1 / scale[0].
  *
  * nrv_net_calibrate runs a BF16 forward on n sample inputs (BF16 NHWC, as for
- * nrv_shade), sets every scale to max|tensor| / 448 and packs the FP8 weights.
+ * nrv_shade), sets every scale to max|tensor| / 448 and packs the E4M3 weights.
  * It synchronises the stream.  nrv_net_set_act_scales sets the scales directly
  * (positive, finite) and packs the weights; nrv_net_get_act_scales reads them.
  * Both packers need parameters loaded (NRV_ERR_STATE otherwise) and are rerun
  * by nrv_net_set_params once scales exist.
  *
- * NRV_PREC_FP8_MIXED uses the same scales for levels 1-3 only: level 0 (the
- * input, e0a, e0b, up1, d0a, d0b) stays BF16 and the input is the BF16 packed
- * input.  All-E4M3 storage misses a 2e-2 max-abs bound against an FP64 forward
- * on full frames; the mixed network meets it. */
+ * NRV_PREC_FP8 uses the scales of levels 1-3 only: level 0 (the input, e0a, e0b,
+ * up1, d0a, d0b) stays BF16 and the input is the BF16 packed input.
+ * NRV_PREC_FP8_E4M3 uses all of them.  Both need the scales (NRV_ERR_STATE). */
 nrv_status nrv_net_calibrate(nrv_net* net, const void* d_netin_bf16, int n, int height, int width,
                              nrv_stream stream);
 nrv_status nrv_net_set_act_scales(nrv_net* net, const float* scale, int n, nrv_stream stream);
@@ -379,8 +385,13 @@ nrv_status nrv_l1_loss(const float* d_y, const float* d_t, int64_t n, float* d_l
  * entry point.
  *  - n may be at most NRV_L1_NOALLOC_MAX_ELEMENTS; larger n returns NRV_ERR_ARG
  *    with a message and launches nothing (use nrv_l1_loss then).
- *  - The first call on a device looks up the array's device address; make that
- *    first call before any stream capture on that device.
+ *  - The first call on a device looks up the array's device address (kept for the
+ *    process; a cudaDeviceReset of that device invalidates it, so do not call this
+ *    entry point after one).  Under CUDA's lazy module loading that first call also
+ *    loads the library's device code and this array onto the device, which is
+ *    device memory and work at first use: make one warm-up call at start-up, before
+ *    the frame loop and before any stream capture on that device.  Later calls
+ *    allocate nothing.
  *  - All calls share the array.  Each call overwrites every slot it reads, so
  *    nothing has to be cleared between calls, but calls whose kernels overlap on
  *    the GPU (different streams without ordering) race on it.
@@ -411,9 +422,11 @@ nrv_status nrv_train_step(nrv_net* net, float* d_params, float* d_grad, float* d
 /* Render n_views views end to end: rasterize, pack and shade every view, each
  * into d_rgb[i] ([H_i][W_i][3] FP32, caller-owned).  Views may have different
  * sizes.  The device work is captured once per (scene, net, sizes, prec) into a
- * CUDA graph and replayed on later calls; the G-buffers and network inputs live
- * in the net's workspace.  in_scale_inv is the FP8 input scale inverse (ignored
- * otherwise, FP8_MIXED included).  Errors: NRV_ERR_ARG, NRV_ERR_OOM, NRV_ERR_CUDA. */
+ * CUDA graph and replayed on later calls; a replay copies one 712-byte table of
+ * the views from host memory (stream-ordered, before the graph launch).  The
+ * G-buffers and network inputs live in the net's workspace.  in_scale_inv is the
+ * E4M3 input scale inverse for NRV_PREC_FP8_E4M3 (ignored otherwise,
+ * NRV_PREC_FP8 included).  Errors: NRV_ERR_ARG, NRV_ERR_OOM, NRV_ERR_CUDA. */
 nrv_status nrv_render_batch(nrv_scene* scene, nrv_net* net, const nrv_pack_desc* desc,
                             const nrv_view* views, int n_views, float* const* d_rgb,
                             nrv_prec prec, float in_scale_inv, nrv_stream stream);

@@ -42,7 +42,6 @@ unsigned* status_word() {
     return g_status;
 }
 
-void set_saved_input(const void* p);  // train.cu
 
 }  // namespace nrv
 
@@ -92,9 +91,9 @@ extern "C" int nrv_render_variants(int multi_view) {
     return nrv::visibility_variant_count(multi_view != 0);
 }
 extern "C" int nrv_pad8(int v) { return (v + 7) / 8 * 8; }
-extern "C" int nrv_netin_channels(nrv_prec p) { return p == NRV_PREC_FP8 ? 16 : 8; }
+extern "C" int nrv_netin_channels(nrv_prec p) { return p == NRV_PREC_FP8_E4M3 ? 16 : 8; }
 // precision of the packed network input (the mixed FP8 network reads a BF16 input)
-static nrv_prec netin_prec(nrv_prec p) { return p == NRV_PREC_FP8_MIXED ? NRV_PREC_BF16 : p; }
+static nrv_prec netin_prec(nrv_prec p) { return p == NRV_PREC_FP8 ? NRV_PREC_BF16 : p; }
 
 static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
@@ -240,7 +239,7 @@ extern "C" nrv_status nrv_pack(const nrv_gbuffer* gb, int h, int w, const nrv_pa
     if (!gb || !netin || !gb->d_depth || !gb->d_mask || !gb->d_attr)
         return fail(NRV_ERR_ARG, "pack needs depth, mask and attribute planes and an output");
     if (h < 1 || w < 1 || h > 16384 || w > 16384) return fail(NRV_ERR_ARG, "bad size");
-    if (prec < NRV_PREC_F32 || prec > NRV_PREC_FP8_MIXED) return fail(NRV_ERR_ARG, "bad precision");
+    if (prec < NRV_PREC_F32 || prec > NRV_PREC_FP8) return fail(NRV_ERR_ARG, "bad precision");
     if (!aligned(netin, 32)) return fail(NRV_ERR_ARG, "d_netin must be 32-byte aligned");
     NRV_TRY(check_pack(d, 8));
     ResolveArgs a;
@@ -384,7 +383,7 @@ static nrv_status check_shade(nrv_net* net, const void* in, int n, int h, int w,
     if (!net || !in || !rgb) return fail(NRV_ERR_ARG, "null argument");
     if (!net->has_params) return fail(NRV_ERR_STATE, "no parameters loaded");
     if (n < 1 || h < 1 || w < 1 || h > 16384 || w > 16384) return fail(NRV_ERR_ARG, "bad size");
-    if (prec < NRV_PREC_F32 || prec > NRV_PREC_FP8_MIXED) return fail(NRV_ERR_ARG, "bad precision");
+    if (prec < NRV_PREC_F32 || prec > NRV_PREC_FP8) return fail(NRV_ERR_ARG, "bad precision");
     if (!aligned(in, 32)) return fail(NRV_ERR_ARG, "d_netin must be 32-byte aligned");
     return NRV_OK;
 }
@@ -444,9 +443,9 @@ extern "C" nrv_status nrv_net_forward_train(nrv_net* net, const void* netin, int
                                             nrv_prec prec, float* rgb, nrv_stream stream) {
     clear_error();
     NRV_TRY(check_shade(net, netin, n, h, w, prec, rgb));
-    if (prec >= NRV_PREC_FP8) return fail(NRV_ERR_UNSUPPORTED, "training runs in F32 or BF16");
+    if (prec >= NRV_PREC_FP8_E4M3) return fail(NRV_ERR_UNSUPPORTED, "training runs in F32 or BF16");
     NRV_TRY(net_forward(net, netin, n, h, w, prec, rgb, (cudaStream_t)stream));
-    set_saved_input(netin);
+    net->saved_in = netin;
     net->saved = true;
     return NRV_OK;
 }
@@ -481,14 +480,14 @@ extern "C" nrv_status nrv_train_step(nrv_net* net, float* params, float* grad, f
     if (!params || !grad || !m || !v || !target || !loss || step < 1)
         return fail(NRV_ERR_ARG, "bad argument");
     NRV_TRY(check_shade(net, netin, n, h, w, prec, target));
-    if (prec >= NRV_PREC_FP8) return fail(NRV_ERR_UNSUPPORTED, "training runs in F32 or BF16");
+    if (prec >= NRV_PREC_FP8_E4M3) return fail(NRV_ERR_UNSUPPORTED, "training runs in F32 or BF16");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t nout = (size_t)n * h * w * 3;
     NRV_TRY(net->batch_ws.ensure(2 * nout * sizeof(float)));
     float* y = (float*)net->batch_ws.p;
     float* dy = y + nout;
     NRV_TRY(net_forward(net, netin, n, h, w, prec, y, st));
-    set_saved_input(netin);
+    net->saved_in = netin;
     net->saved = true;
     NRV_TRY(launch_l1(y, target, (int64_t)nout, loss, dy, st));
     NRV_TRY(net_backward(net, dy, grad, st));

@@ -197,7 +197,7 @@ nrv_status forward_fp8(Net* net, const uint8_t* netin, float* rgb, cudaStream_t 
     auto conv = [&](int l, const void* x1, int c1, const void* x2, int c2, int out,
                     int level) -> nrv_status {
         net->backend[l] = 1;
-        return tc_conv3(net, l, x1, c1, x2, c2, A(out), g, level, NRV_PREC_FP8, s, inv(out));
+        return tc_conv3(net, l, x1, c1, x2, c2, A(out), g, level, NRV_PREC_FP8_E4M3, s, inv(out));
     };
     auto pool = [&](int in, int out, int level_out) -> nrv_status {
         const int c = net->act_c[in];
@@ -208,7 +208,7 @@ nrv_status forward_fp8(Net* net, const uint8_t* netin, float* rgb, cudaStream_t 
     };
     auto up = [&](int l, int in, int out, int level_in) -> nrv_status {
         net->backend[l] = 1;
-        return tc_upconv(net, l, A(in), A(out), g, level_in, NRV_PREC_FP8, s, inv(out));
+        return tc_upconv(net, l, A(in), A(out), g, level_in, NRV_PREC_FP8_E4M3, s, inv(out));
     };
     // a 3x3 conv and the pool of its output to the next level (separate kernels: at level 0
     // the FP8 epilogue is the bottleneck and a fused pool measured slower)
@@ -239,7 +239,7 @@ nrv_status forward_fp8(Net* net, const uint8_t* netin, float* rgb, cudaStream_t 
         const TcHead head{P + Lh.woff, P + Lh.boff, rgb, net->geo_H, net->geo_W,
                           net->act_scale[1 + A_D0B], keep_acts};
         const nrv_status st = tc_conv3(net, L_D0B, A(A_D0A), 16, nullptr, 0, A(A_D0B), g, 0,
-                                       NRV_PREC_FP8, s, inv(A_D0B), &head);
+                                       NRV_PREC_FP8_E4M3, s, inv(A_D0B), &head);
         net->backend[L_D0B] = 1;
         if (st != NRV_ERR_UNSUPPORTED) return st;
         clear_error();
@@ -260,7 +260,7 @@ nrv_status forward_fp8_mixed(Net* net, const void* netin, float* rgb, cudaStream
     for (int l = 0; l < NUM_LAYERS; ++l) net->backend[l] = net->layers[l].kind == HEAD1 ? 0 : 1;
     auto conv8 = [&](int l, const void* x1, int c1, const void* x2, int c2, int out,
                      int level) -> nrv_status {
-        return tc_conv3(net, l, x1, c1, x2, c2, A(out), g, level, NRV_PREC_FP8, s, inv(out));
+        return tc_conv3(net, l, x1, c1, x2, c2, A(out), g, level, NRV_PREC_FP8_E4M3, s, inv(out));
     };
     auto pool8 = [&](int in, int out, int level_out) -> nrv_status {
         const int c = net->act_c[in];
@@ -270,7 +270,7 @@ nrv_status forward_fp8_mixed(Net* net, const void* netin, float* rgb, cudaStream
         return NRV_OK;
     };
     auto up8 = [&](int l, int in, int out, int level_in) -> nrv_status {
-        return tc_upconv(net, l, A(in), A(out), g, level_in, NRV_PREC_FP8, s, inv(out));
+        return tc_upconv(net, l, A(in), A(out), g, level_in, NRV_PREC_FP8_E4M3, s, inv(out));
     };
     // level 0 encoder in BF16 from the BF16 input
     NRV_TRY(tc_conv3(net, L_E0A, netin, net->c0p, nullptr, 0, A(A_E0A), g, 0, NRV_PREC_BF16, s));

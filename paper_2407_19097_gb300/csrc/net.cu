@@ -51,7 +51,7 @@ int net_layers(int c_in, Layer* L) {
 }
 
 // bytes per stored activation value (the mixed FP8 network keeps level 0 in BF16)
-size_t elem_size(nrv_prec p) { return p == NRV_PREC_F32 ? 4 : (p == NRV_PREC_FP8 ? 1 : 2); }
+size_t elem_size(nrv_prec p) { return p == NRV_PREC_F32 ? 4 : (p == NRV_PREC_FP8_E4M3 ? 1 : 2); }
 
 static inline int padded_cin(const Net* net, int l) {
     return l == L_E0A ? net->c0p : net->layers[l].cin;
@@ -312,7 +312,7 @@ nrv_status net_forward(Net* net, const void* netin, int n, int H, int W, nrv_pre
     if (prec == NRV_PREC_BF16)
         return forward_t<__nv_bfloat16>(net, (const __nv_bfloat16*)netin, rgb, s, true, prec,
                                         keep_acts);
-    if (prec == NRV_PREC_FP8_MIXED) return forward_fp8_mixed(net, netin, rgb, s);
+    if (prec == NRV_PREC_FP8) return forward_fp8_mixed(net, netin, rgb, s);
     return forward_fp8(net, (const uint8_t*)netin, rgb, s, keep_acts);
 }
 
@@ -356,7 +356,7 @@ nrv_status net_run_layer(Net* net, int l, const void* x1, const void* x2, int n,
     const bool up = L.kind == UPCONV2;
     int c1 = L.cin, c2 = 0;
     if (!up) {
-        c1 = l == L_E0A ? (prec == NRV_PREC_FP8 ? 16 : net->c0p) : L.cin;
+        c1 = l == L_E0A ? (prec == NRV_PREC_FP8_E4M3 ? 16 : net->c0p) : L.cin;
         if (l == L_D2A || l == L_D1A || l == L_D0A) {
             c1 = L.cin / 2;
             c2 = L.cin / 2;
@@ -378,7 +378,7 @@ nrv_status net_run_layer(Net* net, int l, const void* x1, const void* x2, int n,
                                  TView<const float>{(const float*)x2, c2}, c2,
                                  TView<float>{(float*)y, L.cout}, g, 0, true, s);
     }
-    if (prec != NRV_PREC_BF16 && prec != NRV_PREC_FP8)
+    if (prec != NRV_PREC_BF16 && prec != NRV_PREC_FP8_E4M3)
         return fail(NRV_ERR_UNSUPPORTED, "nrv_net_run_layer: unknown precision");
     const size_t es = elem_size(prec);
     const size_t rows_in = (size_t)n * h, rows_out = up ? 2 * rows_in : rows_in;
@@ -392,7 +392,7 @@ nrv_status net_run_layer(Net* net, int l, const void* x1, const void* x2, int n,
     NRV_TRY(relayout(x1, p1, rows_in, w, c1, es, true, s));
     if (c2) NRV_TRY(relayout(x2, p2, rows_in, w, c2, es, true, s));
     float inv_out = 1.0f;
-    if (prec == NRV_PREC_FP8) {
+    if (prec == NRV_PREC_FP8_E4M3) {
         int in1, in2, out;
         layer_scale_index(l, &in1, &in2, &out);
         inv_out = 1.0f / net->act_scale[out];

@@ -54,6 +54,7 @@ struct Net {
     nrv_prec act_prec = NRV_PREC_F32;
     int backend[NUM_LAYERS];   // 0 SIMT, 1 tcgen05, -1 not run (last forward)
     bool saved = false;      // a training forward's activations are in place
+    const void* saved_in = nullptr;   // that forward's input (the first layer's weight gradient reads it)
     // backward scratch
     DevBuf grads;            // gradient tensors
     DevBuf partial;          // wgrad partial sums

@@ -1127,12 +1127,11 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
     if (smem_for(nslot) > 215 * 1024) return fail(NRV_ERR_UNSUPPORTED, "tile does not fit in shared memory");
     // BF16: one row of read-ahead instead of two where that admits more CTAs per SM (more MMA
     // issuers; the level-1 layers gain 1.4% of a 1080p frame; FP8 layers measured slightly
-    // slower).  NRV_TC_SLOTS=0 keeps two rows everywhere.
-    static int slot_policy = -1;
-    if (slot_policy < 0) {
+    // slower).  NRV_TC_SLOTS=0 keeps two rows everywhere; it is read once per process.
+    static const int slot_policy = [] {
         const char* e = getenv("NRV_TC_SLOTS");
-        slot_policy = (e && e[0] == '0') ? 0 : 1;
-    }
+        return (e && e[0] == '0') ? 0 : 1;
+    }();
     if (slot_policy == 1 && !fp8 && nslot > c.rows + 1 &&
         occupancy(smem_for(c.rows + 1)) > occupancy(smem_for(nslot)))
         nslot = c.rows + 1;
@@ -1253,11 +1252,11 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
 nrv_status tc_conv3(const Net* net, int l, const void* x1, int c1, const void* x2, int c2, void* y,
                     const Geo& g, int level, nrv_prec prec, cudaStream_t s, float inv_out,
                     const TcHead* head, void* pool_y) {
-    if (prec != NRV_PREC_BF16 && prec != NRV_PREC_FP8)
+    if (prec != NRV_PREC_BF16 && prec != NRV_PREC_FP8_E4M3)
         return fail(NRV_ERR_UNSUPPORTED, "tensor-core path is BF16 or FP8");
     const Layer& L = net->layers[l];
     if (L.kind != CONV3) return fail(NRV_ERR_UNSUPPORTED, "not a 3x3 conv");
-    const int fp8 = prec == NRV_PREC_FP8;
+    const int fp8 = prec == NRV_PREC_FP8_E4M3;
     const TcLayerCfg& c = g_cfg[fp8][l];
     const uint8_t* w = (const uint8_t*)(fp8 ? net->wfp8.p : net->wbf16.p) + c.w_off;
     return tc_launch(net, c, w, (const float*)net->params.p + L.boff, 1, nullptr, L.cout, x1, c1,
@@ -1312,11 +1311,11 @@ nrv_status tc_updgrad(const Net* net, int l, const void* g, int g_ld, int g_off,
 
 nrv_status tc_upconv(const Net* net, int l, const void* x, void* y, const Geo& g, int level_in,
                      nrv_prec prec, cudaStream_t s, float inv_out) {
-    if (prec != NRV_PREC_BF16 && prec != NRV_PREC_FP8)
+    if (prec != NRV_PREC_BF16 && prec != NRV_PREC_FP8_E4M3)
         return fail(NRV_ERR_UNSUPPORTED, "tensor-core path is BF16 or FP8");
     const Layer& L = net->layers[l];
     if (L.kind != UPCONV2) return fail(NRV_ERR_UNSUPPORTED, "not a transposed conv");
-    const int fp8 = prec == NRV_PREC_FP8;
+    const int fp8 = prec == NRV_PREC_FP8_E4M3;
     const TcLayerCfg& c = g_cfg[fp8][l];
     const uint8_t* w = (const uint8_t*)(fp8 ? net->wfp8.p : net->wbf16.p) + c.w_off;
     return tc_launch(net, c, w, (const float*)net->params.p + L.boff, 0, nullptr, L.cout, x, L.cin,

@@ -676,8 +676,6 @@ struct Bwd {
 };
 
 // The training forward keeps its input pointer for the first layer's weight gradient.
-static const void* g_saved_netin = nullptr;
-void set_saved_input(const void* p) { g_saved_netin = p; }
 
 nrv_status net_layer_wgrad(Net* net, int l, const void* dy, const void* x1, const void* x2, int n,
                            int h, int w, nrv_prec prec, float* dgrad, cudaStream_t s) {
@@ -824,7 +822,7 @@ nrv_status net_backward(Net* net, const float* drgb, float* dparams, cudaStream_
             b.W1[l] = (float*)((char*)net->grads.p + off[2 * l]);
             b.W2[l] = (float*)((char*)net->grads.p + off[2 * l + 1]);
         }
-        return b.run(drgb, (const float*)g_saved_netin);
+        return b.run(drgb, (const float*)net->saved_in);
     }
     if (net->act_prec == NRV_PREC_BF16) {
         Bwd<__nv_bfloat16> b{net, s, g, dparams, {}, {}};
@@ -832,7 +830,7 @@ nrv_status net_backward(Net* net, const float* drgb, float* dparams, cudaStream_
             b.W1[l] = (__nv_bfloat16*)((char*)net->grads.p + off[2 * l]);
             b.W2[l] = (__nv_bfloat16*)((char*)net->grads.p + off[2 * l + 1]);
         }
-        return b.run(drgb, (const __nv_bfloat16*)g_saved_netin);
+        return b.run(drgb, (const __nv_bfloat16*)net->saved_in);
     }
     return fail(NRV_ERR_UNSUPPORTED, "backward is available for FP32 and BF16 only");
 }

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libnrv.so")
 
 NRV_OK, NRV_ERR_ARG, NRV_ERR_CUDA, NRV_ERR_OOM, NRV_ERR_TIMEOUT, NRV_ERR_UNSUPPORTED, NRV_ERR_STATE = range(7)
 NRV_F32, NRV_U32, NRV_U8X4 = 0, 1, 2
-PREC_F32, PREC_BF16, PREC_FP8, PREC_FP8_MIXED = 0, 1, 2, 3
+PREC_F32, PREC_BF16, PREC_FP8_E4M3, PREC_FP8 = 0, 1, 2, 3
 STATUS_NAMES = ["NRV_OK", "NRV_ERR_ARG", "NRV_ERR_CUDA", "NRV_ERR_OOM", "NRV_ERR_TIMEOUT",
                 "NRV_ERR_UNSUPPORTED", "NRV_ERR_STATE"]
 

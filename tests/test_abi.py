@@ -36,7 +36,7 @@ def test_host_side_queries(lib):
     from oracle import unet
     assert lib.nrv_version() == 1
     assert lib.nrv_pad8(540) == 544 and lib.nrv_pad8(1080) == 1080
-    assert lib.nrv_netin_channels(nrv.PREC_FP8) == 16 and lib.nrv_netin_channels(nrv.PREC_BF16) == 8
+    assert lib.nrv_netin_channels(nrv.PREC_FP8_E4M3) == 16 and lib.nrv_netin_channels(nrv.PREC_BF16) == 8
     # render-pass variants: brute force and culling ones, for one view and for batches
     assert lib.nrv_render_variants(0) >= 4 and lib.nrv_render_variants(1) >= 4
     for c0 in (3, 5, 6, 7):

@@ -77,7 +77,7 @@ def test_fp8_layer(layer, name, kind):
     oh, ow = (h, w) if kind == "conv3" else (2 * h, 2 * w)
     y = torch.empty((n, oh, ow, co), dtype=torch.uint8, device=dev)
     nrv.check(nrv.lib().nrv_net_run_layer(net.h, layer, nrv._ptr(x1), nrv._ptr(x2), n, h, w,
-                                          nrv.PREC_FP8, nrv._ptr(y), nrv._stream()))
+                                          nrv.PREC_FP8_E4M3, nrv._ptr(y), nrv._stream()))
     torch.cuda.synchronize()
     got = y.cpu().numpy()
     # the oracle quantises the weights the same way, in FP32
@@ -122,8 +122,11 @@ def test_fp8_layer(layer, name, kind):
     assert net.backends()[layer] == 1
 
 
-def test_fp8_network_frame_psnr():
-    """Calibrated on the frame itself (BF16), the FP8 network against the float64 oracle."""
+def test_fp8_e4m3_network_frame():
+    """NRV_PREC_FP8_E4M3 (every stored tensor E4M3), calibrated on the frame itself (BF16),
+    against the float64 oracle.  This mode is documented as below the reduced-precision bar
+    (max abs <= 2e-2): its 3-bit mantissas compound over the full-resolution layers.  The test
+    holds it to the PSNR half of the bar and to a max-abs error that stays within 0.15."""
     import torch
     from paper_2407_19097_gb300 import nrv
     sc = I.trajectory_scene(2000, 35, seed=2)
@@ -147,9 +150,9 @@ def test_fp8_network_frame_psnr():
     net.calibrate(xb, 1, H, W)
     s_in = net.act_scales()[0]
     x8 = torch.empty((H, W, 16), dtype=torch.uint8, device=dev)
-    nrv.pack(depth, mask, gattr, H, W, desc, nrv.PREC_FP8, x8, 1.0 / s_in)
+    nrv.pack(depth, mask, gattr, H, W, desc, nrv.PREC_FP8_E4M3, x8, 1.0 / s_in)
     out = torch.empty((H, W, 3), device=dev)
-    net.shade(x8, 1, H, W, nrv.PREC_FP8, out)
+    net.shade(x8, 1, H, W, nrv.PREC_FP8_E4M3, out)
     torch.cuda.synchronize()
     _, d, m, g = oracle.rasterize(sc, view)
     x = oracle.pack(d, m, g, sc.channels, ds, do, H, W, 8, 0).astype(np.float64)
@@ -157,17 +160,17 @@ def test_fp8_network_frame_psnr():
     got = out.cpu().numpy()
     p = psnr_range(got, ref)
     err = float(np.abs(got - ref).max())
-    print(f"FP8 frame vs float64: PSNR {p:.2f} dB, max abs {err:.4f}")
+    print(f"E4M3 frame vs float64: PSNR {p:.2f} dB, max abs {err:.4f}")
     assert all(b == 1 for b, k in zip(net.backends(), [l[1] for l in unet.layers(c0)]) if k != "conv1")
-    assert p >= 25.0
+    assert p >= 40.0 and err <= 0.15, (p, err)
 
 
-def test_fp8_mixed_network_frame_meets_target():
-    """The mixed network (E4M3 for levels 1-3, BF16 for level 0, from the BF16 input), calibrated
-    on the frame, against the float64 oracle: the accuracy bar of the method's reduced-precision
-    pass, PSNR >= 45 dB over the oracle's output range and max abs <= 2e-2.  (All-E4M3 storage
-    misses the max-abs bar: the errors of 3-bit mantissas compound over the full-resolution
-    layers.)"""
+def test_fp8_network_frame_meets_target():
+    """NRV_PREC_FP8, the FP8 network (E4M3 for levels 1-3, BF16 for level 0, from the BF16
+    input), calibrated on the frame, against the float64 oracle: the accuracy bar of the
+    method's reduced-precision pass, PSNR >= 45 dB over the oracle's output range and max abs
+    <= 2e-2.  (All-E4M3 storage misses the max-abs bar: the errors of 3-bit mantissas compound
+    over the full-resolution layers.)"""
     import torch
     from paper_2407_19097_gb300 import nrv
     sc = I.trajectory_scene(2000, 35, seed=2)
@@ -185,13 +188,13 @@ def test_fp8_mixed_network_frame_meets_target():
     nrv.rasterize(scene, [view], [key], [depth], [mask], [gattr])
     hn, wn = (H + 7) // 8 * 8, (W + 7) // 8 * 8
     xb = torch.zeros((hn, wn, 8), dtype=torch.bfloat16, device=dev)
-    nrv.pack(depth, mask, gattr, H, W, desc, nrv.PREC_FP8_MIXED, xb)
+    nrv.pack(depth, mask, gattr, H, W, desc, nrv.PREC_FP8, xb)
     flat = make_params(c0, seed=5, bias_sigma=0.05)
     net = nrv.Net(c0)
     net.set_params(torch.from_numpy(flat).to(dev))
     net.calibrate(xb, 1, H, W)
     out = torch.empty((H, W, 3), device=dev)
-    net.shade(xb, 1, H, W, nrv.PREC_FP8_MIXED, out)
+    net.shade(xb, 1, H, W, nrv.PREC_FP8, out)
     torch.cuda.synchronize()
     _, d, m, g = oracle.rasterize(sc, view)
     x = oracle.pack(d, m, g, sc.channels, ds, do, hn, wn, 8, 0).astype(np.float64)

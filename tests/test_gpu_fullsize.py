@@ -1,7 +1,8 @@
 """Full-size parity of the render and resolve passes (Sec. 3.2) on the benchmark workloads:
 keys and G-buffer planes bit-exact against the CPU oracle for whole frames, for every variant
 of the render pass (the launcher picks one by timing; each must give identical keys), plus the
-BF16 network on the full 1080p trajectory frame against the float64 oracle."""
+BF16 and FP8 networks on the full 1080p trajectory frame against the float64 oracle, element by
+element (PSNR over the oracle's output range >= 45 dB, max abs <= 2e-2)."""
 import os
 
 import numpy as np
@@ -88,3 +89,39 @@ def test_network_bf16_full_frame(trajectories):
     ref = unet.forward(x[None, :, :, :c0], unet.unflatten(flat, c0))[0]
     got = out.cpu().numpy()
     assert psnr_range(got, ref) >= 45.0 and np.abs(got - ref).max() <= 2e-2
+
+
+def test_network_fp8_full_frame(trajectories):
+    """NRV_PREC_FP8 (E4M3 levels 1-3, BF16 level 0) on the whole 350M-point 1080p frame through
+    nrv_render_batch, calibrated on that frame's BF16 input, against the float64 oracle."""
+    import torch
+    from paper_2407_19097_gb300 import nrv
+    sc = trajectories
+    view = I.fitted_view(sc, 1920, 1080)
+    scene = upload_scene(sc)
+    c0 = len(sc.channels) + 2
+    flat = make_params(c0, seed=1)
+    net = nrv.Net(c0)
+    net.set_params(torch.from_numpy(flat).to(torch_dev()))
+    ds, do = I.depth_normalisation(sc, view)
+    desc = nrv.make_pack_desc(sc.channels, ds, do)
+    H, W = 1080, 1920
+    key = torch.empty((H, W), dtype=torch.int64, device=torch_dev())
+    dpl = torch.empty((H, W), dtype=torch.int32, device=torch_dev())
+    msk = torch.empty((H, W), dtype=torch.uint8, device=torch_dev())
+    gat = torch.empty((sc.n_words, H, W), dtype=torch.int32, device=torch_dev())
+    nrv.rasterize(scene, [view], [key], [dpl], [msk], [gat])
+    xb = torch.empty((H, W, 8), dtype=torch.bfloat16, device=torch_dev())
+    nrv.pack(dpl, msk, gat, H, W, desc, nrv.PREC_BF16, xb)
+    net.calibrate(xb, 1, H, W)
+    out = torch.empty((H, W, 3), device=torch_dev())
+    nrv.render_batch(scene, net, desc, [view], [out], nrv.PREC_FP8)
+    torch.cuda.synchronize()
+    _, d, m, g = oracle.rasterize(sc, view)
+    x = oracle.pack(d, m, g, sc.channels, ds, do, H, W, 8, 0).astype(np.float64)
+    ref = unet.forward(x[None, :, :, :c0], unet.unflatten(flat, c0))[0][:H, :W]
+    got = out.cpu().numpy()
+    p, err = psnr_range(got, ref), float(np.abs(got - ref).max())
+    rel = float(np.abs(got - ref).max() / (ref.max() - ref.min()))
+    print(f"FP8 1080p frame vs float64: PSNR {p:.2f} dB, max abs {err:.4f}, relative {rel:.2e}")
+    assert p >= 45.0 and err <= 2e-2, (p, err)

@@ -146,9 +146,8 @@ def test_backward_bf16():
     where the kernels store them, FP32/FP64 accumulation inside each layer.  Across 18 layers
     the two accumulation orders round a few stored values differently and those flip ReLU
     decisions downstream, so the bound is statistical: <= 0.15 relative per tensor and a
-    cosine >= 0.99 for the whole gradient.  The 3x3 layers' weight gradients are checked
-    tightly one layer at a time in test_gpu_wgrad; their data gradients run on the forward's
-    tensor-core kernel, checked per layer in test_gpu_conv."""
+    cosine >= 0.99 for the whole gradient.  Every layer's weight and data gradients are
+    checked tightly one layer at a time in test_gpu_layer_grad.py."""
     from paper_2407_19097_gb300 import nrv
     _grad_case(nrv.PREC_BF16, 0.15)
 

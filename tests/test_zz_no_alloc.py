@@ -37,6 +37,27 @@ def test_noalloc_matches_allocating_entry_point():
         assert torch.equal(d_new, d_ref)
 
 
+def test_noalloc_allocates_nothing_after_warm_up():
+    """After one warm-up call (which may load the library's device code), calls leave the
+    device's free memory unchanged."""
+    import torch
+    from paper_2407_19097_gb300 import nrv
+    L = nrv.lib()
+    dev = torch.device("cuda:0")
+    n = 1 << 22
+    y = torch.randn(n, device=dev)
+    t = torch.randn(n, device=dev)
+    loss, dy = torch.zeros(1, device=dev), torch.empty_like(y)
+    assert _call(L.nrv_l1_loss_noalloc, y, t, n, loss, dy) == nrv.NRV_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(dev)
+    for _ in range(3):
+        assert _call(L.nrv_l1_loss_noalloc, y, t, n, loss, dy) == nrv.NRV_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    assert free1 == free0, (free0, free1)
+
+
 def test_noalloc_refuses_sizes_beyond_its_scratch():
     import torch
     from paper_2407_19097_gb300 import nrv
