@@ -146,6 +146,9 @@ def parse():
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--c5-steps", type=int, default=2000)
+    ap.add_argument("--sparsity", default="1,2,4,10",
+                    help="c5: subsampling factors of the sparsity study (Tab. 6)")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-fp8", action="store_true")
     ap.add_argument("--config", default="c3", choices=["c3", "c2", "c4", "c5", "train"],
@@ -480,93 +483,149 @@ def run_train(a):
 
 
 def run_c5(a):
-    """Training (Sec. 3.3): the U-Net learns to turn G-buffers of a trajectory scene into
-    Gaussian-splat targets (the CPU splatter standing in for the paper's Gaussian Renderer).
-    56 training and 8 held-out hemisphere views at 512^2, random 256^2 crops, batch 16, Adam
-    lr 1e-3, BF16 forward/backward.  Reports the step time and held-out PSNR/SSIM of the trained
-    network and of the method without it (transfer-function colour of the winning point)."""
+    """Training (Sec. 3.3) on config 3's scene (1M particles x 350 steps = 350M points): the
+    U-Net learns to turn G-buffers into Gaussian-splat targets (the CPU splatter standing in for
+    the paper's Gaussian Renderer), 56 training and 8 held-out hemisphere views at 512^2, random
+    256^2 crops, batch 16, Adam lr 1e-3, BF16 forward/backward, 2000 steps.  Reports the step
+    time; held-out PSNR/SSIM of the trained network and of the method without it (transfer-
+    function colour of the winning point); the trained weights' error in BF16, FP8 and all-E4M3
+    against the FP64 oracle; the same training with Eq. 1's reconstruction and TV terms; and
+    the sparsity study of Tab. 6 (inputs rendered from every S-th point, targets from all)."""
     import numpy as np
     import torch
     import nrv_inputs as I
     import oracle
-    from oracle import metrics
+    from oracle import metrics, unet
     from paper_2407_19097_gb300 import nrv
     dev = torch.device("cuda", 0)
-    steps = 2000
+    steps = a.c5_steps
     t0 = time.time()
-    sc = I.trajectory_scene(20000, 350, seed=2)
-    colours = I.point_colours(sc)
+    full = I.trajectory_scene(a.particles, a.steps_per_particle, seed=2)
+    colours = I.point_colours(full)
     size, n_views, n_train, crop, batch = 512, 64, 56, 256, 16
-    views = I.hemisphere_views(sc, n_views, size, size, seed=5)
-    c0 = len(sc.channels) + 2
-    scene = nrv.Scene(torch.from_numpy(sc.xyz).to(dev), torch.from_numpy(sc.attr.view(np.int32)).to(dev),
-                      sc.n_words)
-    ds, do = I.depth_normalisation(sc, views[0])
-    desc = nrv.make_pack_desc(sc.channels, ds, do)
-    X, targets, baselines = [], [], []
-    for v in views:
-        key = torch.empty((size, size), dtype=torch.int64, device=dev)
-        depth = torch.empty((size, size), dtype=torch.int32, device=dev)
-        mask = torch.empty((size, size), dtype=torch.uint8, device=dev)
-        gattr = torch.empty((sc.n_words, size, size), dtype=torch.int32, device=dev)
-        nrv.rasterize(scene, [v], [key], [depth], [mask], [gattr])
-        x = torch.empty((size, size, 8), dtype=torch.bfloat16, device=dev)
-        nrv.pack(depth, mask, gattr, size, size, desc, nrv.PREC_BF16, x)
-        X.append(x)
-        targets.append(np.clip(oracle.splat(sc.xyz, v, colours), 0.0, 1.0).astype(np.float32))
-        k = key.cpu().numpy().view(np.uint64)
-        hit = k != np.uint64(0xFFFFFFFFFFFFFFFF)
-        base = np.zeros((size, size, 3), np.float32)
-        base[hit] = colours[(k[hit] & np.uint64(0xFFFFFFFF)).astype(np.int64)]
-        baselines.append(base)
-    X = torch.stack(X)
+    views = I.hemisphere_views(full, n_views, size, size, seed=5)
+    gen_s = time.time() - t0
+    t0 = time.time()
+    targets = [np.clip(oracle.splat(full.xyz, v, colours), 0.0, 1.0).astype(np.float32) for v in views]
+    splat_s = time.time() - t0
     T = torch.from_numpy(np.stack(targets)).to(dev)
-    prep_s = time.time() - t0
-    net = nrv.Net(c0)
-    p = torch.empty((nrv.param_count(c0),), device=dev)
-    net.init_params(1, p)
-    g, m, vv = torch.zeros_like(p), torch.zeros_like(p), torch.zeros_like(p)
-    loss = torch.zeros(1, device=dev)
-    xb = torch.empty((batch, crop, crop, 8), dtype=torch.bfloat16, device=dev)
-    tb = torch.empty((batch, crop, crop, 3), dtype=torch.float32, device=dev)
-    crops = [I.random_crops(9, s, batch, n_train, size, size, crop) for s in range(steps)]
+    c0 = len(full.channels) + 2
+    held = range(n_train, n_views)
     stream = torch.cuda.current_stream()
+    crops = [I.random_crops(9, s, batch, n_train, size, size, crop) for s in range(steps)]
 
-    def fill(s):
-        for b, (vi, y0, x0) in enumerate(crops[s]):
-            xb[b].copy_(X[vi, y0:y0 + crop, x0:x0 + crop])
-            tb[b].copy_(T[vi, y0:y0 + crop, x0:x0 + crop])
+    def inputs(sc, cols):
+        """G-buffers of every view packed into BF16 network inputs, the colour (cols) of each
+        pixel's winning point (the method without the network), a 1080p frame's time and the
+        scene handle."""
+        scene = nrv.Scene(torch.from_numpy(sc.xyz).to(dev), torch.from_numpy(sc.attr.view(np.int32)).to(dev),
+                          sc.n_words)
+        ds, do = I.depth_normalisation(full, views[0])
+        desc = nrv.make_pack_desc(full.channels, ds, do)
+        X, base = [], []
+        for v in views:
+            key = torch.empty((size, size), dtype=torch.int64, device=dev)
+            x = torch.empty((size, size, 8), dtype=torch.bfloat16, device=dev)
+            nrv.rasterize(scene, [v], [key])
+            nrv.resolve_pack(scene, v, key, desc, nrv.PREC_BF16, x)
+            X.append(x)
+            k = key.cpu().numpy().view(np.uint64)
+            hit = k != np.uint64(0xFFFFFFFFFFFFFFFF)
+            b = np.zeros((size, size, 3), np.float32)
+            b[hit] = cols[(k[hit] & np.uint64(0xFFFFFFFF)).astype(np.int64)]
+            base.append(b)
+        frame_ms = None
+        view = I.fitted_view(full, 1920, 1080)
+        net = nrv.Net(c0)
+        p = torch.empty((nrv.param_count(c0),), device=dev)
+        net.init_params(1, p)
+        rgb = torch.empty((1080, 1920, 3), device=dev)
+        frame_ms = _events_ms(lambda: nrv.render_batch(scene, net, desc, [view], [rgb], nrv.PREC_BF16),
+                              20, 3, stream)
+        return torch.stack(X), base, frame_ms, scene, desc
 
-    # crops are gathered outside the timed region; the step is forward, loss, backward, Adam
-    step_ms, losses = [], []
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for s in range(steps):
-        fill(s)
-        if s >= 10:
-            e0.record(stream)
-        net.train_step(p, g, m, vv, s + 1, 1e-3, xb, tb, batch, crop, crop, nrv.PREC_BF16, loss)
-        if s >= 10:
-            e1.record(stream)
-            torch.cuda.synchronize()
-            step_ms.append(e0.elapsed_time(e1))
-        if (s + 1) % 200 == 0:
-            losses.append(float(loss.item()))
-    out = torch.empty((n_views - n_train, size, size, 3), device=dev)
-    net.shade(X[n_train:].contiguous(), n_views - n_train, size, size, nrv.PREC_BF16, out)
-    torch.cuda.synchronize()
-    y = np.clip(out.cpu().numpy(), 0.0, 1.0)
-    held = range(n_views - n_train)
+    def train(X, loss_w):
+        net = nrv.Net(c0)
+        p = torch.empty((nrv.param_count(c0),), device=dev)
+        net.init_params(1, p)
+        net.set_loss(loss_w)
+        g, m, vv = torch.zeros_like(p), torch.zeros_like(p), torch.zeros_like(p)
+        loss = torch.zeros(1, device=dev)
+        xb = torch.empty((batch, crop, crop, 8), dtype=torch.bfloat16, device=dev)
+        tb = torch.empty((batch, crop, crop, 3), dtype=torch.float32, device=dev)
+        step_ms = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for s_ in range(steps):
+            for b, (vi, y0, x0) in enumerate(crops[s_]):   # crops gathered outside the timed step
+                xb[b].copy_(X[vi, y0:y0 + crop, x0:x0 + crop])
+                tb[b].copy_(T[vi, y0:y0 + crop, x0:x0 + crop])
+            if s_ >= 10:
+                e0.record(stream)
+            net.train_step(p, g, m, vv, s_ + 1, 1e-3, xb, tb, batch, crop, crop, nrv.PREC_BF16, loss)
+            if s_ >= 10:
+                e1.record(stream)
+                torch.cuda.synchronize()
+                step_ms.append(e0.elapsed_time(e1))
+        out = torch.empty((n_views - n_train, size, size, 3), device=dev)
+        net.shade(X[n_train:].contiguous(), n_views - n_train, size, size, nrv.PREC_BF16, out)
+        torch.cuda.synchronize()
+        return net, p, np.clip(out.cpu().numpy(), 0.0, 1.0), float(np.median(step_ms)), float(loss.item())
+
+    def quality(imgs, base):
+        return {"network_psnr_db": float(np.mean([metrics.psnr(imgs[i], targets[n_train + i]) for i in range(len(held))])),
+                "network_ssim": float(np.mean([metrics.ssim(imgs[i], targets[n_train + i]) for i in range(len(held))])),
+                "rasterizer_alone_psnr_db": float(np.mean([metrics.psnr(base[n_train + i], targets[n_train + i]) for i in range(len(held))])),
+                "rasterizer_alone_ssim": float(np.mean([metrics.ssim(base[n_train + i], targets[n_train + i]) for i in range(len(held))]))}
+
+    X, base, frame_ms, scene_full, desc_full = inputs(full, colours)
+    net, p, imgs, step_ms, last_loss = train(X, (1.0, 0.0, 0.0))
     line = {"config": "c5", "metric": "training step time (ms) and held-out PSNR vs splat targets",
-            "workload": f"trajectories 20000x350 = {sc.n} points, {n_train}+{n_views - n_train} views "
-                        f"at {size}^2, {crop}^2 crops, batch {batch}, {steps} steps",
-            "data": "synthetic", "value": float(np.median(step_ms)), "unit": "ms/step",
-            "higher_is_better": False, "precision": "bf16",
-            "pixels_per_step": batch * crop * crop,
-            "held_out_psnr_db": {"network": float(np.mean([metrics.psnr(y[i], targets[n_train + i]) for i in held])),
-                                 "rasterizer_alone": float(np.mean([metrics.psnr(baselines[n_train + i], targets[n_train + i]) for i in held]))},
-            "held_out_ssim": {"network": float(np.mean([metrics.ssim(y[i], targets[n_train + i]) for i in held])),
-                              "rasterizer_alone": float(np.mean([metrics.ssim(baselines[n_train + i], targets[n_train + i]) for i in held]))},
-            "loss_every_200_steps": losses, "prep_s": prep_s}
+            "workload": f"trajectories {a.particles}x{a.steps_per_particle} = {full.n} points, "
+                        f"{n_train}+{n_views - n_train} hemisphere views at {size}^2, {crop}^2 crops, "
+                        f"batch {batch}, {steps} steps",
+            "data": "synthetic", "value": step_ms, "unit": "ms/step", "higher_is_better": False,
+            "precision": "bf16", "pixels_per_step": batch * crop * crop, "loss": "l1",
+            "held_out": quality(imgs, base), "final_loss": last_loss,
+            "scene_gen_s": gen_s, "splat_targets_s": splat_s, "cpu_cores": os.cpu_count()}
+    # the trained weights in every precision against the FP64 oracle (held-out views)
+    xin = X[n_train:].contiguous()
+    xf = xin.float().cpu().numpy().astype(np.float64)
+    flat = p.cpu().numpy()
+    ref = unet.forward(xf[..., :c0], unet.unflatten(flat, c0))
+    net.calibrate(X[:8].contiguous(), 8, size, size)
+    inv8 = 1.0 / net.act_scales()[0]
+    prec_err = {}
+    for name, pr in (("bf16", nrv.PREC_BF16), ("fp8", nrv.PREC_FP8), ("fp8_e4m3", nrv.PREC_FP8_E4M3)):
+        out = torch.empty((n_views - n_train, size, size, 3), device=dev)
+        x_in = xin
+        if pr == nrv.PREC_FP8_E4M3:
+            x_in = torch.empty((n_views - n_train, size, size, 16), dtype=torch.uint8, device=dev)
+            for i in range(n_views - n_train):
+                key = torch.empty((size, size), dtype=torch.int64, device=dev)
+                nrv.rasterize(scene_full, [views[n_train + i]], [key])
+                nrv.resolve_pack(scene_full, views[n_train + i], key, desc_full, pr, x_in[i], inv8)
+        net.shade(x_in, n_views - n_train, size, size, pr, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().astype(np.float64)
+        r = float(ref.max() - ref.min())
+        mse = float(np.mean((got - ref) ** 2))
+        prec_err[name] = {"psnr_db": 10 * np.log10(r * r / mse) if mse > 0 else None,
+                          "max_abs": float(np.abs(got - ref).max()),
+                          "max_rel_to_range": float(np.abs(got - ref).max() / r)}
+    line["trained_weights_vs_fp64"] = prec_err
+    # Eq. 1 without its perceptual term: L2 reconstruction + total variation
+    _, _, imgs2, step2, _ = train(X, (0.0, 1.0, 0.01))
+    line["loss_l2_tv"] = {"weights": {"l2": 1.0, "tv": 0.01}, "step_ms": step2, **quality(imgs2, base)}
+    # sparsity study (Tab. 6): inputs from every S-th point, targets from the whole scene
+    sparsity = {"1": {"frame_1080p_ms": frame_ms, **line["held_out"]}}
+    for S in [int(v) for v in a.sparsity.split(",") if v and int(v) > 1]:
+        sel = np.arange(0, full.n, S)
+        sub = full.subset(sel)
+        Xs, base_s, fms, sc_s, _ = inputs(sub, colours[sel])
+        _, _, imgs_s, _, _ = train(Xs, (1.0, 0.0, 0.0))
+        sparsity[str(S)] = {"points": sub.n, "frame_1080p_ms": fms, **quality(imgs_s, base_s)}
+        del Xs, sc_s
+    line["sparsity"] = sparsity
     print(json.dumps(line), flush=True)
 
 def main():

@@ -55,8 +55,24 @@ typedef enum {
     NRV_ERR_STATE = 6         /* call out of order (e.g. backward before forward) */
 } nrv_status;
 
-/* Attribute word formats (Sec. 3.2: "formats uint8 and fp32"). */
-typedef enum { NRV_F32 = 0, NRV_U32 = 1, NRV_U8X4 = 2 } nrv_fmt;
+/* Attribute word formats (Sec. 3.2: "formats uint8 and fp32"), and the derived
+ * channels the resolve can compute from the winning point (Sec. 3.2 and Sec. 4.5):
+ *  NRV_VEL2D_X, NRV_VEL2D_Y, NRV_VEL2D_ANGLE, NRV_VEL2D_MAG -- "Vel2D" (Sec. 4.5,
+ *    Tab. 7): the point's velocity v = (word w, w+1, w+2 as FP32) projected by the
+ *    camera.  With s(p) = ((c.x/c.w + 1) W/2, (1 - c.y/c.w) H/2), c = viewproj (p, 1),
+ *    v' = (ds/dp) v in pixels per unit time (x right, y down), the channels are
+ *    v'.x, v'.y, atan2(v'.y, v'.x) in (-pi, pi] and |v'|;
+ *  NRV_SPLAT_RADIUS -- the projected splat radius (Sec. 3.2, terrain): a world
+ *    radius r (word w as FP32) in pixels, r (H/2) |viewproj row 1 (x, y, z)| / c.w,
+ *    the pixel radius of a camera-facing disc for a perspective camera.
+ * Derived channels are computed in FP32 (not bit-exact: within about 1e-5 of an FP64
+ * evaluation) and need the point's position and the camera, so only the passes that
+ * resolve from the key image take them (nrv_resolve_pack, nrv_render_batch). */
+typedef enum {
+    NRV_F32 = 0, NRV_U32 = 1, NRV_U8X4 = 2,
+    NRV_VEL2D_X = 3, NRV_VEL2D_Y = 4, NRV_VEL2D_ANGLE = 5, NRV_VEL2D_MAG = 6,
+    NRV_SPLAT_RADIUS = 7
+} nrv_fmt;
 
 /* Network precision.  Accumulation is FP32 in every mode (the paper's App. B quantises to
  * fp16; the reduced-precision modes here go to BF16 and 8 bits).
@@ -110,6 +126,12 @@ typedef struct {
     int stride_words;        /* record stride in 32-bit words: 1, 2, 4 or 8 */
     int n_words;             /* K: record words copied to the G-buffer, 1..stride_words
                                 (Sec. 3.2 tests up to 8 attributes) */
+    uint64_t index_base;     /* global index of the first point (0 for a whole scene): key
+                                low words are index_base + i, index_base + N < 2^32.  A
+                                shard of a larger scene takes its first point's index, so
+                                keys rendered from several shards can be combined by a
+                                minimum, and the resolve of a shard treats winners outside
+                                its own index range as empty pixels */
 } nrv_scene_desc;
 
 typedef struct nrv_scene nrv_scene;
@@ -165,9 +187,25 @@ typedef struct {
 nrv_status nrv_rasterize(nrv_scene* scene, const nrv_view* views, int n_views,
                          const nrv_gbuffer* gbufs, nrv_stream stream);
 
+/* Resolve pass alone (Sec. 3.2) from a key image d_key ([H][W], e.g. combined from
+ * several shards): gbuf's d_depth, d_mask and d_attr planes (any may be NULL) get the
+ * winner's depth bits, coverage and record words where the winner belongs to this
+ * scene (index_base <= index < index_base + N) and zeros elsewhere, so the planes of
+ * all shards add up to those of the whole scene.  gbuf->d_key is ignored.
+ * Errors: NRV_ERR_ARG. */
+nrv_status nrv_resolve(nrv_scene* scene, const nrv_view* view, const uint64_t* d_key,
+                       const nrv_gbuffer* gbuf, nrv_stream stream);
+
+/* Flip bit 63 of n keys in place (an involution).  It maps the unsigned order of keys
+ * onto the signed order of int64 -- the empty key ~0 becomes INT64_MAX -- so that a
+ * signed 64-bit minimum (a collective's MIN on int64) combines key images of shards.
+ * No counterpart in the paper.  Errors: NRV_ERR_ARG. */
+nrv_status nrv_keys_flip_sign(uint64_t* d_key, int64_t n, nrv_stream stream);
+
 /* How to turn one view's G-buffer into the network input ("channel-wise
  * processing" of the rasterizer output, Sec. 4.5 / Tab. 3).  Channel j < n_channels
- * reads G-buffer word word[j] as f32, u32 or byte comp[j] of a u8x4 word and
+ * reads G-buffer word word[j] as f32, u32 or byte comp[j] of a u8x4 word (or, for a
+ * derived format, computes its value from the winning point, see nrv_fmt) and
  * becomes f = float(v) * scale[j] + offset[j] (separate FP32 multiply and add).
  * Then comes depth (float of the depth plane, same affine map with depth_scale
  * and depth_offset), then coverage (1.0), then zero padding.  Empty pixels are
@@ -192,9 +230,19 @@ int nrv_netin_channels(nrv_prec prec);
 /* Pack one view's G-buffer (d_depth, d_mask and d_attr required) into the
  * network input d_netin: NHWC [Hn][Wn][C] of float, bf16 (round to nearest
  * even) or e4m3 (of f * in_scale_inv, saturating, round to nearest even).
- * Errors: NRV_ERR_ARG. */
+ * Errors: NRV_ERR_ARG (also for derived channel formats: use nrv_resolve_pack). */
 nrv_status nrv_pack(const nrv_gbuffer* gbuf, int height, int width, const nrv_pack_desc* desc,
                     nrv_prec prec, float in_scale_inv, void* d_netin, nrv_stream stream);
+
+/* Resolve pass fused with the packing (Sec. 3.2 resolve + Sec. 4.5 channel
+ * processing): from one view's key image d_key ([H][W], as written by
+ * nrv_rasterize for that view) straight to the network input d_netin (layout of
+ * nrv_pack), gathering the winner's record -- and, for derived channels, its
+ * position -- from the scene.  The same pass nrv_render_batch runs.
+ * Errors: NRV_ERR_ARG (null, misaligned, a channel reading past the record). */
+nrv_status nrv_resolve_pack(nrv_scene* scene, const nrv_view* view, const uint64_t* d_key,
+                            const nrv_pack_desc* desc, nrv_prec prec, float in_scale_inv,
+                            void* d_netin, nrv_stream stream);
 
 /* --------------------------------------------------------------------------
  * Network (post-processing U-Net, Sec. 3.3)
@@ -401,14 +449,32 @@ nrv_status nrv_l1_loss(const float* d_y, const float* d_t, int64_t n, float* d_l
 nrv_status nrv_l1_loss_noalloc(const float* d_y, const float* d_t, int64_t n, float* d_loss,
                                float* d_dy, nrv_stream stream);
 
+/* Reconstruction and total-variation loss (Eq. 1 without its perceptual term, which
+ * needs pretrained VGG weights) on RGB images y, t [n][height][width][3] FP32:
+ *   loss = l1 mean|y - t| + l2 mean (y - t)^2
+ *        + tv (mean over horizontal neighbour pairs |y(x+1) - y(x)|
+ *              + mean over vertical neighbour pairs |y(y+1) - y(y)|),
+ * every mean over its own count (all images and channels); the TV term is the
+ * anisotropic L1 total variation of the output alone.  d_loss[0] receives the loss,
+ * d_dy (if not NULL) its gradient with sign(0) = 0.  Deterministic.
+ * nrv_net_set_loss picks the weights nrv_train_step uses (default l1 = 1, l2 = tv = 0,
+ * the L1 loss).  Errors: NRV_ERR_ARG (null, bad size, negative or non-finite weight). */
+typedef struct {
+    float l1, l2, tv;
+} nrv_loss_weights;
+nrv_status nrv_recon_loss(const float* d_y, const float* d_t, int n, int height, int width,
+                          const nrv_loss_weights* weights, float* d_loss, float* d_dy,
+                          nrv_stream stream);
+nrv_status nrv_net_set_loss(nrv_net* net, const nrv_loss_weights* weights);
+
 /* Adam (Kingma & Ba; Sec. 3.3 uses it with lr 1e-3), no weight decay, step >= 1:
  * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
  * p -= lr * (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps), all FP32. */
 nrv_status nrv_adam_step(float* d_params, const float* d_grad, float* d_m, float* d_v, int64_t n,
                          int step, float lr, float beta1, float beta2, float eps, nrv_stream stream);
 
-/* One training step on a batch: forward (saving activations), L1 loss against
- * d_target [n][height][width][3], backward, Adam update of d_params with
+/* One training step on a batch: forward (saving activations), the loss chosen by
+ * nrv_net_set_loss (L1 unless set) against d_target [n][height][width][3], backward, Adam update of d_params with
  * moments d_m, d_v (all flat FP32, parameter layout), then the packed weights
  * are re-derived.  d_loss[0] receives the loss.  prec: F32 or BF16. */
 nrv_status nrv_train_step(nrv_net* net, float* d_params, float* d_grad, float* d_m, float* d_v,
@@ -439,6 +505,23 @@ nrv_status nrv_render_batch(nrv_scene* scene, nrv_net* net, const nrv_pack_desc*
  * recorded calls.  Returns the number of values written (<= cap, at most 4). */
 nrv_status nrv_set_profiling(int on);
 int nrv_get_timings(float* ms, int cap);
+
+/* Tuned launch choices.  The render pass picks one of its variants (per view-count
+ * class and point-count class) and the tensor-core convolution its row read-ahead and
+ * CTAs per SM (per layer, shape and precision) by timing the candidates on the real
+ * data at the first uncaptured launch that needs the choice; every candidate computes
+ * the same result.  nrv_tune_save writes the choices made or loaded so far to a text
+ * file, nrv_tune_load reads one back (a later process then skips the timing); when the
+ * environment variable NRV_TUNE_CACHE names an existing file, the library loads it at
+ * its first lookup.  Format: '#' comment lines and one choice per line,
+ * "<key> = <value>", the key free text ("render multi=1 log2n=27", "conv ...") and
+ * the value a non-negative integer.  nrv_tune_count gives the number of choices held,
+ * nrv_tune_timings the number of tuning runs this process made.  No counterpart in
+ * the paper.  Errors: NRV_ERR_ARG (null path, I/O, a malformed line). */
+nrv_status nrv_tune_load(const char* path);
+nrv_status nrv_tune_save(const char* path);
+int nrv_tune_count(void);
+uint64_t nrv_tune_timings(void);
 
 /* Reads and clears the library's device status word (bounded waits that gave
  * up, bad indices caught by device checks).  Synchronises the stream. */

@@ -143,3 +143,42 @@ def splat(xyz: np.ndarray, view, colour: np.ndarray, sigma: float = 1.5, alpha: 
     _L().oracle_splat(_p(xyz), xyz.shape[0], _p(m), view.width, view.height, float(view.znear),
                       float(view.zfar), _p(colour), float(sigma), float(alpha), _p(out))
     return out
+
+
+# Derived channel formats of the library's pack descriptor (Sec. 4.5 "Vel2D", Sec. 3.2 splat
+# radius); the values follow include/nrv.h's numbering of nrv_fmt.
+VEL2D_X, VEL2D_Y, VEL2D_ANGLE, VEL2D_MAG, SPLAT_RADIUS = 3, 4, 5, 6, 7
+
+
+def derived_channel(key: np.ndarray, xyz: np.ndarray, attr: np.ndarray, view, fmt: int,
+                    word: int) -> np.ndarray:
+    """FP64 value of one derived channel at every pixel of a key image (NaN where empty).
+
+    Vel2D (Sec. 4.5): the velocity v (record words word..word+2, FP32) of the winning point p,
+    perspective-projected: v' = J v with J the Jacobian of the screen map
+    s(p) = ((c_x / c_w + 1) W/2, (1 - c_y / c_w) H/2), c = M (p, 1), so
+        J_x = (W/2) (M_0 c_w - c_x M_3) / c_w^2,   J_y = -(H/2) (M_1 c_w - c_y M_3) / c_w^2
+    (M_r the first three entries of row r); the channels are v'_x, v'_y, the angle atan2(v'_y,
+    v'_x) of v' in the image plane and |v'|.  Splat radius (Sec. 3.2, terrain): the world
+    radius r (record word `word`, FP32) in pixels, r (H/2) |M_1| / c_w."""
+    key = np.asarray(key, np.uint64)
+    hit = key != np.uint64(0xFFFFFFFFFFFFFFFF)
+    idx = (key[hit] & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    M = np.asarray(view.viewproj, np.float32).astype(np.float64).reshape(4, 4)
+    p = np.asarray(xyz, np.float32)[idx].astype(np.float64)
+    rec = np.asarray(attr, np.uint32)[idx]
+    ph = np.concatenate([p, np.ones((len(p), 1))], 1)
+    c = ph @ M.T
+    cx, cy, cw = c[:, 0], c[:, 1], c[:, 3]
+    out = np.full(key.shape, np.nan)
+    if fmt == SPLAT_RADIUS:
+        r = rec[:, word].view(np.float32).astype(np.float64)
+        out[hit] = r * (view.height / 2.0) * np.linalg.norm(M[1, :3]) / cw
+        return out
+    v = np.ascontiguousarray(rec[:, word:word + 3]).view(np.float32).astype(np.float64)
+    jx = (view.width / 2.0) * (M[0, :3][None] * cw[:, None] - cx[:, None] * M[3, :3][None]) / cw[:, None] ** 2
+    jy = -(view.height / 2.0) * (M[1, :3][None] * cw[:, None] - cy[:, None] * M[3, :3][None]) / cw[:, None] ** 2
+    vx, vy = (jx * v).sum(1), (jy * v).sum(1)
+    out[hit] = {VEL2D_X: vx, VEL2D_Y: vy, VEL2D_ANGLE: np.arctan2(vy, vx),
+                VEL2D_MAG: np.hypot(vx, vy)}[fmt]
+    return out

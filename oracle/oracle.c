@@ -155,71 +155,142 @@ void oracle_pack(const uint32_t* depth, const uint8_t* mask, const uint32_t* gat
  * centre p = (px + 0.5, py + 0.5), walking that order over the Gaussians with
  * |p - mu|^2 <= (3 sigma)^2:  a = alpha * exp(-|p - mu|^2 / (2 sigma^2)),
  * C += T * a * c, T *= (1 - a), stopping once T < 1e-4.  Black background.
- * Double precision; tiles of 16 x 16 pixels are independent (OpenMP).
+ * Double precision.
+ *
+ * The steps run on all cores (OpenMP) without changing the result:
+ *  1. project and keep the points near the image, in index order (each thread
+ *     counts its contiguous block, then writes it at its prefix offset);
+ *  2. sort by (w, index): w > 0, so the key (bits(w) << 32) | j, j the kept
+ *     point's position in index order, orders like (w, index); an LSD radix
+ *     sort, eight passes of eight bits, stable in every pass;
+ *  3. bin the sorted Gaussians into every 16 x 16 tile their 3-sigma disc may
+ *     touch, each tile's list in sorted order (threads take contiguous runs
+ *     of the sorted order and write them at per-(tile, thread) prefix offsets);
+ *  4. composite each tile's pixels from its list (tiles are independent).
  * ------------------------------------------------------------------------- */
-typedef struct { float w; uint32_t i; double sx, sy; } splat_t;
+#include <omp.h>
 
-static int splat_cmp(const void* a, const void* b) {
-    const splat_t* x = (const splat_t*)a;
-    const splat_t* y = (const splat_t*)b;
-    if (x->w < y->w) return -1;
-    if (x->w > y->w) return 1;
-    return (x->i > y->i) - (x->i < y->i);
-}
+typedef struct { uint32_t i; double sx, sy; } splat_t;
 
 void oracle_splat(const float* xyz, uint64_t n, const float* M, int W, int H, float znear,
                   float zfar, const float* colour, double sigma, double alpha, double* out) {
     const double rad = 3.0 * sigma, rad2 = rad * rad;
     const float hw = 0.5f * (float)W, hh = 0.5f * (float)H;
+    const int nth = omp_get_max_threads();
+    /* 1. project and filter, keeping index order */
+    uint64_t* cnt_th = (uint64_t*)calloc((size_t)nth + 1, sizeof(uint64_t));
     splat_t* s = (splat_t*)malloc(sizeof(splat_t) * (size_t)(n > 0 ? n : 1));
-    uint64_t m = 0;
-    for (uint64_t i = 0; i < n; ++i) {
-        float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
-        float cx = ((M[0] * x + M[1] * y) + M[2] * z) + M[3];
-        float cy = ((M[4] * x + M[5] * y) + M[6] * z) + M[7];
-        float cw = ((M[12] * x + M[13] * y) + M[14] * z) + M[15];
-        if (!(cw >= znear && cw <= zfar)) continue;
-        float nx = cx / cw, ny = cy / cw;
-        float sx = (nx + 1.0f) * hw, sy = (1.0f - ny) * hh;
-        if (!((double)sx >= -rad && (double)sx < W + rad && (double)sy >= -rad && (double)sy < H + rad))
-            continue;
-        s[m].w = cw; s[m].i = (uint32_t)i; s[m].sx = sx; s[m].sy = sy; ++m;
+    float* wv = (float*)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    for (int pass = 0; pass < 2; ++pass) {
+#pragma omp parallel num_threads(nth)
+        {
+            const int t = omp_get_thread_num();
+            const uint64_t lo = n * (uint64_t)t / (uint64_t)nth, hi = n * (uint64_t)(t + 1) / (uint64_t)nth;
+            uint64_t m = pass ? cnt_th[t] : 0;
+            for (uint64_t i = lo; i < hi; ++i) {
+                float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+                float cx = ((M[0] * x + M[1] * y) + M[2] * z) + M[3];
+                float cy = ((M[4] * x + M[5] * y) + M[6] * z) + M[7];
+                float cw = ((M[12] * x + M[13] * y) + M[14] * z) + M[15];
+                if (!(cw >= znear && cw <= zfar)) continue;
+                float nx = cx / cw, ny = cy / cw;
+                float sx = (nx + 1.0f) * hw, sy = (1.0f - ny) * hh;
+                if (!((double)sx >= -rad && (double)sx < W + rad && (double)sy >= -rad &&
+                      (double)sy < H + rad))
+                    continue;
+                if (pass) {
+                    s[m].i = (uint32_t)i; s[m].sx = sx; s[m].sy = sy; wv[m] = cw;
+                }
+                ++m;
+            }
+            if (!pass) cnt_th[t + 1] = m;
+        }
+        if (!pass)
+            for (int t = 0; t < nth; ++t) cnt_th[t + 1] += cnt_th[t];
     }
-    qsort(s, (size_t)m, sizeof(splat_t), splat_cmp);
+    const uint64_t m = cnt_th[nth];
+    /* 2. sort by (w, index) */
+    uint64_t* key = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(m > 0 ? m : 1));
+    uint64_t* tmp = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(m > 0 ? m : 1));
+#pragma omp parallel for num_threads(nth)
+    for (int64_t j = 0; j < (int64_t)m; ++j) key[j] = ((uint64_t)fbits(wv[j]) << 32) | (uint64_t)j;
+    uint64_t* hist = (uint64_t*)malloc(sizeof(uint64_t) * 256 * (size_t)nth);
+    for (int shift = 0; shift < 64; shift += 8) {
+#pragma omp parallel num_threads(nth)
+        {
+            const int t = omp_get_thread_num();
+            const uint64_t lo = m * (uint64_t)t / (uint64_t)nth, hi = m * (uint64_t)(t + 1) / (uint64_t)nth;
+            uint64_t* h = hist + 256 * (size_t)t;
+            memset(h, 0, 256 * sizeof(uint64_t));
+            for (uint64_t j = lo; j < hi; ++j) ++h[(key[j] >> shift) & 255];
+#pragma omp barrier
+#pragma omp single
+            {
+                uint64_t acc = 0;   /* offsets: digit-major, then thread order (stable) */
+                for (int d = 0; d < 256; ++d)
+                    for (int u = 0; u < nth; ++u) {
+                        const uint64_t c = hist[256 * (size_t)u + d];
+                        hist[256 * (size_t)u + d] = acc;
+                        acc += c;
+                    }
+            }
+            for (uint64_t j = lo; j < hi; ++j) tmp[h[(key[j] >> shift) & 255]++] = key[j];
+        }
+        uint64_t* sw = key; key = tmp; tmp = sw;
+    }
+    free(hist);
+    free(tmp);
+    free(wv);
+    /* 3. bin the sorted splats into every tile their 3-sigma disc may touch, keeping order */
     const int T = 16;
-    int tx = (W + T - 1) / T, ty = (H + T - 1) / T, nt = tx * ty;
-    /* bin the sorted splats into every tile their 3-sigma disc may touch, keeping order */
-    int64_t* cnt = (int64_t*)calloc((size_t)nt + 1, sizeof(int64_t));
-    int64_t* fill = (int64_t*)calloc((size_t)nt, sizeof(int64_t));
-    int64_t* list = NULL;
+    const int tx = (W + T - 1) / T, ty = (H + T - 1) / T, nt = tx * ty;
+    int64_t* cnt = (int64_t*)calloc((size_t)nt * (size_t)nth + 1, sizeof(int64_t));   /* [tile][thread] */
+    int64_t* tile_start = (int64_t*)calloc((size_t)nt + 1, sizeof(int64_t));
+    uint32_t* list = NULL;
     for (int pass = 0; pass < 2; ++pass) {
         if (pass == 1) {
-            for (int t = 0; t < nt; ++t) cnt[t + 1] += cnt[t];
-            list = (int64_t*)malloc(sizeof(int64_t) * (size_t)(cnt[nt] > 0 ? cnt[nt] : 1));
-        }
-        for (uint64_t k = 0; k < m; ++k) {
-            int x0 = (int)floor((s[k].sx - rad) / T), x1 = (int)floor((s[k].sx + rad) / T);
-            int y0 = (int)floor((s[k].sy - rad) / T), y1 = (int)floor((s[k].sy + rad) / T);
-            if (x0 < 0) x0 = 0;
-            if (y0 < 0) y0 = 0;
-            if (x1 > tx - 1) x1 = tx - 1;
-            if (y1 > ty - 1) y1 = ty - 1;
-            for (int b = y0; b <= y1; ++b)
-                for (int a = x0; a <= x1; ++a) {
-                    int t = b * tx + a;
-                    if (pass == 0) cnt[t + 1]++;
-                    else list[cnt[t] + fill[t]++] = (int64_t)k;
+            int64_t acc = 0;
+            for (int t = 0; t < nt; ++t) {
+                tile_start[t] = acc;
+                for (int u = 0; u < nth; ++u) {
+                    const int64_t c = cnt[(size_t)t * nth + u];
+                    cnt[(size_t)t * nth + u] = acc;
+                    acc += c;
                 }
+            }
+            tile_start[nt] = acc;
+            list = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(acc > 0 ? acc : 1));
+        }
+#pragma omp parallel num_threads(nth)
+        {
+            const int u = omp_get_thread_num();
+            const uint64_t lo = m * (uint64_t)u / (uint64_t)nth, hi = m * (uint64_t)(u + 1) / (uint64_t)nth;
+            for (uint64_t k = lo; k < hi; ++k) {
+                const splat_t* g = &s[key[k] & 0xFFFFFFFFull];
+                int x0 = (int)floor((g->sx - rad) / T), x1 = (int)floor((g->sx + rad) / T);
+                int y0 = (int)floor((g->sy - rad) / T), y1 = (int)floor((g->sy + rad) / T);
+                if (x0 < 0) x0 = 0;
+                if (y0 < 0) y0 = 0;
+                if (x1 > tx - 1) x1 = tx - 1;
+                if (y1 > ty - 1) y1 = ty - 1;
+                for (int b = y0; b <= y1; ++b)
+                    for (int a = x0; a <= x1; ++a) {
+                        int64_t* c = &cnt[(size_t)(b * tx + a) * nth + u];
+                        if (pass == 0) ++*c;
+                        else list[(*c)++] = (uint32_t)(key[k] & 0xFFFFFFFFull);
+                    }
+            }
         }
     }
-#pragma omp parallel for schedule(dynamic, 1)
+    /* 4. composite */
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nth)
     for (int t = 0; t < nt; ++t) {
         int bx = (t % tx) * T, by = (t / tx) * T;
         for (int py = by; py < by + T && py < H; ++py)
             for (int px = bx; px < bx + T && px < W; ++px) {
                 double cx = px + 0.5, cy = py + 0.5, Tr = 1.0;
                 double acc[3] = {0.0, 0.0, 0.0};
-                for (int64_t q = cnt[t]; q < cnt[t + 1]; ++q) {
+                for (int64_t q = tile_start[t]; q < tile_start[t + 1]; ++q) {
                     const splat_t* g = &s[list[q]];
                     double dx = cx - g->sx, dy = cy - g->sy, d2 = dx * dx + dy * dy;
                     if (d2 > rad2) continue;
@@ -234,8 +305,10 @@ void oracle_splat(const float* xyz, uint64_t n, const float* M, int W, int H, fl
             }
     }
     free(list);
-    free(fill);
+    free(tile_start);
     free(cnt);
+    free(key);
+    free(cnt_th);
     free(s);
 }
 

@@ -244,6 +244,31 @@ def l1_loss(y, t):
     return float(np.abs(diff).mean()), np.sign(diff) / diff.size
 
 
+def recon_tv_loss(y, t, l1=0.0, l2=0.0, tv=0.0):
+    """Eq. (1) without its perceptual term, on RGB images y, t [n, h, w, 3]:
+    l1 mean|y - t| + l2 mean (y - t)^2 (the pixel-wise reconstruction term) + tv times the 2-D
+    total variation of y (mean |y[:, :, x+1] - y[:, :, x]| over horizontal pairs plus
+    mean |y[:, y+1] - y[:, y]| over vertical pairs).  Returns (loss, dL/dy), sign(0) = 0."""
+    y = np.asarray(y, np.float64)
+    d = y - np.asarray(t, np.float64)
+    loss = l1 * np.abs(d).mean() + l2 * (d * d).mean()
+    g = l1 * np.sign(d) / d.size + 2.0 * l2 * d / d.size
+    if tv != 0.0:
+        dh = y[:, :, 1:] - y[:, :, :-1]
+        dv = y[:, 1:] - y[:, :-1]
+        if dh.size:
+            loss += tv * np.abs(dh).mean()
+            sh = np.sign(dh) / dh.size
+            g[:, :, 1:] += tv * sh
+            g[:, :, :-1] -= tv * sh
+        if dv.size:
+            loss += tv * np.abs(dv).mean()
+            sv = np.sign(dv) / dv.size
+            g[:, 1:] += tv * sv
+            g[:, :-1] -= tv * sv
+    return float(loss), g
+
+
 def adam_step(p, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     """One Adam update (Kingma & Ba), step t >= 1, no weight decay; returns (p, m, v)."""
     m = b1 * m + (1.0 - b1) * g

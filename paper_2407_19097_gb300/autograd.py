@@ -75,6 +75,29 @@ def nrv_l1(y, t):
     return NrvL1Function.apply(y, t)
 
 
+class NrvReconFunction(torch.autograd.Function):
+    """Eq. 1 without its perceptual term -- l1 mean|y - t| + l2 mean (y - t)^2 + tv TV(y) --
+    from nrv_recon_loss on RGB images [n][h][w][3]; gradient as for NrvL1Function."""
+
+    @staticmethod
+    def forward(ctx, y, t, weights):
+        y, t = y.contiguous(), t.contiguous()
+        loss = torch.empty((), dtype=torch.float32, device=y.device)
+        dy = torch.empty_like(y)
+        nrv.recon_loss(y, t, weights, loss.view(1), dy)
+        ctx.save_for_backward(dy)
+        return loss
+
+    @staticmethod
+    def backward(ctx, g):
+        (dy,) = ctx.saved_tensors
+        return dy * g, None, None
+
+
+def nrv_recon(y, t, l1=0.0, l2=1.0, tv=0.0):
+    return NrvReconFunction.apply(y, t, (l1, l2, tv))
+
+
 # Parameter writes made by library kernels (NrvAdam), which torch's version counter does not
 # see: data pointer -> number of writes.
 _library_writes: dict[int, int] = {}

@@ -102,7 +102,8 @@ extern "C" nrv_status nrv_create_scene(const nrv_scene_desc* d, nrv_scene** out)
     clear_error();
     if (!d || !out) return fail(NRV_ERR_ARG, "null argument");
     *out = nullptr;
-    if (d->n_points >= (1ull << 32)) return fail(NRV_ERR_ARG, "n_points must be < 2^32");
+    if (d->n_points >= (1ull << 32) || d->index_base + d->n_points > 0xFFFFFFFFull)
+        return fail(NRV_ERR_ARG, "index_base + n_points must be < 2^32");
     const int sw = d->stride_words;
     if (!(sw == 1 || sw == 2 || sw == 4 || sw == 8))
         return fail(NRV_ERR_ARG, "stride_words must be 1, 2, 4 or 8 (got %d)", sw);
@@ -159,13 +160,20 @@ static RView make_rview(const nrv_view& v, uint64_t* key) {
     return r;
 }
 
-static nrv_status check_pack(const nrv_pack_desc* d, int n_words) {
+static bool is_derived(int fmt) { return fmt >= NRV_VEL2D_X && fmt <= NRV_SPLAT_RADIUS; }
+
+static nrv_status check_pack(const nrv_pack_desc* d, int n_words, bool allow_derived = true) {
     if (!d) return fail(NRV_ERR_ARG, "null pack descriptor");
     if (d->n_channels < 1 || d->n_channels > 6) return fail(NRV_ERR_ARG, "n_channels must be 1..6");
     for (int j = 0; j < d->n_channels; ++j) {
-        if (d->word[j] < 0 || d->word[j] >= n_words)
-            return fail(NRV_ERR_ARG, "channel %d reads word %d of %d", j, d->word[j], n_words);
-        if (d->fmt[j] < 0 || d->fmt[j] > 2) return fail(NRV_ERR_ARG, "channel %d: bad format", j);
+        const int last = d->word[j] + (d->fmt[j] >= NRV_VEL2D_X && d->fmt[j] <= NRV_VEL2D_MAG ? 2 : 0);
+        if (d->word[j] < 0 || last >= n_words)
+            return fail(NRV_ERR_ARG, "channel %d reads words %d..%d of %d", j, d->word[j], last,
+                        n_words);
+        if (d->fmt[j] < 0 || d->fmt[j] > NRV_SPLAT_RADIUS)
+            return fail(NRV_ERR_ARG, "channel %d: bad format", j);
+        if (is_derived(d->fmt[j]) && !allow_derived)
+            return fail(NRV_ERR_ARG, "channel %d: derived channels need the scene (nrv_resolve_pack)", j);
         if (d->fmt[j] == NRV_U8X4 && (d->comp[j] < 0 || d->comp[j] > 3))
             return fail(NRV_ERR_ARG, "channel %d: byte index must be 0..3", j);
     }
@@ -188,11 +196,26 @@ static void fill_pack(ResolveArgs& a, const nrv_pack_desc* d, nrv_prec prec, flo
     a.d_offset = d->depth_offset;
 }
 
+// What the derived channels read: the scene's positions and the view's camera.
+static void fill_derived(ResolveArgs& a, const nrv_pack_desc* d, const nrv_view& v, const float* xyz) {
+    a.derived = 0;
+    for (int j = 0; j < d->n_channels; ++j)
+        if (is_derived(d->fmt[j])) a.derived = 1;
+    a.xyz = xyz;
+    const int rows[3] = {0, 1, 3};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 4; ++j) a.vm[4 * i + j] = v.viewproj[4 * rows[i] + j];
+    a.vhw = 0.5f * (float)v.width;
+    a.vhh = 0.5f * (float)v.height;
+    a.view_dev = nullptr;
+}
+
 static nrv_status raster_views(nrv_scene* s, const nrv_view* views, int n, uint64_t* const* keys,
                                cudaStream_t st) {
     RViews rv;
     memset(&rv, 0, sizeof(rv));
     rv.n = n;
+    rv.base = (uint32_t)s->d.index_base;
     for (int i = 0; i < n; ++i) rv.v[i] = make_rview(views[i], keys[i]);
     NRV_TRY(s->tiles.ensure(visibility_scratch_bytes(rv)));
     NRV_TRY(ensure_chunks(s, st));
@@ -221,6 +244,8 @@ extern "C" nrv_status nrv_rasterize(nrv_scene* s, const nrv_view* views, int n,
         memset(&a, 0, sizeof(a));
         a.key = reinterpret_cast<const unsigned long long*>(gb[i].d_key);
         a.attr = s->d.d_attr;
+        a.base = (uint32_t)s->d.index_base;
+        a.n_local = (uint32_t)s->d.n_points;
         a.stride_words = s->d.stride_words;
         a.n_words = s->d.n_words;
         a.width = views[i].width;
@@ -241,7 +266,7 @@ extern "C" nrv_status nrv_pack(const nrv_gbuffer* gb, int h, int w, const nrv_pa
     if (h < 1 || w < 1 || h > 16384 || w > 16384) return fail(NRV_ERR_ARG, "bad size");
     if (prec < NRV_PREC_F32 || prec > NRV_PREC_FP8) return fail(NRV_ERR_ARG, "bad precision");
     if (!aligned(netin, 32)) return fail(NRV_ERR_ARG, "d_netin must be 32-byte aligned");
-    NRV_TRY(check_pack(d, 8));
+    NRV_TRY(check_pack(d, 8, false));
     ResolveArgs a;
     memset(&a, 0, sizeof(a));
     a.width = w;
@@ -251,6 +276,64 @@ extern "C" nrv_status nrv_pack(const nrv_gbuffer* gb, int h, int w, const nrv_pa
     a.netin = netin;
     fill_pack(a, d, prec, inv);
     return launch_pack_planes(gb->d_depth, gb->d_mask, gb->d_attr, a, (cudaStream_t)stream);
+}
+
+extern "C" nrv_status nrv_resolve(nrv_scene* s, const nrv_view* view, const uint64_t* key,
+                                  const nrv_gbuffer* gb, nrv_stream stream) {
+    clear_error();
+    if (!s || !view || !key || !gb) return fail(NRV_ERR_ARG, "null argument");
+    NRV_TRY(check_view(*view));
+    if (!aligned(key, 16)) return fail(NRV_ERR_ARG, "d_key must be 16-byte aligned");
+    if (!gb->d_depth && !gb->d_mask && !gb->d_attr) return NRV_OK;
+    ResolveArgs a;
+    memset(&a, 0, sizeof(a));
+    a.key = reinterpret_cast<const unsigned long long*>(key);
+    a.attr = s->d.d_attr;
+    a.base = (uint32_t)s->d.index_base;
+    a.n_local = (uint32_t)s->d.n_points;
+    a.stride_words = s->d.stride_words;
+    a.n_words = s->d.n_words;
+    a.width = view->width;
+    a.height = view->height;
+    a.depth = gb->d_depth;
+    a.mask = gb->d_mask;
+    a.gattr = gb->d_attr;
+    return launch_resolve(a, (cudaStream_t)stream);
+}
+
+extern "C" nrv_status nrv_keys_flip_sign(uint64_t* key, int64_t n, nrv_stream stream) {
+    clear_error();
+    if (!key || n < 0) return fail(NRV_ERR_ARG, "bad argument");
+    if (n == 0) return NRV_OK;
+    return launch_flip_sign(key, n, (cudaStream_t)stream);
+}
+
+extern "C" nrv_status nrv_resolve_pack(nrv_scene* s, const nrv_view* view, const uint64_t* key,
+                                       const nrv_pack_desc* d, nrv_prec prec, float inv,
+                                       void* netin, nrv_stream stream) {
+    clear_error();
+    if (!s || !view || !key || !netin) return fail(NRV_ERR_ARG, "null argument");
+    NRV_TRY(check_view(*view));
+    if (prec < NRV_PREC_F32 || prec > NRV_PREC_FP8) return fail(NRV_ERR_ARG, "bad precision");
+    if (!aligned(netin, 32) || !aligned(key, 16))
+        return fail(NRV_ERR_ARG, "d_netin must be 32-byte and d_key 16-byte aligned");
+    NRV_TRY(check_pack(d, s->d.n_words));
+    ResolveArgs a;
+    memset(&a, 0, sizeof(a));
+    a.key = reinterpret_cast<const unsigned long long*>(key);
+    a.attr = s->d.d_attr;
+    a.base = (uint32_t)s->d.index_base;
+    a.n_local = (uint32_t)s->d.n_points;
+    a.stride_words = s->d.stride_words;
+    a.n_words = s->d.n_words;
+    a.width = view->width;
+    a.height = view->height;
+    a.wn = nrv_pad8(a.width);
+    a.hn = nrv_pad8(a.height);
+    a.netin = netin;
+    fill_pack(a, d, prec, inv);
+    fill_derived(a, d, *view, s->d.d_xyz);
+    return launch_resolve(a, (cudaStream_t)stream);
 }
 
 // --------------------------------------------------------------------- network
@@ -464,6 +547,31 @@ extern "C" nrv_status nrv_l1_loss(const float* y, const float* t, int64_t n, flo
     return launch_l1(y, t, n, loss, dy, (cudaStream_t)stream);
 }
 
+static nrv_status check_weights(const nrv_loss_weights* w) {
+    if (!w) return fail(NRV_ERR_ARG, "null weights");
+    for (float v : {w->l1, w->l2, w->tv})
+        if (!(v >= 0.0f) || !isfinite(v)) return fail(NRV_ERR_ARG, "loss weights must be finite and >= 0");
+    return NRV_OK;
+}
+
+extern "C" nrv_status nrv_recon_loss(const float* y, const float* t, int n, int h, int w,
+                                     const nrv_loss_weights* wt, float* loss, float* dy,
+                                     nrv_stream stream) {
+    clear_error();
+    if (!y || !t || !loss) return fail(NRV_ERR_ARG, "null argument");
+    if (n < 1 || h < 1 || w < 1 || h > 16384 || w > 16384) return fail(NRV_ERR_ARG, "bad size");
+    NRV_TRY(check_weights(wt));
+    return launch_recon(y, t, n, h, w, *wt, loss, dy, (cudaStream_t)stream);
+}
+
+extern "C" nrv_status nrv_net_set_loss(nrv_net* net, const nrv_loss_weights* wt) {
+    clear_error();
+    if (!net) return fail(NRV_ERR_ARG, "null net");
+    NRV_TRY(check_weights(wt));
+    net->loss_w = *wt;
+    return NRV_OK;
+}
+
 extern "C" nrv_status nrv_adam_step(float* p, const float* g, float* m, float* v, int64_t n,
                                     int step, float lr, float b1, float b2, float eps,
                                     nrv_stream stream) {
@@ -489,7 +597,11 @@ extern "C" nrv_status nrv_train_step(nrv_net* net, float* params, float* grad, f
     NRV_TRY(net_forward(net, netin, n, h, w, prec, y, st));
     net->saved_in = netin;
     net->saved = true;
-    NRV_TRY(launch_l1(y, target, (int64_t)nout, loss, dy, st));
+    const nrv_loss_weights& lw = net->loss_w;
+    if (lw.l1 == 1.0f && lw.l2 == 0.0f && lw.tv == 0.0f)
+        NRV_TRY(launch_l1(y, target, (int64_t)nout, loss, dy, st));
+    else
+        NRV_TRY(launch_recon(y, target, n, h, w, lw, loss, dy, st));
     NRV_TRY(net_backward(net, dy, grad, st));
     NRV_TRY(launch_adam(params, grad, m, v, net->n_params, step, lr, 0.9f, 0.999f, 1e-8f, st));
     NRV_CHECK_CUDA(cudaMemcpyAsync(net->params.p, params, net->n_params * sizeof(float),
@@ -557,8 +669,29 @@ extern "C" nrv_status nrv_render_batch(nrv_scene* s, nrv_net* net, const nrv_pac
         if (!rgb[i]) return fail(NRV_ERR_ARG, "null output %d", i);
         key_off[i] = tot;
         tot += ((size_t)views[i].width * views[i].height * 8 + 1023) / 1024 * 1024;
-        in_off[i] = tot;
-        tot += ((size_t)nrv_pad8(views[i].width) * nrv_pad8(views[i].height) * es + 1023) / 1024 * 1024;
+    }
+    // views of one size are shaded by one network call: their inputs sit back to back
+    int group_of[8], ngroups = 0, group_first[8], group_n[8];
+    for (int i = 0; i < n; ++i) {
+        group_of[i] = -1;
+        for (int g = 0; g < ngroups; ++g)
+            if (views[group_first[g]].width == views[i].width &&
+                views[group_first[g]].height == views[i].height)
+                group_of[i] = g;
+        if (group_of[i] < 0) {
+            group_of[i] = ngroups;
+            group_first[ngroups] = i;
+            group_n[ngroups++] = 0;
+        }
+        ++group_n[group_of[i]];
+    }
+    for (int g = 0; g < ngroups; ++g) {
+        const size_t per = (size_t)nrv_pad8(views[group_first[g]].width) *
+                           nrv_pad8(views[group_first[g]].height) * es;
+        int j = 0;
+        for (int i = 0; i < n; ++i)
+            if (group_of[i] == g) in_off[i] = tot + per * j++;
+        tot += (per * group_n[g] + 1023) / 1024 * 1024;
     }
     const size_t tiles_off = tot;
     {
@@ -573,6 +706,7 @@ extern "C" nrv_status nrv_render_batch(nrv_scene* s, nrv_net* net, const nrv_pac
     RViews rv;
     memset(&rv, 0, sizeof(rv));
     rv.n = n;
+    rv.base = (uint32_t)s->d.index_base;
     for (int i = 0; i < n; ++i) rv.v[i] = make_rview(views[i], (uint64_t*)(base + key_off[i]));
 
     // everything but the cameras is fixed by this signature; a captured frame is replayed
@@ -614,6 +748,8 @@ extern "C" nrv_status nrv_render_batch(nrv_scene* s, nrv_net* net, const nrv_pac
             memset(&a, 0, sizeof(a));
             a.key = reinterpret_cast<const unsigned long long*>(base + key_off[i]);
             a.attr = s->d.d_attr;
+            a.base = (uint32_t)s->d.index_base;
+            a.n_local = (uint32_t)s->d.n_points;
             a.stride_words = s->d.stride_words;
             a.n_words = s->d.n_words;
             a.width = views[i].width;
@@ -622,12 +758,24 @@ extern "C" nrv_status nrv_render_batch(nrv_scene* s, nrv_net* net, const nrv_pac
             a.hn = nrv_pad8(a.height);
             a.netin = base + in_off[i];
             fill_pack(a, d, prec, inv);
+            fill_derived(a, d, views[i], s->d.d_xyz);
+            // replays take the cameras of the call from the device copy of the views
+            if (views_dev) a.view_dev = &views_dev->v[i];
             NRV_TRY(launch_resolve(a, q));
         }
         if (ev) prof_mark(*ev, q);
-        for (int i = 0; i < n; ++i)
-            NRV_TRY(net_forward(net, base + in_off[i], 1, views[i].height, views[i].width, prec,
-                                rgb[i], q, false));
+        for (int g = 0; g < ngroups; ++g) {
+            const int i0 = group_first[g];
+            RgbTab tab{};
+            tab.on = 1;
+            for (int i = 0, j = 0; i < n; ++i)
+                if (group_of[i] == g) tab.p[j++] = rgb[i];
+            net->rgb_tab = tab;
+            const nrv_status st = net_forward(net, base + in_off[i0], group_n[g], views[i0].height,
+                                              views[i0].width, prec, rgb[i0], q, false);
+            net->rgb_tab = RgbTab{};
+            NRV_TRY(st);
+        }
         if (ev) prof_mark(*ev, q);
         return NRV_OK;
     };

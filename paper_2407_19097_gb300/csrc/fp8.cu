@@ -119,7 +119,7 @@ __global__ void fp8_to_bf16_kernel(const uint8_t* __restrict__ x, __nv_bfloat16*
 // one plane, so the row-planar tensor is also plain NHWC).
 __global__ void head_fp8_kernel(const uint8_t* __restrict__ x, float s, const float* w,
                                 const float* bias, float* rgb, int n, int hn, int wn, int h,
-                                int wd) {
+                                int wd, RgbTab tab) {
     const size_t total = (size_t)n * h * wd;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
          i += (size_t)gridDim.x * blockDim.x) {
@@ -136,7 +136,7 @@ __global__ void head_fp8_kernel(const uint8_t* __restrict__ x, float s, const fl
             float acc = bias[o];
 #pragma unroll
             for (int c = 0; c < 16; ++c) acc = fmaf(w[o * 16 + c], v[c], acc);
-            rgb[3 * i + o] = acc;
+            rgb_image(rgb, tab, img, (size_t)h * wd)[3 * ((size_t)Y * wd + X) + o] = acc;
         }
     }
 }
@@ -237,7 +237,7 @@ nrv_status forward_fp8(Net* net, const uint8_t* netin, float* rgb, cudaStream_t 
         // the head in the last conv's epilogue
         const float* P = (const float*)net->params.p;
         const TcHead head{P + Lh.woff, P + Lh.boff, rgb, net->geo_H, net->geo_W,
-                          net->act_scale[1 + A_D0B], keep_acts};
+                          net->act_scale[1 + A_D0B], keep_acts, net->rgb_tab};
         const nrv_status st = tc_conv3(net, L_D0B, A(A_D0A), 16, nullptr, 0, A(A_D0B), g, 0,
                                        NRV_PREC_FP8_E4M3, s, inv(A_D0B), &head);
         net->backend[L_D0B] = 1;
@@ -247,7 +247,8 @@ nrv_status forward_fp8(Net* net, const uint8_t* netin, float* rgb, cudaStream_t 
     NRV_TRY(conv(L_D0B, A(A_D0A), 16, nullptr, 0, A_D0B, 0));
     head_fp8_kernel<<<blocks_for((size_t)g.n * net->geo_H * net->geo_W), 256, 0, s>>>(
         A(A_D0B), net->act_scale[1 + A_D0B], (const float*)net->params.p + Lh.woff,
-        (const float*)net->params.p + Lh.boff, rgb, g.n, g.h[0], g.w[0], net->geo_H, net->geo_W);
+        (const float*)net->params.p + Lh.boff, rgb, g.n, g.h[0], g.w[0], net->geo_H, net->geo_W,
+        net->rgb_tab);
     NRV_CHECK_LAUNCH();
     return NRV_OK;
 }
@@ -303,7 +304,8 @@ nrv_status forward_fp8_mixed(Net* net, const void* netin, float* rgb, cudaStream
     NRV_TRY(tc_conv3(net, L_D0A, A(A_UP1), 16, A(A_E0B), 16, A(A_D0A), g, 0, NRV_PREC_BF16, s));
     const Layer& Lh = net->layers[L_HEAD];
     const float* P = (const float*)net->params.p;
-    const TcHead head{P + Lh.woff, P + Lh.boff, rgb, net->geo_H, net->geo_W, 1.0f, false};
+    const TcHead head{P + Lh.woff, P + Lh.boff, rgb, net->geo_H, net->geo_W, 1.0f, false,
+                      net->rgb_tab};
     return tc_conv3(net, L_D0B, A(A_D0A), 16, nullptr, 0, A(A_D0B), g, 0, NRV_PREC_BF16, s, 1.0f,
                     &head);
 }

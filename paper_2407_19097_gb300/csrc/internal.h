@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
 #include <vector>
 
 #include "../../include/nrv.h"
@@ -24,6 +25,11 @@ void clear_error();
 
 // Kernels launched by the library so far (nrv_launch_count).
 void count_launch();
+
+// Tuned launch choices (tune.cu): look up / record a choice by key; count a tuning run.
+bool tune_get(const std::string& key, int* value);
+void tune_put(const std::string& key, int value);
+void tune_count_timing();
 
 #define NRV_CHECK_LAUNCH()                                                               \
     do {                                                                                 \
@@ -57,10 +63,13 @@ struct RView {
 struct RViews {
     RView v[8];
     int n;
+    uint32_t base;        // global index of the scene's first point (the key's low word is base + i)
 };
 
 struct ResolveArgs {
     const unsigned long long* key;
+    uint32_t base;          // the scene's points have global indices base .. base + n_local - 1;
+    uint32_t n_local;       // a winner outside that range belongs to another shard: empty here
     const uint32_t* attr;   // records
     int stride_words, n_words;
     int width, height;      // view
@@ -75,6 +84,13 @@ struct ResolveArgs {
     int ch_word[6], ch_fmt[6], ch_comp[6];
     float ch_scale[6], ch_offset[6];
     float d_scale, d_offset;
+    // derived channels (formats NRV_VEL2D_* and NRV_SPLAT_RADIUS): the winner's position
+    // and the camera
+    int derived;            // some channel is derived
+    const float* xyz;
+    float vm[12];           // rows 0, 1 and 3 of the view-projection, row-major
+    float vhw, vhh;         // W/2, H/2
+    const RView* view_dev;  // if set, the camera is read from here instead (graph replays)
 };
 
 nrv_status launch_clear_keys(const RViews& views, cudaStream_t s);
@@ -94,10 +110,23 @@ nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, 
                              const RViews* views_dev = nullptr, uint32_t* tiles = nullptr,
                              const void* chunks = nullptr);
 nrv_status launch_resolve(const ResolveArgs& a, cudaStream_t s);
+nrv_status launch_flip_sign(uint64_t* keys, int64_t n, cudaStream_t s);
 nrv_status launch_pack_planes(const uint32_t* depth, const uint8_t* mask, const uint32_t* gattr,
                               const ResolveArgs& a, cudaStream_t s);
 
 // --------------------------------------------------------------------- network
+// Per-image RGB destinations of one network call (views of one size shaded together, each into
+// its caller's buffer); off: image i goes to base + i * H * W * 3.
+struct RgbTab {
+    float* p[8];
+    int on;
+};
+
+// Where image img's RGB row-major pixel array starts.
+__host__ __device__ inline float* rgb_image(float* base, const RgbTab& t, size_t img, size_t hw) {
+    return t.on ? t.p[img] : base + img * hw * 3;
+}
+
 enum LayerKind { CONV3 = 0, UPCONV2 = 1, HEAD1 = 2 };
 
 struct Layer {

@@ -274,7 +274,8 @@ static nrv_status forward_t(Net* net, const T* netin, float* rgb, cudaStream_t s
     if (use_tc) {
         // the head in the last conv's epilogue
         const float* P = (const float*)net->params.p;
-        const TcHead head{P + Lh.woff, P + Lh.boff, rgb, net->geo_H, net->geo_W, 1.0f, keep_acts};
+        const TcHead head{P + Lh.woff, P + Lh.boff, rgb, net->geo_H, net->geo_W, 1.0f, keep_acts,
+                          net->rgb_tab};
         const nrv_status st = tc_conv3(net, L_D0B, act<T>(net, A_D0A), 16, nullptr, 0,
                                        act<T>(net, A_D0B), g, 0, prec, s, 1.0f, &head);
         net->backend[L_D0B] = 1;
@@ -284,7 +285,7 @@ static nrv_status forward_t(Net* net, const T* netin, float* rgb, cudaStream_t s
     NRV_TRY(conv(L_D0B, CV(A_D0A), 16, none, 0, A_D0B, 0));
     head_kernel<T><<<blocks_for((size_t)g.n * net->geo_H * net->geo_W), 256, 0, s>>>(
         CV(A_D0B), (const float*)net->params.p + Lh.woff, (const float*)net->params.p + Lh.boff,
-        rgb, g.n, g.h[0], g.w[0], net->geo_H, net->geo_W);
+        rgb, g.n, g.h[0], g.w[0], net->geo_H, net->geo_W, net->rgb_tab);
     NRV_CHECK_LAUNCH();
     return NRV_OK;
 }

@@ -53,6 +53,8 @@ struct Net {
     int geo_H = 0, geo_W = 0;
     nrv_prec act_prec = NRV_PREC_F32;
     int backend[NUM_LAYERS];   // 0 SIMT, 1 tcgen05, -1 not run (last forward)
+    nrv_loss_weights loss_w{1.0f, 0.0f, 0.0f};   // training loss of nrv_train_step (L1)
+    RgbTab rgb_tab{};        // per-image RGB destinations of the next forward (render batches)
     bool saved = false;      // a training forward's activations are in place
     const void* saved_in = nullptr;   // that forward's input (the first layer's weight gradient reads it)
     // backward scratch
@@ -96,6 +98,7 @@ struct TcHead {
     int h, w_px;
     float scale;
     bool store_y;
+    RgbTab tab;      // per-image destinations (tab.on), else rgb + img * h * w_px * 3
 };
 
 // tensor-core convolution (tc.cu); returns NRV_ERR_UNSUPPORTED when a shape is not covered
@@ -152,6 +155,8 @@ nrv_status net_calibrate(Net* net, const void* netin, int n, int H, int W, cudaS
 // training kernels (train.cu)
 nrv_status launch_l1(const float* y, const float* t, int64_t n, float* loss, float* dy,
                      cudaStream_t s);
+nrv_status launch_recon(const float* y, const float* t, int n_img, int h, int w,
+                        const nrv_loss_weights& wt, float* loss, float* dy, cudaStream_t s);
 nrv_status launch_adam(float* p, const float* g, float* m, float* v, int64_t n, int step,
                        float lr, float b1, float b2, float eps, cudaStream_t s);
 

@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(128) upconv2_dgrad_kernel(TView<const T> g, in
 // ---------------------------------------------------------------- 1x1 head -> RGB (cropped)
 template <typename T>
 __global__ void head_kernel(TView<const T> x, const float* w, const float* bias, float* rgb,
-                            int n, int hn, int wn, int h, int wd) {
+                            int n, int hn, int wn, int h, int wd, RgbTab tab) {
     const size_t total = (size_t)n * h * wd;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
          i += (size_t)gridDim.x * blockDim.x) {
@@ -286,7 +286,7 @@ __global__ void head_kernel(TView<const T> x, const float* w, const float* bias,
             float s = bias[o];
 #pragma unroll
             for (int c = 0; c < 16; ++c) s = fmaf(w[o * 16 + c], v[c], s);
-            rgb[3 * i + o] = s;
+            rgb_image(rgb, tab, img, (size_t)h * wd)[3 * ((size_t)Y * wd + X) + o] = s;
         }
     }
 }

@@ -73,7 +73,10 @@ __device__ __forceinline__ bool cull_point(const RView& v, float cw, float cx, f
 // Projection + clipping of one point for one view; on success returns the
 // pixel (row-major index) and the depth word of the key (bits of w).  With a
 // tile bound table, points that cull_point rejects are dropped before the
-// exact divisions.
+// exact divisions.  (Locating the pixel from the fast quotient with the error
+// bound of cull_point, and dividing exactly only where that interval straddles
+// a pixel edge, measured slower: the correctly rounded division's own fast path
+// costs fewer instructions than the quotient, its bound and the tests.)
 __device__ __forceinline__ bool project_point(const RView& v, float x, float y, float z,
                                               uint32_t& pix, uint32_t& dbits,
                                               const uint32_t* __restrict__ bound = nullptr,
@@ -187,7 +190,7 @@ __global__ void __launch_bounds__(256, MINB) visibility_kernel(const float4* __r
         const float px[4] = {a.x, a.w, b.z, c.y};
         const float py[4] = {a.y, b.x, b.w, c.z};
         const float pz[4] = {a.z, b.y, c.x, c.w};
-        const uint32_t i0 = 4 * g;
+        const uint32_t i0 = 4 * g + vs.base;
         for (int v = 0; v < (SINGLE ? 1 : vs.n); ++v) {
             const RView& vw = SINGLE ? v0 : vs.v[v];
             uint32_t pix[4], db[4];
@@ -215,7 +218,7 @@ __global__ void __launch_bounds__(256, MINB) visibility_kernel(const float4* __r
     if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
         const uint64_t i = 4 * ngroups + threadIdx.x;
         for (int v = 0; v < vs.n; ++v)
-            render_point(vs.v[v], xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], (uint32_t)i);
+            render_point(vs.v[v], xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], (uint32_t)i + vs.base);
     }
 }
 
@@ -392,7 +395,7 @@ __global__ void __launch_bounds__(256) chunk_render_kernel(const float* __restri
         for (int j = 0; j < 4; ++j) {
             const uint64_t i = (uint64_t)k[j] * RENDER_CHUNK + lane;
             in[j] = j < cnt && i < n;
-            idx[j] = (uint32_t)i;
+            idx[j] = (uint32_t)i + vs.base;
             x[j] = y[j] = z[j] = 0.0f;
             if (in[j]) {
                 x[j] = xyz[3 * i];
@@ -621,6 +624,12 @@ nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, 
     int cls = 0;
     while (cls < 47 && (1ull << (cls + 1)) <= n) ++cls;
     int& choice = g_vis_choice[multi][cls];
+    char tkey[64];
+    snprintf(tkey, sizeof(tkey), "render multi=%d log2n=%d", multi, cls);
+    if (choice == 0) {
+        int v = 0;
+        if (tune_get(tkey, &v) && v >= 0 && v < count) choice = v + 1;
+    }
     // NRV_VIS_VARIANT=<i> pins variant i (used to check every variant)
     if (const char* e = getenv("NRV_VIS_VARIANT")) {
         const int i = atoi(e);
@@ -659,6 +668,8 @@ nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, 
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         choice = arg + 1;
+        tune_put(tkey, arg);
+        tune_count_timing();
         NRV_TRY(launch_clear_keys(views, s));
     }
     int pick = choice > 0 ? choice - 1 : 0;
@@ -668,8 +679,43 @@ nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, 
 
 // ------------------------------------------------------------------ pack helpers
 
+// Derived channel value (Sec. 4.5 "Vel2D", Sec. 3.2 splat radius) of the point at p with
+// record words `words`, in FP32.  v' = (ds/dp) v with s the screen map: for c = M (p, 1),
+// ds_x/dp = (W/2) (M_0 - (c.x/c.w) M_3) / c.w and ds_y/dp = -(H/2) (M_1 - (c.y/c.w) M_3) / c.w
+// (M_r the first three entries of row r).
+struct Camera {
+    float m[12];   // rows 0, 1 and 3 of the view-projection
+    float hw, hh;
+};
+
+__device__ float derived_channel(const Camera& k, int fmt, const uint32_t* words, int wd,
+                                 const float* p) {
+    const float* m = k.m;
+    const float cw = fmaf(m[8], p[0], fmaf(m[9], p[1], fmaf(m[10], p[2], m[11])));
+    const float iw = 1.0f / cw;
+    if (fmt == NRV_SPLAT_RADIUS) {
+        const float r1 = sqrtf(fmaf(m[4], m[4], fmaf(m[5], m[5], m[6] * m[6])));
+        return __uint_as_float(words[wd]) * k.hh * r1 * iw;
+    }
+    const float vx = __uint_as_float(words[wd]), vy = __uint_as_float(words[wd + 1]),
+                vz = __uint_as_float(words[wd + 2]);
+    const float cx = fmaf(m[0], p[0], fmaf(m[1], p[1], fmaf(m[2], p[2], m[3])));
+    const float cy = fmaf(m[4], p[0], fmaf(m[5], p[1], fmaf(m[6], p[2], m[7])));
+    const float mv0 = fmaf(m[0], vx, fmaf(m[1], vy, m[2] * vz));
+    const float mv1 = fmaf(m[4], vx, fmaf(m[5], vy, m[6] * vz));
+    const float mv3 = fmaf(m[8], vx, fmaf(m[9], vy, m[10] * vz));
+    const float px = k.hw * iw * fmaf(-cx * iw, mv3, mv0);
+    const float py = -k.hh * iw * fmaf(-cy * iw, mv3, mv1);
+    if (fmt == NRV_VEL2D_X) return px;
+    if (fmt == NRV_VEL2D_Y) return py;
+    if (fmt == NRV_VEL2D_ANGLE) return atan2f(py, px);
+    return sqrtf(fmaf(px, px, py * py));
+}
+
 __device__ __forceinline__ void pack_channels(const ResolveArgs& a, uint32_t depth_bits,
-                                              const uint32_t* words, float* f) {
+                                              const uint32_t* words, float* f,
+                                              const float* p = nullptr,
+                                              const Camera* cam = nullptr) {
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
         if (j < a.n_ch) {
@@ -677,7 +723,8 @@ __device__ __forceinline__ void pack_channels(const ResolveArgs& a, uint32_t dep
             float v;
             if (a.ch_fmt[j] == NRV_F32) v = __uint_as_float(w);
             else if (a.ch_fmt[j] == NRV_U32) v = __uint2float_rn(w);
-            else v = (float)((w >> (8 * a.ch_comp[j])) & 255u);
+            else if (a.ch_fmt[j] == NRV_U8X4) v = (float)((w >> (8 * a.ch_comp[j])) & 255u);
+            else v = derived_channel(*cam, a.ch_fmt[j], words, a.ch_word[j], p);
             f[j] = __fadd_rn(__fmul_rn(v, a.ch_scale[j]), a.ch_offset[j]);
         }
     }
@@ -727,9 +774,10 @@ __global__ void __launch_bounds__(256) resolve_kernel(const __grid_constant__ Re
         if (inside) key = __ldcs(a.key + p);
         uint32_t words[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
         uint32_t depth_bits = 0u;
-        const bool hit = key != ~0ull;
+        // the winner's index relative to this scene (a winner from another shard: empty here)
+        const uint32_t idx = (uint32_t)(key & 0xFFFFFFFFull) - a.base;
+        const bool hit = key != ~0ull && idx < a.n_local;
         if (hit) {
-            const uint32_t idx = (uint32_t)(key & 0xFFFFFFFFull);
             depth_bits = (uint32_t)(key >> 32);
             const uint32_t* rec = a.attr + (size_t)idx * a.stride_words;
             if (a.stride_words == 8) {
@@ -757,10 +805,31 @@ __global__ void __launch_bounds__(256) resolve_kernel(const __grid_constant__ Re
             float f[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) f[j] = 0.0f;
-            if (hit) pack_channels(a, depth_bits, words, f);
+            if (hit) {
+                float pt[3] = {0.0f, 0.0f, 0.0f};
+                Camera cam;
+                if (a.derived) {
+                    const float* xp = a.xyz + 3 * (size_t)idx;
+                    pt[0] = __ldg(xp);
+                    pt[1] = __ldg(xp + 1);
+                    pt[2] = __ldg(xp + 2);
+                    const float* src = a.view_dev ? a.view_dev->m : a.vm;
+#pragma unroll
+                    for (int j = 0; j < 12; ++j) cam.m[j] = src[j];
+                    cam.hw = a.view_dev ? a.view_dev->hw : a.vhw;
+                    cam.hh = a.view_dev ? a.view_dev->hh : a.vhh;
+                }
+                pack_channels(a, depth_bits, words, f, pt, &cam);
+            }
             store_netin(a, q, f);
         }
     }
+}
+
+__global__ void flip_sign_kernel(unsigned long long* k, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        k[i] ^= 0x8000000000000000ull;
 }
 
 static int grid_for(size_t work, int per_block = 256) {
@@ -768,6 +837,12 @@ static int grid_for(size_t work, int per_block = 256) {
     const size_t cap = 152 * 16;
     if (b > cap) b = cap;
     return (int)(b > 0 ? b : 1);
+}
+
+nrv_status launch_flip_sign(uint64_t* keys, int64_t n, cudaStream_t s) {
+    flip_sign_kernel<<<grid_for((size_t)n), 256, 0, s>>>(reinterpret_cast<unsigned long long*>(keys), n);
+    NRV_CHECK_LAUNCH();
+    return NRV_OK;
 }
 
 nrv_status launch_resolve(const ResolveArgs& a, cudaStream_t s) {

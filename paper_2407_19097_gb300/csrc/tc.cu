@@ -63,7 +63,8 @@ namespace {
 
 constexpr int PLANE = 2048;   // bytes of one (row, 16-byte channel chunk) plane: 128 pixels
 constexpr int MAX_KS = 80;
-constexpr int MAX_SLOTS = 8;
+constexpr int MAX_SLOTS = 16;
+constexpr int MAX_ACC = 4;      // accumulator buffers in TMEM (a power of two)
 constexpr int TILE_M = 128;
 constexpr int NTHREADS = 224;   // producer, MMA issuer, 4 epilogue warps, second MMA issuer
 
@@ -79,6 +80,8 @@ struct TcParams {
     int nslot;               // row slots in the ring
     int nissue;              // MMA issuers (1 or 2): issuer i takes the K-steps ks = i (mod nissue)
                              // into its own partial accumulator, the epilogue adds them
+    int nacc, acc_shift;     // accumulator buffers in TMEM (2 or 4) and log2 of that: tile i uses
+                             // buffer i mod nacc, so the issuers run up to nacc tiles ahead
     int cout;                // output channels
     int out_nch;             // 16-byte planes per output row
     int mode;                // 0: 3x3 conv (+ bias, ReLU); 1: 2x2 stride-2 transposed conv + bias;
@@ -109,6 +112,7 @@ struct TcParams {
     const float* head_w;
     const float* head_b;
     float* rgb;
+    RgbTab rgb_tab;
     int rgb_h, rgb_w;
     float head_s;
     int store_y;
@@ -159,7 +163,8 @@ __device__ __forceinline__ void ring_next(int& slot, uint32_t& phase, int nslot)
 __device__ __forceinline__ void head_store(const TcParams& P, const float* hw, int img, int y,
                                            int x, const float* v) {
     if (y >= P.rgb_h || x >= P.rgb_w) return;
-    float* out = P.rgb + (((size_t)img * P.rgb_h + y) * P.rgb_w + x) * 3;
+    float* out = rgb_image(P.rgb, P.rgb_tab, (size_t)img, (size_t)P.rgb_h * P.rgb_w) +
+                 ((size_t)y * P.rgb_w + x) * 3;
 #pragma unroll
     for (int o = 0; o < 3; ++o) {
         float acc = hw[48 + o];
@@ -174,7 +179,7 @@ __global__ void __launch_bounds__(NTHREADS, 4)
     conv3_tc_kernel(const __grid_constant__ CUtensorMap tm1, const __grid_constant__ CUtensorMap tm2,
                     const __grid_constant__ TcParams P) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t bars[2 * MAX_SLOTS + 6];
+    __shared__ __align__(8) uint64_t bars[2 * MAX_SLOTS + 2 * MAX_ACC + 2];
     __shared__ float bias_s[256];
     __shared__ float colscale_s[256];
     __shared__ float head_ws[52];
@@ -189,8 +194,8 @@ __global__ void __launch_bounds__(NTHREADS, 4)
     auto b_hfull = [&](int i) { return smem_u32(&bars[1 + i]); };
     auto b_hempty = [&](int i) { return smem_u32(&bars[1 + MAX_SLOTS + i]); };
     auto b_afull = [&](int i) { return smem_u32(&bars[1 + 2 * MAX_SLOTS + i]); };
-    auto b_aempty = [&](int i) { return smem_u32(&bars[3 + 2 * MAX_SLOTS + i]); };
-    const uint32_t b_done = smem_u32(&bars[5 + 2 * MAX_SLOTS]);
+    auto b_aempty = [&](int i) { return smem_u32(&bars[1 + 2 * MAX_SLOTS + MAX_ACC + i]); };
+    const uint32_t b_done = smem_u32(&bars[1 + 2 * MAX_SLOTS + 2 * MAX_ACC]);
 
     // this CTA's output-channel slice and its run of tiles
     const int slice = blockIdx.x % P.nslices;
@@ -207,7 +212,7 @@ __global__ void __launch_bounds__(NTHREADS, 4)
             mbar_init(b_hfull(i), 1);
             mbar_init(b_hempty(i), P.nissue);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < MAX_ACC; ++i) {
             mbar_init(b_afull(i), P.nissue);
             mbar_init(b_aempty(i), 4);
         }
@@ -341,8 +346,9 @@ __global__ void __launch_bounds__(NTHREADS, 4)
                     ring_next(wslot, wphase, P.nslot);
                 }
                 if (!ok) break;
-                const int ab = i & 1;
-                if (!mbar_wait(b_aempty(ab), ((i >> 1) & 1) ^ 1, &abort_flag, P.status)) break;
+                const int ab = i & (P.nacc - 1);
+                if (!mbar_wait(b_aempty(ab), ((i >> P.acc_shift) & 1) ^ 1, &abort_flag, P.status))
+                    break;
                 tc_fence_after();
                 // the tile's rows y+row0 .. y+row0+rows-1 are the last `rows` loads
                 int s0 = end_slot - P.rows;
@@ -398,9 +404,10 @@ __global__ void __launch_bounds__(NTHREADS, 4)
         TileWalk w;
         w.init(P, t_begin);
         for (int t = t_begin, i = 0; t < t_end; ++t, ++i, w.next(P)) {
-            const int ab = i & 1;
+            const int ab = i & (P.nacc - 1);
             int ok = 1;
-            if (lane == 0) ok = mbar_wait(b_afull(ab), (i >> 1) & 1, &abort_flag, P.status) ? 1 : 0;
+            if (lane == 0)
+                ok = mbar_wait(b_afull(ab), (i >> P.acc_shift) & 1, &abort_flag, P.status) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             tc_fence_after();
@@ -1081,8 +1088,16 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
     // two MMA issuers where both partial accumulators of both tile buffers fit in 256
     // TMEM columns and every input row has at least two K-steps (the issue loop's read-ahead)
     P.nissue = (4 * c.n_slice <= 256 && c.nks / c.rows >= 2) ? 2 : 1;
+    // four accumulator buffers where they take at most 128 TMEM columns (four CTAs' worth per
+    // SM), else two; NRV_TC_NACC=2 keeps two everywhere (read once per process)
+    static const int nacc_policy = [] {
+        const char* e = getenv("NRV_TC_NACC");
+        return (e && e[0] == '2') ? 2 : 4;
+    }();
+    P.nacc = (nacc_policy == 4 && 4 * P.nissue * c.n_slice <= 128) ? 4 : 2;
+    P.acc_shift = P.nacc == 4 ? 2 : 1;
     uint32_t cols = 32;
-    while (cols < (uint32_t)(2 * P.nissue * c.n_slice)) cols *= 2;
+    while (cols < (uint32_t)(P.nacc * P.nissue * c.n_slice)) cols *= 2;
     P.tmem_cols = cols;
     auto kern = fp8 ? conv3_tc_kernel<true> : conv3_tc_kernel<false>;
     static bool attr_set[2] = {false, false};
@@ -1163,6 +1178,8 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
         P.head_w = head->w;
         P.head_b = head->b;
         P.rgb = head->rgb;
+        P.rgb_tab = head->tab;
+        if (head->tab.on && n > 8) return fail(NRV_ERR_ARG, "per-image outputs for at most 8 images");
         P.rgb_h = head->h;
         P.rgb_w = head->w_px;
         P.head_s = head->scale;

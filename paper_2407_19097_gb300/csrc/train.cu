@@ -372,6 +372,66 @@ nrv_status launch_l1(const float* y, const float* t, int64_t n, float* loss, flo
     return NRV_OK;
 }
 
+// Reconstruction + total-variation loss (Eq. 1 without its perceptual term) on RGB images
+// y, t [n][h][w][3]: l1 mean|y - t| + l2 mean (y - t)^2 + tv (mean over horizontal neighbour
+// pairs of |y_right - y| + mean over vertical pairs of |y_below - y|), each mean over its
+// own count.  dy (if not null) is the gradient, sign(0) = 0.  Partial sums per block, summed
+// in a fixed order (deterministic).
+__global__ void recon_partial_kernel(const float* __restrict__ y, const float* __restrict__ t,
+                                     int64_t n, int h, int w, float* dy, float l1, float l2,
+                                     float tv, float inv_n, float inv_nh, float inv_nv,
+                                     float* part) {
+    __shared__ float red[256];
+    auto sgn = [](float d) { return d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f); };
+    const int64_t row = 3 * (int64_t)w;
+    float s = 0.0f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float yi = y[i], d = yi - t[i];
+        const int x = (int)((i / 3) % w), yy = (int)((i / row) % h);
+        float l = l1 * fabsf(d) * inv_n + l2 * d * d * inv_n;
+        float g = l1 * sgn(d) * inv_n + 2.0f * l2 * d * inv_n;
+        if (tv != 0.0f) {
+            if (x + 1 < w) {
+                const float e = y[i + 3] - yi;
+                l += tv * fabsf(e) * inv_nh;
+                g -= tv * sgn(e) * inv_nh;
+            }
+            if (x > 0) g += tv * sgn(yi - y[i - 3]) * inv_nh;
+            if (yy + 1 < h) {
+                const float e = y[i + row] - yi;
+                l += tv * fabsf(e) * inv_nv;
+                g -= tv * sgn(e) * inv_nv;
+            }
+            if (yy > 0) g += tv * sgn(yi - y[i - row]) * inv_nv;
+        }
+        s += l;
+        if (dy) dy[i] = g;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+nrv_status launch_recon(const float* y, const float* t, int n_img, int h, int w,
+                        const nrv_loss_weights& wt, float* loss, float* dy, cudaStream_t s) {
+    const int nb = 512;
+    NRV_TRY(g_l1_part.ensure(nb * sizeof(float)));
+    const int64_t n = (int64_t)n_img * h * w * 3;
+    const double nh = (double)n_img * h * (w - 1) * 3, nv = (double)n_img * (h - 1) * w * 3;
+    recon_partial_kernel<<<nb, 256, 0, s>>>(y, t, n, h, w, dy, wt.l1, wt.l2, wt.tv,
+                                            (float)(1.0 / (double)n), nh > 0 ? (float)(1.0 / nh) : 0.0f,
+                                            nv > 0 ? (float)(1.0 / nv) : 0.0f, (float*)g_l1_part.p);
+    NRV_CHECK_LAUNCH();
+    l1_final_kernel<<<1, 256, 0, s>>>((const float*)g_l1_part.p, nb, 1.0, loss);
+    NRV_CHECK_LAUNCH();
+    return NRV_OK;
+}
+
 __global__ void adam_kernel(float* p, const float* g, float* m, float* v, int64_t n, float lr,
                             float b1, float b2, float eps, float bc1, float bc2) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;

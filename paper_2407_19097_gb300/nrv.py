@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libnrv.so")
 
 NRV_OK, NRV_ERR_ARG, NRV_ERR_CUDA, NRV_ERR_OOM, NRV_ERR_TIMEOUT, NRV_ERR_UNSUPPORTED, NRV_ERR_STATE = range(7)
 NRV_F32, NRV_U32, NRV_U8X4 = 0, 1, 2
+NRV_VEL2D_X, NRV_VEL2D_Y, NRV_VEL2D_ANGLE, NRV_VEL2D_MAG, NRV_SPLAT_RADIUS = 3, 4, 5, 6, 7
 PREC_F32, PREC_BF16, PREC_FP8_E4M3, PREC_FP8 = 0, 1, 2, 3
 STATUS_NAMES = ["NRV_OK", "NRV_ERR_ARG", "NRV_ERR_CUDA", "NRV_ERR_OOM", "NRV_ERR_TIMEOUT",
                 "NRV_ERR_UNSUPPORTED", "NRV_ERR_STATE"]
@@ -28,7 +29,8 @@ class NrvError(RuntimeError):
 
 class nrv_scene_desc(ctypes.Structure):
     _fields_ = [("n_points", ctypes.c_uint64), ("d_xyz", ctypes.c_void_p), ("d_attr", ctypes.c_void_p),
-                ("stride_words", ctypes.c_int), ("n_words", ctypes.c_int)]
+                ("stride_words", ctypes.c_int), ("n_words", ctypes.c_int),
+                ("index_base", ctypes.c_uint64)]
 
 
 class nrv_view(ctypes.Structure):
@@ -45,6 +47,10 @@ class nrv_pack_desc(ctypes.Structure):
     _fields_ = [("n_channels", ctypes.c_int), ("word", ctypes.c_int * 6), ("fmt", ctypes.c_int * 6),
                 ("comp", ctypes.c_int * 6), ("scale", ctypes.c_float * 6), ("offset", ctypes.c_float * 6),
                 ("depth_scale", ctypes.c_float), ("depth_offset", ctypes.c_float)]
+
+
+class nrv_loss_weights(ctypes.Structure):
+    _fields_ = [("l1", ctypes.c_float), ("l2", ctypes.c_float), ("tv", ctypes.c_float)]
 
 
 class nrv_layer_info(ctypes.Structure):
@@ -66,6 +72,9 @@ SIGNATURES = {
     "nrv_scene_refresh": (I, [P]),
     "nrv_rasterize": (I, [P, ctypes.POINTER(nrv_view), I, ctypes.POINTER(nrv_gbuffer), P]),
     "nrv_pack": (I, [ctypes.POINTER(nrv_gbuffer), I, I, ctypes.POINTER(nrv_pack_desc), I, F, P, P]),
+    "nrv_resolve": (I, [P, ctypes.POINTER(nrv_view), P, ctypes.POINTER(nrv_gbuffer), P]),
+    "nrv_keys_flip_sign": (I, [P, I64, P]),
+    "nrv_resolve_pack": (I, [P, ctypes.POINTER(nrv_view), P, ctypes.POINTER(nrv_pack_desc), I, F, P, P]),
     "nrv_net_num_layers": (I, []),
     "nrv_net_layer": (I, [I, I, ctypes.POINTER(nrv_layer_info)]),
     "nrv_net_param_count": (I, [I, ctypes.POINTER(I64)]),
@@ -91,12 +100,18 @@ SIGNATURES = {
     "nrv_l1_loss": (I, [P, P, I64, P, P, P]),
     "nrv_l1_loss_noalloc": (I, [P, P, I64, P, P, P]),
     "nrv_adam_step": (I, [P, P, P, P, I64, I, F, F, F, F, P]),
+    "nrv_recon_loss": (I, [P, P, I, I, I, ctypes.POINTER(nrv_loss_weights), P, P, P]),
+    "nrv_net_set_loss": (I, [P, ctypes.POINTER(nrv_loss_weights)]),
     "nrv_train_step": (I, [P, P, P, P, P, I, F, P, P, I, I, I, I, P, P]),
     "nrv_render_batch": (I, [P, P, ctypes.POINTER(nrv_pack_desc), ctypes.POINTER(nrv_view), I,
                              ctypes.POINTER(P), I, F, P]),
     "nrv_set_profiling": (I, [I]),
     "nrv_get_timings": (I, [ctypes.POINTER(F), I]),
     "nrv_sync_status": (I, [P]),
+    "nrv_tune_load": (I, [ctypes.c_char_p]),
+    "nrv_tune_save": (I, [ctypes.c_char_p]),
+    "nrv_tune_count": (I, []),
+    "nrv_tune_timings": (ctypes.c_uint64, []),
 }
 
 _lib = None
@@ -159,9 +174,10 @@ def make_pack_desc(channels, depth_scale: float, depth_offset: float) -> nrv_pac
 class Scene:
     """A scene handle borrowing device tensors xyz [N,3] float32 and attr [N,S] int32/uint32."""
 
-    def __init__(self, xyz, attr, n_words: int):
+    def __init__(self, xyz, attr, n_words: int, index_base: int = 0):
         self.xyz, self.attr = xyz, attr      # keep the borrowed memory alive
-        d = nrv_scene_desc(int(xyz.shape[0]), _ptr(xyz), _ptr(attr), int(attr.shape[1]), int(n_words))
+        d = nrv_scene_desc(int(xyz.shape[0]), _ptr(xyz), _ptr(attr), int(attr.shape[1]), int(n_words),
+                           int(index_base))
         h = ctypes.c_void_p()
         check(lib().nrv_create_scene(ctypes.byref(d), ctypes.byref(h)))
         self.h = h
@@ -193,6 +209,26 @@ def pack(depth, mask, gattr, height, width, desc: nrv_pack_desc, prec: int, neti
     gb = nrv_gbuffer(None, _ptr(depth), _ptr(mask), _ptr(gattr))
     check(lib().nrv_pack(ctypes.byref(gb), height, width, ctypes.byref(desc), prec,
                          in_scale_inv, _ptr(netin), _stream(stream)))
+
+
+def resolve(scene: Scene, view, key, depth=None, mask=None, gattr=None, stream=None):
+    """Resolve planes from a key image; winners outside the scene's index range read as empty."""
+    cv = make_view(view)
+    gb = nrv_gbuffer(None, _ptr(depth), _ptr(mask), _ptr(gattr))
+    check(lib().nrv_resolve(scene.h, ctypes.byref(cv), _ptr(key), ctypes.byref(gb), _stream(stream)))
+
+
+def keys_flip_sign(key, stream=None):
+    """Flip bit 63 of every key in place: unsigned key order becomes signed int64 order."""
+    check(lib().nrv_keys_flip_sign(_ptr(key), key.numel(), _stream(stream)))
+
+
+def resolve_pack(scene: Scene, view, key, desc: nrv_pack_desc, prec: int, netin,
+                 in_scale_inv: float = 1.0, stream=None):
+    """Resolve one view's key image straight into the network input (derived channels allowed)."""
+    cv = make_view(view)
+    check(lib().nrv_resolve_pack(scene.h, ctypes.byref(cv), _ptr(key), ctypes.byref(desc), prec,
+                                 in_scale_inv, _ptr(netin), _stream(stream)))
 
 
 def param_count(c_in: int) -> int:
@@ -266,6 +302,11 @@ class Net:
         check(lib().nrv_net_layer_dgrad(self.h, layer, _ptr(dy), None if mask is None else _ptr(mask),
                                         n, height, width, prec, _ptr(dx), _stream(stream)))
 
+    def set_loss(self, weights):
+        """Loss of train_step: weights (l1, l2, tv) of nrv_recon_loss; (1, 0, 0) is L1."""
+        wt = nrv_loss_weights(*[float(x) for x in weights])
+        check(lib().nrv_net_set_loss(self.h, ctypes.byref(wt)))
+
     def backward(self, drgb, grad, stream=None):
         check(lib().nrv_net_backward(self.h, _ptr(drgb), _ptr(grad), _stream(stream)))
 
@@ -285,6 +326,14 @@ class Net:
 
 def l1_loss(y, t, loss, dy=None, stream=None):
     check(lib().nrv_l1_loss(_ptr(y), _ptr(t), y.numel(), _ptr(loss), _ptr(dy), _stream(stream)))
+
+
+def recon_loss(y, t, weights, loss, dy=None, stream=None):
+    """Eq. 1 without the perceptual term on RGB images y, t [n][h][w][3]; weights (l1, l2, tv)."""
+    n, h, w, _ = y.shape
+    wt = nrv_loss_weights(*[float(x) for x in weights])
+    check(lib().nrv_recon_loss(_ptr(y), _ptr(t), n, h, w, ctypes.byref(wt), _ptr(loss), _ptr(dy),
+                               _stream(stream)))
 
 
 def adam_step(p, g, m, v, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, stream=None):
@@ -309,6 +358,14 @@ def timings():
     arr = (F * 4)()
     k = lib().nrv_get_timings(arr, 4)
     return [arr[i] for i in range(k)]
+
+
+def tune_load(path):
+    check(lib().nrv_tune_load(str(path).encode()))
+
+
+def tune_save(path):
+    check(lib().nrv_tune_save(str(path).encode()))
 
 
 def sync_status(stream=None):

@@ -62,6 +62,11 @@ def test_argument_errors(lib):
     assert lib.nrv_create_scene(ctypes.byref(d), ctypes.byref(h)) == nrv.NRV_ERR_ARG
     d = nrv.nrv_scene_desc(10, 16, 16, 4, 5)         # K > stride
     assert lib.nrv_create_scene(ctypes.byref(d), ctypes.byref(h)) == nrv.NRV_ERR_ARG
+    d = nrv.nrv_scene_desc(10, 16, 16, 4, 3, (1 << 32) - 10)   # shard indices past 2^32 - 1
+    assert lib.nrv_create_scene(ctypes.byref(d), ctypes.byref(h)) == nrv.NRV_ERR_ARG
+    assert lib.nrv_keys_flip_sign(None, 4, None) == nrv.NRV_ERR_ARG
+    w = nrv.nrv_loss_weights(1.0, -0.5, 0.0)
+    assert lib.nrv_recon_loss(16, 16, 1, 4, 4, ctypes.byref(w), 16, None, None) == nrv.NRV_ERR_ARG
     d = nrv.nrv_scene_desc(0, None, None, 4, 3)      # empty scene is valid
     assert lib.nrv_create_scene(ctypes.byref(d), ctypes.byref(h)) == nrv.NRV_OK
     assert lib.nrv_rasterize(h, None, 1, None, None) == nrv.NRV_ERR_ARG
@@ -76,3 +81,22 @@ def test_argument_errors(lib):
     assert lib.nrv_net_get_params(h, 32, None) == nrv.NRV_ERR_STATE
     assert lib.nrv_net_load(h, b"/nonexistent/net.bin", None) == nrv.NRV_ERR_ARG
     assert lib.nrv_destroy_net(h) == nrv.NRV_OK
+
+
+def test_tune_cache_file_host_side(lib, tmp_path):
+    """The tuned-choice cache is host-side: a malformed or missing file is refused, a valid one
+    loads and saves again with its entries."""
+    from paper_2407_19097_gb300 import nrv
+    bad = tmp_path / "bad.txt"
+    bad.write_text("render multi=0 log2n=20 = seven\n")
+    with pytest.raises(nrv.NrvError, match="expected"):
+        nrv.tune_load(bad)
+    with pytest.raises(nrv.NrvError):
+        nrv.tune_load(tmp_path / "missing.txt")
+    good = tmp_path / "good.txt"
+    good.write_text("# comment\nrender multi=1 log2n=27 = 4\n")
+    nrv.tune_load(good)
+    out = tmp_path / "out.txt"
+    nrv.tune_save(out)
+    assert "render multi=1 log2n=27 = 4" in out.read_text()
+    assert lib.nrv_tune_count() >= 1

@@ -92,3 +92,40 @@ def test_render_batch_matches_oracle_pipeline():
     ref = unet.forward(x[None, :, :, :c0], unet.unflatten(flat, c0))[0]
     got = out.cpu().numpy()
     assert psnr_range(got, ref) >= 45.0 and np.abs(got - ref).max() <= 2e-2
+
+
+@pytest.mark.parametrize("prec", [0, 1, 3])
+def test_render_batch_groups_views_of_one_size(prec):
+    """Views of equal size are shaded by one network call (their images written to each
+    caller's buffer); every frame equals the views rendered one at a time through
+    nrv_render_batch, captured and replayed alike."""
+    import torch
+    from paper_2407_19097_gb300 import nrv
+    sc = I.terrain_scene(500, seed=7)
+    c0 = len(sc.channels) + 2
+    scene = upload_scene(sc)
+    net = nrv.Net(c0)
+    net.set_params(torch.from_numpy(make_params(c0, seed=8, bias_sigma=0.05)).to(torch_dev()))
+    sizes = [(96, 64), (160, 96), (96, 64), (96, 64), (160, 96)]
+    if prec == nrv.PREC_FP8:
+        v0 = I.orbit_views(sc, sizes[:1], seed=3)[0]
+        xb = torch.zeros((64, 96, 8), dtype=torch.bfloat16, device=torch_dev())
+        key = torch.empty((64, 96), dtype=torch.int64, device=torch_dev())
+        ds, do = I.depth_normalisation(sc, v0)
+        nrv.rasterize(scene, [v0], [key])
+        nrv.resolve_pack(scene, v0, key, nrv.make_pack_desc(sc.channels, ds, do), nrv.PREC_BF16, xb)
+        net.calibrate(xb, 1, 64, 96)
+    outs = [torch.empty((h, w, 3), device=torch_dev()) for (w, h) in sizes]
+    single = torch.empty((64, 96, 3), device=torch_dev())
+    for frame, seed in enumerate((3, 3, 17)):
+        views = I.orbit_views(sc, sizes, seed=seed)
+        ds, do = I.depth_normalisation(sc, views[0])
+        desc = nrv.make_pack_desc(sc.channels, ds, do)
+        nrv.render_batch(scene, net, desc, views, outs, prec)
+        torch.cuda.synchronize()
+        for v, o in zip(views, outs):
+            ref = torch.empty((v.height, v.width, 3), device=torch_dev())
+            nrv.render_batch(scene, net, desc, [v], [ref], prec)
+            torch.cuda.synchronize()
+            assert torch.equal(o, ref), f"frame {frame}: grouped view differs"
+    nrv.sync_status()

@@ -164,3 +164,32 @@ def test_scene_refresh_after_points_move():
     scene.xyz.copy_(torch.from_numpy(xyz).to(scene.xyz.device))
     nrv.check(nrv.lib().nrv_scene_refresh(scene.h))
     _every_variant(dataclasses.replace(sc, xyz=xyz), [v], scene)
+
+
+def test_points_on_pixel_edges_every_variant(simple_view):
+    """Points whose projections fall on or within a few ulps of pixel and screen edges, where
+    the fast quotient cannot decide the pixel and the exact division must: keys and planes
+    bit-exact for every render-pass variant."""
+    import os
+    from paper_2407_19097_gb300 import nrv
+    rng = np.random.default_rng(21)
+    W, H, n = 64, 48, 200_003
+    m = [2, 0, 0, 0, 0, 2, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0]   # sx = (2x/z + 1) W/2, sy = (1 - 2y/z) H/2
+    v = simple_view(m, W, H, 0.5, 10.0)
+    z = rng.uniform(1.0, 4.0, n)
+    sx = rng.integers(-1, W + 2, n) + rng.choice([0.0, 1e-7, -1e-7, 3e-6, -3e-6, 0.4999], n)
+    sy = rng.integers(-1, H + 2, n) + rng.choice([0.0, 2e-7, -2e-7, 5e-6, -5e-6, 0.5], n)
+    xyz = np.stack([(sx / (W / 2) - 1) * z / 2, (1 - sy / (H / 2)) * z / 2, z], 1).astype(np.float32)
+    base = I.cube_scene(n, k=3, seed=3)
+    sc = I.Scene("edges", xyz, base.attr, base.n_words, base.channels)
+    scene = upload_scene(sc)
+    ref = oracle.rasterize(sc, v)
+    assert (ref[2] > 0).mean() > 0.9
+    for i in range(nrv.lib().nrv_render_variants(0)):
+        os.environ["NRV_VIS_VARIANT"] = str(i)
+        try:
+            got = gpu_raster(scene, [v])[0]
+        finally:
+            del os.environ["NRV_VIS_VARIANT"]
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b), f"variant {i} differs"

@@ -153,3 +153,43 @@ def test_random_multi_tile_scene_matches_unbinned_loop(simple_view):
     want = _brute_force_splat(pts, colour, 0.5, 10.0)
     np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-15)
     assert (got.sum(axis=2) > 0).mean() > 0.5          # the scene covers most tiles
+
+
+def test_many_points_match_a_per_pixel_reference(simple_view):
+    """50k Gaussians on a 96 x 80 screen (30 tiles), enough for every thread of the splatter's
+    parallel filter, sort and binning to hold many points: each pixel against a reference that
+    sorts all covering Gaussians by (w, index) with numpy and composites them in that order."""
+    W, H = 96, 80
+    m = [2, 0, 0, 0, 0, 2, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0]
+    v = simple_view(m, W, H, 0.5, 10.0)
+    rng = np.random.default_rng(12)
+    n = 50_000
+    sx = rng.uniform(-6.0, W + 6.0, n)
+    sy = rng.uniform(-6.0, H + 6.0, n)
+    z = rng.choice(np.linspace(0.4, 3.0, 4000), n)          # many exact depth ties
+    pts = np.stack([(sx / (W / 2) - 1) * z / 2, (1 - sy / (H / 2)) * z / 2, z], 1).astype(np.float32)
+    colour = rng.uniform(0, 1, (n, 3)).astype(np.float32)
+    got = oracle.splat(pts, v, colour)
+    x, y, zz = (pts[:, k].astype(np.float32) for k in range(3))
+    cw = zz
+    px = ((np.float32(2) * x / cw + np.float32(1)) * np.float32(W / 2)).astype(np.float64)
+    py = ((np.float32(1) - np.float32(2) * y / cw) * np.float32(H / 2)).astype(np.float64)
+    keep = (cw >= np.float32(0.5)) & (cw <= np.float32(10.0)) & (px >= -4.5) & (px < W + 4.5) & \
+        (py >= -4.5) & (py < H + 4.5)
+    idx = np.nonzero(keep)[0]
+    order = idx[np.lexsort((idx, cw[idx]))]                   # by w, then index
+    ox, oy, oc = px[order], py[order], colour[order].astype(np.float64)
+    want = np.zeros((H, W, 3))
+    for yy in range(H):
+        for xx in range(W):
+            d2 = (xx + 0.5 - ox) ** 2 + (yy + 0.5 - oy) ** 2
+            sel = np.nonzero(d2 <= 4.5 * 4.5)[0]
+            tr, acc = 1.0, np.zeros(3)
+            for k in sel:
+                a = 0.6 * math.exp(-d2[k] / (2.0 * 1.5 * 1.5))
+                acc += tr * a * oc[k]
+                tr *= 1.0 - a
+                if tr < 1e-4:
+                    break
+            want[yy, xx] = acc
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-15)

@@ -196,3 +196,33 @@ def test_storage_rounding_hook_matches_torch():
     y2 = unet.forward(x, unet.unflatten(flat, c0), q=lambda t: t)
     np.testing.assert_array_equal(y2, unet.forward(x, unet.unflatten(flat, c0)))
     assert 0.0 < unet.relu_margin(s) < 1.0
+
+
+def test_recon_tv_loss_closed_forms():
+    """Eq. (1) without its perceptual term: a horizontal ramp y = a x has total variation a
+    (all horizontal differences a, no vertical ones); a constant offset c gives L2 = c^2 and
+    L1 = |c|."""
+    n, h, w = 2, 5, 7
+    a = 0.25
+    y = np.broadcast_to((a * np.arange(w))[None, None, :, None], (n, h, w, 3)).copy()
+    loss, _ = unet.recon_tv_loss(y, y, tv=1.0)
+    assert abs(loss - a) < 1e-15
+    c = -0.3
+    loss, g = unet.recon_tv_loss(y + c, y, l1=1.0, l2=1.0)
+    assert abs(loss - (abs(c) + c * c)) < 1e-15
+    np.testing.assert_allclose(g, (np.sign(c) + 2 * c) / y.size, rtol=1e-15)
+
+
+def test_recon_tv_loss_gradient_by_finite_differences():
+    rng = np.random.default_rng(3)
+    y = rng.standard_normal((2, 4, 5, 3))
+    t = rng.standard_normal((2, 4, 5, 3))
+    wts = dict(l1=0.7, l2=1.3, tv=0.4)
+    _, g = unet.recon_tv_loss(y, t, **wts)
+    h = 1e-7
+    for idx in [(0, 0, 0, 0), (1, 3, 4, 2), (0, 2, 1, 1), (1, 0, 4, 0), (0, 3, 2, 2)]:
+        yp, ym = y.copy(), y.copy()
+        yp[idx] += h
+        ym[idx] -= h
+        fd = (unet.recon_tv_loss(yp, t, **wts)[0] - unet.recon_tv_loss(ym, t, **wts)[0]) / (2 * h)
+        assert abs(fd - g[idx]) <= 1e-6 * max(1.0, abs(fd)), (idx, fd, g[idx])
