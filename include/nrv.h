@@ -126,6 +126,12 @@ typedef struct {
     int stride_words;        /* record stride in 32-bit words: 1, 2, 4 or 8 */
     int n_words;             /* K: record words copied to the G-buffer, 1..stride_words
                                 (Sec. 3.2 tests up to 8 attributes) */
+    int point_stride;        /* 0 or 1: every point.  S > 1: the scene's point j is point j*S of
+                                the arrays (position d_xyz[3 j S], record d_attr at j S
+                                stride_words) and keys carry j*S -- a masked render pass over a
+                                sparse subset, e.g. the glyph points (every 50th, Sec. 4.3) for
+                                "VisGlyph" (Tab. 2: the frontmost glyph point, ignoring the
+                                non-glyph points in front of it).  N counts the subset */
     uint64_t index_base;     /* global index of the first point (0 for a whole scene): key
                                 low words are index_base + i, index_base + N < 2^32.  A
                                 shard of a larger scene takes its first point's index, so

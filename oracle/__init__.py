@@ -47,6 +47,7 @@ def _L():
         lib.oracle_resolve.argtypes = [P, I64, P, I64, I, P, P, P]
         lib.oracle_pack.argtypes = [P, P, P, I, I, I, I, I, P, P, P, P, P, F, F, I, I, F, P]
         lib.oracle_splat.argtypes = [P, U64, P, I, I, F, F, P, D, D, P]
+        lib.oracle_splat_aniso.argtypes = [P, U64, P, I, I, F, F, P, P, D, D, D, P]
         lib.oracle_bf16_array.argtypes = [P, I64, P]
         lib.oracle_e4m3_array.argtypes = [P, I64, P]
         _lib = lib
@@ -102,6 +103,22 @@ def pack(depth, mask, gattr, channels, d_scale: float, d_offset: float, hn: int,
                      _p(np.ascontiguousarray(gattr, np.uint32)), h, w, hn, wn, nch, _p(cw), _p(cf),
                      _p(cc), _p(cs), _p(co), float(d_scale), float(d_offset), cpad, out_fmt,
                      float(in_scale_inv), _p(out))
+    return out
+
+
+def splat_aniso(xyz: np.ndarray, view, colour: np.ndarray, velocity: np.ndarray, r0: float,
+                stretch: float, alpha: float = 0.6):
+    """Elongated Gaussians (covariance r0^2 R diag(s^2, 1, 1) R^T along each point's velocity,
+    projected with the screen map's Jacobian), composited front to back -> float64 RGB [H, W, 3].
+    Serial: for pins and small stylised targets."""
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    colour = np.ascontiguousarray(colour, np.float32)
+    velocity = np.ascontiguousarray(velocity, np.float32)
+    m = np.ascontiguousarray(view.viewproj, np.float32)
+    out = np.empty((view.height, view.width, 3), np.float64)
+    _L().oracle_splat_aniso(_p(xyz), xyz.shape[0], _p(m), view.width, view.height, float(view.znear),
+                            float(view.zfar), _p(colour), _p(velocity), float(r0), float(stretch),
+                            float(alpha), _p(out))
     return out
 
 

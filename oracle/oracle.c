@@ -312,6 +312,101 @@ void oracle_splat(const float* xyz, uint64_t n, const float* M, int W, int H, fl
     free(s);
 }
 
+/* ---------------------------------------------------------------------------
+ * Anisotropic Gaussian splat renderer (the Gaussian Renderer's elongated
+ * Gaussians, Sec. 4.2): every point is a 3-D Gaussian N(p, Sigma) with
+ * Sigma = r0^2 R diag(s^2, 1, 1) R^T, R a rotation whose first axis is the
+ * point's velocity v (Sigma = r0^2 (I + (s^2 - 1) u u^T), u = v / |v|; an
+ * isotropic r0^2 I where v = 0).  It is projected to the screen with the
+ * Jacobian J of the screen map at p (first-order, EWA-style):
+ *   J_x = (W/2) (M_0 c_w - c_x M_3) / c_w^2,  J_y = -(H/2) (M_1 c_w - c_y M_3) / c_w^2,
+ *   Sigma' = J Sigma J^T = [[a, b], [b, c]],
+ * centred at the same (sx, sy) as the isotropic renderer.  For a pixel centre p
+ * the Mahalanobis distance q = d^T Sigma'^-1 d, d = p - (sx, sy); a Gaussian
+ * counts where q <= 9 (3 sigma) with alpha * exp(-q / 2), composited front to
+ * back in (w, index) order exactly as the isotropic renderer (T < 1e-4 stops).
+ * Points whose 3-sigma box misses the image, or whose Sigma' is singular, are
+ * dropped.  Serial and plain: it pins and makes small stylised targets.
+ * ------------------------------------------------------------------------- */
+typedef struct { float w; uint32_t i; double sx, sy, a, b, c, rx, ry; } asplat_t;
+
+static int asplat_cmp(const void* x, const void* y) {
+    const asplat_t* p = (const asplat_t*)x;
+    const asplat_t* q = (const asplat_t*)y;
+    if (p->w < q->w) return -1;
+    if (p->w > q->w) return 1;
+    return (p->i > q->i) - (p->i < q->i);
+}
+
+void oracle_splat_aniso(const float* xyz, uint64_t n, const float* M, int W, int H, float znear,
+                        float zfar, const float* colour, const float* vel, double r0, double s,
+                        double alpha, double* out) {
+    const float hw = 0.5f * (float)W, hh = 0.5f * (float)H;
+    asplat_t* g = (asplat_t*)malloc(sizeof(asplat_t) * (size_t)(n > 0 ? n : 1));
+    uint64_t m = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+        float cx = ((M[0] * x + M[1] * y) + M[2] * z) + M[3];
+        float cy = ((M[4] * x + M[5] * y) + M[6] * z) + M[7];
+        float cw = ((M[12] * x + M[13] * y) + M[14] * z) + M[15];
+        if (!(cw >= znear && cw <= zfar)) continue;
+        float nx = cx / cw, ny = cy / cw;
+        float sx = (nx + 1.0f) * hw, sy = (1.0f - ny) * hh;
+        /* the 3-D covariance */
+        double v[3] = {vel[3 * i], vel[3 * i + 1], vel[3 * i + 2]};
+        double vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        double S3[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int k = 0; k < 3; ++k) {
+                double u_rk = vn > 0.0 ? (v[r] / vn) * (v[k] / vn) : 0.0;
+                S3[r][k] = r0 * r0 * ((r == k ? 1.0 : 0.0) + (s * s - 1.0) * u_rk);
+            }
+        /* the screen-map Jacobian at p, in double from the FP32 clip coordinates */
+        double dcw = cw, dcx = cx, dcy = cy, J[2][3];
+        for (int k = 0; k < 3; ++k) {
+            J[0][k] = 0.5 * W * ((double)M[k] * dcw - dcx * (double)M[12 + k]) / (dcw * dcw);
+            J[1][k] = -0.5 * H * ((double)M[4 + k] * dcw - dcy * (double)M[12 + k]) / (dcw * dcw);
+        }
+        double JS[2][3];
+        for (int r = 0; r < 2; ++r)
+            for (int k = 0; k < 3; ++k)
+                JS[r][k] = J[r][0] * S3[0][k] + J[r][1] * S3[1][k] + J[r][2] * S3[2][k];
+        double a = JS[0][0] * J[0][0] + JS[0][1] * J[0][1] + JS[0][2] * J[0][2];
+        double b = JS[0][0] * J[1][0] + JS[0][1] * J[1][1] + JS[0][2] * J[1][2];
+        double c = JS[1][0] * J[1][0] + JS[1][1] * J[1][1] + JS[1][2] * J[1][2];
+        if (!(a > 0.0 && c > 0.0 && a * c - b * b > 0.0)) continue;
+        double rx = 3.0 * sqrt(a), ry = 3.0 * sqrt(c);
+        if (!((double)sx + rx >= 0.0 && (double)sx - rx < W && (double)sy + ry >= 0.0 &&
+              (double)sy - ry < H))
+            continue;
+        asplat_t* o = &g[m++];
+        o->w = cw; o->i = (uint32_t)i; o->sx = sx; o->sy = sy;
+        o->a = a; o->b = b; o->c = c; o->rx = rx; o->ry = ry;
+    }
+    qsort(g, (size_t)m, sizeof(asplat_t), asplat_cmp);
+    for (int py = 0; py < H; ++py)
+        for (int px = 0; px < W; ++px) {
+            double cxp = px + 0.5, cyp = py + 0.5, Tr = 1.0;
+            double acc[3] = {0.0, 0.0, 0.0};
+            for (uint64_t k = 0; k < m; ++k) {
+                const asplat_t* e = &g[k];
+                double dx = cxp - e->sx, dy = cyp - e->sy;
+                if (fabs(dx) > e->rx || fabs(dy) > e->ry) continue;
+                double det = e->a * e->c - e->b * e->b;
+                double q = (e->c * dx * dx - 2.0 * e->b * dx * dy + e->a * dy * dy) / det;
+                if (q > 9.0) continue;
+                double al = alpha * exp(-0.5 * q);
+                const float* col = colour + 3 * (uint64_t)e->i;
+                for (int j = 0; j < 3; ++j) acc[j] += Tr * al * (double)col[j];
+                Tr *= 1.0 - al;
+                if (Tr < 1e-4) break;
+            }
+            double* o = out + 3 * ((int64_t)py * W + px);
+            o[0] = acc[0]; o[1] = acc[1]; o[2] = acc[2];
+        }
+    free(g);
+}
+
 void oracle_bf16_array(const float* in, int64_t n, uint16_t* out) {
     for (int64_t i = 0; i < n; ++i) out[i] = oracle_bf16(in[i]);
 }

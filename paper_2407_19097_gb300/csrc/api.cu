@@ -56,7 +56,7 @@ struct nrv_scene {
 
 // The chunk bounds are derived from the positions on first use and after nrv_scene_refresh.
 static nrv_status ensure_chunks(nrv_scene* s, cudaStream_t st) {
-    if (s->chunks_ok || s->d.n_points == 0) return NRV_OK;
+    if (s->chunks_ok || s->d.n_points == 0 || s->d.point_stride > 1) return NRV_OK;
     NRV_TRY(s->chunks.ensure(chunk_count(s->d.n_points) * 6 * sizeof(float)));
     NRV_TRY(launch_chunk_bounds(s->d.d_xyz, s->d.n_points, s->chunks.p, st));
     s->chunks_ok = true;
@@ -102,8 +102,10 @@ extern "C" nrv_status nrv_create_scene(const nrv_scene_desc* d, nrv_scene** out)
     clear_error();
     if (!d || !out) return fail(NRV_ERR_ARG, "null argument");
     *out = nullptr;
-    if (d->n_points >= (1ull << 32) || d->index_base + d->n_points > 0xFFFFFFFFull)
-        return fail(NRV_ERR_ARG, "index_base + n_points must be < 2^32");
+    if (d->point_stride < 0) return fail(NRV_ERR_ARG, "point_stride must be >= 0");
+    const uint64_t ps = d->point_stride > 1 ? (uint64_t)d->point_stride : 1;
+    if (d->n_points >= (1ull << 32) || d->index_base + d->n_points * ps > 0xFFFFFFFFull)
+        return fail(NRV_ERR_ARG, "index_base + n_points * point_stride must be < 2^32");
     const int sw = d->stride_words;
     if (!(sw == 1 || sw == 2 || sw == 4 || sw == 8))
         return fail(NRV_ERR_ARG, "stride_words must be 1, 2, 4 or 8 (got %d)", sw);
@@ -117,6 +119,7 @@ extern "C" nrv_status nrv_create_scene(const nrv_scene_desc* d, nrv_scene** out)
     }
     nrv_scene* s = new nrv_scene;
     s->d = *d;
+    s->d.point_stride = (int)ps;
     *out = s;
     return NRV_OK;
 }
@@ -217,9 +220,11 @@ static nrv_status raster_views(nrv_scene* s, const nrv_view* views, int n, uint6
     rv.n = n;
     rv.base = (uint32_t)s->d.index_base;
     for (int i = 0; i < n; ++i) rv.v[i] = make_rview(views[i], keys[i]);
+    NRV_TRY(launch_clear_keys(rv, st));
+    if (s->d.point_stride > 1)
+        return launch_visibility_strided(s->d.d_xyz, s->d.n_points, s->d.point_stride, rv, st, nullptr);
     NRV_TRY(s->tiles.ensure(visibility_scratch_bytes(rv)));
     NRV_TRY(ensure_chunks(s, st));
-    NRV_TRY(launch_clear_keys(rv, st));
     return launch_visibility(s->d.d_xyz, s->d.n_points, rv, st, nullptr, (uint32_t*)s->tiles.p,
                              s->chunks.p);
 }
@@ -245,7 +250,7 @@ extern "C" nrv_status nrv_rasterize(nrv_scene* s, const nrv_view* views, int n,
         a.key = reinterpret_cast<const unsigned long long*>(gb[i].d_key);
         a.attr = s->d.d_attr;
         a.base = (uint32_t)s->d.index_base;
-        a.n_local = (uint32_t)s->d.n_points;
+        a.n_local = (uint32_t)(s->d.n_points * s->d.point_stride);
         a.stride_words = s->d.stride_words;
         a.n_words = s->d.n_words;
         a.width = views[i].width;
@@ -290,7 +295,7 @@ extern "C" nrv_status nrv_resolve(nrv_scene* s, const nrv_view* view, const uint
     a.key = reinterpret_cast<const unsigned long long*>(key);
     a.attr = s->d.d_attr;
     a.base = (uint32_t)s->d.index_base;
-    a.n_local = (uint32_t)s->d.n_points;
+    a.n_local = (uint32_t)(s->d.n_points * s->d.point_stride);
     a.stride_words = s->d.stride_words;
     a.n_words = s->d.n_words;
     a.width = view->width;
@@ -323,7 +328,7 @@ extern "C" nrv_status nrv_resolve_pack(nrv_scene* s, const nrv_view* view, const
     a.key = reinterpret_cast<const unsigned long long*>(key);
     a.attr = s->d.d_attr;
     a.base = (uint32_t)s->d.index_base;
-    a.n_local = (uint32_t)s->d.n_points;
+    a.n_local = (uint32_t)(s->d.n_points * s->d.point_stride);
     a.stride_words = s->d.stride_words;
     a.n_words = s->d.n_words;
     a.width = view->width;
@@ -740,8 +745,12 @@ extern "C" nrv_status nrv_render_batch(nrv_scene* s, nrv_net* net, const nrv_pac
         if (ev) prof_mark(*ev, q);
         NRV_TRY(launch_clear_keys(rv, q));
         if (ev) prof_mark(*ev, q);
-        NRV_TRY(launch_visibility(s->d.d_xyz, s->d.n_points, rv, q, views_dev,
-                                  (uint32_t*)(base + tiles_off), s->chunks.p));
+        if (s->d.point_stride > 1)
+            NRV_TRY(launch_visibility_strided(s->d.d_xyz, s->d.n_points, s->d.point_stride, rv, q,
+                                              views_dev));
+        else
+            NRV_TRY(launch_visibility(s->d.d_xyz, s->d.n_points, rv, q, views_dev,
+                                      (uint32_t*)(base + tiles_off), s->chunks.p));
         if (ev) prof_mark(*ev, q);
         for (int i = 0; i < n; ++i) {
             ResolveArgs a;
@@ -749,7 +758,7 @@ extern "C" nrv_status nrv_render_batch(nrv_scene* s, nrv_net* net, const nrv_pac
             a.key = reinterpret_cast<const unsigned long long*>(base + key_off[i]);
             a.attr = s->d.d_attr;
             a.base = (uint32_t)s->d.index_base;
-            a.n_local = (uint32_t)s->d.n_points;
+            a.n_local = (uint32_t)(s->d.n_points * s->d.point_stride);
             a.stride_words = s->d.stride_words;
             a.n_words = s->d.n_words;
             a.width = views[i].width;

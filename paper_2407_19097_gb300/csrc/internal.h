@@ -109,6 +109,10 @@ const char* visibility_variant_name(int multi, int i);
 nrv_status launch_visibility(const float* xyz, uint64_t n, const RViews& views, cudaStream_t s,
                              const RViews* views_dev = nullptr, uint32_t* tiles = nullptr,
                              const void* chunks = nullptr);
+// Render pass over every S-th point (scene point j is array point j * S; keys carry j * S):
+// one point per thread, no culling.
+nrv_status launch_visibility_strided(const float* xyz, uint64_t n, int stride, const RViews& views,
+                                     cudaStream_t s, const RViews* views_dev = nullptr);
 nrv_status launch_resolve(const ResolveArgs& a, cudaStream_t s);
 nrv_status launch_flip_sign(uint64_t* keys, int64_t n, cudaStream_t s);
 nrv_status launch_pack_planes(const uint32_t* depth, const uint8_t* mask, const uint32_t* gattr,

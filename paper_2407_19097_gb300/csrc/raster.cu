@@ -222,6 +222,39 @@ __global__ void __launch_bounds__(256, MINB) visibility_kernel(const float4* __r
     }
 }
 
+// Render pass over a strided subset (a masked pass, e.g. over glyph points): scene point j is
+// array point j * S, its key carries j * S + base.  One point per thread, the exact projection
+// and the early depth test of the full pass, no culling (the subset is sparse).
+__global__ void __launch_bounds__(256) visibility_strided_kernel(const float* __restrict__ xyz,
+                                                                 uint64_t n, uint32_t S,
+                                                                 const __grid_constant__ RViews vs_arg,
+                                                                 const RViews* __restrict__ views_dev) {
+    __shared__ RViews vs;
+    {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(views_dev ? views_dev : &vs_arg);
+        for (int i = threadIdx.x; i < (int)(sizeof(RViews) / 4); i += blockDim.x)
+            reinterpret_cast<uint32_t*>(&vs)[i] = src[i];
+    }
+    __syncthreads();
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < n;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = j * S;
+        const float x = __ldg(xyz + 3 * i), y = __ldg(xyz + 3 * i + 1), z = __ldg(xyz + 3 * i + 2);
+        for (int v = 0; v < vs.n; ++v) render_point(vs.v[v], x, y, z, (uint32_t)i + vs.base);
+    }
+}
+
+nrv_status launch_visibility_strided(const float* xyz, uint64_t n, int stride, const RViews& views,
+                                     cudaStream_t s, const RViews* views_dev) {
+    if (n == 0) return NRV_OK;
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    visibility_strided_kernel<<<(unsigned)blocks, 256, 0, s>>>(xyz, n, (uint32_t)stride, views,
+                                                               views_dev);
+    NRV_CHECK_LAUNCH();
+    return NRV_OK;
+}
+
 // Tile bounds: one warp per tile takes the maximum depth word over its pixels
 // (empty pixels hold ~0, so a tile with an empty pixel never culls).
 __global__ void tile_bound_kernel(RViews vs_arg, const RViews* __restrict__ views_dev,

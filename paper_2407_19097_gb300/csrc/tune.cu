@@ -39,7 +39,7 @@ nrv_status load_file(const char* path) {
         char* eq = strrchr(line, '=');
         char* end = nullptr;
         const long v = eq ? strtol(eq + 1, &end, 10) : 0;
-        if (!eq || end == eq + 1 || v < 0 || v > 1000000) {
+        if (!eq || end == eq + 1 || v < 0 || v > 0x7FFFFFFFL) {
             st = fail(NRV_ERR_ARG, "tune cache %s line %d: expected '<key> = <value>'", path, lineno);
             break;
         }

@@ -30,7 +30,7 @@ class NrvError(RuntimeError):
 class nrv_scene_desc(ctypes.Structure):
     _fields_ = [("n_points", ctypes.c_uint64), ("d_xyz", ctypes.c_void_p), ("d_attr", ctypes.c_void_p),
                 ("stride_words", ctypes.c_int), ("n_words", ctypes.c_int),
-                ("index_base", ctypes.c_uint64)]
+                ("point_stride", ctypes.c_int), ("index_base", ctypes.c_uint64)]
 
 
 class nrv_view(ctypes.Structure):
@@ -174,10 +174,15 @@ def make_pack_desc(channels, depth_scale: float, depth_offset: float) -> nrv_pac
 class Scene:
     """A scene handle borrowing device tensors xyz [N,3] float32 and attr [N,S] int32/uint32."""
 
-    def __init__(self, xyz, attr, n_words: int, index_base: int = 0):
+    def __init__(self, xyz, attr, n_words: int, index_base: int = 0, point_stride: int = 1):
+        """point_stride S > 1: the scene is every S-th point of xyz/attr (a masked render pass
+        over a subset, e.g. glyph points); keys then carry the index in the full arrays."""
         self.xyz, self.attr = xyz, attr      # keep the borrowed memory alive
-        d = nrv_scene_desc(int(xyz.shape[0]), _ptr(xyz), _ptr(attr), int(attr.shape[1]), int(n_words),
-                           int(index_base))
+        n = int(xyz.shape[0])
+        if point_stride > 1:
+            n = (n + point_stride - 1) // point_stride
+        d = nrv_scene_desc(n, _ptr(xyz), _ptr(attr), int(attr.shape[1]), int(n_words),
+                           int(point_stride), int(index_base))
         h = ctypes.c_void_p()
         check(lib().nrv_create_scene(ctypes.byref(d), ctypes.byref(h)))
         self.h = h

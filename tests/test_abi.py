@@ -62,7 +62,9 @@ def test_argument_errors(lib):
     assert lib.nrv_create_scene(ctypes.byref(d), ctypes.byref(h)) == nrv.NRV_ERR_ARG
     d = nrv.nrv_scene_desc(10, 16, 16, 4, 5)         # K > stride
     assert lib.nrv_create_scene(ctypes.byref(d), ctypes.byref(h)) == nrv.NRV_ERR_ARG
-    d = nrv.nrv_scene_desc(10, 16, 16, 4, 3, (1 << 32) - 10)   # shard indices past 2^32 - 1
+    d = nrv.nrv_scene_desc(10, 16, 16, 4, 3, 1, (1 << 32) - 10)   # shard indices past 2^32 - 1
+    assert lib.nrv_create_scene(ctypes.byref(d), ctypes.byref(h)) == nrv.NRV_ERR_ARG
+    d = nrv.nrv_scene_desc(1 << 30, 16, 16, 4, 3, 8, 0)       # strided indices past 2^32 - 1
     assert lib.nrv_create_scene(ctypes.byref(d), ctypes.byref(h)) == nrv.NRV_ERR_ARG
     assert lib.nrv_keys_flip_sign(None, 4, None) == nrv.NRV_ERR_ARG
     w = nrv.nrv_loss_weights(1.0, -0.5, 0.0)
@@ -94,9 +96,10 @@ def test_tune_cache_file_host_side(lib, tmp_path):
     with pytest.raises(nrv.NrvError):
         nrv.tune_load(tmp_path / "missing.txt")
     good = tmp_path / "good.txt"
-    good.write_text("# comment\nrender multi=1 log2n=27 = 4\n")
+    good.write_text("# comment\nrender multi=1 log2n=27 = 4\nconv test key = 2230020\n")
     nrv.tune_load(good)
     out = tmp_path / "out.txt"
     nrv.tune_save(out)
     assert "render multi=1 log2n=27 = 4" in out.read_text()
+    assert "conv test key = 2230020" in out.read_text()
     assert lib.nrv_tune_count() >= 1

@@ -1,9 +1,11 @@
-"""Pins for the Gaussian splat target renderer (stands in for the Gaussian Renderer of
+"""Pins for the Gaussian splat target renderers (they stand in for the Gaussian Renderer of
 Sec. 4.2): closed forms for one and two Gaussians, the 3-sigma cut-off, early termination,
-and invariance to input order."""
+invariance to input order, multi-tile binning against unbinned compositing; and for the
+anisotropic (velocity-elongated) Gaussians, closed-form screen covariances."""
 import math
 
 import numpy as np
+import pytest
 
 import oracle
 
@@ -193,3 +195,69 @@ def test_many_points_match_a_per_pixel_reference(simple_view):
                     break
             want[yy, xx] = acc
     np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-15)
+
+
+# ----------------------------------------------------------------- anisotropic Gaussians
+# On the 64 x 64 screen (cx = 2x, cy = 2y, cw = z) a point on the axis at depth 1 has the
+# screen-map Jacobian J = [[64, 0, 0], [0, -64, 0]], so a velocity along x gives the screen
+# covariance diag((64 r0 s)^2, (64 r0)^2); r0 = 1.5 / 64 makes the short axis 1.5 px.
+R0 = 1.5 / 64.0
+
+
+def _aniso_closed_form(sx, sy, cov, colour):
+    py, px = np.mgrid[0:64, 0:64]
+    dx, dy = px + 0.5 - sx, py + 0.5 - sy
+    a, b, c = cov
+    det = a * c - b * b
+    q = (c * dx * dx - 2 * b * dx * dy + a * dy * dy) / det
+    inside = (q <= 9.0) & (np.abs(dx) <= 3 * np.sqrt(a)) & (np.abs(dy) <= 3 * np.sqrt(c))
+    al = np.where(inside, 0.6 * np.exp(-0.5 * q), 0.0)
+    return al[..., None] * np.asarray(colour, np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("stretch", [1.0, 3.0, 6.0])
+def test_aniso_single_gaussian_along_x(simple_view, stretch):
+    v = simple_view(M64, 64, 64, 0.5, 10.0)
+    p = np.array([[0.0, 0.0, 1.0]], np.float32)            # projects to (32, 32)
+    col = [[0.2, 0.7, 0.4]]
+    img = oracle.splat_aniso(p, v, np.array(col, np.float32), np.array([[2.5, 0, 0]], np.float32),
+                             R0, stretch)
+    cov = ((64 * R0 * stretch) ** 2, 0.0, (64 * R0) ** 2)
+    np.testing.assert_allclose(img, _aniso_closed_form(32.0, 32.0, cov, col[0]), rtol=1e-12, atol=1e-15)
+    if stretch == 1.0:   # the isotropic renderer with sigma = 1.5 px
+        iso = oracle.splat(p, v, np.array(col, np.float32))
+        np.testing.assert_allclose(img, iso, rtol=1e-12, atol=1e-15)
+
+
+def test_aniso_diagonal_velocity_and_zero_velocity(simple_view):
+    """A velocity along (1, 1, 0) (screen y points down, so the long axis is (1, -1)) and a point
+    without velocity (isotropic), each against its closed-form covariance."""
+    v = simple_view(M64, 64, 64, 0.5, 10.0)
+    p = np.array([[0.0, 0.0, 1.0]], np.float32)
+    col = [[1.0, 0.5, 0.25]]
+    s = 4.0
+    img = oracle.splat_aniso(p, v, np.array(col, np.float32), np.array([[1, 1, 0]], np.float32), R0, s)
+    u = np.array([1.0, -1.0]) / np.sqrt(2.0)
+    cov2 = (64 * R0) ** 2 * (np.eye(2) + (s * s - 1) * np.outer(u, u))
+    np.testing.assert_allclose(img, _aniso_closed_form(32.0, 32.0, (cov2[0, 0], cov2[0, 1], cov2[1, 1]), col[0]),
+                               rtol=1e-10, atol=1e-14)
+    img0 = oracle.splat_aniso(p, v, np.array(col, np.float32), np.zeros((1, 3), np.float32), R0, s)
+    np.testing.assert_allclose(img0, oracle.splat(p, v, np.array(col, np.float32)), rtol=1e-12, atol=1e-15)
+
+
+def test_aniso_depth_scaling_and_order(simple_view):
+    """At depth z the Jacobian scales by 1/z (the footprint shrinks), nearer points composite
+    first whatever the input order."""
+    v = simple_view(M64, 64, 64, 0.5, 10.0)
+    col = np.array([[1, 0, 0], [0, 1, 0]], np.float32)
+    vel = np.array([[1, 0, 0], [0, 1, 0]], np.float32)
+    pts = np.array([[0.0, 0.0, 2.0], [0.0, 0.0, 1.0]], np.float32)   # the second is nearer
+    img = oracle.splat_aniso(pts, v, col, vel, R0, 3.0)
+    img2 = oracle.splat_aniso(pts[::-1].copy(), v, col[::-1].copy(), vel[::-1].copy(), R0, 3.0)
+    np.testing.assert_array_equal(img, img2)
+    # centre pixel: the near Gaussian (alpha 0.6 at its centre offset) over the far one
+    near = _aniso_closed_form(32.0, 32.0, ((64 * R0) ** 2, 0.0, (64 * R0 * 3) ** 2), [0, 1, 0])
+    far = _aniso_closed_form(32.0, 32.0, ((32 * R0 * 3) ** 2, 0.0, (32 * R0) ** 2), [1, 0, 0])
+    a_near = near[..., 1]
+    np.testing.assert_allclose(img[..., 1], a_near, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(img[..., 0], (1 - a_near) * far[..., 0], rtol=1e-12, atol=1e-15)
