@@ -79,9 +79,11 @@ typedef enum {
  *  NRV_PREC_F32       FP32 on the CUDA cores.
  *  NRV_PREC_BF16      BF16 operands and activations on the tensor cores.
  *  NRV_PREC_FP8       the FP8 network: E4M3 operands and activations for levels 1-3, BF16
- *                     for the full-resolution level 0 (its input is the BF16 G-buffer).  This
- *                     is the mode that meets a 2e-2 max-abs bound (and 45 dB) against an FP64
- *                     forward on full frames.
+ *                     for the full-resolution level 0 (its input is the BF16 G-buffer).  With
+ *                     Xavier-initialised weights it stays within 2e-2 max abs (and 45 dB) of
+ *                     an FP64 forward on full frames; with trained weights its PSNR stays
+ *                     above 45 dB but single pixels reach several percent of the output
+ *                     range (E4M3 keeps 3 mantissa bits).
  *  NRV_PREC_FP8_E4M3  every stored tensor E4M3 (a 16-channel E4M3 input): faster, but its
  *                     3-bit mantissas compound over the full-resolution layers to max-abs
  *                     errors of about 0.1 on full frames, above that bound. */
@@ -397,6 +399,43 @@ nrv_status nrv_net_layer_wgrad(nrv_net* net, int layer, const void* d_dy, const 
 nrv_status nrv_net_layer_dgrad(nrv_net* net, int layer, const void* d_dy, const void* d_mask,
                                int n, int h, int w, nrv_prec prec, void* d_dx, nrv_stream stream);
 
+/* --------------------------------------------------------------------------
+ * Gated post-processing network (Sec. 3.3's form of the network)
+ *
+ * Gated convolutions (feature and gate 3x3 convolutions, out = ELU(feature) *
+ * sigmoid(gate)), a 1x1 convolution of the G-buffers (keeping their C_in channels)
+ * injected, average-pooled by 0.5 per level, into the first block of every encoder
+ * level; 2x2 average pooling in the encoder, 2x2 stride-2 transposed convolutions and
+ * skip concatenations in the decoder, a linear 1x1 head to RGB.  Four levels of
+ * 16/32/64/128 channels (the paper's progression starts at 64 over five levels; at
+ * this width every layer keeps its weights resident on the tensor-core kernel):
+ *   g0 = 1x1(x), g_l = avgpool(g_{l-1});  e0 = gated(g0), e_l = gated([avgpool(e_{l-1}), g_l]);
+ *   u_l = convT(d_{l+1}), d_l = gated([u_l, e_l]) for l = 2, 1, 0 (d_3 = e_3);  rgb = 1x1(d0).
+ * Layer order: inj e0 e1 e2 e3 up2 d2 up1 d1 up0 d0 head; nrv_gnet_layer reports kind
+ * 2 (1x1), 1 (transposed) or 3 (gated, with weight_offset the feature weight W_f
+ * (C_out, C_in, 3, 3) and bias_offset its bias; the gate's W_g and b_g follow).  The
+ * flat FP32 parameters: per layer its weight(s) and bias(es) in that order, PyTorch
+ * layouts.  Inference only, BF16 activations with FP32 accumulation: nrv_gnet_shade
+ * takes n BF16 packed inputs [n][Hn][Wn][8] (nrv_pack) and writes [n][height][width][3]
+ * FP32.  Errors: NRV_ERR_ARG, NRV_ERR_STATE (no parameters), NRV_ERR_OOM. */
+typedef struct nrv_gnet nrv_gnet;
+int nrv_gnet_num_layers(void);
+nrv_status nrv_gnet_layer(int c_in, int layer, nrv_layer_info* out);
+nrv_status nrv_gnet_param_count(int c_in, int64_t* count);
+nrv_status nrv_gnet_create(int c_in, nrv_gnet** out);
+nrv_status nrv_gnet_destroy(nrv_gnet* net);
+nrv_status nrv_gnet_set_params(nrv_gnet* net, const float* d_params, nrv_stream stream);
+nrv_status nrv_gnet_shade(nrv_gnet* net, const void* d_netin_bf16, int n, int height, int width,
+                          float* d_rgb, nrv_stream stream);
+/* One layer (inj .. d0) alone, NHWC BF16 [n][h][w][.] in and out (h, w even), on the kernels
+ * nrv_gnet_shade runs: inj reads the 8-channel packed input and writes 8 channels (C_in real);
+ * the encoder layers e1..e3 take x1 = the pooled features and x2 = the injected 8-channel
+ * tensor, the decoder layers d2..d0 x1 = upsampled and x2 = skip; e0 and the transposed convs
+ * take x1 only (x2 NULL); a transposed conv writes [n][2h][2w][C_out].
+ * Errors: NRV_ERR_ARG, NRV_ERR_STATE. */
+nrv_status nrv_gnet_run_layer(nrv_gnet* net, int layer, const void* d_x1, const void* d_x2, int n,
+                              int h, int w, void* d_y, nrv_stream stream);
+
 /* Microbenchmarks behind rooflines that need a measured peak (asynchronous on `stream`;
  * the caller times them).  nrv_probe_ffma: `blocks` blocks of 256 threads, each thread
  * 8 independent FP32 FMA chains of `iters` steps (16 * iters FLOPs per thread), one result
@@ -513,10 +552,12 @@ nrv_status nrv_set_profiling(int on);
 int nrv_get_timings(float* ms, int cap);
 
 /* Tuned launch choices.  The render pass picks one of its variants (per view-count
- * class and point-count class) and the tensor-core convolution its row read-ahead and
- * CTAs per SM (per layer, shape and precision) by timing the candidates on the real
- * data at the first uncaptured launch that needs the choice; every candidate computes
- * the same result.  nrv_tune_save writes the choices made or loaded so far to a text
+ * class and point-count class) by timing them on the real data at the first uncaptured
+ * launch that needs the choice; the tensor-core convolution does the same for its
+ * launch shape (image rows per tile, accumulator buffers, ring slots, CTAs per SM; per
+ * layer, shape and precision) when the environment variable NRV_TC_TUNE is 1, and
+ * otherwise uses a choice found in the table or its default shape.  Every candidate
+ * computes the same result.  nrv_tune_save writes the choices made or loaded so far to a text
  * file, nrv_tune_load reads one back (a later process then skips the timing); when the
  * environment variable NRV_TUNE_CACHE names an existing file, the library loads it at
  * its first lookup.  Format: '#' comment lines and one choice per line,

@@ -44,6 +44,7 @@ def _L():
         P, I, I64, U64, F, D = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
                                 ctypes.c_float, ctypes.c_double)
         lib.oracle_visibility.argtypes = [P, U64, P, I, I, F, F, P]
+        lib.oracle_visibility_mt.argtypes = [P, U64, P, I, I, F, F, P]
         lib.oracle_resolve.argtypes = [P, I64, P, I64, I, P, P, P]
         lib.oracle_pack.argtypes = [P, P, P, I, I, I, I, I, P, P, P, P, P, F, F, I, I, F, P]
         lib.oracle_splat.argtypes = [P, U64, P, I, I, F, F, P, D, D, P]
@@ -59,13 +60,15 @@ def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def visibility(xyz: np.ndarray, view) -> np.ndarray:
-    """Per-pixel minimum key (bits(depth) << 32 | index) over all points; ~0 where empty."""
+def visibility(xyz: np.ndarray, view, threads: str = "one") -> np.ndarray:
+    """Per-pixel minimum key (bits(depth) << 32 | index) over all points; ~0 where empty.
+    threads="all": the same keys from per-thread minima combined by a minimum."""
     xyz = np.ascontiguousarray(xyz, np.float32)
     m = np.ascontiguousarray(view.viewproj, np.float32)
     key = np.empty((view.height, view.width), np.uint64)
-    _L().oracle_visibility(_p(xyz), xyz.shape[0], _p(m), view.width, view.height,
-                           float(view.znear), float(view.zfar), _p(key))
+    fn = _L().oracle_visibility_mt if threads == "all" else _L().oracle_visibility
+    fn(_p(xyz), xyz.shape[0], _p(m), view.width, view.height, float(view.znear),
+       float(view.zfar), _p(key))
     return key
 
 

@@ -22,6 +22,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <omp.h>
+
 static inline uint32_t fbits(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
 static inline float bitsf(uint32_t u) { float f; memcpy(&f, &u, 4); return f; }
 
@@ -50,6 +52,39 @@ void oracle_visibility(const float* xyz, uint64_t n, const float* M, int W, int 
         int64_t p = (int64_t)py * W + px;
         if (k < key[p]) key[p] = k;
     }
+}
+
+/*
+ * The same render pass on all cores: each thread keeps its own key image over a
+ * contiguous range of points (the per-pixel minimum of its points), then the
+ * images are combined by an element-wise minimum.  A minimum does not depend on
+ * the order its operands are taken in, so the keys equal oracle_visibility's.
+ */
+void oracle_visibility_mt(const float* xyz, uint64_t n, const float* M, int W, int H,
+                          float znear, float zfar, uint64_t* key) {
+    const int nth = omp_get_max_threads();
+    const int64_t npx = (int64_t)W * H;
+    uint64_t* part = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)npx * (size_t)nth);
+#pragma omp parallel num_threads(nth)
+    {
+        const int t = omp_get_thread_num();
+        const uint64_t lo = n * (uint64_t)t / (uint64_t)nth, hi = n * (uint64_t)(t + 1) / (uint64_t)nth;
+        uint64_t* k = part + (size_t)npx * (size_t)t;
+        oracle_visibility(xyz + 3 * lo, hi - lo, M, W, H, znear, zfar, k);
+        /* the sub-range's indices start at lo */
+        for (int64_t p = 0; p < npx; ++p)
+            if (k[p] != ~0ull) k[p] += lo;
+    }
+#pragma omp parallel for
+    for (int64_t p = 0; p < npx; ++p) {
+        uint64_t m = ~0ull;
+        for (int t = 0; t < nth; ++t) {
+            const uint64_t v = part[(size_t)npx * (size_t)t + (size_t)p];
+            if (v < m) m = v;
+        }
+        key[p] = m;
+    }
+    free(part);
 }
 
 /*
@@ -168,7 +203,6 @@ void oracle_pack(const uint32_t* depth, const uint8_t* mask, const uint32_t* gat
  *     of the sorted order and write them at per-(tile, thread) prefix offsets);
  *  4. composite each tile's pixels from its list (tiles are independent).
  * ------------------------------------------------------------------------- */
-#include <omp.h>
 
 typedef struct { uint32_t i; double sx, sy; } splat_t;
 

@@ -144,6 +144,23 @@ nrv_status tc_dgrad(const Net* net, int l, const void* gin, void* out, const voi
 // which C_out from g_off on, zeroed where mask (shaped like out) is not positive
 nrv_status tc_updgrad(const Net* net, int l, const void* g, int g_ld, int g_off, const void* mask,
                       void* out, int n, int H, int W, cudaStream_t s);
+// A layer of another network on the tensor-core conv kernel (tc.cu): a 3x3 conv (plain or
+// gated) or a 2x2 stride-2 transposed conv, BF16 row-planar in and out.  c1, c2: the stored
+// channels of the sources (multiples of 8; c2 = 0 without a second source), cin_real: the
+// weights' input channels (<= c1 + c2; the real channels come first in each source);
+// woff / boff: the weights and bias in the flat parameter vector, woff2 / boff2 the gate's.
+struct TcGeneric {
+    int kind, gated;
+    int c1, c2, cin_real, cout;
+    int64_t woff, boff, woff2, boff2;
+};
+struct TcPacked;
+nrv_status tc_generic_prepare(const TcGeneric* L, int n, const float* params, TcPacked** state,
+                              cudaStream_t s);
+nrv_status tc_generic_run(const TcPacked* st, int l, const float* params, const void* x1,
+                          const void* x2, void* y, int n, int H, int W, cudaStream_t s,
+                          const TcHead* head = nullptr, void* pool_y = nullptr);
+void tc_generic_free(TcPacked* st);
 nrv_status forward_fp8(Net* net, const uint8_t* netin, float* rgb, cudaStream_t s, bool keep_acts);
 // levels 1-3 in E4M3, level 0 in BF16 (fp8.cu); netin is the BF16 packed input
 nrv_status forward_fp8_mixed(Net* net, const void* netin, float* rgb, cudaStream_t s);

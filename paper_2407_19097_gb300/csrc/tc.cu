@@ -103,6 +103,10 @@ struct TcParams {
     uint32_t tmem_cols;
     const uint8_t* wpk;      // packed weights [slice][ks][half][n][16 bytes] (BF16 or E4M3)
     const float* bias;       // null: no bias (the data gradient)
+    int gated;               // gated conv: columns in groups of 32 -- 16 feature columns, then
+                             // the 16 gate columns of the same output channels; the output is
+                             // ELU(feature + bias) * sigmoid(gate + bias2), C_out = N / 2
+    const float* bias2;      // gated: the gate convolution's bias
     const uint8_t* mask;     // null, or a row-planar BF16 tensor shaped like the output: outputs
                              // where it is not positive are zeroed (ReLU of the layer below)
     void* y;                 // BF16 or E4M3 row-planar output
@@ -234,7 +238,13 @@ __global__ void __launch_bounds__(NTHREADS, 4)
     }
     // per output column of this slice: its bias (column n maps to channel n mod cout)
     for (int i = threadIdx.x; i < P.n_slice; i += NTHREADS) {
-        bias_s[i] = P.bias ? P.bias[(slice * P.n_slice + i) % P.cout] : 0.0f;
+        const int gcol = slice * P.n_slice + i;
+        if (P.gated) {
+            const int ch = 16 * (gcol / 32) + (gcol & 15);
+            bias_s[i] = (gcol & 16) ? P.bias2[ch] : P.bias[ch];
+        } else {
+            bias_s[i] = P.bias ? P.bias[gcol % P.cout] : 0.0f;
+        }
         colscale_s[i] = FP8 ? P.colscale[slice * P.n_slice + i] : 1.0f;
     }
     for (int i = threadIdx.x; i <= MAX_KS; i += NTHREADS) alo_s[i] = i < P.nks ? P.a_lo[i] : 0u;
@@ -431,7 +441,7 @@ __global__ void __launch_bounds__(NTHREADS, 4)
                 const bool valid = valid_x && yy < P.h;
                 const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) +
                                        (uint32_t)((ab * P.rpt + r) * P.nissue * P.n_slice);
-                for (int c0 = 0; c0 < P.n_slice; c0 += 16) {
+                for (int c0 = 0; c0 < P.n_slice; c0 += (P.gated ? 32 : 16)) {
                     uint32_t v32[16];
                     tmem_ld16(tbase + (uint32_t)c0, v32);
                     float acc[16];
@@ -448,8 +458,26 @@ __global__ void __launch_bounds__(NTHREADS, 4)
                         v[j] = fmaf(acc[j], colscale_s[c0 + j], bias_s[c0 + j]);
                         if (P.relu) v[j] = fmaxf(v[j], 0.0f);
                     }
+                    if (!FP8 && P.gated) {
+                        // ELU(feature) * sigmoid(gate): the gate columns follow the features
+                        tmem_ld16(tbase + (uint32_t)(c0 + 16), v32);
+                        float gte[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) gte[j] = __uint_as_float(v32[j]);
+                        if (P.nissue == 2) {
+                            tmem_ld16(tbase + (uint32_t)(P.n_slice + c0 + 16), v32);
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) gte[j] += __uint_as_float(v32[j]);
+                        }
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const float gv = gte[j] + bias_s[c0 + 16 + j];
+                            const float f = v[j] > 0.0f ? v[j] : expm1f(v[j]);
+                            v[j] = f / (1.0f + expf(-gv));
+                        }
+                    }
                     if (valid) {
-                        const int ng = slice * P.n_slice + c0;
+                        const int ng = (slice * P.n_slice + c0) >> (P.gated ? 1 : 0);
                         size_t row;   // output image row
                         int xo, wo, o;
                         if (P.mode != 1) {
@@ -519,7 +547,7 @@ __global__ void __launch_bounds__(NTHREADS, 4)
                             if (P.pool_y && r == 0) {
                                 // the even row as stored, for the pool after the odd row
                                 uint4* st = reinterpret_cast<uint4*>(smem + P.stash_off) +
-                                            (c0 / 8) * TILE_M + m;
+                                            ((c0 >> (P.gated ? 1 : 0)) / 8) * TILE_M + m;
                                 st[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
                                 st[TILE_M] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
                             }
@@ -542,13 +570,14 @@ __global__ void __launch_bounds__(NTHREADS, 4)
                         // x + 1 (the next lane), as stored; the mean is rounded to BF16
                         const size_t prow = (size_t)w.img * (P.h >> 1) + (w.y >> 1);
                         const int wp = P.w >> 1;
-                        const int o = slice * P.n_slice + c0;
+                        const int o = (slice * P.n_slice + c0) >> (P.gated ? 1 : 0);
 #pragma unroll
                         for (int h8 = 0; h8 < 16; h8 += 8) {
                             float a[8], c[8];
                             if (valid) {
                                 const uint4 raw = *reinterpret_cast<const uint4*>(
-                                    smem + P.stash_off + (((c0 + h8) / 8) * TILE_M + m) * 16);
+                                    smem + P.stash_off +
+                                    ((((c0 >> (P.gated ? 1 : 0)) + h8) / 8) * TILE_M + m) * 16);
                                 const uint32_t rw[4] = {raw.x, raw.y, raw.z, raw.w};
 #pragma unroll
                                 for (int j = 0; j < 4; ++j) {
@@ -663,6 +692,7 @@ struct Half {
 struct TcLayerCfg {
     bool ok = false;
     int kind = CONV3;
+    int gated = 0;           // gated 3x3 conv: N = 2 C_out in groups of 16 feature + 16 gate columns
     int c1 = 0, c2 = 0;      // channels per source (padded input width for the first layer)
     int rows = 3, row0 = -1;
     int ncols = 0;           // GEMM N (C_out, or 4 C_out)
@@ -685,6 +715,8 @@ constexpr int KIND_UPDGRAD = 4;  // packing of the transposed conv's data-gradie
 // One packing job: a layer's weights in one operand layout.
 struct PackJob {
     int64_t woff;
+    int64_t woff2;           // gated: the gate weights (the feature weights at woff)
+    int gated;
     int kind, cin_real, cout, n_slice, nslices, nks, c1, fp8;
     float fold;
     const float* s_w;
@@ -716,7 +748,11 @@ __device__ __forceinline__ void pack_element(const float* __restrict__ P, const 
             if (c < J.cout && n < J.cin_real)
                 v = P[J.woff + ((size_t)c * J.cin_real + n) * 9 + (8 - h.x)];
         } else if (c < J.cin_real) {
-            if (J.kind == CONV3) v = P[J.woff + ((size_t)n * J.cin_real + c) * 9 + h.x];
+            if (J.kind == CONV3 && J.gated) {
+                // column n: group n / 32 of 16 output channels, feature (n % 32 < 16) or gate
+                const int o = 16 * (n / 32) + (n & 15);
+                v = P[((n & 16) ? J.woff2 : J.woff) + ((size_t)o * J.cin_real + c) * 9 + h.x];
+            } else if (J.kind == CONV3) v = P[J.woff + ((size_t)n * J.cin_real + c) * 9 + h.x];
             else v = P[J.woff + ((size_t)c * J.cout + n % J.cout) * 4 + n / J.cout];
             if (h.y == 1) v *= J.fold;
         }
@@ -959,7 +995,7 @@ static nrv_status tc_repack_dgrad(Net* net, cudaStream_t s) {
         if (!c.ok) continue;
         const Layer& L = net->layers[l];
         const int kind = c.kind == KIND_UPDGRAD ? KIND_UPDGRAD : KIND_DGRAD;
-        J.job[J.n++] = PackJob{L.woff, kind, L.cin, L.cout, c.n_slice, c.nslices, c.nks, c.c1, 0,
+        J.job[J.n++] = PackJob{L.woff, 0, 0, kind, L.cin, L.cout, c.n_slice, c.nslices, c.nks, c.c1, 0,
                                1.0f, nullptr, (const int4*)g_halves[2].p + hoff[l],
                                (uint8_t*)net->wtbf16.p + c.w_off};
     }
@@ -980,7 +1016,7 @@ nrv_status tc_repack(Net* net, cudaStream_t s) {
         const TcLayerCfg& c = g_cfg[0][l];
         if (!c.ok) continue;
         const Layer& L = net->layers[l];
-        J.job[J.n++] = PackJob{L.woff, c.kind, L.cin, L.cout, c.n_slice, c.nslices, c.nks, c.c1, 0,
+        J.job[J.n++] = PackJob{L.woff, 0, 0, c.kind, L.cin, L.cout, c.n_slice, c.nslices, c.nks, c.c1, 0,
                                1.0f, nullptr, (const int4*)g_halves[0].p + hoff[l],
                                (uint8_t*)net->wbf16.p + c.w_off};
     }
@@ -1035,7 +1071,7 @@ nrv_status tc_repack_fp8(Net* net, cudaStream_t s) {
             (const float*)net->params.p, L.woff, c.kind, L.cin, c1_real, L.cout, c.ncols, fold,
             s_in, s_w + c.cs_off, colscale + c.cs_off);
         NRV_CHECK_LAUNCH();
-        const PackJob job{L.woff, c.kind, L.cin, L.cout, c.n_slice, c.nslices, c.nks, c.c1, 1,
+        const PackJob job{L.woff, 0, 0, c.kind, L.cin, L.cout, c.n_slice, c.nslices, c.nks, c.c1, 1,
                           fold, s_w + c.cs_off, (const int4*)g_halves[1].p + hoff[l],
                           (uint8_t*)net->wfp8.p + c.w_off};
         pack_tc_weights_kernel<<<64, 256, 0, s>>>((const float*)net->params.p, job);
@@ -1066,7 +1102,8 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
                             const float* bias, int relu, const void* mask, int cout, const void* x1,
                             int c1, const void* x2, int c2, void* y, int n, int H, int W,
                             cudaStream_t s, int fp8, float inv_out, const TcHead* head = nullptr,
-                            void* pool_y = nullptr, int g_ld = 0, int g_off = 0) {
+                            void* pool_y = nullptr, int g_ld = 0, int g_off = 0,
+                            const float* bias2 = nullptr) {
     if (!c.ok || c.c1 != c1 || c.c2 != c2) return fail(NRV_ERR_UNSUPPORTED, "layer not configured");
     if (fp8 && !net->fp8_ready) return fail(NRV_ERR_STATE, "FP8 needs activation scales");
     if (n <= 0 || H <= 0 || W <= 0) return fail(NRV_ERR_ARG, "empty tensor");
@@ -1091,6 +1128,10 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
     P.out_nch = cout / ce;
     P.mode = conv ? 0 : (updg ? 2 : 1);
     P.relu = relu;
+    P.gated = c.gated;
+    P.bias2 = bias2;
+    if (c.gated && (fp8 || !bias || !bias2 || relu || mask || c.n_slice % 32))
+        return fail(NRV_ERR_UNSUPPORTED, "gated conv: BF16, both biases, slices of 32 columns");
     P.mask = (const uint8_t*)mask;
     P.has_src2 = c.c2 > 0;
     const uint32_t nch1 = c.c1 / ce, nch2 = c.c2 / ce;
@@ -1180,7 +1221,8 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
         P.pool_y = pool_y;
     }
     if (head) {
-        if (!conv || c.nslices != 1 || c.n_slice != 16 || cout != 16 || !relu)
+        if (!conv || c.nslices != 1 || c.n_slice != (c.gated ? 32 : 16) || cout != 16 ||
+            !(relu || c.gated))
             return fail(NRV_ERR_UNSUPPORTED, "the fused head needs a 16-channel conv");
         P.head_w = head->w;
         P.head_b = head->b;
@@ -1286,14 +1328,16 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
         NRV_CHECK_LAUNCH();
         return NRV_OK;
     };
-    // Tuned choice of (ring slots, CTAs per SM) for this layer shape: looked up, else -- unless
-    // NRV_TC_TUNE=0 or the stream is capturing -- timed on the real data at this first launch
-    // (every candidate computes the same output; the chosen one runs last).
+    // Tuned launch shape for this layer shape: a choice in the tuned-choice table (loaded from a
+    // cache file) is used; with NRV_TC_TUNE=1 a missing one is timed on the real data at this
+    // first launch unless the stream is capturing (every candidate computes the same output; the
+    // chosen one runs last).  Otherwise the default shape above.  Tuning is opt-in: its timings
+    // are only as good as the quiet of the GPU it runs on (a profiler's serialisation, for one,
+    // misleads it), and it gains about 1% on the 1080p network.
     static const int tune_on = [] {
         const char* e = getenv("NRV_TC_TUNE");
-        return (e && e[0] == '0') ? 0 : 1;
+        return (e && e[0] == '1') ? 1 : 0;
     }();
-    if (!tune_on) return launch_with(rpt0, nacc0, nslot, 0);
     char key[200];
     snprintf(key, sizeof(key),
              "conv fp8=%d mode=%d c1=%d c2=%d cout=%d nks=%d slice=%dx%d pool=%d head=%d mask=%d "
@@ -1312,6 +1356,7 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
     };
     int choice = 0;
     if (tune_get(key, &choice) && valid_choice(choice)) return launch_choice(choice);
+    if (!tune_on) return launch_with(rpt0, nacc0, nslot, 0);
     cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
     NRV_CHECK_CUDA(cudaStreamIsCapturing(s, &capst));
     if (capst != cudaStreamCaptureStatusNone) return launch_with(rpt0, nacc0, nslot, 0);
@@ -1357,6 +1402,104 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
     tune_put(key, arg);
     tune_count_timing();
     return launch_choice(arg);
+}
+
+// ------------------------------------------------------------------ layers of other networks
+// The same kernel for a list of layers described by TcGeneric (the gated network): their
+// configurations, their K-order tables and their BF16 weights, packed from a flat parameter
+// vector in one launch.
+struct TcPacked {
+    std::vector<TcGeneric> spec;
+    std::vector<TcLayerCfg> cfg;
+    DevBuf w;        // packed BF16 weights of every layer
+    DevBuf halves;   // K-order tables of every layer
+};
+
+nrv_status tc_generic_prepare(const TcGeneric* L, int n, const float* params, TcPacked** state,
+                              cudaStream_t s) {
+    if (n < 1 || n > NUM_LAYERS) return fail(NRV_ERR_ARG, "1..%d layers", NUM_LAYERS);
+    TcPacked* st = *state;
+    if (!st) *state = st = new TcPacked();
+    st->spec.assign(L, L + n);
+    st->cfg.assign(n, TcLayerCfg());
+    std::vector<int4> all;
+    std::vector<size_t> hoff(n, 0);
+    size_t off = 0;
+    const int ce = 8;
+    for (int l = 0; l < n; ++l) {
+        TcLayerCfg& c = st->cfg[l];
+        c.kind = L[l].kind;
+        c.gated = L[l].gated;
+        c.c1 = L[l].c1;
+        c.c2 = L[l].c2;
+        if (c.c1 % ce || c.c2 % ce || L[l].cout % 16) return fail(NRV_ERR_UNSUPPORTED, "channel counts");
+        if (c.kind == CONV3) {
+            c.rows = 3;
+            c.row0 = -1;
+            c.ncols = (c.gated ? 2 : 1) * L[l].cout;
+            // K order within a kernel row: source, channel chunk, dx -- ascending slot offsets,
+            // so the two halves of every K-step are in order whatever the chunk counts
+            for (int dy = 0; dy < 3; ++dy) {
+                const size_t start = c.halves.size();
+                for (int src = 0; src < 2; ++src)
+                    for (int ch = 0; ch < (src == 0 ? c.c1 : c.c2) / ce; ++ch)
+                        for (int dx = 0; dx < 3; ++dx)
+                            c.halves.push_back(Half{3 * dy + dx, src, ch});
+                if ((c.halves.size() - start) % 2) c.halves.push_back(Half{-1, 0, 0});
+            }
+        } else if (c.kind == UPCONV2 && !c.gated && c.c2 == 0) {
+            c.rows = 1;
+            c.row0 = 0;
+            c.ncols = 4 * L[l].cout;
+            for (int ch = 0; ch < c.c1 / ce; ++ch) c.halves.push_back(Half{0, 0, ch});
+            if (c.halves.size() % 2) c.halves.push_back(Half{-1, 0, 0});
+        } else {
+            return fail(NRV_ERR_UNSUPPORTED, "layer kind");
+        }
+        c.nks = (int)c.halves.size() / 2;
+        if (c.nks > MAX_KS) return fail(NRV_ERR_UNSUPPORTED, "K too long for resident weights");
+        // widest output slice whose weights fit in 80 KB (gated: whole 32-column groups)
+        const int minw = c.gated ? 32 : 16;
+        int ns = c.ncols;
+        while (ns > minw && (size_t)c.nks * 2 * ns * 16 > 80 * 1024) ns /= 2;
+        if (c.ncols % ns || ns % minw) return fail(NRV_ERR_UNSUPPORTED, "slice width");
+        c.n_slice = ns;
+        c.nslices = c.ncols / ns;
+        c.w_bytes = (uint32_t)c.nks * 2 * ns * 16;
+        c.w_off = off;
+        off += ((size_t)c.w_bytes * c.nslices + 1023) / 1024 * 1024;
+        hoff[l] = all.size();
+        for (const Half& h : c.halves) all.push_back(make_int4(h.tap, h.src, h.chunk, 0));
+        c.ok = true;
+    }
+    NRV_TRY(st->w.ensure(off));
+    NRV_TRY(st->halves.ensure(all.size() * sizeof(int4)));
+    // the tables depend on shapes only; the copy is stream-ordered before the packing
+    NRV_CHECK_CUDA(cudaMemcpyAsync(st->halves.p, all.data(), all.size() * sizeof(int4),
+                                   cudaMemcpyHostToDevice, s));
+    NRV_CHECK_CUDA(cudaStreamSynchronize(s));   // `all` goes out of scope
+    PackJobs J;
+    memset(&J, 0, sizeof(J));
+    for (int l = 0; l < n; ++l) {
+        const TcLayerCfg& c = st->cfg[l];
+        J.job[J.n++] = PackJob{L[l].woff, L[l].woff2, L[l].gated, c.kind, L[l].cin_real, L[l].cout,
+                               c.n_slice, c.nslices, c.nks, c.c1, 0, 1.0f, nullptr,
+                               (const int4*)st->halves.p + hoff[l], (uint8_t*)st->w.p + c.w_off};
+    }
+    return pack_all(params, J, s);
+}
+
+void tc_generic_free(TcPacked* st) { delete st; }
+
+nrv_status tc_generic_run(const TcPacked* st, int l, const float* params, const void* x1,
+                          const void* x2, void* y, int n, int H, int W, cudaStream_t s,
+                          const TcHead* head, void* pool_y) {
+    if (!st || l < 0 || l >= (int)st->cfg.size()) return fail(NRV_ERR_ARG, "bad layer");
+    const TcLayerCfg& c = st->cfg[l];
+    const TcGeneric& L = st->spec[l];
+    return tc_launch(nullptr, c, (const uint8_t*)st->w.p + c.w_off, params + L.boff,
+                     (c.kind == CONV3 && !c.gated) ? 1 : 0, nullptr, L.cout, x1, c.c1, x2, c.c2, y,
+                     n, H, W, s, 0, 1.0f, head, pool_y, 0, 0, c.gated ? params + L.boff2 : nullptr);
 }
 
 nrv_status tc_conv3(const Net* net, int l, const void* x1, int c1, const void* x2, int c2, void* y,

@@ -108,6 +108,14 @@ SIGNATURES = {
     "nrv_set_profiling": (I, [I]),
     "nrv_get_timings": (I, [ctypes.POINTER(F), I]),
     "nrv_sync_status": (I, [P]),
+    "nrv_gnet_num_layers": (I, []),
+    "nrv_gnet_layer": (I, [I, I, ctypes.POINTER(nrv_layer_info)]),
+    "nrv_gnet_param_count": (I, [I, ctypes.POINTER(I64)]),
+    "nrv_gnet_create": (I, [I, ctypes.POINTER(P)]),
+    "nrv_gnet_destroy": (I, [P]),
+    "nrv_gnet_set_params": (I, [P, P, P]),
+    "nrv_gnet_shade": (I, [P, P, I, I, I, P, P]),
+    "nrv_gnet_run_layer": (I, [P, I, P, P, I, I, I, P, P]),
     "nrv_tune_load": (I, [ctypes.c_char_p]),
     "nrv_tune_save": (I, [ctypes.c_char_p]),
     "nrv_tune_count": (I, []),
@@ -324,6 +332,38 @@ class Net:
     def close(self):
         if self.h:
             lib().nrv_destroy_net(self.h)
+            self.h = None
+
+    __del__ = close
+
+
+class GatedNet:
+    """The gated post-processing network (include/nrv.h, nrv_gnet_*): BF16 inference."""
+
+    def __init__(self, c_in: int):
+        h = ctypes.c_void_p()
+        check(lib().nrv_gnet_create(c_in, ctypes.byref(h)))
+        self.h, self.c_in = h, c_in
+
+    @staticmethod
+    def param_count(c_in: int) -> int:
+        n = ctypes.c_int64()
+        check(lib().nrv_gnet_param_count(c_in, ctypes.byref(n)))
+        return n.value
+
+    def set_params(self, params, stream=None):
+        check(lib().nrv_gnet_set_params(self.h, _ptr(params), _stream(stream)))
+
+    def shade(self, netin, n, height, width, rgb, stream=None):
+        check(lib().nrv_gnet_shade(self.h, _ptr(netin), n, height, width, _ptr(rgb), _stream(stream)))
+
+    def run_layer(self, layer, x1, x2, n, height, width, y, stream=None):
+        check(lib().nrv_gnet_run_layer(self.h, layer, _ptr(x1), None if x2 is None else _ptr(x2), n,
+                                       height, width, _ptr(y), _stream(stream)))
+
+    def close(self):
+        if self.h:
+            lib().nrv_gnet_destroy(self.h)
             self.h = None
 
     __del__ = close

@@ -41,7 +41,7 @@ print("timings", nrv.lib().nrv_tune_timings(), "count", nrv.lib().nrv_tune_count
 def _run(tmp, args, env_extra):
     script = tmp / "tune_run.py"
     script.write_text(SCRIPT.format(root=ROOT))
-    env = dict(os.environ, PYTHONPATH=os.path.join(ROOT, "tests"), **env_extra)
+    env = dict(os.environ, PYTHONPATH=os.path.join(ROOT, "tests"), NRV_TC_TUNE="1", **env_extra)
     env.pop("NRV_VIS_VARIANT", None)
     r = subprocess.run([sys.executable, str(script), *args], env=env, capture_output=True, text=True,
                        timeout=600)
@@ -55,7 +55,7 @@ def test_cached_choices_are_reused_and_frames_identical(tmp_path):
     timed_a, count_a = _run(tmp_path, [str(tmp_path / "a.npy"), str(cache)], {"NRV_TUNE_CACHE": ""})
     assert timed_a > 0 and count_a > 0
     text = cache.read_text()
-    assert "render multi=1" in text and "render multi=0" in text
+    assert "render multi=1" in text and "render multi=0" in text and "conv " in text
     timed_b, count_b = _run(tmp_path, [str(tmp_path / "b.npy")], {"NRV_TUNE_CACHE": str(cache)})
     assert timed_b == 0 and count_b == count_a
     assert np.array_equal(np.load(tmp_path / "a.npy"), np.load(tmp_path / "b.npy"))

@@ -134,3 +134,16 @@ def test_resolve_copies_the_winners_record():
         assert np.all(gattr[c][~hit] == 0)
     assert np.all(depth[~hit] == 0)
     assert 0.05 < hit.mean() < 1.0
+
+
+def test_all_core_render_pass_equals_the_sequential_one():
+    """The multi-threaded oracle render pass (per-thread minima combined by a minimum) gives the
+    sequential pass's keys, ties and duplicates included."""
+    import nrv_inputs as I
+    sc = I.trajectory_scene(3001, 35, seed=2)
+    xyz = np.concatenate([sc.xyz, sc.xyz[::7]])               # duplicates: lowest index wins
+    view = I.fitted_view(sc, 200, 120)
+    a = oracle.visibility(xyz, view)
+    b = oracle.visibility(xyz, view, threads="all")
+    assert np.array_equal(a, b)
+    assert (a != np.uint64(0xFFFFFFFFFFFFFFFF)).mean() > 0.1
