@@ -129,6 +129,16 @@ struct TcParams {
     void* pool_y;            // (BF16 only)
     uint32_t stash_off;      // pool: shared-memory copy of the tile's even row as stored,
                              // [16-byte word][128 lanes][16 bytes], after the ring
+    // Row streaming (mode 0): the weights of the three kernel rows side by side as B,
+    // N = 3 n_slice, columns [kernel row 2 | row 1 | row 0]; each input row is multiplied
+    // once and its products land in the TMEM blocks of the output rows above, at and below
+    // it.  The blocks form a ring of nb blocks of n_slice columns (output row slot q uses
+    // block q mod nb), zeroed by the epilogue after it drains them, so every MMA
+    // accumulates.  Input rows are committed in groups of grp; the issuer stays at most
+    // gm groups ahead of the epilogue.
+    int stream;
+    int nb, grp, gm;
+    uint32_t idesc2, idesc1;   // instruction descriptors for N = 2 n_slice and n_slice
     // per K-step of one input row (every row of a tile has the same pattern):
     // low word of the A descriptor relative to the row's slot,
     // (offset >> 4) | (LBO >> 4) << 16; K-step ks reads row ks / (nks / rows)
@@ -161,6 +171,41 @@ struct TileWalk {
     }
 };
 
+// Row streaming: the output row held by each ring slot in turn.  A CTA's run of tiles splits
+// into segments (one tile column each); a segment of R output rows streams R + 2 input rows,
+// and its slots hold output rows y0 - 2 .. y0 + R - 1, the first two belonging to no one.
+struct SlotCursor {
+    int t, seg_left, y0, r, img, x;
+    bool vx;
+    __device__ __forceinline__ void init(int t_begin) {
+        t = t_begin;
+        seg_left = 0;
+        y0 = r = img = x = 0;
+        vx = false;
+    }
+    __device__ __forceinline__ void next(const TcParams& P, int t_end, int m, bool& real, int& si,
+                                         int& sx, bool& sv, int& sy) {
+        if (seg_left == 0) {
+            const int col = t / P.hr;
+            const int te = t_end < (col + 1) * P.hr ? t_end : (col + 1) * P.hr;
+            y0 = (t - col * P.hr) * P.rpt;
+            seg_left = (te - t) * P.rpt + 2;
+            r = 0;
+            img = col / P.tiles_x;
+            x = (col - img * P.tiles_x) * P.tile_w + m;
+            vx = m < P.tile_w && x < P.w;
+            t = te;
+        }
+        real = r >= 2;
+        si = img;
+        sx = x;
+        sy = y0 + r - 2;
+        sv = vx && sy < P.h;
+        ++r;
+        --seg_left;
+    }
+};
+
 // Ring position (slot, phase parity of its use) advanced without divisions.
 __device__ __forceinline__ void ring_next(int& slot, uint32_t& phase, int nslot) {
     if (++slot == nslot) {
@@ -176,24 +221,31 @@ __device__ __forceinline__ void head_store(const TcParams& P, const float* hw, i
     if (y >= P.rgb_h || x >= P.rgb_w) return;
     float* out = rgb_image(P.rgb, P.rgb_tab, (size_t)img, (size_t)P.rgb_h * P.rgb_w) +
                  ((size_t)y * P.rgb_w + x) * 3;
+    const float4* h4 = reinterpret_cast<const float4*>(hw);   // 16-byte aligned
 #pragma unroll
     for (int o = 0; o < 3; ++o) {
         float acc = hw[48 + o];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) acc = fmaf(hw[o * 16 + c], v[c], acc);
+        for (int c4 = 0; c4 < 4; ++c4) {
+            const float4 w4 = h4[o * 4 + c4];
+            acc = fmaf(w4.x, v[4 * c4], acc);
+            acc = fmaf(w4.y, v[4 * c4 + 1], acc);
+            acc = fmaf(w4.z, v[4 * c4 + 2], acc);
+            acc = fmaf(w4.w, v[4 * c4 + 3], acc);
+        }
         out[o] = acc;
     }
 }
 
-template <bool FP8>
-__global__ void __launch_bounds__(NTHREADS, 4)
+template <bool FP8, bool STREAM, bool GATED>
+__global__ void __launch_bounds__(NTHREADS, STREAM ? 3 : 4)
     conv3_tc_kernel(const __grid_constant__ CUtensorMap tm1, const __grid_constant__ CUtensorMap tm2,
                     const __grid_constant__ TcParams P) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t bars[2 * MAX_SLOTS + 2 * MAX_ACC + 2];
-    __shared__ float bias_s[256];
-    __shared__ float colscale_s[256];
-    __shared__ float head_ws[52];
+    __shared__ __align__(16) float bias_s[256];
+    __shared__ __align__(16) float colscale_s[256];
+    __shared__ __align__(16) float head_ws[52];
     __shared__ uint32_t alo_s[MAX_KS + 1];
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
@@ -239,7 +291,7 @@ __global__ void __launch_bounds__(NTHREADS, 4)
     // per output column of this slice: its bias (column n maps to channel n mod cout)
     for (int i = threadIdx.x; i < P.n_slice; i += NTHREADS) {
         const int gcol = slice * P.n_slice + i;
-        if (P.gated) {
+        if (GATED) {
             const int ch = 16 * (gcol / 32) + (gcol & 15);
             bias_s[i] = (gcol & 16) ? P.bias2[ch] : P.bias[ch];
         } else {
@@ -261,6 +313,17 @@ __global__ void __launch_bounds__(NTHREADS, 4)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
+    if (STREAM) {
+        // row streaming accumulates into every block: start from zeros
+        if (warp >= 2 && warp <= 5) {
+            const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
+            for (int c = 0; c < P.nb * P.n_slice; c += 16) tmem_zero16(tmem + lanes + (uint32_t)c);
+            tmem_st_wait();
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
     // Programmatic dependent launch: everything above may overlap the previous kernel
     // (it reads only weights, biases and scales, written at least two launches earlier);
     // activations are read, and outputs written, only after the previous kernel has
@@ -335,6 +398,73 @@ __global__ void __launch_bounds__(NTHREADS, 4)
             const uint32_t ring16 = s_ring >> 4, slot16 = P.slot_bytes >> 4;
             const int ks_row = P.nks / P.rows;   // K-steps per input row
             const int nis = P.nissue;
+            if (STREAM) {
+                // B of one row K-step: 3 n_slice rows, halves 3 n_slice * 16 bytes apart
+                const uint32_t b_lbo3 = (uint32_t)P.n_slice * 48;
+                const uint32_t b_lo0s = ((s_w >> 4) & 0x3FFFu) | ((b_lbo3 >> 4) << 16);
+                const uint32_t b_jstep = (2 * b_lbo3) >> 4;
+                const uint32_t b_n1 = (uint32_t)P.n_slice;   // n_slice rows of B, in 16 bytes
+                const uint32_t ns = (uint32_t)P.n_slice;
+                int slot = 0, blk = 0, gin = 0, k = 0;
+                uint32_t ph = 0;
+                // segments: runs of tiles in one tile column; a segment of R output rows
+                // streams its R + 2 input rows, whose slots hold output rows y0 - 2 .. y0 + R - 1
+                for (int t = t_begin; ok && t < t_end;) {
+                    const int col = t / P.hr;
+                    const int te = t_end < (col + 1) * P.hr ? t_end : (col + 1) * P.hr;
+                    const int nrows = (te - t) * P.rpt + 2;
+                    t = te;
+                    for (int r = 0; r < nrows; ++r) {
+                        if (gin == 0 && k >= P.gm) {
+                            // the blocks this group writes were last drained in group k - gm
+                            const int kk = k - P.gm;
+                            if (!mbar_wait(b_aempty(kk & 3), (kk >> 2) & 1, &abort_flag, P.status)) {
+                                ok = false;
+                                break;
+                            }
+                        }
+                        if (!mbar_wait(b_hfull(slot), ph, &abort_flag, P.status)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t base = ring16 + (uint32_t)slot * slot16;
+                        const uint32_t d = tmem + (uint32_t)blk * ns;
+                        uint32_t b_lo = b_lo0s;
+                        if (blk <= P.nb - 3) {
+                            for (int j = 0; j < ks_row; ++j, b_lo += b_jstep) {
+                                const uint64_t a = hi | (uint64_t)(base + alo_s[j]);
+                                if (FP8) mma_fp8(d, a, hi | (uint64_t)b_lo, P.idesc, 1u);
+                                else mma_bf16(d, a, hi | (uint64_t)b_lo, P.idesc, 1u);
+                            }
+                        } else {
+                            // the three blocks wrap around the ring: two MMAs per K-step
+                            const uint32_t id_a = blk == P.nb - 2 ? P.idesc2 : P.idesc1;
+                            const uint32_t id_b = blk == P.nb - 2 ? P.idesc1 : P.idesc2;
+                            const uint32_t b_off = blk == P.nb - 2 ? 2 * b_n1 : b_n1;
+                            for (int j = 0; j < ks_row; ++j, b_lo += b_jstep) {
+                                const uint64_t a = hi | (uint64_t)(base + alo_s[j]);
+                                if (FP8) {
+                                    mma_fp8(d, a, hi | (uint64_t)b_lo, id_a, 1u);
+                                    mma_fp8(tmem, a, hi | (uint64_t)(b_lo + b_off), id_b, 1u);
+                                } else {
+                                    mma_bf16(d, a, hi | (uint64_t)b_lo, id_a, 1u);
+                                    mma_bf16(tmem, a, hi | (uint64_t)(b_lo + b_off), id_b, 1u);
+                                }
+                            }
+                        }
+                        mma_commit(b_hempty(slot));   // the row is read once
+                        ring_next(slot, ph, P.nslot);
+                        if (++blk == P.nb) blk = 0;
+                        if (++gin == P.grp) {
+                            mma_commit(b_afull(k & 3));
+                            gin = 0;
+                            ++k;
+                        }
+                    }
+                }
+                if (ok && gin > 0) mma_commit(b_afull(k & 3));   // the last, partial group
+            } else {
             TileWalk w;
             w.init(P, t_begin);
             int cur_col = -1, next_row = 0;
@@ -414,6 +544,7 @@ __global__ void __launch_bounds__(NTHREADS, 4)
                 mma_commit(b_afull(ab));
                 w = w2;
             }
+            }
             // wait until every MMA issued above (by both issuers) has completed
             mma_commit(b_done);
             mbar_wait(b_done, 0, &abort_flag, P.status, false);
@@ -423,6 +554,395 @@ __global__ void __launch_bounds__(NTHREADS, 4)
         const int q = warp & 3;
         const int m = 32 * q + lane;
         constexpr int ce = FP8 ? 16 : 8;   // channels per 16-byte plane
+        // one output row of this thread's pixel x from the accumulator columns at tbase (and,
+        // with two issuers, their partials n_slice columns on): scale, bias, activation,
+        // mask, store, and the fused pool (even rows kept, odd rows pooled) and head
+        auto emit_row = [&](uint32_t tbase, int img, int x, bool valid, int yy) {
+            for (int c0 = 0; c0 < P.n_slice; c0 += (GATED ? 32 : 16)) {
+                uint32_t v32[16];
+                tmem_ld16(tbase + (uint32_t)c0, v32);
+                float acc[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc[j] = __uint_as_float(v32[j]);
+                if (P.nissue == 2) {
+                    tmem_ld16(tbase + (uint32_t)(P.n_slice + c0), v32);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) acc[j] += __uint_as_float(v32[j]);
+                }
+                // scale (FP8: input x weight scale per column) and bias, four columns per
+                // shared-memory load
+                float v[16];
+                const float4* b4 = reinterpret_cast<const float4*>(bias_s + c0);
+                const float4* s4 = reinterpret_cast<const float4*>(colscale_s + c0);
+#pragma unroll
+                for (int q4 = 0; q4 < 4; ++q4) {
+                    const float4 bb = b4[q4];
+                    const float bq[4] = {bb.x, bb.y, bb.z, bb.w};
+                    float sq[4] = {1.0f, 1.0f, 1.0f, 1.0f};
+                    if (FP8) {
+                        const float4 ss = s4[q4];
+                        sq[0] = ss.x;
+                        sq[1] = ss.y;
+                        sq[2] = ss.z;
+                        sq[3] = ss.w;
+                    }
+#pragma unroll
+                    for (int i4 = 0; i4 < 4; ++i4) {
+                        const int j = 4 * q4 + i4;
+                        v[j] = FP8 ? fmaf(acc[j], sq[i4], bq[i4]) : acc[j] + bq[i4];
+                        if (P.relu) v[j] = fmaxf(v[j], 0.0f);
+                    }
+                }
+                if (!FP8 && GATED) {
+                    // ELU(feature) * sigmoid(gate): the gate columns follow the features
+                    tmem_ld16(tbase + (uint32_t)(c0 + 16), v32);
+                    float gte[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) gte[j] = __uint_as_float(v32[j]);
+                    if (P.nissue == 2) {
+                        tmem_ld16(tbase + (uint32_t)(P.n_slice + c0 + 16), v32);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) gte[j] += __uint_as_float(v32[j]);
+                    }
+                    // ELU(f) = f for f > 0, e^f - 1 otherwise; sigmoid(g) = 1 / (1 + e^-g) --
+                    // with the fast exponential and quotient (relative error ~1e-6, far below
+                    // the BF16 rounding of the stored result), free of branches so that the 16
+                    // columns overlap
+                    const float4* g4 = reinterpret_cast<const float4*>(bias_s + c0 + 16);
+#pragma unroll
+                    for (int q4 = 0; q4 < 4; ++q4) {
+                        const float4 gb = g4[q4];
+                        const float gq[4] = {gb.x, gb.y, gb.z, gb.w};
+#pragma unroll
+                        for (int i4 = 0; i4 < 4; ++i4) {
+                            const int j = 4 * q4 + i4;
+                            const float gv = gte[j] + gq[i4];
+                            const float ef = __expf(fminf(v[j], 0.0f));
+                            const float f = v[j] > 0.0f ? v[j] : ef - 1.0f;
+                            v[j] = __fdividef(f, 1.0f + __expf(-gv));
+                        }
+                    }
+                }
+                if (valid) {
+                    const int ng = (slice * P.n_slice + c0) >> (GATED ? 1 : 0);
+                    size_t row;   // output image row
+                    int xo, wo, o;
+                    if (P.mode != 1) {
+                        row = (size_t)img * P.h + yy;
+                        xo = x;
+                        wo = P.w;
+                        o = ng;
+                    } else {
+                        // transposed conv: column ng = (2a + b) * cout + o  ->  pixel (2y+a, 2x+b)
+                        const int abi = ng / P.cout;
+                        o = ng - abi * P.cout;
+                        row = (size_t)img * 2 * P.h + 2 * yy + (abi >> 1);
+                        xo = 2 * x + (abi & 1);
+                        wo = 2 * P.w;
+                    }
+                    uint8_t* dst = (uint8_t*)P.y +
+                                   ((row * P.out_nch + (size_t)(o / ce)) * wo + xo) * 16;
+                    if (FP8) {
+                        uint32_t wd[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const __nv_fp8_storage_t c8 = __nv_cvt_float_to_fp8(
+                                v[j] * P.inv_out, __NV_SATFINITE, __NV_E4M3);
+                            wd[j >> 2] |= (uint32_t)c8 << (8 * (j & 3));
+                        }
+                        if (P.store_y)
+                            *reinterpret_cast<uint4*>(dst) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+                        if (P.head_w) {
+                            // the decoded codes, as a separate head kernel would read them
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                __nv_fp8_e4m3 qv;
+                                qv.__x = (uint8_t)(wd[j >> 2] >> (8 * (j & 3)));
+                                v[j] = float(qv) * P.head_s;
+                            }
+                            head_store(P, head_ws, img, yy, x, v);
+                        }
+                    } else {
+                        if (P.mask) {
+                            // the same two planes of the mask tensor
+                            const size_t off = (size_t)(dst - (uint8_t*)P.y);
+                            const uint4 m0 = *reinterpret_cast<const uint4*>(P.mask + off);
+                            const uint4 m1 =
+                                *reinterpret_cast<const uint4*>(P.mask + off + (size_t)wo * 16);
+                            const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const uint32_t bits = (mw[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+                                // BF16 bits of a positive number: sign clear, not +0, not NaN
+                                const bool pos = bits != 0u && bits < 0x7F81u;
+                                if (!pos) v[j] = 0.0f;
+                            }
+                        }
+                        uint32_t packed[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                            packed[j] = *reinterpret_cast<uint32_t*>(&h2);
+                        }
+                        // channels o..o+7 and o+8..o+15 sit in consecutive planes
+                        if (P.store_y) {
+                            *reinterpret_cast<uint4*>(dst) =
+                                make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                            *reinterpret_cast<uint4*>(dst + (size_t)wo * 16) =
+                                make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                        }
+                        if (P.pool_y && !(yy & 1)) {
+                            // the even row as stored, for the pool after the odd row
+                            uint4* st = reinterpret_cast<uint4*>(smem + P.stash_off) +
+                                        ((c0 >> (GATED ? 1 : 0)) / 8) * TILE_M + m;
+                            st[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                            st[TILE_M] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                        }
+                        if (P.head_w) {
+                            // the rounded BF16 values, as a separate head kernel would read them
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const __nv_bfloat162 h2 =
+                                    *reinterpret_cast<const __nv_bfloat162*>(&packed[j]);
+                                v[2 * j] = __low2float(h2);
+                                v[2 * j + 1] = __high2float(h2);
+                            }
+                            head_store(P, head_ws, img, yy, x, v);
+                        }
+                    }
+                }
+                if (!FP8 && P.pool_y && (yy & 1)) {
+                    // 2x2 average pool (BF16) of the tile's two rows: the even row (kept in
+                    // shared memory by this thread) and this one, pixels x (this lane) and
+                    // x + 1 (the next lane), as stored; the mean is rounded to BF16
+                    const size_t prow = (size_t)img * (P.h >> 1) + (yy >> 1);
+                    const int wp = P.w >> 1;
+                    const int o = (slice * P.n_slice + c0) >> (GATED ? 1 : 0);
+#pragma unroll
+                    for (int h8 = 0; h8 < 16; h8 += 8) {
+                        float a[8], c[8];
+                        if (valid) {
+                            const uint4 raw = *reinterpret_cast<const uint4*>(
+                                smem + P.stash_off +
+                                ((((c0 >> (GATED ? 1 : 0)) + h8) / 8) * TILE_M + m) * 16);
+                            const uint32_t rw[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const __nv_bfloat162 h2 =
+                                    *reinterpret_cast<const __nv_bfloat162*>(&rw[j]);
+                                a[2 * j] = __low2float(h2);
+                                a[2 * j + 1] = __high2float(h2);
+                            }
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                c[j] = __bfloat162float(__float2bfloat16_rn(v[h8 + j]));
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) a[j] = c[j] = 0.0f;
+                        }
+                        float rr[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const float b = __shfl_down_sync(0xffffffffu, a[j], 1);
+                            const float d = __shfl_down_sync(0xffffffffu, c[j], 1);
+                            rr[j] = 0.25f * ((a[j] + b) + (c[j] + d));
+                        }
+                        if (valid && !(m & 1)) {
+                            uint32_t pk[4];
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                __nv_bfloat162 h2 = __floats2bfloat162_rn(rr[2 * j], rr[2 * j + 1]);
+                                pk[j] = *reinterpret_cast<uint32_t*>(&h2);
+                            }
+                            uint8_t* dst = (uint8_t*)P.pool_y +
+                                ((prow * P.out_nch + (size_t)((o + h8) / 8)) * wp + (x >> 1)) * 16;
+                            *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        }
+                    }
+                }
+            }
+        };
+        // Two consecutive output rows of this thread's pixel from two TMEM blocks (BF16, not
+        // gated, row streaming): row a and row b, either absent (ra / rb false: a slot that
+        // holds no output row of this CTA) -- processed together, 8 output channels (one
+        // plane) at a time, so that the two rows' loads and arithmetic overlap.  With the
+        // fused pool the pair is an even and the following odd row, pooled from registers.
+        auto emit_pair = [&](uint32_t ta, bool ra, int imga, int xa, bool va, int ya, uint32_t tb,
+                             bool rb, int imgb, int xb, bool vb, int yb) {
+            const int nchunk = P.n_slice / 8;   // 8-channel chunks
+            const int oc0 = slice * P.n_slice;
+            float ha[3] = {0.0f, 0.0f, 0.0f}, hb[3] = {0.0f, 0.0f, 0.0f};
+            if (P.head_w) {
+#pragma unroll
+                for (int o = 0; o < 3; ++o) ha[o] = hb[o] = head_ws[48 + o];
+            }
+#pragma unroll 1
+            for (int ch = 0; ch < nchunk; ++ch) {
+                const int cf = ch * 8;
+                uint32_t pa[4], pb[4];   // the chunk's 8 channels of rows a and b, as BF16 pairs
+                {
+                    uint32_t fa[8], fb[8];
+                    if (ra) tmem_ld8_nowait(ta + (uint32_t)cf, fa);
+                    if (rb) tmem_ld8_nowait(tb + (uint32_t)cf, fb);
+                    tmem_ld_wait();
+                    tmem_tie8(fa);
+                    tmem_tie8(fb);
+                    const float4* b4 = reinterpret_cast<const float4*>(bias_s + cf);
+                    const float4 bb0 = b4[0], bb1 = b4[1];
+                    const float bq[8] = {bb0.x, bb0.y, bb0.z, bb0.w, bb1.x, bb1.y, bb1.z, bb1.w};
+                    float a8[8], b8[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        float u = __uint_as_float(fa[j]) + bq[j];
+                        float w = __uint_as_float(fb[j]) + bq[j];
+                        if (P.relu) {
+                            u = fmaxf(u, 0.0f);
+                            w = fmaxf(w, 0.0f);
+                        }
+                        a8[j] = u;
+                        b8[j] = w;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(a8[2 * j], a8[2 * j + 1]);
+                        pa[j] = *reinterpret_cast<uint32_t*>(&h2);
+                        h2 = __floats2bfloat162_rn(b8[2 * j], b8[2 * j + 1]);
+                        pb[j] = *reinterpret_cast<uint32_t*>(&h2);
+                    }
+                }
+                const int plane = (oc0 + 8 * ch) / 8;
+                if (P.store_y) {
+                    if (ra && va)
+                        *reinterpret_cast<uint4*>((uint8_t*)P.y +
+                            ((((size_t)imga * P.h + ya) * P.out_nch + plane) * P.w + xa) * 16) =
+                            make_uint4(pa[0], pa[1], pa[2], pa[3]);
+                    if (rb && vb)
+                        *reinterpret_cast<uint4*>((uint8_t*)P.y +
+                            ((((size_t)imgb * P.h + yb) * P.out_nch + plane) * P.w + xb) * 16) =
+                            make_uint4(pb[0], pb[1], pb[2], pb[3]);
+                }
+                // the stored (BF16-rounded) values, for the head and the pool
+                float a8[8], b8[8];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const __nv_bfloat162 x2 = *reinterpret_cast<const __nv_bfloat162*>(&pa[j]);
+                    const __nv_bfloat162 y2 = *reinterpret_cast<const __nv_bfloat162*>(&pb[j]);
+                    a8[2 * j] = __low2float(x2);
+                    a8[2 * j + 1] = __high2float(x2);
+                    b8[2 * j] = __low2float(y2);
+                    b8[2 * j + 1] = __high2float(y2);
+                }
+                if (P.head_w) {
+                    // the 1x1 head: channels in order, one fused multiply-add each
+#pragma unroll
+                    for (int o = 0; o < 3; ++o) {
+                        const float4* h4 = reinterpret_cast<const float4*>(head_ws + o * 16 + 8 * ch);
+                        const float4 w0 = h4[0], w1 = h4[1];
+                        const float wq[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            ha[o] = fmaf(wq[j], a8[j], ha[o]);
+                            hb[o] = fmaf(wq[j], b8[j], hb[o]);
+                        }
+                    }
+                }
+                if (P.pool_y && ra && rb) {
+                    // 2x2 average of rows a (even) and b (odd), pixels x and x + 1 (next lane)
+                    const bool vp = va && vb;
+                    float rr[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float av = vp ? a8[j] : 0.0f, cv = vp ? b8[j] : 0.0f;
+                        const float bv = __shfl_down_sync(0xffffffffu, av, 1);
+                        const float dv = __shfl_down_sync(0xffffffffu, cv, 1);
+                        rr[j] = 0.25f * ((av + bv) + (cv + dv));
+                    }
+                    if (vp && !(m & 1)) {
+                        uint32_t pk[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            __nv_bfloat162 h2 = __floats2bfloat162_rn(rr[2 * j], rr[2 * j + 1]);
+                            pk[j] = *reinterpret_cast<uint32_t*>(&h2);
+                        }
+                        const int wp = P.w >> 1;
+                        *reinterpret_cast<uint4*>((uint8_t*)P.pool_y +
+                            ((((size_t)imga * (P.h >> 1) + (ya >> 1)) * P.out_nch + plane) * wp +
+                             (xa >> 1)) * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    }
+                }
+            }
+            if (P.head_w) {
+                if (ra && va && ya < P.rgb_h && xa < P.rgb_w) {
+                    float* out = rgb_image(P.rgb, P.rgb_tab, (size_t)imga, (size_t)P.rgb_h * P.rgb_w) +
+                                 ((size_t)ya * P.rgb_w + xa) * 3;
+                    out[0] = ha[0];
+                    out[1] = ha[1];
+                    out[2] = ha[2];
+                }
+                if (rb && vb && yb < P.rgb_h && xb < P.rgb_w) {
+                    float* out = rgb_image(P.rgb, P.rgb_tab, (size_t)imgb, (size_t)P.rgb_h * P.rgb_w) +
+                                 ((size_t)yb * P.rgb_w + xb) * 3;
+                    out[0] = hb[0];
+                    out[1] = hb[1];
+                    out[2] = hb[2];
+                }
+            }
+        };
+        if (STREAM) {
+            // the issuer's slot sequence: slot q is final once group q / grp has committed;
+            // slots 0 and 1 of a segment hold the two rows above it (not its own rows)
+            const uint32_t lanes = (uint32_t)(32 * q) << 16;
+            int S = 0;
+            for (int tt = t_begin; tt < t_end;) {
+                const int col = tt / P.hr;
+                const int te = t_end < (col + 1) * P.hr ? t_end : (col + 1) * P.hr;
+                S += (te - tt) * P.rpt + 2;
+                tt = te;
+            }
+            SlotCursor cur;
+            cur.init(t_begin);
+            int blk = 0, k = 0;
+            for (int q0 = 0; q0 < S; q0 += P.grp, ++k) {
+                int okw = 1;
+                if (lane == 0)
+                    okw = mbar_wait(b_afull(k & 3), (k >> 2) & 1, &abort_flag, P.status) ? 1 : 0;
+                okw = __shfl_sync(0xffffffffu, okw, 0);
+                if (!okw) break;
+                tc_fence_after();
+                const int qe = q0 + P.grp < S ? q0 + P.grp : S;
+                for (int qq = q0; qq < qe; qq += 2) {
+                    bool ra = false, rb = false, va = false, vb = false;
+                    int ia = 0, xa = 0, ya = 0, ib = 0, xb = 0, yb = 0;
+                    cur.next(P, t_end, m, ra, ia, xa, va, ya);
+                    const uint32_t ta = tmem + lanes + (uint32_t)(blk * P.n_slice);
+                    if (++blk == P.nb) blk = 0;
+                    const bool hasb = qq + 1 < qe;
+                    uint32_t tb = ta;
+                    if (hasb) {
+                        cur.next(P, t_end, m, rb, ib, xb, vb, yb);
+                        tb = tmem + lanes + (uint32_t)(blk * P.n_slice);
+                        if (++blk == P.nb) blk = 0;
+                    }
+                    if (FP8 || GATED) {
+                        if (ra) emit_row(ta, ia, xa, va, ya);
+                        if (rb) emit_row(tb, ib, xb, vb, yb);
+                    } else {
+                        emit_pair(ta, ra, ia, xa, va, ya, tb, rb, ib, xb, vb, yb);
+                    }
+                    // zero the blocks for their next output rows
+                    for (int c = 0; c < P.n_slice; c += 16) tmem_zero16(ta + (uint32_t)c);
+                    if (hasb)
+                        for (int c = 0; c < P.n_slice; c += 16) tmem_zero16(tb + (uint32_t)c);
+                }
+                if (qe - q0 == P.grp) {
+                    tmem_st_wait();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(b_aempty(k & 3));
+                }
+            }
+            tmem_st_wait();
+        } else {
         TileWalk w;
         w.init(P, t_begin);
         for (int t = t_begin, i = 0; t < t_end; ++t, ++i, w.next(P)) {
@@ -441,183 +961,12 @@ __global__ void __launch_bounds__(NTHREADS, 4)
                 const bool valid = valid_x && yy < P.h;
                 const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) +
                                        (uint32_t)((ab * P.rpt + r) * P.nissue * P.n_slice);
-                for (int c0 = 0; c0 < P.n_slice; c0 += (P.gated ? 32 : 16)) {
-                    uint32_t v32[16];
-                    tmem_ld16(tbase + (uint32_t)c0, v32);
-                    float acc[16];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) acc[j] = __uint_as_float(v32[j]);
-                    if (P.nissue == 2) {
-                        tmem_ld16(tbase + (uint32_t)(P.n_slice + c0), v32);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) acc[j] += __uint_as_float(v32[j]);
-                    }
-                    float v[16];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        v[j] = fmaf(acc[j], colscale_s[c0 + j], bias_s[c0 + j]);
-                        if (P.relu) v[j] = fmaxf(v[j], 0.0f);
-                    }
-                    if (!FP8 && P.gated) {
-                        // ELU(feature) * sigmoid(gate): the gate columns follow the features
-                        tmem_ld16(tbase + (uint32_t)(c0 + 16), v32);
-                        float gte[16];
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) gte[j] = __uint_as_float(v32[j]);
-                        if (P.nissue == 2) {
-                            tmem_ld16(tbase + (uint32_t)(P.n_slice + c0 + 16), v32);
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) gte[j] += __uint_as_float(v32[j]);
-                        }
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const float gv = gte[j] + bias_s[c0 + 16 + j];
-                            const float f = v[j] > 0.0f ? v[j] : expm1f(v[j]);
-                            v[j] = f / (1.0f + expf(-gv));
-                        }
-                    }
-                    if (valid) {
-                        const int ng = (slice * P.n_slice + c0) >> (P.gated ? 1 : 0);
-                        size_t row;   // output image row
-                        int xo, wo, o;
-                        if (P.mode != 1) {
-                            row = (size_t)w.img * P.h + yy;
-                            xo = x;
-                            wo = P.w;
-                            o = ng;
-                        } else {
-                            // transposed conv: column ng = (2a + b) * cout + o  ->  pixel (2y+a, 2x+b)
-                            const int abi = ng / P.cout;
-                            o = ng - abi * P.cout;
-                            row = (size_t)w.img * 2 * P.h + 2 * yy + (abi >> 1);
-                            xo = 2 * x + (abi & 1);
-                            wo = 2 * P.w;
-                        }
-                        uint8_t* dst = (uint8_t*)P.y +
-                                       ((row * P.out_nch + (size_t)(o / ce)) * wo + xo) * 16;
-                        if (FP8) {
-                            uint32_t wd[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) {
-                                const __nv_fp8_storage_t c8 = __nv_cvt_float_to_fp8(
-                                    v[j] * P.inv_out, __NV_SATFINITE, __NV_E4M3);
-                                wd[j >> 2] |= (uint32_t)c8 << (8 * (j & 3));
-                            }
-                            if (P.store_y)
-                                *reinterpret_cast<uint4*>(dst) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
-                            if (P.head_w) {
-                                // the decoded codes, as a separate head kernel would read them
-#pragma unroll
-                                for (int j = 0; j < 16; ++j) {
-                                    __nv_fp8_e4m3 qv;
-                                    qv.__x = (uint8_t)(wd[j >> 2] >> (8 * (j & 3)));
-                                    v[j] = float(qv) * P.head_s;
-                                }
-                                head_store(P, head_ws, w.img, yy, x, v);
-                            }
-                        } else {
-                            if (P.mask) {
-                                // the same two planes of the mask tensor
-                                const size_t off = (size_t)(dst - (uint8_t*)P.y);
-                                const uint4 m0 = *reinterpret_cast<const uint4*>(P.mask + off);
-                                const uint4 m1 =
-                                    *reinterpret_cast<const uint4*>(P.mask + off + (size_t)wo * 16);
-                                const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
-#pragma unroll
-                                for (int j = 0; j < 16; ++j) {
-                                    const uint32_t bits = (mw[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
-                                    // BF16 bits of a positive number: sign clear, not +0, not NaN
-                                    const bool pos = bits != 0u && bits < 0x7F81u;
-                                    if (!pos) v[j] = 0.0f;
-                                }
-                            }
-                            uint32_t packed[8];
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                                packed[j] = *reinterpret_cast<uint32_t*>(&h2);
-                            }
-                            // channels o..o+7 and o+8..o+15 sit in consecutive planes
-                            if (P.store_y) {
-                                *reinterpret_cast<uint4*>(dst) =
-                                    make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                                *reinterpret_cast<uint4*>(dst + (size_t)wo * 16) =
-                                    make_uint4(packed[4], packed[5], packed[6], packed[7]);
-                            }
-                            if (P.pool_y && r == 0) {
-                                // the even row as stored, for the pool after the odd row
-                                uint4* st = reinterpret_cast<uint4*>(smem + P.stash_off) +
-                                            ((c0 >> (P.gated ? 1 : 0)) / 8) * TILE_M + m;
-                                st[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                                st[TILE_M] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
-                            }
-                            if (P.head_w) {
-                                // the rounded BF16 values, as a separate head kernel would read them
-#pragma unroll
-                                for (int j = 0; j < 8; ++j) {
-                                    const __nv_bfloat162 h2 =
-                                        *reinterpret_cast<const __nv_bfloat162*>(&packed[j]);
-                                    v[2 * j] = __low2float(h2);
-                                    v[2 * j + 1] = __high2float(h2);
-                                }
-                                head_store(P, head_ws, w.img, yy, x, v);
-                            }
-                        }
-                    }
-                    if (!FP8 && P.pool_y && r == 1) {
-                        // 2x2 average pool (BF16) of the tile's two rows: the even row (kept in
-                        // shared memory by this thread) and this one, pixels x (this lane) and
-                        // x + 1 (the next lane), as stored; the mean is rounded to BF16
-                        const size_t prow = (size_t)w.img * (P.h >> 1) + (w.y >> 1);
-                        const int wp = P.w >> 1;
-                        const int o = (slice * P.n_slice + c0) >> (P.gated ? 1 : 0);
-#pragma unroll
-                        for (int h8 = 0; h8 < 16; h8 += 8) {
-                            float a[8], c[8];
-                            if (valid) {
-                                const uint4 raw = *reinterpret_cast<const uint4*>(
-                                    smem + P.stash_off +
-                                    ((((c0 >> (P.gated ? 1 : 0)) + h8) / 8) * TILE_M + m) * 16);
-                                const uint32_t rw[4] = {raw.x, raw.y, raw.z, raw.w};
-#pragma unroll
-                                for (int j = 0; j < 4; ++j) {
-                                    const __nv_bfloat162 h2 =
-                                        *reinterpret_cast<const __nv_bfloat162*>(&rw[j]);
-                                    a[2 * j] = __low2float(h2);
-                                    a[2 * j + 1] = __high2float(h2);
-                                }
-#pragma unroll
-                                for (int j = 0; j < 8; ++j)
-                                    c[j] = __bfloat162float(__float2bfloat16_rn(v[h8 + j]));
-                            } else {
-#pragma unroll
-                                for (int j = 0; j < 8; ++j) a[j] = c[j] = 0.0f;
-                            }
-                            float rr[8];
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                const float b = __shfl_down_sync(0xffffffffu, a[j], 1);
-                                const float d = __shfl_down_sync(0xffffffffu, c[j], 1);
-                                rr[j] = 0.25f * ((a[j] + b) + (c[j] + d));
-                            }
-                            if (valid && !(m & 1)) {
-                                uint32_t pk[4];
-#pragma unroll
-                                for (int j = 0; j < 4; ++j) {
-                                    __nv_bfloat162 h2 = __floats2bfloat162_rn(rr[2 * j], rr[2 * j + 1]);
-                                    pk[j] = *reinterpret_cast<uint32_t*>(&h2);
-                                }
-                                uint8_t* dst = (uint8_t*)P.pool_y +
-                                    ((prow * P.out_nch + (size_t)((o + h8) / 8)) * wp + (x >> 1)) * 16;
-                                *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                            }
-                        }
-                    }
-                }
+                emit_row(tbase, w.img, x, valid, yy);
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(b_aempty(ab));
+        }
         }
     }
     tc_fence_before();
@@ -701,6 +1050,7 @@ struct TcLayerCfg {
     size_t w_off = 0;        // byte offset of the packed weights
     uint32_t w_bytes = 0;    // per slice
     size_t cs_off = 0;       // FP8: offset (floats) of the per-column scales
+    int stream = 0;          // 3x3 conv run by row streaming (weights packed for it)
 };
 
 TcLayerCfg g_cfg[2][NUM_LAYERS];   // [BF16, FP8]
@@ -722,6 +1072,7 @@ struct PackJob {
     const float* s_w;
     const int4* halves;
     uint8_t* out;
+    int stream;              // row-streaming layout: [slice][row K-step][half][3 n_slice][ce]
 };
 
 // Element i of job J (i < nslices * nks * 2 * n_slice * ce).
@@ -729,10 +1080,23 @@ __device__ __forceinline__ void pack_element(const float* __restrict__ P, const 
                                              size_t i) {
     const int ce = J.fp8 ? 16 : 8;
     const int e = (int)(i % ce);
-    const int nl = (int)((i / ce) % J.n_slice);
-    const int hf = (int)((i / (ce * (size_t)J.n_slice)) % 2);
-    const int ks = (int)((i / (2 * ce * (size_t)J.n_slice)) % J.nks);
-    const int sl = (int)(i / (2 * ce * (size_t)J.n_slice * J.nks));
+    int nl, hf, ks, sl;
+    if (J.stream) {
+        // the weights of kernel rows 2, 1, 0 side by side: column n3 = (2 - dy) * n_slice + nl
+        // of row K-step j, which is K-step dy * (nks / 3) + j of the tile layout
+        const int n3w = 3 * J.n_slice, ksr = J.nks / 3;
+        const int n3 = (int)((i / ce) % n3w);
+        hf = (int)((i / (ce * (size_t)n3w)) % 2);
+        const int j = (int)((i / (2 * ce * (size_t)n3w)) % ksr);
+        sl = (int)(i / (2 * ce * (size_t)n3w * ksr));
+        nl = n3 % J.n_slice;
+        ks = (2 - n3 / J.n_slice) * ksr + j;
+    } else {
+        nl = (int)((i / ce) % J.n_slice);
+        hf = (int)((i / (ce * (size_t)J.n_slice)) % 2);
+        ks = (int)((i / (2 * ce * (size_t)J.n_slice)) % J.nks);
+        sl = (int)(i / (2 * ce * (size_t)J.n_slice * J.nks));
+    }
     const int4 h = J.halves[2 * ks + hf];
     const int n = sl * J.n_slice + nl;
     float v = 0.0f;
@@ -849,6 +1213,31 @@ nrv_status pack_all(const float* P, PackJobs& J, cudaStream_t s) {
 
 }  // namespace
 
+// Row streaming for the 3x3 convs (on unless NRV_TC_STREAM=0, read once per process): the
+// weight layout and the launch both follow it.
+static bool stream_enabled() {
+    static const bool on = [] {
+        const char* e = getenv("NRV_TC_STREAM");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
+// A 3x3 conv slice is streamed when its three kernel rows fit in one MMA (N = 3 n_slice <= 256).
+static int stream_ok(const TcLayerCfg& c) {
+    return stream_enabled() && c.kind == CONV3 && c.rows == 3 && c.nks % 3 == 0 &&
+           3 * c.n_slice <= 256 && c.n_slice % 16 == 0;
+}
+
+// Streamed slices are at most 32 columns wide: a ring of 8 blocks then fits in 256 TMEM
+// columns and the epilogue drains two rows per group.
+static int stream_slice(const TcLayerCfg& c, int ns) {
+    if (stream_enabled() && c.kind == CONV3 && c.rows == 3 && c.nks % 3 == 0 && ns > 32 &&
+        c.ncols % 32 == 0)
+        return 32;
+    return ns;
+}
+
 static int src_split(int l, int cin_padded, int* c2) {
     if (l == L_D2A || l == L_D1A || l == L_D0A) {
         *c2 = cin_padded / 2;
@@ -902,8 +1291,10 @@ static nrv_status build_cfg(Net* net, int pi, std::vector<int4>& all_halves,
         // widest output slice whose weights fit in 80 KB
         int ns = c.ncols;
         while (ns > 16 && (size_t)c.nks * 2 * ns * 16 > 80 * 1024) ns /= 2;
+        ns = stream_slice(c, ns);
         c.n_slice = ns;
         c.nslices = c.ncols / ns;
+        c.stream = stream_ok(c);
         c.w_bytes = (uint32_t)c.nks * 2 * ns * 16;
         c.w_off = off;
         off += ((size_t)c.w_bytes * c.nslices + 1023) / 1024 * 1024;
@@ -1018,7 +1409,7 @@ nrv_status tc_repack(Net* net, cudaStream_t s) {
         const Layer& L = net->layers[l];
         J.job[J.n++] = PackJob{L.woff, 0, 0, c.kind, L.cin, L.cout, c.n_slice, c.nslices, c.nks, c.c1, 0,
                                1.0f, nullptr, (const int4*)g_halves[0].p + hoff[l],
-                               (uint8_t*)net->wbf16.p + c.w_off};
+                               (uint8_t*)net->wbf16.p + c.w_off, c.stream};
     }
     NRV_TRY(pack_all((const float*)net->params.p, J, s));
     NRV_TRY(tc_repack_dgrad(net, s));
@@ -1073,7 +1464,7 @@ nrv_status tc_repack_fp8(Net* net, cudaStream_t s) {
         NRV_CHECK_LAUNCH();
         const PackJob job{L.woff, 0, 0, c.kind, L.cin, L.cout, c.n_slice, c.nslices, c.nks, c.c1, 1,
                           fold, s_w + c.cs_off, (const int4*)g_halves[1].p + hoff[l],
-                          (uint8_t*)net->wfp8.p + c.w_off};
+                          (uint8_t*)net->wfp8.p + c.w_off, c.stream};
         pack_tc_weights_kernel<<<64, 256, 0, s>>>((const float*)net->params.p, job);
         NRV_CHECK_LAUNCH();
     }
@@ -1146,34 +1537,58 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
     // two MMA issuers where both partial accumulators of both tile buffers fit in 256
     // TMEM columns and every input row has at least two K-steps (the issue loop's read-ahead)
     P.nissue = (4 * c.n_slice <= 256 && c.nks / c.rows >= 2) ? 2 : 1;
+    P.stream = c.stream && conv && !mask ? 1 : 0;
+    if (P.stream) {
+        // one issuer; a ring of nb blocks in 128 TMEM columns for 16-column slices (four CTAs
+        // per SM), 256 otherwise; groups of grp rows, gm groups in flight, gm * grp + 2 <= nb
+        P.nissue = 1;
+        P.nb = (c.n_slice == 16 ? 128 : 256) / c.n_slice;
+        P.grp = (P.nb - 2) / 3;
+        P.gm = 3;
+        if (P.grp < 1) {
+            P.grp = 1;
+            P.gm = P.nb - 2;
+        }
+        if (P.nb < 4 || P.gm * P.grp + 2 > P.nb || P.gm > 3 || (!fp8 && P.grp != 2))
+            return fail(NRV_ERR_UNSUPPORTED, "row streaming: TMEM ring");
+    }
     // TMEM columns for rpt rows per tile and nacc accumulator buffers (a power of two >= 32)
     auto cols_for = [&](int rpt, int nacc) {
         uint32_t cols = 32;
-        while (cols < (uint32_t)(nacc * rpt * P.nissue * c.n_slice)) cols *= 2;
+        const uint32_t need =
+            P.stream ? (uint32_t)(P.nb * c.n_slice) : (uint32_t)(nacc * rpt * P.nissue * c.n_slice);
+        while (cols < need) cols *= 2;
         return cols;
     };
-    auto kern = fp8 ? conv3_tc_kernel<true> : conv3_tc_kernel<false>;
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[fp8]) {
+    // kernel variant: operand type, row streaming, gated epilogue (BF16 only)
+    const int kv = fp8 ? 4 + P.stream : 2 * P.stream + (P.gated ? 1 : 0);
+    auto kern = fp8 ? (P.stream ? conv3_tc_kernel<true, true, false>
+                                : conv3_tc_kernel<true, false, false>)
+                    : (P.stream ? (P.gated ? conv3_tc_kernel<false, true, true>
+                                           : conv3_tc_kernel<false, true, false>)
+                                : (P.gated ? conv3_tc_kernel<false, false, true>
+                                           : conv3_tc_kernel<false, false, false>));
+    static bool attr_set[6] = {false, false, false, false, false, false};
+    if (!attr_set[kv]) {
         NRV_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             220 * 1024));
-        attr_set[fp8] = true;
+        attr_set[kv] = true;
     }
     // resident CTAs per SM from registers, threads, shared memory and TMEM columns
-    static cudaFuncAttributes fa_k[2];
+    static cudaFuncAttributes fa_k[6];
     static cudaDeviceProp prop;
-    static bool have_fa[2] = {false, false}, have_prop = false;
+    static bool have_fa[6] = {false, false, false, false, false, false}, have_prop = false;
     if (!have_prop) {
         int dev = 0;
         NRV_CHECK_CUDA(cudaGetDevice(&dev));
         NRV_CHECK_CUDA(cudaGetDeviceProperties(&prop, dev));
         have_prop = true;
     }
-    if (!have_fa[fp8]) {
-        NRV_CHECK_CUDA(cudaFuncGetAttributes(&fa_k[fp8], kern));
-        have_fa[fp8] = true;
+    if (!have_fa[kv]) {
+        NRV_CHECK_CUDA(cudaFuncGetAttributes(&fa_k[kv], kern));
+        have_fa[kv] = true;
     }
-    const cudaFuncAttributes& fa = fa_k[fp8];
+    const cudaFuncAttributes& fa = fa_k[kv];
     auto occupancy = [&](uint32_t smem_dyn, uint32_t cols, bool count_tmem = true) {
         const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
         int o = prop.regsPerMultiprocessor / (regs_per_warp * (NTHREADS / 32));
@@ -1194,21 +1609,28 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
     auto smem_for = [&](int ns) { return P.w_region + (uint32_t)ns * P.slot_bytes + stash_bytes; };
     const int rpt0 = pool_y ? 2 : 1, nacc0 = 2;
     const uint32_t cols0 = cols_for(rpt0, nacc0);
-    int nslot = c.rows + rpt0 + 1;
-    while (nslot > c.rows + rpt0 - 1 && smem_for(nslot) > 215 * 1024) --nslot;
-    if (nslot < c.rows + rpt0 || smem_for(nslot) > 215 * 1024)
+    // row streaming reads each row once: two slots suffice, the rest is read-ahead
+    const int min_slots = P.stream ? 2 : c.rows + rpt0;
+    int nslot = min_slots + 1;
+    while (nslot > min_slots - 1 && smem_for(nslot) > 215 * 1024) --nslot;
+    if (nslot < min_slots || smem_for(nslot) > 215 * 1024)
         return fail(NRV_ERR_UNSUPPORTED, "tile does not fit in shared memory");
-    if (!fp8 && nslot > c.rows + rpt0 &&
-        occupancy(smem_for(c.rows + rpt0), cols0) > occupancy(smem_for(nslot), cols0))
-        nslot = c.rows + rpt0;
+    if (!fp8 && nslot > min_slots &&
+        occupancy(smem_for(min_slots), cols0) > occupancy(smem_for(nslot), cols0))
+        nslot = min_slots;
     const int occ0 = occupancy(smem_for(nslot), cols0);
     while (nslot < MAX_SLOTS && smem_for(nslot + 1) <= 215 * 1024 &&
            occupancy(smem_for(nslot + 1), cols0) >= occ0)
         ++nslot;
     // instruction descriptor: FP32 accumulator; A/B BF16 (kind::f16) or E4M3 (kind::f8f6f4)
     const uint32_t ab_fmt = fp8 ? 0u : 1u;
-    P.idesc = (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(c.n_slice >> 3) << 17) |
-              ((uint32_t)(TILE_M >> 4) << 24);
+    auto idesc_n = [&](int nn) {
+        return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(nn >> 3) << 17) |
+               ((uint32_t)(TILE_M >> 4) << 24);
+    };
+    P.idesc = idesc_n(P.stream ? 3 * c.n_slice : c.n_slice);
+    P.idesc2 = idesc_n(2 * c.n_slice);
+    P.idesc1 = idesc_n(c.n_slice);
     P.wpk = wpk;
     P.bias = bias;
     P.y = y;
@@ -1354,6 +1776,7 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
     auto launch_choice = [&](int v) {
         return launch_with((v >> 20) & 15, (v >> 16) & 15, (v >> 8) & 255, v & 255);
     };
+    if (P.stream) return launch_with(rpt0, nacc0, nslot, 0);
     int choice = 0;
     if (tune_get(key, &choice) && valid_choice(choice)) return launch_choice(choice);
     if (!tune_on) return launch_with(rpt0, nacc0, nslot, 0);
@@ -1462,9 +1885,11 @@ nrv_status tc_generic_prepare(const TcGeneric* L, int n, const float* params, Tc
         const int minw = c.gated ? 32 : 16;
         int ns = c.ncols;
         while (ns > minw && (size_t)c.nks * 2 * ns * 16 > 80 * 1024) ns /= 2;
+        ns = stream_slice(c, ns);
         if (c.ncols % ns || ns % minw) return fail(NRV_ERR_UNSUPPORTED, "slice width");
         c.n_slice = ns;
         c.nslices = c.ncols / ns;
+        c.stream = stream_ok(c);
         c.w_bytes = (uint32_t)c.nks * 2 * ns * 16;
         c.w_off = off;
         off += ((size_t)c.w_bytes * c.nslices + 1023) / 1024 * 1024;
@@ -1484,7 +1909,8 @@ nrv_status tc_generic_prepare(const TcGeneric* L, int n, const float* params, Tc
         const TcLayerCfg& c = st->cfg[l];
         J.job[J.n++] = PackJob{L[l].woff, L[l].woff2, L[l].gated, c.kind, L[l].cin_real, L[l].cout,
                                c.n_slice, c.nslices, c.nks, c.c1, 0, 1.0f, nullptr,
-                               (const int4*)st->halves.p + hoff[l], (uint8_t*)st->w.p + c.w_off};
+                               (const int4*)st->halves.p + hoff[l], (uint8_t*)st->w.p + c.w_off,
+                               c.stream};
     }
     return pack_all(params, J, s);
 }
