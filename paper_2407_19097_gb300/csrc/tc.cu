@@ -769,8 +769,16 @@ __global__ void __launch_bounds__(NTHREADS, STREAM ? 3 : 4)
         // fused pool the pair is an even and the following odd row, pooled from registers.
         auto emit_pair = [&](uint32_t ta, bool ra, int imga, int xa, bool va, int ya, uint32_t tb,
                              bool rb, int imgb, int xb, bool vb, int yb) {
-            const int nchunk = P.n_slice / 8;   // 8-channel chunks
-            const int oc0 = slice * P.n_slice;
+            const int nchunk = P.n_slice / 8;   // 8-channel chunks (one plane each)
+            const int plane0 = slice * P.n_slice / 8;
+            const size_t pstride = (size_t)P.w * 16;   // bytes between planes of a row
+            // this pixel's 16-byte word in plane 0 of rows a and b
+            uint8_t* const pya = (uint8_t*)P.y + (((size_t)imga * P.h + ya) * P.out_nch * P.w + xa) * 16;
+            uint8_t* const pyb = (uint8_t*)P.y + (((size_t)imgb * P.h + yb) * P.out_nch * P.w + xb) * 16;
+            const bool sa = P.store_y && ra && va, sb = P.store_y && rb && vb;
+            const bool relu = P.relu != 0;
+            const bool pool = P.pool_y && ra && rb;
+            const bool vp = va && vb;
             float ha[3] = {0.0f, 0.0f, 0.0f}, hb[3] = {0.0f, 0.0f, 0.0f};
             if (P.head_w) {
 #pragma unroll
@@ -779,95 +787,85 @@ __global__ void __launch_bounds__(NTHREADS, STREAM ? 3 : 4)
 #pragma unroll 1
             for (int ch = 0; ch < nchunk; ++ch) {
                 const int cf = ch * 8;
-                uint32_t pa[4], pb[4];   // the chunk's 8 channels of rows a and b, as BF16 pairs
-                {
-                    uint32_t fa[8], fb[8];
-                    if (ra) tmem_ld8_nowait(ta + (uint32_t)cf, fa);
-                    if (rb) tmem_ld8_nowait(tb + (uint32_t)cf, fb);
-                    tmem_ld_wait();
-                    tmem_tie8(fa);
-                    tmem_tie8(fb);
-                    const float4* b4 = reinterpret_cast<const float4*>(bias_s + cf);
-                    const float4 bb0 = b4[0], bb1 = b4[1];
-                    const float bq[8] = {bb0.x, bb0.y, bb0.z, bb0.w, bb1.x, bb1.y, bb1.z, bb1.w};
-                    float a8[8], b8[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        float u = __uint_as_float(fa[j]) + bq[j];
-                        float w = __uint_as_float(fb[j]) + bq[j];
-                        if (P.relu) {
-                            u = fmaxf(u, 0.0f);
-                            w = fmaxf(w, 0.0f);
-                        }
-                        a8[j] = u;
-                        b8[j] = w;
-                    }
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        __nv_bfloat162 h2 = __floats2bfloat162_rn(a8[2 * j], a8[2 * j + 1]);
-                        pa[j] = *reinterpret_cast<uint32_t*>(&h2);
-                        h2 = __floats2bfloat162_rn(b8[2 * j], b8[2 * j + 1]);
-                        pb[j] = *reinterpret_cast<uint32_t*>(&h2);
-                    }
-                }
-                const int plane = (oc0 + 8 * ch) / 8;
-                if (P.store_y) {
-                    if (ra && va)
-                        *reinterpret_cast<uint4*>((uint8_t*)P.y +
-                            ((((size_t)imga * P.h + ya) * P.out_nch + plane) * P.w + xa) * 16) =
-                            make_uint4(pa[0], pa[1], pa[2], pa[3]);
-                    if (rb && vb)
-                        *reinterpret_cast<uint4*>((uint8_t*)P.y +
-                            ((((size_t)imgb * P.h + yb) * P.out_nch + plane) * P.w + xb) * 16) =
-                            make_uint4(pb[0], pb[1], pb[2], pb[3]);
-                }
-                // the stored (BF16-rounded) values, for the head and the pool
-                float a8[8], b8[8];
+                uint32_t fa[8], fb[8];
+                if (ra) tmem_ld8_nowait(ta + (uint32_t)cf, fa);
+                if (rb) tmem_ld8_nowait(tb + (uint32_t)cf, fb);
+                tmem_ld_wait();
+                tmem_tie8(fa);
+                tmem_tie8(fb);
+                const float4* b4 = reinterpret_cast<const float4*>(bias_s + cf);
+                const float4 bb0 = b4[0], bb1 = b4[1];
+                const float bq[8] = {bb0.x, bb0.y, bb0.z, bb0.w, bb1.x, bb1.y, bb1.z, bb1.w};
+                uint32_t pa[4], pb[4];   // rows a and b as BF16 pairs
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const __nv_bfloat162 x2 = *reinterpret_cast<const __nv_bfloat162*>(&pa[j]);
-                    const __nv_bfloat162 y2 = *reinterpret_cast<const __nv_bfloat162*>(&pb[j]);
-                    a8[2 * j] = __low2float(x2);
-                    a8[2 * j + 1] = __high2float(x2);
-                    b8[2 * j] = __low2float(y2);
-                    b8[2 * j + 1] = __high2float(y2);
+                    float u0 = __uint_as_float(fa[2 * j]) + bq[2 * j];
+                    float u1 = __uint_as_float(fa[2 * j + 1]) + bq[2 * j + 1];
+                    float w0 = __uint_as_float(fb[2 * j]) + bq[2 * j];
+                    float w1 = __uint_as_float(fb[2 * j + 1]) + bq[2 * j + 1];
+                    if (relu) {
+                        u0 = fmaxf(u0, 0.0f);
+                        u1 = fmaxf(u1, 0.0f);
+                        w0 = fmaxf(w0, 0.0f);
+                        w1 = fmaxf(w1, 0.0f);
+                    }
+                    __nv_bfloat162 h2 = __floats2bfloat162_rn(u0, u1);
+                    pa[j] = *reinterpret_cast<uint32_t*>(&h2);
+                    h2 = __floats2bfloat162_rn(w0, w1);
+                    pb[j] = *reinterpret_cast<uint32_t*>(&h2);
                 }
-                if (P.head_w) {
-                    // the 1x1 head: channels in order, one fused multiply-add each
+                const size_t poff = (size_t)(plane0 + ch) * pstride;
+                if (sa) *reinterpret_cast<uint4*>(pya + poff) = make_uint4(pa[0], pa[1], pa[2], pa[3]);
+                if (sb) *reinterpret_cast<uint4*>(pyb + poff) = make_uint4(pb[0], pb[1], pb[2], pb[3]);
+                if (P.head_w || pool) {
+                    // the stored (BF16-rounded) values, for the head and the pool
+                    float a8[8], b8[8];
 #pragma unroll
-                    for (int o = 0; o < 3; ++o) {
-                        const float4* h4 = reinterpret_cast<const float4*>(head_ws + o * 16 + 8 * ch);
-                        const float4 w0 = h4[0], w1 = h4[1];
-                        const float wq[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+                    for (int j = 0; j < 4; ++j) {
+                        const __nv_bfloat162 x2 = *reinterpret_cast<const __nv_bfloat162*>(&pa[j]);
+                        const __nv_bfloat162 y2 = *reinterpret_cast<const __nv_bfloat162*>(&pb[j]);
+                        a8[2 * j] = __low2float(x2);
+                        a8[2 * j + 1] = __high2float(x2);
+                        b8[2 * j] = __low2float(y2);
+                        b8[2 * j + 1] = __high2float(y2);
+                    }
+                    if (P.head_w) {
+                        // the 1x1 head: channels in order, one fused multiply-add each
+#pragma unroll
+                        for (int o = 0; o < 3; ++o) {
+                            const float4* h4 =
+                                reinterpret_cast<const float4*>(head_ws + o * 16 + 8 * ch);
+                            const float4 w0 = h4[0], w1 = h4[1];
+                            const float wq[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                ha[o] = fmaf(wq[j], a8[j], ha[o]);
+                                hb[o] = fmaf(wq[j], b8[j], hb[o]);
+                            }
+                        }
+                    }
+                    if (pool) {
+                        // 2x2 average of rows a (even) and b (odd), pixels x and x + 1 (next lane)
+                        float rr[8];
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
-                            ha[o] = fmaf(wq[j], a8[j], ha[o]);
-                            hb[o] = fmaf(wq[j], b8[j], hb[o]);
+                            const float av = vp ? a8[j] : 0.0f, cv = vp ? b8[j] : 0.0f;
+                            const float bv = __shfl_down_sync(0xffffffffu, av, 1);
+                            const float dv = __shfl_down_sync(0xffffffffu, cv, 1);
+                            rr[j] = 0.25f * ((av + bv) + (cv + dv));
                         }
-                    }
-                }
-                if (P.pool_y && ra && rb) {
-                    // 2x2 average of rows a (even) and b (odd), pixels x and x + 1 (next lane)
-                    const bool vp = va && vb;
-                    float rr[8];
+                        if (vp && !(m & 1)) {
+                            uint32_t pk[4];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float av = vp ? a8[j] : 0.0f, cv = vp ? b8[j] : 0.0f;
-                        const float bv = __shfl_down_sync(0xffffffffu, av, 1);
-                        const float dv = __shfl_down_sync(0xffffffffu, cv, 1);
-                        rr[j] = 0.25f * ((av + bv) + (cv + dv));
-                    }
-                    if (vp && !(m & 1)) {
-                        uint32_t pk[4];
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            __nv_bfloat162 h2 = __floats2bfloat162_rn(rr[2 * j], rr[2 * j + 1]);
-                            pk[j] = *reinterpret_cast<uint32_t*>(&h2);
+                            for (int j = 0; j < 4; ++j) {
+                                __nv_bfloat162 h2 = __floats2bfloat162_rn(rr[2 * j], rr[2 * j + 1]);
+                                pk[j] = *reinterpret_cast<uint32_t*>(&h2);
+                            }
+                            const int wp = P.w >> 1;
+                            *reinterpret_cast<uint4*>((uint8_t*)P.pool_y +
+                                ((((size_t)imga * (P.h >> 1) + (ya >> 1)) * P.out_nch + plane0 + ch) *
+                                     wp + (xa >> 1)) * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                         }
-                        const int wp = P.w >> 1;
-                        *reinterpret_cast<uint4*>((uint8_t*)P.pool_y +
-                            ((((size_t)imga * (P.h >> 1) + (ya >> 1)) * P.out_nch + plane) * wp +
-                             (xa >> 1)) * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                     }
                 }
             }
