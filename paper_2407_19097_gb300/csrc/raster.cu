@@ -380,13 +380,15 @@ __device__ __forceinline__ bool chunk_hidden(const RView& v, const float* c, con
     return wlo > __uint_as_float(m);
 }
 
-// Chunk-culling render pass.  prepass != 0: chunks 0, S, 2S, ... in full, one
+// Chunk-culling render pass (SINGLE: one view, its parameters held in registers rather than
+// read from shared memory for every point).  prepass != 0: chunks 0, S, 2S, ... in full, one
 // warp per chunk, one point per lane.  prepass == 0: every other chunk of the
 // groups [g_begin, g_end), 32 chunks per warp step -- each lane tests one chunk against every view and the
 // survivors join the warp's queue in shared memory; whenever four are queued the
 // warp renders them (each lane takes one point of each, so four early depth
 // reads are in flight per lane).  Rendering only full groups of four keeps the
 // lanes busy: a group costs the same instructions however many chunks it holds.
+template <bool SINGLE>
 __global__ void __launch_bounds__(256) chunk_render_kernel(const float* __restrict__ xyz, uint64_t n,
                                                            const float* __restrict__ chunks,
                                                            const __grid_constant__ RViews vs_arg,
@@ -417,6 +419,9 @@ __global__ void __launch_bounds__(256) chunk_render_kernel(const float* __restri
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const uint32_t nwarps = (gridDim.x * blockDim.x) / 32;
     const uint32_t all = (1u << vs.n) - 1u;
+    // one view: its parameters live in registers for the whole pass
+    RView vreg;
+    if (SINGLE) vreg = vs.v[0];
     // up to four chunks: one point of each per lane, then per view four projections,
     // four early depth reads and the atomics
     auto render4 = [&](const uint32_t* k, const uint32_t* vm, int cnt) {
@@ -440,7 +445,7 @@ __global__ void __launch_bounds__(256) chunk_render_kernel(const float* __restri
         while (vall) {
             const int v = __ffs(vall) - 1;
             vall &= vall - 1;
-            const RView& vw = vs.v[v];
+            const RView& vw = SINGLE ? vreg : vs.v[v];
             uint32_t pix[4], db[4];
             bool ok[4];
 #pragma unroll
@@ -495,10 +500,14 @@ __global__ void __launch_bounds__(256) chunk_render_kernel(const float* __restri
             const float2* cp = reinterpret_cast<const float2*>(chunks + 6 * (size_t)kk);
             const float2 a = __ldg(cp), b = __ldg(cp + 1), d = __ldg(cp + 2);
             const float c[3] = {a.x, a.y, b.x}, e[3] = {b.y, d.x, d.y};
-            for (int v = 0; v < vs.n; ++v)
-                if (!chunk_hidden(vs.v[v], c, e, bound ? bound + tile_off[v] : nullptr, tiles_x[v],
-                                  tiles_y[v]))
-                    vis |= 1u << v;
+            if (SINGLE) {
+                if (!chunk_hidden(vreg, c, e, bound, tiles_x[0], tiles_y[0])) vis = 1u;
+            } else {
+                for (int v = 0; v < vs.n; ++v)
+                    if (!chunk_hidden(vs.v[v], c, e, bound ? bound + tile_off[v] : nullptr,
+                                      tiles_x[v], tiles_y[v]))
+                        vis |= 1u << v;
+            }
         }
         const uint32_t ball = __ballot_sync(0xffffffffu, vis != 0);
         if (vis) {
@@ -544,6 +553,7 @@ struct VisVariant {
     int blocks_per_sm;   // resident blocks, from the compiled register count
     uint32_t chunk_S;    // chunk culling: every S-th chunk renders in the prepass (0: not chunked)
     int phases;          // chunk culling: culled passes, tile bounds rebuilt before each
+    int single;          // chunk culling, one view: the view's parameters held in registers
 };
 
 static VisVariant kSingle[] = {
@@ -558,6 +568,9 @@ static VisVariant kSingle[] = {
     {nullptr, true, "single/chunks/16", 0, 16, 1},
     {nullptr, true, "single/chunks/16x2", 0, 16, 2},
     {nullptr, true, "single/chunks/16x4", 0, 16, 4},
+    {nullptr, true, "single/chunks/16/r", 0, 16, 1, 1},
+    {nullptr, true, "single/chunks/16x2/r", 0, 16, 2, 1},
+    {nullptr, true, "single/chunks/16x4/r", 0, 16, 4, 1},
 };
 static VisVariant kMulti[] = {
     {visibility_kernel<false, true, 3, false>, false, "multi/prefetch/3", 0},
@@ -573,7 +586,8 @@ static nrv_status resident_blocks(VisVariant& v) {
     if (v.blocks_per_sm) return NRV_OK;
     cudaFuncAttributes fa;
     if (v.fn) NRV_CHECK_CUDA(cudaFuncGetAttributes(&fa, v.fn));
-    else NRV_CHECK_CUDA(cudaFuncGetAttributes(&fa, chunk_render_kernel));
+    else if (v.single) NRV_CHECK_CUDA(cudaFuncGetAttributes(&fa, chunk_render_kernel<true>));
+    else NRV_CHECK_CUDA(cudaFuncGetAttributes(&fa, chunk_render_kernel<false>));
     const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
     int b = 65536 / (regs_per_warp * 8);
     if (b > 8) b = 8;
@@ -594,8 +608,8 @@ static nrv_status run_variant(VisVariant& v, const float* xyz, uint64_t n,
         const int blocks = g_vis_sms * v.blocks_per_sm;
         const float* ch = reinterpret_cast<const float*>(chunks);
         const uint32_t ngroups = (uint32_t)((chunk_count(n) + 31) / 32);
-        chunk_render_kernel<<<blocks, 256, 0, s>>>(xyz, n, ch, views, views_dev, nullptr, 1, v.chunk_S,
-                                                   0u, 0u);
+        auto kern = v.single ? chunk_render_kernel<true> : chunk_render_kernel<false>;
+        kern<<<blocks, 256, 0, s>>>(xyz, n, ch, views, views_dev, nullptr, 1, v.chunk_S, 0u, 0u);
         NRV_CHECK_LAUNCH();
         // the chunk groups in `phases` consecutive parts, the tile bounds rebuilt from the
         // keys so far before each part (later parts meet tighter bounds)
@@ -604,8 +618,7 @@ static nrv_status run_variant(VisVariant& v, const float* xyz, uint64_t n,
             const uint32_t g1 = (uint32_t)((uint64_t)ngroups * (ph + 1) / v.phases);
             tile_bound_kernel<<<(unsigned)((ntiles * 32 + 255) / 256), 256, 0, s>>>(views, views_dev, tiles);
             NRV_CHECK_LAUNCH();
-            chunk_render_kernel<<<blocks, 256, 0, s>>>(xyz, n, ch, views, views_dev, tiles, 0,
-                                                       v.chunk_S, g0, g1);
+            kern<<<blocks, 256, 0, s>>>(xyz, n, ch, views, views_dev, tiles, 0, v.chunk_S, g0, g1);
             NRV_CHECK_LAUNCH();
         }
         return NRV_OK;
