@@ -69,6 +69,7 @@ constexpr int MAX_SLOTS = 16;
 constexpr int MAX_ACC = 4;      // accumulator buffers in TMEM (a power of two)
 constexpr int TILE_M = 128;
 constexpr int NTHREADS = 224;   // producer, MMA issuer, 4 epilogue warps, second MMA issuer
+constexpr int NTHREADS_S = 320; // row streaming: producer, MMA issuer, two groups of 4 epilogue warps
 
 struct TcParams {
     int n, h, w;             // input level geometry
@@ -238,7 +239,7 @@ __device__ __forceinline__ void head_store(const TcParams& P, const float* hw, i
 }
 
 template <bool FP8, bool STREAM, bool GATED>
-__global__ void __launch_bounds__(NTHREADS, STREAM ? 3 : 4)
+__global__ void __launch_bounds__(STREAM ? NTHREADS_S : NTHREADS, STREAM ? 2 : 4)
     conv3_tc_kernel(const __grid_constant__ CUtensorMap tm1, const __grid_constant__ CUtensorMap tm2,
                     const __grid_constant__ TcParams P) {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -289,7 +290,8 @@ __global__ void __launch_bounds__(NTHREADS, STREAM ? 3 : 4)
         }
     }
     // per output column of this slice: its bias (column n maps to channel n mod cout)
-    for (int i = threadIdx.x; i < P.n_slice; i += NTHREADS) {
+    constexpr int NT = STREAM ? NTHREADS_S : NTHREADS;
+    for (int i = threadIdx.x; i < P.n_slice; i += NT) {
         const int gcol = slice * P.n_slice + i;
         if (GATED) {
             const int ch = 16 * (gcol / 32) + (gcol & 15);
@@ -299,7 +301,7 @@ __global__ void __launch_bounds__(NTHREADS, STREAM ? 3 : 4)
         }
         colscale_s[i] = FP8 ? P.colscale[slice * P.n_slice + i] : 1.0f;
     }
-    for (int i = threadIdx.x; i <= MAX_KS; i += NTHREADS) alo_s[i] = i < P.nks ? P.a_lo[i] : 0u;
+    for (int i = threadIdx.x; i <= MAX_KS; i += NT) alo_s[i] = i < P.nks ? P.a_lo[i] : 0u;
     if (P.head_w && threadIdx.x < 51)
         head_ws[threadIdx.x] = threadIdx.x < 48 ? P.head_w[threadIdx.x] : P.head_b[threadIdx.x - 48];
     if (warp == 1) {
@@ -386,7 +388,7 @@ __global__ void __launch_bounds__(NTHREADS, STREAM ? 3 : 4)
             }
             mbar_wait(b_w, 0, &abort_flag, P.status, false);
         }
-    } else if (warp == 1 || warp == 6) {
+    } else if (warp == 1 || (!STREAM && warp == 6)) {
         const int iss = warp == 1 ? 0 : 1;   // this warp's issuer number
         if (lane == 0 && iss < P.nissue) {
             bool ok = mbar_wait(b_w, 0, &abort_flag, P.status);
@@ -549,7 +551,7 @@ __global__ void __launch_bounds__(NTHREADS, STREAM ? 3 : 4)
             mma_commit(b_done);
             mbar_wait(b_done, 0, &abort_flag, P.status, false);
         }
-    } else if (warp >= 2 && warp <= 5) {
+    } else if ((warp >= 2 && warp <= 5) || (STREAM && warp >= 6 && warp <= 9)) {
         // epilogue: warps 2..5 own TMEM lanes 32*(warp%4) ..; one lane per warp polls
         const int q = warp & 3;
         const int m = 32 * q + lane;
@@ -899,8 +901,21 @@ __global__ void __launch_bounds__(NTHREADS, STREAM ? 3 : 4)
             }
             SlotCursor cur;
             cur.init(t_begin);
+            // two groups of epilogue warps (2-5 and 6-9) take alternate slot groups
+            const int wg = warp >= 6 ? 1 : 0;
             int blk = 0, k = 0;
             for (int q0 = 0; q0 < S; q0 += P.grp, ++k) {
+                if ((k & 1) != wg) {
+                    // the other warp group's slots: step the cursor and the ring past them
+                    const int qe = q0 + P.grp < S ? q0 + P.grp : S;
+                    for (int qq = q0; qq < qe; ++qq) {
+                        bool rr = false, vv = false;
+                        int ii = 0, xx = 0, yy = 0;
+                        cur.next(P, t_end, m, rr, ii, xx, vv, yy);
+                        if (++blk == P.nb) blk = 0;
+                    }
+                    continue;
+                }
                 int okw = 1;
                 if (lane == 0)
                     okw = mbar_wait(b_afull(k & 3), (k >> 2) & 1, &abort_flag, P.status) ? 1 : 0;
@@ -1589,8 +1604,9 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
     const cudaFuncAttributes& fa = fa_k[kv];
     auto occupancy = [&](uint32_t smem_dyn, uint32_t cols, bool count_tmem = true) {
         const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
-        int o = prop.regsPerMultiprocessor / (regs_per_warp * (NTHREADS / 32));
-        o = o < prop.maxThreadsPerMultiProcessor / NTHREADS ? o : prop.maxThreadsPerMultiProcessor / NTHREADS;
+        const int nt = P.stream ? NTHREADS_S : NTHREADS;
+        int o = prop.regsPerMultiprocessor / (regs_per_warp * (nt / 32));
+        o = o < prop.maxThreadsPerMultiProcessor / nt ? o : prop.maxThreadsPerMultiProcessor / nt;
         const size_t smem_cta = smem_dyn + fa.sharedSizeBytes + prop.reservedSharedMemPerBlock;
         const int by_smem = (int)(prop.sharedMemPerMultiprocessor / smem_cta);
         o = o < by_smem ? o : by_smem;
@@ -1736,7 +1752,7 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
         cudaLaunchConfig_t cfg;
         memset(&cfg, 0, sizeof(cfg));
         cfg.gridDim = dim3((unsigned)(per_slice * c.nslices));
-        cfg.blockDim = dim3(NTHREADS);
+        cfg.blockDim = dim3(P.stream ? NTHREADS_S : NTHREADS);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = s;
         cudaLaunchAttribute attr[1];
