@@ -1555,14 +1555,14 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
         // one issuer; a ring of nb blocks in 128 TMEM columns for 16-column slices (four CTAs
         // per SM), 256 otherwise; groups of grp rows, gm groups in flight, gm * grp + 2 <= nb
         P.nissue = 1;
-        P.nb = (c.n_slice == 16 ? 128 : 256) / c.n_slice;
+        P.nb = 256 / c.n_slice;
         P.grp = (P.nb - 2) / 3;
         P.gm = 3;
         if (P.grp < 1) {
             P.grp = 1;
             P.gm = P.nb - 2;
         }
-        if (P.nb < 4 || P.gm * P.grp + 2 > P.nb || P.gm > 3 || (!fp8 && P.grp != 2))
+        if (P.nb < 4 || P.gm * P.grp + 2 > P.nb || P.gm > 3 || (!fp8 && (P.grp & 1)))
             return fail(NRV_ERR_UNSUPPORTED, "row streaming: TMEM ring");
     }
     // TMEM columns for rpt rows per tile and nacc accumulator buffers (a power of two >= 32)
