@@ -67,6 +67,14 @@ int64_t gnet_layers(int c0, GLayer* L) {
 // packed G-buffers (8 BF16 channels per pixel in and out), FP32 accumulation.
 __global__ void inj_kernel(const uint4* __restrict__ x, uint4* __restrict__ g, size_t npx, int c0,
                            const float* __restrict__ w, const float* __restrict__ b) {
+    // the weights in registers (channels from c0 on are neither read nor written but as zero)
+    float wr[8][8], br[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        br[k] = k < c0 ? b[k] : 0.0f;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) wr[k][c] = (k < c0 && c < c0) ? w[k * c0 + c] : 0.0f;
+    }
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < npx;
          i += (size_t)gridDim.x * blockDim.x) {
         const uint4 raw = x[i];
@@ -81,11 +89,10 @@ __global__ void inj_kernel(const uint4* __restrict__ x, uint4* __restrict__ g, s
         float o[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            float acc = 0.0f;
-            if (k < c0) {
-                acc = b[k];
-                for (int c = 0; c < c0; ++c) acc = fmaf(w[k * c0 + c], in[c], acc);
-            }
+            float acc = br[k];
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (c < c0) acc = fmaf(wr[k][c], in[c], acc);
             o[k] = acc;
         }
         uint32_t pk[4];

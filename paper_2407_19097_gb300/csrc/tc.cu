@@ -771,8 +771,9 @@ __global__ void __launch_bounds__(STREAM ? NTHREADS_S : NTHREADS, STREAM ? 2 : 4
         // fused pool the pair is an even and the following odd row, pooled from registers.
         auto emit_pair = [&](uint32_t ta, bool ra, int imga, int xa, bool va, int ya, uint32_t tb,
                              bool rb, int imgb, int xb, bool vb, int yb) {
-            const int nchunk = P.n_slice / 8;   // 8-channel chunks (one plane each)
-            const int plane0 = slice * P.n_slice / 8;
+            // 8-output-channel chunks (one plane each); gated: features and gates of 8 channels
+            const int nchunk = GATED ? P.n_slice / 16 : P.n_slice / 8;
+            const int plane0 = ((slice * P.n_slice) >> (GATED ? 1 : 0)) / 8;
             const size_t pstride = (size_t)P.w * 16;   // bytes between planes of a row
             // this pixel's 16-byte word in plane 0 of rows a and b
             uint8_t* const pya = (uint8_t*)P.y + (((size_t)imga * P.h + ya) * P.out_nch * P.w + xa) * 16;
@@ -788,16 +789,30 @@ __global__ void __launch_bounds__(STREAM ? NTHREADS_S : NTHREADS, STREAM ? 2 : 4
             }
 #pragma unroll 1
             for (int ch = 0; ch < nchunk; ++ch) {
-                const int cf = ch * 8;
-                uint32_t fa[8], fb[8];
+                const int cf = GATED ? (ch >> 1) * 32 + (ch & 1) * 8 : ch * 8;
+                uint32_t fa[8], fb[8], ga[8], gb[8];
                 if (ra) tmem_ld8_nowait(ta + (uint32_t)cf, fa);
                 if (rb) tmem_ld8_nowait(tb + (uint32_t)cf, fb);
+                if (GATED) {
+                    if (ra) tmem_ld8_nowait(ta + (uint32_t)(cf + 16), ga);
+                    if (rb) tmem_ld8_nowait(tb + (uint32_t)(cf + 16), gb);
+                }
                 tmem_ld_wait();
                 tmem_tie8(fa);
                 tmem_tie8(fb);
+                if (GATED) {
+                    tmem_tie8(ga);
+                    tmem_tie8(gb);
+                }
                 const float4* b4 = reinterpret_cast<const float4*>(bias_s + cf);
                 const float4 bb0 = b4[0], bb1 = b4[1];
                 const float bq[8] = {bb0.x, bb0.y, bb0.z, bb0.w, bb1.x, bb1.y, bb1.z, bb1.w};
+                float gq[8];
+                if (GATED) {
+                    const float4 g0 = b4[4], g1 = b4[5];   // the gate columns' biases, 16 on
+                    gq[0] = g0.x; gq[1] = g0.y; gq[2] = g0.z; gq[3] = g0.w;
+                    gq[4] = g1.x; gq[5] = g1.y; gq[6] = g1.z; gq[7] = g1.w;
+                }
                 uint32_t pa[4], pb[4];   // rows a and b as BF16 pairs
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -805,7 +820,17 @@ __global__ void __launch_bounds__(STREAM ? NTHREADS_S : NTHREADS, STREAM ? 2 : 4
                     float u1 = __uint_as_float(fa[2 * j + 1]) + bq[2 * j + 1];
                     float w0 = __uint_as_float(fb[2 * j]) + bq[2 * j];
                     float w1 = __uint_as_float(fb[2 * j + 1]) + bq[2 * j + 1];
-                    if (relu) {
+                    if (GATED) {
+                        // ELU(f) * sigmoid(g), as in the per-row epilogue
+                        auto gate = [](float f, float g) {
+                            const float e = __expf(fminf(f, 0.0f));
+                            return __fdividef(f > 0.0f ? f : e - 1.0f, 1.0f + __expf(-g));
+                        };
+                        u0 = gate(u0, __uint_as_float(ga[2 * j]) + gq[2 * j]);
+                        u1 = gate(u1, __uint_as_float(ga[2 * j + 1]) + gq[2 * j + 1]);
+                        w0 = gate(w0, __uint_as_float(gb[2 * j]) + gq[2 * j]);
+                        w1 = gate(w1, __uint_as_float(gb[2 * j + 1]) + gq[2 * j + 1]);
+                    } else if (relu) {
                         u0 = fmaxf(u0, 0.0f);
                         u1 = fmaxf(u1, 0.0f);
                         w0 = fmaxf(w0, 0.0f);
@@ -936,7 +961,7 @@ __global__ void __launch_bounds__(STREAM ? NTHREADS_S : NTHREADS, STREAM ? 2 : 4
                         tb = tmem + lanes + (uint32_t)(blk * P.n_slice);
                         if (++blk == P.nb) blk = 0;
                     }
-                    if (FP8 || GATED) {
+                    if (FP8) {
                         if (ra) emit_row(ta, ia, xa, va, ya);
                         if (rb) emit_row(tb, ib, xb, vb, yb);
                     } else {
