@@ -773,7 +773,8 @@ __global__ void __launch_bounds__(STREAM ? NTHREADS_S : NTHREADS, STREAM ? 2 : 4
                              bool rb, int imgb, int xb, bool vb, int yb) {
             // 8-output-channel chunks (one plane each); gated: features and gates of 8 channels
             const int nchunk = GATED ? P.n_slice / 16 : P.n_slice / 8;
-            const int plane0 = ((slice * P.n_slice) >> (GATED ? 1 : 0)) / 8;
+            const int oc0 = (slice * P.n_slice) >> (GATED ? 1 : 0);   // first output channel
+            const int plane0 = oc0 / 8;                                    // (BF16 planes)
             const size_t pstride = (size_t)P.w * 16;   // bytes between planes of a row
             // this pixel's 16-byte word in plane 0 of rows a and b
             uint8_t* const pya = (uint8_t*)P.y + (((size_t)imga * P.h + ya) * P.out_nch * P.w + xa) * 16;
@@ -813,48 +814,81 @@ __global__ void __launch_bounds__(STREAM ? NTHREADS_S : NTHREADS, STREAM ? 2 : 4
                     gq[0] = g0.x; gq[1] = g0.y; gq[2] = g0.z; gq[3] = g0.w;
                     gq[4] = g1.x; gq[5] = g1.y; gq[6] = g1.z; gq[7] = g1.w;
                 }
-                uint32_t pa[4], pb[4];   // rows a and b as BF16 pairs
+                // scale, bias, activation and the stored form: BF16 pairs, or E4M3 codes of
+                // v / s_out (8 channels = 8 bytes, half of a 16-channel plane)
+                uint32_t pa[4], pb[4];
+                uint32_t qa[2] = {0u, 0u}, qb[2] = {0u, 0u};
+                if (FP8) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    float u0 = __uint_as_float(fa[2 * j]) + bq[2 * j];
-                    float u1 = __uint_as_float(fa[2 * j + 1]) + bq[2 * j + 1];
-                    float w0 = __uint_as_float(fb[2 * j]) + bq[2 * j];
-                    float w1 = __uint_as_float(fb[2 * j + 1]) + bq[2 * j + 1];
-                    if (GATED) {
-                        // ELU(f) * sigmoid(g), as in the per-row epilogue
-                        auto gate = [](float f, float g) {
-                            const float e = __expf(fminf(f, 0.0f));
-                            return __fdividef(f > 0.0f ? f : e - 1.0f, 1.0f + __expf(-g));
-                        };
-                        u0 = gate(u0, __uint_as_float(ga[2 * j]) + gq[2 * j]);
-                        u1 = gate(u1, __uint_as_float(ga[2 * j + 1]) + gq[2 * j + 1]);
-                        w0 = gate(w0, __uint_as_float(gb[2 * j]) + gq[2 * j]);
-                        w1 = gate(w1, __uint_as_float(gb[2 * j + 1]) + gq[2 * j + 1]);
-                    } else if (relu) {
-                        u0 = fmaxf(u0, 0.0f);
-                        u1 = fmaxf(u1, 0.0f);
-                        w0 = fmaxf(w0, 0.0f);
-                        w1 = fmaxf(w1, 0.0f);
+                    for (int j = 0; j < 8; ++j) {
+                        const float sc = colscale_s[cf + j];
+                        float u = fmaf(__uint_as_float(fa[j]), sc, bq[j]);
+                        float w = fmaf(__uint_as_float(fb[j]), sc, bq[j]);
+                        if (relu) {
+                            u = fmaxf(u, 0.0f);
+                            w = fmaxf(w, 0.0f);
+                        }
+                        const uint32_t ca = __nv_cvt_float_to_fp8(u * P.inv_out, __NV_SATFINITE, __NV_E4M3);
+                        const uint32_t cb = __nv_cvt_float_to_fp8(w * P.inv_out, __NV_SATFINITE, __NV_E4M3);
+                        qa[j >> 2] |= ca << (8 * (j & 3));
+                        qb[j >> 2] |= cb << (8 * (j & 3));
                     }
-                    __nv_bfloat162 h2 = __floats2bfloat162_rn(u0, u1);
-                    pa[j] = *reinterpret_cast<uint32_t*>(&h2);
-                    h2 = __floats2bfloat162_rn(w0, w1);
-                    pb[j] = *reinterpret_cast<uint32_t*>(&h2);
-                }
-                const size_t poff = (size_t)(plane0 + ch) * pstride;
-                if (sa) *reinterpret_cast<uint4*>(pya + poff) = make_uint4(pa[0], pa[1], pa[2], pa[3]);
-                if (sb) *reinterpret_cast<uint4*>(pyb + poff) = make_uint4(pb[0], pb[1], pb[2], pb[3]);
-                if (P.head_w || pool) {
-                    // the stored (BF16-rounded) values, for the head and the pool
-                    float a8[8], b8[8];
+                } else {
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const __nv_bfloat162 x2 = *reinterpret_cast<const __nv_bfloat162*>(&pa[j]);
-                        const __nv_bfloat162 y2 = *reinterpret_cast<const __nv_bfloat162*>(&pb[j]);
-                        a8[2 * j] = __low2float(x2);
-                        a8[2 * j + 1] = __high2float(x2);
-                        b8[2 * j] = __low2float(y2);
-                        b8[2 * j + 1] = __high2float(y2);
+                        float u0 = __uint_as_float(fa[2 * j]) + bq[2 * j];
+                        float u1 = __uint_as_float(fa[2 * j + 1]) + bq[2 * j + 1];
+                        float w0 = __uint_as_float(fb[2 * j]) + bq[2 * j];
+                        float w1 = __uint_as_float(fb[2 * j + 1]) + bq[2 * j + 1];
+                        if (GATED) {
+                            // ELU(f) * sigmoid(g), as in the per-row epilogue
+                            auto gate = [](float f, float g) {
+                                const float e = __expf(fminf(f, 0.0f));
+                                return __fdividef(f > 0.0f ? f : e - 1.0f, 1.0f + __expf(-g));
+                            };
+                            u0 = gate(u0, __uint_as_float(ga[2 * j]) + gq[2 * j]);
+                            u1 = gate(u1, __uint_as_float(ga[2 * j + 1]) + gq[2 * j + 1]);
+                            w0 = gate(w0, __uint_as_float(gb[2 * j]) + gq[2 * j]);
+                            w1 = gate(w1, __uint_as_float(gb[2 * j + 1]) + gq[2 * j + 1]);
+                        } else if (relu) {
+                            u0 = fmaxf(u0, 0.0f);
+                            u1 = fmaxf(u1, 0.0f);
+                            w0 = fmaxf(w0, 0.0f);
+                            w1 = fmaxf(w1, 0.0f);
+                        }
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(u0, u1);
+                        pa[j] = *reinterpret_cast<uint32_t*>(&h2);
+                        h2 = __floats2bfloat162_rn(w0, w1);
+                        pb[j] = *reinterpret_cast<uint32_t*>(&h2);
+                    }
+                }
+                if (FP8) {
+                    const int oc = oc0 + 8 * ch;
+                    const size_t poff = (size_t)(oc / 16) * pstride + (size_t)(oc & 15);
+                    if (sa) *reinterpret_cast<uint2*>(pya + poff) = make_uint2(qa[0], qa[1]);
+                    if (sb) *reinterpret_cast<uint2*>(pyb + poff) = make_uint2(qb[0], qb[1]);
+                } else {
+                    const size_t poff = (size_t)(plane0 + ch) * pstride;
+                    if (sa) *reinterpret_cast<uint4*>(pya + poff) = make_uint4(pa[0], pa[1], pa[2], pa[3]);
+                    if (sb) *reinterpret_cast<uint4*>(pyb + poff) = make_uint4(pb[0], pb[1], pb[2], pb[3]);
+                }
+                if (P.head_w || pool) {
+                    // the values as stored (BF16-rounded, or E4M3 decoded), for the head and pool
+                    float a8[8], b8[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        if (FP8) {
+                            __nv_fp8_e4m3 x8, y8;
+                            x8.__x = (uint8_t)(qa[j >> 2] >> (8 * (j & 3)));
+                            y8.__x = (uint8_t)(qb[j >> 2] >> (8 * (j & 3)));
+                            a8[j] = float(x8) * P.head_s;
+                            b8[j] = float(y8) * P.head_s;
+                        } else {
+                            const __nv_bfloat162 x2 = *reinterpret_cast<const __nv_bfloat162*>(&pa[j >> 1]);
+                            const __nv_bfloat162 y2 = *reinterpret_cast<const __nv_bfloat162*>(&pb[j >> 1]);
+                            a8[j] = (j & 1) ? __high2float(x2) : __low2float(x2);
+                            b8[j] = (j & 1) ? __high2float(y2) : __low2float(y2);
+                        }
                     }
                     if (P.head_w) {
                         // the 1x1 head: channels in order, one fused multiply-add each
@@ -961,12 +995,7 @@ __global__ void __launch_bounds__(STREAM ? NTHREADS_S : NTHREADS, STREAM ? 2 : 4
                         tb = tmem + lanes + (uint32_t)(blk * P.n_slice);
                         if (++blk == P.nb) blk = 0;
                     }
-                    if (FP8) {
-                        if (ra) emit_row(ta, ia, xa, va, ya);
-                        if (rb) emit_row(tb, ib, xb, vb, yb);
-                    } else {
-                        emit_pair(ta, ra, ia, xa, va, ya, tb, rb, ib, xb, vb, yb);
-                    }
+                    emit_pair(ta, ra, ia, xa, va, ya, tb, rb, ib, xb, vb, yb);
                     // zero the blocks for their next output rows
                     for (int c = 0; c < P.n_slice; c += 16) tmem_zero16(ta + (uint32_t)c);
                     if (hasb)
@@ -1587,7 +1616,7 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
             P.grp = 1;
             P.gm = P.nb - 2;
         }
-        if (P.nb < 4 || P.gm * P.grp + 2 > P.nb || P.gm > 3 || (!fp8 && (P.grp & 1)))
+        if (P.nb < 4 || P.gm * P.grp + 2 > P.nb || P.gm > 3 || (P.grp & 1))
             return fail(NRV_ERR_UNSUPPORTED, "row streaming: TMEM ring");
     }
     // TMEM columns for rpt rows per tile and nacc accumulator buffers (a power of two >= 32)
