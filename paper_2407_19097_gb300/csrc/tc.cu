@@ -1010,6 +1010,60 @@ __global__ void __launch_bounds__(STREAM ? NTHREADS_S : NTHREADS, STREAM ? 2 : 4
             }
             tmem_st_wait();
         } else {
+        // The 2x2 stride-2 transposed conv (BF16, one slice of all 4 C_out columns): column
+        // (2a + b) C_out + o of input row y, pixel x goes to output row 2y + a, pixel 2x + b.
+        // Both pixel parities of one 8-channel chunk are loaded together and stored as 32
+        // contiguous bytes.
+        auto emit_up = [&](uint32_t tbase, int img, int x, bool valid, int yy) {
+            const size_t wo = 2 * (size_t)P.w;
+#pragma unroll 1
+            for (int a = 0; a < 2; ++a) {
+                uint8_t* const prow =
+                    (uint8_t*)P.y + ((((size_t)img * 2 * P.h + 2 * yy + a) * P.out_nch) * wo + 2 * x) * 16;
+#pragma unroll 1
+                for (int o8 = 0; o8 < P.cout; o8 += 8) {
+                    const int c0 = 2 * a * P.cout + o8, c1 = c0 + P.cout;   // b = 0 and b = 1
+                    uint32_t f0[8], f1[8];
+                    tmem_ld8_nowait(tbase + (uint32_t)c0, f0);
+                    tmem_ld8_nowait(tbase + (uint32_t)c1, f1);
+                    tmem_ld_wait();
+                    tmem_tie8(f0);
+                    tmem_tie8(f1);
+                    const float4* b4 = reinterpret_cast<const float4*>(bias_s + c0);
+                    const float4 bb0 = b4[0], bb1 = b4[1];
+                    const float bq[8] = {bb0.x, bb0.y, bb0.z, bb0.w, bb1.x, bb1.y, bb1.z, bb1.w};
+                    uint32_t p0[4], p1[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float u[2], v[2];
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const int q = 2 * j + e;
+                            u[e] = __uint_as_float(f0[q]);
+                            v[e] = __uint_as_float(f1[q]);
+                            u[e] += bq[q];
+                            v[e] += bq[q];
+                            if (P.relu) {
+                                u[e] = fmaxf(u[e], 0.0f);
+                                v[e] = fmaxf(v[e], 0.0f);
+                            }
+                        }
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(u[0], u[1]);
+                        p0[j] = *reinterpret_cast<uint32_t*>(&h2);
+                        h2 = __floats2bfloat162_rn(v[0], v[1]);
+                        p1[j] = *reinterpret_cast<uint32_t*>(&h2);
+                    }
+                    if (valid) {
+                        uint4* dst = reinterpret_cast<uint4*>(prow + (size_t)(o8 / 8) * wo * 16);
+                        dst[0] = make_uint4(p0[0], p0[1], p0[2], p0[3]);
+                        dst[1] = make_uint4(p1[0], p1[1], p1[2], p1[3]);
+                    }
+                }
+            }
+        };
+        const bool up_fast = !FP8 && !GATED && P.mode == 1 && P.nslices == 1 && P.nissue == 1 &&
+                             !P.mask &&
+                             P.store_y && !P.head_w && !P.pool_y && (P.cout % 8) == 0;
         TileWalk w;
         w.init(P, t_begin);
         for (int t = t_begin, i = 0; t < t_end; ++t, ++i, w.next(P)) {
@@ -1028,7 +1082,8 @@ __global__ void __launch_bounds__(STREAM ? NTHREADS_S : NTHREADS, STREAM ? 2 : 4
                 const bool valid = valid_x && yy < P.h;
                 const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) +
                                        (uint32_t)((ab * P.rpt + r) * P.nissue * P.n_slice);
-                emit_row(tbase, w.img, x, valid, yy);
+                if (up_fast) emit_up(tbase, w.img, x, valid, yy);
+                else emit_row(tbase, w.img, x, valid, yy);
             }
             tc_fence_before();
             __syncwarp();
@@ -1603,7 +1658,8 @@ static nrv_status tc_launch(const Net* net, const TcLayerCfg& c, const uint8_t* 
     P.w_region = (c.w_bytes + 1023) / 1024 * 1024;
     // two MMA issuers where both partial accumulators of both tile buffers fit in 256
     // TMEM columns and every input row has at least two K-steps (the issue loop's read-ahead)
-    P.nissue = (4 * c.n_slice <= 256 && c.nks / c.rows >= 2) ? 2 : 1;
+    // (transposed convs: one, their N is 4 C_out wide and their epilogue reads no partials)
+    P.nissue = (4 * c.n_slice <= 256 && c.nks / c.rows >= 2 && c.kind != UPCONV2) ? 2 : 1;
     P.stream = c.stream && conv && !mask ? 1 : 0;
     if (P.stream) {
         // one issuer; a ring of nb blocks in 128 TMEM columns for 16-column slices (four CTAs
