@@ -29,7 +29,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 BYTES_PER_POINT = 12.0          # xyz read once per frame for every view
 # DRAM bytes the render pass of the 350M-point 1080p trajectory frame moves (one ncu capture:
 # chunk boxes and the positions of prepass and surviving chunks, tile-bound reads, atomics)
-RENDER_TRAFFIC_BYTES = 1.251e9
+RENDER_TRAFFIC_BYTES = 1.2507e9
 # host -> device bytes of one replayed nrv_render_batch frame: the library's table of the views
 # (8 slots of 88 bytes and a count, 712 bytes), copied whole whatever the view count
 VIEW_TABLE_BYTES = 712
@@ -847,13 +847,13 @@ def main():
     vis_gbs = sc.n * BYTES_PER_POINT / (vis_ms * 1e-3) / 1e9
     bf_ms = stages_bf[1]
     bf_gbs = sc.n * BYTES_PER_POINT / (bf_ms * 1e-3) / 1e9
-    roof = {"kernel": "render pass (chunk_render_kernel x2 + tile_bound_kernel, tuned variant)",
+    roof = {"kernel": "render pass (chunk_render_kernel x3 + tile_bound_kernel x2, tuned variant)",
             "bound": "hbm", "achieved": vis_gbs,
             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": vis_gbs / peaks["hbm_gbs"],
             "traffic": RENDER_TRAFFIC_BYTES if (a.particles, a.steps_per_particle, W, H) ==
                        (1_000_000, 350, 1920, 1080) else None,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum summed over the "
-                              "render pass's launches of one frame (variant single/chunks/16x2), "
+                              "render pass's five launches of one frame (variant single/chunks/16x2/r), "
                               "profiles/render_pass_dram_traffic_trajectories_350m_1080p.md",
             "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": sc.n * BYTES_PER_POINT,
