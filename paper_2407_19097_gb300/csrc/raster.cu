@@ -273,10 +273,11 @@ __global__ void tile_bound_kernel(RViews vs_arg, const RViews* __restrict__ view
     if (v >= vs.n) return;    // whole warps leave together
     const RView& vw = vs.v[v];
     const int tx = (vw.width + TILE - 1) / TILE;
-    const int x0 = (t % tx) * TILE + (lane & 1) * 8, y = (t / tx) * TILE + lane / 2;
+    constexpr int LPR = 32 / TILE, PPL = TILE / LPR;   // lanes per tile row, pixels per lane
+    const int x0 = (t % tx) * TILE + (lane % LPR) * PPL, y = (t / tx) * TILE + lane / LPR;
     unsigned m = 0;
     if (y < vw.height)
-        for (int k = 0; k < 8; ++k)
+        for (int k = 0; k < PPL; ++k)
             if (x0 + k < vw.width)
                 m = max(m, (unsigned)(__ldcg(vw.key + (size_t)y * vw.width + x0 + k) >> 32));
     m = __reduce_max_sync(0xffffffffu, m);
