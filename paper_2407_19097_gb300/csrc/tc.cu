@@ -244,6 +244,9 @@ __global__ void __launch_bounds__(STREAM ? NTHREADS_S : NTHREADS, STREAM ? 2 : 4
                     const __grid_constant__ TcParams P) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t bars[2 * MAX_SLOTS + 2 * MAX_ACC + 2];
+    // row streaming: "group k's MMAs are done" (ring of 16, k mod 16): the epilogue's signal to
+    // drain the group and the loader's to reuse the slots of its rows
+    __shared__ __align__(8) uint64_t bars_g[16];
     __shared__ __align__(16) float bias_s[256];
     __shared__ __align__(16) float colscale_s[256];
     __shared__ __align__(16) float head_ws[52];
@@ -279,6 +282,8 @@ __global__ void __launch_bounds__(STREAM ? NTHREADS_S : NTHREADS, STREAM ? 2 : 4
             mbar_init(b_aempty(i), 4);
         }
         mbar_init(b_done, P.nissue);
+        if (STREAM)
+            for (int i = 0; i < 16; ++i) mbar_init(smem_u32(&bars_g[i]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         // the weights (packed long before this launch; see the dependency wait below)
@@ -351,7 +356,18 @@ __global__ void __launch_bounds__(STREAM ? NTHREADS_S : NTHREADS, STREAM ? 2 : 4
                 // 8-byte elements: pixel x starts at element 2x (16-byte aligned)
                 const int xe = 2 * (w.xt * P.tile_w + P.xoff);
                 for (; next_row <= last; ++next_row) {
-                    if (!mbar_wait(b_hempty(slot), phase ^ 1u, &abort_flag, P.status)) {
+                    if (STREAM) {
+                        // load number nloads reuses the slot of input row nloads - nslot: wait
+                        // until that row's group has committed
+                        if (nloads >= P.nslot) {
+                            const int g = (nloads - P.nslot) / P.grp;
+                            if (!mbar_wait(smem_u32(&bars_g[g & 15]), (uint32_t)(g >> 4) & 1u,
+                                           &abort_flag, P.status)) {
+                                ok = false;
+                                break;
+                            }
+                        }
+                    } else if (!mbar_wait(b_hempty(slot), phase ^ 1u, &abort_flag, P.status)) {
                         ok = false;
                         break;
                     }
@@ -455,17 +471,17 @@ __global__ void __launch_bounds__(STREAM ? NTHREADS_S : NTHREADS, STREAM ? 2 : 4
                                 }
                             }
                         }
-                        mma_commit(b_hempty(slot));   // the row is read once
                         ring_next(slot, ph, P.nslot);
                         if (++blk == P.nb) blk = 0;
                         if (++gin == P.grp) {
-                            mma_commit(b_afull(k & 3));
+                            // the group's rows are consumed and its output rows final
+                            mma_commit(smem_u32(&bars_g[k & 15]));
                             gin = 0;
                             ++k;
                         }
                     }
                 }
-                if (ok && gin > 0) mma_commit(b_afull(k & 3));   // the last, partial group
+                if (ok && gin > 0) mma_commit(smem_u32(&bars_g[k & 15]));   // the last, partial group
             } else {
             TileWalk w;
             w.init(P, t_begin);
@@ -977,7 +993,7 @@ __global__ void __launch_bounds__(STREAM ? NTHREADS_S : NTHREADS, STREAM ? 2 : 4
                 }
                 int okw = 1;
                 if (lane == 0)
-                    okw = mbar_wait(b_afull(k & 3), (k >> 2) & 1, &abort_flag, P.status) ? 1 : 0;
+                    okw = mbar_wait(smem_u32(&bars_g[k & 15]), (k >> 4) & 1, &abort_flag, P.status) ? 1 : 0;
                 okw = __shfl_sync(0xffffffffu, okw, 0);
                 if (!okw) break;
                 tc_fence_after();
