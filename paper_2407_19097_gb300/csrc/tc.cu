@@ -425,6 +425,9 @@ __global__ void __launch_bounds__(STREAM ? NTHREADS_S : NTHREADS, STREAM ? 2 : 4
                 const uint32_t ns = (uint32_t)P.n_slice;
                 int slot = 0, blk = 0, gin = 0, k = 0;
                 uint32_t ph = 0;
+                uint32_t alo_r[6];
+#pragma unroll
+                for (int j = 0; j < 6; ++j) alo_r[j] = j < ks_row ? alo_s[j] : 0u;
                 // segments: runs of tiles in one tile column; a segment of R output rows
                 // streams its R + 2 input rows, whose slots hold output rows y0 - 2 .. y0 + R - 1
                 for (int t = t_begin; ok && t < t_end;) {
@@ -449,7 +452,17 @@ __global__ void __launch_bounds__(STREAM ? NTHREADS_S : NTHREADS, STREAM ? 2 : 4
                         const uint32_t base = ring16 + (uint32_t)slot * slot16;
                         const uint32_t d = tmem + (uint32_t)blk * ns;
                         uint32_t b_lo = b_lo0s;
-                        if (blk <= P.nb - 3) {
+                        if (blk <= P.nb - 3 && ks_row <= 6) {
+                            // short rows (the narrow layers): descriptor words from registers
+#pragma unroll
+                            for (int j = 0; j < 6; ++j)
+                                if (j < ks_row) {
+                                    const uint64_t a = hi | (uint64_t)(base + alo_r[j]);
+                                    const uint64_t b = hi | (uint64_t)(b_lo0s + (uint32_t)j * b_jstep);
+                                    if (FP8) mma_fp8(d, a, b, P.idesc, 1u);
+                                    else mma_bf16(d, a, b, P.idesc, 1u);
+                                }
+                        } else if (blk <= P.nb - 3) {
                             for (int j = 0; j < ks_row; ++j, b_lo += b_jstep) {
                                 const uint64_t a = hi | (uint64_t)(base + alo_s[j]);
                                 if (FP8) mma_fp8(d, a, hi | (uint64_t)b_lo, P.idesc, 1u);
