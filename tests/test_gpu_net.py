@@ -152,6 +152,46 @@ def test_backward_bf16():
     _grad_case(nrv.PREC_BF16, 0.15)
 
 
+def test_backward_bf16_training_shape():
+    """The BF16 backward at the training configuration's shape (16 crops of 256 x 256, Sec. 3.3
+    training) against the oracle at BF16 storage precision, seeded weights and inputs: the same
+    statistical bound as the small case (<= 0.15 relative per tensor, cosine >= 0.99)."""
+    import torch
+    from paper_2407_19097_gb300 import nrv
+    c0, n, h, w = 5, 16, 256, 256
+    flat = make_params(c0, seed=7, bias_sigma=0.05)
+    x = _input(n, h, w, c0, seed=11)
+    q = _bf16
+    _, s = unet.forward(_bf16(x)[..., :c0], _fwd_params(flat, c0, 1), save=True, q=q)
+    net, p = _net(c0, flat)
+    dev = torch_dev()
+    xt = torch.from_numpy(x).to(dev).to(torch.bfloat16)
+    rgb = torch.empty((n, h, w, 3), device=dev)
+    net.forward_train(xt, n, h, w, nrv.PREC_BF16, rgb)
+    rng = np.random.default_rng(4)
+    dy = (rng.standard_normal((n, h, w, 3)) * 1e-2).astype(np.float32)
+    g = torch.zeros_like(p)
+    net.backward(torch.from_numpy(dy).to(dev), g)
+    gr, _ = unet.backward(dy.astype(np.float64), unet.unflatten(flat, c0), s, q=q)
+    torch.cuda.synchronize()
+    gg = g.cpu().numpy().astype(np.float64)
+    o = 0
+    errs = {}
+    for name, kind, ci, co in unet.layers(c0):
+        wref, bref = gr[name]
+        for part, ref in (("w", wref), ("b", bref)):
+            got = gg[o:o + ref.size]
+            errs[name + "." + part] = np.linalg.norm(got - ref.ravel()) / max(np.linalg.norm(ref), 1e-30)
+            o += ref.size
+    assert o == gg.size
+    report = " ".join(f"{k}={v:.2e}" for k, v in errs.items())
+    print(report)
+    assert all(v <= 0.15 for v in errs.values()), report
+    ref_all = unet.flatten(gr, c0)
+    cos = float(gg @ ref_all / (np.linalg.norm(gg) * np.linalg.norm(ref_all)))
+    assert cos >= 0.99, cos
+
+
 def test_l1_and_adam():
     import torch
     from paper_2407_19097_gb300 import nrv
