@@ -50,7 +50,19 @@
 // The 2x2 stride-2 transposed conv runs through the same kernel as a GEMM of
 // one input row (K = C_in, tiles of 128 pixels, no halo) against all four
 // kernel positions at once (N = 4 C_out); its epilogue scatters column
-// (2a + b) * C_out + o to output pixel (2y + a, 2x + b).
+// (2a + b) * C_out + o to output pixel (2y + a, 2x + b), both pixel parities of an
+// 8-channel chunk together.
+//
+// Row streaming (the STREAM instantiations; every forward 3x3 conv): the tile walk above
+// becomes a stream of input rows.  The weights of the slice's three kernel rows sit side by
+// side as B (N = 3 * n_slice, columns [row 2 | row 1 | row 0]), each input row is multiplied
+// once (K = 3 taps * C_in) into three consecutive blocks of a ring of TMEM blocks (output row
+// q in block q mod nb; an MMA whose blocks straddle the ring's end is split in two), the
+// epilogue zeroes each block after draining it, and input rows are committed in groups (one
+// commit per group releases the group's slots to the loader and hands its final output rows
+// to the epilogue).  One MMA issuer; two groups of four epilogue warps (warps 2-5 and 6-9)
+// take alternate groups and drain two output rows at a time, 8 channels per step, with the
+// fused 2x2 pool computed from the even/odd pair in registers.
 #include <cuda.h>
 #include <string.h>
 
