@@ -193,7 +193,9 @@ def parse():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples every 20 ms while the timed region runs."""
+    """nvidia-smi clock/throttle samples every 10 ms while the timed region runs.  start() returns
+    once the first sample has been written (nvidia-smi takes a while to come up), so that a short
+    timed region is still covered."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -209,10 +211,17 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                          "--format=csv,noheader,nounits", "-lms", "10"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
+        self.skip = os.path.getsize(self.path)  # samples taken before the timed region are not used
 
     def stop(self):
         if not self.proc:
@@ -223,6 +232,7 @@ class ClockSampler:
         mhz, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
+            f.seek(getattr(self, "skip", 0))
             for line in f:
                 t = [x.strip() for x in line.split(",")]
                 if len(t) < 9:

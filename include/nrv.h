@@ -146,8 +146,9 @@ typedef struct nrv_scene nrv_scene;
 
 /* Describe a scene.  Borrows d_xyz and d_attr, which must outlive the scene.
  * The first render derives from d_xyz a bounding box for every chunk of 32
- * consecutive points (ceil(N/32) * 24 bytes of device memory, owned by the
- * scene) for occlusion culling in the render pass.
+ * consecutive points and for each of its four sub-chunks of 8 points
+ * (ceil(N/32) * 120 bytes of device memory, owned by the scene) for occlusion
+ * culling in the render pass.
  * Errors: NRV_ERR_ARG for a null pointer with N > 0, a d_xyz base that is not
  * 16-byte aligned, a d_attr base not aligned to min(16, 4*stride_words) bytes,
  * N >= 2^32, a stride not in {1,2,4,8} or K out of range. */

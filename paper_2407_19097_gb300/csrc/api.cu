@@ -50,14 +50,14 @@ using namespace nrv;
 struct nrv_scene {
     nrv_scene_desc d;
     DevBuf tiles;    // per-tile depth bounds of the render pass (nrv_rasterize)
-    DevBuf chunks;   // bounding box of every 32-point chunk (chunk culling)
+    DevBuf chunks;   // bounding boxes of every 32-point chunk and its 8-point sub-chunks (culling)
     bool chunks_ok = false;
 };
 
 // The chunk bounds are derived from the positions on first use and after nrv_scene_refresh.
 static nrv_status ensure_chunks(nrv_scene* s, cudaStream_t st) {
     if (s->chunks_ok || s->d.n_points == 0 || s->d.point_stride > 1) return NRV_OK;
-    NRV_TRY(s->chunks.ensure(chunk_count(s->d.n_points) * 6 * sizeof(float)));
+    NRV_TRY(s->chunks.ensure(chunk_box_bytes(s->d.n_points)));
     NRV_TRY(launch_chunk_bounds(s->d.d_xyz, s->d.n_points, s->chunks.p, st));
     s->chunks_ok = true;
     return NRV_OK;

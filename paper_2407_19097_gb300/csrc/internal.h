@@ -97,11 +97,16 @@ nrv_status launch_clear_keys(const RViews& views, cudaStream_t s);
 // Render pass.  `tiles` is scratch for the per-tile depth bounds of the culling
 // variants: visibility_scratch_bytes(views) bytes of device memory (may be null,
 // which disables culling).  `chunks` holds the bounding boxes of the scene's
-// 32-point chunks (6 floats each, chunk_count(n) of them, from
-// launch_chunk_bounds; may be null, which disables chunk culling).
+// 32-point chunks (6 floats each, chunk_count(n) of them) followed by those of
+// their 8-point sub-chunks (RENDER_SUBS per chunk, 6 floats each), from
+// launch_chunk_bounds (chunk_box_bytes(n) bytes); may be null, which disables
+// chunk culling.
 size_t visibility_scratch_bytes(const RViews& views);
 constexpr int RENDER_CHUNK = 32;
+constexpr int RENDER_SUB = 8;                               // points per sub-chunk
+constexpr int RENDER_SUBS = RENDER_CHUNK / RENDER_SUB;      // sub-chunks per chunk
 __host__ __device__ inline uint64_t chunk_count(uint64_t n) { return (n + RENDER_CHUNK - 1) / RENDER_CHUNK; }
+inline size_t chunk_box_bytes(uint64_t n) { return chunk_count(n) * (1 + RENDER_SUBS) * 6 * sizeof(float); }
 nrv_status launch_chunk_bounds(const float* xyz, uint64_t n, void* chunks, cudaStream_t s);
 // Render-pass variants (raster.cu): how many there are for one view / a batch, and their names.
 int visibility_variant_count(int multi);

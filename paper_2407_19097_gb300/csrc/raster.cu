@@ -44,6 +44,29 @@ nrv_status launch_clear_keys(const RViews& views, cudaStream_t s) {
 // word exceeds its tile's bound can never win there.
 constexpr int TILE = 16;
 
+// The bounds of one view form a pyramid: level 0 one word per tile, level l (up to
+// HIZ_LEVELS - 1) one word per 2^l x 2^l level-0 tiles (the maximum over those that exist),
+// level after level; the views' pyramids lie back to back.  A box test reads the level at
+// which the box's tile range spans at most 2 x 2 words.
+constexpr int HIZ_LEVELS = 4;
+struct TileDims {
+    int off[HIZ_LEVELS];   // word offset of each level in the view's pyramid (off[0] = 0)
+    int w0, h0;            // level-0 tiles per row and rows
+    int words;             // words of the pyramid
+};
+__host__ __device__ inline TileDims tile_dims(int width, int height) {
+    TileDims d;
+    d.w0 = (width + TILE - 1) / TILE;
+    d.h0 = (height + TILE - 1) / TILE;
+    int off = 0;
+    for (int l = 0; l < HIZ_LEVELS; ++l) {
+        d.off[l] = off;
+        off += (((d.w0 - 1) >> l) + 1) * (((d.h0 - 1) >> l) + 1);
+    }
+    d.words = off;
+    return d;
+}
+
 // Certainly rejected without the exact division?  The pixel is located with the
 // fast quotient __fdividef (documented error <= 2 ulp for divisors in
 // [2^-126, 2^126]).  Carrying that error and the roundings of the exact
@@ -156,9 +179,10 @@ __global__ void __launch_bounds__(256, MINB) visibility_kernel(const float4* __r
     if (threadIdx.x == 0) {
         int off = 0;
         for (int v = 0; v < vs.n; ++v) {
-            tiles_x[v] = (vs.v[v].width + TILE - 1) / TILE;
+            const TileDims d = tile_dims(vs.v[v].width, vs.v[v].height);
+            tiles_x[v] = d.w0;
             tile_off[v] = off;
-            off += tiles_x[v] * ((vs.v[v].height + TILE - 1) / TILE);
+            off += d.words;
         }
     }
     __syncthreads();
@@ -265,10 +289,10 @@ __global__ void tile_bound_kernel(RViews vs_arg, const RViews* __restrict__ view
     int v = 0;
     uint32_t* out = bound;
     for (; v < vs.n; ++v) {
-        const int tx = (vs.v[v].width + TILE - 1) / TILE, ty = (vs.v[v].height + TILE - 1) / TILE;
-        if (t < tx * ty) break;
-        t -= tx * ty;
-        out += tx * ty;
+        const TileDims d = tile_dims(vs.v[v].width, vs.v[v].height);
+        if (t < d.w0 * d.h0) break;
+        t -= d.w0 * d.h0;
+        out += d.words;
     }
     if (v >= vs.n) return;    // whole warps leave together
     const RView& vw = vs.v[v];
@@ -284,6 +308,56 @@ __global__ void tile_bound_kernel(RViews vs_arg, const RViews* __restrict__ view
     if (lane == 0) out[t] = m;
 }
 
+// Levels 1.. of the bound pyramids: one thread per word, the maximum over its level-0 tiles.
+__global__ void tile_pyramid_kernel(RViews vs_arg, const RViews* __restrict__ views_dev,
+                                    uint32_t* __restrict__ bound) {
+    const RViews& vs = views_dev ? *views_dev : vs_arg;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t* pyr = bound;
+    for (int v = 0; v < vs.n; ++v) {
+        const TileDims d = tile_dims(vs.v[v].width, vs.v[v].height);
+        const int coarse = d.words - d.off[1];
+        if (t < coarse) {
+            int l = 1;
+            while (l + 1 < HIZ_LEVELS && t >= d.off[l + 1] - d.off[1]) ++l;
+            const int i = t - (d.off[l] - d.off[1]);
+            const int wl = ((d.w0 - 1) >> l) + 1;
+            const int x0 = (i % wl) << l, y0 = (i / wl) << l;
+            const int x1 = min(x0 + (1 << l), d.w0), y1 = min(y0 + (1 << l), d.h0);
+            uint32_t m = 0;
+            for (int y = y0; y < y1; ++y)
+                for (int x = x0; x < x1; ++x) m = max(m, pyr[y * d.w0 + x]);
+            pyr[d.off[l] + i] = m;
+            return;
+        }
+        t -= coarse;
+        pyr += d.words;
+    }
+}
+
+static void tile_counts(const RViews& views, size_t& level0, size_t& coarse) {
+    level0 = coarse = 0;
+    for (int v = 0; v < views.n; ++v) {
+        const TileDims d = tile_dims(views.v[v].width, views.v[v].height);
+        level0 += (size_t)d.w0 * d.h0;
+        coarse += (size_t)(d.words - d.off[1]);
+    }
+}
+
+// Tile bounds of every view (level 0), and with hiz the levels above it.
+static nrv_status launch_tile_bounds(const RViews& views, const RViews* views_dev, uint32_t* tiles,
+                                     bool hiz, cudaStream_t s) {
+    size_t level0, coarse;
+    tile_counts(views, level0, coarse);
+    tile_bound_kernel<<<(unsigned)((level0 * 32 + 255) / 256), 256, 0, s>>>(views, views_dev, tiles);
+    NRV_CHECK_LAUNCH();
+    if (hiz) {
+        tile_pyramid_kernel<<<(unsigned)((coarse + 255) / 256), 256, 0, s>>>(views, views_dev, tiles);
+        NRV_CHECK_LAUNCH();
+    }
+    return NRV_OK;
+}
+
 // ------------------------------------------------------------------ chunk culling
 // The points are taken in chunks of 32 consecutive points, each with a bounding
 // box (centre and half extents) computed from the positions once per scene.  A
@@ -295,24 +369,36 @@ __global__ void tile_bound_kernel(RViews vs_arg, const RViews* __restrict__ view
 // point could not have set one (keys only decrease, so a bound read earlier
 // stays a valid bound).
 
-// Chunk box: centre c = (lo + hi) / 2 and half extents e >= max(hi - c, c - lo),
-// the differences rounded up, so |p - c| <= e holds exactly for every point p.
-// Stored as 6 floats per chunk: cx cy cz ex ey ez.  One warp per chunk.
+// Box of a chunk or sub-chunk: centre c = (lo + hi) / 2 and half extents
+// e >= max(hi - c, c - lo), the differences rounded up, so |p - c| <= e holds
+// exactly for every point p.  Stored as 6 floats: cx cy cz ex ey ez; the chunk
+// boxes first, then the sub-chunk boxes (sub-chunk s of chunk c at 4c + s).
+// One warp per chunk: the minimum and maximum over each group of 8 lanes give
+// the sub-chunk boxes, over all 32 lanes the chunk box.
 __global__ void chunk_bounds_kernel(const float* __restrict__ xyz, uint64_t n,
                                     float* __restrict__ out) {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, sub = lane / RENDER_SUB, sl = lane % RENDER_SUB;
     const uint64_t nch = chunk_count(n);
+    float* const out_sub = out + 6 * nch;
     const uint64_t warps = (gridDim.x * (uint64_t)blockDim.x) / 32;
     for (uint64_t c = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; c < nch; c += warps) {
         const uint64_t i0 = c * RENDER_CHUNK;
         const uint64_t i = i0 + lane < n ? i0 + lane : i0;   // lanes past the end repeat the first point
         float v[3] = {xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]};
+        float* const sb = out_sub + 6 * (RENDER_SUBS * c + sub);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             float lo = v[d], hi = v[d];
-            for (int o = 16; o > 0; o >>= 1) {
+            for (int o = 1; o < 32; o <<= 1) {
                 lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
                 hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+                if (o == RENDER_SUB / 2) {
+                    // lo, hi: this lane's sub-chunk
+                    const float ctr = 0.5f * lo + 0.5f * hi;
+                    const float e = fmaxf(__fsub_ru(hi, ctr), __fsub_ru(ctr, lo));
+                    if (sl == d) sb[d] = ctr;
+                    if (sl == 3 + d) sb[3 + d] = e;
+                }
             }
             const float ctr = 0.5f * lo + 0.5f * hi;
             const float e = fmaxf(__fsub_ru(hi, ctr), __fsub_ru(ctr, lo));
@@ -336,9 +422,10 @@ nrv_status launch_chunk_bounds(const float* xyz, uint64_t n, void* chunks, cudaS
 // magnitudes summed in each clip coordinate covers the rounding of the points'
 // own FP32 sequences and of this arithmetic (both below 1e-6 of that sum); the
 // screen rectangle is widened by half a pixel plus 1e-5 of its extent.
+template <bool HIZ>
 __device__ __forceinline__ bool chunk_hidden(const RView& v, const float* c, const float* e,
-                                             const uint32_t* __restrict__ bound, int tiles_x,
-                                             int tiles_y) {
+                                             const uint32_t* __restrict__ bound, const TileDims& td) {
+    const int tiles_x = td.w0, tiles_y = td.h0;
     const float ax = fabsf(c[0]) + e[0], ay = fabsf(c[1]) + e[1], az = fabsf(c[2]) + e[2];
     const float w = fmaf(v.m[8], c[0], fmaf(v.m[9], c[1], fmaf(v.m[10], c[2], v.m[11])));
     const float X = fmaf(v.m[0], c[0], fmaf(v.m[1], c[1], fmaf(v.m[2], c[2], v.m[3])));
@@ -356,10 +443,12 @@ __device__ __forceinline__ bool chunk_hidden(const RView& v, const float* c, con
     if (!(wlo > 0.5f * v.znear)) return false;                // w may come near 0: no screen bound
     const float dx = spread(0, ex) + ex, dy = spread(1, ey) + ey;
     const float xl = X - dx, xh = X + dx, yl = Y - dy, yh = Y + dy;
-    const float nxl = fminf(__fdividef(xl, wlo), __fdividef(xl, whi));
-    const float nxh = fmaxf(__fdividef(xh, wlo), __fdividef(xh, whi));
-    const float nyl = fminf(__fdividef(yl, wlo), __fdividef(yl, whi));
-    const float nyh = fmaxf(__fdividef(yh, wlo), __fdividef(yh, whi));
+    // 0 < wlo <= w <= whi over the box: the smallest quotient x / w is x / whi for x >= 0 and
+    // x / wlo otherwise (the largest the other way round); fast reciprocals, whose error the
+    // margins below cover
+    const float rlo = __fdividef(1.0f, wlo), rhi = __fdividef(1.0f, whi);
+    const float nxl = xl * (xl >= 0.0f ? rhi : rlo), nxh = xh * (xh >= 0.0f ? rlo : rhi);
+    const float nyl = yl * (yl >= 0.0f ? rhi : rlo), nyh = yh * (yh >= 0.0f ? rlo : rhi);
     const float mx = 0.5f + 1e-5f * v.hw * (fabsf(nxl) + fabsf(nxh) + 2.0f);
     const float my = 0.5f + 1e-5f * v.hh * (fabsf(nyl) + fabsf(nyh) + 2.0f);
     const float sx0 = (nxl + 1.0f) * v.hw - mx, sx1 = (nxh + 1.0f) * v.hw + mx;
@@ -373,24 +462,41 @@ __device__ __forceinline__ bool chunk_hidden(const RView& v, const float* c, con
     const int ty0 = sy0 > 0.0f ? (int)(sy0 * (1.0f / TILE)) : 0;
     const int tx1 = sx1 < v.fw ? (int)(sx1 * (1.0f / TILE)) : tiles_x - 1;
     const int ty1 = sy1 < v.fh ? (int)(sy1 * (1.0f / TILE)) : tiles_y - 1;
-    if (tx1 - tx0 >= 8 || ty1 - ty0 >= 8) return false;        // larger than 8 x 8 tiles: not tested
     uint32_t m = 0;
-    for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) m = max(m, __ldg(bound + ty * tiles_x + tx));
+    if (HIZ) {
+        // the lowest pyramid level at which the tile range spans at most 2 x 2 words
+        int l = 0;
+        while ((tx1 >> l) - (tx0 >> l) > 1 || (ty1 >> l) - (ty0 >> l) > 1)
+            if (++l == HIZ_LEVELS) return false;                  // wider still: not tested
+        const int off = l == 0 ? 0 : l == 1 ? td.off[1] : l == 2 ? td.off[2] : td.off[3];
+        const int wl = ((tiles_x - 1) >> l) + 1;
+        const uint32_t* b = bound + off;
+        const int x0 = tx0 >> l, x1 = tx1 >> l, r0 = (ty0 >> l) * wl, r1 = (ty1 >> l) * wl;
+        m = max(max(__ldg(b + r0 + x0), __ldg(b + r0 + x1)), max(__ldg(b + r1 + x0), __ldg(b + r1 + x1)));
+    } else {
+        if (tx1 - tx0 >= 8 || ty1 - ty0 >= 8) return false;    // larger than 8 x 8 tiles: not tested
+        for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx) m = max(m, __ldg(bound + ty * tiles_x + tx));
+    }
     // an empty pixel leaves the bound at 0xFFFFFFFF (a NaN): never hidden
     return wlo > __uint_as_float(m);
 }
 
 // Chunk-culling render pass (SINGLE: one view, its parameters held in registers rather than
-// read from shared memory for every point).  prepass != 0: chunks 0, S, 2S, ... in full, one
-// warp per chunk, one point per lane.  prepass == 0: every other chunk of the
+// read from shared memory for every point).  S is a power of two.  prepass != 0: chunks 0, S,
+// 2S, ... in full, one warp per chunk, one point per lane.  prepass == 0: every other chunk of the
 // groups [g_begin, g_end), 32 chunks per warp step -- each lane tests one chunk against every view and the
 // survivors join the warp's queue in shared memory; whenever four are queued the
 // warp renders them (each lane takes one point of each, so four early depth
 // reads are in flight per lane).  Rendering only full groups of four keeps the
 // lanes busy: a group costs the same instructions however many chunks it holds.
-template <bool SINGLE>
-__global__ void __launch_bounds__(256) chunk_render_kernel(const float* __restrict__ xyz, uint64_t n,
+// SUB: the surviving chunks are tested again, eight at a time, by their 8-point
+// sub-chunk boxes (one per lane); the surviving sub-chunks join a second queue
+// and render sixteen at a time (each lane takes one point of four of them).
+// HIZ: box tests read the bound pyramid (at most four words) instead of every
+// level-0 tile the box reaches.
+template <bool SINGLE, bool SUB, bool HIZ>
+__global__ void __launch_bounds__(256, 4) chunk_render_kernel(const float* __restrict__ xyz, uint64_t n,
                                                            const float* __restrict__ chunks,
                                                            const __grid_constant__ RViews vs_arg,
                                                            const RViews* __restrict__ views_dev,
@@ -398,7 +504,8 @@ __global__ void __launch_bounds__(256) chunk_render_kernel(const float* __restri
                                                            int prepass, uint32_t S, uint32_t g_begin,
                                                            uint32_t g_end) {
     __shared__ RViews vs;
-    __shared__ int tile_off[8], tiles_x[8], tiles_y[8];
+    __shared__ int tile_off[8];
+    __shared__ TileDims tdim[8];
     {
         const uint32_t* src = reinterpret_cast<const uint32_t*>(views_dev ? views_dev : &vs_arg);
         for (int i = threadIdx.x; i < (int)(sizeof(RViews) / 4); i += blockDim.x)
@@ -408,10 +515,9 @@ __global__ void __launch_bounds__(256) chunk_render_kernel(const float* __restri
     if (threadIdx.x == 0) {
         int off = 0;
         for (int v = 0; v < vs.n; ++v) {
-            tiles_x[v] = (vs.v[v].width + TILE - 1) / TILE;
-            tiles_y[v] = (vs.v[v].height + TILE - 1) / TILE;
+            tdim[v] = tile_dims(vs.v[v].width, vs.v[v].height);
             tile_off[v] = off;
-            off += tiles_x[v] * tiles_y[v];
+            off += tdim[v].words;
         }
     }
     __syncthreads();
@@ -422,18 +528,30 @@ __global__ void __launch_bounds__(256) chunk_render_kernel(const float* __restri
     const uint32_t all = (1u << vs.n) - 1u;
     // one view: its parameters live in registers for the whole pass
     RView vreg;
-    if (SINGLE) vreg = vs.v[0];
-    // up to four chunks: one point of each per lane, then per view four projections,
-    // four early depth reads and the atomics
-    auto render4 = [&](const uint32_t* k, const uint32_t* vm, int cnt) {
+    TileDims treg;
+    if (SINGLE) {
+        vreg = vs.v[0];
+        treg = tdim[0];
+    }
+    // the views of mask vm in which the box (c, e) may set a key
+    auto box_visible = [&](const float* c, const float* e, uint32_t vm) -> uint32_t {
+        if (SINGLE) return chunk_hidden<HIZ>(vreg, c, e, bound, treg) ? 0u : 1u;
+        uint32_t vis = 0;
+        for (int v = 0; v < vs.n; ++v)
+            if (((vm >> v) & 1u) &&
+                !chunk_hidden<HIZ>(vs.v[v], c, e, bound ? bound + tile_off[v] : nullptr, tdim[v]))
+                vis |= 1u << v;
+        return vis;
+    };
+    // points ip[j] of this lane (those with in[j]), each in the views of its mask vm[j]:
+    // per view four projections, four early depth reads, then the atomics
+    auto render_pts = [&](const uint64_t* ip, const bool* in, const uint32_t* vm) {
         float x[4], y[4], z[4];
         uint32_t idx[4];
-        bool in[4];
         uint32_t vall = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const uint64_t i = (uint64_t)k[j] * RENDER_CHUNK + lane;
-            in[j] = j < cnt && i < n;
+            const uint64_t i = ip[j];
             idx[j] = (uint32_t)i + vs.base;
             x[j] = y[j] = z[j] = 0.0f;
             if (in[j]) {
@@ -462,6 +580,17 @@ __global__ void __launch_bounds__(256) chunk_render_kernel(const float* __restri
             }
         }
     };
+    // up to four chunks: one point of each per lane
+    auto render4 = [&](const uint32_t* k, const uint32_t* vm, int cnt) {
+        uint64_t ip[4];
+        bool in[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            ip[j] = (uint64_t)k[j] * RENDER_CHUNK + lane;
+            in[j] = j < cnt && ip[j] < n;
+        }
+        render_pts(ip, in, vm);
+    };
     if (prepass) {
         // four prepass chunks per warp step
         for (uint32_t k0 = warp * 4 * S; k0 < nch; k0 += nwarps * 4 * S) {
@@ -477,12 +606,17 @@ __global__ void __launch_bounds__(256) chunk_render_kernel(const float* __restri
         }
         return;
     }
-    // this warp's queue of surviving chunks (at most 3 left over + 32 new)
-    __shared__ uint32_t q_k[8][36];
-    __shared__ uint8_t q_m[8][36];
+    // this warp's queue of surviving chunks (at most 7 left over + 32 new) and, SUB, of
+    // surviving sub-chunks (at most 15 left over + 32 new)
+    __shared__ uint32_t q_k[8][40];
+    __shared__ uint8_t q_m[8][40];
+    __shared__ uint32_t s_k[SUB ? 8 : 1][48];
+    __shared__ uint8_t s_m[SUB ? 8 : 1][48];
     uint32_t* qk = q_k[threadIdx.x / 32];
     uint8_t* qm = q_m[threadIdx.x / 32];
-    int qn = 0;   // queued, the same in every lane
+    uint32_t* sk = s_k[SUB ? threadIdx.x / 32 : 0];
+    uint8_t* sm = s_m[SUB ? threadIdx.x / 32 : 0];
+    int qn = 0, sn = 0;   // queued, the same in every lane
     auto render_queued = [&](int from, int cnt) {
         uint32_t k[4] = {0u, 0u, 0u, 0u}, vm[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
@@ -493,22 +627,61 @@ __global__ void __launch_bounds__(256) chunk_render_kernel(const float* __restri
             }
         render4(k, vm, cnt);
     };
+    // sub-chunks sk[from .. from + cnt), cnt <= 16: lane takes point lane % 8 of
+    // sub-chunks 4j + lane / 8, j = 0..3
+    auto render_subs = [&](int from, int cnt) {
+        uint64_t ip[4];
+        bool in[4];
+        uint32_t vm[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int q = 4 * j + lane / RENDER_SUB;
+            const bool have = q < cnt;
+            const uint32_t ks = have ? sk[from + q] : 0u;
+            vm[j] = have ? sm[from + q] : 0u;
+            ip[j] = (uint64_t)ks * RENDER_SUB + lane % RENDER_SUB;
+            in[j] = have && ip[j] < n;
+        }
+        render_pts(ip, in, vm);
+    };
+    // sub-chunk tests of the queued chunks qk[from .. from + cnt), cnt <= 8: lane tests
+    // sub-chunk lane % 4 of chunk lane / 4 in the views its chunk survived; the visible
+    // ones join the sub-chunk queue, which renders whenever sixteen are queued
+    auto test_subs = [&](int from, int cnt) {
+        const int c = lane / RENDER_SUBS;
+        uint32_t vis = 0, ks = 0;
+        if (c < cnt) {
+            ks = qk[from + c] * RENDER_SUBS + lane % RENDER_SUBS;
+            if ((uint64_t)ks * RENDER_SUB < n) {   // a sub-chunk past the last point holds none
+                const float2* cp = reinterpret_cast<const float2*>(chunks + 6 * ((size_t)nch + ks));
+                const float2 a = __ldg(cp), b = __ldg(cp + 1), d = __ldg(cp + 2);
+                const float cc[3] = {a.x, a.y, b.x}, ee[3] = {b.y, d.x, d.y};
+                vis = box_visible(cc, ee, qm[from + c]);
+            }
+        }
+        const uint32_t ball = __ballot_sync(0xffffffffu, vis != 0);
+        if (vis) {
+            const int at = sn + __popc(ball & ((1u << lane) - 1u));
+            sk[at] = ks;
+            sm[at] = (uint8_t)vis;
+        }
+        sn += __popc(ball);
+        __syncwarp();
+        while (sn >= 16) {
+            sn -= 16;
+            render_subs(sn, 16);
+        }
+        __syncwarp();
+    };
     // culled pass over the chunk groups [g_begin, g_end) of 32 chunks
     for (uint32_t g = g_begin + warp; g < g_end; g += nwarps) {
         const uint32_t kk = g * 32 + lane;
         uint32_t vis = 0;
-        if (kk < nch && kk % S != 0) {
+        if (kk < nch && (kk & (S - 1)) != 0) {
             const float2* cp = reinterpret_cast<const float2*>(chunks + 6 * (size_t)kk);
             const float2 a = __ldg(cp), b = __ldg(cp + 1), d = __ldg(cp + 2);
             const float c[3] = {a.x, a.y, b.x}, e[3] = {b.y, d.x, d.y};
-            if (SINGLE) {
-                if (!chunk_hidden(vreg, c, e, bound, tiles_x[0], tiles_y[0])) vis = 1u;
-            } else {
-                for (int v = 0; v < vs.n; ++v)
-                    if (!chunk_hidden(vs.v[v], c, e, bound ? bound + tile_off[v] : nullptr,
-                                      tiles_x[v], tiles_y[v]))
-                        vis |= 1u << v;
-            }
+            vis = box_visible(c, e, all);
         }
         const uint32_t ball = __ballot_sync(0xffffffffu, vis != 0);
         if (vis) {
@@ -518,20 +691,31 @@ __global__ void __launch_bounds__(256) chunk_render_kernel(const float* __restri
         }
         qn += __popc(ball);
         __syncwarp();
-        while (qn >= 4) {
-            qn -= 4;
-            render_queued(qn, 4);
+        if (SUB) {
+            while (qn >= 8) {
+                qn -= 8;
+                test_subs(qn, 8);
+            }
+        } else {
+            while (qn >= 4) {
+                qn -= 4;
+                render_queued(qn, 4);
+            }
         }
         __syncwarp();
     }
-    if (qn > 0) render_queued(0, qn);
+    if (SUB) {
+        if (qn > 0) test_subs(0, qn);
+        if (sn > 0) render_subs(0, sn);
+    } else if (qn > 0) {
+        render_queued(0, qn);
+    }
 }
 
 size_t visibility_scratch_bytes(const RViews& views) {
-    size_t tiles = 0;
-    for (int v = 0; v < views.n; ++v)
-        tiles += (size_t)((views.v[v].width + TILE - 1) / TILE) * ((views.v[v].height + TILE - 1) / TILE);
-    return tiles * sizeof(uint32_t);
+    size_t words = 0;
+    for (int v = 0; v < views.n; ++v) words += (size_t)tile_dims(views.v[v].width, views.v[v].height).words;
+    return words * sizeof(uint32_t);
 }
 
 // ------------------------------------------------------------------ variant choice
@@ -552,9 +736,12 @@ struct VisVariant {
     bool cull;
     const char* name;
     int blocks_per_sm;   // resident blocks, from the compiled register count
-    uint32_t chunk_S;    // chunk culling: every S-th chunk renders in the prepass (0: not chunked)
+    uint32_t chunk_S;    // chunk culling: every S-th chunk renders in the prepass (0: not chunked;
+                         // otherwise a power of two)
     int phases;          // chunk culling: culled passes, tile bounds rebuilt before each
     int single;          // chunk culling, one view: the view's parameters held in registers
+    int sub;             // chunk culling: surviving chunks tested again by their 8-point sub-chunks
+    int hiz;             // chunk culling: box tests read the bound pyramid (at most 4 words)
 };
 
 static VisVariant kSingle[] = {
@@ -572,6 +759,15 @@ static VisVariant kSingle[] = {
     {nullptr, true, "single/chunks/16/r", 0, 16, 1, 1},
     {nullptr, true, "single/chunks/16x2/r", 0, 16, 2, 1},
     {nullptr, true, "single/chunks/16x4/r", 0, 16, 4, 1},
+    {nullptr, true, "single/chunks/16/r/sub", 0, 16, 1, 1, 1},
+    {nullptr, true, "single/chunks/16x2/r/sub", 0, 16, 2, 1, 1},
+    {nullptr, true, "single/chunks/16x4/r/sub", 0, 16, 4, 1, 1},
+    {nullptr, true, "single/chunks/16x2/r/hiz", 0, 16, 2, 1, 0, 1},
+    {nullptr, true, "single/chunks/16/r/sub/hiz", 0, 16, 1, 1, 1, 1},
+    {nullptr, true, "single/chunks/16x2/r/sub/hiz", 0, 16, 2, 1, 1, 1},
+    {nullptr, true, "single/chunks/16x4/r/sub/hiz", 0, 16, 4, 1, 1, 1},
+    {nullptr, true, "single/chunks/32x2/r/sub/hiz", 0, 32, 2, 1, 1, 1},
+    {nullptr, true, "single/chunks/8x2/r/sub/hiz", 0, 8, 2, 1, 1, 1},
 };
 static VisVariant kMulti[] = {
     {visibility_kernel<false, true, 3, false>, false, "multi/prefetch/3", 0},
@@ -581,14 +777,26 @@ static VisVariant kMulti[] = {
     {nullptr, true, "multi/chunks/16", 0, 16, 1},
     {nullptr, true, "multi/chunks/16x2", 0, 16, 2},
     {nullptr, true, "multi/chunks/16x4", 0, 16, 4},
+    {nullptr, true, "multi/chunks/16x2/sub", 0, 16, 2, 0, 1},
+    {nullptr, true, "multi/chunks/16x2/sub/hiz", 0, 16, 2, 0, 1, 1},
 };
+
+typedef void (*ChunkFn)(const float*, uint64_t, const float*, RViews, const RViews*,
+                        const uint32_t*, int, uint32_t, uint32_t, uint32_t);
+template <bool SINGLE>
+static ChunkFn chunk_kernel_of(const VisVariant& v) {
+    if (v.hiz) return v.sub ? chunk_render_kernel<SINGLE, true, true> : chunk_render_kernel<SINGLE, false, true>;
+    return v.sub ? chunk_render_kernel<SINGLE, true, false> : chunk_render_kernel<SINGLE, false, false>;
+}
+static ChunkFn chunk_kernel(const VisVariant& v) {
+    return v.single ? chunk_kernel_of<true>(v) : chunk_kernel_of<false>(v);
+}
 
 static nrv_status resident_blocks(VisVariant& v) {
     if (v.blocks_per_sm) return NRV_OK;
     cudaFuncAttributes fa;
     if (v.fn) NRV_CHECK_CUDA(cudaFuncGetAttributes(&fa, v.fn));
-    else if (v.single) NRV_CHECK_CUDA(cudaFuncGetAttributes(&fa, chunk_render_kernel<true>));
-    else NRV_CHECK_CUDA(cudaFuncGetAttributes(&fa, chunk_render_kernel<false>));
+    else NRV_CHECK_CUDA(cudaFuncGetAttributes(&fa, chunk_kernel(v)));
     const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
     int b = 65536 / (regs_per_warp * 8);
     if (b > 8) b = 8;
@@ -603,13 +811,12 @@ static nrv_status run_variant(VisVariant& v, const float* xyz, uint64_t n,
                               const RViews& views, cudaStream_t s, const RViews* views_dev,
                               uint32_t* tiles, const void* chunks) {
     NRV_TRY(resident_blocks(v));
-    const size_t ntiles = visibility_scratch_bytes(views) / sizeof(uint32_t);
     if (v.chunk_S) {
         if (!tiles || !chunks) return fail(NRV_ERR_ARG, "chunk culling needs tiles and chunk bounds");
         const int blocks = g_vis_sms * v.blocks_per_sm;
         const float* ch = reinterpret_cast<const float*>(chunks);
         const uint32_t ngroups = (uint32_t)((chunk_count(n) + 31) / 32);
-        auto kern = v.single ? chunk_render_kernel<true> : chunk_render_kernel<false>;
+        const ChunkFn kern = chunk_kernel(v);
         kern<<<blocks, 256, 0, s>>>(xyz, n, ch, views, views_dev, nullptr, 1, v.chunk_S, 0u, 0u);
         NRV_CHECK_LAUNCH();
         // the chunk groups in `phases` consecutive parts, the tile bounds rebuilt from the
@@ -617,8 +824,7 @@ static nrv_status run_variant(VisVariant& v, const float* xyz, uint64_t n,
         for (int ph = 0; ph < v.phases; ++ph) {
             const uint32_t g0 = (uint32_t)((uint64_t)ngroups * ph / v.phases);
             const uint32_t g1 = (uint32_t)((uint64_t)ngroups * (ph + 1) / v.phases);
-            tile_bound_kernel<<<(unsigned)((ntiles * 32 + 255) / 256), 256, 0, s>>>(views, views_dev, tiles);
-            NRV_CHECK_LAUNCH();
+            NRV_TRY(launch_tile_bounds(views, views_dev, tiles, v.hiz != 0, s));
             kern<<<blocks, 256, 0, s>>>(xyz, n, ch, views, views_dev, tiles, 0, v.chunk_S, g0, g1);
             NRV_CHECK_LAUNCH();
         }
@@ -637,8 +843,7 @@ static nrv_status run_variant(VisVariant& v, const float* xyz, uint64_t n,
     if (!v.cull || !tiles || ngroups < 64) return launch(0, ngroups, n, nullptr);
     const uint64_t gsub = ngroups / 16;
     NRV_TRY(launch(0, gsub, 4 * gsub, nullptr));
-    tile_bound_kernel<<<(unsigned)((ntiles * 32 + 255) / 256), 256, 0, s>>>(views, views_dev, tiles);
-    NRV_CHECK_LAUNCH();
+    NRV_TRY(launch_tile_bounds(views, views_dev, tiles, false, s));
     return launch(gsub, ngroups, n, tiles);
 }
 
