@@ -308,27 +308,33 @@ __global__ void tile_bound_kernel(RViews vs_arg, const RViews* __restrict__ view
     if (lane == 0) out[t] = m;
 }
 
-// Levels 1.. of the bound pyramids: one thread per word, the maximum over its level-0 tiles.
+// Levels 1.. of the bound pyramids: one warp per word, its lanes taking the maximum over the
+// word's level-0 tiles.
 __global__ void tile_pyramid_kernel(RViews vs_arg, const RViews* __restrict__ views_dev,
                                     uint32_t* __restrict__ bound) {
     const RViews& vs = views_dev ? *views_dev : vs_arg;
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / 32);
+    const int lane = threadIdx.x & 31;
     uint32_t* pyr = bound;
     for (int v = 0; v < vs.n; ++v) {
         const TileDims d = tile_dims(vs.v[v].width, vs.v[v].height);
         const int coarse = d.words - d.off[1];
         if (t < coarse) {
-            int l = 1;
-            while (l + 1 < HIZ_LEVELS && t >= d.off[l + 1] - d.off[1]) ++l;
-            const int i = t - (d.off[l] - d.off[1]);
+            int l = 1, lo = 0;
+            for (int k = 2; k < HIZ_LEVELS; ++k)
+                if (t >= d.off[k] - d.off[1]) {
+                    l = k;
+                    lo = d.off[k] - d.off[1];
+                }
+            const int i = t - lo;
             const int wl = ((d.w0 - 1) >> l) + 1;
             const int x0 = (i % wl) << l, y0 = (i / wl) << l;
-            const int x1 = min(x0 + (1 << l), d.w0), y1 = min(y0 + (1 << l), d.h0);
+            const int nx = min(x0 + (1 << l), d.w0) - x0, ny = min(y0 + (1 << l), d.h0) - y0;
             uint32_t m = 0;
-            for (int y = y0; y < y1; ++y)
-                for (int x = x0; x < x1; ++x) m = max(m, pyr[y * d.w0 + x]);
-            pyr[d.off[l] + i] = m;
-            return;
+            for (int q = lane; q < nx * ny; q += 32) m = max(m, pyr[(y0 + q / nx) * d.w0 + x0 + q % nx]);
+            m = __reduce_max_sync(0xffffffffu, m);
+            if (lane == 0) pyr[d.off[1] + t] = m;
+            return;      // whole warps leave together
         }
         t -= coarse;
         pyr += d.words;
@@ -352,7 +358,7 @@ static nrv_status launch_tile_bounds(const RViews& views, const RViews* views_de
     tile_bound_kernel<<<(unsigned)((level0 * 32 + 255) / 256), 256, 0, s>>>(views, views_dev, tiles);
     NRV_CHECK_LAUNCH();
     if (hiz) {
-        tile_pyramid_kernel<<<(unsigned)((coarse + 255) / 256), 256, 0, s>>>(views, views_dev, tiles);
+        tile_pyramid_kernel<<<(unsigned)((coarse * 32 + 255) / 256), 256, 0, s>>>(views, views_dev, tiles);
         NRV_CHECK_LAUNCH();
     }
     return NRV_OK;
@@ -742,6 +748,7 @@ struct VisVariant {
     int single;          // chunk culling, one view: the view's parameters held in registers
     int sub;             // chunk culling: surviving chunks tested again by their 8-point sub-chunks
     int hiz;             // chunk culling: box tests read the bound pyramid (at most 4 words)
+    int first_part;      // chunk culling, two parts: the first part's share in percent (0: equal)
 };
 
 static VisVariant kSingle[] = {
@@ -768,6 +775,8 @@ static VisVariant kSingle[] = {
     {nullptr, true, "single/chunks/16x4/r/sub/hiz", 0, 16, 4, 1, 1, 1},
     {nullptr, true, "single/chunks/32x2/r/sub/hiz", 0, 32, 2, 1, 1, 1},
     {nullptr, true, "single/chunks/8x2/r/sub/hiz", 0, 8, 2, 1, 1, 1},
+    {nullptr, true, "single/chunks/16x2/r/sub/hiz/33", 0, 16, 2, 1, 1, 1, 33},
+    {nullptr, true, "single/chunks/16x2/r/sub/hiz/25", 0, 16, 2, 1, 1, 1, 25},
 };
 static VisVariant kMulti[] = {
     {visibility_kernel<false, true, 3, false>, false, "multi/prefetch/3", 0},
@@ -822,8 +831,13 @@ static nrv_status run_variant(VisVariant& v, const float* xyz, uint64_t n,
         // the chunk groups in `phases` consecutive parts, the tile bounds rebuilt from the
         // keys so far before each part (later parts meet tighter bounds)
         for (int ph = 0; ph < v.phases; ++ph) {
-            const uint32_t g0 = (uint32_t)((uint64_t)ngroups * ph / v.phases);
-            const uint32_t g1 = (uint32_t)((uint64_t)ngroups * (ph + 1) / v.phases);
+            uint32_t g0 = (uint32_t)((uint64_t)ngroups * ph / v.phases);
+            uint32_t g1 = (uint32_t)((uint64_t)ngroups * (ph + 1) / v.phases);
+            if (v.phases == 2 && v.first_part) {
+                const uint32_t cut = (uint32_t)((uint64_t)ngroups * v.first_part / 100);
+                g0 = ph ? cut : 0u;
+                g1 = ph ? ngroups : cut;
+            }
             NRV_TRY(launch_tile_bounds(views, views_dev, tiles, v.hiz != 0, s));
             kern<<<blocks, 256, 0, s>>>(xyz, n, ch, views, views_dev, tiles, 0, v.chunk_S, g0, g1);
             NRV_CHECK_LAUNCH();
