@@ -30,7 +30,7 @@ BYTES_PER_POINT = 12.0          # xyz read once per frame for every view
 # DRAM bytes the render pass of the 350M-point 1080p trajectory frame moves (one ncu capture of
 # its seven launches: every chunk box, the sub-chunk boxes of surviving chunks, the positions of
 # the prepass chunks and of the surviving sub-chunks, tile-bound reads, atomics)
-RENDER_TRAFFIC_BYTES = 1.2804e9
+RENDER_TRAFFIC_BYTES = 1.2343e9
 # host -> device bytes of one replayed nrv_render_batch frame: the library's table of the views
 # (8 slots of 88 bytes and a count, 712 bytes), copied whole whatever the view count
 VIEW_TABLE_BYTES = 712
@@ -869,7 +869,7 @@ def main():
             "traffic": RENDER_TRAFFIC_BYTES if known else None,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum summed over the "
                               "render pass's seven launches of one frame (variant "
-                              "single/chunks/16x2/r/sub/hiz), "
+                              "single/chunks/16x2/r/sub/hiz/33), "
                               "profiles/render_pass_dram_traffic_trajectories_350m_1080p.md",
             "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": RENDER_TRAFFIC_BYTES if known else sc.n * BYTES_PER_POINT,
