@@ -219,6 +219,19 @@ struct SlotCursor {
     }
 };
 
+// Two floats as a BF16 pair (lo in the low half), rounded to nearest; with relu, negative
+// values (and -0) become +0 in the same conversion.
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+__device__ __forceinline__ uint32_t bf16x2_relu(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
 // Ring position (slot, phase parity of its use) advanced without divisions.
 __device__ __forceinline__ void ring_next(int& slot, uint32_t& phase, int nslot) {
     if (++slot == nslot) {
@@ -891,16 +904,14 @@ __global__ void __launch_bounds__(STREAM ? NTHREADS_S : NTHREADS, STREAM ? 2 : 4
                             u1 = gate(u1, __uint_as_float(ga[2 * j + 1]) + gq[2 * j + 1]);
                             w0 = gate(w0, __uint_as_float(gb[2 * j]) + gq[2 * j]);
                             w1 = gate(w1, __uint_as_float(gb[2 * j + 1]) + gq[2 * j + 1]);
-                        } else if (relu) {
-                            u0 = fmaxf(u0, 0.0f);
-                            u1 = fmaxf(u1, 0.0f);
-                            w0 = fmaxf(w0, 0.0f);
-                            w1 = fmaxf(w1, 0.0f);
                         }
-                        __nv_bfloat162 h2 = __floats2bfloat162_rn(u0, u1);
-                        pa[j] = *reinterpret_cast<uint32_t*>(&h2);
-                        h2 = __floats2bfloat162_rn(w0, w1);
-                        pb[j] = *reinterpret_cast<uint32_t*>(&h2);
+                        if (!GATED && relu) {
+                            pa[j] = bf16x2_relu(u0, u1);
+                            pb[j] = bf16x2_relu(w0, w1);
+                        } else {
+                            pa[j] = bf16x2(u0, u1);
+                            pb[j] = bf16x2(w0, w1);
+                        }
                     }
                 }
                 if (FP8) {
@@ -1084,15 +1095,9 @@ __global__ void __launch_bounds__(STREAM ? NTHREADS_S : NTHREADS, STREAM ? 2 : 4
                             v[e] = __uint_as_float(f1[q]);
                             u[e] += bq[q];
                             v[e] += bq[q];
-                            if (P.relu) {
-                                u[e] = fmaxf(u[e], 0.0f);
-                                v[e] = fmaxf(v[e], 0.0f);
-                            }
                         }
-                        __nv_bfloat162 h2 = __floats2bfloat162_rn(u[0], u[1]);
-                        p0[j] = *reinterpret_cast<uint32_t*>(&h2);
-                        h2 = __floats2bfloat162_rn(v[0], v[1]);
-                        p1[j] = *reinterpret_cast<uint32_t*>(&h2);
+                        p0[j] = P.relu ? bf16x2_relu(u[0], u[1]) : bf16x2(u[0], u[1]);
+                        p1[j] = P.relu ? bf16x2_relu(v[0], v[1]) : bf16x2(v[0], v[1]);
                     }
                     if (valid) {
                         uint4* dst = reinterpret_cast<uint4*>(prow + (size_t)(o8 / 8) * wo * 16);
