@@ -216,7 +216,12 @@ __global__ void __launch_bounds__(256, MINB) visibility_kernel(const float4* __r
         const float pz[4] = {a.z, b.y, c.x, c.w};
         const uint32_t i0 = 4 * g + vs.base;
         for (int v = 0; v < (SINGLE ? 1 : vs.n); ++v) {
-            const RView& vw = SINGLE ? v0 : vs.v[v];
+            // several views: this view's parameters read from shared memory once into
+            // registers for the four points (read per use, they made a third of the L1
+            // wavefronts of the pass)
+            RView vcopy;
+            if (!SINGLE) vcopy = vs.v[v];
+            const RView& vw = SINGLE ? v0 : vcopy;
             uint32_t pix[4], db[4];
             unsigned long long cur[4];
             bool ok[4];
