@@ -185,6 +185,8 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-fp8", action="store_true")
     ap.add_argument("--no-gated", action="store_true")
+    ap.add_argument("--terrain-grid", type=int, default=14142,
+                    help="c4: terrain points per side (14142: 200M points; smaller for profiling)")
     ap.add_argument("--config", default="c3", choices=["c3", "c2", "c4", "c5", "train"],
                     help="c3 (default): the 350M-point trajectory frame; c2: 50M-point vortex grid "
                          "frame with network precision vs FP64; c4: 200M-point terrain, 8 views of "
@@ -473,7 +475,7 @@ def run_c4(a):
     from paper_2407_19097_gb300 import nrv
     dev = torch.device("cuda", 0)
     t0 = time.time()
-    sc = I.terrain_scene(14142, seed=7)
+    sc = I.terrain_scene(a.terrain_grid, seed=7)
     sizes = [(2160, 2160), (2160, 2160), (1920, 1080), (1920, 1080), (1920, 1080), (1920, 1080),
              (960, 540), (960, 540)]
     views = I.orbit_views(sc, sizes, seed=11, stereo_pairs=1)
@@ -495,7 +497,7 @@ def run_c4(a):
     st = nrv.timings()
     px = sum(v.width * v.height for v in views)
     line = {"config": "c4", "metric": "aggregate point-views/s and frames/s, 8 views",
-            "workload": f"terrain 14142^2 = {sc.n} points, 8 views {sizes}", "data": "synthetic",
+            "workload": f"terrain {a.terrain_grid}^2 = {sc.n} points, 8 views {sizes}", "data": "synthetic",
             "value": sc.n * len(views) / (ms * 1e-3), "unit": "point-views/s",
             "frames_per_s": len(views) / (ms * 1e-3), "batch_ms": ms, "pixels_per_batch": px,
             "stages_ms": {"clear": st[0], "render_pass_all_views": st[1], "resolve_pack": st[2],
