@@ -166,6 +166,25 @@ def test_scene_refresh_after_points_move():
     _every_variant(dataclasses.replace(sc, xyz=xyz), [v], scene)
 
 
+def test_partly_visible_chunks_every_variant():
+    """One 8-point sub-chunk of every 5th 32-point chunk pulled towards the camera: those
+    chunks are visible through one sub-chunk only, so a sub-chunk test that dropped the wrong
+    one (or a tile-bound pyramid word below a pixel it covers) would lose keys."""
+    import dataclasses
+    sc = I.trajectory_scene(20000, 50, seed=5)          # 1M points: chunks mostly hidden
+    v = I.fitted_view(sc, 640, 480)
+    xyz = sc.xyz.copy()
+    eye = np.asarray(v.eye, np.float32)
+    idx = np.arange(len(xyz))
+    chunk, sub = idx // 32, (idx // 8) % 4
+    sel = (chunk % 5 == 2) & (sub == (chunk // 5) % 4)
+    xyz[sel] = 0.6 * xyz[sel] + 0.4 * eye
+    refs = _every_variant(dataclasses.replace(sc, xyz=xyz), [v])
+    # the moved points win a good share of the pixels they reach
+    moved = np.isin(refs[0][0] & 0xFFFFFFFF, idx[sel])
+    assert moved.sum() > 1000
+
+
 def test_points_on_pixel_edges_every_variant(simple_view):
     """Points whose projections fall on or within a few ulps of pixel and screen edges, where
     the fast quotient cannot decide the pixel and the exact division must: keys and planes
