@@ -429,7 +429,8 @@ nrv_status launch_chunk_bounds(const float* xyz, uint64_t n, void* chunks, cudaS
 }
 
 // True when no point in the box (c, e) can set a key of view v, given the tile
-// depth bounds (null: depth range and screen only).  Allowances: 1e-5 of the
+// depth bounds (null: depth range and screen only; HIZ: the view's bound pyramid,
+// read at one level, else its level-0 tiles).  Allowances: 1e-5 of the
 // magnitudes summed in each clip coordinate covers the rounding of the points'
 // own FP32 sequences and of this arithmetic (both below 1e-6 of that sum); the
 // screen rectangle is widened by half a pixel plus 1e-5 of its extent.
@@ -495,9 +496,10 @@ __device__ __forceinline__ bool chunk_hidden(const RView& v, const float* c, con
 
 // Chunk-culling render pass (SINGLE: one view, its parameters held in registers rather than
 // read from shared memory for every point).  S is a power of two.  prepass != 0: chunks 0, S,
-// 2S, ... in full, one warp per chunk, one point per lane.  prepass == 0: every other chunk of the
-// groups [g_begin, g_end), 32 chunks per warp step -- each lane tests one chunk against every view and the
-// survivors join the warp's queue in shared memory; whenever four are queued the
+// 2S, ... in full, four per warp step, one point of each per lane.  prepass == 0: every other
+// chunk of the groups [g_begin, g_end), 32 chunks per warp step -- each lane tests one chunk
+// against every view and the survivors join the warp's queue in shared memory; whenever four
+// are queued the
 // warp renders them (each lane takes one point of each, so four early depth
 // reads are in flight per lane).  Rendering only full groups of four keeps the
 // lanes busy: a group costs the same instructions however many chunks it holds.
