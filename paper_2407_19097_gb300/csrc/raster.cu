@@ -795,6 +795,7 @@ static VisVariant kMulti[] = {
     {nullptr, true, "multi/chunks/16x4", 0, 16, 4},
     {nullptr, true, "multi/chunks/16x2/sub", 0, 16, 2, 0, 1},
     {nullptr, true, "multi/chunks/16x2/sub/hiz", 0, 16, 2, 0, 1, 1},
+    {visibility_kernel<false, false, 4, false>, false, "multi/plain/4", 0},
 };
 
 typedef void (*ChunkFn)(const float*, uint64_t, const float*, RViews, const RViews*,
