@@ -14,12 +14,50 @@
 // front of it; keys only ever decrease, so a stale read only costs an atomic.
 #include <stdio.h>
 #include <stdlib.h>
+#include <string.h>
+
+#include <utility>
 
 #include "internal.h"
 
 namespace nrv {
 
+// Programmatic dependent launch inside the chunk-culling render pass (unless NRV_PDL=0): each
+// of its kernels is launched while the previous one drains and waits (griddepcontrol.wait)
+// for it to complete before reading anything it wrote; the kernel before the pass lets it
+// start early.  Both instructions do nothing for a plain launch.
+__device__ __forceinline__ void pdl_wait_and_release() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+static bool render_pdl() {
+    static int on = -1;
+    if (on < 0) {
+        const char* e = getenv("NRV_PDL");
+        on = (e && e[0] == '0') ? 0 : 1;
+    }
+    return on == 1;
+}
+template <typename... KArgs, typename... Args>
+static nrv_status launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
+                             Args&&... args) {
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = render_pdl() ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    NRV_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
+    NRV_CHECK_LAUNCH();
+    return NRV_OK;
+}
+
 __global__ void clear_keys_kernel(RViews vs) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int v = blockIdx.y;
     if (v >= vs.n) return;
     const uint64_t npx = (uint64_t)vs.v[v].width * vs.v[v].height;
@@ -288,6 +326,7 @@ nrv_status launch_visibility_strided(const float* xyz, uint64_t n, int stride, c
 // (empty pixels hold ~0, so a tile with an empty pixel never culls).
 __global__ void tile_bound_kernel(RViews vs_arg, const RViews* __restrict__ views_dev,
                                   uint32_t* __restrict__ bound) {
+    pdl_wait_and_release();
     const RViews& vs = views_dev ? *views_dev : vs_arg;
     int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / 32);
     const int lane = threadIdx.x & 31;
@@ -317,6 +356,7 @@ __global__ void tile_bound_kernel(RViews vs_arg, const RViews* __restrict__ view
 // word's level-0 tiles.
 __global__ void tile_pyramid_kernel(RViews vs_arg, const RViews* __restrict__ views_dev,
                                     uint32_t* __restrict__ bound) {
+    pdl_wait_and_release();
     const RViews& vs = views_dev ? *views_dev : vs_arg;
     int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) / 32);
     const int lane = threadIdx.x & 31;
@@ -360,12 +400,11 @@ static nrv_status launch_tile_bounds(const RViews& views, const RViews* views_de
                                      bool hiz, cudaStream_t s) {
     size_t level0, coarse;
     tile_counts(views, level0, coarse);
-    tile_bound_kernel<<<(unsigned)((level0 * 32 + 255) / 256), 256, 0, s>>>(views, views_dev, tiles);
-    NRV_CHECK_LAUNCH();
-    if (hiz) {
-        tile_pyramid_kernel<<<(unsigned)((coarse * 32 + 255) / 256), 256, 0, s>>>(views, views_dev, tiles);
-        NRV_CHECK_LAUNCH();
-    }
+    NRV_TRY(launch_pdl(tile_bound_kernel, dim3((unsigned)((level0 * 32 + 255) / 256)), dim3(256), s,
+                       views, views_dev, tiles));
+    if (hiz)
+        NRV_TRY(launch_pdl(tile_pyramid_kernel, dim3((unsigned)((coarse * 32 + 255) / 256)), dim3(256),
+                           s, views, views_dev, tiles));
     return NRV_OK;
 }
 
@@ -516,6 +555,7 @@ __global__ void __launch_bounds__(256, 4) chunk_render_kernel(const float* __res
                                                            const uint32_t* __restrict__ bound,
                                                            int prepass, uint32_t S, uint32_t g_begin,
                                                            uint32_t g_end) {
+    pdl_wait_and_release();
     __shared__ RViews vs;
     __shared__ int tile_off[8];
     __shared__ TileDims tdim[8];
@@ -834,8 +874,8 @@ static nrv_status run_variant(VisVariant& v, const float* xyz, uint64_t n,
         const float* ch = reinterpret_cast<const float*>(chunks);
         const uint32_t ngroups = (uint32_t)((chunk_count(n) + 31) / 32);
         const ChunkFn kern = chunk_kernel(v);
-        kern<<<blocks, 256, 0, s>>>(xyz, n, ch, views, views_dev, nullptr, 1, v.chunk_S, 0u, 0u);
-        NRV_CHECK_LAUNCH();
+        NRV_TRY(launch_pdl(kern, dim3(blocks), dim3(256), s, xyz, n, ch, views, views_dev,
+                           (const uint32_t*)nullptr, 1, v.chunk_S, 0u, 0u));
         // the chunk groups in `phases` consecutive parts, the tile bounds rebuilt from the
         // keys so far before each part (later parts meet tighter bounds)
         for (int ph = 0; ph < v.phases; ++ph) {
@@ -847,8 +887,8 @@ static nrv_status run_variant(VisVariant& v, const float* xyz, uint64_t n,
                 g1 = ph ? ngroups : cut;
             }
             NRV_TRY(launch_tile_bounds(views, views_dev, tiles, v.hiz != 0, s));
-            kern<<<blocks, 256, 0, s>>>(xyz, n, ch, views, views_dev, tiles, 0, v.chunk_S, g0, g1);
-            NRV_CHECK_LAUNCH();
+            NRV_TRY(launch_pdl(kern, dim3(blocks), dim3(256), s, xyz, n, ch, views, views_dev,
+                               (const uint32_t*)tiles, 0, v.chunk_S, g0, g1));
         }
         return NRV_OK;
     }
