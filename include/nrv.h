@@ -114,7 +114,10 @@ uint64_t nrv_launch_count(void);
  * view (multi_view = 0) or a batch of views (multi_view != 0).  All variants
  * compute the same keys; the library times them on the first large launch and
  * keeps the fastest.  Setting the environment variable NRV_VIS_VARIANT to an
- * index below this count pins that variant (used to check each one). */
+ * index below this count pins that variant (used to check each one).  The
+ * kernels of the chunk-culling variants and the tensor-core network layers are
+ * launched as programmatic dependents of their predecessors (each waits for the
+ * previous kernel before reading its results); NRV_PDL=0 launches them plainly. */
 int nrv_render_variants(int multi_view);
 
 /* --------------------------------------------------------------------------
